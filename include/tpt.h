@@ -1,0 +1,183 @@
+/*
+ * tpt.h -- C ABI of the GB300 tensor-product--Thomas Poisson/Helmholtz solver.
+ *
+ * The library solves, on one GPU, the constant-coefficient problem
+ *
+ *     (alpha I + beta L) phi = f
+ *
+ * on a staggered, cell-centred Cartesian grid with non-uniform spacing in every
+ * direction (paper Sec. 2.2).  L is the Kronecker sum of the three 1D
+ * second-difference operators of Eq. (poisson-fd2)/(tridiagonal-coefficients)
+ * (Sec. 2.2.2).  Poisson is (alpha, beta) = (0, 1); the Crank--Nicolson
+ * Helmholtz problem of Sec. 2.1 is (1, -gamma nu dt / 2).  The x and y
+ * operators are diagonalised in their numerical eigenbases (Sec. 2.2.1,
+ * Eq. reverse-similarity-transform, Eq. q-from-tildeq), or by FFT/DCT in a
+ * uniform direction; one tridiagonal system per (i, j) mode pair remains along
+ * z and is solved by the Thomas algorithm (Sec. 2.2.2, solution steps 2.1-2.5;
+ * Algorithm 1 steps 1, 3, 5, 7, 9).
+ *
+ * Conventions shared by every entry point:
+ *  - Fields are float64, Fortran order (Nx, Ny, Nz): x fastest, element
+ *    (i, j, k) at i + Nx*(j + Ny*k).
+ *  - Every call returns an int status (TPT_OK = 0); no exception or abort
+ *    crosses the ABI.  tpt_status_string() names a status.
+ *  - Pointers named *_dev are device pointers on the plan's device; pointers
+ *    named *_host are host pointers.  The caller owns every buffer it passes;
+ *    the plan owns only its own device tables (eigenbases, eigenvalues,
+ *    operator rows) and frees them in tpt_plan_destroy().
+ *  - Calls taking a `stream` (a cudaStream_t passed as void*, NULL = legacy
+ *    default stream) are asynchronous on that stream unless stated otherwise.
+ */
+#ifndef TPT_H
+#define TPT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define TPT_OK                 0
+#define TPT_ERR_INVALID_ARG    1  /* null pointer, size <= 0, bad enum, bad spacing */
+#define TPT_ERR_UNSUPPORTED    2  /* valid request this build does not implement    */
+#define TPT_ERR_OOM            3  /* device allocation failed                        */
+#define TPT_ERR_CUDA           4  /* a CUDA runtime/driver call failed               */
+#define TPT_ERR_NOT_CONVERGED  5  /* refinement did not reach rtol in max_refine     */
+#define TPT_ERR_TIMEOUT        6  /* a bounded device-side wait gave up              */
+#define TPT_ERR_NONFINITE      7  /* NaN/Inf in the right-hand side or residual      */
+#define TPT_ERR_NUMERICAL      8  /* eigensolver failed or null pivot did not vanish */
+
+/* ---- enumerations ---------------------------------------------------- */
+/* Boundary rows of Sec. 2.2.1 ("modified as required by the boundary
+ * conditions"): Neumann drops the outside coupling; periodic keeps it as the
+ * cyclic corner (set on both ends); homogeneous Dirichlet (zero wall value at
+ * the face) drops it and adds 2/dx^2 to -b of that row.                    */
+enum { TPT_BC_PERIODIC = 0, TPT_BC_NEUMANN = 1, TPT_BC_DIRICHLET = 2 };
+
+/* Transform of a diagonalised direction (x or y), Sec. 3: numerical eigenbasis
+ * applied as a GEMM, or the Fourier-based transform of a uniform direction
+ * (real DFT for periodic, DCT-II/III for Neumann-Neumann).  AUTO picks FFT
+ * when the spacing is uniform and the boundary pair has a fast transform.  */
+enum { TPT_XFORM_AUTO = 0, TPT_XFORM_GEMM = 1, TPT_XFORM_FFT = 2 };
+
+/* Arithmetic of the transforms and the Thomas sweep.  FP64: float64
+ * throughout.  MIXED_*: correction solves with the transforms on the tensor
+ * cores (BF16, split BF16 with three products, or TF32; FP32 accumulation),
+ * FP32 Thomas except the singular null line (float64), and a float64
+ * residual driving iterative refinement to `rtol`.                          */
+enum { TPT_PREC_FP64 = 0, TPT_PREC_MIXED_BF16 = 1, TPT_PREC_MIXED_BF16X3 = 2,
+       TPT_PREC_MIXED_TF32 = 3 };
+
+/* ---- plan ------------------------------------------------------------ */
+typedef struct tpt_plan_s* tpt_plan;
+
+typedef struct {
+  int n[3];              /* Nx, Ny, Nz >= 1                                        */
+  const double* dxf[3];  /* host, n[d] cell widths dx_i > 0 (copied at create)     */
+  const double* dxc[3];  /* host, n[d]+1 centre spacings: dxc[i] = distance between
+                            the centres of cells i-1 and i (1 <= i < n); dxc[0] and
+                            dxc[n] are the wrap spacing, read only when periodic   */
+  int bc[3][2];          /* lower/upper boundary per direction (TPT_BC_*)          */
+  int xform[2];          /* transform for x and y (TPT_XFORM_*); z is Thomas       */
+  double alpha, beta;    /* operator alpha I + beta L                              */
+  int precision;         /* TPT_PREC_*                                             */
+  double rtol;           /* refinement target ||f - A phi||_2 / ||f||_2; <= 0 runs
+                            exactly max_refine refinement steps with no host sync  */
+  int max_refine;        /* refinement steps after the first solve (>= 0)          */
+} tpt_desc;
+
+typedef struct {
+  int iters;             /* correction solves performed (first solve included)     */
+  double rel_residual;   /* last ||f - A phi||_2 / ||f||_2 (f after projection);
+                            -1 when no residual was evaluated                      */
+  double compat_defect;  /* singular problems: cell-volume-weighted mean removed
+                            from f to make it compatible; 0 otherwise              */
+  float ms_stage[8];     /* reserved for per-stage timings (0 unless measured)     */
+} tpt_info;
+
+/* Build a plan on CUDA device `cuda_device` (or, with cuda_device < 0, a
+ * host-only plan holding the setup tables for inspection through
+ * tpt_plan_eigenvalues / tpt_plan_rows; every device entry point rejects it
+ * with INVALID_ARG).  Setup: 1D rows with boundary rows,
+ * symmetrisation D^{1/2} T D^{-1/2}, symmetric eigendecomposition on the host
+ * in float64 with eigenvalues refined as long-double Rayleigh quotients, the
+ * forward/inverse transform matrices Q^{-1} = Q~^T D^{1/2}, Q = D^{-1/2} Q~
+ * (Sec. 2.2.1 steps 1.1-1.3; Algorithm 1 initialisation), and their upload.
+ * Synchronous.  Errors: INVALID_ARG (bad descriptor), UNSUPPORTED (FFT on a
+ * non-uniform direction, periodic z), NUMERICAL (eigensolver did not
+ * converge), OOM, CUDA.  On error *out is set to NULL.                    */
+int tpt_plan_create(const tpt_desc* desc, int cuda_device, tpt_plan* out);
+
+/* Bytes of device workspace tpt_solve() needs (256-byte aligned).          */
+int tpt_workspace_bytes(tpt_plan plan, size_t* bytes);
+
+/* Solve (alpha I + beta L) phi = f.  f_dev and phi_dev hold Nx*Ny*Nz float64
+ * (phi_dev may equal f_dev); work_dev holds tpt_workspace_bytes() bytes, is
+ * 256-byte aligned and is not used concurrently by another call.  With
+ * rtol > 0 the call reads the residual norm on the host after every
+ * correction (so it synchronises `stream`) and stops at rtol; otherwise it
+ * runs 1 + max_refine corrections asynchronously.  A singular problem
+ * (alpha = 0, every direction periodic or Neumann-Neumann) is solved for the
+ * solution with zero cell-volume-weighted mean after removing that mean from
+ * f.  `info` may be NULL; it is filled when the call returns if rtol > 0,
+ * else after `stream` is synchronised.  Errors: INVALID_ARG, CUDA,
+ * NOT_CONVERGED (phi holds the last iterate), NONFINITE, TIMEOUT.          */
+int tpt_solve(tpt_plan plan, const double* f_dev, double* phi_dev, void* work_dev,
+              void* stream, tpt_info* info);
+
+/* End-to-end solve from host memory: copies f_host to the device, solves, and
+ * copies phi back to phi_host, all on `stream`; returns after the stream is
+ * synchronised.  Device buffers: f_dev/phi_dev staging of Nx*Ny*Nz doubles
+ * (may be equal) and work_dev as for tpt_solve().  Pinned host memory gives
+ * full copy bandwidth.                                                     */
+int tpt_solve_host(tpt_plan plan, const double* f_host, double* phi_host, double* f_dev,
+                   double* phi_dev, void* work_dev, void* stream, tpt_info* info);
+
+/* Change alpha and beta of an existing plan: the eigenbases do not depend on
+ * them (Sec. 2.2.2: Poisson and Helmholtz share eigenvectors; Helmholtz is a
+ * modal shift).  Not to be called while a solve on this plan is in flight.  */
+int tpt_set_coefficients(tpt_plan plan, double alpha, double beta);
+
+int tpt_plan_destroy(tpt_plan plan);
+const char* tpt_status_string(int status);
+
+/* ---- single steps of the solve (the same kernels tpt_solve launches) ---- */
+/* Forward or inverse transform along x (dir = 0) or y (dir = 1) in float64:
+ * forward applies Q^{-1} (Eq. forward-xy), inverse applies Q (Eq. inverse-xy),
+ * with whichever transform the plan chose for that direction.  in_dev and
+ * out_dev hold Nx*Ny*Nz doubles and must not overlap.                      */
+int tpt_transform(tpt_plan plan, int dir, int inverse, const double* in_dev, double* out_dev,
+                  void* stream);
+
+/* Modal tridiagonal solve along z for every (i, j) (solution step 2.3):
+ * (alpha + beta(lx_i + ly_j)) phi + beta T_z phi = fhat, float64, in place
+ * allowed.  For a singular problem the null line is projected to compatible
+ * form, its last modal unknown set to zero and the line shifted to zero
+ * dz-weighted mean.  scratch_dev holds Nx*Ny*Nz doubles.                   */
+int tpt_thomas(tpt_plan plan, const double* fhat_dev, double* phihat_dev, double* scratch_dev,
+               void* stream);
+
+/* r = f - (alpha I + beta L) phi with the 7-point stencil of the plan's 1D rows
+ * (Sec. 4.1 residual), float64.  sums_dev (may be NULL) receives 3 doubles:
+ * sum r^2, sum r, sum vol*r.                                               */
+int tpt_residual(tpt_plan plan, const double* f_dev, const double* phi_dev, double* r_dev,
+                 double* sums_dev, void* stream);
+
+/* Host copies of the plan's tables, for inspection and tests.  lam: n[dir]
+ * eigenvalues of direction dir (0 = x, 1 = y) in the plan's mode order;
+ * a, b, c: the 1D rows of direction dir (0..2), n[dir] each.              */
+int tpt_plan_eigenvalues(tpt_plan plan, int dir, double* lam_host);
+int tpt_plan_rows(tpt_plan plan, int dir, double* a_host, double* b_host, double* c_host);
+
+/* ---- grid helper -------------------------------------------------------- */
+/* Cell widths and centre spacings of an n-cell grid on [0, L] whose faces are
+ * x(k/n), k = 0..n, of Eq. (tanh_stretching) (Sec. 4.1); stretch = 0 is the
+ * uniform grid.  dxf_out: n doubles; dxc_out: n+1 doubles with the wrap
+ * spacing (dx_0 + dx_{n-1})/2 at both ends.                               */
+int tpt_grid_tanh(int n, double L, double stretch, double* dxf_out, double* dxc_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TPT_H */

@@ -1,0 +1,103 @@
+"""ctypes binding of libtpt.so: the C ABI of include/tpt.h under the same names.
+
+Argument marshalling only.  Every step of a solve runs in the library's CUDA
+kernels; there is no Python or CPU fallback.  Importing this module on a
+machine where libtpt.so is missing raises ImportError.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import build as _build
+
+TPT_OK = 0
+TPT_ERR_INVALID_ARG = 1
+TPT_ERR_UNSUPPORTED = 2
+TPT_ERR_OOM = 3
+TPT_ERR_CUDA = 4
+TPT_ERR_NOT_CONVERGED = 5
+TPT_ERR_TIMEOUT = 6
+TPT_ERR_NONFINITE = 7
+TPT_ERR_NUMERICAL = 8
+
+TPT_BC_PERIODIC, TPT_BC_NEUMANN, TPT_BC_DIRICHLET = 0, 1, 2
+TPT_XFORM_AUTO, TPT_XFORM_GEMM, TPT_XFORM_FFT = 0, 1, 2
+TPT_PREC_FP64, TPT_PREC_MIXED_BF16, TPT_PREC_MIXED_BF16X3, TPT_PREC_MIXED_TF32 = 0, 1, 2, 3
+
+_dp = C.POINTER(C.c_double)
+
+
+class tpt_desc(C.Structure):
+    _fields_ = [
+        ("n", C.c_int * 3),
+        ("dxf", _dp * 3),
+        ("dxc", _dp * 3),
+        ("bc", (C.c_int * 2) * 3),
+        ("xform", C.c_int * 2),
+        ("alpha", C.c_double),
+        ("beta", C.c_double),
+        ("precision", C.c_int),
+        ("rtol", C.c_double),
+        ("max_refine", C.c_int),
+    ]
+
+
+class tpt_info(C.Structure):
+    _fields_ = [
+        ("iters", C.c_int),
+        ("rel_residual", C.c_double),
+        ("compat_defect", C.c_double),
+        ("ms_stage", C.c_float * 8),
+    ]
+
+
+# (name, restype, argtypes) of every entry point declared in include/tpt.h
+SIGNATURES = [
+    ("tpt_plan_create", C.c_int, [C.POINTER(tpt_desc), C.c_int, C.POINTER(C.c_void_p)]),
+    ("tpt_workspace_bytes", C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
+    ("tpt_solve", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                            C.POINTER(tpt_info)]),
+    ("tpt_solve_host", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                 C.c_void_p, C.c_void_p, C.POINTER(tpt_info)]),
+    ("tpt_set_coefficients", C.c_int, [C.c_void_p, C.c_double, C.c_double]),
+    ("tpt_plan_destroy", C.c_int, [C.c_void_p]),
+    ("tpt_status_string", C.c_char_p, [C.c_int]),
+    ("tpt_transform", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("tpt_thomas", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("tpt_residual", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                               C.c_void_p]),
+    ("tpt_plan_eigenvalues", C.c_int, [C.c_void_p, C.c_int, _dp]),
+    ("tpt_plan_rows", C.c_int, [C.c_void_p, C.c_int, _dp, _dp, _dp]),
+    ("tpt_grid_tanh", C.c_int, [C.c_int, C.c_double, C.c_double, _dp, _dp]),
+]
+
+LIB_PATH = _build.LIB
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libtpt.so is not built (%s); run __graft_entry__.build() or "
+                          "python -m paper_2603_09528_gb300.build" % LIB_PATH)
+    lib = C.CDLL(LIB_PATH)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+class TptError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = lib.tpt_status_string(status)
+        super().__init__("%s failed: %s (status %d)" % (where, msg.decode() if msg else "?", status))
+
+
+def check(status: int, where: str) -> int:
+    if status != TPT_OK:
+        raise TptError(status, where)
+    return status

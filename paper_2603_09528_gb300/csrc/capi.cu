@@ -1,0 +1,418 @@
+// C ABI of the solver: plan creation (host setup + upload), the solve driver
+// (transforms, modal Thomas, residual, iterative refinement) and the single-step
+// entry points.  Declarations and contracts: include/tpt.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "tpt_internal.h"
+
+using tpt::Dir1D;
+
+namespace {
+
+struct DeviceGuard {   // restores the caller's current device
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return TPT_OK;
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? TPT_ERR_OOM : TPT_ERR_CUDA;
+}
+
+#define TPT_TRY(expr)                 \
+  do {                                \
+    int st_ = (expr);                 \
+    if (st_ != TPT_OK) return st_;    \
+  } while (0)
+#define TPT_CUDA(expr) TPT_TRY(cuda_status(expr))
+
+template <typename T>
+int upload(tpt_plan_s* p, const std::vector<T>& h, T** d) {
+  void* ptr = nullptr;
+  const size_t bytes = h.size() * sizeof(T);
+  cudaError_t e = cudaMalloc(&ptr, bytes > 0 ? bytes : 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return TPT_ERR_OOM;
+  }
+  p->allocs.push_back(ptr);
+  *d = static_cast<T*>(ptr);
+  if (bytes) TPT_CUDA(cudaMemcpy(ptr, h.data(), bytes, cudaMemcpyHostToDevice));
+  return TPT_OK;
+}
+
+void free_plan(tpt_plan_s* p) {
+  if (!p) return;
+  if (p->dev >= 0 && (!p->allocs.empty() || p->h_ring)) {
+    DeviceGuard g(p->dev);
+    for (void* a : p->allocs) cudaFree(a);
+    if (p->h_ring) cudaFreeHost(p->h_ring);
+  }
+  delete p;
+}
+
+bool on_device(const tpt_plan_s* p) { return p && p->dev >= 0 && p->d_scal; }
+
+// Device matrices of one diagonalised direction for the float64 GEMM roles:
+//   x: C = A B with A = Q^{-1} (forward) or Q (inverse), column-major n x n;
+//   y: C_k = F_k B with B = (Q^{-1})^T (forward) or Q^T (inverse), column-major.
+int upload_basis(tpt_plan_s* p, int d) {
+  const int n = p->n[d];
+  const std::vector<double>& qt = p->eig[d].qt;   // Q~(i, p) at p*n + i
+  const std::vector<double>& dxf = p->dir[d].dxf;
+  std::vector<double> fwd(static_cast<size_t>(n) * n), inv(static_cast<size_t>(n) * n);
+  for (int m = 0; m < n; ++m) {        // mode
+    for (int i = 0; i < n; ++i) {      // grid point
+      const double s = std::sqrt(dxf[i]);
+      const double q = qt[static_cast<size_t>(m) * n + i];
+      const double qinv_mi = q * s;    // Q^{-1}(m, i) = Q~(i, m) sqrt(dx_i)
+      const double q_im = q / s;       // Q(i, m) = Q~(i, m) / sqrt(dx_i)
+      if (d == 0) {
+        fwd[m + static_cast<size_t>(n) * i] = qinv_mi;   // A(m, i), column-major
+        inv[i + static_cast<size_t>(n) * m] = q_im;      // A(i, m)
+      } else {
+        fwd[i + static_cast<size_t>(n) * m] = qinv_mi;   // B(k = i, n = m) = Q^{-1}(m, i)
+        inv[m + static_cast<size_t>(n) * i] = q_im;      // B(k = m, n = i) = Q(i, m)
+      }
+    }
+  }
+  TPT_TRY(upload(p, fwd, &p->ddir[d].fwd));
+  TPT_TRY(upload(p, inv, &p->ddir[d].inv));
+  TPT_TRY(upload(p, p->eig[d].lam, &p->ddir[d].lam));
+  return TPT_OK;
+}
+
+int apply_transform(const tpt_plan_s* p, int d, bool inverse, const double* in, double* out,
+                    bool accumulate, cudaStream_t s) {
+  const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
+  const double* mat = inverse ? p->ddir[d].inv : p->ddir[d].fwd;
+  if (d == 0) {
+    return cuda_status(tpt::dgemm_cm(nx, ny * nz, nx, mat, nx, 0, in, nx, 0, out, nx, 0, 1,
+                                     accumulate, s));
+  }
+  const long long slab = static_cast<long long>(nx) * ny;
+  return cuda_status(tpt::dgemm_cm(nx, ny, ny, in, nx, slab, mat, ny, 0, out, nx, slab, nz,
+                                   accumulate, s));
+}
+
+// Workspace layout (float64 path): scalars (256 B) | r | t1 | t2 | fcopy, each
+// field region npts doubles, every region 256-byte aligned.  The scalars are
+// [0] modal defect of the corrections, [1..3] residual sums, [4] constant
+// removed from f, [5..7] sums of f.
+constexpr int kRingSlots = 64, kSlot = 16;
+size_t region_bytes(const tpt_plan_s* p) {
+  return (tpt::npts(p) * sizeof(double) + 255) & ~static_cast<size_t>(255);
+}
+
+// One correction solve: out (=|+=) Q_x Q_y (Thomas) Q_y^{-1} Q_x^{-1} rhs.
+int inner_fp64(const tpt_plan_s* p, const double* rhs, double* out, bool accumulate, double* t1,
+               double* t2, double* defect, cudaStream_t s) {
+  TPT_TRY(apply_transform(p, 0, false, rhs, t1, false, s));               // step 2.1
+  TPT_TRY(apply_transform(p, 1, false, t1, t2, false, s));                // step 2.2
+  TPT_CUDA(tpt::thomas_fp64(p, t2, t2, t1, defect, s));                   // step 2.3
+  TPT_TRY(apply_transform(p, 1, true, t2, t1, false, s));                 // step 2.4
+  TPT_TRY(apply_transform(p, 0, true, t1, out, accumulate, s));           // step 2.5
+  return TPT_OK;
+}
+
+struct InfoCallback {
+  tpt_info* info;
+  const double* h_scal;   // pinned copy of the workspace scalars
+  double npts, vol;
+  int iters;
+  bool singular;
+};
+
+double projected_norm2(double s2, double s1, double sv, double npts, double vol, bool singular) {
+  if (!singular) return s2;
+  const double c = sv / vol;
+  return s2 - 2.0 * c * s1 + npts * c * c;
+}
+
+void CUDART_CB fill_info(void* arg) {
+  InfoCallback* cb = static_cast<InfoCallback*>(arg);
+  const double* h = cb->h_scal;
+  const double fn2 = projected_norm2(h[5], h[6], h[7], cb->npts, cb->vol, cb->singular);
+  cb->info->iters = cb->iters;
+  cb->info->compat_defect = h[4];
+  cb->info->rel_residual = (fn2 > 0.0) ? std::sqrt(h[1]) / std::sqrt(fn2) : std::sqrt(h[1]);
+  delete cb;
+}
+
+}  // namespace
+
+namespace tpt {
+size_t npts(const tpt_plan_s* p) {
+  return static_cast<size_t>(p->n[0]) * p->n[1] * p->n[2];
+}
+}  // namespace tpt
+
+extern "C" {
+
+const char* tpt_status_string(int status) {
+  switch (status) {
+    case TPT_OK: return "ok";
+    case TPT_ERR_INVALID_ARG: return "invalid argument";
+    case TPT_ERR_UNSUPPORTED: return "unsupported configuration";
+    case TPT_ERR_OOM: return "device out of memory";
+    case TPT_ERR_CUDA: return "CUDA error";
+    case TPT_ERR_NOT_CONVERGED: return "refinement did not converge";
+    case TPT_ERR_TIMEOUT: return "device wait timed out";
+    case TPT_ERR_NONFINITE: return "non-finite value in right-hand side or residual";
+    case TPT_ERR_NUMERICAL: return "numerical failure in setup";
+    default: return "unknown status";
+  }
+}
+
+int tpt_grid_tanh(int n, double L, double stretch, double* dxf_out, double* dxc_out) {
+  return tpt::grid_tanh(n, L, stretch, dxf_out, dxc_out);
+}
+
+int tpt_plan_create(const tpt_desc* desc, int cuda_device, tpt_plan* out) {
+  if (!out) return TPT_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!desc) return TPT_ERR_INVALID_ARG;
+  for (int d = 0; d < 3; ++d)
+    if (desc->n[d] < 1 || !desc->dxf[d] || !desc->dxc[d]) return TPT_ERR_INVALID_ARG;
+  if (!std::isfinite(desc->alpha) || !std::isfinite(desc->beta)) return TPT_ERR_INVALID_ARG;
+  if (desc->alpha == 0.0 && desc->beta == 0.0) return TPT_ERR_INVALID_ARG;
+  if (desc->max_refine < 0 || desc->max_refine > 1000) return TPT_ERR_INVALID_ARG;
+  if (desc->precision < TPT_PREC_FP64 || desc->precision > TPT_PREC_MIXED_TF32)
+    return TPT_ERR_INVALID_ARG;
+  for (int d = 0; d < 2; ++d)
+    if (desc->xform[d] < TPT_XFORM_AUTO || desc->xform[d] > TPT_XFORM_FFT) return TPT_ERR_INVALID_ARG;
+  if (desc->precision != TPT_PREC_FP64) return TPT_ERR_UNSUPPORTED;
+
+  tpt_plan_s* p = new (std::nothrow) tpt_plan_s();
+  if (!p) return TPT_ERR_OOM;
+  p->dev = cuda_device;
+  auto fail = [&](int st) {
+    free_plan(p);
+    return st;
+  };
+  for (int d = 0; d < 3; ++d) {
+    p->n[d] = desc->n[d];
+    int st = tpt::build_dir(desc->n[d], desc->dxf[d], desc->dxc[d], desc->bc[d], &p->dir[d]);
+    if (st != TPT_OK) return fail(st);
+  }
+  if (p->dir[2].periodic) return fail(TPT_ERR_UNSUPPORTED);
+  for (int d = 0; d < 2; ++d) {
+    if (desc->xform[d] == TPT_XFORM_FFT) return fail(TPT_ERR_UNSUPPORTED);
+    p->xform[d] = TPT_XFORM_GEMM;
+  }
+  p->alpha = desc->alpha;
+  p->beta = desc->beta;
+  p->precision = desc->precision;
+  p->rtol = desc->rtol;
+  p->max_refine = desc->max_refine;
+  for (int d = 0; d < 2; ++d) {
+    int st = tpt::eigen_dir(p->dir[d], &p->eig[d]);
+    if (st != TPT_OK) return fail(st);
+  }
+  p->singular = (p->alpha == 0.0) && p->dir[0].has_null() && p->dir[1].has_null() &&
+                p->dir[2].has_null();
+  p->null_i = p->eig[0].null_mode;
+  p->null_j = p->eig[1].null_mode;
+  p->vol = 1.0;
+  for (int d = 0; d < 3; ++d) {
+    double L = 0.0;
+    for (double w : p->dir[d].dxf) L += w;
+    p->vol *= L;
+  }
+  if (cuda_device < 0) {   // host-only plan: setup tables for inspection, no device state
+    *out = p;
+    return TPT_OK;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(TPT_ERR_CUDA);
+  }
+  if (cuda_device >= ndev) return fail(TPT_ERR_INVALID_ARG);
+  DeviceGuard guard(cuda_device);
+  for (int d = 0; d < 2; ++d) {
+    int st = upload_basis(p, d);
+    if (st != TPT_OK) return fail(st);
+  }
+  for (int d = 0; d < 3; ++d) {
+    const Dir1D& dd = p->dir[d];
+    std::vector<double> rows(3 * static_cast<size_t>(dd.n));
+    std::copy(dd.a.begin(), dd.a.end(), rows.begin());
+    std::copy(dd.b.begin(), dd.b.end(), rows.begin() + dd.n);
+    std::copy(dd.c.begin(), dd.c.end(), rows.begin() + 2 * dd.n);
+    int st = upload(p, rows, &p->d_rows[d]);
+    if (st == TPT_OK) st = upload(p, dd.dxf, &p->d_dxf[d]);
+    if (st != TPT_OK) return fail(st);
+  }
+  std::vector<double> scal(16, 0.0);
+  int st = upload(p, scal, &p->d_scal);
+  if (st != TPT_OK) return fail(st);
+  const size_t ring_bytes = static_cast<size_t>(kRingSlots) * kSlot * sizeof(double);
+  if (cudaMallocHost(reinterpret_cast<void**>(&p->h_ring), ring_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(TPT_ERR_OOM);
+  }
+  std::memset(p->h_ring, 0, ring_bytes);
+  *out = p;
+  return TPT_OK;
+}
+
+int tpt_plan_destroy(tpt_plan p) {
+  if (!p) return TPT_ERR_INVALID_ARG;
+  free_plan(p);
+  return TPT_OK;
+}
+
+int tpt_set_coefficients(tpt_plan p, double alpha, double beta) {
+  if (!p || !std::isfinite(alpha) || !std::isfinite(beta) || (alpha == 0.0 && beta == 0.0))
+    return TPT_ERR_INVALID_ARG;
+  p->alpha = alpha;
+  p->beta = beta;
+  p->singular = (alpha == 0.0) && p->dir[0].has_null() && p->dir[1].has_null() &&
+                p->dir[2].has_null();
+  return TPT_OK;
+}
+
+int tpt_workspace_bytes(tpt_plan p, size_t* bytes) {
+  if (!p || !bytes) return TPT_ERR_INVALID_ARG;
+  *bytes = 256 + 4 * region_bytes(p);
+  return TPT_OK;
+}
+
+int tpt_solve(tpt_plan p, const double* f, double* phi, void* work, void* stream, tpt_info* info) {
+  if (!on_device(p) || !f || !phi || !work) return TPT_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(work) % 256 != 0) return TPT_ERR_INVALID_ARG;
+  DeviceGuard guard(p->dev);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t rb = region_bytes(p);
+  char* w = static_cast<char*>(work);
+  double* ds = reinterpret_cast<double*>(w);
+  w += 256;
+  double* r = reinterpret_cast<double*>(w);
+  double* t1 = reinterpret_cast<double*>(w + rb);
+  double* t2 = reinterpret_cast<double*>(w + 2 * rb);
+  double* fcopy = reinterpret_cast<double*>(w + 3 * rb);
+  const int corrections = 1 + p->max_refine;
+  const bool adaptive = p->rtol > 0.0;
+  const double* fu = f;
+  if (phi == f && (corrections > 1 || adaptive || info)) {   // f is needed after phi is written
+    TPT_CUDA(cudaMemcpyAsync(fcopy, f, tpt::npts(p) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    fu = fcopy;
+  }
+  TPT_CUDA(cudaMemsetAsync(ds, 0, 16 * sizeof(double), s));
+  TPT_CUDA(tpt::field_sums(p, fu, ds + 5, s));
+  TPT_TRY(inner_fp64(p, fu, phi, false, t1, t2, ds + 4, s));
+  int iters = 1;
+  const double np = static_cast<double>(tpt::npts(p));
+  double fn2 = -1.0, rel = -1.0;
+  double h[kSlot] = {0.0};
+  auto read_residual = [&]() -> int {
+    TPT_CUDA(cudaMemcpyAsync(h, ds, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TPT_CUDA(cudaStreamSynchronize(s));
+    fn2 = projected_norm2(h[5], h[6], h[7], np, p->vol, p->singular);
+    if (!std::isfinite(h[1]) || !std::isfinite(fn2)) return TPT_ERR_NONFINITE;
+    rel = (fn2 > 0.0) ? std::sqrt(h[1] / fn2) : std::sqrt(h[1]);
+    return TPT_OK;
+  };
+  int status = TPT_OK;
+  bool converged = false;
+  for (;;) {
+    const bool need_residual = (iters < corrections) || adaptive || info;
+    if (!need_residual) break;
+    TPT_CUDA(cudaMemsetAsync(ds + 1, 0, 3 * sizeof(double), s));
+    TPT_CUDA(tpt::residual_fp64(p, fu, phi, r, ds + 1, p->singular ? ds + 4 : nullptr, s));
+    if (adaptive) {
+      TPT_TRY(read_residual());
+      if (rel <= p->rtol) {
+        converged = true;
+        break;
+      }
+    }
+    if (iters >= corrections) break;
+    TPT_TRY(inner_fp64(p, r, phi, true, t1, t2, ds, s));
+    ++iters;
+  }
+  if (adaptive && !converged) status = TPT_ERR_NOT_CONVERGED;
+  if (info) {
+    if (adaptive) {
+      info->iters = iters;
+      info->rel_residual = rel;
+      info->compat_defect = h[4];
+      for (float& t : info->ms_stage) t = 0.0f;
+    } else {
+      std::memset(info, 0, sizeof(*info));
+      double* slot = p->h_ring + static_cast<size_t>(p->ring_next) * kSlot;
+      p->ring_next = (p->ring_next + 1) % kRingSlots;
+      TPT_CUDA(cudaMemcpyAsync(slot, ds, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      InfoCallback* cb = new (std::nothrow) InfoCallback{info, slot, np, p->vol, iters, p->singular};
+      if (!cb) return TPT_ERR_OOM;
+      TPT_CUDA(cudaLaunchHostFunc(s, fill_info, cb));
+    }
+  }
+  return status;
+}
+
+int tpt_solve_host(tpt_plan p, const double* f_host, double* phi_host, double* f_dev,
+                   double* phi_dev, void* work, void* stream, tpt_info* info) {
+  if (!on_device(p) || !f_host || !phi_host || !f_dev || !phi_dev) return TPT_ERR_INVALID_ARG;
+  DeviceGuard guard(p->dev);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t bytes = tpt::npts(p) * sizeof(double);
+  TPT_CUDA(cudaMemcpyAsync(f_dev, f_host, bytes, cudaMemcpyHostToDevice, s));
+  int st = tpt_solve(p, f_dev, phi_dev, work, stream, info);
+  if (st != TPT_OK && st != TPT_ERR_NOT_CONVERGED) return st;
+  TPT_CUDA(cudaMemcpyAsync(phi_host, phi_dev, bytes, cudaMemcpyDeviceToHost, s));
+  TPT_CUDA(cudaStreamSynchronize(s));
+  return st;
+}
+
+int tpt_transform(tpt_plan p, int dir, int inverse, const double* in, double* out, void* stream) {
+  if (!on_device(p) || !in || !out || in == out || (dir != 0 && dir != 1)) return TPT_ERR_INVALID_ARG;
+  DeviceGuard guard(p->dev);
+  return apply_transform(p, dir, inverse != 0, in, out, false, static_cast<cudaStream_t>(stream));
+}
+
+int tpt_thomas(tpt_plan p, const double* fhat, double* phihat, double* scratch, void* stream) {
+  if (!on_device(p) || !fhat || !phihat || !scratch) return TPT_ERR_INVALID_ARG;
+  DeviceGuard guard(p->dev);
+  return cuda_status(tpt::thomas_fp64(p, fhat, phihat, scratch, p->d_scal,
+                                      static_cast<cudaStream_t>(stream)));
+}
+
+int tpt_residual(tpt_plan p, const double* f, const double* phi, double* r, double* sums,
+                 void* stream) {
+  if (!on_device(p) || !f || !phi || !r) return TPT_ERR_INVALID_ARG;
+  DeviceGuard guard(p->dev);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the single-step residual uses f as given (no compatibility shift)
+  return cuda_status(tpt::residual_fp64(p, f, phi, r, sums, nullptr, s));
+}
+
+int tpt_plan_eigenvalues(tpt_plan p, int dir, double* lam) {
+  if (!p || !lam || (dir != 0 && dir != 1)) return TPT_ERR_INVALID_ARG;
+  std::copy(p->eig[dir].lam.begin(), p->eig[dir].lam.end(), lam);
+  return TPT_OK;
+}
+
+int tpt_plan_rows(tpt_plan p, int dir, double* a, double* b, double* c) {
+  if (!p || !a || !b || !c || dir < 0 || dir > 2) return TPT_ERR_INVALID_ARG;
+  const Dir1D& d = p->dir[dir];
+  std::copy(d.a.begin(), d.a.end(), a);
+  std::copy(d.b.begin(), d.b.end(), b);
+  std::copy(d.c.begin(), d.c.end(), c);
+  return TPT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,293 @@
+// float64 kernels of the solve: the eigenbasis-transform GEMM (Sec. 2.2.2,
+// Eq. forward-xy / inverse-xy; lines stacked as one GEMM), the modal Thomas
+// sweep along z (solution step 2.3, with the gauge of Sec. 3), and the
+// 7-point residual r = f - (alpha I + beta L) phi (Sec. 4.1).
+//
+// float64 arithmetic on GB300 runs at about 1 TFLOP/s (FMA and DMMA alike), so
+// these kernels are bound by the float64 pipe, not by HBM; the layouts below
+// keep every global access coalesced so that the float64 units stay fed.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "tpt_internal.h"
+
+namespace tpt {
+namespace {
+
+constexpr int TM = 64, TN = 64, TK = 16;   // block tile and k-step
+constexpr int TX = 16, TY = 16;            // 256 threads, 4 x 4 outputs each
+
+// C_b = A_b B_b (+ C_b): column-major, ragged edges zero-filled in shared memory.
+__global__ void __launch_bounds__(TX * TY)
+dgemm_cm_kernel(int M, int N, int K, const double* __restrict__ A, int lda, long long sA,
+                const double* __restrict__ B, int ldb, long long sB, double* __restrict__ C,
+                int ldc, long long sC, int accumulate) {
+  __shared__ double As[TK][TM + 1];
+  __shared__ double Bs[TK][TN + 1];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+  const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
+  const long long b = blockIdx.z;
+  A += b * sA;
+  B += b * sB;
+  C += b * sC;
+  double acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
+
+  for (int k0 = 0; k0 < K; k0 += TK) {
+#pragma unroll
+    for (int r = 0; r < (TM * TK) / (TX * TY); ++r) {   // A tile, coalesced along m
+      const int e = tid + r * TX * TY, m = e % TM, k = e / TM;
+      const int gm = m0 + m, gk = k0 + k;
+      As[k][m] = (gm < M && gk < K) ? A[gm + static_cast<long long>(gk) * lda] : 0.0;
+    }
+#pragma unroll
+    for (int r = 0; r < (TN * TK) / (TX * TY); ++r) {   // B tile, coalesced along k
+      const int e = tid + r * TX * TY, k = e % TK, n = e / TK;
+      const int gk = k0 + k, gn = n0 + n;
+      Bs[k][n] = (gk < K && gn < N) ? B[gk + static_cast<long long>(gn) * ldb] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < TK; ++kk) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) av[r] = As[kk][tx + TX * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) bv[c] = Bs[kk][ty + TY * c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = fma(av[r], bv[c], acc[r][c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int gn = n0 + ty + TY * c;
+    if (gn >= N) continue;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int gm = m0 + tx + TX * r;
+      if (gm >= M) continue;
+      double* p = C + gm + static_cast<long long>(gn) * ldc;
+      *p = accumulate ? *p + acc[r][c] : acc[r][c];
+    }
+  }
+}
+
+// One thread per (i, j) line.  Forward elimination keeps c' in `scratch`
+// and d' in `out`; back substitution overwrites `out`.  The singular line
+// (null_i, null_j) is first projected to compatible form (its dz-weighted
+// mean removed, recorded in *defect), its last modal unknown is set to zero,
+// and the result is shifted to zero dz-weighted mean.
+__global__ void __launch_bounds__(128)
+thomas_fp64_kernel(int nx, int ny, int nz, const double* __restrict__ f, double* out,
+                   double* __restrict__ scratch, const double* __restrict__ lamx,
+                   const double* __restrict__ lamy, const double* __restrict__ az,
+                   const double* __restrict__ bz, const double* __restrict__ cz,
+                   const double* __restrict__ dz, double alpha, double beta, int null_i,
+                   int null_j, double null_scale, double* defect) {
+  const long long lines = static_cast<long long>(nx) * ny;
+  const long long line = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+  if (line >= lines) return;
+  const int i = static_cast<int>(line % nx), j = static_cast<int>(line / nx);
+  const bool is_null = (i == null_i && j == null_j);
+  const double shift = alpha + beta * (lamx[i] + lamy[j]);
+  double fshift = 0.0;
+  if (is_null) {
+    double s = 0.0, w = 0.0;
+    for (int k = 0; k < nz; ++k) {
+      s = fma(dz[k], f[line + k * lines], s);
+      w += dz[k];
+    }
+    fshift = s / w;
+    if (defect) *defect = fshift * null_scale;
+  }
+  double cp = 0.0, dp = 0.0;
+  for (int k = 0; k < nz; ++k) {
+    const long long o = line + k * lines;
+    const double sub = (k > 0) ? beta * az[k] : 0.0;
+    const double m = (beta * bz[k] + shift) - sub * cp;
+    const double rhs = (f[o] - fshift) - sub * dp;
+    if (is_null && k == nz - 1) {
+      dp = 0.0;   // vanishing final pivot: the modal unknown is set to zero
+    } else {
+      const double inv = 1.0 / m;
+      cp = (k < nz - 1) ? beta * cz[k] * inv : 0.0;
+      dp = rhs * inv;
+    }
+    scratch[o] = cp;
+    out[o] = dp;
+  }
+  double x = dp;
+  double xs = dz[nz - 1] * x, w = dz[nz - 1];
+  for (int k = nz - 2; k >= 0; --k) {
+    const long long o = line + k * lines;
+    x = out[o] - scratch[o] * x;
+    out[o] = x;
+    xs = fma(dz[k], x, xs);
+    w += dz[k];
+  }
+  if (is_null) {
+    const double mean = xs / w;
+    for (int k = 0; k < nz; ++k) out[line + k * lines] -= mean;
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// r = (f - fshift) - (alpha phi + beta (Lx + Ly + Lz) phi); one thread per
+// (i, j) marching along k.  End couplings of non-periodic directions are zero,
+// so wrapped neighbour indices only ever meet a zero coefficient.
+__global__ void __launch_bounds__(128)
+residual_fp64_kernel(int nx, int ny, int nz, const double* __restrict__ f,
+                     const double* __restrict__ phi, double* __restrict__ r,
+                     const double* __restrict__ rx, const double* __restrict__ ry,
+                     const double* __restrict__ rz, const double* __restrict__ dxf,
+                     const double* __restrict__ dyf, const double* __restrict__ dzf,
+                     double alpha, double beta, const double* __restrict__ fshift_p,
+                     double* sums) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  double s2 = 0.0, s1 = 0.0, sv = 0.0;
+  if (i < nx && j < ny) {
+    const long long sx = 1, sy = nx, sz = static_cast<long long>(nx) * ny;
+    const long long base = i + sy * j;
+    const int im = (i == 0) ? nx - 1 : i - 1, ip = (i == nx - 1) ? 0 : i + 1;
+    const int jm = (j == 0) ? ny - 1 : j - 1, jp = (j == ny - 1) ? 0 : j + 1;
+    const double ax = rx[i], bx = rx[nx + i], cx = rx[2 * nx + i];
+    const double ay = ry[j], by = ry[ny + j], cy = ry[2 * ny + j];
+    const double fshift = fshift_p ? *fshift_p : 0.0;
+    const double vxy = dxf[i] * dyf[j];
+    (void)sx;
+    double pm = phi[base + sz * (nz - 1)];   // wrap partner, multiplied by a_0 = 0
+    double p0 = phi[base];
+    for (int k = 0; k < nz; ++k) {
+      const long long o = base + sz * k;
+      const double pp = phi[base + sz * ((k == nz - 1) ? 0 : k + 1)];
+      const double lx = fma(ax, phi[im + sy * j + sz * k], fma(cx, phi[ip + sy * j + sz * k], bx * p0));
+      const double ly = fma(ay, phi[i + sy * jm + sz * k], fma(cy, phi[i + sy * jp + sz * k], by * p0));
+      const double lz = fma(rz[k], pm, fma(rz[2 * nz + k], pp, rz[nz + k] * p0));
+      const double val = (f[o] - fshift) - fma(alpha, p0, beta * ((lx + ly) + lz));
+      r[o] = val;
+      s2 = fma(val, val, s2);
+      s1 += val;
+      sv = fma(vxy * dzf[k], val, sv);
+      pm = p0;
+      p0 = pp;
+    }
+  }
+  if (sums) {
+    s2 = warp_sum(s2);
+    s1 = warp_sum(s1);
+    sv = warp_sum(sv);
+    if ((threadIdx.x + blockDim.x * threadIdx.y) % 32 == 0) {
+      atomicAdd(&sums[0], s2);
+      atomicAdd(&sums[1], s1);
+      atomicAdd(&sums[2], sv);
+    }
+  }
+}
+
+// sums[0] += sum f^2, sums[1] += sum f, sums[2] += sum vol*f  (grid-stride)
+__global__ void __launch_bounds__(256)
+field_sums_kernel(int nx, int ny, int nz, const double* __restrict__ f, const double* __restrict__ dxf,
+                  const double* __restrict__ dyf, const double* __restrict__ dzf, double* sums) {
+  const long long n = static_cast<long long>(nx) * ny * nz;
+  double s2 = 0.0, s1 = 0.0, sv = 0.0;
+  for (long long o = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; o < n;
+       o += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int i = static_cast<int>(o % nx);
+    const long long jk = o / nx;
+    const int j = static_cast<int>(jk % ny), k = static_cast<int>(jk / ny);
+    const double v = f[o];
+    s2 = fma(v, v, s2);
+    s1 += v;
+    sv = fma(dxf[i] * dyf[j] * dzf[k], v, sv);
+  }
+  s2 = warp_sum(s2);
+  s1 = warp_sum(s1);
+  sv = warp_sum(sv);
+  if (threadIdx.x % 32 == 0) {
+    atomicAdd(&sums[0], s2);
+    atomicAdd(&sums[1], s1);
+    atomicAdd(&sums[2], sv);
+  }
+}
+
+}  // namespace
+
+cudaError_t field_sums(const tpt_plan_s* p, const double* f, double* sums, cudaStream_t s) {
+  int dev_sms = 152;
+  cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, p->dev);
+  const long long n = static_cast<long long>(p->n[0]) * p->n[1] * p->n[2];
+  long long nb = (n + 255) / 256;
+  if (nb > 8LL * dev_sms) nb = 8LL * dev_sms;
+  field_sums_kernel<<<static_cast<unsigned>(nb), 256, 0, s>>>(p->n[0], p->n[1], p->n[2], f, p->d_dxf[0],
+                                                              p->d_dxf[1], p->d_dxf[2], sums);
+  return cudaGetLastError();
+}
+
+cudaError_t dgemm_cm(int M, int N, int K, const double* A, int lda, long long sA,
+                     const double* B, int ldb, long long sB, double* C, int ldc, long long sC,
+                     int batch, bool accumulate, cudaStream_t s) {
+  if (M <= 0 || N <= 0 || K <= 0 || batch <= 0) return cudaSuccess;
+  if (batch > 65535) return cudaErrorInvalidConfiguration;
+  // split N so that the grid's y extent stays within the hardware limit
+  const int nchunk = 65535 * TN;
+  for (int n0 = 0; n0 < N; n0 += nchunk) {
+    const int nn = (N - n0 < nchunk) ? N - n0 : nchunk;
+    dim3 grid((M + TM - 1) / TM, (nn + TN - 1) / TN, batch);
+    dgemm_cm_kernel<<<grid, dim3(TX, TY), 0, s>>>(M, nn, K, A, lda, sA,
+                                                  B + static_cast<long long>(n0) * ldb, ldb, sB,
+                                                  C + static_cast<long long>(n0) * ldc, ldc, sC,
+                                                  accumulate ? 1 : 0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t thomas_fp64(const tpt_plan_s* p, const double* fhat, double* phihat, double* scratch,
+                        double* defect, cudaStream_t s) {
+  const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
+  const long long lines = static_cast<long long>(nx) * ny;
+  const int bs = 128;
+  const long long nb = (lines + bs - 1) / bs;
+  const double* rz = p->d_rows[2];
+  double null_scale = 0.0;
+  if (p->singular) {
+    // f-hat of the null line equals (g_x g_y) times the physical constant,
+    // with g = sum_i Q~[i, null] sqrt(dx_i)
+    double gx = 0.0, gy = 0.0;
+    for (int i = 0; i < nx; ++i) gx += p->eig[0].qt[i] * std::sqrt(p->dir[0].dxf[i]);
+    for (int j = 0; j < ny; ++j) gy += p->eig[1].qt[j] * std::sqrt(p->dir[1].dxf[j]);
+    null_scale = 1.0 / (gx * gy);
+  }
+  thomas_fp64_kernel<<<static_cast<unsigned>(nb), bs, 0, s>>>(
+      nx, ny, nz, fhat, phihat, scratch, p->ddir[0].lam, p->ddir[1].lam, rz, rz + nz, rz + 2 * nz,
+      p->d_dxf[2], p->alpha, p->beta, p->singular ? p->null_i : -1, p->singular ? p->null_j : -1,
+      null_scale, p->singular ? defect : nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t residual_fp64(const tpt_plan_s* p, const double* f, const double* phi, double* r,
+                          double* sums, const double* fshift, cudaStream_t s) {
+  const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
+  dim3 block(32, 4);
+  dim3 grid((nx + 31) / 32, (ny + 3) / 4);
+  residual_fp64_kernel<<<grid, block, 0, s>>>(nx, ny, nz, f, phi, r, p->d_rows[0], p->d_rows[1],
+                                              p->d_rows[2], p->d_dxf[0], p->d_dxf[1], p->d_dxf[2],
+                                              p->alpha, p->beta, fshift, sums);
+  return cudaGetLastError();
+}
+
+}  // namespace tpt

@@ -1,0 +1,95 @@
+// Internal declarations shared by the host setup, the kernels and the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "../../include/tpt.h"
+
+namespace tpt {
+
+// ----------------------------------------------------------------- host setup
+// One direction's 1D operator rows (Eq. tridiagonal-coefficients with boundary
+// rows) and, for diagonalised directions, its eigenbasis.
+struct Dir1D {
+  int n = 0;
+  int bc[2] = {TPT_BC_NEUMANN, TPT_BC_NEUMANN};
+  bool periodic = false;
+  bool uniform = false;           // all cell widths and centre spacings equal
+  std::vector<double> dxf, dxc;   // n, n+1
+  std::vector<double> a, b, c;    // rows: a_i phi_{i-1} + b_i phi_i + c_i phi_{i+1}
+  bool has_null() const {
+    return periodic || (bc[0] == TPT_BC_NEUMANN && bc[1] == TPT_BC_NEUMANN);
+  }
+};
+
+// Eigenbasis of one diagonalised direction: T = Q Lambda Q^{-1} with
+// Q = D^{-1/2} Q~ and Q^{-1} = Q~^T D^{1/2}.  Modes are sorted by decreasing
+// eigenvalue, so a null mode (lambda = 0) is mode 0.
+struct Eigen1D {
+  std::vector<double> lam;        // n
+  std::vector<double> qt;         // Q~, column-major n x n (column p = mode p)
+  int null_mode = -1;
+};
+
+int build_dir(int n, const double* dxf, const double* dxc, const int bc[2], Dir1D* out);
+int eigen_dir(const Dir1D& d, Eigen1D* out);
+int grid_tanh(int n, double L, double stretch, double* dxf, double* dxc);
+
+// ----------------------------------------------------------------- device plan
+struct DevDir {       // device tables of a diagonalised direction (float64)
+  double* fwd = nullptr;  // forward transform operand (layout set by the GEMM role)
+  double* inv = nullptr;  // inverse transform operand
+  double* lam = nullptr;  // eigenvalues in mode order
+};
+
+}  // namespace tpt
+
+struct tpt_plan_s {
+  int dev = 0;
+  int n[3] = {0, 0, 0};
+  int xform[2] = {TPT_XFORM_GEMM, TPT_XFORM_GEMM};
+  double alpha = 0.0, beta = 1.0;
+  int precision = TPT_PREC_FP64;
+  double rtol = 0.0;
+  int max_refine = 1;
+  bool singular = false;
+  int null_i = 0, null_j = 0;     // mode indices of the null line when singular
+  tpt::Dir1D dir[3];
+  tpt::Eigen1D eig[2];
+  tpt::DevDir ddir[2];
+  double* d_rows[3] = {nullptr, nullptr, nullptr};  // a|b|c per direction, 3n doubles
+  double* d_dxf[3] = {nullptr, nullptr, nullptr};
+  double* d_scal = nullptr;       // device scalars of the single-step entry points
+  double* h_ring = nullptr;       // pinned host slots for asynchronous info reports
+  int ring_next = 0;
+  double vol = 1.0;               // domain volume Lx Ly Lz
+  std::vector<void*> allocs;      // every device allocation owned by the plan
+};
+
+namespace tpt {
+
+size_t npts(const tpt_plan_s* p);
+
+// ----------------------------------------------------------------- kernels
+// Batched column-major float64 GEMM: C_b = A_b B_b (+ C_b when accumulate),
+// A_b = A + b*sA (M x K, lda), B_b = B + b*sB (K x N, ldb), C_b (M x N, ldc).
+cudaError_t dgemm_cm(int M, int N, int K, const double* A, int lda, long long sA,
+                     const double* B, int ldb, long long sB, double* C, int ldc, long long sC,
+                     int batch, bool accumulate, cudaStream_t s);
+
+// `defect` (device, may be NULL) receives the physical constant removed from
+// the right-hand side of a singular problem.
+cudaError_t thomas_fp64(const tpt_plan_s* p, const double* fhat, double* phihat, double* scratch,
+                        double* defect, cudaStream_t s);
+
+// sums[0..2] += (sum f^2, sum f, sum vol*f) over the field
+cudaError_t field_sums(const tpt_plan_s* p, const double* f, double* sums, cudaStream_t s);
+
+// r = (f - fshift) - (alpha I + beta L) phi; fshift (device scalar) may be NULL.
+cudaError_t residual_fp64(const tpt_plan_s* p, const double* f, const double* phi, double* r,
+                          double* sums, const double* fshift, cudaStream_t s);
+
+}  // namespace tpt

@@ -1,0 +1,167 @@
+"""Python face of the C ABI: a Plan object over torch device memory and streams.
+
+Fields are float64 in Fortran order (Nx, Ny, Nz), x fastest.  On the torch side
+a field is a contiguous float64 CUDA tensor with Nx*Ny*Nz elements (any shape;
+``field_to_device`` / ``field_to_host`` convert from/to numpy (Nx, Ny, Nz)
+arrays).  This module only marshals arguments: every computation runs in
+libtpt.so.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import check, lib
+
+AUTO, GEMM, FFT = _lib.TPT_XFORM_AUTO, _lib.TPT_XFORM_GEMM, _lib.TPT_XFORM_FFT
+PERIODIC, NEUMANN, DIRICHLET = _lib.TPT_BC_PERIODIC, _lib.TPT_BC_NEUMANN, _lib.TPT_BC_DIRICHLET
+FP64 = _lib.TPT_PREC_FP64
+MIXED_BF16, MIXED_BF16X3, MIXED_TF32 = (_lib.TPT_PREC_MIXED_BF16, _lib.TPT_PREC_MIXED_BF16X3,
+                                        _lib.TPT_PREC_MIXED_TF32)
+_BC = {"periodic": PERIODIC, "neumann": NEUMANN, "dirichlet": DIRICHLET}
+
+
+def _ptr(t) -> C.c_void_p:
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+def _stream(stream) -> C.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def grid_tanh(n: int, L: float = 1.0, stretch: float = 0.0):
+    """tpt_grid_tanh: (dxf, dxc) of Eq. (tanh_stretching) as float64 numpy arrays."""
+    dxf = np.empty(n)
+    dxc = np.empty(n + 1)
+    check(lib.tpt_grid_tanh(n, L, stretch, dxf.ctypes.data_as(_lib._dp),
+                            dxc.ctypes.data_as(_lib._dp)), "tpt_grid_tanh")
+    return dxf, dxc
+
+
+def field_to_device(f: np.ndarray, device="cuda") -> torch.Tensor:
+    """numpy (Nx, Ny, Nz) -> flat contiguous float64 tensor in Fortran order."""
+    flat = np.asarray(f, dtype=np.float64).ravel(order="F")
+    return torch.from_numpy(np.ascontiguousarray(flat)).to(device)
+
+
+def field_to_host(t: torch.Tensor, n) -> np.ndarray:
+    return t.detach().cpu().numpy().reshape(tuple(n), order="F")
+
+
+class Plan:
+    """tpt_plan_create / tpt_solve / tpt_plan_destroy on one CUDA device."""
+
+    def __init__(self, n, dxf, dxc, bc, xform=(AUTO, AUTO), alpha=0.0, beta=1.0,
+                 precision=FP64, rtol=0.0, max_refine=1, device: int = 0):
+        self.n = tuple(int(v) for v in n)
+        self.device = int(device)
+        self._dxf = [np.ascontiguousarray(d, dtype=np.float64) for d in dxf]
+        self._dxc = [np.ascontiguousarray(d, dtype=np.float64) for d in dxc]
+        desc = _lib.tpt_desc()
+        for a in range(3):
+            desc.n[a] = self.n[a]
+            desc.dxf[a] = self._dxf[a].ctypes.data_as(_lib._dp)
+            desc.dxc[a] = self._dxc[a].ctypes.data_as(_lib._dp)
+            lo, hi = bc[a]
+            desc.bc[a][0] = _BC.get(lo, lo) if isinstance(lo, str) else int(lo)
+            desc.bc[a][1] = _BC.get(hi, hi) if isinstance(hi, str) else int(hi)
+        desc.xform[0], desc.xform[1] = int(xform[0]), int(xform[1])
+        desc.alpha, desc.beta = float(alpha), float(beta)
+        desc.precision = int(precision)
+        desc.rtol = float(rtol)
+        desc.max_refine = int(max_refine)
+        h = C.c_void_p()
+        check(lib.tpt_plan_create(C.byref(desc), self.device, C.byref(h)), "tpt_plan_create")
+        self._h = h
+        nb = C.c_size_t()
+        check(lib.tpt_workspace_bytes(self._h, C.byref(nb)), "tpt_workspace_bytes")
+        self.workspace_bytes = int(nb.value)
+        self.npts = self.n[0] * self.n[1] * self.n[2]
+
+    # ------------------------------------------------------------------
+    def new_workspace(self) -> torch.Tensor:
+        return torch.empty(self.workspace_bytes, dtype=torch.uint8, device="cuda:%d" % self.device)
+
+    def new_field(self) -> torch.Tensor:
+        return torch.empty(self.npts, dtype=torch.float64, device="cuda:%d" % self.device)
+
+    def solve(self, f: torch.Tensor, phi: torch.Tensor = None, work: torch.Tensor = None,
+              stream=None, want_info: bool = True, raise_not_converged: bool = True):
+        """tpt_solve.  Returns (phi, info dict or None); info is read after a
+        stream synchronisation when the plan runs a fixed number of steps."""
+        phi = self.new_field() if phi is None else phi
+        work = self.new_workspace() if work is None else work
+        info = _lib.tpt_info() if want_info else None
+        st = lib.tpt_solve(self._h, _ptr(f), _ptr(phi), _ptr(work), _stream(stream),
+                           C.byref(info) if info is not None else None)
+        if st == _lib.TPT_ERR_NOT_CONVERGED and not raise_not_converged:
+            pass
+        else:
+            check(st, "tpt_solve")
+        if info is None:
+            return phi, None
+        (torch.cuda.current_stream() if stream is None else stream).synchronize()
+        return phi, dict(iters=info.iters, rel_residual=info.rel_residual,
+                         compat_defect=info.compat_defect, status=st)
+
+    def solve_host(self, f_host: torch.Tensor, phi_host: torch.Tensor, f_dev: torch.Tensor,
+                   phi_dev: torch.Tensor, work: torch.Tensor, stream=None):
+        info = _lib.tpt_info()
+        st = lib.tpt_solve_host(self._h, _ptr(f_host), _ptr(phi_host), _ptr(f_dev), _ptr(phi_dev),
+                                _ptr(work), _stream(stream), C.byref(info))
+        check(st, "tpt_solve_host")
+        return dict(iters=info.iters, rel_residual=info.rel_residual,
+                    compat_defect=info.compat_defect)
+
+    def set_coefficients(self, alpha: float, beta: float):
+        check(lib.tpt_set_coefficients(self._h, float(alpha), float(beta)), "tpt_set_coefficients")
+
+    # ------------------------------------------------------------ single steps
+    def transform(self, x: torch.Tensor, direction: int, inverse: bool, out=None, stream=None):
+        out = self.new_field() if out is None else out
+        check(lib.tpt_transform(self._h, int(direction), int(bool(inverse)), _ptr(x), _ptr(out),
+                                _stream(stream)), "tpt_transform")
+        return out
+
+    def thomas(self, fhat: torch.Tensor, out=None, scratch=None, stream=None):
+        out = self.new_field() if out is None else out
+        scratch = self.new_field() if scratch is None else scratch
+        check(lib.tpt_thomas(self._h, _ptr(fhat), _ptr(out), _ptr(scratch), _stream(stream)),
+              "tpt_thomas")
+        return out
+
+    def residual(self, f: torch.Tensor, phi: torch.Tensor, out=None, sums=None, stream=None):
+        out = self.new_field() if out is None else out
+        check(lib.tpt_residual(self._h, _ptr(f), _ptr(phi), _ptr(out), _ptr(sums), _stream(stream)),
+              "tpt_residual")
+        return out
+
+    def eigenvalues(self, direction: int) -> np.ndarray:
+        lam = np.empty(self.n[direction])
+        check(lib.tpt_plan_eigenvalues(self._h, int(direction), lam.ctypes.data_as(_lib._dp)),
+              "tpt_plan_eigenvalues")
+        return lam
+
+    def rows(self, direction: int):
+        m = self.n[direction]
+        a, b, c = np.empty(m), np.empty(m), np.empty(m)
+        check(lib.tpt_plan_rows(self._h, int(direction), a.ctypes.data_as(_lib._dp),
+                                b.ctypes.data_as(_lib._dp), c.ctypes.data_as(_lib._dp)),
+              "tpt_plan_rows")
+        return a, b, c
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.tpt_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

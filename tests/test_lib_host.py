@@ -1,0 +1,124 @@
+"""Host-side checks of libtpt.so: exported symbols, descriptor validation and
+the host setup (rows, eigenvalues) against the oracle.  No GPU needed: these
+use host-only plans (cuda_device < 0)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+from _tpt import ROOT, load
+
+tpt, L = load()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "tpt.h")).read()
+    return re.findall(r"^(?:int|const char\*)\s+(tpt_\w+)\s*\(", src, flags=re.M)
+
+
+def test_every_declared_symbol_is_exported_and_bound():
+    names = _declared()
+    assert len(names) >= 10
+    for name in names:
+        assert hasattr(L.lib, name), name
+    bound = {s[0] for s in L.SIGNATURES}
+    assert set(names) <= bound, set(names) - bound
+
+
+def _desc(n, grids, bcs, alpha=0.0, beta=1.0, prec=0, xform=(1, 1)):
+    d = L.tpt_desc()
+    keep = []
+    for a in range(3):
+        dxf = np.ascontiguousarray(grids[a][0], dtype=np.float64)
+        dxc = np.ascontiguousarray(grids[a][1], dtype=np.float64)
+        keep += [dxf, dxc]
+        d.n[a] = n[a]
+        d.dxf[a] = dxf.ctypes.data_as(L._dp)
+        d.dxc[a] = dxc.ctypes.data_as(L._dp)
+        d.bc[a][0], d.bc[a][1] = bcs[a]
+    d.xform[0], d.xform[1] = xform
+    d.alpha, d.beta, d.precision, d.rtol, d.max_refine = alpha, beta, prec, 0.0, 1
+    return d, keep
+
+
+def _host_plan(n, stretch, bcs, **kw):
+    grids = [O.tanh_grid(n[a], 1.0, stretch[a]) for a in range(3)]
+    d, keep = _desc(n, grids, bcs, **kw)
+    h = C.c_void_p()
+    st = L.lib.tpt_plan_create(C.byref(d), -1, C.byref(h))
+    return st, h, grids
+
+
+def test_descriptor_validation():
+    h = C.c_void_p()
+    assert L.lib.tpt_plan_create(None, -1, C.byref(h)) == L.TPT_ERR_INVALID_ARG
+    grids = [O.tanh_grid(8, 1.0, 1.0)] * 3
+    d, keep = _desc((8, 8, 8), grids, [(1, 1)] * 3)
+    d.n[1] = 0
+    assert L.lib.tpt_plan_create(C.byref(d), -1, C.byref(h)) == L.TPT_ERR_INVALID_ARG
+    d, keep = _desc((8, 8, 8), grids, [(0, 1), (1, 1), (1, 1)])   # periodic on one end only
+    assert L.lib.tpt_plan_create(C.byref(d), -1, C.byref(h)) == L.TPT_ERR_INVALID_ARG
+    d, keep = _desc((8, 8, 8), grids, [(1, 1), (1, 1), (0, 0)])   # periodic z
+    assert L.lib.tpt_plan_create(C.byref(d), -1, C.byref(h)) == L.TPT_ERR_UNSUPPORTED
+    d, keep = _desc((8, 8, 8), grids, [(1, 1)] * 3, alpha=0.0, beta=0.0)
+    assert L.lib.tpt_plan_create(C.byref(d), -1, C.byref(h)) == L.TPT_ERR_INVALID_ARG
+    bad = [g for g in grids]
+    neg = (grids[0][0].copy(), grids[0][1])
+    neg[0][3] = -1.0
+    d, keep = _desc((8, 8, 8), [neg, grids[1], grids[2]], [(1, 1)] * 3)
+    assert L.lib.tpt_plan_create(C.byref(d), -1, C.byref(h)) == L.TPT_ERR_INVALID_ARG
+    assert not h.value
+
+
+def test_host_plan_rejected_by_device_entry_points():
+    st, h, _ = _host_plan((6, 6, 6), (1, 1, 1), [(1, 1)] * 3)
+    assert st == L.TPT_OK
+    x = C.c_void_p(256)
+    assert L.lib.tpt_solve(h, x, x, x, None, None) == L.TPT_ERR_INVALID_ARG
+    assert L.lib.tpt_transform(h, 0, 0, x, C.c_void_p(512), None) == L.TPT_ERR_INVALID_ARG
+    assert L.lib.tpt_plan_destroy(h) == L.TPT_OK
+
+
+@pytest.mark.parametrize("bcs", [[(1, 1), (1, 1), (1, 1)], [(0, 0), (2, 1), (1, 2)],
+                                 [(2, 2), (1, 2), (2, 1)]])
+def test_rows_bitwise_equal_to_oracle(bcs):
+    n, stretch = (21, 17, 13), (1.5, 2.0, 2.5)
+    st, h, grids = _host_plan(n, stretch, bcs)
+    assert st == L.TPT_OK
+    for a in range(3):
+        ref = O.Direction(*grids[a], bcs[a])
+        ra, rb, rc = (np.empty(n[a]) for _ in range(3))
+        assert L.lib.tpt_plan_rows(h, a, ra.ctypes.data_as(L._dp), rb.ctypes.data_as(L._dp),
+                                   rc.ctypes.data_as(L._dp)) == L.TPT_OK
+        assert np.array_equal(ra, ref.a) and np.array_equal(rb, ref.b) and np.array_equal(rc, ref.c)
+    L.lib.tpt_plan_destroy(h)
+
+
+@pytest.mark.parametrize("n,stretch,bc", [(64, 2.0, (1, 1)), (200, 2.5, (1, 1)), (33, 1.0, (2, 1)),
+                                          (40, 0.0, (0, 0)), (24, 1.5, (0, 0)), (1, 0.0, (1, 1))])
+def test_eigenvalues_match_oracle(n, stretch, bc):
+    st, h, grids = _host_plan((n, n, 4), (stretch, stretch, 1.0), [bc, bc, (1, 1)])
+    assert st == L.TPT_OK
+    lam = np.empty(n)
+    assert L.lib.tpt_plan_eigenvalues(h, 0, lam.ctypes.data_as(L._dp)) == L.TPT_OK
+    ref = O.Eigenbasis(O.Direction(*grids[0], bc)).lam
+    got, exp = np.sort(lam), np.sort(ref)
+    scale = np.abs(exp).max() if n > 1 else 1.0
+    assert np.all(np.abs(got - exp) <= 1e-13 * np.maximum(np.abs(exp), 1e-3 * scale))
+    # modes are ordered by decreasing eigenvalue; a null mode is mode 0 and exactly 0
+    assert np.all(np.diff(lam) <= 0)
+    if bc != (2, 1):
+        assert lam[0] == 0.0
+    L.lib.tpt_plan_destroy(h)
+
+
+def test_grid_helper_matches_oracle_grid():
+    for n, s in [(128, 2.0), (128, 4.0), (37, 1.3), (16, 0.0)]:
+        dxf, dxc = tpt.grid_tanh(n, 1.0, s)
+        rf, rc = O.tanh_grid(n, 1.0, s)
+        # face differences near x = L lose a few bits to cancellation
+        assert np.allclose(dxf, rf, rtol=1e-12, atol=0) and np.allclose(dxc, rc, rtol=1e-12, atol=0)
+    assert L.lib.tpt_grid_tanh(0, 1.0, 1.0, None, None) == L.TPT_ERR_INVALID_ARG
