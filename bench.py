@@ -1,0 +1,367 @@
+"""Benchmark of the tensor-product--Thomas solve on GB300.
+
+Workload (one step = one complete solve): Poisson on a 512x512x512
+staggered grid, tanh-stretched in x, y, z with factors 1.5 / 2.0 / 2.5,
+homogeneous Neumann walls, x and y by eigenbasis GEMM, z by Thomas, seeded
+uniform[-1, 1] right-hand side with its volume-weighted mean removed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--precision fp64|mixed_bf16x3|...] [--size 512]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun, one rank per GPU) every
+rank solves its own instances with no collective on the data path
+(independent replicas, weak scaling); the timed region is bracketed by a
+barrier and a device synchronisation, and the time is the maximum over ranks.
+``--impl reference`` times the CPU oracle (the reference arm of this
+project) on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Poisson solves/s & Gpts/s at 512³ stretched, FP64 vs mixed+refine; p99 latency"
+STRETCH = (1.5, 2.0, 2.5)
+SEED = 4
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self._t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ inputs
+
+def workload(size):
+    n = (size, size, size)
+    return n, STRETCH
+
+
+def rhs_host(n, grids):
+    import seeded_inputs as S
+    f = S.uniform_rhs(n, SEED)
+    return S.remove_weighted_mean(f, [g[0] for g in grids])
+
+
+# ------------------------------------------------------------- reference arm
+
+def cpu_sample(n, nslab, reps=1):
+    """Times the oracle on a bounded sample of the workload: one correction
+    pass (forward x, forward y, Thomas, inverse y, inverse x) plus one residual
+    on an Nx x Ny x nslab slab of the same stretched grid, repeated ``reps``
+    times; returns seconds per full-size refined solve (two passes and two
+    residuals over all Nz slabs), scaled by points."""
+    import oracle as O
+    import seeded_inputs as S
+    nz_full = n[2]
+    dirs = O.make_dirs((n[0], n[1], nslab), STRETCH, [(O.NEUMANN, O.NEUMANN)] * 3)
+    f = S.remove_weighted_mean(S.uniform_rhs((n[0], n[1], nslab), SEED), [d.dxf for d in dirs])
+    solver = O.TensorSolver(dirs, 0.0, 1.0)
+    best = None
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        phi = solver.direct(f)
+        O.residual(f, phi, dirs, 0.0, 1.0)
+        dt = time.perf_counter() - t0
+        best = dt if best is None else min(best, dt)
+    per_point = best / (n[0] * n[1] * nslab)
+    return 2.0 * per_point * n[0] * n[1] * nz_full
+
+
+def _threads():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        return max([i.get("num_threads", 1) for i in info] + [1])
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    n, _ = workload(args.size)
+    nslab = max(1, min(n[2], args.cpu_slabs))
+    for _ in range(args.warmup):
+        cpu_sample(n, nslab)
+    times = [cpu_sample(n, nslab) for _ in range(args.steps)]
+    s_per_solve = float(np.mean(times))
+    val = 1.0 / s_per_solve
+    sample = ("oracle (numpy float64) correction pass + residual on a %dx%dx%d slab of the "
+              "512^3 stretched Neumann grid, scaled by points to one refined solve "
+              "(2 passes + 2 residuals)" % (n[0], n[1], nslab))
+    out = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "solves/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": s_per_solve * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "poisson_512cube_tanh1.5-2.0-2.5_neumann_GG_thomas", "size": list(n),
+                   "sample": "z-slab of %d" % nslab},
+        "gpts_per_s": val * n[0] * n[1] * n[2] / 1e9,
+        "cpu_baseline": {"value": val, "unit": "solves/s", "cores": _threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------- our arm
+
+PRECISIONS = {"fp64": 0, "mixed_bf16": 1, "mixed_bf16x3": 2, "mixed_tf32": 3}
+DTYPE = {"fp64": "f64", "mixed_bf16": "bf16/f32/f64", "mixed_bf16x3": "bf16x3/f32/f64",
+         "mixed_tf32": "tf32/f32/f64"}
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2603_09528_gb300 import build as _build
+    _build.build()
+    import paper_2603_09528_gb300 as tpt
+    from paper_2603_09528_gb300 import _lib
+
+    n, stretch = workload(args.size)
+    grids = [tpt.grid_tanh(n[a], 1.0, stretch[a]) for a in range(3)]
+    prec = PRECISIONS[args.precision]
+    rtol = args.rtol if prec != 0 else 0.0
+    refine = args.max_refine if args.max_refine is not None else (1 if prec == 0 else 8)
+    plan = tpt.Plan(n, [g[0] for g in grids], [g[1] for g in grids], [(1, 1)] * 3,
+                    xform=(tpt.GEMM, tpt.GEMM), alpha=0.0, beta=1.0, precision=prec,
+                    rtol=rtol, max_refine=refine, device=local)
+    f_host = rhs_host(n, grids)
+    f_pin = torch.from_numpy(np.ascontiguousarray(f_host.ravel(order="F"))).pin_memory()
+    f_dev = f_pin.to("cuda", non_blocking=False)
+    phi = plan.new_field()
+    work = plan.new_workspace()
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # warm-up
+    info = None
+    for _ in range(args.warmup):
+        _, info = plan.solve(f_dev, phi, work, stream=stream, want_info=True)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = _lib.kernel_launches()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    evs[0].record(stream)
+    infos = []
+    for k in range(args.steps):
+        _, inf = plan.solve(f_dev, phi, work, stream=stream, want_info=rtol > 0)
+        infos.append(inf)
+        evs[k + 1].record(stream)
+    torch.cuda.synchronize()
+    l1 = _lib.kernel_launches()
+    barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    per = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
+    total_ms = evs[0].elapsed_time(evs[-1])
+    t_max = total_ms
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    solves = world * args.steps
+    value = solves / (t_max / 1e3)
+    npts = n[0] * n[1] * n[2]
+
+    # dominant kernel, timed alone on the same stream with the same launch shape
+    dom = dominant_kernel(plan, prec, n, f_dev, args.steps, stream)
+
+    # end-to-end through the host-buffer entry point
+    e2e = None
+    if not args.no_e2e:
+        phi_pin = torch.empty_like(f_pin).pin_memory()
+        f2 = plan.new_field()
+        plan.solve_host(f_pin, phi_pin, f2, phi, work, stream=stream)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            plan.solve_host(f_pin, phi_pin, f2, phi, work, stream=stream)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": solves / dt, "unit": "solves/s", "h2d_bytes_per_step": npts * 8,
+               "d2h_bytes_per_step": npts * 8}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        nslab = max(1, min(n[2], args.cpu_slabs))
+        s_per = cpu_sample(n, nslab)
+        cpu = {"value": 1.0 / s_per, "unit": "solves/s", "cores": _threads(), "kind": "oracle",
+               "sample": "oracle (numpy float64) correction pass + residual on a %dx%dx%d slab "
+                         "of the same grid, scaled by points to one refined solve" % (n[0], n[1], nslab)}
+
+    if rank == 0:
+        last = next((i for i in reversed(infos) if i), info)
+        out = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPE[args.precision], "data": "synthetic",
+            "config": {"workload": "poisson_512cube_tanh1.5-2.0-2.5_neumann_GG_thomas"
+                       if args.size == 512 else "poisson_%dcube_tanh1.5-2.0-2.5_neumann" % args.size,
+                       "size": list(n), "stretch": list(stretch), "precision": args.precision,
+                       "rtol": rtol, "max_refine": refine, "parallelism": "replicas%d" % world,
+                       "l2": "inputs larger than L2 (%.2f GB field)" % (npts * 8 / 1e9)},
+            "gpts_per_s": value * npts / 1e9,
+            "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99)),
+                           "mean20fastest": float(np.mean(sorted(per)[:20]))},
+            "solve_info": last,
+            "gpu_launches": l1 - l0,
+            "roofline": dom,
+            "clocks": clk,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def dominant_kernel(plan, prec, n, f_dev, steps, stream):
+    """Times the solve's dominant kernel alone (same kernel and launch shape as
+    inside tpt_solve) with CUDA events on the launching stream."""
+    import torch
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    out = plan.new_field()
+    reps = max(3, steps)
+    plan.transform(f_dev, 0, False, out=out, stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        plan.transform(f_dev, 0, False, out=out, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    flops = 2.0 * n[0] * n[0] * n[1] * n[2]
+    achieved = flops / (ms / 1e3) / 1e12
+    if prec == 0:
+        peak = 1.25   # GB300 float64 (FMA = DMMA), nominal; see the design doc
+        return {"kernel": "dgemm_cm_kernel (x forward transform)", "bound": "alu",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": "nominal GB300 float64 rate (MEASURED_PEAKS.json has no float64 entry)",
+                "traffic": None, "ms_per_launch": ms, "flops_per_launch": flops}
+    peak = peaks.get("bf16_tflops", 1900.0)
+    return {"kernel": "x forward transform", "bound": "tensor", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "ms_per_launch": ms}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=list(PRECISIONS))
+    ap.add_argument("--size", type=int, default=512)
+    ap.add_argument("--rtol", type=float, default=1e-10)
+    ap.add_argument("--max-refine", type=int, default=None)
+    ap.add_argument("--cpu-slabs", type=int, default=128)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -170,6 +170,12 @@ int tpt_residual(tpt_plan plan, const double* f_dev, const double* phi_dev, doub
 int tpt_plan_eigenvalues(tpt_plan plan, int dir, double* lam_host);
 int tpt_plan_rows(tpt_plan plan, int dir, double* a_host, double* b_host, double* c_host);
 
+/* ---- diagnostics -------------------------------------------------------- */
+/* Number of CUDA kernels this library has launched since it was loaded
+ * (every device, every thread); benchmarks read it before and after a timed
+ * region to count the kernels inside it.                                   */
+int tpt_kernel_launches(unsigned long long* count);
+
 /* ---- grid helper -------------------------------------------------------- */
 /* Cell widths and centre spacings of an n-cell grid on [0, L] whose faces are
  * x(k/n), k = 0..n, of Eq. (tanh_stretching) (Sec. 4.1); stretch = 0 is the

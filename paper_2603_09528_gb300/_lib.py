@@ -70,6 +70,7 @@ SIGNATURES = [
     ("tpt_plan_eigenvalues", C.c_int, [C.c_void_p, C.c_int, _dp]),
     ("tpt_plan_rows", C.c_int, [C.c_void_p, C.c_int, _dp, _dp, _dp]),
     ("tpt_grid_tanh", C.c_int, [C.c_int, C.c_double, C.c_double, _dp, _dp]),
+    ("tpt_kernel_launches", C.c_int, [C.POINTER(C.c_ulonglong)]),
 ]
 
 LIB_PATH = _build.LIB
@@ -95,6 +96,12 @@ class TptError(RuntimeError):
         self.status = status
         msg = lib.tpt_status_string(status)
         super().__init__("%s failed: %s (status %d)" % (where, msg.decode() if msg else "?", status))
+
+
+def kernel_launches() -> int:
+    v = C.c_ulonglong()
+    check(lib.tpt_kernel_launches(C.byref(v)), "tpt_kernel_launches")
+    return int(v.value)
 
 
 def check(status: int, where: str) -> int:

@@ -3,6 +3,7 @@
 // entry points.  Declarations and contracts: include/tpt.h.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -157,6 +158,10 @@ namespace tpt {
 size_t npts(const tpt_plan_s* p) {
   return static_cast<size_t>(p->n[0]) * p->n[1] * p->n[2];
 }
+namespace {
+std::atomic<unsigned long long> g_launches{0};
+}
+void note_launch(unsigned long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 }  // namespace tpt
 
 extern "C" {
@@ -174,6 +179,12 @@ const char* tpt_status_string(int status) {
     case TPT_ERR_NUMERICAL: return "numerical failure in setup";
     default: return "unknown status";
   }
+}
+
+int tpt_kernel_launches(unsigned long long* count) {
+  if (!count) return TPT_ERR_INVALID_ARG;
+  *count = tpt::g_launches.load(std::memory_order_relaxed);
+  return TPT_OK;
 }
 
 int tpt_grid_tanh(int n, double L, double stretch, double* dxf_out, double* dxc_out) {

@@ -231,6 +231,7 @@ cudaError_t field_sums(const tpt_plan_s* p, const double* f, double* sums, cudaS
   const long long n = static_cast<long long>(p->n[0]) * p->n[1] * p->n[2];
   long long nb = (n + 255) / 256;
   if (nb > 8LL * dev_sms) nb = 8LL * dev_sms;
+  note_launch();
   field_sums_kernel<<<static_cast<unsigned>(nb), 256, 0, s>>>(p->n[0], p->n[1], p->n[2], f, p->d_dxf[0],
                                                               p->d_dxf[1], p->d_dxf[2], sums);
   return cudaGetLastError();
@@ -246,6 +247,7 @@ cudaError_t dgemm_cm(int M, int N, int K, const double* A, int lda, long long sA
   for (int n0 = 0; n0 < N; n0 += nchunk) {
     const int nn = (N - n0 < nchunk) ? N - n0 : nchunk;
     dim3 grid((M + TM - 1) / TM, (nn + TN - 1) / TN, batch);
+    note_launch();
     dgemm_cm_kernel<<<grid, dim3(TX, TY), 0, s>>>(M, nn, K, A, lda, sA,
                                                   B + static_cast<long long>(n0) * ldb, ldb, sB,
                                                   C + static_cast<long long>(n0) * ldc, ldc, sC,
@@ -272,6 +274,7 @@ cudaError_t thomas_fp64(const tpt_plan_s* p, const double* fhat, double* phihat,
     for (int j = 0; j < ny; ++j) gy += p->eig[1].qt[j] * std::sqrt(p->dir[1].dxf[j]);
     null_scale = 1.0 / (gx * gy);
   }
+  note_launch();
   thomas_fp64_kernel<<<static_cast<unsigned>(nb), bs, 0, s>>>(
       nx, ny, nz, fhat, phihat, scratch, p->ddir[0].lam, p->ddir[1].lam, rz, rz + nz, rz + 2 * nz,
       p->d_dxf[2], p->alpha, p->beta, p->singular ? p->null_i : -1, p->singular ? p->null_j : -1,
@@ -284,6 +287,7 @@ cudaError_t residual_fp64(const tpt_plan_s* p, const double* f, const double* ph
   const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
   dim3 block(32, 4);
   dim3 grid((nx + 31) / 32, (ny + 3) / 4);
+  note_launch();
   residual_fp64_kernel<<<grid, block, 0, s>>>(nx, ny, nz, f, phi, r, p->d_rows[0], p->d_rows[1],
                                               p->d_rows[2], p->d_dxf[0], p->d_dxf[1], p->d_dxf[2],
                                               p->alpha, p->beta, fshift, sums);

@@ -73,6 +73,9 @@ namespace tpt {
 
 size_t npts(const tpt_plan_s* p);
 
+// Count of kernels this library has launched (all devices, all threads).
+void note_launch(unsigned long long k = 1);
+
 // ----------------------------------------------------------------- kernels
 // Batched column-major float64 GEMM: C_b = A_b B_b (+ C_b when accumulate),
 // A_b = A + b*sA (M x K, lda), B_b = B + b*sB (K x N, ldb), C_b (M x N, ldc).
