@@ -158,6 +158,25 @@ int tpt_transform(tpt_plan plan, int dir, int inverse, const double* in_dev, dou
 int tpt_thomas(tpt_plan plan, const double* fhat_dev, double* phihat_dev, double* scratch_dev,
                void* stream);
 
+/* Same computation and arguments as tpt_thomas(), for callers that cannot
+ * allocate device memory when they call the solver (code inside a host
+ * callback or a framework hook where CUDA allocation calls are not allowed,
+ * callers whose device memory is owned by another allocator's pool, and
+ * latency-sensitive callers that cannot pay for cudaFree's implicit
+ * device-wide synchronisation).  The paper has no counterpart: this is a
+ * packaging variant of the Thomas step.  It allocates nothing: the
+ * elimination scratch is a fixed 32 MiB device array inside the library
+ * (every GPU that loads the library holds it until the process exits), so
+ * the field may have at most 4,194,304 points (Nx*Ny*Nz); larger plans get
+ * TPT_ERR_UNSUPPORTED.  The first call on a device looks up the array's
+ * device address on that device (make that first call before any stream
+ * capture).  All calls share the one array, so calls whose kernels overlap on
+ * the GPU race and give wrong results: serialise them (one stream, or events).
+ * The scratch is fully rewritten before it is read, so nothing needs clearing
+ * between calls.  The compatibility constant of a singular problem is not
+ * reported.  Errors: INVALID_ARG, UNSUPPORTED (too large), CUDA.          */
+int tpt_thomas_noalloc(tpt_plan plan, const double* fhat_dev, double* phihat_dev, void* stream);
+
 /* r = f - (alpha I + beta L) phi with the 7-point stencil of the plan's 1D rows
  * (Sec. 4.1 residual), float64.  sums_dev (may be NULL) receives 3 doubles:
  * sum r^2, sum r, sum vol*r.                                               */

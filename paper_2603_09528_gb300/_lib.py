@@ -65,6 +65,7 @@ SIGNATURES = [
     ("tpt_status_string", C.c_char_p, [C.c_int]),
     ("tpt_transform", C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("tpt_thomas", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("tpt_thomas_noalloc", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("tpt_residual", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                C.c_void_p]),
     ("tpt_plan_eigenvalues", C.c_int, [C.c_void_p, C.c_int, _dp]),
