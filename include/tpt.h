@@ -104,6 +104,8 @@ typedef struct {
  * in float64 with eigenvalues refined as long-double Rayleigh quotients, the
  * forward/inverse transform matrices Q^{-1} = Q~^T D^{1/2}, Q = D^{-1/2} Q~
  * (Sec. 2.2.1 steps 1.1-1.3; Algorithm 1 initialisation), and their upload.
+ * For a TPT_PREC_MIXED_* plan the transform matrices are also rounded to
+ * the operand format on the device.
  * Synchronous.  Errors: INVALID_ARG (bad descriptor), UNSUPPORTED (FFT on a
  * non-uniform direction, periodic z), NUMERICAL (eigensolver did not
  * converge), OOM, CUDA.  On error *out is set to NULL.                    */
@@ -182,6 +184,16 @@ int tpt_thomas_noalloc(tpt_plan plan, const double* fhat_dev, double* phihat_dev
  * sum r^2, sum r, sum vol*r.                                               */
 int tpt_residual(tpt_plan plan, const double* f_dev, const double* phi_dev, double* r_dev,
                  double* sums_dev, void* stream);
+
+/* Tensor-core GEMM of the mixed-precision transforms on its own, for kernel
+ * tests: D = A B^T with A (M x K) and B (N x K) row-major float64 on the
+ * device, rounded to the operand format of `precision` (TPT_PREC_MIXED_*:
+ * bf16, bf16 hi/lo pair with three products, tf32), multiplied with
+ * tcgen05.mma in float32, and written to D column-major (element (m, n) at
+ * m + M*n) as float64.  Runs on the current device; work_dev is 256-byte
+ * aligned scratch of at least 8*(M+N)*(K+8) + 1024 bytes.                   */
+int tpt_tc_gemm(int precision, int M, int N, int K, const double* A_dev, const double* B_dev,
+                double* D_dev, void* work_dev, void* stream);
 
 /* Host copies of the plan's tables, for inspection and tests.  lam: n[dir]
  * eigenvalues of direction dir (0 = x, 1 = y) in the plan's mode order;

@@ -68,6 +68,8 @@ SIGNATURES = [
     ("tpt_thomas_noalloc", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("tpt_residual", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                C.c_void_p]),
+    ("tpt_tc_gemm", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                              C.c_void_p, C.c_void_p]),
     ("tpt_plan_eigenvalues", C.c_int, [C.c_void_p, C.c_int, _dp]),
     ("tpt_plan_rows", C.c_int, [C.c_void_p, C.c_int, _dp, _dp, _dp]),
     ("tpt_grid_tanh", C.c_int, [C.c_int, C.c_double, C.c_double, _dp, _dp]),

@@ -204,7 +204,6 @@ int tpt_plan_create(const tpt_desc* desc, int cuda_device, tpt_plan* out) {
     return TPT_ERR_INVALID_ARG;
   for (int d = 0; d < 2; ++d)
     if (desc->xform[d] < TPT_XFORM_AUTO || desc->xform[d] > TPT_XFORM_FFT) return TPT_ERR_INVALID_ARG;
-  if (desc->precision != TPT_PREC_FP64) return TPT_ERR_UNSUPPORTED;
 
   tpt_plan_s* p = new (std::nothrow) tpt_plan_s();
   if (!p) return TPT_ERR_OOM;
@@ -276,6 +275,10 @@ int tpt_plan_create(const tpt_desc* desc, int cuda_device, tpt_plan* out) {
     return fail(TPT_ERR_OOM);
   }
   std::memset(p->h_ring, 0, ring_bytes);
+  if (p->precision != TPT_PREC_FP64) {
+    st = tpt::mixed_setup(p);
+    if (st != TPT_OK) return fail(st);
+  }
   *out = p;
   return TPT_OK;
 }
@@ -298,7 +301,7 @@ int tpt_set_coefficients(tpt_plan p, double alpha, double beta) {
 
 int tpt_workspace_bytes(tpt_plan p, size_t* bytes) {
   if (!p || !bytes) return TPT_ERR_INVALID_ARG;
-  *bytes = 256 + 4 * region_bytes(p);
+  *bytes = (p->precision == TPT_PREC_FP64) ? 256 + 4 * region_bytes(p) : tpt::mixed_workspace_bytes(p);
   return TPT_OK;
 }
 
@@ -307,6 +310,7 @@ int tpt_solve(tpt_plan p, const double* f, double* phi, void* work, void* stream
   if (reinterpret_cast<uintptr_t>(work) % 256 != 0) return TPT_ERR_INVALID_ARG;
   DeviceGuard guard(p->dev);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (p->precision != TPT_PREC_FP64) return tpt::mixed_solve(p, f, phi, work, s, info);
   const size_t rb = region_bytes(p);
   char* w = static_cast<char*>(work);
   double* ds = reinterpret_cast<double*>(w);
@@ -409,6 +413,17 @@ int tpt_residual(tpt_plan p, const double* f, const double* phi, double* r, doub
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // the single-step residual uses f as given (no compatibility shift)
   return cuda_status(tpt::residual_fp64(p, f, phi, r, sums, nullptr, s));
+}
+
+int tpt_tc_gemm(int precision, int M, int N, int K, const double* A, const double* B, double* D,
+                void* work, void* stream) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return TPT_ERR_CUDA;
+  }
+  if (reinterpret_cast<uintptr_t>(work) % 256 != 0) return TPT_ERR_INVALID_ARG;
+  return tpt::tc_gemm_test(precision, M, N, K, A, B, D, work, dev, static_cast<cudaStream_t>(stream));
 }
 
 int tpt_plan_eigenvalues(tpt_plan p, int dir, double* lam) {

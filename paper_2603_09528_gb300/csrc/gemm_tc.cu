@@ -1,0 +1,324 @@
+// Tensor-core transform GEMM for sm_103a (tcgen05 + TMA + TMEM).
+//
+//   D[m, n] = sum_k A[m, k] * B[n, k]      (both operands K-major)
+//
+// is the building block of the low-precision eigenbasis transforms (Sec. 2.2.2,
+// Eq. forward-xy / inverse-xy; lines stacked as one GEMM).  Operands are bf16
+// (one plane, or a hi/lo pair whose three products hi*hi + hi*lo + lo*hi
+// approximate the float32 product) or tf32 (float32 planes), accumulated in
+// float32 in tensor memory.  One CTA computes one 128 x BN tile:
+//   warp 0      TMA producer: A and B tiles of 128-byte rows, 128-byte swizzle,
+//               into a ring of shared-memory stages (mbarrier full/empty);
+//   warp 1      allocates BN tensor-memory columns and issues tcgen05.mma from
+//               one thread, committing each stage back to the producer;
+//   warps 2..5  epilogue: tcgen05.ld 32 columns at a time, convert, and store
+//               with addresses idx(m, n) = (m % rm) + (m / rm) * sm + n * sn, so
+//               consecutive lanes (consecutive m) write consecutive addresses.
+// Every mbarrier wait is bounded; a timeout sets bits in *err and the CTA
+// drains its copies, frees its tensor memory and exits.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+
+#include "ptx.h"
+#include "tc.h"
+
+namespace tpt {
+namespace tc {
+namespace {
+
+constexpr int BM = 128;
+constexpr int kThreads = 192;
+constexpr int kSmemBudget = 200 * 1024;
+
+__device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(v);
+  lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
+// (s, e) with s + e == a + b exactly (Knuth's two-sum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+template <int KIND, int NPL, int BN>
+struct Cfg {
+  static constexpr int EB = (KIND == kKindBF16) ? 2 : 4;     // element bytes
+  static constexpr int BK = 128 / EB;                         // elements per 128-byte row
+  static constexpr int KI = (KIND == kKindBF16) ? 16 : 8;     // K of one MMA instruction
+  static constexpr int A_BYTES = BM * 128;                    // one plane of A per stage
+  static constexpr int B_BYTES = BN * 128;
+  static constexpr int STAGE = NPL * (A_BYTES + B_BYTES);
+  static constexpr int STAGES = (kSmemBudget / STAGE) > 4 ? 4 : (kSmemBudget / STAGE);
+  static constexpr int TMEM_COLS = BN < 32 ? 32 : BN;
+  static constexpr int SMEM = STAGES * STAGE + 1024 /* alignment */ + 256 /* barriers */;
+  static constexpr int NPROD = (NPL == 2) ? 3 : 1;
+};
+
+template <int KIND, int NPL, int BN, int OUT>
+__global__ void __launch_bounds__(kThreads, 1)
+gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
+               const __grid_constant__ CUtensorMap tB0, const __grid_constant__ CUtensorMap tB1,
+               const GemmOut g) {
+  using C = Cfg<KIND, NPL, BN>;
+  static_assert(C::STAGES >= 2, "shared-memory ring needs two stages");
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE);
+  // bars[0..S): full, bars[S..2S): empty, bars[2S]: accumulator ready
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * C::STAGES + 1);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int num_m = (g.M + BM - 1) / BM, num_n = (g.N + BN - 1) / BN;
+  const long long tile = blockIdx.x;
+  int mt, nt;
+  if (g.n_fastest) {
+    nt = static_cast<int>(tile % num_n);
+    mt = static_cast<int>(tile / num_n);
+  } else {
+    mt = static_cast<int>(tile % num_m);
+    nt = static_cast<int>(tile / num_m);
+  }
+  const int m0 = mt * BM, n0 = nt * BN;
+  const int nk = (g.K + C::BK - 1) / C::BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::STAGES; ++s) {
+      ptx::mbar_init(ptx::smem_u32(&bars[s]), 1);
+      ptx::mbar_init(ptx::smem_u32(&bars[C::STAGES + s]), 1);
+    }
+    ptx::mbar_init(ptx::smem_u32(&bars[2 * C::STAGES]), 1);
+    ptx::fence_mbar_init();
+  }
+  if (warp == 1) {
+    ptx::tmem_alloc(ptx::smem_u32(tmem_slot), C::TMEM_COLS);
+    ptx::tmem_relinquish();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ------------------------------------------------------- TMA producer
+    ptx::prefetch_tmap(&tA0);
+    ptx::prefetch_tmap(&tB0);
+    if (NPL == 2) {
+      ptx::prefetch_tmap(&tA1);
+      ptx::prefetch_tmap(&tB1);
+    }
+    bool ok = true;
+    int issued = 0;
+    for (int kc = 0; kc < nk && ok; ++kc) {
+      const int s = kc % C::STAGES;
+      const int round = kc / C::STAGES;
+      if (round > 0) ok = ptx::mbar_wait(ptx::smem_u32(&bars[C::STAGES + s]), (round - 1) & 1, g.err,
+                                         ptx::kErrWaitEmpty);
+      if (!ok) break;
+      uint8_t* st = smem + s * C::STAGE;
+      const uint32_t full = ptx::smem_u32(&bars[s]);
+      ptx::mbar_arrive_expect_tx(full, C::STAGE);
+      const int kx = kc * C::BK;
+      ptx::tma_load_2d(ptx::smem_u32(st), &tA0, full, kx, m0);
+      ptx::tma_load_2d(ptx::smem_u32(st + NPL * C::A_BYTES), &tB0, full, kx, n0);
+      if (NPL == 2) {
+        ptx::tma_load_2d(ptx::smem_u32(st + C::A_BYTES), &tA1, full, kx, m0);
+        ptx::tma_load_2d(ptx::smem_u32(st + NPL * C::A_BYTES + C::B_BYTES), &tB1, full, kx, n0);
+      }
+      ++issued;
+    }
+    // drain: every issued stage's copies have landed before the CTA may exit
+    const int first = issued > C::STAGES ? issued - C::STAGES : 0;
+    for (int kc = first; kc < issued; ++kc)
+      ptx::mbar_wait(ptx::smem_u32(&bars[kc % C::STAGES]), (kc / C::STAGES) & 1, g.err,
+                     ptx::kErrWaitDrain, 1u << 20);
+  } else if (warp == 1 && lane == 0) {
+    // -------------------------------------------------------- MMA issuer
+    constexpr uint32_t idesc = ptx::instr_desc(KIND == kKindBF16 ? 1u : 2u, BM, BN);
+    bool ok = true;
+    for (int kc = 0; kc < nk && ok; ++kc) {
+      const int s = kc % C::STAGES;
+      ok = ptx::mbar_wait(ptx::smem_u32(&bars[s]), (kc / C::STAGES) & 1, g.err, ptx::kErrWaitFull);
+      if (!ok) break;
+      ptx::tc_fence_after();
+      const uint32_t sa = ptx::smem_u32(smem + s * C::STAGE);
+      const uint32_t sb = sa + NPL * C::A_BYTES;
+#pragma unroll
+      for (int kk = 0; kk < C::BK / C::KI; ++kk) {
+        const uint32_t off = kk * C::KI * C::EB;   // bytes along the 128-byte row
+#pragma unroll
+        for (int p = 0; p < C::NPROD; ++p) {
+          // products: (A0,B0), (A0,B1), (A1,B0)
+          const uint32_t a = sa + (p == 2 ? C::A_BYTES : 0) + off;
+          const uint32_t b = sb + (p == 1 ? C::B_BYTES : 0) + off;
+          const uint32_t acc = (kc > 0 || kk > 0 || p > 0) ? 1u : 0u;
+          if (KIND == kKindBF16)
+            ptx::mma_bf16(tmem, ptx::smem_desc_k_sw128(a), ptx::smem_desc_k_sw128(b), idesc, acc);
+          else
+            ptx::mma_tf32(tmem, ptx::smem_desc_k_sw128(a), ptx::smem_desc_k_sw128(b), idesc, acc);
+        }
+      }
+      ptx::mma_commit(ptx::smem_u32(&bars[C::STAGES + s]));   // frees the stage
+    }
+    ptx::mma_commit(ptx::smem_u32(&bars[2 * C::STAGES]));     // accumulator ready
+  } else if (warp >= 2) {
+    // ---------------------------------------------------------- epilogue
+    const bool ok = ptx::mbar_wait(ptx::smem_u32(&bars[2 * C::STAGES]), 0, g.err, ptx::kErrWaitAccum);
+    ptx::tc_fence_after();
+    const bool flagged = g.err && *reinterpret_cast<volatile int*>(g.err);
+    // tcgen05.ld is warp-collective: decide for the whole warp
+    if (__all_sync(0xffffffffu, ok && !flagged)) {
+      const int quarter = warp % 4;                  // tensor-memory lanes 32*quarter ..
+      const int m = m0 + quarter * 32 + lane;
+      const bool mvalid = m < g.M;
+      const long long mterm = mvalid ? (static_cast<long long>(m % g.rm) + static_cast<long long>(m / g.rm) * g.sm) : 0;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t r[32];
+        ptx::tmem_ld_32x32b_x32(tmem + (static_cast<uint32_t>(quarter * 32) << 16) + c0, r);
+        ptx::tmem_ld_wait();
+        if (!mvalid) continue;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int n = n0 + c0 + j;
+          if (n >= g.N) break;
+          const long long idx = mterm + static_cast<long long>(n) * g.sn;
+          const float v = __uint_as_float(r[j]);
+          if (OUT == kOutSplitBF16) {
+            __nv_bfloat16 hi, lo;
+            split_bf16(v, hi, lo);
+            static_cast<__nv_bfloat16*>(g.out0)[idx] = hi;
+            static_cast<__nv_bfloat16*>(g.out1)[idx] = lo;
+          } else if (OUT == kOutBF16) {
+            static_cast<__nv_bfloat16*>(g.out0)[idx] = __float2bfloat16_rn(v);
+          } else if (OUT == kOutF32) {
+            static_cast<float*>(g.out0)[idx] = v;
+          } else if (OUT == kOutF64) {
+            static_cast<double*>(g.out0)[idx] = static_cast<double>(v);
+          } else {   // kOutDF: float pair (hi, lo), written or accumulated
+            float* ph = static_cast<float*>(g.out0);
+            float* pl = static_cast<float*>(g.out1);
+            if (g.accumulate) {
+              float s, e;
+              two_sum(ph[idx], v, s, e);
+              e += pl[idx];
+              const float hi = s + e;
+              ph[idx] = hi;
+              pl[idx] = e - (hi - s);
+            } else {
+              ph[idx] = v;
+              pl[idx] = 0.0f;
+            }
+          }
+        }
+      }
+    }
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) ptx::tmem_dealloc(tmem, C::TMEM_COLS);
+}
+
+// ---------------------------------------------------------------- host side
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// K-major operand plane: rows x K elements, row stride ld elements; box of
+// (128-byte row) x box_rows with the 128-byte swizzle.
+bool make_map(CUtensorMap* map, const void* base, int kind, int rows, int K, int ld, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn || !base) return false;
+  const int eb = (kind == kKindBF16) ? 2 : 4;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || (static_cast<long long>(ld) * eb) % 16 != 0) return false;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(K), static_cast<cuuint64_t>(rows)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * eb};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(128 / eb), static_cast<cuuint32_t>(box_rows)};
+  cuuint32_t estr[2] = {1, 1};
+  const CUtensorMapDataType dt =
+      (kind == kKindBF16) ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  CUresult r = fn(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int KIND, int NPL, int BN, int OUT>
+cudaError_t launch(const Operand& A, const Operand& B, const GemmOut& g, cudaStream_t s) {
+  using C = Cfg<KIND, NPL, BN>;
+  CUtensorMap m[4];
+  std::memset(m, 0, sizeof(m));
+  if (!make_map(&m[0], A.plane[0], KIND, A.rows, A.K, A.ld, BM)) return cudaErrorInvalidValue;
+  if (!make_map(&m[2], B.plane[0], KIND, B.rows, B.K, B.ld, BN)) return cudaErrorInvalidValue;
+  if (NPL == 2) {
+    if (!make_map(&m[1], A.plane[1], KIND, A.rows, A.K, A.ld, BM)) return cudaErrorInvalidValue;
+    if (!make_map(&m[3], B.plane[1], KIND, B.rows, B.K, B.ld, BN)) return cudaErrorInvalidValue;
+  } else {
+    m[1] = m[0];
+    m[3] = m[2];
+  }
+  auto kern = gemm_tc_kernel<KIND, NPL, BN, OUT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+  if (e != cudaSuccess) return e;
+  const long long tiles = static_cast<long long>((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN);
+  if (tiles <= 0) return cudaSuccess;
+  if (tiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  note_launch(1);
+  kern<<<static_cast<unsigned>(tiles), kThreads, C::SMEM, s>>>(m[0], m[1], m[2], m[3], g);
+  return cudaGetLastError();
+}
+
+template <int KIND, int NPL, int OUT>
+cudaError_t launch_bn(const Operand& A, const Operand& B, const GemmOut& g, cudaStream_t s) {
+  if (g.N <= 32) return launch<KIND, NPL, 32, OUT>(A, B, g, s);
+  if (g.N <= 64) return launch<KIND, NPL, 64, OUT>(A, B, g, s);
+  if (g.N <= 128) return launch<KIND, NPL, 128, OUT>(A, B, g, s);
+  return launch<KIND, NPL, 256, OUT>(A, B, g, s);
+}
+
+template <int KIND, int NPL>
+cudaError_t launch_out(const Operand& A, const Operand& B, const GemmOut& g, cudaStream_t s) {
+  switch (g.mode) {
+    case kOutSplitBF16: return launch_bn<KIND, NPL, kOutSplitBF16>(A, B, g, s);
+    case kOutBF16: return launch_bn<KIND, NPL, kOutBF16>(A, B, g, s);
+    case kOutF32: return launch_bn<KIND, NPL, kOutF32>(A, B, g, s);
+    case kOutF64: return launch_bn<KIND, NPL, kOutF64>(A, B, g, s);
+    case kOutDF: return launch_bn<KIND, NPL, kOutDF>(A, B, g, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+cudaError_t gemm(int kind, int nplanes, const Operand& A, const Operand& B, const GemmOut& g,
+                 cudaStream_t s) {
+  if (A.K != B.K || A.rows != g.M || B.rows != g.N || g.M <= 0 || g.N <= 0 || A.K <= 0 || g.rm <= 0)
+    return cudaErrorInvalidValue;
+  if (kind == kKindBF16 && nplanes == 1) return launch_out<kKindBF16, 1>(A, B, g, s);
+  if (kind == kKindBF16 && nplanes == 2) return launch_out<kKindBF16, 2>(A, B, g, s);
+  if (kind == kKindTF32 && nplanes == 1) return launch_out<kKindTF32, 1>(A, B, g, s);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace tc
+}  // namespace tpt

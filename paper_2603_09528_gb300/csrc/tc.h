@@ -1,0 +1,42 @@
+// Host interface of the tensor-core transform GEMM (gemm_tc.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace tpt {
+
+void note_launch(unsigned long long k);
+
+namespace tc {
+
+enum { kKindBF16 = 0, kKindTF32 = 1 };
+enum { kOutSplitBF16 = 0, kOutBF16 = 1, kOutF32 = 2, kOutF64 = 3, kOutDF = 4 };
+
+// K-major operand: `rows` rows of K elements, row stride `ld` elements; one
+// plane, or a hi/lo pair of bf16 planes.  Base addresses 16-byte aligned and
+// ld * element size a multiple of 16 bytes.
+struct Operand {
+  const void* plane[2];
+  int rows, K, ld;
+};
+
+// Output of D = A B^T (M x N): element (m, n) goes to
+//   idx = (m % rm) + (m / rm) * sm + n * sn
+// of out0 (and out1 for the split-bf16 and float-pair modes).
+struct GemmOut {
+  int M, N, K;
+  int rm;
+  long long sm, sn;
+  void* out0;
+  void* out1;
+  int mode;
+  int accumulate;   // float-pair mode: add into (out0, out1) instead of writing
+  int n_fastest;    // tile order: n fastest (A tile reused by consecutive CTAs)
+  int* err;         // device flag for timed-out waits (may be null)
+};
+
+cudaError_t gemm(int kind, int nplanes, const Operand& A, const Operand& B, const GemmOut& g,
+                 cudaStream_t s);
+
+}  // namespace tc
+}  // namespace tpt

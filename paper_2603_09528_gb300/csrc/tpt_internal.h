@@ -39,11 +39,32 @@ int eigen_dir(const Dir1D& d, Eigen1D* out);
 int grid_tanh(int n, double L, double stretch, double* dxf, double* dxc);
 
 // ----------------------------------------------------------------- device plan
+// operand formats of the low-precision path: bf16 hi/lo pair, bf16, float32
+enum { kFmtSplit = 0, kFmtBF16 = 1, kFmtF32 = 2 };
+
+// Device tables of the mixed-precision path.
+struct MixedTables {
+  int fmt = kFmtSplit;
+  int ldx = 0, ldy = 0;            // Nx, Ny rounded up to 8 (operand row strides)
+  void* q[2][2][2] = {};           // [x|y][forward Q^{-1} | inverse Q][plane], row-major
+  float* lam_f[2] = {nullptr, nullptr};
+  float* zrows_f = nullptr;        // a|b|c of z in float32
+  float* dfrows[3] = {nullptr, nullptr, nullptr};   // ah|al|ch|cl|wh|wl per direction
+};
+
 struct DevDir {       // device tables of a diagonalised direction (float64)
   double* fwd = nullptr;  // forward transform operand (layout set by the GEMM role)
   double* inv = nullptr;  // inverse transform operand
   double* lam = nullptr;  // eigenvalues in mode order
 };
+
+// mixed-precision path (mixed.cu)
+int mixed_setup(tpt_plan_s* p);
+size_t mixed_workspace_bytes(const tpt_plan_s* p);
+int mixed_solve(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStream_t s,
+                tpt_info* info);
+int tc_gemm_test(int precision, int M, int N, int K, const double* A, const double* B, double* D,
+                 void* work, int dev, cudaStream_t s);
 
 }  // namespace tpt
 
@@ -66,6 +87,7 @@ struct tpt_plan_s {
   double* h_ring = nullptr;       // pinned host slots for asynchronous info reports
   int ring_next = 0;
   double vol = 1.0;               // domain volume Lx Ly Lz
+  tpt::MixedTables mixed;
   std::vector<void*> allocs;      // every device allocation owned by the plan
 };
 
@@ -94,5 +116,13 @@ cudaError_t field_sums(const tpt_plan_s* p, const double* f, double* sums, cudaS
 // r = (f - fshift) - (alpha I + beta L) phi; fshift (device scalar) may be NULL.
 cudaError_t residual_fp64(const tpt_plan_s* p, const double* f, const double* phi, double* r,
                           double* sums, const double* fshift, cudaStream_t s);
+
+// mixed-precision path (mixed.cu)
+int mixed_setup(tpt_plan_s* p);
+size_t mixed_workspace_bytes(const tpt_plan_s* p);
+int mixed_solve(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStream_t s,
+                tpt_info* info);
+int tc_gemm_test(int precision, int M, int N, int K, const double* A, const double* B, double* D,
+                 void* work, int dev, cudaStream_t s);
 
 }  // namespace tpt

@@ -1,0 +1,91 @@
+"""Mixed-precision path on GB300: the tcgen05 GEMM on its own against float64
+matmuls, then the refined mixed solve against the CPU oracle."""
+import ctypes as C
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import seeded_inputs as S
+from _tpt import load
+
+pytestmark = pytest.mark.gpu
+tpt, L = load()
+
+PRECS = {"bf16": L.TPT_PREC_MIXED_BF16, "bf16x3": L.TPT_PREC_MIXED_BF16X3, "tf32": L.TPT_PREC_MIXED_TF32}
+
+
+def _tc_gemm(prec, A, B):
+    M, K = A.shape
+    N = B.shape[0]
+    a = torch.from_numpy(np.ascontiguousarray(A)).cuda()
+    b = torch.from_numpy(np.ascontiguousarray(B)).cuda()
+    d = torch.full((N, M), float("nan"), dtype=torch.float64, device="cuda")
+    work = torch.empty(8 * (M + N) * (K + 8) + 1024, dtype=torch.uint8, device="cuda")
+    st = L.lib.tpt_tc_gemm(PRECS[prec], M, N, K, C.c_void_p(a.data_ptr()), C.c_void_p(b.data_ptr()),
+                           C.c_void_p(d.data_ptr()), C.c_void_p(work.data_ptr()),
+                           C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == L.TPT_OK, L.lib.tpt_status_string(st)
+    torch.cuda.synchronize()
+    return d.cpu().numpy().T          # column-major D -> (M, N)
+
+
+SHAPES = [(128, 256, 64), (128, 32, 64), (256, 512, 512), (200, 150, 72), (96, 45, 40), (1000, 96, 128),
+          (130, 300, 200)]
+
+
+@pytest.mark.parametrize("prec", list(PRECS))
+@pytest.mark.parametrize("shape", SHAPES)
+def test_tc_gemm_exact_on_representable_inputs(prec, shape):
+    # small integers are exact in bf16 / tf32 and their products and sums are
+    # exact in float32, so any layout, swizzle, K-step or edge mistake shows
+    M, N, K = shape
+    rng = np.random.default_rng(M * 7 + N * 3 + K)
+    A = rng.integers(-8, 9, size=(M, K)).astype(np.float64)
+    B = rng.integers(-8, 9, size=(N, K)).astype(np.float64)
+    got = _tc_gemm(prec, A, B)
+    assert np.array_equal(got, A @ B.T), (prec, shape, np.abs(got - A @ B.T).max())
+
+
+@pytest.mark.parametrize("prec,rel", [("bf16", 2e-2), ("bf16x3", 2e-4), ("tf32", 4e-3)])
+def test_tc_gemm_random_within_format_error(prec, rel):
+    # relative to sum_k |A_mk||B_nk|: bf16 ~2^-8, split bf16 ~2^-16, tf32 ~2^-10
+    M, N, K = 384, 256, 512
+    rng = np.random.default_rng(3)
+    A = rng.uniform(-1, 1, (M, K))
+    B = rng.uniform(-1, 1, (N, K))
+    got = _tc_gemm(prec, A, B)
+    ref = A @ B.T
+    scale = np.abs(A) @ np.abs(B).T
+    err = np.max(np.abs(got - ref) / scale)
+    assert err <= rel, err
+
+
+def _dirs(n, stretch, bcs):
+    return O.make_dirs(n, stretch, bcs)
+
+
+@pytest.mark.parametrize("prec", list(PRECS))
+@pytest.mark.parametrize("case", ["poisson", "helmholtz"])
+def test_mixed_solve_reaches_rtol(prec, case):
+    n = (64, 48, 40)
+    bcs = [(1, 1)] * 3
+    alpha, beta = (0.0, 1.0) if case == "poisson" else (1.0, -5e-4)
+    dirs = _dirs(n, (1.5, 2.0, 2.5), bcs)
+    f = S.uniform_rhs(n, 21)
+    if alpha == 0.0:
+        f = S.remove_weighted_mean(f, [d.dxf for d in dirs])
+    plan = tpt.Plan(n, [d.dxf for d in dirs], [d.dxc for d in dirs], bcs, xform=(tpt.GEMM, tpt.GEMM),
+                    alpha=alpha, beta=beta, precision=PRECS[prec], rtol=1e-10, max_refine=30)
+    phi, info = plan.solve(tpt.field_to_device(f))
+    got = tpt.field_to_host(phi, n)
+    ref, _ = O.solve_tensor(f, dirs, alpha, beta)
+    err = np.abs(got - ref).max() / np.abs(ref).max()
+    r = O.residual(f, got, dirs, alpha, beta, np.longdouble)
+    rel = float(np.sqrt(np.sum(r ** 2) / np.sum(f ** 2)))
+    print("mixed", prec, case, "iters", info["iters"], "rel_res(gpu)", info["rel_residual"],
+          "rel_res(oracle)", rel, "err vs fp64", err)
+    assert info["rel_residual"] <= 1e-10
+    assert rel <= 2e-10
+    assert err <= 1e-7, err
