@@ -217,6 +217,8 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
+    if prec != 0:
+        plan.set_stage_timing(True)
     # warm-up
     info = None
     for _ in range(args.warmup):
@@ -232,7 +234,7 @@ def run_ours(args):
     evs[0].record(stream)
     infos = []
     for k in range(args.steps):
-        _, inf = plan.solve(f_dev, phi, work, stream=stream, want_info=rtol > 0)
+        _, inf = plan.solve(f_dev, phi, work, stream=stream, want_info=(rtol > 0 or prec != 0))
         infos.append(inf)
         evs[k + 1].record(stream)
     torch.cuda.synchronize()
@@ -250,9 +252,42 @@ def run_ours(args):
     solves = world * args.steps
     value = solves / (t_max / 1e3)
     npts = n[0] * n[1] * n[2]
+    stages = None
+    if prec != 0 and infos and infos[0]:
+        ms = np.mean([i["ms_stage"] for i in infos], axis=0)
+        its = float(np.mean([i["iters"] for i in infos]))
+        stages = stage_rooflines(ms, its, n, prec)
+        plan.set_stage_timing(False)
 
-    # dominant kernel, timed alone on the same stream with the same launch shape
-    dom = dominant_kernel(plan, prec, n, f_dev, args.steps, stream)
+    # roofline of the dominant kernel
+    if prec == 0:
+        dom = dominant_kernel(plan, prec, n, f_dev, args.steps, stream)
+    else:
+        dom = max(stages["per_stage"], key=lambda d: d["ms_per_launch"] * d["launches_per_solve"])
+
+    # float64 path on the same workload, for the FP64-vs-mixed comparison
+    fp64 = None
+    if prec != 0 and not args.no_fp64:
+        plan64 = tpt.Plan(n, [g[0] for g in grids], [g[1] for g in grids], [(1, 1)] * 3,
+                          xform=(tpt.GEMM, tpt.GEMM), alpha=0.0, beta=1.0, precision=0,
+                          max_refine=1, device=local)
+        w64 = plan64.new_workspace()
+        phi64 = plan64.new_field()
+        _, i64 = plan64.solve(f_dev, phi64, w64, stream=stream, want_info=True)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 2
+        a.record(stream)
+        for _ in range(reps):
+            plan64.solve(f_dev, phi64, w64, stream=stream, want_info=False)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms64 = a.elapsed_time(b) / reps
+        diff = (phi - phi64).abs().max().item() / phi64.abs().max().item()
+        fp64 = {"solves_per_s": world * 1e3 / ms64, "ms_per_solve": ms64, "steps": reps,
+                "rel_residual": i64["rel_residual"], "mixed_vs_fp64_max_rel_diff": diff}
+        del w64, phi64, plan64
+        torch.cuda.empty_cache()
 
     # end-to-end through the host-buffer entry point
     e2e = None
@@ -297,7 +332,9 @@ def run_ours(args):
             "gpts_per_s": value * npts / 1e9,
             "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99)),
                            "mean20fastest": float(np.mean(sorted(per)[:20]))},
-            "solve_info": last,
+            "solve_info": {k: v for k, v in (last or {}).items() if k != "ms_stage"},
+            "stages": stages,
+            "fp64": fp64,
             "gpu_launches": l1 - l0,
             "roofline": dom,
             "clocks": clk,
@@ -308,6 +345,50 @@ def run_ours(args):
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def stage_rooflines(ms, iters, n, prec):
+    """Per-stage achieved rates from the solve's own CUDA-event stage timings.
+    Algorithmic work per point and launch: transforms 2*N_alpha flop per
+    product (3 products for split bf16) and their operand/result bytes;
+    Thomas and residual their field bytes."""
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    tflops = peaks.get("bf16_tflops", 1900.0)
+    if prec == 3:
+        tflops = tflops / 2.0          # tf32 dense rate is half the bf16 rate
+    npts = float(n[0] * n[1] * n[2])
+    eb = {1: 2, 2: 4, 3: 4}[prec]      # bytes per stored intermediate value
+    prods = 3 if prec == 2 else 1
+    names = ["prepare", "x_forward", "y_forward", "thomas", "y_inverse", "x_inverse", "residual"]
+    out = []
+    for i, nm in enumerate(names[1:], start=1):
+        per_launch = ms[i] / max(iters, 1)
+        if nm in ("x_forward", "y_forward", "y_inverse", "x_inverse"):
+            na = n[0] if nm.startswith("x") else n[1]
+            flops = 2.0 * na * npts * prods
+            byts = npts * (eb + (16 if nm == "x_inverse" else eb))
+            t_tensor = flops / (tflops * 1e12)
+            t_hbm = byts / (hbm * 1e9)
+            if t_tensor >= t_hbm:
+                d = {"bound": "tensor", "achieved": flops / (per_launch / 1e3) / 1e12, "peak": tflops,
+                     "unit": "TFLOP/s"}
+            else:
+                d = {"bound": "hbm", "achieved": byts / (per_launch / 1e3) / 1e9, "peak": hbm, "unit": "GB/s"}
+            d["flops_per_launch"] = flops
+        else:
+            byts = npts * (2 * eb if nm == "thomas" else 8 + 8 + eb)
+            d = {"bound": "hbm", "achieved": byts / (per_launch / 1e3) / 1e9, "peak": hbm, "unit": "GB/s"}
+        d.update({"kernel": nm, "ms_per_launch": per_launch, "launches_per_solve": iters,
+                  "bytes_per_launch": byts, "traffic": None})
+        d["frac"] = d["achieved"] / d["peak"]
+        out.append(d)
+    return {"per_stage": out, "iters": iters, "peak_source": "MEASURED_PEAKS.json (burst)"}
 
 
 def dominant_kernel(plan, prec, n, f_dev, steps, stream):
@@ -350,7 +431,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=list(PRECISIONS))
+    ap.add_argument("--precision", default="mixed_bf16x3", choices=list(PRECISIONS))
+    ap.add_argument("--no-fp64", action="store_true", help="skip the float64-path comparison leg")
     ap.add_argument("--size", type=int, default=512)
     ap.add_argument("--rtol", type=float, default=1e-10)
     ap.add_argument("--max-refine", type=int, default=None)

@@ -93,7 +93,10 @@ typedef struct {
                             -1 when no residual was evaluated                      */
   double compat_defect;  /* singular problems: cell-volume-weighted mean removed
                             from f to make it compatible; 0 otherwise              */
-  float ms_stage[8];     /* reserved for per-stage timings (0 unless measured)     */
+  float ms_stage[8];     /* with tpt_set_stage_timing(plan, 1), mixed plans: GPU
+                            milliseconds summed over the corrections of the call,
+                            [1] x forward, [2] y forward, [3] Thomas, [4] y inverse,
+                            [5] x inverse, [6] residual; 0 otherwise              */
 } tpt_info;
 
 /* Build a plan on CUDA device `cuda_device` (or, with cuda_device < 0, a
@@ -206,6 +209,12 @@ int tpt_plan_rows(tpt_plan plan, int dir, double* a_host, double* b_host, double
  * (every device, every thread); benchmarks read it before and after a timed
  * region to count the kernels inside it.                                   */
 int tpt_kernel_launches(unsigned long long* count);
+
+/* Record CUDA events around each stage of tpt_solve on a TPT_PREC_MIXED_*
+ * plan and report the summed stage times in tpt_info.ms_stage (filled only
+ * when `info` is given; the call then synchronises the stream once per
+ * correction).  enable = 0 turns it off.                                    */
+int tpt_set_stage_timing(tpt_plan plan, int enable);
 
 /* ---- grid helper -------------------------------------------------------- */
 /* Cell widths and centre spacings of an n-cell grid on [0, L] whose faces are

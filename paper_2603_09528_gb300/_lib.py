@@ -74,6 +74,7 @@ SIGNATURES = [
     ("tpt_plan_rows", C.c_int, [C.c_void_p, C.c_int, _dp, _dp, _dp]),
     ("tpt_grid_tanh", C.c_int, [C.c_int, C.c_double, C.c_double, _dp, _dp]),
     ("tpt_kernel_launches", C.c_int, [C.POINTER(C.c_ulonglong)]),
+    ("tpt_set_stage_timing", C.c_int, [C.c_void_p, C.c_int]),
 ]
 
 LIB_PATH = _build.LIB

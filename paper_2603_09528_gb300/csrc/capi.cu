@@ -58,6 +58,8 @@ void free_plan(tpt_plan_s* p) {
   if (!p) return;
   if (p->dev >= 0 && (!p->allocs.empty() || p->h_ring)) {
     DeviceGuard g(p->dev);
+    for (cudaEvent_t e : p->ev)
+      if (e) cudaEventDestroy(e);
     for (void* a : p->allocs) cudaFree(a);
     if (p->h_ring) cudaFreeHost(p->h_ring);
   }
@@ -296,6 +298,10 @@ int tpt_set_coefficients(tpt_plan p, double alpha, double beta) {
   p->beta = beta;
   p->singular = (alpha == 0.0) && p->dir[0].has_null() && p->dir[1].has_null() &&
                 p->dir[2].has_null();
+  if (p->precision != TPT_PREC_FP64 && p->dev >= 0 && p->mixed.dfrows[0]) {
+    DeviceGuard guard(p->dev);
+    return tpt::mixed_set_beta(p);
+  }
   return TPT_OK;
 }
 
@@ -424,6 +430,12 @@ int tpt_tc_gemm(int precision, int M, int N, int K, const double* A, const doubl
   }
   if (reinterpret_cast<uintptr_t>(work) % 256 != 0) return TPT_ERR_INVALID_ARG;
   return tpt::tc_gemm_test(precision, M, N, K, A, B, D, work, dev, static_cast<cudaStream_t>(stream));
+}
+
+int tpt_set_stage_timing(tpt_plan p, int enable) {
+  if (!p) return TPT_ERR_INVALID_ARG;
+  p->stage_timing = enable ? 1 : 0;
+  return TPT_OK;
 }
 
 int tpt_plan_eigenvalues(tpt_plan p, int dir, double* lam) {

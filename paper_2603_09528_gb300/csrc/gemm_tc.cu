@@ -185,6 +185,33 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
         ptx::tmem_ld_32x32b_x32(tmem + (static_cast<uint32_t>(quarter * 32) << 16) + c0, r);
         ptx::tmem_ld_wait();
         if (!mvalid) continue;
+        if (OUT == kOutDF) {
+          // read-modify-write of the float pair: issue every load of the chunk
+          // before any dependent arithmetic so the 64 loads overlap
+          float* ph = static_cast<float*>(g.out0);
+          float* pl = static_cast<float*>(g.out1);
+          float oh[32], ol[32];
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int n = n0 + c0 + j;
+            const long long idx = mterm + static_cast<long long>(n < g.N ? n : 0) * g.sn;
+            oh[j] = (g.accumulate && n < g.N) ? ph[idx] : 0.0f;
+            ol[j] = (g.accumulate && n < g.N) ? pl[idx] : 0.0f;
+          }
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int n = n0 + c0 + j;
+            if (n >= g.N) break;
+            const long long idx = mterm + static_cast<long long>(n) * g.sn;
+            float sh, se;
+            two_sum(oh[j], __uint_as_float(r[j]), sh, se);
+            se += ol[j];
+            const float hi = sh + se;
+            ph[idx] = hi;
+            pl[idx] = se - (hi - sh);
+          }
+          continue;
+        }
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int n = n0 + c0 + j;
@@ -202,20 +229,6 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
             static_cast<float*>(g.out0)[idx] = v;
           } else if (OUT == kOutF64) {
             static_cast<double*>(g.out0)[idx] = static_cast<double>(v);
-          } else {   // kOutDF: float pair (hi, lo), written or accumulated
-            float* ph = static_cast<float*>(g.out0);
-            float* pl = static_cast<float*>(g.out1);
-            if (g.accumulate) {
-              float s, e;
-              two_sum(ph[idx], v, s, e);
-              e += pl[idx];
-              const float hi = s + e;
-              ph[idx] = hi;
-              pl[idx] = e - (hi - s);
-            } else {
-              ph[idx] = v;
-              pl[idx] = 0.0f;
-            }
           }
         }
       }

@@ -62,6 +62,41 @@ __device__ __forceinline__ df df_from_double(double v) {
   const float h = static_cast<float>(v);
   return {h, static_cast<float>(v - static_cast<double>(h))};
 }
+// the rare-path conversion, kept out of line so the compiler cannot predicate
+// its float64 instructions into the common path
+__device__ __noinline__ df df_from_double_slow(double v) { return df_from_double(v); }
+
+// float64 -> float pair with integer operations only (GB300's float64 pipe,
+// which also runs float64 conversions, is ~1/55 of the float32 rate): hi
+// takes the leading 24 significant bits, lo the remaining 29 truncated to 24,
+// so hi + lo equals v to 2^-47 relative.  Zero, |v| < 2^-47 and values beyond
+// the float range go through the conversion instructions instead.
+__device__ __forceinline__ df split_double_int(double v) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
+  const unsigned sign = static_cast<unsigned>(b >> 63) << 31;
+  const int e = static_cast<int>((b >> 52) & 0x7FF);
+  const int fe = e - 896;                            // float biased exponent of hi
+  if (fe < 80 || fe >= 255) return df_from_double_slow(v);   // keeps lo a normal float
+  const unsigned long long m = b & ((1ull << 52) - 1);
+  const float hi = __uint_as_float(sign | (static_cast<unsigned>(fe) << 23) | static_cast<unsigned>(m >> 29));
+  const unsigned r = static_cast<unsigned>(m & ((1u << 29) - 1));
+  if (r == 0) return {hi, 0.0f};
+  const int p = 31 - __clz(r);                       // leading bit of the remainder
+  const int le = fe - 52 + p;                        // its float biased exponent (> 0 here)
+  const unsigned frac = ((r << (31 - p)) << 1) >> 9; // bits below the leading one, 23 kept
+  return {hi, __uint_as_float(sign | (static_cast<unsigned>(le) << 23) | frac)};
+}
+
+// float -> float64, exact, with integer operations (normal numbers and zero).
+__device__ __forceinline__ double f2d_int(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xFF;
+  if (e == 0 || e == 255) return static_cast<double>(f);
+  const unsigned long long b = (static_cast<unsigned long long>(u >> 31) << 63) |
+                               (static_cast<unsigned long long>(e + 896) << 52) |
+                               (static_cast<unsigned long long>(u & 0x7FFFFF) << 29);
+  return __longlong_as_double(static_cast<long long>(b));
+}
 
 // ------------------------------------------------------ operand element I/O
 template <int FMT>
@@ -103,201 +138,385 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-// f (float64, (Nx,Ny,Nz)) -> f as float pair, R = f in operand format, and the
-// sums (sum f^2, sum f, sum vol*f) into sums[0..2].
+// f (float64, (Nx,Ny,Nz)) -> f as float pair, R = f in operand format, and
+// the sums sum f^2 (float), sum f and sum vol*f (float pairs) added to
+// sums[0..2].  No float64 arithmetic per point.
 template <int FMT>
 __global__ void __launch_bounds__(256)
 prepare_kernel(int nx, int ny, int nz, int ldx, const double* __restrict__ f, float* __restrict__ fh,
-               float* __restrict__ fl, void* r0, void* r1, const double* __restrict__ dxf,
-               const double* __restrict__ dyf, const double* __restrict__ dzf, double* sums) {
+               float* __restrict__ fl, void* r0, void* r1, const float* __restrict__ gx,
+               const float* __restrict__ gy, const float* __restrict__ gz, double* sums) {
   const long long n = static_cast<long long>(nx) * ny * nz;
-  double s2 = 0.0, s1 = 0.0, sv = 0.0;
+  float s2 = 0.0f;
+  df s1 = {0.0f, 0.0f}, sv = {0.0f, 0.0f};
   for (long long o = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; o < n;
        o += static_cast<long long>(gridDim.x) * blockDim.x) {
     const int i = static_cast<int>(o % nx);
     const long long line = o / nx;
     const int j = static_cast<int>(line % ny), k = static_cast<int>(line / ny);
-    const double v = f[o];
-    const df d = df_from_double(v);
+    const df d = split_double_int(f[o]);
     fh[o] = d.hi;
     fl[o] = d.lo;
     Elem<FMT>::store(r0, r1, i + static_cast<long long>(ldx) * line, d.hi + d.lo);
-    s2 = fma(v, v, s2);
-    s1 += v;
-    sv = fma(dxf[i] * dyf[j] * dzf[k], v, sv);
+    s2 = fmaf(d.hi, d.hi, s2);
+    s1 = df_add(s1, d);
+    const df vol = df_mul(df_mul({gx[i], gx[nx + i]}, {gy[j], gy[ny + j]}), {gz[k], gz[nz + k]});
+    sv = df_add(sv, df_mul(vol, d));
   }
-  s2 = warp_sum_d(s2);
-  s1 = warp_sum_d(s1);
-  sv = warp_sum_d(sv);
+  double a = s2, b = static_cast<double>(s1.hi) + s1.lo, c = static_cast<double>(sv.hi) + sv.lo;
+  a = warp_sum_d(a);
+  b = warp_sum_d(b);
+  c = warp_sum_d(c);
   if (threadIdx.x % 32 == 0) {
-    atomicAdd(&sums[0], s2);
-    atomicAdd(&sums[1], s1);
-    atomicAdd(&sums[2], sv);
+    atomicAdd(&sums[0], a);
+    atomicAdd(&sums[1], b);
+    atomicAdd(&sums[2], c);
   }
 }
 
-// Thomas sweep on T2 (q, p, k), rows of ldy: one thread per (q, p) line with
-// q fastest.  float32 recurrence with c' in `scratch`; the singular null line
-// (q, p) = (0, 0) is solved in float64 with the compatibility projection and
-// the zero-mean gauge of the float64 path.
-template <int FMT>
-__global__ void __launch_bounds__(128)
-thomas_mixed_kernel(int nx, int ny, int nz, int ldy, void* t0, void* t1, float* __restrict__ scratch,
-                    double* __restrict__ nl_c, double* __restrict__ nl_d,
-                    const float* __restrict__ lamx, const float* __restrict__ lamy,
-                    const float* __restrict__ az, const float* __restrict__ bz,
-                    const float* __restrict__ cz, const double* __restrict__ az64,
-                    const double* __restrict__ bz64, const double* __restrict__ cz64,
-                    const double* __restrict__ dz64, double alpha, double beta, int singular) {
+// ---------------------------------------------------------------- Thomas
+// Tridiagonal solves along z on T2 (q, p, k), rows of ldy, by the partition
+// method with every value in registers.  A block holds TL consecutive lines
+// (consecutive q: coalesced loads) times nseg segments of M rows; thread
+// (l, s) owns rows [sM, min(Nz, (s+1)M)) of line l.  The segment's last row is
+// its interface unknown y_s; its interior rows are solved by one Thomas
+// factorisation for three right-hand sides, giving
+//     x_t = g_t + u_t y_{s-1} + v_t y_s ,
+// the interface rows then form a tridiagonal system in (y_0 .. y_{S-1}) per
+// line, solved in shared memory by one thread, and each thread finishes its
+// rows.  float32 throughout; the singular null line (q, p) = (0, 0) is taken
+// from the float64 result of null_line_kernel.  A block is TL x NSEG = 512
+// threads (TL warps solve the TL reduced systems, one warp per line) and M is
+// the smallest segment length with NSEG * M >= Nz.
+constexpr int TL = 16;     // lines per block
+constexpr int NSEG = 32;   // segments per line (rows past Nz are identity rows)
+
+template <int FMT, int M>
+__global__ void __launch_bounds__(512)
+thomas_part_kernel(int nx, int ny, int nz, int ldy, void* t0, void* t1,
+                   const float* __restrict__ lamx, const float* __restrict__ lamy,
+                   const float* __restrict__ az, const float* __restrict__ bz,
+                   const float* __restrict__ cz, float alpha, float beta, int singular,
+                   const double* __restrict__ nl_x) {
+  // Rows past Nz are identity rows (a = c = 0, diagonal 1, right side 0): they
+  // decouple because c_{Nz-1} = 0, and make every segment exactly M rows long,
+  // so all per-row arrays stay in registers with compile-time indices.
+  constexpr int nseg = NSEG;
+  __shared__ float shm[7 * NSEG * TL];
+  float* G0 = shm;                       // [nseg][TL] first-interior g, u, v of each segment
+  float* U0 = G0 + nseg * TL;
+  float* V0 = U0 + nseg * TL;
+  float* RA = V0 + nseg * TL;            // reduced rows
+  float* RB = RA + nseg * TL;
+  float* RC = RB + nseg * TL;
+  float* RD = RC + nseg * TL;            // right-hand side, then y
+  const int l = threadIdx.x % TL, s = threadIdx.x / TL;
   const long long lines = static_cast<long long>(nx) * ny;
-  const long long line = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
-  if (line >= lines) return;
-  const int q = static_cast<int>(line % ny), p = static_cast<int>(line / ny);
+  const long long L = static_cast<long long>(blockIdx.x) * TL + l;
+  const bool valid = L < lines;
+  const int q = valid ? static_cast<int>(L % ny) : 0, p = valid ? static_cast<int>(L / ny) : 0;
   const long long base = q + static_cast<long long>(ldy) * p;
   const long long stride = static_cast<long long>(ldy) * nx;
-  if (singular && q == 0 && p == 0) {
-    // float64 null line: project to compatible form, zero the last modal
-    // unknown, shift to zero dz-weighted mean (c', d' kept in nl_c, nl_d)
-    double s = 0.0, w = 0.0;
-    for (int k = 0; k < nz; ++k) {
-      s = fma(dz64[k], static_cast<double>(Elem<FMT>::load(t0, t1, base + k * stride)), s);
-      w += dz64[k];
+  const int s0 = s * M;
+  const float shift = alpha + beta * (lamx[p] + lamy[q]);
+
+  float d[M];
+#pragma unroll
+  for (int t = 0; t < M; ++t) {
+    const int k = s0 + t;
+    d[t] = (valid && k < nz) ? Elem<FMT>::load(t0, t1, base + k * stride) : 0.0f;
+  }
+  // interior rows t = 0 .. M-2: one factorisation, three right-hand sides
+  float cp[M - 1], g[M - 1], u[M - 1];
+  float cprev = 0.0f, gprev = 0.0f, uprev = 0.0f;
+#pragma unroll
+  for (int t = 0; t < M - 1; ++t) {
+    const int k = s0 + t;
+    const bool real = k < nz;
+    const float a = (real && k > 0) ? beta * az[k] : 0.0f;
+    const float m = real ? fmaf(-a, cprev, fmaf(beta, bz[k], shift)) : 1.0f;
+    const float inv = __fdividef(1.0f, m);
+    cp[t] = real ? beta * cz[k] * inv : 0.0f;
+    g[t] = fmaf(-a, gprev, d[t]) * inv;
+    u[t] = (t == 0 ? -a : -a * uprev) * inv;
+    cprev = cp[t];
+    gprev = g[t];
+    uprev = u[t];
+  }
+#pragma unroll
+  for (int t = M - 3; t >= 0; --t) {
+    g[t] = fmaf(-cp[t], g[t + 1], g[t]);
+    u[t] = fmaf(-cp[t], u[t + 1], u[t]);
+  }
+  // v_t: interior response to a unit interface y_s; v_{M-2} = -cp[M-2]
+  float v0 = -cp[M - 2];
+#pragma unroll
+  for (int t = M - 3; t >= 0; --t) v0 = -cp[t] * v0;
+  const int o = s * TL + l;
+  G0[o] = g[0];
+  U0[o] = u[0];
+  V0[o] = v0;
+  __syncthreads();
+  {
+    const int k = s0 + M - 1;            // interface row of this segment
+    const bool real = k < nz;
+    const float a1 = (real && k > 0) ? beta * az[k] : 0.0f;
+    const float b1 = real ? fmaf(beta, bz[k], shift) : 1.0f;
+    const float c1 = real ? beta * cz[k] : 0.0f;
+    const float A = a1 * u[M - 2];
+    float B = fmaf(-a1, cp[M - 2], b1);
+    float D = fmaf(-a1, g[M - 2], d[M - 1]);
+    float Cc = 0.0f;
+    if (s + 1 < nseg) {
+      const int on = o + TL;
+      B = fmaf(c1, U0[on], B);
+      Cc = c1 * V0[on];
+      D = fmaf(-c1, G0[on], D);
     }
-    const double fshift = s / w;
-    double cp = 0.0, dp = 0.0;
-    for (int k = 0; k < nz; ++k) {
-      const double sub = (k > 0) ? beta * az64[k] : 0.0;
-      const double m = beta * bz64[k] - sub * cp;   // alpha = 0 and lambda = 0 on this line
-      const double rhs = (static_cast<double>(Elem<FMT>::load(t0, t1, base + k * stride)) - fshift) - sub * dp;
-      if (k == nz - 1) {
-        dp = 0.0;
-      } else {
-        const double inv = 1.0 / m;
-        cp = beta * cz64[k] * inv;
-        dp = rhs * inv;
+    RA[o] = A;
+    RB[o] = B;
+    RC[o] = Cc;
+    RD[o] = D;
+  }
+  __syncthreads();
+  // Reduced system of every line by parallel cyclic reduction: warp w solves
+  // line w (w < TL) with lane r holding interface row r; rows past nseg are
+  // identity rows.  log2(32) = 5 shuffle steps leave decoupled rows.
+  {
+    const int w = threadIdx.x / 32, r = threadIdx.x % 32;
+    if (w < TL) {
+      const int i = r * TL + w;
+      const bool in = r < nseg;
+      float A = in ? RA[i] : 0.0f, B = in ? RB[i] : 1.0f, Cc = in ? RC[i] : 0.0f, D = in ? RD[i] : 0.0f;
+#pragma unroll
+      for (int dlt = 1; dlt < 32; dlt <<= 1) {
+        const float Am = __shfl_up_sync(0xffffffffu, A, dlt), Bm = __shfl_up_sync(0xffffffffu, B, dlt);
+        const float Cm = __shfl_up_sync(0xffffffffu, Cc, dlt), Dm = __shfl_up_sync(0xffffffffu, D, dlt);
+        const float Ap = __shfl_down_sync(0xffffffffu, A, dlt), Bp = __shfl_down_sync(0xffffffffu, B, dlt);
+        const float Cp = __shfl_down_sync(0xffffffffu, Cc, dlt), Dp = __shfl_down_sync(0xffffffffu, D, dlt);
+        const bool hasm = r >= dlt, hasp = r + dlt < 32;
+        const float k1 = hasm ? __fdividef(A, Bm) : 0.0f;
+        const float k2 = hasp ? __fdividef(Cc, Bp) : 0.0f;
+        const float nA = hasm ? -Am * k1 : 0.0f;
+        const float nC = hasp ? -Cp * k2 : 0.0f;
+        B = B - (hasm ? Cm * k1 : 0.0f) - (hasp ? Ap * k2 : 0.0f);
+        D = D - (hasm ? Dm * k1 : 0.0f) - (hasp ? Dp * k2 : 0.0f);
+        A = nA;
+        Cc = nC;
       }
-      nl_c[k] = cp;
-      nl_d[k] = dp;
+      if (in) RD[i] = __fdividef(D, B);
     }
-    double x = dp, xs = dz64[nz - 1] * dp;
-    for (int k = nz - 2; k >= 0; --k) {
-      x = nl_d[k] - nl_c[k] * x;
-      nl_d[k] = x;
-      xs = fma(dz64[k], x, xs);
-    }
-    const double mean = xs / w;
-    for (int k = 0; k < nz; ++k)
-      Elem<FMT>::store(t0, t1, base + k * stride, static_cast<float>(nl_d[k] - mean));
+  }
+  __syncthreads();
+  if (!valid) return;
+  if (singular && L == 0) {   // float64 null line
+#pragma unroll
+    for (int t = 0; t < M; ++t)
+      if (s0 + t < nz) Elem<FMT>::store(t0, t1, base + (s0 + t) * stride, static_cast<float>(nl_x[s0 + t]));
     return;
   }
-  const float fb = static_cast<float>(beta);
-  const float shift = static_cast<float>(alpha) + fb * (lamx[p] + lamy[q]);
-  float cp = 0.0f, dp = 0.0f;
-  for (int k = 0; k < nz; ++k) {
-    const long long o = base + k * stride;
-    const float sub = (k > 0) ? fb * az[k] : 0.0f;
-    const float m = fmaf(-sub, cp, fmaf(fb, bz[k], shift));
-    const float inv = 1.0f / m;
-    cp = (k < nz - 1) ? fb * cz[k] * inv : 0.0f;
-    dp = fmaf(-sub, dp, Elem<FMT>::load(t0, t1, o)) * inv;
-    scratch[o] = cp;
-    Elem<FMT>::store(t0, t1, o, dp);
-  }
-  float x = dp;
-  for (int k = nz - 2; k >= 0; --k) {
-    const long long o = base + k * stride;
-    x = fmaf(-scratch[o], x, Elem<FMT>::load(t0, t1, o));
-    Elem<FMT>::store(t0, t1, o, x);
+  const float ys = RD[o];
+  const float ym = (s > 0) ? RD[o - TL] : 0.0f;
+  if (s0 + M - 1 < nz) Elem<FMT>::store(t0, t1, base + (s0 + M - 1) * stride, ys);
+  float v = 1.0f;
+#pragma unroll
+  for (int t = M - 2; t >= 0; --t) {
+    v = -cp[t] * v;
+    if (s0 + t < nz) Elem<FMT>::store(t0, t1, base + (s0 + t) * stride, fmaf(u[t], ym, fmaf(v, ys, g[t])));
   }
 }
 
-// Float-pair coefficient tables of one direction: a, c and the diagonal
-// remainder w = -(a + b + c) of the float64 rows, so that
-//   a phi_{i-1} + b phi_i + c phi_{i+1} = a (phi_{i-1} - phi_i) + c (phi_{i+1} - phi_i) - w phi_i.
-struct DFRows {
+// Singular null line (q, p) = (0, 0) in float64: the line is staged in shared
+// memory, projected to compatible form (dz-weighted mean removed), solved with
+// the plan's precomputed factorisation of T_z (last modal unknown set to zero)
+// and shifted to zero dz-weighted mean; result in nl_x.  One warp.
+template <int FMT>
+__global__ void __launch_bounds__(32)
+null_line_kernel(int nz, long long stride, const void* t0, const void* t1,
+                 const double* __restrict__ az, const double* __restrict__ ncp,
+                 const double* __restrict__ ninvm, const double* __restrict__ dz, double beta,
+                 double* __restrict__ nl_x) {
+  extern __shared__ double line[];
+  const int lane = threadIdx.x;
+  double s = 0.0, w = 0.0;
+  for (int k = lane; k < nz; k += 32) {
+    const double f = static_cast<double>(Elem<FMT>::load(t0, t1, static_cast<long long>(k) * stride));
+    line[k] = f;
+    s = fma(dz[k], f, s);
+    w += dz[k];
+  }
+  s = warp_sum_d(s);
+  w = warp_sum_d(w);
+  __syncwarp();
+  if (lane == 0) {
+    const double fshift = s / w;
+    double dp = 0.0;
+    for (int k = 0; k < nz - 1; ++k) {
+      dp = fma(-az[k], dp, line[k] - fshift) * ninvm[k];
+      line[k] = dp;
+    }
+    double x = 0.0;
+    line[nz - 1] = 0.0;
+    for (int k = nz - 2; k >= 0; --k) {
+      x = fma(-ncp[k], x, line[k]);
+      line[k] = x;
+    }
+  }
+  __syncwarp();
+  double xs = 0.0;
+  for (int k = lane; k < nz; k += 32) xs = fma(dz[k], line[k], xs);
+  xs = warp_sum_d(xs);
+  const double mean = xs / w;
+  for (int k = lane; k < nz; k += 32) nl_x[k] = (line[k] - mean) / beta;
+}
+
+// ------------------------------------------------------------- residual
+// beta-scaled float-pair rows of one direction: beta*a, beta*c and beta*w with
+// w = -(a + b + c) the diagonal remainder of the float64 rows (zero except at
+// Dirichlet walls), so that beta (a phi_- + b phi + c phi_+) =
+// beta a (phi_- - phi) + beta c (phi_+ - phi) - beta w phi.
+struct BRows {
   const float *ah, *al, *ch, *cl, *wh, *wl;
 };
 
-__device__ __forceinline__ df ld_df(const float* h, const float* l, long long i) { return {h[i], l[i]}; }
-
-__device__ __forceinline__ df flux3(const DFRows& R, int i, df pm, df p0, df pp) {
-  const df t1 = df_mul({R.ah[i], R.al[i]}, df_sub(pm, p0));
-  const df t2 = df_mul({R.ch[i], R.cl[i]}, df_sub(pp, p0));
-  const df t3 = df_mul({R.wh[i], R.wl[i]}, p0);
-  return df_sub(df_add(t1, t2), t3);
+// acc += coef * (x - y) with float pairs; acc stays unnormalised (hi, lo)
+__device__ __forceinline__ void acc_flux(df& acc, float ch, float cl, df x, df y) {
+  df d = two_sum(x.hi, -y.hi);
+  d.lo += x.lo - y.lo;
+  const float pr = ch * d.hi;
+  float pe = fmaf(ch, d.hi, -pr);
+  pe = fmaf(ch, d.lo, pe);
+  pe = fmaf(cl, d.hi, pe);
+  const df t = two_sum(acc.hi, pr);
+  acc.hi = t.hi;
+  acc.lo += t.lo + pe;
+}
+// acc += coef * x
+__device__ __forceinline__ void acc_mul(df& acc, float ch, float cl, df x) {
+  const float pr = ch * x.hi;
+  float pe = fmaf(ch, x.hi, -pr);
+  pe = fmaf(ch, x.lo, pe);
+  pe = fmaf(cl, x.hi, pe);
+  const df t = two_sum(acc.hi, pr);
+  acc.hi = t.hi;
+  acc.lo += t.lo + pe;
 }
 
-// r = (f - fshift) - alpha phi - beta L phi in float-pair arithmetic; r goes to
-// R (operand format, rows of ldx) and sum r^2 to sums[0].  One thread per
-// (i, j), marching along k.
-template <int FMT>
+__device__ __forceinline__ df ld_df(const float* __restrict__ h, const float* __restrict__ l, long long i) {
+  return {h[i], l[i]};
+}
+
+// r = (f - fshift) - alpha phi - beta L phi in float-pair arithmetic, written
+// to R (operand format, rows of ldx); sum r^2 -> sums[0] and, for a singular
+// problem, sum vol*phi -> sums[1].  Block (32, 4) over (i, j); blockIdx.z picks
+// a segment of kseg planes that the thread marches through.
+template <int FMT, int HAS_ALPHA, int WX, int WY, int WZ>
 __global__ void __launch_bounds__(128)
-residual_df_kernel(int nx, int ny, int nz, int ldx, const float* __restrict__ fh,
+residual_df_kernel(int nx, int ny, int nz, int ldx, int kseg, const float* __restrict__ fh,
                    const float* __restrict__ fl, const float* __restrict__ ph,
-                   const float* __restrict__ pl, void* r0, void* r1, DFRows RX, DFRows RY, DFRows RZ,
-                   double alpha, double beta, const double* __restrict__ fsums, double inv_vol,
-                   int singular, double* sums) {
+                   const float* __restrict__ pl, void* r0, void* r1, BRows RX, BRows RY, BRows RZ,
+                   const float* __restrict__ gx, const float* __restrict__ gy,
+                   const float* __restrict__ gz, float alpha_h, float alpha_l,
+                   const double* __restrict__ fsums, double inv_vol, int singular, double* sums) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  double s2 = 0.0;
-  if (i < nx && j < ny) {
+  const int k0 = blockIdx.z * kseg;
+  const int k1 = min(nz, k0 + kseg);
+  double s2 = 0.0, swp = 0.0;
+  if (i < nx && j < ny && k0 < nz) {
     const long long sy = nx, sz = static_cast<long long>(nx) * ny;
     const long long base = i + sy * j;
     const int im = (i == 0) ? nx - 1 : i - 1, ip = (i == nx - 1) ? 0 : i + 1;
     const int jm = (j == 0) ? ny - 1 : j - 1, jp = (j == ny - 1) ? 0 : j + 1;
-    const df dalpha = df_from_double(alpha), dbeta = df_from_double(beta);
-    const df fshift = df_from_double(singular ? fsums[2] * inv_vol : 0.0);
-    df pm = ld_df(ph, pl, base + sz * (nz - 1));
-    df p0 = ld_df(ph, pl, base);
-    float acc = 0.0f;
-    for (int k = 0; k < nz; ++k) {
+    const float axh = RX.ah[i], axl = RX.al[i], cxh = RX.ch[i], cxl = RX.cl[i];
+    const float ayh = RY.ah[j], ayl = RY.al[j], cyh = RY.ch[j], cyl = RY.cl[j];
+    df fshift = {0.0f, 0.0f};
+    if (singular) {
+      const double c = fsums[2] * inv_vol;
+      const float chi = static_cast<float>(c);
+      fshift = {chi, static_cast<float>(c - static_cast<double>(chi))};
+    }
+    const df vxy = df_mul({gx[i], gx[nx + i]}, {gy[j], gy[ny + j]});
+    df pm = ld_df(ph, pl, base + sz * (k0 == 0 ? nz - 1 : k0 - 1));
+    df p0 = ld_df(ph, pl, base + sz * k0);
+    float acc2 = 0.0f;
+    df wp = {0.0f, 0.0f};
+    for (int k = k0; k < k1; ++k) {
       const long long o = base + sz * k;
       const df pp = ld_df(ph, pl, base + sz * ((k == nz - 1) ? 0 : k + 1));
-      const df lx = flux3(RX, i, ld_df(ph, pl, im + sy * j + sz * k), p0, ld_df(ph, pl, ip + sy * j + sz * k));
-      const df ly = flux3(RY, j, ld_df(ph, pl, i + sy * jm + sz * k), p0, ld_df(ph, pl, i + sy * jp + sz * k));
-      const df lz = flux3(RZ, k, pm, p0, pp);
-      const df lap = df_add(df_add(lx, ly), lz);
-      const df ap = df_add(df_mul(dalpha, p0), df_mul(dbeta, lap));
-      const df r = df_sub(df_sub(ld_df(fh, fl, o), fshift), ap);
-      const float rv = r.hi + r.lo;
+      const df xm = ld_df(ph, pl, im + sy * j + sz * k), xp = ld_df(ph, pl, ip + sy * j + sz * k);
+      const df ym = ld_df(ph, pl, i + sy * jm + sz * k), yp = ld_df(ph, pl, i + sy * jp + sz * k);
+      const df fv = ld_df(fh, fl, o);
+      df acc = {0.0f, 0.0f};
+      acc_flux(acc, axh, axl, xm, p0);
+      acc_flux(acc, cxh, cxl, xp, p0);
+      acc_flux(acc, ayh, ayl, ym, p0);
+      acc_flux(acc, cyh, cyl, yp, p0);
+      acc_flux(acc, RZ.ah[k], RZ.al[k], pm, p0);
+      acc_flux(acc, RZ.ch[k], RZ.cl[k], pp, p0);
+      if (WX) acc_mul(acc, -RX.wh[i], -RX.wl[i], p0);
+      if (WY) acc_mul(acc, -RY.wh[j], -RY.wl[j], p0);
+      if (WZ) acc_mul(acc, -RZ.wh[k], -RZ.wl[k], p0);
+      if (HAS_ALPHA) acc_mul(acc, alpha_h, alpha_l, p0);
+      // r = (f - fshift) - acc
+      df r = two_sum(fv.hi, -fshift.hi);
+      r.lo += fv.lo - fshift.lo;
+      const df t = two_sum(r.hi, -acc.hi);
+      const float rv = t.hi + (t.lo + (r.lo - acc.lo));
       Elem<FMT>::store(r0, r1, i + static_cast<long long>(ldx) * (j + static_cast<long long>(ny) * k), rv);
-      acc = fmaf(rv, rv, acc);
+      acc2 = fmaf(rv, rv, acc2);
+      if (singular) {
+        const df vp = df_mul(df_mul(vxy, {gz[k], gz[nz + k]}), p0);
+        const df t2 = two_sum(wp.hi, vp.hi);
+        wp.hi = t2.hi;
+        wp.lo += t2.lo + vp.lo;
+      }
       pm = p0;
       p0 = pp;
     }
-    s2 = acc;
+    s2 = acc2;
+    swp = static_cast<double>(wp.hi) + wp.lo;
   }
   s2 = warp_sum_d(s2);
-  if ((threadIdx.x + blockDim.x * threadIdx.y) % 32 == 0) atomicAdd(&sums[0], s2);
+  swp = warp_sum_d(swp);
+  if ((threadIdx.x + blockDim.x * threadIdx.y) % 32 == 0) {
+    atomicAdd(&sums[0], s2);
+    if (singular) atomicAdd(&sums[1], swp);
+  }
 }
 
 // sum of cell volume times phi (float pair) into *out, for the exact gauge
 __global__ void __launch_bounds__(256)
 wsum_df_kernel(int nx, int ny, int nz, const float* __restrict__ h, const float* __restrict__ l,
-               const double* __restrict__ dxf, const double* __restrict__ dyf,
-               const double* __restrict__ dzf, double* out) {
+               const float* __restrict__ gx, const float* __restrict__ gy,
+               const float* __restrict__ gz, double* out) {
   const long long n = static_cast<long long>(nx) * ny * nz;
-  double s = 0.0;
+  df s = {0.0f, 0.0f};
   for (long long o = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; o < n;
        o += static_cast<long long>(gridDim.x) * blockDim.x) {
     const int i = static_cast<int>(o % nx);
     const long long line = o / nx;
     const int j = static_cast<int>(line % ny), k = static_cast<int>(line / ny);
-    s = fma(dxf[i] * dyf[j] * dzf[k], static_cast<double>(h[o]) + static_cast<double>(l[o]), s);
+    const df vol = df_mul(df_mul({gx[i], gx[nx + i]}, {gy[j], gy[ny + j]}), {gz[k], gz[nz + k]});
+    s = df_add(s, df_mul(vol, {h[o], l[o]}));
   }
-  s = warp_sum_d(s);
-  if (threadIdx.x % 32 == 0) atomicAdd(out, s);
+  double v = static_cast<double>(s.hi) + s.lo;
+  v = warp_sum_d(v);
+  if (threadIdx.x % 32 == 0) atomicAdd(out, v);
 }
 
-// phi = hi + lo - shift, shift = (*wsum) * inv_vol when wsum is given (the
-// singular problem's zero volume-weighted-mean gauge, applied exactly)
+// phi = (hi + lo) - shift, shift = (*wsum) * inv_vol when wsum is given (the
+// singular problem's zero volume-weighted-mean gauge, applied exactly); the
+// pair is converted with integer operations and one float64 add.
 __global__ void __launch_bounds__(256)
 df_to_f64_kernel(long long n, const float* __restrict__ h, const float* __restrict__ l,
                  const double* __restrict__ wsum, double inv_vol, double* out) {
-  const double shift = wsum ? *wsum * inv_vol : 0.0;
+  const df shift = df_from_double(wsum ? *wsum * inv_vol : 0.0);
   for (long long o = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; o < n;
-       o += static_cast<long long>(gridDim.x) * blockDim.x)
-    out[o] = (static_cast<double>(h[o]) + static_cast<double>(l[o])) - shift;
+       o += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const df x = df_sub({h[o], l[o]}, shift);
+    out[o] = f2d_int(x.hi) + f2d_int(x.lo);
+  }
 }
 
 // rows x K float64 (row-major, stride K) -> operand planes with row stride ld
@@ -496,8 +715,21 @@ cudaError_t launch_prepare(const tpt_plan_s* p, const double* f, const MixedWork
   const long long n = static_cast<long long>(p->n[0]) * p->n[1] * p->n[2];
   note_launch(1);
   prepare_kernel<FMT><<<grid_for(n, 256, p->dev), 256, 0, s>>>(
-      p->n[0], p->n[1], p->n[2], p->mixed.ldx, f, w.fh, w.fl, w.R[0], w.R[1], p->d_dxf[0], p->d_dxf[1],
-      p->d_dxf[2], w.scal + 5);
+      p->n[0], p->n[1], p->n[2], p->mixed.ldx, f, w.fh, w.fl, w.R[0], w.R[1], p->mixed.dfgeom[0],
+      p->mixed.dfgeom[1], p->mixed.dfgeom[2], w.scal + 5);
+  return cudaGetLastError();
+}
+
+template <int FMT, int M>
+cudaError_t launch_part(const tpt_plan_s* p, const MixedWork& w, cudaStream_t s) {
+  const MixedTables& m = p->mixed;
+  const long long lines = static_cast<long long>(p->n[0]) * p->n[1];
+  const int nz = p->n[2];
+  note_launch(1);
+  thomas_part_kernel<FMT, M><<<static_cast<unsigned>((lines + TL - 1) / TL), TL * NSEG, 0, s>>>(
+      p->n[0], p->n[1], nz, m.ldy, w.B[0], w.B[1], m.lam_f[0], m.lam_f[1], m.zrows_f,
+      m.zrows_f + nz, m.zrows_f + 2 * nz, static_cast<float>(p->alpha), static_cast<float>(p->beta),
+      p->singular ? 1 : 0, w.nl);
   return cudaGetLastError();
 }
 
@@ -505,34 +737,62 @@ template <int FMT>
 cudaError_t launch_thomas(const tpt_plan_s* p, const MixedWork& w, cudaStream_t s) {
   const MixedTables& m = p->mixed;
   const int nz = p->n[2];
-  const long long lines = static_cast<long long>(p->n[0]) * p->n[1];
-  const double* rz = p->d_rows[2];
-  note_launch(1);
-  thomas_mixed_kernel<FMT><<<static_cast<unsigned>((lines + 127) / 128), 128, 0, s>>>(
-      p->n[0], p->n[1], nz, m.ldy, w.B[0], w.B[1], w.scratch, w.nl, w.nl + nz, m.lam_f[0], m.lam_f[1],
-      m.zrows_f, m.zrows_f + nz, m.zrows_f + 2 * nz, rz, rz + nz, rz + 2 * nz, p->d_dxf[2], p->alpha,
-      p->beta, p->singular ? 1 : 0);
-  return cudaGetLastError();
+  if (p->singular) {
+    const double* rz = p->d_rows[2];
+    note_launch(1);
+    null_line_kernel<FMT><<<1, 32, static_cast<size_t>(nz) * sizeof(double), s>>>(
+        nz, static_cast<long long>(m.ldy) * p->n[0], w.B[0], w.B[1], rz, m.null_cp, m.null_invm,
+        p->d_dxf[2], p->beta, w.nl);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (nz <= NSEG * 4) return launch_part<FMT, 4>(p, w, s);
+  if (nz <= NSEG * 8) return launch_part<FMT, 8>(p, w, s);
+  if (nz <= NSEG * 16) return launch_part<FMT, 16>(p, w, s);
+  if (nz <= NSEG * 32) return launch_part<FMT, 32>(p, w, s);
+  return cudaErrorInvalidConfiguration;
 }
 
-DFRows rows_of(const float* t, int n) {
-  return DFRows{t, t + n, t + 2 * n, t + 3 * n, t + 4 * n, t + 5 * n};
+BRows rows_of(const float* t, int n) {
+  return BRows{t, t + n, t + 2 * n, t + 3 * n, t + 4 * n, t + 5 * n};
+}
+
+template <int FMT, int HA, int WX, int WY, int WZ>
+cudaError_t launch_res(const tpt_plan_s* p, const MixedWork& w, cudaStream_t s) {
+  const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
+  const int kseg = 32;
+  dim3 block(32, 4), grid((nx + 31) / 32, (ny + 3) / 4, (nz + kseg - 1) / kseg);
+  const float ah = static_cast<float>(p->alpha);
+  const float al = static_cast<float>(p->alpha - static_cast<double>(ah));
+  note_launch(1);
+  residual_df_kernel<FMT, HA, WX, WY, WZ><<<grid, block, 0, s>>>(
+      nx, ny, nz, p->mixed.ldx, kseg, w.fh, w.fl, w.ph, w.pl, w.R[0], w.R[1],
+      rows_of(p->mixed.dfrows[0], nx), rows_of(p->mixed.dfrows[1], ny), rows_of(p->mixed.dfrows[2], nz),
+      p->mixed.dfgeom[0], p->mixed.dfgeom[1], p->mixed.dfgeom[2], ah, al, w.scal + 5, 1.0 / p->vol,
+      p->singular ? 1 : 0, w.scal + 1);
+  return cudaGetLastError();
 }
 
 template <int FMT>
 cudaError_t launch_residual(const tpt_plan_s* p, const MixedWork& w, cudaStream_t s) {
-  const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
-  dim3 block(32, 4), grid((nx + 31) / 32, (ny + 3) / 4);
-  note_launch(1);
-  residual_df_kernel<FMT><<<grid, block, 0, s>>>(
-      nx, ny, nz, p->mixed.ldx, w.fh, w.fl, w.ph, w.pl, w.R[0], w.R[1], rows_of(p->mixed.dfrows[0], nx),
-      rows_of(p->mixed.dfrows[1], ny), rows_of(p->mixed.dfrows[2], nz), p->alpha, p->beta, w.scal + 5,
-      1.0 / p->vol, p->singular ? 1 : 0, w.scal + 1);
-  return cudaGetLastError();
+  const int* hw = p->mixed.has_w;
+  const int code = (p->alpha != 0.0 ? 8 : 0) | (hw[0] ? 4 : 0) | (hw[1] ? 2 : 0) | (hw[2] ? 1 : 0);
+  switch (code) {
+    case 0: return launch_res<FMT, 0, 0, 0, 0>(p, w, s);
+    case 8: return launch_res<FMT, 1, 0, 0, 0>(p, w, s);
+    default: break;
+  }
+  // walls with a diagonal remainder (Dirichlet): one general instantiation
+  if (p->alpha != 0.0) return launch_res<FMT, 1, 1, 1, 1>(p, w, s);
+  return launch_res<FMT, 0, 1, 1, 1>(p, w, s);
 }
 
 template <int FMT>
 int correction(tpt_plan_s* p, const MixedWork& w, bool accumulate, cudaStream_t s) {
+  auto mark = [&](int i) {
+    if (p->stage_timing) cudaEventRecord(p->ev[i], s);
+  };
+  mark(0);
   const MixedTables& m = p->mixed;
   const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
   const int kind = kind_of(FMT), npl = nplanes(FMT), om = out_mode(FMT);
@@ -542,20 +802,25 @@ int correction(tpt_plan_s* p, const MixedWork& w, bool accumulate, cudaStream_t 
                    gout(ny * nz, nx, nx, ny, static_cast<long long>(m.ldy) * nx, m.ldy, w.A[0], w.A[1], om,
                         0, 1, err),
                    s));
+  mark(1);
   // step 2.2: y forward.  A = Q_y^{-1} rows q, B = T1 rows (p,k) -> T2 (q, p, k)
   MX_CUDA(tc::gemm(kind, npl, operand(m.q[1][0], ny, ny, m.ldy), operand(w.A, nx * nz, ny, m.ldy),
                    gout(ny, nx * nz, ny, kBig, 0, m.ldy, w.B[0], w.B[1], om, 0, 0, err), s));
+  mark(2);
   // step 2.3: modal Thomas along z, in place on T2
   MX_CUDA(launch_thomas<FMT>(p, w, s));
+  mark(3);
   // step 2.4: y inverse.  A = T3 rows (p,k), B = Q_y rows j -> T4 (p, j, k)
   MX_CUDA(tc::gemm(kind, npl, operand(w.B, nx * nz, ny, m.ldy), operand(m.q[1][1], ny, ny, m.ldy),
                    gout(nx * nz, ny, ny, nx, static_cast<long long>(m.ldx) * ny, m.ldx, w.A[0], w.A[1], om,
                         0, 1, err),
                    s));
+  mark(4);
   // step 2.5: x inverse.  A = Q_x rows i, B = T4 rows (j,k) -> phi (float pair) (+)= result
   MX_CUDA(tc::gemm(kind, npl, operand(m.q[0][1], nx, nx, m.ldx), operand(w.A, ny * nz, nx, m.ldx),
                    gout(nx, ny * nz, nx, kBig, 0, nx, w.ph, w.pl, tc::kOutDF, accumulate ? 1 : 0, 0, err),
                    s));
+  mark(5);
   return TPT_OK;
 }
 
@@ -565,9 +830,26 @@ double proj_norm2(const double* h, double npts, double vol, bool singular) {
   return h[5] - 2.0 * c * h[6] + npts * c * c;
 }
 
+// Adds the elapsed times between the stage events of one correction (and its
+// residual, when recorded) to ms[1..6]; the stream must be synchronised.
+void add_stage_times(tpt_plan_s* p, float* ms, bool with_residual) {
+  for (int i = 0; i < (with_residual ? 6 : 5); ++i) {
+    float t = 0.0f;
+    if (cudaEventElapsedTime(&t, p->ev[i], p->ev[i + 1]) == cudaSuccess) ms[i + 1] += t;
+    else cudaGetLastError();
+  }
+}
+
 template <int FMT>
 int solve_fmt(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStream_t s, tpt_info* info) {
   const MixedWork w = carve(p, work);
+  float ms[8] = {0.0f};
+  const bool timing = p->stage_timing && info;
+  if (timing && !p->ev[0])
+    for (cudaEvent_t& e : p->ev)
+      if (cudaEventCreate(&e) != cudaSuccess) return TPT_ERR_CUDA;
+  const int saved_timing = p->stage_timing;
+  p->stage_timing = timing ? 1 : 0;
   MX_CUDA(cudaMemsetAsync(w.scal, 0, 16 * sizeof(double), s));
   MX_CUDA(launch_prepare<FMT>(p, f, w, s));
   const int corrections = 1 + p->max_refine;
@@ -576,14 +858,27 @@ int solve_fmt(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStrea
   double h[16] = {0.0};
   double rel = -1.0;
   int iters = 0, status = TPT_OK;
-  bool converged = false;
+  bool converged = false, residual_after_last = false;
   for (;;) {
     MX_TRY(correction<FMT>(p, w, iters > 0, s));
     ++iters;
+    residual_after_last = false;
     const bool need_residual = iters < corrections || adaptive || info;
-    if (!need_residual) break;
-    MX_CUDA(cudaMemsetAsync(w.scal + 1, 0, sizeof(double), s));
+    if (!need_residual) {
+      if (timing) {
+        MX_CUDA(cudaEventSynchronize(p->ev[5]));
+        add_stage_times(p, ms, false);
+      }
+      break;
+    }
+    MX_CUDA(cudaMemsetAsync(w.scal + 1, 0, 2 * sizeof(double), s));
     MX_CUDA(launch_residual<FMT>(p, w, s));
+    residual_after_last = true;
+    if (timing) {
+      cudaEventRecord(p->ev[6], s);
+      MX_CUDA(cudaEventSynchronize(p->ev[6]));
+      add_stage_times(p, ms, true);
+    }
     if (adaptive) {
       MX_CUDA(cudaMemcpyAsync(h, w.scal, 16 * sizeof(double), cudaMemcpyDeviceToHost, s));
       MX_CUDA(cudaStreamSynchronize(s));
@@ -601,11 +896,12 @@ int solve_fmt(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStrea
     if (iters >= corrections) break;
   }
   const long long n = static_cast<long long>(np);
-  if (p->singular) {
+  if (p->singular && !residual_after_last) {   // the residual pass already summed vol*phi
     MX_CUDA(cudaMemsetAsync(w.scal + 2, 0, sizeof(double), s));
     note_launch(1);
-    wsum_df_kernel<<<grid_for(n, 256, p->dev), 256, 0, s>>>(p->n[0], p->n[1], p->n[2], w.ph, w.pl, p->d_dxf[0],
-                                                            p->d_dxf[1], p->d_dxf[2], w.scal + 2);
+    wsum_df_kernel<<<grid_for(n, 256, p->dev), 256, 0, s>>>(p->n[0], p->n[1], p->n[2], w.ph, w.pl,
+                                                            p->mixed.dfgeom[0], p->mixed.dfgeom[1],
+                                                            p->mixed.dfgeom[2], w.scal + 2);
     MX_CUDA(cudaGetLastError());
   }
   note_launch(1);
@@ -623,8 +919,9 @@ int solve_fmt(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStrea
     info->iters = iters;
     info->rel_residual = rel;
     info->compat_defect = p->singular ? h[7] / p->vol : 0.0;
-    for (float& t : info->ms_stage) t = 0.0f;
+    for (int i = 0; i < 8; ++i) info->ms_stage[i] = ms[i];
   }
+  p->stage_timing = saved_timing;
   return status;
 }
 
@@ -672,18 +969,59 @@ int mixed_setup(tpt_plan_s* p) {
     MX_TRY(upload_vec(p, zr, &m.zrows_f));
   }
   for (int d = 0; d < 3; ++d) {
+    const int n = p->dir[d].n;
+    void* ptr = nullptr;
+    MX_TRY(dev_alloc(p, 6 * sizeof(float) * static_cast<size_t>(n), &ptr));
+    m.dfrows[d] = static_cast<float*>(ptr);
+  }
+  MX_TRY(mixed_set_beta(p));
+  {
+    // factorisation of T_z with the last (singular) row left out: c'_k, 1/m_k
+    const Dir1D& z = p->dir[2];
+    std::vector<double> ncp(z.n, 0.0), ninv(z.n, 0.0);
+    double cprev = 0.0;
+    for (int k = 0; k + 1 < z.n; ++k) {
+      const double mk = z.b[k] - z.a[k] * cprev;
+      ninv[k] = 1.0 / mk;
+      ncp[k] = z.c[k] * ninv[k];
+      cprev = ncp[k];
+    }
+    MX_TRY(upload_vec(p, ncp, &m.null_cp));
+    MX_TRY(upload_vec(p, ninv, &m.null_invm));
+  }
+  for (int d = 0; d < 3; ++d) {
+    const int n = p->dir[d].n;
+    std::vector<float> t(2 * static_cast<size_t>(n));
+    for (int i = 0; i < n; ++i) split_ld(p->dir[d].dxf[i], &t[i], &t[n + i]);
+    MX_TRY(upload_vec(p, t, &m.dfgeom[d]));
+  }
+  MX_CUDA(cudaDeviceSynchronize());
+  return TPT_OK;
+}
+
+int mixed_set_beta(tpt_plan_s* p) {
+  MixedTables& m = p->mixed;
+  const long double beta = p->beta;
+  for (int d = 0; d < 3; ++d) {
     const Dir1D& dd = p->dir[d];
     const int n = dd.n;
     std::vector<float> t(6 * static_cast<size_t>(n));
+    int hw = 0;
     for (int i = 0; i < n; ++i) {
       const long double a = dd.a[i], b = dd.b[i], c = dd.c[i];
-      split_ld(a, &t[i], &t[n + i]);
-      split_ld(c, &t[2 * n + i], &t[3 * n + i]);
-      split_ld(-(a + b + c), &t[4 * n + i], &t[5 * n + i]);
+      long double w = -(a + b + c);
+      // the remainder of b = -(a + c) rounded is ~1e-16 |b|: dropped; a
+      // Dirichlet wall term (2 / dx^2) is kept
+      if (std::fabs(static_cast<double>(w)) <= 1e-12 * (std::fabs(dd.a[i]) + std::fabs(dd.c[i]))) w = 0.0L;
+      if (w != 0.0L) hw = 1;
+      split_ld(beta * a, &t[i], &t[n + i]);
+      split_ld(beta * c, &t[2 * n + i], &t[3 * n + i]);
+      split_ld(beta * w, &t[4 * n + i], &t[5 * n + i]);
     }
-    MX_TRY(upload_vec(p, t, &m.dfrows[d]));
+    m.has_w[d] = hw;
+    MX_CUDA(cudaMemcpy(m.dfrows[d], t.data(), t.size() * sizeof(float), cudaMemcpyHostToDevice));
   }
-  MX_CUDA(cudaDeviceSynchronize());
+  m.rows_beta = p->beta;
   return TPT_OK;
 }
 

@@ -49,7 +49,12 @@ struct MixedTables {
   void* q[2][2][2] = {};           // [x|y][forward Q^{-1} | inverse Q][plane], row-major
   float* lam_f[2] = {nullptr, nullptr};
   float* zrows_f = nullptr;        // a|b|c of z in float32
-  float* dfrows[3] = {nullptr, nullptr, nullptr};   // ah|al|ch|cl|wh|wl per direction
+  float* dfrows[3] = {nullptr, nullptr, nullptr};   // beta*(a|c|w) as float pairs: ah|al|ch|cl|wh|wl
+  int has_w[3] = {0, 0, 0};        // direction has a nonzero diagonal remainder (Dirichlet wall)
+  double rows_beta = 0.0;          // beta the tables were scaled with
+  float* dfgeom[3] = {nullptr, nullptr, nullptr};   // cell widths as float pairs: h|l
+  double* null_cp = nullptr;       // factorisation of T_z (beta = 1) for the null line:
+  double* null_invm = nullptr;     //   c'_k and 1/m_k, k < Nz - 1
 };
 
 struct DevDir {       // device tables of a diagonalised direction (float64)
@@ -60,6 +65,7 @@ struct DevDir {       // device tables of a diagonalised direction (float64)
 
 // mixed-precision path (mixed.cu)
 int mixed_setup(tpt_plan_s* p);
+int mixed_set_beta(tpt_plan_s* p);   // rescale the residual tables after a coefficient change
 size_t mixed_workspace_bytes(const tpt_plan_s* p);
 int mixed_solve(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStream_t s,
                 tpt_info* info);
@@ -88,6 +94,8 @@ struct tpt_plan_s {
   int ring_next = 0;
   double vol = 1.0;               // domain volume Lx Ly Lz
   tpt::MixedTables mixed;
+  int stage_timing = 0;           // record per-stage CUDA events in tpt_solve
+  cudaEvent_t ev[8] = {};         // stage boundaries (created on first use)
   std::vector<void*> allocs;      // every device allocation owned by the plan
 };
 
@@ -119,6 +127,7 @@ cudaError_t residual_fp64(const tpt_plan_s* p, const double* f, const double* ph
 
 // mixed-precision path (mixed.cu)
 int mixed_setup(tpt_plan_s* p);
+int mixed_set_beta(tpt_plan_s* p);   // rescale the residual tables after a coefficient change
 size_t mixed_workspace_bytes(const tpt_plan_s* p);
 int mixed_solve(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStream_t s,
                 tpt_info* info);

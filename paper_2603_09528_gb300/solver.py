@@ -107,7 +107,11 @@ class Plan:
             return phi, None
         (torch.cuda.current_stream() if stream is None else stream).synchronize()
         return phi, dict(iters=info.iters, rel_residual=info.rel_residual,
-                         compat_defect=info.compat_defect, status=st)
+                         compat_defect=info.compat_defect, status=st,
+                         ms_stage=[float(x) for x in info.ms_stage])
+
+    def set_stage_timing(self, enable: bool):
+        check(lib.tpt_set_stage_timing(self._h, int(bool(enable))), "tpt_set_stage_timing")
 
     def solve_host(self, f_host: torch.Tensor, phi_host: torch.Tensor, f_dev: torch.Tensor,
                    phi_dev: torch.Tensor, work: torch.Tensor, stream=None):

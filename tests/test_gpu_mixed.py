@@ -89,3 +89,18 @@ def test_mixed_solve_reaches_rtol(prec, case):
     assert info["rel_residual"] <= 1e-10
     assert rel <= 2e-10
     assert err <= 1e-7, err
+
+
+@pytest.mark.parametrize("prec", list(PRECS))
+def test_mixed_identity_operator_returns_rhs(prec):
+    # alpha = 1, beta = 0: the refined solution is f itself; exercises the
+    # float64 <-> float-pair conversions end to end
+    n = (40, 24, 16)
+    dirs = _dirs(n, (1.0, 2.0, 3.0), [(1, 1)] * 3)
+    f = S.uniform_rhs(n, 5) * 1e3
+    plan = tpt.Plan(n, [d.dxf for d in dirs], [d.dxc for d in dirs], [(1, 1)] * 3,
+                    xform=(tpt.GEMM, tpt.GEMM), alpha=1.0, beta=0.0, precision=PRECS[prec],
+                    rtol=1e-13, max_refine=10)
+    phi, info = plan.solve(tpt.field_to_device(f))
+    got = tpt.field_to_host(phi, n)
+    assert np.abs(got - f).max() <= 1e-12 * np.abs(f).max(), np.abs(got - f).max()
