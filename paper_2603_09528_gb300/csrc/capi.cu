@@ -60,6 +60,9 @@ void free_plan(tpt_plan_s* p) {
     DeviceGuard g(p->dev);
     for (cudaEvent_t e : p->ev)
       if (e) cudaEventDestroy(e);
+    if (p->mixed.fork) cudaEventDestroy(p->mixed.fork);
+    if (p->mixed.join) cudaEventDestroy(p->mixed.join);
+    if (p->mixed.side) cudaStreamDestroy(p->mixed.side);
     for (void* a : p->allocs) cudaFree(a);
     if (p->h_ring) cudaFreeHost(p->h_ring);
   }

@@ -185,19 +185,18 @@ prepare_kernel(int nx, int ny, int nz, int ldx, const double* __restrict__ f, fl
 // the interface rows then form a tridiagonal system in (y_0 .. y_{S-1}) per
 // line, solved in shared memory by one thread, and each thread finishes its
 // rows.  float32 throughout; the singular null line (q, p) = (0, 0) is taken
-// from the float64 result of null_line_kernel.  A block is TL x NSEG = 512
+// by null_line_kernel (float64), which writes that line itself.  A block is TL x NSEG = 512
 // threads (TL warps solve the TL reduced systems, one warp per line) and M is
 // the smallest segment length with NSEG * M >= Nz.
 constexpr int TL = 16;     // lines per block
 constexpr int NSEG = 32;   // segments per line (rows past Nz are identity rows)
 
-template <int FMT, int M>
+template <int FMT, int M, bool FULL>
 __global__ void __launch_bounds__(512)
 thomas_part_kernel(int nx, int ny, int nz, int ldy, void* t0, void* t1,
                    const float* __restrict__ lamx, const float* __restrict__ lamy,
                    const float* __restrict__ az, const float* __restrict__ bz,
-                   const float* __restrict__ cz, float alpha, float beta, int singular,
-                   const double* __restrict__ nl_x) {
+                   const float* __restrict__ cz, float alpha, float beta, int singular) {
   // Rows past Nz are identity rows (a = c = 0, diagonal 1, right side 0): they
   // decouple because c_{Nz-1} = 0, and make every segment exactly M rows long,
   // so all per-row arrays stay in registers with compile-time indices.
@@ -224,7 +223,7 @@ thomas_part_kernel(int nx, int ny, int nz, int ldy, void* t0, void* t1,
 #pragma unroll
   for (int t = 0; t < M; ++t) {
     const int k = s0 + t;
-    d[t] = (valid && k < nz) ? Elem<FMT>::load(t0, t1, base + k * stride) : 0.0f;
+    d[t] = (valid && (FULL || k < nz)) ? Elem<FMT>::load(t0, t1, base + k * stride) : 0.0f;
   }
   // interior rows t = 0 .. M-2: one factorisation, three right-hand sides
   float cp[M - 1], g[M - 1], u[M - 1];
@@ -232,7 +231,7 @@ thomas_part_kernel(int nx, int ny, int nz, int ldy, void* t0, void* t1,
 #pragma unroll
   for (int t = 0; t < M - 1; ++t) {
     const int k = s0 + t;
-    const bool real = k < nz;
+    const bool real = FULL || k < nz;
     const float a = (real && k > 0) ? beta * az[k] : 0.0f;
     const float m = real ? fmaf(-a, cprev, fmaf(beta, bz[k], shift)) : 1.0f;
     const float inv = __fdividef(1.0f, m);
@@ -259,7 +258,7 @@ thomas_part_kernel(int nx, int ny, int nz, int ldy, void* t0, void* t1,
   __syncthreads();
   {
     const int k = s0 + M - 1;            // interface row of this segment
-    const bool real = k < nz;
+    const bool real = FULL || k < nz;
     const float a1 = (real && k > 0) ? beta * az[k] : 0.0f;
     const float b1 = real ? fmaf(beta, bz[k], shift) : 1.0f;
     const float c1 = real ? beta * cz[k] : 0.0f;
@@ -309,33 +308,29 @@ thomas_part_kernel(int nx, int ny, int nz, int ldy, void* t0, void* t1,
   }
   __syncthreads();
   if (!valid) return;
-  if (singular && L == 0) {   // float64 null line
-#pragma unroll
-    for (int t = 0; t < M; ++t)
-      if (s0 + t < nz) Elem<FMT>::store(t0, t1, base + (s0 + t) * stride, static_cast<float>(nl_x[s0 + t]));
-    return;
-  }
+  if (singular && L == 0) return;   // the null line is written by null_line_kernel
   const float ys = RD[o];
   const float ym = (s > 0) ? RD[o - TL] : 0.0f;
-  if (s0 + M - 1 < nz) Elem<FMT>::store(t0, t1, base + (s0 + M - 1) * stride, ys);
+  if (FULL || s0 + M - 1 < nz) Elem<FMT>::store(t0, t1, base + (s0 + M - 1) * stride, ys);
   float v = 1.0f;
 #pragma unroll
   for (int t = M - 2; t >= 0; --t) {
     v = -cp[t] * v;
-    if (s0 + t < nz) Elem<FMT>::store(t0, t1, base + (s0 + t) * stride, fmaf(u[t], ym, fmaf(v, ys, g[t])));
+    if (FULL || s0 + t < nz) Elem<FMT>::store(t0, t1, base + (s0 + t) * stride, fmaf(u[t], ym, fmaf(v, ys, g[t])));
   }
 }
 
 // Singular null line (q, p) = (0, 0) in float64: the line is staged in shared
 // memory, projected to compatible form (dz-weighted mean removed), solved with
 // the plan's precomputed factorisation of T_z (last modal unknown set to zero)
-// and shifted to zero dz-weighted mean; result in nl_x.  One warp.
+// and shifted to zero dz-weighted mean; the result overwrites the line in
+// place.  One warp; it touches no other line, so it runs beside
+// thomas_part_kernel on a second stream.
 template <int FMT>
 __global__ void __launch_bounds__(32)
-null_line_kernel(int nz, long long stride, const void* t0, const void* t1,
+null_line_kernel(int nz, long long stride, void* t0, void* t1,
                  const double* __restrict__ az, const double* __restrict__ ncp,
-                 const double* __restrict__ ninvm, const double* __restrict__ dz, double beta,
-                 double* __restrict__ nl_x) {
+                 const double* __restrict__ ninvm, const double* __restrict__ dz, double beta) {
   extern __shared__ double line[];
   const int lane = threadIdx.x;
   double s = 0.0, w = 0.0;
@@ -367,7 +362,8 @@ null_line_kernel(int nz, long long stride, const void* t0, const void* t1,
   for (int k = lane; k < nz; k += 32) xs = fma(dz[k], line[k], xs);
   xs = warp_sum_d(xs);
   const double mean = xs / w;
-  for (int k = lane; k < nz; k += 32) nl_x[k] = (line[k] - mean) / beta;
+  for (int k = lane; k < nz; k += 32)
+    Elem<FMT>::store(t0, t1, static_cast<long long>(k) * stride, static_cast<float>((line[k] - mean) / beta));
 }
 
 // ------------------------------------------------------------- residual
@@ -720,37 +716,51 @@ cudaError_t launch_prepare(const tpt_plan_s* p, const double* f, const MixedWork
   return cudaGetLastError();
 }
 
-template <int FMT, int M>
-cudaError_t launch_part(const tpt_plan_s* p, const MixedWork& w, cudaStream_t s) {
+template <int FMT, int M, bool FULL>
+cudaError_t launch_part_k(const tpt_plan_s* p, const MixedWork& w, cudaStream_t s) {
   const MixedTables& m = p->mixed;
   const long long lines = static_cast<long long>(p->n[0]) * p->n[1];
   const int nz = p->n[2];
   note_launch(1);
-  thomas_part_kernel<FMT, M><<<static_cast<unsigned>((lines + TL - 1) / TL), TL * NSEG, 0, s>>>(
+  thomas_part_kernel<FMT, M, FULL><<<static_cast<unsigned>((lines + TL - 1) / TL), TL * NSEG, 0, s>>>(
       p->n[0], p->n[1], nz, m.ldy, w.B[0], w.B[1], m.lam_f[0], m.lam_f[1], m.zrows_f,
       m.zrows_f + nz, m.zrows_f + 2 * nz, static_cast<float>(p->alpha), static_cast<float>(p->beta),
-      p->singular ? 1 : 0, w.nl);
+      p->singular ? 1 : 0);
   return cudaGetLastError();
+}
+
+template <int FMT, int M>
+cudaError_t launch_part(const tpt_plan_s* p, const MixedWork& w, cudaStream_t s) {
+  // every segment full (Nz = NSEG * M): no padding predicates
+  if (p->n[2] == NSEG * M) return launch_part_k<FMT, M, true>(p, w, s);
+  return launch_part_k<FMT, M, false>(p, w, s);
 }
 
 template <int FMT>
 cudaError_t launch_thomas(const tpt_plan_s* p, const MixedWork& w, cudaStream_t s) {
   const MixedTables& m = p->mixed;
   const int nz = p->n[2];
-  if (p->singular) {
+  cudaStream_t side = m.side;
+  if (p->singular) {   // fork: the float64 null line runs beside the partition kernel
+    cudaError_t e = cudaEventRecord(m.fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(side, m.fork, 0);
+    if (e != cudaSuccess) return e;
     const double* rz = p->d_rows[2];
     note_launch(1);
-    null_line_kernel<FMT><<<1, 32, static_cast<size_t>(nz) * sizeof(double), s>>>(
+    null_line_kernel<FMT><<<1, 32, static_cast<size_t>(nz) * sizeof(double), side>>>(
         nz, static_cast<long long>(m.ldy) * p->n[0], w.B[0], w.B[1], rz, m.null_cp, m.null_invm,
-        p->d_dxf[2], p->beta, w.nl);
-    cudaError_t e = cudaGetLastError();
+        p->d_dxf[2], p->beta);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaEventRecord(m.join, side);
     if (e != cudaSuccess) return e;
   }
-  if (nz <= NSEG * 4) return launch_part<FMT, 4>(p, w, s);
-  if (nz <= NSEG * 8) return launch_part<FMT, 8>(p, w, s);
-  if (nz <= NSEG * 16) return launch_part<FMT, 16>(p, w, s);
-  if (nz <= NSEG * 32) return launch_part<FMT, 32>(p, w, s);
-  return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaErrorInvalidConfiguration;
+  if (nz <= NSEG * 4) e = launch_part<FMT, 4>(p, w, s);
+  else if (nz <= NSEG * 8) e = launch_part<FMT, 8>(p, w, s);
+  else if (nz <= NSEG * 16) e = launch_part<FMT, 16>(p, w, s);
+  else if (nz <= NSEG * 32) e = launch_part<FMT, 32>(p, w, s);
+  if (e == cudaSuccess && p->singular) e = cudaStreamWaitEvent(s, m.join, 0);   // join
+  return e;
 }
 
 BRows rows_of(const float* t, int n) {
@@ -995,6 +1005,9 @@ int mixed_setup(tpt_plan_s* p) {
     for (int i = 0; i < n; ++i) split_ld(p->dir[d].dxf[i], &t[i], &t[n + i]);
     MX_TRY(upload_vec(p, t, &m.dfgeom[d]));
   }
+  MX_CUDA(cudaStreamCreateWithFlags(&m.side, cudaStreamNonBlocking));
+  MX_CUDA(cudaEventCreateWithFlags(&m.fork, cudaEventDisableTiming));
+  MX_CUDA(cudaEventCreateWithFlags(&m.join, cudaEventDisableTiming));
   MX_CUDA(cudaDeviceSynchronize());
   return TPT_OK;
 }

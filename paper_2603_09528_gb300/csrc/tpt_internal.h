@@ -55,6 +55,8 @@ struct MixedTables {
   float* dfgeom[3] = {nullptr, nullptr, nullptr};   // cell widths as float pairs: h|l
   double* null_cp = nullptr;       // factorisation of T_z (beta = 1) for the null line:
   double* null_invm = nullptr;     //   c'_k and 1/m_k, k < Nz - 1
+  cudaStream_t side = nullptr;     // second stream for the null line, with fork/join events
+  cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 struct DevDir {       // device tables of a diagonalised direction (float64)
