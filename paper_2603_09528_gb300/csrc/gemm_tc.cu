@@ -6,7 +6,8 @@
 // Eq. forward-xy / inverse-xy; lines stacked as one GEMM).  Operands are bf16
 // (one plane, or a hi/lo pair whose three products hi*hi + hi*lo + lo*hi
 // approximate the float32 product) or tf32 (float32 planes), accumulated in
-// float32 in tensor memory.  One CTA computes one 128 x BN tile:
+// float32 in tensor memory.  The kernel is persistent (one CTA per SM walking
+// 128 x BN tiles) with a double-buffered tensor-memory accumulator:
 //   warp 0      TMA producer: A and B tiles of 128-byte rows, 128-byte swizzle,
 //               into a ring of shared-memory stages (mbarrier full/empty);
 //   warp 1      allocates BN tensor-memory columns and issues tcgen05.mma from
@@ -57,11 +58,83 @@ struct Cfg {
   static constexpr int B_BYTES = BN * 128;
   static constexpr int STAGE = NPL * (A_BYTES + B_BYTES);
   static constexpr int STAGES = (kSmemBudget / STAGE) > 4 ? 4 : (kSmemBudget / STAGE);
-  static constexpr int TMEM_COLS = BN < 32 ? 32 : BN;
+  static constexpr int TMEM_COLS = 2 * BN < 32 ? 32 : 2 * BN;   // two accumulator buffers
   static constexpr int SMEM = STAGES * STAGE + 1024 /* alignment */ + 256 /* barriers */;
   static constexpr int NPROD = (NPL == 2) ? 3 : 1;
 };
 
+// Store one 32-column chunk of the accumulator (registers r) for row m.
+template <int OUT>
+__device__ __forceinline__ void store_chunk(const GemmOut& g, long long mterm, int nb, const uint32_t (&r)[32]) {
+  if (OUT == kOutDF) {
+    // read-modify-write of the float pair: issue every load of the chunk
+    // before any dependent arithmetic so the 64 loads overlap
+    float* ph = static_cast<float*>(g.out0);
+    float* pl = static_cast<float*>(g.out1);
+    float oh[32], ol[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int n = nb + j;
+      const long long idx = mterm + static_cast<long long>(n < g.N ? n : 0) * g.sn;
+      oh[j] = (g.accumulate && n < g.N) ? ph[idx] : 0.0f;
+      ol[j] = (g.accumulate && n < g.N) ? pl[idx] : 0.0f;
+    }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int n = nb + j;
+      if (n >= g.N) break;
+      const long long idx = mterm + static_cast<long long>(n) * g.sn;
+      float sh, se;
+      two_sum(oh[j], __uint_as_float(r[j]), sh, se);
+      se += ol[j];
+      const float hi = sh + se;
+      ph[idx] = hi;
+      pl[idx] = se - (hi - sh);
+    }
+    return;
+  }
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    const int n = nb + j;
+    if (n >= g.N) break;
+    const long long idx = mterm + static_cast<long long>(n) * g.sn;
+    const float v = __uint_as_float(r[j]);
+    if (OUT == kOutSplitBF16) {
+      __nv_bfloat16 hi, lo;
+      split_bf16(v, hi, lo);
+      static_cast<__nv_bfloat16*>(g.out0)[idx] = hi;
+      static_cast<__nv_bfloat16*>(g.out1)[idx] = lo;
+    } else if (OUT == kOutBF16) {
+      static_cast<__nv_bfloat16*>(g.out0)[idx] = __float2bfloat16_rn(v);
+    } else if (OUT == kOutF32) {
+      static_cast<float*>(g.out0)[idx] = v;
+    } else if (OUT == kOutF64) {
+      static_cast<double*>(g.out0)[idx] = static_cast<double>(v);
+    }
+  }
+}
+
+template <int BN>
+__device__ __forceinline__ void tile_coords(const GemmOut& g, int num_m, int num_n, long long tile,
+                                            int& m0, int& n0) {
+  int mt, nt;
+  if (g.n_fastest) {
+    nt = static_cast<int>(tile % num_n);
+    mt = static_cast<int>(tile / num_n);
+  } else {
+    mt = static_cast<int>(tile % num_m);
+    nt = static_cast<int>(tile / num_m);
+  }
+  m0 = mt * BM;
+  n0 = nt * BN;
+}
+
+// Persistent kernel: each CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x,
+// ...  The tensor-memory accumulator is double-buffered (2 x BN columns): the
+// MMA warp fills buffer b for tile t while the epilogue drains buffer b^1 of
+// tile t-1.  Barriers: full/empty per smem stage (TMA <-> MMA), acc_full[b]
+// (MMA -> epilogue, one commit) and acc_empty[b] (epilogue -> MMA, one arrive
+// per epilogue warp).
 template <int KIND, int NPL, int BN, int OUT>
 __global__ void __launch_bounds__(kThreads, 1)
 gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
@@ -72,29 +145,26 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE);
-  // bars[0..S): full, bars[S..2S): empty, bars[2S]: accumulator ready
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * C::STAGES + 1);
+  // bars[0..S) full, [S..2S) empty, [2S, 2S+2) acc_full, [2S+2, 2S+4) acc_empty
+  uint64_t* accf = bars + 2 * C::STAGES;
+  uint64_t* acce = accf + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int num_m = (g.M + BM - 1) / BM, num_n = (g.N + BN - 1) / BN;
-  const long long tile = blockIdx.x;
-  int mt, nt;
-  if (g.n_fastest) {
-    nt = static_cast<int>(tile % num_n);
-    mt = static_cast<int>(tile / num_n);
-  } else {
-    mt = static_cast<int>(tile % num_m);
-    nt = static_cast<int>(tile / num_m);
-  }
-  const int m0 = mt * BM, n0 = nt * BN;
+  const long long num_tiles = static_cast<long long>(num_m) * num_n;
   const int nk = (g.K + C::BK - 1) / C::BK;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(g.err);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) {
       ptx::mbar_init(ptx::smem_u32(&bars[s]), 1);
       ptx::mbar_init(ptx::smem_u32(&bars[C::STAGES + s]), 1);
     }
-    ptx::mbar_init(ptx::smem_u32(&bars[2 * C::STAGES]), 1);
+    for (int b = 0; b < 2; ++b) {
+      ptx::mbar_init(ptx::smem_u32(&accf[b]), 1);
+      ptx::mbar_init(ptx::smem_u32(&acce[b]), 4);
+    }
     ptx::fence_mbar_init();
   }
   if (warp == 1) {
@@ -115,123 +185,107 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
       ptx::prefetch_tmap(&tB1);
     }
     bool ok = true;
-    int issued = 0;
-    for (int kc = 0; kc < nk && ok; ++kc) {
-      const int s = kc % C::STAGES;
-      const int round = kc / C::STAGES;
-      if (round > 0) ok = ptx::mbar_wait(ptx::smem_u32(&bars[C::STAGES + s]), (round - 1) & 1, g.err,
-                                         ptx::kErrWaitEmpty);
-      if (!ok) break;
-      uint8_t* st = smem + s * C::STAGE;
-      const uint32_t full = ptx::smem_u32(&bars[s]);
-      ptx::mbar_arrive_expect_tx(full, C::STAGE);
-      const int kx = kc * C::BK;
-      ptx::tma_load_2d(ptx::smem_u32(st), &tA0, full, kx, m0);
-      ptx::tma_load_2d(ptx::smem_u32(st + NPL * C::A_BYTES), &tB0, full, kx, n0);
-      if (NPL == 2) {
-        ptx::tma_load_2d(ptx::smem_u32(st + C::A_BYTES), &tA1, full, kx, m0);
-        ptx::tma_load_2d(ptx::smem_u32(st + NPL * C::A_BYTES + C::B_BYTES), &tB1, full, kx, n0);
+    long long it = 0;
+    for (long long tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
+      int m0, n0;
+      tile_coords<BN>(g, num_m, num_n, tile, m0, n0);
+      for (int kc = 0; kc < nk; ++kc, ++it) {
+        const int s = static_cast<int>(it % C::STAGES);
+        const long long round = it / C::STAGES;
+        if (round > 0)
+          ok = ptx::mbar_wait(ptx::smem_u32(&bars[C::STAGES + s]), static_cast<uint32_t>((round - 1) & 1), g.err,
+                              ptx::kErrWaitEmpty);
+        if (!ok || (abort_flag && *abort_flag)) {
+          ok = false;
+          break;
+        }
+        uint8_t* st = smem + s * C::STAGE;
+        const uint32_t full = ptx::smem_u32(&bars[s]);
+        ptx::mbar_arrive_expect_tx(full, C::STAGE);
+        const int kx = kc * C::BK;
+        ptx::tma_load_2d(ptx::smem_u32(st), &tA0, full, kx, m0);
+        ptx::tma_load_2d(ptx::smem_u32(st + NPL * C::A_BYTES), &tB0, full, kx, n0);
+        if (NPL == 2) {
+          ptx::tma_load_2d(ptx::smem_u32(st + C::A_BYTES), &tA1, full, kx, m0);
+          ptx::tma_load_2d(ptx::smem_u32(st + NPL * C::A_BYTES + C::B_BYTES), &tB1, full, kx, n0);
+        }
       }
-      ++issued;
     }
     // drain: every issued stage's copies have landed before the CTA may exit
-    const int first = issued > C::STAGES ? issued - C::STAGES : 0;
-    for (int kc = first; kc < issued; ++kc)
-      ptx::mbar_wait(ptx::smem_u32(&bars[kc % C::STAGES]), (kc / C::STAGES) & 1, g.err,
+    const long long first = it > C::STAGES ? it - C::STAGES : 0;
+    for (long long k = first; k < it; ++k)
+      ptx::mbar_wait(ptx::smem_u32(&bars[k % C::STAGES]), static_cast<uint32_t>((k / C::STAGES) & 1), g.err,
                      ptx::kErrWaitDrain, 1u << 20);
   } else if (warp == 1 && lane == 0) {
     // -------------------------------------------------------- MMA issuer
     constexpr uint32_t idesc = ptx::instr_desc(KIND == kKindBF16 ? 1u : 2u, BM, BN);
     bool ok = true;
-    for (int kc = 0; kc < nk && ok; ++kc) {
-      const int s = kc % C::STAGES;
-      ok = ptx::mbar_wait(ptx::smem_u32(&bars[s]), (kc / C::STAGES) & 1, g.err, ptx::kErrWaitFull);
-      if (!ok) break;
+    long long it = 0;
+    int tcount = 0;
+    for (long long tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x, ++tcount) {
+      const int b = tcount & 1, use = tcount >> 1;
+      if (use > 0)
+        ok = ptx::mbar_wait(ptx::smem_u32(&acce[b]), static_cast<uint32_t>((use - 1) & 1), g.err,
+                            ptx::kErrWaitAccum);
+      if (!ok || (abort_flag && *abort_flag)) break;
       ptx::tc_fence_after();
-      const uint32_t sa = ptx::smem_u32(smem + s * C::STAGE);
-      const uint32_t sb = sa + NPL * C::A_BYTES;
+      const uint32_t d = tmem + static_cast<uint32_t>(b * BN);
+      for (int kc = 0; kc < nk; ++kc, ++it) {
+        const int s = static_cast<int>(it % C::STAGES);
+        ok = ptx::mbar_wait(ptx::smem_u32(&bars[s]), static_cast<uint32_t>((it / C::STAGES) & 1), g.err,
+                            ptx::kErrWaitFull);
+        if (!ok) break;
+        ptx::tc_fence_after();
+        const uint32_t sa = ptx::smem_u32(smem + s * C::STAGE);
+        const uint32_t sb = sa + NPL * C::A_BYTES;
 #pragma unroll
-      for (int kk = 0; kk < C::BK / C::KI; ++kk) {
-        const uint32_t off = kk * C::KI * C::EB;   // bytes along the 128-byte row
+        for (int kk = 0; kk < C::BK / C::KI; ++kk) {
+          const uint32_t off = kk * C::KI * C::EB;   // bytes along the 128-byte row
 #pragma unroll
-        for (int p = 0; p < C::NPROD; ++p) {
-          // products: (A0,B0), (A0,B1), (A1,B0)
-          const uint32_t a = sa + (p == 2 ? C::A_BYTES : 0) + off;
-          const uint32_t b = sb + (p == 1 ? C::B_BYTES : 0) + off;
-          const uint32_t acc = (kc > 0 || kk > 0 || p > 0) ? 1u : 0u;
-          if (KIND == kKindBF16)
-            ptx::mma_bf16(tmem, ptx::smem_desc_k_sw128(a), ptx::smem_desc_k_sw128(b), idesc, acc);
-          else
-            ptx::mma_tf32(tmem, ptx::smem_desc_k_sw128(a), ptx::smem_desc_k_sw128(b), idesc, acc);
+          for (int p = 0; p < C::NPROD; ++p) {
+            // products: (A0,B0), (A0,B1), (A1,B0)
+            const uint32_t a = sa + (p == 2 ? C::A_BYTES : 0) + off;
+            const uint32_t bb = sb + (p == 1 ? C::B_BYTES : 0) + off;
+            const uint32_t acc = (kc > 0 || kk > 0 || p > 0) ? 1u : 0u;
+            if (KIND == kKindBF16)
+              ptx::mma_bf16(d, ptx::smem_desc_k_sw128(a), ptx::smem_desc_k_sw128(bb), idesc, acc);
+            else
+              ptx::mma_tf32(d, ptx::smem_desc_k_sw128(a), ptx::smem_desc_k_sw128(bb), idesc, acc);
+          }
         }
+        ptx::mma_commit(ptx::smem_u32(&bars[C::STAGES + s]));   // frees the stage
       }
-      ptx::mma_commit(ptx::smem_u32(&bars[C::STAGES + s]));   // frees the stage
+      ptx::mma_commit(ptx::smem_u32(&accf[b]));                 // accumulator b ready
     }
-    ptx::mma_commit(ptx::smem_u32(&bars[2 * C::STAGES]));     // accumulator ready
   } else if (warp >= 2) {
     // ---------------------------------------------------------- epilogue
-    const bool ok = ptx::mbar_wait(ptx::smem_u32(&bars[2 * C::STAGES]), 0, g.err, ptx::kErrWaitAccum);
-    ptx::tc_fence_after();
-    const bool flagged = g.err && *reinterpret_cast<volatile int*>(g.err);
-    // tcgen05.ld is warp-collective: decide for the whole warp
-    if (__all_sync(0xffffffffu, ok && !flagged)) {
-      const int quarter = warp % 4;                  // tensor-memory lanes 32*quarter ..
+    const int quarter = warp % 4;                  // tensor-memory lanes 32*quarter ..
+    int tcount = 0;
+    for (long long tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++tcount) {
+      const int b = tcount & 1, use = tcount >> 1;
+      const bool ok = ptx::mbar_wait(ptx::smem_u32(&accf[b]), static_cast<uint32_t>(use & 1), g.err,
+                                     ptx::kErrWaitAccum);
+      ptx::tc_fence_after();
+      const bool flagged = abort_flag && *abort_flag;
+      // tcgen05.ld is warp-collective: decide for the whole warp
+      if (!__all_sync(0xffffffffu, ok && !flagged)) break;
+      int m0, n0;
+      tile_coords<BN>(g, num_m, num_n, tile, m0, n0);
       const int m = m0 + quarter * 32 + lane;
       const bool mvalid = m < g.M;
-      const long long mterm = mvalid ? (static_cast<long long>(m % g.rm) + static_cast<long long>(m / g.rm) * g.sm) : 0;
+      const long long mterm =
+          mvalid ? (static_cast<long long>(m % g.rm) + static_cast<long long>(m / g.rm) * g.sm) : 0;
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
         uint32_t r[32];
-        ptx::tmem_ld_32x32b_x32(tmem + (static_cast<uint32_t>(quarter * 32) << 16) + c0, r);
+        ptx::tmem_ld_32x32b_x32(tmem + (static_cast<uint32_t>(quarter * 32) << 16) +
+                                    static_cast<uint32_t>(b * BN + c0), r);
         ptx::tmem_ld_wait();
-        if (!mvalid) continue;
-        if (OUT == kOutDF) {
-          // read-modify-write of the float pair: issue every load of the chunk
-          // before any dependent arithmetic so the 64 loads overlap
-          float* ph = static_cast<float*>(g.out0);
-          float* pl = static_cast<float*>(g.out1);
-          float oh[32], ol[32];
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int n = n0 + c0 + j;
-            const long long idx = mterm + static_cast<long long>(n < g.N ? n : 0) * g.sn;
-            oh[j] = (g.accumulate && n < g.N) ? ph[idx] : 0.0f;
-            ol[j] = (g.accumulate && n < g.N) ? pl[idx] : 0.0f;
-          }
-#pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            const int n = n0 + c0 + j;
-            if (n >= g.N) break;
-            const long long idx = mterm + static_cast<long long>(n) * g.sn;
-            float sh, se;
-            two_sum(oh[j], __uint_as_float(r[j]), sh, se);
-            se += ol[j];
-            const float hi = sh + se;
-            ph[idx] = hi;
-            pl[idx] = se - (hi - sh);
-          }
-          continue;
-        }
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int n = n0 + c0 + j;
-          if (n >= g.N) break;
-          const long long idx = mterm + static_cast<long long>(n) * g.sn;
-          const float v = __uint_as_float(r[j]);
-          if (OUT == kOutSplitBF16) {
-            __nv_bfloat16 hi, lo;
-            split_bf16(v, hi, lo);
-            static_cast<__nv_bfloat16*>(g.out0)[idx] = hi;
-            static_cast<__nv_bfloat16*>(g.out1)[idx] = lo;
-          } else if (OUT == kOutBF16) {
-            static_cast<__nv_bfloat16*>(g.out0)[idx] = __float2bfloat16_rn(v);
-          } else if (OUT == kOutF32) {
-            static_cast<float*>(g.out0)[idx] = v;
-          } else if (OUT == kOutF64) {
-            static_cast<double*>(g.out0)[idx] = static_cast<double>(v);
-          }
-        }
+        if (mvalid) store_chunk<OUT>(g, mterm, n0 + c0, r);
       }
+      ptx::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&acce[b]));   // buffer b may be refilled
     }
   }
   ptx::tc_fence_before();
@@ -295,9 +349,12 @@ cudaError_t launch(const Operand& A, const Operand& B, const GemmOut& g, cudaStr
   if (e != cudaSuccess) return e;
   const long long tiles = static_cast<long long>((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN);
   if (tiles <= 0) return cudaSuccess;
-  if (tiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long ctas = tiles < sms ? tiles : sms;   // persistent: one CTA per SM
   note_launch(1);
-  kern<<<static_cast<unsigned>(tiles), kThreads, C::SMEM, s>>>(m[0], m[1], m[2], m[3], g);
+  kern<<<static_cast<unsigned>(ctas), kThreads, C::SMEM, s>>>(m[0], m[1], m[2], m[3], g);
   return cudaGetLastError();
 }
 
