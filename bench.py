@@ -180,6 +180,11 @@ def run_reference(args):
 # --------------------------------------------------------------- our arm
 
 PRECISIONS = {"fp64": 0, "mixed_bf16": 1, "mixed_bf16x3": 2, "mixed_tf32": 3}
+
+# DRAM bytes (read + write) per grid point of one launch, from one ncu capture
+# of the named kernel (profiles/mixed_bf16x3_poisson512.md: 256^3 case, scaled
+# by points).  An entry must be removed when its kernel changes.
+MEASURED_TRAFFIC_PER_POINT = {("residual", "mixed_bf16x3"): (274.215936e6 + 54.527488e6) / 256 ** 3}
 DTYPE = {"fp64": "f64", "mixed_bf16": "bf16/f32/f64", "mixed_bf16x3": "bf16x3/f32/f64",
          "mixed_tf32": "tf32/f32/f64"}
 
@@ -388,6 +393,10 @@ def stage_rooflines(ms, iters, n, prec):
                   "bytes_per_launch": byts, "traffic": None})
         d["frac"] = d["achieved"] / d["peak"]
         out.append(d)
+    for d in out:
+        key = (d["kernel"], {1: "mixed_bf16", 2: "mixed_bf16x3", 3: "mixed_tf32"}[prec])
+        if key in MEASURED_TRAFFIC_PER_POINT:
+            d["traffic"] = MEASURED_TRAFFIC_PER_POINT[key] * npts
     return {"per_stage": out, "iters": iters, "peak_source": "MEASURED_PEAKS.json (burst)"}
 
 
