@@ -57,8 +57,9 @@ enum { TPT_BC_PERIODIC = 0, TPT_BC_NEUMANN = 1, TPT_BC_DIRICHLET = 2 };
 
 /* Transform of a diagonalised direction (x or y), Sec. 3: numerical eigenbasis
  * applied as a GEMM, or the Fourier-based transform of a uniform direction
- * (real DFT for periodic, DCT-II/III for Neumann-Neumann).  AUTO picks FFT
- * when the spacing is uniform and the boundary pair has a fast transform.  */
+ * (real DFT for periodic, DCT-II/III for Neumann-Neumann; Makhoul's
+ * reordering, footnote to Sec. 4.2).  FFT needs a float64 plan, uniform
+ * spacing and a power-of-two size; AUTO picks it when it applies.          */
 enum { TPT_XFORM_AUTO = 0, TPT_XFORM_GEMM = 1, TPT_XFORM_FFT = 2 };
 
 /* Arithmetic of the transforms and the Thomas sweep.  FP64: float64
@@ -202,6 +203,12 @@ int tpt_tc_gemm(int precision, int M, int N, int K, const double* A_dev, const d
  * eigenvalues of direction dir (0 = x, 1 = y) in the plan's mode order;
  * a, b, c: the 1D rows of direction dir (0..2), n[dir] each.              */
 int tpt_plan_eigenvalues(tpt_plan plan, int dir, double* lam_host);
+/* Transform the plan chose for x and y (TPT_XFORM_GEMM or TPT_XFORM_FFT; AUTO
+ * resolves to FFT on a uniform power-of-two periodic or Neumann-Neumann
+ * direction of a float64 plan).  For FFT directions the mode order is the
+ * real-DFT half-complex order (periodic: constant, cos 1, sin 1, ..., Nyquist)
+ * or the DCT-II order (Neumann), and lam holds matching eigenvalues.        */
+int tpt_plan_transforms(tpt_plan plan, int* xform_host /* 2 ints */);
 int tpt_plan_rows(tpt_plan plan, int dir, double* a_host, double* b_host, double* c_host);
 
 /* ---- diagnostics -------------------------------------------------------- */

@@ -100,8 +100,31 @@ int upload_basis(tpt_plan_s* p, int d) {
   return TPT_OK;
 }
 
+// Trigonometric tables of a Fourier-transformed direction and its eigenvalues.
+int upload_fft(tpt_plan_s* p, int d) {
+  const int n = p->n[d];
+  const long double pi = 3.141592653589793238462643383279502884L;
+  std::vector<double> twc(n / 2 > 0 ? n / 2 : 1, 1.0), tws(twc.size(), 0.0), hc(n), hs(n);
+  for (int m = 0; m < n / 2; ++m) {
+    twc[m] = static_cast<double>(std::cos(2.0L * pi * m / n));
+    tws[m] = static_cast<double>(std::sin(2.0L * pi * m / n));
+  }
+  for (int k = 0; k < n; ++k) {
+    hc[k] = static_cast<double>(std::cos(pi * k / (2.0L * n)));
+    hs[k] = static_cast<double>(std::sin(pi * k / (2.0L * n)));
+  }
+  tpt::FftTables& t = p->fft[d];
+  TPT_TRY(upload(p, twc, &t.twc));
+  TPT_TRY(upload(p, tws, &t.tws));
+  TPT_TRY(upload(p, hc, &t.hc));
+  TPT_TRY(upload(p, hs, &t.hs));
+  TPT_TRY(upload(p, p->eig[d].lam, &p->ddir[d].lam));
+  return TPT_OK;
+}
+
 int apply_transform(const tpt_plan_s* p, int d, bool inverse, const double* in, double* out,
                     bool accumulate, cudaStream_t s) {
+  if (p->xform[d] == TPT_XFORM_FFT) return cuda_status(tpt::fft_fp64(p, d, inverse, in, out, accumulate, s));
   const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
   const double* mat = inverse ? p->ddir[d].inv : p->ddir[d].fwd;
   if (d == 0) {
@@ -224,8 +247,12 @@ int tpt_plan_create(const tpt_desc* desc, int cuda_device, tpt_plan* out) {
   }
   if (p->dir[2].periodic) return fail(TPT_ERR_UNSUPPORTED);
   for (int d = 0; d < 2; ++d) {
-    if (desc->xform[d] == TPT_XFORM_FFT) return fail(TPT_ERR_UNSUPPORTED);
-    p->xform[d] = TPT_XFORM_GEMM;
+    // Fourier-based transforms: float64 path, uniform power-of-two directions
+    const bool ok = tpt::fft_supported(p->dir[d]) && desc->precision == TPT_PREC_FP64;
+    if (desc->xform[d] == TPT_XFORM_FFT && !ok) return fail(TPT_ERR_UNSUPPORTED);
+    p->xform[d] = (desc->xform[d] == TPT_XFORM_FFT || (desc->xform[d] == TPT_XFORM_AUTO && ok))
+                      ? TPT_XFORM_FFT
+                      : TPT_XFORM_GEMM;
   }
   p->alpha = desc->alpha;
   p->beta = desc->beta;
@@ -233,8 +260,18 @@ int tpt_plan_create(const tpt_desc* desc, int cuda_device, tpt_plan* out) {
   p->rtol = desc->rtol;
   p->max_refine = desc->max_refine;
   for (int d = 0; d < 2; ++d) {
-    int st = tpt::eigen_dir(p->dir[d], &p->eig[d]);
+    int st = (p->xform[d] == TPT_XFORM_FFT) ? tpt::fft_dir(p->dir[d], &p->eig[d], &p->fft[d].kind)
+                                           : tpt::eigen_dir(p->dir[d], &p->eig[d]);
     if (st != TPT_OK) return fail(st);
+    // f-hat of the constant 1 on the null mode: N for the Fourier transforms,
+    // sum_i Q~[i, null] sqrt(dx_i) for the eigenbasis
+    if (p->xform[d] == TPT_XFORM_FFT) {
+      p->null_g[d] = p->n[d];
+    } else {
+      double g = 0.0;
+      for (int i = 0; i < p->n[d]; ++i) g += p->eig[d].qt[i] * std::sqrt(p->dir[d].dxf[i]);
+      p->null_g[d] = g;
+    }
   }
   p->singular = (p->alpha == 0.0) && p->dir[0].has_null() && p->dir[1].has_null() &&
                 p->dir[2].has_null();
@@ -258,7 +295,7 @@ int tpt_plan_create(const tpt_desc* desc, int cuda_device, tpt_plan* out) {
   if (cuda_device >= ndev) return fail(TPT_ERR_INVALID_ARG);
   DeviceGuard guard(cuda_device);
   for (int d = 0; d < 2; ++d) {
-    int st = upload_basis(p, d);
+    int st = (p->xform[d] == TPT_XFORM_FFT) ? upload_fft(p, d) : upload_basis(p, d);
     if (st != TPT_OK) return fail(st);
   }
   for (int d = 0; d < 3; ++d) {
@@ -438,6 +475,13 @@ int tpt_tc_gemm(int precision, int M, int N, int K, const double* A, const doubl
 int tpt_set_stage_timing(tpt_plan p, int enable) {
   if (!p) return TPT_ERR_INVALID_ARG;
   p->stage_timing = enable ? 1 : 0;
+  return TPT_OK;
+}
+
+int tpt_plan_transforms(tpt_plan p, int* xform) {
+  if (!p || !xform) return TPT_ERR_INVALID_ARG;
+  xform[0] = p->xform[0];
+  xform[1] = p->xform[1];
   return TPT_OK;
 }
 

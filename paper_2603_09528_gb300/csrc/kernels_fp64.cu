@@ -265,15 +265,8 @@ cudaError_t thomas_fp64(const tpt_plan_s* p, const double* fhat, double* phihat,
   const int bs = 128;
   const long long nb = (lines + bs - 1) / bs;
   const double* rz = p->d_rows[2];
-  double null_scale = 0.0;
-  if (p->singular) {
-    // f-hat of the null line equals (g_x g_y) times the physical constant,
-    // with g = sum_i Q~[i, null] sqrt(dx_i)
-    double gx = 0.0, gy = 0.0;
-    for (int i = 0; i < nx; ++i) gx += p->eig[0].qt[i] * std::sqrt(p->dir[0].dxf[i]);
-    for (int j = 0; j < ny; ++j) gy += p->eig[1].qt[j] * std::sqrt(p->dir[1].dxf[j]);
-    null_scale = 1.0 / (gx * gy);
-  }
+  // f-hat of the null line equals (g_x g_y) times the physical constant
+  const double null_scale = p->singular ? 1.0 / (p->null_g[0] * p->null_g[1]) : 0.0;
   note_launch();
   thomas_fp64_kernel<<<static_cast<unsigned>(nb), bs, 0, s>>>(
       nx, ny, nz, fhat, phihat, scratch, p->ddir[0].lam, p->ddir[1].lam, rz, rz + nz, rz + 2 * nz,

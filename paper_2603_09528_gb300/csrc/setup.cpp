@@ -270,4 +270,42 @@ int eigen_dir(const Dir1D& d, Eigen1D* out) {
   return TPT_OK;
 }
 
+bool fft_supported(const Dir1D& d) {
+  const int n = d.n;
+  const bool pow2 = n >= 1 && (n & (n - 1)) == 0;
+  const bool bcs = d.periodic || (d.bc[0] == TPT_BC_NEUMANN && d.bc[1] == TPT_BC_NEUMANN);
+  return pow2 && d.uniform && bcs;
+}
+
+int fft_dir(const Dir1D& d, Eigen1D* out, int* kind) {
+  if (!fft_supported(d)) return TPT_ERR_UNSUPPORTED;
+  const int n = d.n;
+  *kind = d.periodic ? 0 : 1;
+  const long double pi = 3.141592653589793238462643383279502884L;
+  std::vector<double> v(n);
+  out->lam.assign(n, 0.0);
+  out->qt.clear();
+  for (int p = 0; p < n; ++p) {
+    for (int i = 0; i < n; ++i) {
+      long double x;
+      if (*kind == 1) {
+        x = std::cos(pi * p * (2.0L * i + 1.0L) / (2.0L * n));
+      } else if (p == 0) {
+        x = 1.0L;
+      } else if (p == n - 1) {
+        x = (i % 2 == 0) ? 1.0L : -1.0L;
+      } else {
+        const int k = (p + 1) / 2;
+        const long double arg = 2.0L * pi * i * k / n;
+        x = (p % 2 == 1) ? std::cos(arg) : std::sin(arg);
+      }
+      v[i] = static_cast<double>(x);
+    }
+    // the Rayleigh quotient takes D^{1/2} v; on a uniform grid that is a constant factor
+    out->lam[p] = (p == 0) ? 0.0 : rayleigh(d, v.data());
+  }
+  out->null_mode = 0;
+  return TPT_OK;
+}
+
 }  // namespace tpt

@@ -35,6 +35,13 @@ struct Eigen1D {
 };
 
 int build_dir(int n, const double* dxf, const double* dxc, const int bc[2], Dir1D* out);
+// Fourier-based transform of a uniform direction: true when N is a power of
+// two, the spacing uniform and the boundary pair periodic or Neumann-Neumann.
+bool fft_supported(const Dir1D& d);
+// Eigenvalues in the mode order of the Fourier-based transform (real DFT for
+// periodic, DCT-II for Neumann), as Rayleigh quotients of the exact
+// trigonometric vectors with the float64 rows; kind: 0 real DFT, 1 DCT.
+int fft_dir(const Dir1D& d, Eigen1D* out, int* kind);
 int eigen_dir(const Dir1D& d, Eigen1D* out);
 int grid_tanh(int n, double L, double stretch, double* dxf, double* dxc);
 
@@ -57,6 +64,14 @@ struct MixedTables {
   double* null_invm = nullptr;     //   c'_k and 1/m_k, k < Nz - 1
   cudaStream_t side = nullptr;     // second stream for the null line, with fork/join events
   cudaEvent_t fork = nullptr, join = nullptr;
+};
+
+struct FftTables {    // device tables of a Fourier-transformed direction
+  int kind = 0;          // 0 real DFT (periodic), 1 DCT-II/III (Neumann)
+  double* twc = nullptr; // cos, sin of 2 pi m / N, m < N/2
+  double* tws = nullptr;
+  double* hc = nullptr;  // cos, sin of pi k / 2N, k < N (DCT pre/post rotation)
+  double* hs = nullptr;
 };
 
 struct DevDir {       // device tables of a diagonalised direction (float64)
@@ -89,6 +104,8 @@ struct tpt_plan_s {
   tpt::Dir1D dir[3];
   tpt::Eigen1D eig[2];
   tpt::DevDir ddir[2];
+  tpt::FftTables fft[2];
+  double null_g[2] = {1.0, 1.0};  // f-hat of a constant 1 on the null mode, per direction
   double* d_rows[3] = {nullptr, nullptr, nullptr};  // a|b|c per direction, 3n doubles
   double* d_dxf[3] = {nullptr, nullptr, nullptr};
   double* d_scal = nullptr;       // device scalars of the single-step entry points
@@ -117,6 +134,11 @@ cudaError_t dgemm_cm(int M, int N, int K, const double* A, int lda, long long sA
 
 // `defect` (device, may be NULL) receives the physical constant removed from
 // the right-hand side of a singular problem.
+// Fourier-based transform along x (d = 0) or y (d = 1) of a float64 field in
+// the natural layout (fft.cu); out (+)= result.
+cudaError_t fft_fp64(const tpt_plan_s* p, int d, bool inverse, const double* in, double* out,
+                     bool accumulate, cudaStream_t s);
+
 cudaError_t thomas_fp64(const tpt_plan_s* p, const double* fhat, double* phihat, double* scratch,
                         double* defect, cudaStream_t s);
 

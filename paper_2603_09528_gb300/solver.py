@@ -151,6 +151,11 @@ class Plan:
               "tpt_plan_eigenvalues")
         return lam
 
+    def transforms(self):
+        x = (C.c_int * 2)()
+        check(lib.tpt_plan_transforms(self._h, x), "tpt_plan_transforms")
+        return int(x[0]), int(x[1])
+
     def rows(self, direction: int):
         m = self.n[direction]
         a, b, c = np.empty(m), np.empty(m), np.empty(m)

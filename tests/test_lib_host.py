@@ -122,3 +122,54 @@ def test_grid_helper_matches_oracle_grid():
         # face differences near x = L lose a few bits to cancellation
         assert np.allclose(dxf, rf, rtol=1e-12, atol=0) and np.allclose(dxc, rc, rtol=1e-12, atol=0)
     assert L.lib.tpt_grid_tanh(0, 1.0, 1.0, None, None) == L.TPT_ERR_INVALID_ARG
+
+
+def _xforms(h):
+    x = (C.c_int * 2)()
+    assert L.lib.tpt_plan_transforms(h, x) == L.TPT_OK
+    return int(x[0]), int(x[1])
+
+
+def test_fft_eigenvalues_in_transform_order():
+    # periodic N = 32 (real DFT, half-complex order) and Neumann N = 64 (DCT-II order)
+    for n, bc, kind in [(32, (0, 0), "dft"), (64, (1, 1), "dct"), (2, (0, 0), "dft"), (1, (1, 1), "dct")]:
+        grids = [O.uniform_grid(n), O.uniform_grid(n), O.tanh_grid(8, 1.0, 1.0)]
+        d, keep = _desc((n, n, 8), grids, [bc, bc, (1, 1)], xform=(L.TPT_XFORM_FFT, L.TPT_XFORM_AUTO))
+        h = C.c_void_p()
+        assert L.lib.tpt_plan_create(C.byref(d), -1, C.byref(h)) == L.TPT_OK
+        assert _xforms(h) == (L.TPT_XFORM_FFT, L.TPT_XFORM_FFT)
+        lam = np.empty(n)
+        assert L.lib.tpt_plan_eigenvalues(h, 0, lam.ctypes.data_as(L._dp)) == L.TPT_OK
+        hh = 1.0 / n
+        if kind == "dct":
+            ref = -4 * np.sin(np.pi * np.arange(n) / (2 * n)) ** 2 / hh ** 2
+        else:
+            ks = [0] + [(p + 1) // 2 for p in range(1, n - 1)] + ([n // 2] if n > 1 else [])
+            ref = -4 * np.sin(np.pi * np.array(ks[:n]) / n) ** 2 / hh ** 2
+        assert np.allclose(lam, ref, rtol=1e-13, atol=1e-9), (n, kind, lam[:4], ref[:4])
+        assert lam[0] == 0.0
+        L.lib.tpt_plan_destroy(h)
+
+
+def test_transform_selection_rules():
+    st_grid = O.tanh_grid(32, 1.0, 1.5)
+    un = O.uniform_grid(32)
+    h = C.c_void_p()
+    # AUTO: FFT on uniform power of two, GEMM on stretched or non-power-of-two
+    d, keep = _desc((32, 32, 8), [un, st_grid, O.tanh_grid(8, 1.0, 1.0)], [(0, 0), (1, 1), (1, 1)],
+                    xform=(L.TPT_XFORM_AUTO, L.TPT_XFORM_AUTO))
+    assert L.lib.tpt_plan_create(C.byref(d), -1, C.byref(h)) == L.TPT_OK
+    assert _xforms(h) == (L.TPT_XFORM_FFT, L.TPT_XFORM_GEMM)
+    L.lib.tpt_plan_destroy(h)
+    d, keep = _desc((24, 32, 8), [O.uniform_grid(24), un, O.tanh_grid(8, 1.0, 1.0)], [(1, 1), (2, 1), (1, 1)],
+                    xform=(L.TPT_XFORM_AUTO, L.TPT_XFORM_AUTO))
+    assert L.lib.tpt_plan_create(C.byref(d), -1, C.byref(h)) == L.TPT_OK
+    assert _xforms(h) == (L.TPT_XFORM_GEMM, L.TPT_XFORM_GEMM)   # 24 not a power of two; Dirichlet y
+    L.lib.tpt_plan_destroy(h)
+    # explicit FFT where it does not apply, or on a mixed-precision plan
+    d, keep = _desc((32, 32, 8), [st_grid, un, O.tanh_grid(8, 1.0, 1.0)], [(1, 1), (1, 1), (1, 1)],
+                    xform=(L.TPT_XFORM_FFT, L.TPT_XFORM_GEMM))
+    assert L.lib.tpt_plan_create(C.byref(d), -1, C.byref(h)) == L.TPT_ERR_UNSUPPORTED
+    d, keep = _desc((32, 32, 8), [un, un, O.tanh_grid(8, 1.0, 1.0)], [(1, 1), (1, 1), (1, 1)],
+                    prec=L.TPT_PREC_MIXED_BF16X3, xform=(L.TPT_XFORM_FFT, L.TPT_XFORM_GEMM))
+    assert L.lib.tpt_plan_create(C.byref(d), -1, C.byref(h)) == L.TPT_ERR_UNSUPPORTED
