@@ -104,3 +104,54 @@ def test_mixed_identity_operator_returns_rhs(prec):
     phi, info = plan.solve(tpt.field_to_device(f))
     got = tpt.field_to_host(phi, n)
     assert np.abs(got - f).max() <= 1e-12 * np.abs(f).max(), np.abs(got - f).max()
+
+
+MIXED_BCS = {
+    "NNN": [(1, 1)] * 3,
+    "DND": [(2, 1), (1, 2), (2, 2)],
+    "PNN": [(0, 0), (1, 1), (1, 1)],
+}
+
+
+@pytest.mark.parametrize("prec", list(PRECS))
+@pytest.mark.parametrize("bcs", list(MIXED_BCS))
+@pytest.mark.parametrize("coef", [(0.0, 1.0), (1.0, -5e-4)])
+def test_mixed_ragged_sizes_and_boundaries(prec, bcs, coef):
+    # 70 and 45 are not multiples of 8 (padded operand rows) and span two
+    # 128-row tiles / partial 256-column tiles; Nz = 33 leaves identity rows in
+    # the partition Thomas; periodic x uses the cyclic (Jacobi) eigenbasis
+    n = (70, 45, 33)
+    stretch = (1.5 if bcs != "PNN" else 1.2, 2.0, 2.5)
+    dirs = _dirs(n, stretch, MIXED_BCS[bcs])
+    f = S.uniform_rhs(n, 17)
+    if O.is_singular(dirs, coef[0]):
+        f = S.remove_weighted_mean(f, [d.dxf for d in dirs])
+    plan = tpt.Plan(n, [d.dxf for d in dirs], [d.dxc for d in dirs], MIXED_BCS[bcs],
+                    xform=(tpt.GEMM, tpt.GEMM), alpha=coef[0], beta=coef[1], precision=PRECS[prec],
+                    rtol=1e-10, max_refine=40)
+    phi, info = plan.solve(tpt.field_to_device(f))
+    got = tpt.field_to_host(phi, n)
+    r = O.residual(f, got, dirs, *coef, np.longdouble)
+    rel = float(np.sqrt(np.sum(r ** 2) / np.sum(f ** 2)))
+    ref, _ = O.solve_tensor(f, dirs, *coef)
+    err = np.abs(got - ref).max() / np.abs(ref).max()
+    print("ragged", prec, bcs, coef, "iters", info["iters"], "rel_res", rel, "err", err)
+    assert info["rel_residual"] <= 1e-10 and rel <= 2e-10
+    assert err <= 1e-7
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+def test_mixed_refined_to_float64_accuracy_matches_oracle(prec):
+    # refining the tensor-core correction solves to rtol 1e-13 gives a
+    # float64-accurate result: the 1e-12 parity bar of the float64 path
+    n = (96, 80, 64)
+    dirs = _dirs(n, (1.5, 2.0, 2.5), [(1, 1)] * 3)
+    f = S.remove_weighted_mean(S.uniform_rhs(n, 29), [d.dxf for d in dirs])
+    plan = tpt.Plan(n, [d.dxf for d in dirs], [d.dxc for d in dirs], [(1, 1)] * 3,
+                    xform=(tpt.GEMM, tpt.GEMM), alpha=0.0, beta=1.0, precision=PRECS[prec],
+                    rtol=1e-13, max_refine=40)
+    phi, info = plan.solve(tpt.field_to_device(f))
+    ref, _ = O.solve_tensor(f, dirs, 0.0, 1.0)
+    err = np.abs(tpt.field_to_host(phi, n) - ref).max() / np.abs(ref).max()
+    print("fp64-accurate", prec, "iters", info["iters"], "err", err)
+    assert err <= 1e-12
