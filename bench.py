@@ -262,6 +262,7 @@ def run_ours(args):
         ms = np.mean([i["ms_stage"] for i in infos], axis=0)
         its = float(np.mean([i["iters"] for i in infos]))
         stages = stage_rooflines(ms, its, n, prec)
+        stages["per_solve_ms"] = {"input_conversion": float(ms[0]), "gauge_and_output": float(ms[7])}
         plan.set_stage_timing(False)
 
     # roofline of the dominant kernel

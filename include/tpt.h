@@ -95,9 +95,10 @@ typedef struct {
   double compat_defect;  /* singular problems: cell-volume-weighted mean removed
                             from f to make it compatible; 0 otherwise              */
   float ms_stage[8];     /* with tpt_set_stage_timing(plan, 1), mixed plans: GPU
-                            milliseconds summed over the corrections of the call,
-                            [1] x forward, [2] y forward, [3] Thomas, [4] y inverse,
-                            [5] x inverse, [6] residual; 0 otherwise              */
+                            milliseconds: [0] input conversion, summed over the
+                            corrections [1] x forward, [2] y forward, [3] Thomas,
+                            [4] y inverse, [5] x inverse, [6] residual, and [7]
+                            gauge and float64 output; 0 otherwise                 */
 } tpt_info;
 
 /* Build a plan on CUDA device `cuda_device` (or, with cuda_device < 0, a

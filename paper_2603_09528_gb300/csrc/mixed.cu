@@ -88,14 +88,15 @@ __device__ __forceinline__ df split_double_int(double v) {
 }
 
 // float -> float64, exact, with integer operations (normal numbers and zero).
+// Zero and subnormals map to a signed zero, infinities and NaN to the float64
+// exponent 2047, all without conversion instructions.
 __device__ __forceinline__ double f2d_int(float f) {
   const unsigned u = __float_as_uint(f);
   const unsigned e = (u >> 23) & 0xFF;
-  if (e == 0 || e == 255) return static_cast<double>(f);
-  const unsigned long long b = (static_cast<unsigned long long>(u >> 31) << 63) |
-                               (static_cast<unsigned long long>(e + 896) << 52) |
-                               (static_cast<unsigned long long>(u & 0x7FFFFF) << 29);
-  return __longlong_as_double(static_cast<long long>(b));
+  const unsigned long long sign = static_cast<unsigned long long>(u >> 31) << 63;
+  const unsigned long long ee = (e == 0) ? 0ull : (e == 255 ? 2047ull : static_cast<unsigned long long>(e + 896));
+  const unsigned long long mm = (e == 0) ? 0ull : (static_cast<unsigned long long>(u & 0x7FFFFF) << 29);
+  return __longlong_as_double(static_cast<long long>(sign | (ee << 52) | mm));
 }
 
 // ------------------------------------------------------ operand element I/O
@@ -138,36 +139,102 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
+// acc += coef * (x - y) with float pairs; acc stays unnormalised (hi, lo)
+__device__ __forceinline__ void acc_flux(df& acc, float ch, float cl, df x, df y) {
+  df d = two_sum(x.hi, -y.hi);
+  d.lo += x.lo - y.lo;
+  const float pr = ch * d.hi;
+  float pe = fmaf(ch, d.hi, -pr);
+  pe = fmaf(ch, d.lo, pe);
+  pe = fmaf(cl, d.hi, pe);
+  const df t = two_sum(acc.hi, pr);
+  acc.hi = t.hi;
+  acc.lo += t.lo + pe;
+}
+// acc += coef * x
+__device__ __forceinline__ void acc_mul(df& acc, float ch, float cl, df x) {
+  const float pr = ch * x.hi;
+  float pe = fmaf(ch, x.hi, -pr);
+  pe = fmaf(ch, x.lo, pe);
+  pe = fmaf(cl, x.hi, pe);
+  const df t = two_sum(acc.hi, pr);
+  acc.hi = t.hi;
+  acc.lo += t.lo + pe;
+}
+
+
 // f (float64, (Nx,Ny,Nz)) -> f as float pair, R = f in operand format, and
 // the sums sum f^2 (float), sum f and sum vol*f (float pairs) added to
 // sums[0..2].  No float64 arithmetic per point.
 template <int FMT>
 __global__ void __launch_bounds__(256)
-prepare_kernel(int nx, int ny, int nz, int ldx, const double* __restrict__ f, float* __restrict__ fh,
+prepare_kernel(int nx, int ny, int nz, int ldx, int nbi, const double* __restrict__ f, float* __restrict__ fh,
                float* __restrict__ fl, void* r0, void* r1, const float* __restrict__ gx,
                const float* __restrict__ gy, const float* __restrict__ gz, double* sums) {
-  const long long n = static_cast<long long>(nx) * ny * nz;
-  float s2 = 0.0f;
-  df s1 = {0.0f, 0.0f}, sv = {0.0f, 0.0f};
-  for (long long o = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; o < n;
-       o += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const int i = static_cast<int>(o % nx);
-    const long long line = o / nx;
-    const int j = static_cast<int>(line % ny), k = static_cast<int>(line / ny);
-    const df d = split_double_int(f[o]);
-    fh[o] = d.hi;
-    fl[o] = d.lo;
-    Elem<FMT>::store(r0, r1, i + static_cast<long long>(ldx) * line, d.hi + d.lo);
-    s2 = fmaf(d.hi, d.hi, s2);
-    s1 = df_add(s1, d);
-    const df vol = df_mul(df_mul({gx[i], gx[nx + i]}, {gy[j], gy[ny + j]}), {gz[k], gz[nz + k]});
-    sv = df_add(sv, df_mul(vol, d));
+  // work item t covers x-line (j, k) = t / nbi, points (t % nbi) * 256 + 0..255;
+  // one division per item (uniform over the block), none per element.
+  // sum f^2 and sum f feed only the norm of f (float is enough); sum vol*f
+  // fixes the compatibility constant and is kept as a float pair, with the
+  // line weight dy_j dz_k applied once per item.
+  const long long items = static_cast<long long>(nbi) * ny * nz;
+  float s2 = 0.0f, s1f = 0.0f;
+  df sv = {0.0f, 0.0f};
+  constexpr int U = 4;   // items in flight per thread
+  for (long long t0 = blockIdx.x; t0 < items; t0 += static_cast<long long>(U) * gridDim.x) {
+    double v[U];
+    long long line[U];
+    int ii[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long t = t0 + static_cast<long long>(u) * gridDim.x;
+      line[u] = t / nbi;
+      ii[u] = static_cast<int>(t % nbi) * 256 + threadIdx.x;
+      const bool ok = t < items && ii[u] < nx;
+      if (!ok) ii[u] = -1;
+      v[u] = ok ? f[ii[u] + static_cast<long long>(nx) * line[u]] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = ii[u];
+      if (i < 0) continue;
+      const int j = static_cast<int>(line[u] % ny), k = static_cast<int>(line[u] / ny);
+      const long long o = i + static_cast<long long>(nx) * line[u];
+      const df d = split_double_int(v[u]);
+      fh[o] = d.hi;
+      fl[o] = d.lo;
+      Elem<FMT>::store(r0, r1, i + static_cast<long long>(ldx) * line[u], d.hi + d.lo);
+      s2 = fmaf(d.hi, d.hi, s2);
+      s1f += d.hi;
+      const df wline = df_mul({gy[j], gy[ny + j]}, {gz[k], gz[nz + k]});
+      acc_mul(sv, wline.hi, wline.lo, df_mul({gx[i], gx[nx + i]}, d));
+    }
   }
-  double a = s2, b = static_cast<double>(s1.hi) + s1.lo, c = static_cast<double>(sv.hi) + sv.lo;
-  a = warp_sum_d(a);
-  b = warp_sum_d(b);
-  c = warp_sum_d(c);
-  if (threadIdx.x % 32 == 0) {
+  df s1 = {s1f, 0.0f};
+  sv = fast_two_sum(sv.hi, sv.lo);
+  // block reduction in float pairs, one float64 atomic per block and sum
+  __shared__ float red[3][2][8];
+  const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    s1 = df_add(s1, {__shfl_xor_sync(0xffffffffu, s1.hi, o), __shfl_xor_sync(0xffffffffu, s1.lo, o)});
+    sv = df_add(sv, {__shfl_xor_sync(0xffffffffu, sv.hi, o), __shfl_xor_sync(0xffffffffu, sv.lo, o)});
+  }
+  if (lane == 0) {
+    red[0][0][w] = s2;
+    red[1][0][w] = s1.hi;
+    red[1][1][w] = s1.lo;
+    red[2][0][w] = sv.hi;
+    red[2][1][w] = sv.lo;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int q = 0; q < 8; ++q) {
+      a += red[0][0][q];
+      b += static_cast<double>(red[1][0][q]) + red[1][1][q];
+      c += static_cast<double>(red[2][0][q]) + red[2][1][q];
+    }
     atomicAdd(&sums[0], a);
     atomicAdd(&sums[1], b);
     atomicAdd(&sums[2], c);
@@ -375,55 +442,29 @@ struct BRows {
   const float *ah, *al, *ch, *cl, *wh, *wl;
 };
 
-// acc += coef * (x - y) with float pairs; acc stays unnormalised (hi, lo)
-__device__ __forceinline__ void acc_flux(df& acc, float ch, float cl, df x, df y) {
-  df d = two_sum(x.hi, -y.hi);
-  d.lo += x.lo - y.lo;
-  const float pr = ch * d.hi;
-  float pe = fmaf(ch, d.hi, -pr);
-  pe = fmaf(ch, d.lo, pe);
-  pe = fmaf(cl, d.hi, pe);
-  const df t = two_sum(acc.hi, pr);
-  acc.hi = t.hi;
-  acc.lo += t.lo + pe;
-}
-// acc += coef * x
-__device__ __forceinline__ void acc_mul(df& acc, float ch, float cl, df x) {
-  const float pr = ch * x.hi;
-  float pe = fmaf(ch, x.hi, -pr);
-  pe = fmaf(ch, x.lo, pe);
-  pe = fmaf(cl, x.hi, pe);
-  const df t = two_sum(acc.hi, pr);
-  acc.hi = t.hi;
-  acc.lo += t.lo + pe;
-}
-
-__device__ __forceinline__ df ld_df(const float* __restrict__ h, const float* __restrict__ l, long long i) {
-  return {h[i], l[i]};
-}
-
 // r = (f - fshift) - alpha phi - beta L phi in float-pair arithmetic, written
-// to R (operand format, rows of ldx); sum r^2 -> sums[0] and, for a singular
-// problem, sum vol*phi -> sums[1].  Block (32, 4) over (i, j); blockIdx.z picks
-// a segment of kseg planes that the thread marches through.
+// to R (operand format, rows of ldx), and sum r^2 -> sums[0].  Block (32, 4)
+// over (i, j); blockIdx.z picks a segment of kseg planes that the thread
+// marches through with pointer increments (neighbour offsets are fixed per
+// thread; a neighbour past a non-periodic wall is the wrapped index and meets a
+// zero coefficient).
 template <int FMT, int HAS_ALPHA, int WX, int WY, int WZ>
 __global__ void __launch_bounds__(128)
 residual_df_kernel(int nx, int ny, int nz, int ldx, int kseg, const float* __restrict__ fh,
                    const float* __restrict__ fl, const float* __restrict__ ph,
                    const float* __restrict__ pl, void* r0, void* r1, BRows RX, BRows RY, BRows RZ,
-                   const float* __restrict__ gx, const float* __restrict__ gy,
-                   const float* __restrict__ gz, float alpha_h, float alpha_l,
-                   const double* __restrict__ fsums, double inv_vol, int singular, double* sums) {
+                   float alpha_h, float alpha_l, const double* __restrict__ fsums, double inv_vol,
+                   int singular, double* sums) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k0 = blockIdx.z * kseg;
   const int k1 = min(nz, k0 + kseg);
-  double s2 = 0.0, swp = 0.0;
+  float acc2 = 0.0f;
   if (i < nx && j < ny && k0 < nz) {
-    const long long sy = nx, sz = static_cast<long long>(nx) * ny;
-    const long long base = i + sy * j;
-    const int im = (i == 0) ? nx - 1 : i - 1, ip = (i == nx - 1) ? 0 : i + 1;
-    const int jm = (j == 0) ? ny - 1 : j - 1, jp = (j == ny - 1) ? 0 : j + 1;
+    const long long sz = static_cast<long long>(nx) * ny;
+    const long long base = i + static_cast<long long>(nx) * j;
+    const int dxm = (i == 0) ? nx - 1 : -1, dxp = (i == nx - 1) ? -(nx - 1) : 1;
+    const int dym = (j == 0) ? (ny - 1) * nx : -nx, dyp = (j == ny - 1) ? -(ny - 1) * nx : nx;
     const float axh = RX.ah[i], axl = RX.al[i], cxh = RX.ch[i], cxl = RX.cl[i];
     const float ayh = RY.ah[j], ayl = RY.al[j], cyh = RY.ch[j], cyl = RY.cl[j];
     df fshift = {0.0f, 0.0f};
@@ -432,17 +473,21 @@ residual_df_kernel(int nx, int ny, int nz, int ldx, int kseg, const float* __res
       const float chi = static_cast<float>(c);
       fshift = {chi, static_cast<float>(c - static_cast<double>(chi))};
     }
-    const df vxy = df_mul({gx[i], gx[nx + i]}, {gy[j], gy[ny + j]});
-    df pm = ld_df(ph, pl, base + sz * (k0 == 0 ? nz - 1 : k0 - 1));
-    df p0 = ld_df(ph, pl, base + sz * k0);
-    float acc2 = 0.0f;
-    df wp = {0.0f, 0.0f};
+    const float* hk = ph + base + sz * k0;
+    const float* lk = pl + base + sz * k0;
+    const float* fhk = fh + base + sz * k0;
+    const float* flk = fl + base + sz * k0;
+    const long long back = (k0 == 0) ? sz * (nz - 1) : -sz;
+    df pm = {hk[back], lk[back]};
+    df p0 = {hk[0], lk[0]};
+    long long ro = i + static_cast<long long>(ldx) * (j + static_cast<long long>(ny) * k0);
+    const long long rstep = static_cast<long long>(ldx) * ny;
     for (int k = k0; k < k1; ++k) {
-      const long long o = base + sz * k;
-      const df pp = ld_df(ph, pl, base + sz * ((k == nz - 1) ? 0 : k + 1));
-      const df xm = ld_df(ph, pl, im + sy * j + sz * k), xp = ld_df(ph, pl, ip + sy * j + sz * k);
-      const df ym = ld_df(ph, pl, i + sy * jm + sz * k), yp = ld_df(ph, pl, i + sy * jp + sz * k);
-      const df fv = ld_df(fh, fl, o);
+      const long long fwd = (k == nz - 1) ? -sz * (nz - 1) : sz;
+      const df pp = {hk[fwd], lk[fwd]};
+      const df xm = {hk[dxm], lk[dxm]}, xp = {hk[dxp], lk[dxp]};
+      const df ym = {hk[dym], lk[dym]}, yp = {hk[dyp], lk[dyp]};
+      const df fv = {*fhk, *flk};
       df acc = {0.0f, 0.0f};
       acc_flux(acc, axh, axl, xm, p0);
       acc_flux(acc, cxh, cxl, xp, p0);
@@ -454,48 +499,60 @@ residual_df_kernel(int nx, int ny, int nz, int ldx, int kseg, const float* __res
       if (WY) acc_mul(acc, -RY.wh[j], -RY.wl[j], p0);
       if (WZ) acc_mul(acc, -RZ.wh[k], -RZ.wl[k], p0);
       if (HAS_ALPHA) acc_mul(acc, alpha_h, alpha_l, p0);
-      // r = (f - fshift) - acc
       df r = two_sum(fv.hi, -fshift.hi);
       r.lo += fv.lo - fshift.lo;
       const df t = two_sum(r.hi, -acc.hi);
       const float rv = t.hi + (t.lo + (r.lo - acc.lo));
-      Elem<FMT>::store(r0, r1, i + static_cast<long long>(ldx) * (j + static_cast<long long>(ny) * k), rv);
+      Elem<FMT>::store(r0, r1, ro, rv);
       acc2 = fmaf(rv, rv, acc2);
-      if (singular) {
-        const df vp = df_mul(df_mul(vxy, {gz[k], gz[nz + k]}), p0);
-        const df t2 = two_sum(wp.hi, vp.hi);
-        wp.hi = t2.hi;
-        wp.lo += t2.lo + vp.lo;
-      }
       pm = p0;
       p0 = pp;
+      hk += sz;
+      lk += sz;
+      fhk += sz;
+      flk += sz;
+      ro += rstep;
     }
-    s2 = acc2;
-    swp = static_cast<double>(wp.hi) + wp.lo;
   }
-  s2 = warp_sum_d(s2);
-  swp = warp_sum_d(swp);
-  if ((threadIdx.x + blockDim.x * threadIdx.y) % 32 == 0) {
-    atomicAdd(&sums[0], s2);
-    if (singular) atomicAdd(&sums[1], swp);
-  }
+  double s2 = warp_sum_d(static_cast<double>(acc2));
+  if ((threadIdx.x + blockDim.x * threadIdx.y) % 32 == 0) atomicAdd(&sums[0], s2);
 }
 
-// sum of cell volume times phi (float pair) into *out, for the exact gauge
+// sum of cell volume times phi (float pair) into *out, for the exact gauge;
+// work items are 256-point chunks of x-lines (one division per item)
 __global__ void __launch_bounds__(256)
 wsum_df_kernel(int nx, int ny, int nz, const float* __restrict__ h, const float* __restrict__ l,
                const float* __restrict__ gx, const float* __restrict__ gy,
                const float* __restrict__ gz, double* out) {
-  const long long n = static_cast<long long>(nx) * ny * nz;
+  const int nbi = (nx + 255) / 256;
+  const long long items = static_cast<long long>(nbi) * ny * nz;
   df s = {0.0f, 0.0f};
-  for (long long o = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; o < n;
-       o += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const int i = static_cast<int>(o % nx);
-    const long long line = o / nx;
-    const int j = static_cast<int>(line % ny), k = static_cast<int>(line / ny);
-    const df vol = df_mul(df_mul({gx[i], gx[nx + i]}, {gy[j], gy[ny + j]}), {gz[k], gz[nz + k]});
-    s = df_add(s, df_mul(vol, {h[o], l[o]}));
+  constexpr int U = 4;
+  for (long long t0 = blockIdx.x; t0 < items; t0 += static_cast<long long>(U) * gridDim.x) {
+    float hh[U], ll[U];
+    long long line[U];
+    int ii[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long t = t0 + static_cast<long long>(u) * gridDim.x;
+      line[u] = t / nbi;
+      ii[u] = static_cast<int>(t % nbi) * 256 + threadIdx.x;
+      const bool ok = t < items && ii[u] < nx;
+      if (!ok) ii[u] = -1;
+      const long long o = ok ? ii[u] + static_cast<long long>(nx) * line[u] : 0;
+      hh[u] = ok ? h[o] : 0.0f;
+      ll[u] = ok ? l[o] : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = ii[u];
+      if (i < 0) continue;
+      const int j = static_cast<int>(line[u] % ny), k = static_cast<int>(line[u] / ny);
+      const df wline = df_mul({gy[j], gy[ny + j]}, {gz[k], gz[nz + k]});
+      acc_mul(s, wline.hi, wline.lo, df_mul({gx[i], gx[nx + i]}, {hh[u], ll[u]}));
+    }
   }
+  s = fast_two_sum(s.hi, s.lo);
   double v = static_cast<double>(s.hi) + s.lo;
   v = warp_sum_d(v);
   if (threadIdx.x % 32 == 0) atomicAdd(out, v);
@@ -508,10 +565,23 @@ __global__ void __launch_bounds__(256)
 df_to_f64_kernel(long long n, const float* __restrict__ h, const float* __restrict__ l,
                  const double* __restrict__ wsum, double inv_vol, double* out) {
   const df shift = df_from_double(wsum ? *wsum * inv_vol : 0.0);
-  for (long long o = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; o < n;
-       o += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const df x = df_sub({h[o], l[o]}, shift);
-    out[o] = f2d_int(x.hi) + f2d_int(x.lo);
+  constexpr int U = 4;
+  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+  for (long long o0 = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; o0 < n; o0 += U * stride) {
+    float hh[U], ll[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long o = o0 + u * stride;
+      hh[u] = o < n ? h[o] : 0.0f;
+      ll[u] = o < n ? l[o] : 0.0f;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long o = o0 + u * stride;
+      if (o >= n) break;
+      const df x = df_sub({hh[u], ll[u]}, shift);
+      out[o] = f2d_int(x.hi) + f2d_int(x.lo);
+    }
   }
 }
 
@@ -708,10 +778,11 @@ constexpr int kBig = 1 << 30;
 
 template <int FMT>
 cudaError_t launch_prepare(const tpt_plan_s* p, const double* f, const MixedWork& w, cudaStream_t s) {
-  const long long n = static_cast<long long>(p->n[0]) * p->n[1] * p->n[2];
+  const int nbi = (p->n[0] + 255) / 256;
+  const long long items = static_cast<long long>(nbi) * p->n[1] * p->n[2];
   note_launch(1);
-  prepare_kernel<FMT><<<grid_for(n, 256, p->dev), 256, 0, s>>>(
-      p->n[0], p->n[1], p->n[2], p->mixed.ldx, f, w.fh, w.fl, w.R[0], w.R[1], p->mixed.dfgeom[0],
+  prepare_kernel<FMT><<<grid_for(items * 256, 256, p->dev), 256, 0, s>>>(
+      p->n[0], p->n[1], p->n[2], p->mixed.ldx, nbi, f, w.fh, w.fl, w.R[0], w.R[1], p->mixed.dfgeom[0],
       p->mixed.dfgeom[1], p->mixed.dfgeom[2], w.scal + 5);
   return cudaGetLastError();
 }
@@ -778,8 +849,7 @@ cudaError_t launch_res(const tpt_plan_s* p, const MixedWork& w, cudaStream_t s) 
   residual_df_kernel<FMT, HA, WX, WY, WZ><<<grid, block, 0, s>>>(
       nx, ny, nz, p->mixed.ldx, kseg, w.fh, w.fl, w.ph, w.pl, w.R[0], w.R[1],
       rows_of(p->mixed.dfrows[0], nx), rows_of(p->mixed.dfrows[1], ny), rows_of(p->mixed.dfrows[2], nz),
-      p->mixed.dfgeom[0], p->mixed.dfgeom[1], p->mixed.dfgeom[2], ah, al, w.scal + 5, 1.0 / p->vol,
-      p->singular ? 1 : 0, w.scal + 1);
+      ah, al, w.scal + 5, 1.0 / p->vol, p->singular ? 1 : 0, w.scal + 1);
   return cudaGetLastError();
 }
 
@@ -860,19 +930,20 @@ int solve_fmt(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStrea
       if (cudaEventCreate(&e) != cudaSuccess) return TPT_ERR_CUDA;
   const int saved_timing = p->stage_timing;
   p->stage_timing = timing ? 1 : 0;
+  if (timing) cudaEventRecord(p->ev[8], s);
   MX_CUDA(cudaMemsetAsync(w.scal, 0, 16 * sizeof(double), s));
   MX_CUDA(launch_prepare<FMT>(p, f, w, s));
+  if (timing) cudaEventRecord(p->ev[9], s);
   const int corrections = 1 + p->max_refine;
   const bool adaptive = p->rtol > 0.0;
   const double np = static_cast<double>(npts(p));
   double h[16] = {0.0};
   double rel = -1.0;
   int iters = 0, status = TPT_OK;
-  bool converged = false, residual_after_last = false;
+  bool converged = false;
   for (;;) {
     MX_TRY(correction<FMT>(p, w, iters > 0, s));
     ++iters;
-    residual_after_last = false;
     const bool need_residual = iters < corrections || adaptive || info;
     if (!need_residual) {
       if (timing) {
@@ -883,7 +954,6 @@ int solve_fmt(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStrea
     }
     MX_CUDA(cudaMemsetAsync(w.scal + 1, 0, 2 * sizeof(double), s));
     MX_CUDA(launch_residual<FMT>(p, w, s));
-    residual_after_last = true;
     if (timing) {
       cudaEventRecord(p->ev[6], s);
       MX_CUDA(cudaEventSynchronize(p->ev[6]));
@@ -906,7 +976,8 @@ int solve_fmt(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStrea
     if (iters >= corrections) break;
   }
   const long long n = static_cast<long long>(np);
-  if (p->singular && !residual_after_last) {   // the residual pass already summed vol*phi
+  if (timing) cudaEventRecord(p->ev[10], s);
+  if (p->singular) {
     MX_CUDA(cudaMemsetAsync(w.scal + 2, 0, sizeof(double), s));
     note_launch(1);
     wsum_df_kernel<<<grid_for(n, 256, p->dev), 256, 0, s>>>(p->n[0], p->n[1], p->n[2], w.ph, w.pl,
@@ -918,6 +989,14 @@ int solve_fmt(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStrea
   df_to_f64_kernel<<<grid_for(n, 256, p->dev), 256, 0, s>>>(n, w.ph, w.pl, p->singular ? w.scal + 2 : nullptr,
                                                             1.0 / p->vol, phi);
   MX_CUDA(cudaGetLastError());
+  if (timing) {
+    cudaEventRecord(p->ev[11], s);
+    MX_CUDA(cudaEventSynchronize(p->ev[11]));
+    float t = 0.0f;
+    if (cudaEventElapsedTime(&t, p->ev[8], p->ev[9]) == cudaSuccess) ms[0] = t;
+    if (cudaEventElapsedTime(&t, p->ev[10], p->ev[11]) == cudaSuccess) ms[7] = t;
+    cudaGetLastError();
+  }
   if (adaptive && !converged) status = TPT_ERR_NOT_CONVERGED;
   if (info) {
     if (!adaptive) {

@@ -114,7 +114,7 @@ struct tpt_plan_s {
   double vol = 1.0;               // domain volume Lx Ly Lz
   tpt::MixedTables mixed;
   int stage_timing = 0;           // record per-stage CUDA events in tpt_solve
-  cudaEvent_t ev[8] = {};         // stage boundaries (created on first use)
+  cudaEvent_t ev[12] = {};        // stage boundaries (created on first use)
   std::vector<void*> allocs;      // every device allocation owned by the plan
 };
 
