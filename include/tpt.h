@@ -224,6 +224,77 @@ int tpt_kernel_launches(unsigned long long* count);
  * correction).  enable = 0 turns it off.                                    */
 int tpt_set_stage_timing(tpt_plan plan, int enable);
 
+/* Change rtol and max_refine of an existing plan (same meaning and limits as
+ * in tpt_desc).  Not to be called while a solve on this plan is in flight.  */
+int tpt_set_refinement(tpt_plan plan, double rtol, int max_refine);
+
+/* ---- transform tiles ---------------------------------------------------- */
+/* Tile autotuner for the transform GEMMs of a TPT_PREC_MIXED_* plan (the
+ * forward/inverse eigenbasis projections of Algorithm 1 steps 1, 3, 7, 9):
+ * times the four GEMMs of one correction (x forward, y forward, y inverse,
+ * x inverse) over the column-tile widths 32, 64, 128, 256 that do not exceed
+ * the GEMM's column count rounded up to a power of two, and keeps the fastest
+ * per stage for later solves.  work_dev as for tpt_solve (its contents are
+ * overwritten); synchronises `stream`.  tiles_out (4 ints, may be NULL)
+ * receives the chosen widths.  A float64 plan is left unchanged and reports
+ * zeros.  Errors: INVALID_ARG, CUDA, TIMEOUT.                              */
+int tpt_plan_autotune(tpt_plan plan, void* work_dev, void* stream, int* tiles_out);
+
+/* Set the four column-tile widths directly (0 = default: the smallest of
+ * 32..256 covering the column count), e.g. to reuse a tuned choice on a plan
+ * of the same shape.  Each width 0, 32, 64, 128 or 256, else INVALID_ARG.
+ * Not to be called while a solve on this plan is in flight.                */
+int tpt_plan_set_tiles(tpt_plan plan, const int* tiles);
+int tpt_plan_get_tiles(tpt_plan plan, int* tiles_out);
+
+/* ---- batched solves ------------------------------------------------------ */
+/* A batch owns `count` plans of possibly different sizes and coefficients on
+ * one device (Sec. 2.2: each instance is an independent tensor-product-Thomas
+ * solve).  tpt_batch_solve runs every instance with a fixed 1 + max_refine
+ * corrections and a final residual (rtol only classifies the result) as one
+ * CUDA graph: the instances are spread over `nstreams` capture streams
+ * (longest first onto the least-loaded stream; 0 picks min(count, 8)) so
+ * that independent instances overlap on the device, and the whole batch is
+ * replayed with one graph launch.  The graph is captured on the first call
+ * and again whenever a buffer pointer or a plan's coefficients or tiles
+ * change; a capturing call runs the batch eagerly first.                   */
+typedef struct tpt_batch_s* tpt_batch;
+
+int tpt_batch_create(const tpt_desc* descs, int count, int cuda_device, int nstreams, tpt_batch* out);
+
+/* Device workspace of one tpt_batch_solve (256-byte aligned): per capture
+ * stream the largest tpt_workspace_bytes of its instances.                 */
+int tpt_batch_workspace_bytes(tpt_batch batch, size_t* bytes);
+
+/* Borrowed handle of instance i (owned by the batch; valid until
+ * tpt_batch_destroy).  Changing its coefficients or tiles makes the next
+ * tpt_batch_solve recapture.                                                */
+int tpt_batch_plan(tpt_batch batch, int i, tpt_plan* out);
+
+/* Autotune the transform tiles of every distinct (size, precision) in the
+ * batch once and share the choice among instances of that shape.            */
+int tpt_batch_autotune(tpt_batch batch, void* work_dev, void* stream);
+
+/* Solve every instance: f_dev[i] and phi_dev[i] hold instance i's field
+ * (phi_dev[i] may equal f_dev[i]; distinct instances must not overlap).
+ * work_dev holds tpt_batch_workspace_bytes() bytes.  Asynchronous on
+ * `stream` when infos and statuses are both NULL; otherwise the call
+ * synchronises `stream` and fills infos[i] (iters, rel_residual,
+ * compat_defect; ms_stage zero) and statuses[i] (OK, NOT_CONVERGED against
+ * the instance's rtol when rtol > 0, NONFINITE, TIMEOUT).  Returns the
+ * first failing status of an instance, else OK; INVALID_ARG, CUDA.        */
+int tpt_batch_solve(tpt_batch batch, const double* const* f_dev, double* const* phi_dev, void* work_dev,
+                    void* stream, tpt_info* infos, int* statuses);
+
+/* Per-instance reports of the last tpt_batch_solve, after its stream has
+ * been synchronised by the caller.  Returns as tpt_batch_solve does.        */
+int tpt_batch_infos(tpt_batch batch, tpt_info* infos, int* statuses);
+
+/* Kernels one graph replay launches (0 before the first capture).           */
+int tpt_batch_launches(tpt_batch batch, unsigned long long* count);
+
+int tpt_batch_destroy(tpt_batch batch);
+
 /* ---- grid helper -------------------------------------------------------- */
 /* Cell widths and centre spacings of an n-cell grid on [0, L] whose faces are
  * x(k/n), k = 0..n, of Eq. (tanh_stretching) (Sec. 4.1); stretch = 0 is the

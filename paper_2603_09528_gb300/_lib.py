@@ -76,6 +76,19 @@ SIGNATURES = [
     ("tpt_grid_tanh", C.c_int, [C.c_int, C.c_double, C.c_double, _dp, _dp]),
     ("tpt_kernel_launches", C.c_int, [C.POINTER(C.c_ulonglong)]),
     ("tpt_set_stage_timing", C.c_int, [C.c_void_p, C.c_int]),
+    ("tpt_set_refinement", C.c_int, [C.c_void_p, C.c_double, C.c_int]),
+    ("tpt_plan_autotune", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]),
+    ("tpt_plan_set_tiles", C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    ("tpt_plan_get_tiles", C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    ("tpt_batch_create", C.c_int, [C.POINTER(tpt_desc), C.c_int, C.c_int, C.c_int, C.POINTER(C.c_void_p)]),
+    ("tpt_batch_workspace_bytes", C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
+    ("tpt_batch_plan", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
+    ("tpt_batch_autotune", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    ("tpt_batch_solve", C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_void_p,
+                                  C.c_void_p, C.POINTER(tpt_info), C.POINTER(C.c_int)]),
+    ("tpt_batch_infos", C.c_int, [C.c_void_p, C.POINTER(tpt_info), C.POINTER(C.c_int)]),
+    ("tpt_batch_launches", C.c_int, [C.c_void_p, C.POINTER(C.c_ulonglong)]),
+    ("tpt_batch_destroy", C.c_int, [C.c_void_p]),
 ]
 
 LIB_PATH = _build.LIB

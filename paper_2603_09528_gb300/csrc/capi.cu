@@ -180,6 +180,79 @@ void CUDART_CB fill_info(void* arg) {
   delete cb;
 }
 
+// The float64 solve of tpt_solve(); enqueue_only runs 1 + max_refine
+// corrections and a final residual with no host synchronisation (capturable
+// in a CUDA graph) and leaves the sums in the workspace scalars.
+int fp64_solve(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStream_t s, tpt_info* info,
+               bool enqueue_only) {
+  const size_t rb = region_bytes(p);
+  char* w = static_cast<char*>(work);
+  double* ds = reinterpret_cast<double*>(w);
+  w += 256;
+  double* r = reinterpret_cast<double*>(w);
+  double* t1 = reinterpret_cast<double*>(w + rb);
+  double* t2 = reinterpret_cast<double*>(w + 2 * rb);
+  double* fcopy = reinterpret_cast<double*>(w + 3 * rb);
+  const int corrections = 1 + p->max_refine;
+  const bool adaptive = p->rtol > 0.0 && !enqueue_only;
+  const double* fu = f;
+  if (phi == f && (corrections > 1 || adaptive || info || enqueue_only)) {   // f is needed after phi is written
+    TPT_CUDA(cudaMemcpyAsync(fcopy, f, tpt::npts(p) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    fu = fcopy;
+  }
+  TPT_CUDA(cudaMemsetAsync(ds, 0, 16 * sizeof(double), s));
+  TPT_CUDA(tpt::field_sums(p, fu, ds + 5, s));
+  TPT_TRY(inner_fp64(p, fu, phi, false, t1, t2, ds + 4, s));
+  int iters = 1;
+  const double np = static_cast<double>(tpt::npts(p));
+  double fn2 = -1.0, rel = -1.0;
+  double h[kSlot] = {0.0};
+  auto read_residual = [&]() -> int {
+    TPT_CUDA(cudaMemcpyAsync(h, ds, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TPT_CUDA(cudaStreamSynchronize(s));
+    fn2 = projected_norm2(h[5], h[6], h[7], np, p->vol, p->singular);
+    if (!std::isfinite(h[1]) || !std::isfinite(fn2)) return TPT_ERR_NONFINITE;
+    rel = (fn2 > 0.0) ? std::sqrt(h[1] / fn2) : std::sqrt(h[1]);
+    return TPT_OK;
+  };
+  int status = TPT_OK;
+  bool converged = false;
+  for (;;) {
+    const bool need_residual = (iters < corrections) || adaptive || info || enqueue_only;
+    if (!need_residual) break;
+    TPT_CUDA(cudaMemsetAsync(ds + 1, 0, 3 * sizeof(double), s));
+    TPT_CUDA(tpt::residual_fp64(p, fu, phi, r, ds + 1, p->singular ? ds + 4 : nullptr, s));
+    if (adaptive) {
+      TPT_TRY(read_residual());
+      if (rel <= p->rtol) {
+        converged = true;
+        break;
+      }
+    }
+    if (iters >= corrections) break;
+    TPT_TRY(inner_fp64(p, r, phi, true, t1, t2, ds, s));
+    ++iters;
+  }
+  if (adaptive && !converged) status = TPT_ERR_NOT_CONVERGED;
+  if (info && !enqueue_only) {
+    if (adaptive) {
+      info->iters = iters;
+      info->rel_residual = rel;
+      info->compat_defect = h[4];
+      for (float& t : info->ms_stage) t = 0.0f;
+    } else {
+      std::memset(info, 0, sizeof(*info));
+      double* slot = p->h_ring + static_cast<size_t>(p->ring_next) * kSlot;
+      p->ring_next = (p->ring_next + 1) % kRingSlots;
+      TPT_CUDA(cudaMemcpyAsync(slot, ds, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      InfoCallback* cb = new (std::nothrow) InfoCallback{info, slot, np, p->vol, iters, p->singular};
+      if (!cb) return TPT_ERR_OOM;
+      TPT_CUDA(cudaLaunchHostFunc(s, fill_info, cb));
+    }
+  }
+  return status;
+}
+
 }  // namespace
 
 namespace tpt {
@@ -190,6 +263,29 @@ namespace {
 std::atomic<unsigned long long> g_launches{0};
 }
 void note_launch(unsigned long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+void forget_launches(unsigned long long k) { g_launches.fetch_sub(k, std::memory_order_relaxed); }
+
+int solve_enqueue(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStream_t s) {
+  if (p->precision != TPT_PREC_FP64) return mixed_enqueue(p, f, phi, work, s);
+  return fp64_solve(p, f, phi, work, s, nullptr, true);
+}
+
+int solve_info(const tpt_plan_s* p, const double* h, tpt_info* info) {
+  if (p->precision != TPT_PREC_FP64) return mixed_info(p, h, info);
+  const double np = static_cast<double>(npts(p));
+  const double fn2 = projected_norm2(h[5], h[6], h[7], np, p->vol, p->singular);
+  const double rel = (fn2 > 0.0) ? std::sqrt(h[1] / fn2) : std::sqrt(h[1]);
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->iters = 1 + p->max_refine;
+    info->rel_residual = rel;
+    info->compat_defect = h[4];
+  }
+  if (!std::isfinite(rel)) return TPT_ERR_NONFINITE;
+  if (p->rtol > 0.0 && !(rel <= p->rtol)) return TPT_ERR_NOT_CONVERGED;
+  return TPT_OK;
+}
 }  // namespace tpt
 
 extern "C" {
@@ -336,12 +432,50 @@ int tpt_set_coefficients(tpt_plan p, double alpha, double beta) {
     return TPT_ERR_INVALID_ARG;
   p->alpha = alpha;
   p->beta = beta;
+  ++p->generation;
   p->singular = (alpha == 0.0) && p->dir[0].has_null() && p->dir[1].has_null() &&
                 p->dir[2].has_null();
   if (p->precision != TPT_PREC_FP64 && p->dev >= 0 && p->mixed.dfrows[0]) {
     DeviceGuard guard(p->dev);
     return tpt::mixed_set_beta(p);
   }
+  return TPT_OK;
+}
+
+int tpt_set_refinement(tpt_plan p, double rtol, int max_refine) {
+  if (!p || !std::isfinite(rtol) || rtol < 0.0 || max_refine < 0 || max_refine > 1000)
+    return TPT_ERR_INVALID_ARG;
+  p->rtol = rtol;
+  p->max_refine = max_refine;
+  ++p->generation;
+  return TPT_OK;
+}
+
+int tpt_plan_autotune(tpt_plan p, void* work, void* stream, int* tiles_out) {
+  if (!on_device(p) || !work || reinterpret_cast<uintptr_t>(work) % 256 != 0) return TPT_ERR_INVALID_ARG;
+  DeviceGuard guard(p->dev);
+  const int st = tpt::autotune_gemms(p, work, static_cast<cudaStream_t>(stream));
+  if (tiles_out) tpt_plan_get_tiles(p, tiles_out);
+  return st;
+}
+
+int tpt_plan_set_tiles(tpt_plan p, const int* tiles) {
+  if (!p || !tiles) return TPT_ERR_INVALID_ARG;
+  for (int i = 0; i < 4; ++i)
+    if (tiles[i] != 0 && tiles[i] != 32 && tiles[i] != 64 && tiles[i] != 128 && tiles[i] != 256)
+      return TPT_ERR_INVALID_ARG;
+  if (p->precision == TPT_PREC_FP64) return TPT_OK;
+  for (int i = 0; i < 4; ++i) {
+    p->mixed.gemm_bn[i] = tiles[i];
+    p->mixed.gemm_ctas[i] = 0;
+  }
+  ++p->generation;
+  return TPT_OK;
+}
+
+int tpt_plan_get_tiles(tpt_plan p, int* tiles_out) {
+  if (!p || !tiles_out) return TPT_ERR_INVALID_ARG;
+  for (int i = 0; i < 4; ++i) tiles_out[i] = (p->precision == TPT_PREC_FP64) ? 0 : p->mixed.gemm_bn[i];
   return TPT_OK;
 }
 
@@ -357,72 +491,7 @@ int tpt_solve(tpt_plan p, const double* f, double* phi, void* work, void* stream
   DeviceGuard guard(p->dev);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (p->precision != TPT_PREC_FP64) return tpt::mixed_solve(p, f, phi, work, s, info);
-  const size_t rb = region_bytes(p);
-  char* w = static_cast<char*>(work);
-  double* ds = reinterpret_cast<double*>(w);
-  w += 256;
-  double* r = reinterpret_cast<double*>(w);
-  double* t1 = reinterpret_cast<double*>(w + rb);
-  double* t2 = reinterpret_cast<double*>(w + 2 * rb);
-  double* fcopy = reinterpret_cast<double*>(w + 3 * rb);
-  const int corrections = 1 + p->max_refine;
-  const bool adaptive = p->rtol > 0.0;
-  const double* fu = f;
-  if (phi == f && (corrections > 1 || adaptive || info)) {   // f is needed after phi is written
-    TPT_CUDA(cudaMemcpyAsync(fcopy, f, tpt::npts(p) * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    fu = fcopy;
-  }
-  TPT_CUDA(cudaMemsetAsync(ds, 0, 16 * sizeof(double), s));
-  TPT_CUDA(tpt::field_sums(p, fu, ds + 5, s));
-  TPT_TRY(inner_fp64(p, fu, phi, false, t1, t2, ds + 4, s));
-  int iters = 1;
-  const double np = static_cast<double>(tpt::npts(p));
-  double fn2 = -1.0, rel = -1.0;
-  double h[kSlot] = {0.0};
-  auto read_residual = [&]() -> int {
-    TPT_CUDA(cudaMemcpyAsync(h, ds, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
-    TPT_CUDA(cudaStreamSynchronize(s));
-    fn2 = projected_norm2(h[5], h[6], h[7], np, p->vol, p->singular);
-    if (!std::isfinite(h[1]) || !std::isfinite(fn2)) return TPT_ERR_NONFINITE;
-    rel = (fn2 > 0.0) ? std::sqrt(h[1] / fn2) : std::sqrt(h[1]);
-    return TPT_OK;
-  };
-  int status = TPT_OK;
-  bool converged = false;
-  for (;;) {
-    const bool need_residual = (iters < corrections) || adaptive || info;
-    if (!need_residual) break;
-    TPT_CUDA(cudaMemsetAsync(ds + 1, 0, 3 * sizeof(double), s));
-    TPT_CUDA(tpt::residual_fp64(p, fu, phi, r, ds + 1, p->singular ? ds + 4 : nullptr, s));
-    if (adaptive) {
-      TPT_TRY(read_residual());
-      if (rel <= p->rtol) {
-        converged = true;
-        break;
-      }
-    }
-    if (iters >= corrections) break;
-    TPT_TRY(inner_fp64(p, r, phi, true, t1, t2, ds, s));
-    ++iters;
-  }
-  if (adaptive && !converged) status = TPT_ERR_NOT_CONVERGED;
-  if (info) {
-    if (adaptive) {
-      info->iters = iters;
-      info->rel_residual = rel;
-      info->compat_defect = h[4];
-      for (float& t : info->ms_stage) t = 0.0f;
-    } else {
-      std::memset(info, 0, sizeof(*info));
-      double* slot = p->h_ring + static_cast<size_t>(p->ring_next) * kSlot;
-      p->ring_next = (p->ring_next + 1) % kRingSlots;
-      TPT_CUDA(cudaMemcpyAsync(slot, ds, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
-      InfoCallback* cb = new (std::nothrow) InfoCallback{info, slot, np, p->vol, iters, p->singular};
-      if (!cb) return TPT_ERR_OOM;
-      TPT_CUDA(cudaLaunchHostFunc(s, fill_info, cb));
-    }
-  }
-  return status;
+  return fp64_solve(p, f, phi, work, s, info, false);
 }
 
 int tpt_solve_host(tpt_plan p, const double* f_host, double* phi_host, double* f_dev,

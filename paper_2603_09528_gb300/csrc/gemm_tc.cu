@@ -352,7 +352,8 @@ cudaError_t launch(const Operand& A, const Operand& B, const GemmOut& g, cudaStr
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const long long ctas = tiles < sms ? tiles : sms;   // persistent: one CTA per SM
+  const long long cap = (g.max_ctas > 0 && g.max_ctas < sms) ? g.max_ctas : sms;
+  const long long ctas = tiles < cap ? tiles : cap;   // persistent: one CTA per SM
   note_launch(1);
   kern<<<static_cast<unsigned>(ctas), kThreads, C::SMEM, s>>>(m[0], m[1], m[2], m[3], g);
   return cudaGetLastError();
@@ -360,10 +361,13 @@ cudaError_t launch(const Operand& A, const Operand& B, const GemmOut& g, cudaStr
 
 template <int KIND, int NPL, int OUT>
 cudaError_t launch_bn(const Operand& A, const Operand& B, const GemmOut& g, cudaStream_t s) {
-  if (g.N <= 32) return launch<KIND, NPL, 32, OUT>(A, B, g, s);
-  if (g.N <= 64) return launch<KIND, NPL, 64, OUT>(A, B, g, s);
-  if (g.N <= 128) return launch<KIND, NPL, 128, OUT>(A, B, g, s);
-  return launch<KIND, NPL, 256, OUT>(A, B, g, s);
+  switch (g.bn ? g.bn : default_bn(g.N)) {
+    case 32: return launch<KIND, NPL, 32, OUT>(A, B, g, s);
+    case 64: return launch<KIND, NPL, 64, OUT>(A, B, g, s);
+    case 128: return launch<KIND, NPL, 128, OUT>(A, B, g, s);
+    case 256: return launch<KIND, NPL, 256, OUT>(A, B, g, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 template <int KIND, int NPL>
@@ -379,6 +383,8 @@ cudaError_t launch_out(const Operand& A, const Operand& B, const GemmOut& g, cud
 }
 
 }  // namespace
+
+int default_bn(int N) { return N <= 32 ? 32 : N <= 64 ? 64 : N <= 128 ? 128 : 256; }
 
 cudaError_t gemm(int kind, int nplanes, const Operand& A, const Operand& B, const GemmOut& g,
                  cudaStream_t s) {

@@ -693,11 +693,10 @@ struct MixedWork {
   void* R[2];
   void* A[2];
   void* B[2];
-  float* scratch;
 };
 
 struct MixedSizes {
-  size_t nf, nr, nab, nscr, eb, np;
+  size_t nf, nr, nab, eb, np;
 };
 
 MixedSizes sizes_of(const tpt_plan_s* p) {
@@ -707,7 +706,6 @@ MixedSizes sizes_of(const tpt_plan_s* p) {
   s.nf = nx * ny * nz;
   s.nr = static_cast<size_t>(m.ldx) * ny * nz;
   s.nab = std::max(static_cast<size_t>(m.ldy) * nx, static_cast<size_t>(m.ldx) * ny) * nz;
-  s.nscr = static_cast<size_t>(m.ldy) * nx * nz;
   s.eb = elem_bytes(m.fmt);
   s.np = nplanes(m.fmt);
   return s;
@@ -738,7 +736,6 @@ MixedWork carve(const tpt_plan_s* p, void* work) {
     mw.B[pl] = (pl < static_cast<int>(z.np)) ? static_cast<void*>(w) : nullptr;
     if (pl < static_cast<int>(z.np)) w += align256(z.nab * z.eb);
   }
-  mw.scratch = reinterpret_cast<float*>(w);
   return mw;
 }
 
@@ -771,6 +768,13 @@ tc::GemmOut gout(int M, int N, int K, int rm, long long sm, long long sn, void* 
   g.accumulate = acc;
   g.n_fastest = n_fastest;
   g.err = err;
+  return g;
+}
+
+// Applies the plan's tile choice for transform stage i (0..3).
+tc::GemmOut tuned(tc::GemmOut g, const MixedTables& m, int i) {
+  g.bn = m.gemm_bn[i];
+  g.max_ctas = m.gemm_ctas[i];
   return g;
 }
 
@@ -867,39 +871,63 @@ cudaError_t launch_residual(const tpt_plan_s* p, const MixedWork& w, cudaStream_
   return launch_res<FMT, 0, 1, 1, 1>(p, w, s);
 }
 
+// Operands and output of transform stage i of one correction (Algorithm 1
+// steps 1, 3, 7, 9): 0 x forward, 1 y forward, 2 y inverse, 3 x inverse.
+struct StageGemm {
+  tc::Operand a, b;
+  tc::GemmOut g;
+};
+
+StageGemm stage_gemm(const tpt_plan_s* p, const MixedWork& w, int i, bool accumulate) {
+  const MixedTables& m = p->mixed;
+  const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
+  const int om = out_mode(m.fmt);
+  int* err = reinterpret_cast<int*>(w.scal + 15);
+  StageGemm t;
+  switch (i) {
+    case 0:   // A = R rows (j,k), B = Q_x^{-1} rows p -> T1 (j, p, k)
+      t.a = operand(w.R, ny * nz, nx, m.ldx);
+      t.b = operand(m.q[0][0], nx, nx, m.ldx);
+      t.g = gout(ny * nz, nx, nx, ny, static_cast<long long>(m.ldy) * nx, m.ldy, w.A[0], w.A[1], om, 0, 1, err);
+      break;
+    case 1:   // A = Q_y^{-1} rows q, B = T1 rows (p,k) -> T2 (q, p, k)
+      t.a = operand(m.q[1][0], ny, ny, m.ldy);
+      t.b = operand(w.A, nx * nz, ny, m.ldy);
+      t.g = gout(ny, nx * nz, ny, kBig, 0, m.ldy, w.B[0], w.B[1], om, 0, 0, err);
+      break;
+    case 2:   // A = T3 rows (p,k), B = Q_y rows j -> T4 (p, j, k)
+      t.a = operand(w.B, nx * nz, ny, m.ldy);
+      t.b = operand(m.q[1][1], ny, ny, m.ldy);
+      t.g = gout(nx * nz, ny, ny, nx, static_cast<long long>(m.ldx) * ny, m.ldx, w.A[0], w.A[1], om, 0, 1, err);
+      break;
+    default:  // A = Q_x rows i, B = T4 rows (j,k) -> phi (float pair) (+)= result
+      t.a = operand(m.q[0][1], nx, nx, m.ldx);
+      t.b = operand(w.A, ny * nz, nx, m.ldx);
+      t.g = gout(nx, ny * nz, nx, kBig, 0, nx, w.ph, w.pl, tc::kOutDF, accumulate ? 1 : 0, 0, err);
+      break;
+  }
+  return t;
+}
+
 template <int FMT>
 int correction(tpt_plan_s* p, const MixedWork& w, bool accumulate, cudaStream_t s) {
   auto mark = [&](int i) {
     if (p->stage_timing) cudaEventRecord(p->ev[i], s);
   };
+  auto xform = [&](int i) {
+    const StageGemm t = stage_gemm(p, w, i, accumulate);
+    return tc::gemm(kind_of(FMT), nplanes(FMT), t.a, t.b, tuned(t.g, p->mixed, i), s);
+  };
   mark(0);
-  const MixedTables& m = p->mixed;
-  const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
-  const int kind = kind_of(FMT), npl = nplanes(FMT), om = out_mode(FMT);
-  int* err = reinterpret_cast<int*>(w.scal + 15);
-  // step 2.1: x forward.  A = R rows (j,k), B = Q_x^{-1} rows p -> T1 (j, p, k)
-  MX_CUDA(tc::gemm(kind, npl, operand(w.R, ny * nz, nx, m.ldx), operand(m.q[0][0], nx, nx, m.ldx),
-                   gout(ny * nz, nx, nx, ny, static_cast<long long>(m.ldy) * nx, m.ldy, w.A[0], w.A[1], om,
-                        0, 1, err),
-                   s));
+  MX_CUDA(xform(0));                    // step 2.1: x forward
   mark(1);
-  // step 2.2: y forward.  A = Q_y^{-1} rows q, B = T1 rows (p,k) -> T2 (q, p, k)
-  MX_CUDA(tc::gemm(kind, npl, operand(m.q[1][0], ny, ny, m.ldy), operand(w.A, nx * nz, ny, m.ldy),
-                   gout(ny, nx * nz, ny, kBig, 0, m.ldy, w.B[0], w.B[1], om, 0, 0, err), s));
+  MX_CUDA(xform(1));                    // step 2.2: y forward
   mark(2);
-  // step 2.3: modal Thomas along z, in place on T2
-  MX_CUDA(launch_thomas<FMT>(p, w, s));
+  MX_CUDA(launch_thomas<FMT>(p, w, s)); // step 2.3: modal Thomas along z, in place on T2
   mark(3);
-  // step 2.4: y inverse.  A = T3 rows (p,k), B = Q_y rows j -> T4 (p, j, k)
-  MX_CUDA(tc::gemm(kind, npl, operand(w.B, nx * nz, ny, m.ldy), operand(m.q[1][1], ny, ny, m.ldy),
-                   gout(nx * nz, ny, ny, nx, static_cast<long long>(m.ldx) * ny, m.ldx, w.A[0], w.A[1], om,
-                        0, 1, err),
-                   s));
+  MX_CUDA(xform(2));                    // step 2.4: y inverse
   mark(4);
-  // step 2.5: x inverse.  A = Q_x rows i, B = T4 rows (j,k) -> phi (float pair) (+)= result
-  MX_CUDA(tc::gemm(kind, npl, operand(m.q[0][1], nx, nx, m.ldx), operand(w.A, ny * nz, nx, m.ldx),
-                   gout(nx, ny * nz, nx, kBig, 0, nx, w.ph, w.pl, tc::kOutDF, accumulate ? 1 : 0, 0, err),
-                   s));
+  MX_CUDA(xform(3));                    // step 2.5: x inverse
   mark(5);
   return TPT_OK;
 }
@@ -920,11 +948,15 @@ void add_stage_times(tpt_plan_s* p, float* ms, bool with_residual) {
   }
 }
 
+// enqueue_only: fixed 1 + max_refine corrections and a final residual, with
+// no host synchronisation (capturable in a CUDA graph); the sums stay in the
+// workspace scalars for mixed_info().
 template <int FMT>
-int solve_fmt(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStream_t s, tpt_info* info) {
+int solve_fmt(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStream_t s, tpt_info* info,
+              bool enqueue_only) {
   const MixedWork w = carve(p, work);
   float ms[8] = {0.0f};
-  const bool timing = p->stage_timing && info;
+  const bool timing = p->stage_timing && info && !enqueue_only;
   if (timing && !p->ev[0])
     for (cudaEvent_t& e : p->ev)
       if (cudaEventCreate(&e) != cudaSuccess) return TPT_ERR_CUDA;
@@ -935,7 +967,7 @@ int solve_fmt(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStrea
   MX_CUDA(launch_prepare<FMT>(p, f, w, s));
   if (timing) cudaEventRecord(p->ev[9], s);
   const int corrections = 1 + p->max_refine;
-  const bool adaptive = p->rtol > 0.0;
+  const bool adaptive = p->rtol > 0.0 && !enqueue_only;
   const double np = static_cast<double>(npts(p));
   double h[16] = {0.0};
   double rel = -1.0;
@@ -944,7 +976,7 @@ int solve_fmt(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStrea
   for (;;) {
     MX_TRY(correction<FMT>(p, w, iters > 0, s));
     ++iters;
-    const bool need_residual = iters < corrections || adaptive || info;
+    const bool need_residual = iters < corrections || adaptive || info || enqueue_only;
     if (!need_residual) {
       if (timing) {
         MX_CUDA(cudaEventSynchronize(p->ev[5]));
@@ -998,7 +1030,7 @@ int solve_fmt(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStrea
     cudaGetLastError();
   }
   if (adaptive && !converged) status = TPT_ERR_NOT_CONVERGED;
-  if (info) {
+  if (info && !enqueue_only) {
     if (!adaptive) {
       MX_CUDA(cudaMemcpyAsync(h, w.scal, 16 * sizeof(double), cudaMemcpyDeviceToHost, s));
       MX_CUDA(cudaStreamSynchronize(s));
@@ -1123,16 +1155,90 @@ size_t mixed_workspace_bytes(const tpt_plan_s* p) {
   b += 4 * align256(z.nf * sizeof(float));
   b += z.np * align256(z.nr * z.eb);
   b += 2 * z.np * align256(z.nab * z.eb);
-  b += align256(z.nscr * sizeof(float));
   return b;
 }
 
 int mixed_solve(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStream_t s, tpt_info* info) {
   switch (p->mixed.fmt) {
-    case kFmtSplit: return solve_fmt<kFmtSplit>(p, f, phi, work, s, info);
-    case kFmtBF16: return solve_fmt<kFmtBF16>(p, f, phi, work, s, info);
-    default: return solve_fmt<kFmtF32>(p, f, phi, work, s, info);
+    case kFmtSplit: return solve_fmt<kFmtSplit>(p, f, phi, work, s, info, false);
+    case kFmtBF16: return solve_fmt<kFmtBF16>(p, f, phi, work, s, info, false);
+    default: return solve_fmt<kFmtF32>(p, f, phi, work, s, info, false);
   }
+}
+
+int mixed_enqueue(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStream_t s) {
+  switch (p->mixed.fmt) {
+    case kFmtSplit: return solve_fmt<kFmtSplit>(p, f, phi, work, s, nullptr, true);
+    case kFmtBF16: return solve_fmt<kFmtBF16>(p, f, phi, work, s, nullptr, true);
+    default: return solve_fmt<kFmtF32>(p, f, phi, work, s, nullptr, true);
+  }
+}
+
+int autotune_gemms(tpt_plan_s* p, void* work, cudaStream_t s) {
+  if (p->precision == TPT_PREC_FP64) return TPT_OK;
+  MixedTables& m = p->mixed;
+  const MixedWork w = carve(p, work);
+  MX_CUDA(cudaMemsetAsync(work, 0, mixed_workspace_bytes(p), s));   // finite operands
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  int status = TPT_OK;
+  for (cudaEvent_t& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) status = TPT_ERR_CUDA;
+  const int kind = kind_of(m.fmt), npl = nplanes(m.fmt);
+  constexpr int kReps = 3;
+  for (int i = 0; i < 4 && status == TPT_OK; ++i) {
+    const StageGemm t = stage_gemm(p, w, i, false);
+    const int top = tc::default_bn(t.g.N);
+    float best = 0.0f;
+    int best_bn = top;
+    for (int bn = 32; bn <= top && status == TPT_OK; bn *= 2) {
+      tc::GemmOut g = t.g;
+      g.bn = bn;
+      g.max_ctas = 0;
+      cudaError_t e = tc::gemm(kind, npl, t.a, t.b, g, s);   // warm-up
+      if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
+      for (int r = 0; r < kReps && e == cudaSuccess; ++r) e = tc::gemm(kind, npl, t.a, t.b, g, s);
+      if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+      float ms = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+      if (e != cudaSuccess) {
+        status = TPT_ERR_CUDA;
+        break;
+      }
+      if (bn == 32 || ms < best) {
+        best = ms;
+        best_bn = bn;
+      }
+    }
+    m.gemm_bn[i] = best_bn;
+    m.gemm_ctas[i] = 0;
+  }
+  for (cudaEvent_t& e : ev)
+    if (e) cudaEventDestroy(e);
+  if (status != TPT_OK) return status;
+  int errflag = 0;
+  MX_CUDA(cudaMemcpyAsync(&errflag, w.scal + 15, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MX_CUDA(cudaStreamSynchronize(s));
+  ++p->generation;
+  return errflag ? TPT_ERR_TIMEOUT : TPT_OK;
+}
+
+int mixed_info(const tpt_plan_s* p, const double* h, tpt_info* info) {
+  int errflag = 0;
+  std::memcpy(&errflag, &h[15], sizeof(int));
+  const double np = static_cast<double>(npts(p));
+  const double fn2 = proj_norm2(h, np, p->vol, p->singular);
+  const double rel = fn2 > 0.0 ? std::sqrt(h[1] / fn2) : std::sqrt(h[1]);
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->iters = 1 + p->max_refine;
+    info->rel_residual = rel;
+    info->compat_defect = p->singular ? h[7] / p->vol : 0.0;
+  }
+  if (errflag) return TPT_ERR_TIMEOUT;
+  if (!std::isfinite(rel)) return TPT_ERR_NONFINITE;
+  if (p->rtol > 0.0 && !(rel <= p->rtol)) return TPT_ERR_NOT_CONVERGED;
+  return TPT_OK;
 }
 
 int tc_gemm_test(int precision, int M, int N, int K, const double* A, const double* B, double* D,

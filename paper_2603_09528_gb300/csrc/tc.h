@@ -33,7 +33,12 @@ struct GemmOut {
   int accumulate;   // float-pair mode: add into (out0, out1) instead of writing
   int n_fastest;    // tile order: n fastest (A tile reused by consecutive CTAs)
   int* err;         // device flag for timed-out waits (may be null)
+  int bn = 0;       // column tile width 32/64/128/256; 0 picks the smallest >= N
+  int max_ctas = 0; // cap on the persistent CTAs; 0 = one per SM
 };
+
+// Column tile width used when GemmOut::bn is 0.
+int default_bn(int N);
 
 cudaError_t gemm(int kind, int nplanes, const Operand& A, const Operand& B, const GemmOut& g,
                  cudaStream_t s);

@@ -64,6 +64,10 @@ struct MixedTables {
   double* null_invm = nullptr;     //   c'_k and 1/m_k, k < Nz - 1
   cudaStream_t side = nullptr;     // second stream for the null line, with fork/join events
   cudaEvent_t fork = nullptr, join = nullptr;
+  // transform GEMM tiles per stage (x forward, y forward, y inverse, x
+  // inverse): column tile width (0 = default) and persistent-CTA cap (0 = all)
+  int gemm_bn[4] = {0, 0, 0, 0};
+  int gemm_ctas[4] = {0, 0, 0, 0};
 };
 
 struct FftTables {    // device tables of a Fourier-transformed direction
@@ -115,6 +119,7 @@ struct tpt_plan_s {
   tpt::MixedTables mixed;
   int stage_timing = 0;           // record per-stage CUDA events in tpt_solve
   cudaEvent_t ev[12] = {};        // stage boundaries (created on first use)
+  unsigned generation = 0;        // bumped when coefficients or tiles change
   std::vector<void*> allocs;      // every device allocation owned by the plan
 };
 
@@ -124,6 +129,8 @@ size_t npts(const tpt_plan_s* p);
 
 // Count of kernels this library has launched (all devices, all threads).
 void note_launch(unsigned long long k = 1);
+unsigned long long launch_count();
+void forget_launches(unsigned long long k);   // undo counts of captured (not run) launches
 
 // ----------------------------------------------------------------- kernels
 // Batched column-major float64 GEMM: C_b = A_b B_b (+ C_b when accumulate),
@@ -157,5 +164,17 @@ int mixed_solve(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStr
                 tpt_info* info);
 int tc_gemm_test(int precision, int M, int N, int K, const double* A, const double* B, double* D,
                  void* work, int dev, cudaStream_t s);
+
+// Capturable solves: 1 + max_refine corrections and a final residual, no host
+// synchronisation; the residual sums are left in the first 16 doubles of the
+// workspace.  *_info turns a host copy of those 16 doubles into a report and a
+// status (TIMEOUT, NONFINITE, NOT_CONVERGED against rtol when rtol > 0).
+int mixed_enqueue(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStream_t s);
+int mixed_info(const tpt_plan_s* p, const double* h, tpt_info* info);
+int solve_enqueue(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStream_t s);
+int solve_info(const tpt_plan_s* p, const double* h, tpt_info* info);
+// Times the transform GEMMs of a mixed plan over the candidate tiles and keeps
+// the fastest per stage (gemm_tune.cu).
+int autotune_gemms(tpt_plan_s* p, void* work, cudaStream_t s);
 
 }  // namespace tpt

@@ -53,31 +53,60 @@ def field_to_host(t: torch.Tensor, n) -> np.ndarray:
     return t.detach().cpu().numpy().reshape(tuple(n), order="F")
 
 
+def make_desc(n, dxf, dxc, bc, xform=(AUTO, AUTO), alpha=0.0, beta=1.0, precision=FP64, rtol=0.0,
+              max_refine=1, desc=None):
+    """Fill a tpt_desc; returns (desc, arrays that must stay alive until the
+    plan is created)."""
+    desc = _lib.tpt_desc() if desc is None else desc
+    keep = []
+    for a in range(3):
+        f = np.ascontiguousarray(dxf[a], dtype=np.float64)
+        c = np.ascontiguousarray(dxc[a], dtype=np.float64)
+        keep += [f, c]
+        desc.n[a] = int(n[a])
+        desc.dxf[a] = f.ctypes.data_as(_lib._dp)
+        desc.dxc[a] = c.ctypes.data_as(_lib._dp)
+        lo, hi = bc[a]
+        desc.bc[a][0] = _BC.get(lo, lo) if isinstance(lo, str) else int(lo)
+        desc.bc[a][1] = _BC.get(hi, hi) if isinstance(hi, str) else int(hi)
+    desc.xform[0], desc.xform[1] = int(xform[0]), int(xform[1])
+    desc.alpha, desc.beta = float(alpha), float(beta)
+    desc.precision = int(precision)
+    desc.rtol = float(rtol)
+    desc.max_refine = int(max_refine)
+    return desc, keep
+
+
+def _info_dict(info, status):
+    return dict(iters=info.iters, rel_residual=info.rel_residual, compat_defect=info.compat_defect,
+                status=status, ms_stage=[float(x) for x in info.ms_stage])
+
+
 class Plan:
     """tpt_plan_create / tpt_solve / tpt_plan_destroy on one CUDA device."""
 
     def __init__(self, n, dxf, dxc, bc, xform=(AUTO, AUTO), alpha=0.0, beta=1.0,
                  precision=FP64, rtol=0.0, max_refine=1, device: int = 0):
-        self.n = tuple(int(v) for v in n)
         self.device = int(device)
-        self._dxf = [np.ascontiguousarray(d, dtype=np.float64) for d in dxf]
-        self._dxc = [np.ascontiguousarray(d, dtype=np.float64) for d in dxc]
-        desc = _lib.tpt_desc()
-        for a in range(3):
-            desc.n[a] = self.n[a]
-            desc.dxf[a] = self._dxf[a].ctypes.data_as(_lib._dp)
-            desc.dxc[a] = self._dxc[a].ctypes.data_as(_lib._dp)
-            lo, hi = bc[a]
-            desc.bc[a][0] = _BC.get(lo, lo) if isinstance(lo, str) else int(lo)
-            desc.bc[a][1] = _BC.get(hi, hi) if isinstance(hi, str) else int(hi)
-        desc.xform[0], desc.xform[1] = int(xform[0]), int(xform[1])
-        desc.alpha, desc.beta = float(alpha), float(beta)
-        desc.precision = int(precision)
-        desc.rtol = float(rtol)
-        desc.max_refine = int(max_refine)
+        desc, keep = make_desc(n, dxf, dxc, bc, xform, alpha, beta, precision, rtol, max_refine)
         h = C.c_void_p()
         check(lib.tpt_plan_create(C.byref(desc), self.device, C.byref(h)), "tpt_plan_create")
+        del keep
+        self._owned = True
+        self._attach(h, n)
+
+    @classmethod
+    def borrowed(cls, handle: C.c_void_p, n, device: int) -> "Plan":
+        """View of a plan owned elsewhere (a batch instance); never destroyed here."""
+        obj = cls.__new__(cls)
+        obj.device = int(device)
+        obj._owned = False
+        obj._attach(handle, n)
+        return obj
+
+    def _attach(self, h, n):
         self._h = h
+        self.n = tuple(int(v) for v in n)
         nb = C.c_size_t()
         check(lib.tpt_workspace_bytes(self._h, C.byref(nb)), "tpt_workspace_bytes")
         self.workspace_bytes = int(nb.value)
@@ -122,6 +151,9 @@ class Plan:
         return dict(iters=info.iters, rel_residual=info.rel_residual,
                     compat_defect=info.compat_defect)
 
+    def set_refinement(self, rtol: float, max_refine: int):
+        check(lib.tpt_set_refinement(self._h, float(rtol), int(max_refine)), "tpt_set_refinement")
+
     def set_coefficients(self, alpha: float, beta: float):
         check(lib.tpt_set_coefficients(self._h, float(alpha), float(beta)), "tpt_set_coefficients")
 
@@ -164,9 +196,109 @@ class Plan:
               "tpt_plan_rows")
         return a, b, c
 
+    def autotune(self, work: torch.Tensor = None, stream=None):
+        """tpt_plan_autotune: the four transform column-tile widths it keeps."""
+        work = self.new_workspace() if work is None else work
+        t = (C.c_int * 4)()
+        check(lib.tpt_plan_autotune(self._h, _ptr(work), _stream(stream), t), "tpt_plan_autotune")
+        return tuple(int(v) for v in t)
+
+    def set_tiles(self, tiles):
+        t = (C.c_int * 4)(*[int(v) for v in tiles])
+        check(lib.tpt_plan_set_tiles(self._h, t), "tpt_plan_set_tiles")
+
+    def tiles(self):
+        t = (C.c_int * 4)()
+        check(lib.tpt_plan_get_tiles(self._h, t), "tpt_plan_get_tiles")
+        return tuple(int(v) for v in t)
+
     def close(self):
         if getattr(self, "_h", None):
-            lib.tpt_plan_destroy(self._h)
+            if self._owned:
+                lib.tpt_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """tpt_batch_*: independent instances of uneven size solved as one CUDA
+    graph.  ``specs`` is a list of dicts of Plan's keyword arguments (n, dxf,
+    dxc, bc, xform, alpha, beta, precision, rtol, max_refine)."""
+
+    def __init__(self, specs, nstreams: int = 0, device: int = 0):
+        self.device = int(device)
+        self.count = len(specs)
+        descs = (_lib.tpt_desc * self.count)()
+        keep = []
+        for i, sp in enumerate(specs):
+            _, k = make_desc(desc=descs[i], **sp)
+            keep.append(k)
+        h = C.c_void_p()
+        check(lib.tpt_batch_create(descs, self.count, self.device, int(nstreams), C.byref(h)),
+              "tpt_batch_create")
+        self._h = h
+        del keep
+        nb = C.c_size_t()
+        check(lib.tpt_batch_workspace_bytes(self._h, C.byref(nb)), "tpt_batch_workspace_bytes")
+        self.workspace_bytes = int(nb.value)
+        self.plans = []
+        for i, sp in enumerate(specs):
+            ph = C.c_void_p()
+            check(lib.tpt_batch_plan(self._h, i, C.byref(ph)), "tpt_batch_plan")
+            self.plans.append(Plan.borrowed(ph, sp["n"], self.device))
+
+    def new_workspace(self) -> torch.Tensor:
+        return torch.empty(self.workspace_bytes, dtype=torch.uint8, device="cuda:%d" % self.device)
+
+    def autotune(self, work: torch.Tensor, stream=None):
+        check(lib.tpt_batch_autotune(self._h, _ptr(work), _stream(stream)), "tpt_batch_autotune")
+        return [p.tiles() for p in self.plans]
+
+    def calibrate(self, fs, phis, work: torch.Tensor, rtol: float = 1e-10, max_refine: int = 40,
+                  stream=None):
+        """Fix each instance's number of corrections for capture: one adaptive
+        solve to ``rtol`` per instance, then max_refine = corrections used - 1.
+        Returns the corrections per instance."""
+        used = []
+        for p, f, phi in zip(self.plans, fs, phis):
+            p.set_refinement(rtol, max_refine)
+            _, info = p.solve(f, phi, work, stream=stream, raise_not_converged=False)
+            used.append(int(info["iters"]))
+            p.set_refinement(rtol, max(0, used[-1] - 1))
+        return used
+
+    def solve(self, fs, phis, work: torch.Tensor, stream=None, want_info: bool = True,
+              raise_errors: bool = True):
+        """tpt_batch_solve.  Returns a list of info dicts (with per-instance
+        status) after a stream synchronisation, or None when want_info is
+        False (the call is then asynchronous)."""
+        n = self.count
+        fa = (C.c_void_p * n)(*[f.data_ptr() for f in fs])
+        pa = (C.c_void_p * n)(*[p.data_ptr() for p in phis])
+        infos = (_lib.tpt_info * n)() if want_info else None
+        sts = (C.c_int * n)() if want_info else None
+        st = lib.tpt_batch_solve(self._h, fa, pa, _ptr(work), _stream(stream), infos, sts)
+        if raise_errors and st not in (_lib.TPT_OK, _lib.TPT_ERR_NOT_CONVERGED):
+            check(st, "tpt_batch_solve")
+        if not want_info:
+            return None
+        return [_info_dict(infos[i], int(sts[i])) for i in range(n)]
+
+    def launches_per_replay(self) -> int:
+        v = C.c_ulonglong()
+        check(lib.tpt_batch_launches(self._h, C.byref(v)), "tpt_batch_launches")
+        return int(v.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            for p in self.plans:
+                p._h = None
+            lib.tpt_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

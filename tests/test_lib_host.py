@@ -173,3 +173,36 @@ def test_transform_selection_rules():
     d, keep = _desc((32, 32, 8), [un, un, O.tanh_grid(8, 1.0, 1.0)], [(1, 1), (1, 1), (1, 1)],
                     prec=L.TPT_PREC_MIXED_BF16X3, xform=(L.TPT_XFORM_FFT, L.TPT_XFORM_GEMM))
     assert L.lib.tpt_plan_create(C.byref(d), -1, C.byref(h)) == L.TPT_ERR_UNSUPPORTED
+
+
+def test_tile_setters_and_batch_argument_checks():
+    st, h, _ = _host_plan((6, 6, 6), (1, 1, 1), [(1, 1)] * 3, prec=L.TPT_PREC_MIXED_BF16X3)
+    assert st == L.TPT_OK
+    t = (C.c_int * 4)(32, 64, 0, 256)
+    assert L.lib.tpt_plan_set_tiles(h, t) == L.TPT_OK
+    got = (C.c_int * 4)()
+    assert L.lib.tpt_plan_get_tiles(h, got) == L.TPT_OK
+    assert list(got) == [32, 64, 0, 256]
+    bad = (C.c_int * 4)(32, 48, 0, 0)
+    assert L.lib.tpt_plan_set_tiles(h, bad) == L.TPT_ERR_INVALID_ARG
+    assert list(got) == [32, 64, 0, 256]
+    # host-only plans are rejected by the device entry points
+    x = C.c_void_p(256)
+    assert L.lib.tpt_plan_autotune(h, x, None, got) == L.TPT_ERR_INVALID_ARG
+    L.lib.tpt_plan_destroy(h)
+    st, h, _ = _host_plan((6, 6, 6), (1, 1, 1), [(1, 1)] * 3)
+    assert L.lib.tpt_plan_set_tiles(h, t) == L.TPT_OK       # float64 plan: nothing to tune
+    assert L.lib.tpt_plan_get_tiles(h, got) == L.TPT_OK and list(got) == [0, 0, 0, 0]
+    L.lib.tpt_plan_destroy(h)
+    # a batch needs a device, at least one instance and an output handle
+    grids = [O.tanh_grid(8, 1.0, 1.0)] * 3
+    d, keep = _desc((8, 8, 8), grids, [(1, 1)] * 3)
+    b = C.c_void_p()
+    assert L.lib.tpt_batch_create(C.byref(d), 1, -1, 0, C.byref(b)) == L.TPT_ERR_INVALID_ARG
+    assert L.lib.tpt_batch_create(C.byref(d), 0, 0, 0, C.byref(b)) == L.TPT_ERR_INVALID_ARG
+    assert L.lib.tpt_batch_create(None, 1, 0, 0, C.byref(b)) == L.TPT_ERR_INVALID_ARG
+    assert L.lib.tpt_batch_create(C.byref(d), 1, 0, -1, C.byref(b)) == L.TPT_ERR_INVALID_ARG
+    assert not b.value
+    n = C.c_size_t()
+    assert L.lib.tpt_batch_workspace_bytes(None, C.byref(n)) == L.TPT_ERR_INVALID_ARG
+    assert L.lib.tpt_batch_destroy(None) == L.TPT_ERR_INVALID_ARG
