@@ -384,6 +384,24 @@ cudaError_t launch_out(const Operand& A, const Operand& B, const GemmOut& g, cud
 
 }  // namespace
 
+bool make_plain_map(CUtensorMap* map, const void* base, int elem_bytes, long long inner, long long outer,
+                    long long row_stride_bytes, int box_inner, int box_outer) {
+  auto fn = encode_fn();
+  if (!fn || !base || (elem_bytes != 2 && elem_bytes != 4)) return false;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || row_stride_bytes % 16 != 0) return false;
+  cuuint64_t dims[2] = {static_cast<cuuint64_t>(inner), static_cast<cuuint64_t>(outer)};
+  cuuint64_t strides[1] = {static_cast<cuuint64_t>(row_stride_bytes)};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(box_inner), static_cast<cuuint32_t>(box_outer)};
+  cuuint32_t estr[2] = {1, 1};
+  const CUtensorMapDataType dt =
+      elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  std::memset(map, 0, sizeof(*map));
+  CUresult r = fn(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 int default_bn(int N) { return N <= 32 ? 32 : N <= 64 ? 64 : N <= 128 ? 128 : 256; }
 
 cudaError_t gemm(int kind, int nplanes, const Operand& A, const Operand& B, const GemmOut& g,

@@ -25,6 +25,7 @@
 #include <cstring>
 #include <vector>
 
+#include "ptx.h"
 #include "tc.h"
 #include "tpt_internal.h"
 
@@ -242,125 +243,244 @@ prepare_kernel(int nx, int ny, int nz, int ldx, int nbi, const double* __restric
 }
 
 // ---------------------------------------------------------------- Thomas
-// Tridiagonal solves along z on T2 (q, p, k), rows of ldy, by the partition
-// method with every value in registers.  A block holds TL consecutive lines
-// (consecutive q: coalesced loads) times nseg segments of M rows; thread
-// (l, s) owns rows [sM, min(Nz, (s+1)M)) of line l.  The segment's last row is
-// its interface unknown y_s; its interior rows are solved by one Thomas
-// factorisation for three right-hand sides, giving
-//     x_t = g_t + u_t y_{s-1} + v_t y_s ,
-// the interface rows then form a tridiagonal system in (y_0 .. y_{S-1}) per
-// line, solved in shared memory by one thread, and each thread finishes its
-// rows.  float32 throughout; the singular null line (q, p) = (0, 0) is taken
-// by null_line_kernel (float64), which writes that line itself.  A block is TL x NSEG = 512
-// threads (TL warps solve the TL reduced systems, one warp per line) and M is
-// the smallest segment length with NSEG * M >= Nz.
-constexpr int TL = 16;     // lines per block
-constexpr int NSEG = 32;   // segments per line (rows past Nz are identity rows)
+// Tridiagonal solves along z (Algorithm 1 step 5) from T2 (float32, written by
+// the y-forward GEMM) into T3 (the y-inverse GEMM operand format), by the
+// partition method.  Line L = q + ldy p has its rows k at L + k ldy Nx, so
+// for a fixed k all lines are contiguous; a tile is TLT consecutive lines
+// times all rows.  The kernel is persistent (one CTA per SM): one thread
+// claims tiles from a global counter and streams them into a ring of
+// shared-memory input stages with 2D TMA loads (box TLT lines x up to 256
+// rows, rows past Nz zero-filled) running ahead of the solve; the CTA solves
+// a tile into an output tile that one thread stores with a TMA store.
+// Claiming tiles dynamically lets a CTA that starts late (its SM busy with the
+// null line) take fewer tiles.
+//
+// Per tile, warp s owns rows [sM, (s+1)M) of all TLT lines (lane l = line l),
+// for s < nseg = ceil(Nz / M); further warps idle (identity rows of the
+// reduced system).  Rows past Nz are identity rows (a = c = 0, diagonal 1,
+// right side 0), folded into a per-row coefficient table in shared memory
+// (beta a, beta b, beta c, and 1 or 0 for the modal shift).  The segment's
+// last row is its interface unknown y_s.  One forward elimination over the
+// interior rows, for the right side and for the coupling to y_{s-1}, gives
+// with x_t = g_t + u_t y_{s-1} + v_t y_s the values the interface rows need
+// (g, u of the last interior row, and g_0, u_0, v_0 of the first, accumulated
+// during the sweep as sums with the running product of -c'_t, so no row is
+// kept); the interface rows form a tridiagonal system in (y_0 .. y_{nseg-1})
+// per line, solved by parallel cyclic reduction on nseg lanes; finally each
+// segment is solved by Thomas with its two interface values as boundary
+// values, the eliminated right side kept in place of the input.  Only the
+// reciprocal pivots stay in registers.  float32 throughout.  The singular
+// null line (q, p) = (0, 0) is taken by null_line_kernel (float64) on a
+// second stream, which writes that line of T3 itself, so the tile holding it
+// is stored with plain stores that skip it.  Lines with q >= Ny are padding:
+// solved with a dummy shift and stored into the padding of T3, which no
+// later step reads.
+constexpr int kThomasThreads = 512;
+constexpr int kThomasSmemBudget = 212 * 1024;   // dynamic shared memory of the kernel
+constexpr int kThomasMaxStages = 8;
 
-template <int FMT, int M, bool FULL>
-__global__ void __launch_bounds__(512)
-thomas_part_kernel(int nx, int ny, int nz, int ldy, void* t0, void* t1,
-                   const float* __restrict__ lamx, const float* __restrict__ lamy,
-                   const float* __restrict__ az, const float* __restrict__ bz,
-                   const float* __restrict__ cz, float alpha, float beta, int singular) {
-  // Rows past Nz are identity rows (a = c = 0, diagonal 1, right side 0): they
-  // decouple because c_{Nz-1} = 0, and make every segment exactly M rows long,
-  // so all per-row arrays stay in registers with compile-time indices.
-  constexpr int nseg = NSEG;
-  __shared__ float shm[7 * NSEG * TL];
-  float* G0 = shm;                       // [nseg][TL] first-interior g, u, v of each segment
-  float* U0 = G0 + nseg * TL;
-  float* V0 = U0 + nseg * TL;
-  float* RA = V0 + nseg * TL;            // reduced rows
-  float* RB = RA + nseg * TL;
-  float* RC = RB + nseg * TL;
-  float* RD = RC + nseg * TL;            // right-hand side, then y
-  const int l = threadIdx.x % TL, s = threadIdx.x / TL;
-  const long long lines = static_cast<long long>(nx) * ny;
-  const long long L = static_cast<long long>(blockIdx.x) * TL + l;
-  const bool valid = L < lines;
-  const int q = valid ? static_cast<int>(L % ny) : 0, p = valid ? static_cast<int>(L / ny) : 0;
-  const long long base = q + static_cast<long long>(ldy) * p;
-  const long long stride = static_cast<long long>(ldy) * nx;
+struct RowCoef {
+  float a, b, c, m;   // beta a_k (0 at k = 0), beta b_k, beta c_k (0 from Nz - 1), shift factor
+};
+
+// Geometry of one launch (host and device): stage rows SR = nb * rb >= nseg * M.
+struct ThomasGeom {
+  int nseg, nb, rb, sr;
+  int stages;
+  int in_bytes, out_bytes, coef_bytes;   // one input stage, the output tile, the table
+};
+
+template <int FMT>
+struct T3Fmt {
+  static constexpr int NPL = (FMT == kFmtSplit) ? 2 : 1;
+  static constexpr int EB = (FMT == kFmtF32) ? 4 : 2;
+};
+
+// Raw copy of element i of an output tile (planes s0, s1) to element j of T3.
+template <int FMT>
+__device__ __forceinline__ void copy_elem(const void* s0, const void* s1, int i, void* g0, void* g1, long long j) {
+  if (FMT == kFmtF32) {
+    static_cast<float*>(g0)[j] = static_cast<const float*>(s0)[i];
+  } else {
+    static_cast<uint16_t*>(g0)[j] = static_cast<const uint16_t*>(s0)[i];
+    if (FMT == kFmtSplit) static_cast<uint16_t*>(g1)[j] = static_cast<const uint16_t*>(s1)[i];
+  }
+}
+
+template <int FMT, int M, int TLT>
+__global__ void __launch_bounds__(kThomasThreads, 1)
+thomas_tma_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ CUtensorMap map_o0,
+                  const __grid_constant__ CUtensorMap map_o1, ThomasGeom geo, int nx, int ny, int nz, int ldy,
+                  int ntiles, int* next_tile, void* t3_0, void* t3_1, const float* __restrict__ lamx,
+                  const float* __restrict__ lamy, const float* __restrict__ az, const float* __restrict__ bz,
+                  const float* __restrict__ cz, float alpha, float beta, int singular, int* err) {
+  using O = T3Fmt<FMT>;
+  constexpr int NSEG = kThomasThreads / TLT;   // segment slots per line (16 or 32)
+  extern __shared__ __align__(128) uint8_t dsm_raw[];
+  // 1024-byte aligned start, offset on the shared pointer itself so that every
+  // access below stays a shared-memory (not generic) access
+  uint8_t* dsm = dsm_raw + ((1024u - (ptx::smem_u32(dsm_raw) & 1023u)) & 1023u);
+  RowCoef* coef = reinterpret_cast<RowCoef*>(dsm);
+  uint8_t* in_base = dsm + geo.coef_bytes;
+  uint8_t* ot = in_base + static_cast<size_t>(geo.stages) * geo.in_bytes;
+  void* o0 = ot;
+  void* o1 = ot + (O::NPL == 2 ? geo.out_bytes / 2 : 0);
+  __shared__ float red[7 * kThomasThreads];
+  __shared__ __align__(8) uint64_t full[kThomasMaxStages];
+  __shared__ int tile_of[kThomasMaxStages];   // tile loaded into each stage, -1: none left
+  __shared__ int go;
+  float* G0 = red;                       // [slot][TLT] g_0, u_0, v_0 of each segment
+  float* U0 = G0 + kThomasThreads;
+  float* V0 = U0 + kThomasThreads;
+  float* RA = V0 + kThomasThreads;       // reduced rows
+  float* RB = RA + kThomasThreads;
+  float* RC = RB + kThomasThreads;
+  float* RD = RC + kThomasThreads;       // right-hand side, then y
+  const int tid = threadIdx.x;
+  const int l = tid % TLT, s = tid / TLT;
   const int s0 = s * M;
-  const float shift = alpha + beta * (lamx[p] + lamy[q]);
+  const bool active = s < geo.nseg;
+  const int lines = ldy * nx;            // also the row stride of T2 / T3
+  const int S = geo.stages;
+  long long issued = 0;                  // (thread 0) local stages issued so far
+  bool exhausted = false;                // (thread 0) the counter has run past ntiles
+  int claim = -1;                        // (thread 0) next claimed tile, fetched a tile early
 
-  float d[M];
-#pragma unroll
-  for (int t = 0; t < M; ++t) {
-    const int k = s0 + t;
-    d[t] = (valid && (FULL || k < nz)) ? Elem<FMT>::load(t0, t1, base + k * stride) : 0.0f;
-  }
-  // interior rows t = 0 .. M-2: one factorisation, three right-hand sides
-  float cp[M - 1], g[M - 1], u[M - 1];
-  float cprev = 0.0f, gprev = 0.0f, uprev = 0.0f;
-#pragma unroll
-  for (int t = 0; t < M - 1; ++t) {
-    const int k = s0 + t;
-    const bool real = FULL || k < nz;
-    const float a = (real && k > 0) ? beta * az[k] : 0.0f;
-    const float m = real ? fmaf(-a, cprev, fmaf(beta, bz[k], shift)) : 1.0f;
-    const float inv = __fdividef(1.0f, m);
-    cp[t] = real ? beta * cz[k] * inv : 0.0f;
-    g[t] = fmaf(-a, gprev, d[t]) * inv;
-    u[t] = (t == 0 ? -a : -a * uprev) * inv;
-    cprev = cp[t];
-    gprev = g[t];
-    uprev = u[t];
-  }
-#pragma unroll
-  for (int t = M - 3; t >= 0; --t) {
-    g[t] = fmaf(-cp[t], g[t + 1], g[t]);
-    u[t] = fmaf(-cp[t], u[t + 1], u[t]);
-  }
-  // v_t: interior response to a unit interface y_s; v_{M-2} = -cp[M-2]
-  float v0 = -cp[M - 2];
-#pragma unroll
-  for (int t = M - 3; t >= 0; --t) v0 = -cp[t] * v0;
-  const int o = s * TL + l;
-  G0[o] = g[0];
-  U0[o] = u[0];
-  V0[o] = v0;
-  __syncthreads();
-  {
-    const int k = s0 + M - 1;            // interface row of this segment
-    const bool real = FULL || k < nz;
-    const float a1 = (real && k > 0) ? beta * az[k] : 0.0f;
-    const float b1 = real ? fmaf(beta, bz[k], shift) : 1.0f;
-    const float c1 = real ? beta * cz[k] : 0.0f;
-    const float A = a1 * u[M - 2];
-    float B = fmaf(-a1, cp[M - 2], b1);
-    float D = fmaf(-a1, g[M - 2], d[M - 1]);
-    float Cc = 0.0f;
-    if (s + 1 < nseg) {
-      const int on = o + TL;
-      B = fmaf(c1, U0[on], B);
-      Cc = c1 * V0[on];
-      D = fmaf(-c1, G0[on], D);
+  auto issue = [&](long long i, int tile) {   // one thread: load claimed `tile` as local tile i
+    const int st = static_cast<int>(i % S);
+    const uint32_t bar = ptx::smem_u32(&full[st]);
+    ++issued;
+    if (tile >= ntiles) {                // none left: complete the phase without data
+      exhausted = true;
+      tile_of[st] = -1;
+      ptx::mbar_arrive(bar);
+      return;
     }
-    RA[o] = A;
-    RB[o] = B;
-    RC[o] = Cc;
-    RD[o] = D;
+    tile_of[st] = tile;
+    ptx::mbar_arrive_expect_tx(bar, static_cast<uint32_t>(geo.in_bytes));
+    uint8_t* base = in_base + static_cast<size_t>(st) * geo.in_bytes;
+    for (int b = 0; b < geo.nb; ++b)
+      ptx::tma_load_2d(ptx::smem_u32(base + b * geo.rb * TLT * 4), &map_in, bar, tile * TLT, b * geo.rb);
+  };
+
+  for (int k = tid; k < geo.sr; k += blockDim.x) {
+    RowCoef rc{0.0f, 1.0f, 0.0f, 0.0f};
+    if (k < nz) {
+      rc.a = k > 0 ? beta * az[k] : 0.0f;
+      rc.b = beta * bz[k];
+      rc.c = k < nz - 1 ? beta * cz[k] : 0.0f;
+      rc.m = 1.0f;
+    }
+    coef[k] = rc;
+  }
+  if (tid == 0) {
+    for (int i = 0; i < S; ++i) ptx::mbar_init(ptx::smem_u32(&full[i]), 1);
+    ptx::fence_mbar_init();
+    ptx::prefetch_tmap(&map_in);
+    ptx::prefetch_tmap(&map_o0);
+    if (O::NPL == 2) ptx::prefetch_tmap(&map_o1);
   }
   __syncthreads();
-  // Reduced system of every line by parallel cyclic reduction: warp w solves
-  // line w (w < TL) with lane r holding interface row r; rows past nseg are
-  // identity rows.  log2(32) = 5 shuffle steps leave decoupled rows.
-  {
-    const int w = threadIdx.x / 32, r = threadIdx.x % 32;
-    if (w < TL) {
-      const int i = r * TL + w;
-      const bool in = r < nseg;
-      float A = in ? RA[i] : 0.0f, B = in ? RB[i] : 1.0f, Cc = in ? RC[i] : 0.0f, D = in ? RD[i] : 0.0f;
+  if (tid == 0) {
+    for (long long i = 0; i < S && !exhausted; ++i) issue(i, atomicAdd(next_tile, 1));
+    if (!exhausted) claim = atomicAdd(next_tile, 1);   // its latency hides behind a tile
+  }
+
+  long long i = 0;
+  bool ok = true;
+  for (;; ++i) {
+    const int st = static_cast<int>(i % S);
+    const uint32_t bar = ptx::smem_u32(&full[st]);
+    const uint32_t par = static_cast<uint32_t>((i / S) & 1);
+    if (tid == 0) go = ptx::mbar_wait(bar, par, err, ptx::kErrWaitFull) ? 1 : 0;
+    __syncthreads();
+    if (!go) {
+      ok = false;
+      break;
+    }
+    const int tile = tile_of[st];
+    if (tile < 0) break;
+    for (int k = 0; k < 64 && !ptx::mbar_try_wait(bar, par); ++k) {
+    }   // the phase is complete: this acquires the TMA writes for every thread
+    float* in = reinterpret_cast<float*>(in_base + static_cast<size_t>(st) * geo.in_bytes);
+
+    const int L = tile * TLT + l;
+    int q = L % ldy, p = L / ldy;
+    if (L >= lines || q >= ny) q = p = 0;        // padding line: dummy shift
+    const float shift = alpha + beta * (lamx[p] + lamy[q]);
+    const int o = s * TLT + l;
+
+    // forward elimination of the interior rows t = 0 .. M-2 for the right
+    // side (g) and the coupling to y_{s-1} (u); g_0, u_0 after the back
+    // substitution are sum_t P_t g_t, sum_t P_t u_t with P_t = prod_{j<t} -c'_j
+    float inv[M - 1];
+    float cprev = 0.0f, gprev = 0.0f, uprev = 0.0f;
+    if (active) {
+      float P = 1.0f, Gs = 0.0f, Us = 0.0f;
 #pragma unroll
-      for (int dlt = 1; dlt < 32; dlt <<= 1) {
-        const float Am = __shfl_up_sync(0xffffffffu, A, dlt), Bm = __shfl_up_sync(0xffffffffu, B, dlt);
-        const float Cm = __shfl_up_sync(0xffffffffu, Cc, dlt), Dm = __shfl_up_sync(0xffffffffu, D, dlt);
-        const float Ap = __shfl_down_sync(0xffffffffu, A, dlt), Bp = __shfl_down_sync(0xffffffffu, B, dlt);
-        const float Cp = __shfl_down_sync(0xffffffffu, Cc, dlt), Dp = __shfl_down_sync(0xffffffffu, D, dlt);
-        const bool hasm = r >= dlt, hasp = r + dlt < 32;
+      for (int t = 0; t < M - 1; ++t) {
+        const RowCoef rc = coef[s0 + t];
+        const float m = fmaf(-rc.a, cprev, fmaf(rc.m, shift, rc.b));
+        const float iv = __fdividef(1.0f, m);
+        const float d = in[(s0 + t) * TLT + l];
+        inv[t] = iv;
+        const float cp = rc.c * iv;
+        const float g = fmaf(-rc.a, gprev, d) * iv;
+        const float u = (t == 0 ? -rc.a : -rc.a * uprev) * iv;
+        Gs = fmaf(P, g, Gs);
+        Us = fmaf(P, u, Us);
+        P *= -cp;
+        cprev = cp;
+        gprev = g;
+        uprev = u;
+      }
+      G0[o] = Gs;
+      U0[o] = Us;
+      V0[o] = P;                         // v_0 = prod_t -c'_t
+    } else {
+      G0[o] = 0.0f;
+      U0[o] = 0.0f;
+      V0[o] = 0.0f;
+    }
+    __syncthreads();
+    if (active) {
+      const int k = s0 + M - 1;          // interface row of this segment
+      const RowCoef rc = coef[k];
+      const float dl = in[k * TLT + l];
+      const float A = rc.a * uprev;
+      float B = fmaf(-rc.a, cprev, fmaf(rc.m, shift, rc.b));
+      float D = fmaf(-rc.a, gprev, dl);
+      float Cc = 0.0f;
+      if (s + 1 < NSEG) {
+        const int on = o + TLT;
+        B = fmaf(rc.c, U0[on], B);
+        Cc = rc.c * V0[on];
+        D = fmaf(-rc.c, G0[on], D);
+      }
+      RA[o] = A;
+      RB[o] = B;
+      RC[o] = Cc;
+      RD[o] = D;
+    } else {
+      RA[o] = 0.0f;
+      RB[o] = 1.0f;
+      RC[o] = 0.0f;
+      RD[o] = 0.0f;
+    }
+    __syncthreads();
+    // Reduced system of every line by parallel cyclic reduction: NSEG lanes
+    // per line (lane r holds interface row r), log2(NSEG) shuffle steps.
+    {
+      const int r = tid % NSEG, line = tid / NSEG;
+      const int ix = r * TLT + line;
+      float A = RA[ix], B = RB[ix], Cc = RC[ix], D = RD[ix];
+#pragma unroll
+      for (int dlt = 1; dlt < NSEG; dlt <<= 1) {
+        const float Am = __shfl_up_sync(0xffffffffu, A, dlt, NSEG), Bm = __shfl_up_sync(0xffffffffu, B, dlt, NSEG);
+        const float Cm = __shfl_up_sync(0xffffffffu, Cc, dlt, NSEG), Dm = __shfl_up_sync(0xffffffffu, D, dlt, NSEG);
+        const float Ap = __shfl_down_sync(0xffffffffu, A, dlt, NSEG), Bp = __shfl_down_sync(0xffffffffu, B, dlt, NSEG);
+        const float Cp = __shfl_down_sync(0xffffffffu, Cc, dlt, NSEG), Dp = __shfl_down_sync(0xffffffffu, D, dlt, NSEG);
+        const bool hasm = r >= dlt, hasp = r + dlt < NSEG;
         const float k1 = hasm ? __fdividef(A, Bm) : 0.0f;
         const float k2 = hasp ? __fdividef(Cc, Bp) : 0.0f;
         const float nA = hasm ? -Am * k1 : 0.0f;
@@ -370,39 +490,81 @@ thomas_part_kernel(int nx, int ny, int nz, int ldy, void* t0, void* t1,
         A = nA;
         Cc = nC;
       }
-      if (in) RD[i] = __fdividef(D, B);
+      RD[ix] = __fdividef(D, B);
+    }
+    if (tid == 0) {                      // the output tile of tile i-1 has been stored
+      ptx::bulk_wait_read<0>();
+    }
+    __syncthreads();
+    if (active) {
+      // Thomas on the segment with boundary values y_{s-1} and y_s
+      const float ys = RD[o];
+      float gp = (s > 0) ? RD[o - TLT] : 0.0f;
+#pragma unroll
+      for (int t = 0; t < M - 1; ++t) {
+        const int ix = (s0 + t) * TLT + l;
+        gp = fmaf(-coef[s0 + t].a, gp, in[ix]) * inv[t];
+        in[ix] = gp;
+      }
+      Elem<FMT>::store(o0, o1, (s0 + M - 1) * TLT + l, ys);
+      float x = ys;
+#pragma unroll
+      for (int t = M - 2; t >= 0; --t) {
+        const int ix = (s0 + t) * TLT + l;
+        x = fmaf(-coef[s0 + t].c * inv[t], x, in[ix]);
+        Elem<FMT>::store(o0, o1, ix, x);
+      }
+    }
+    ptx::fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0 && !exhausted) {        // the input stage is free: refill it
+      issue(i + S, claim);
+      if (!exhausted) claim = atomicAdd(next_tile, 1);
+    }
+    if (!(singular && tile == 0)) {
+      if (tid == 0) {
+        for (int b = 0; b < geo.nb; ++b) {
+          const int off = b * geo.rb * TLT * O::EB;
+          ptx::tma_store_2d(&map_o0, ptx::smem_u32(static_cast<uint8_t*>(o0) + off), tile * TLT, b * geo.rb);
+          if (O::NPL == 2)
+            ptx::tma_store_2d(&map_o1, ptx::smem_u32(static_cast<uint8_t*>(o1) + off), tile * TLT, b * geo.rb);
+        }
+        ptx::bulk_commit();
+      }
+    } else {                             // the null line is not ours to write
+      for (int e = tid; e < TLT * nz; e += blockDim.x) {
+        const int ll = e % TLT, k = e / TLT;
+        if (ll == 0 || ll >= lines) continue;
+        copy_elem<FMT>(o0, o1, e, t3_0, t3_1, ll + static_cast<long long>(k) * lines);
+      }
+      __syncthreads();                   // the output tile is rewritten by the next tile
     }
   }
-  __syncthreads();
-  if (!valid) return;
-  if (singular && L == 0) return;   // the null line is written by null_line_kernel
-  const float ys = RD[o];
-  const float ym = (s > 0) ? RD[o - TL] : 0.0f;
-  if (FULL || s0 + M - 1 < nz) Elem<FMT>::store(t0, t1, base + (s0 + M - 1) * stride, ys);
-  float v = 1.0f;
-#pragma unroll
-  for (int t = M - 2; t >= 0; --t) {
-    v = -cp[t] * v;
-    if (FULL || s0 + t < nz) Elem<FMT>::store(t0, t1, base + (s0 + t) * stride, fmaf(u[t], ym, fmaf(v, ys, g[t])));
+  if (tid == 0) {
+    if (!ok)   // the loads of local tiles i .. issued - 1 may still be landing
+      for (long long k = i; k < issued; ++k)
+        ptx::mbar_wait(ptx::smem_u32(&full[k % S]), static_cast<uint32_t>((k / S) & 1), err,
+                       ptx::kErrWaitDrain, 1u << 20);
+    ptx::bulk_wait_all();
   }
 }
 
-// Singular null line (q, p) = (0, 0) in float64: the line is staged in shared
-// memory, projected to compatible form (dz-weighted mean removed), solved with
-// the plan's precomputed factorisation of T_z (last modal unknown set to zero)
-// and shifted to zero dz-weighted mean; the result overwrites the line in
-// place.  One warp; it touches no other line, so it runs beside
-// thomas_part_kernel on a second stream.
+// Singular null line (q, p) = (0, 0) in float64: the line of T2 is staged in
+// shared memory, projected to compatible form (dz-weighted mean removed),
+// solved with the plan's precomputed factorisation of T_z (last modal unknown
+// set to zero) and shifted to zero dz-weighted mean; the result is written to
+// the line of T3.  One warp; it touches no other line, so it runs beside
+// thomas_tma_kernel on a second stream.
 template <int FMT>
 __global__ void __launch_bounds__(32)
-null_line_kernel(int nz, long long stride, void* t0, void* t1,
+null_line_kernel(int nz, long long stride, const float* __restrict__ t2, void* t3_0, void* t3_1,
                  const double* __restrict__ az, const double* __restrict__ ncp,
                  const double* __restrict__ ninvm, const double* __restrict__ dz, double beta) {
   extern __shared__ double line[];
   const int lane = threadIdx.x;
   double s = 0.0, w = 0.0;
   for (int k = lane; k < nz; k += 32) {
-    const double f = static_cast<double>(Elem<FMT>::load(t0, t1, static_cast<long long>(k) * stride));
+    const double f = static_cast<double>(t2[static_cast<long long>(k) * stride]);
     line[k] = f;
     s = fma(dz[k], f, s);
     w += dz[k];
@@ -430,7 +592,7 @@ null_line_kernel(int nz, long long stride, void* t0, void* t1,
   xs = warp_sum_d(xs);
   const double mean = xs / w;
   for (int k = lane; k < nz; k += 32)
-    Elem<FMT>::store(t0, t1, static_cast<long long>(k) * stride, static_cast<float>((line[k] - mean) / beta));
+    Elem<FMT>::store(t3_0, t3_1, static_cast<long long>(k) * stride, static_cast<float>((line[k] - mean) / beta));
 }
 
 // ------------------------------------------------------------- residual
@@ -687,7 +849,8 @@ void split_ld(long double v, float* h, float* l) {
 
 // Workspace regions of the mixed path.
 struct MixedWork {
-  double* scal;        // 16 doubles: [1] sum r^2, [2] sum vol*phi, [5..7] sums of f, [15] error flag
+  double* scal;        // 16 doubles: [1] sum r^2, [2] sum vol*phi, [5..7] sums of f,
+                       // [14] Thomas tile counter (int), [15] error flag
   double* nl;          // 2 * Nz doubles: c', d' of the null line
   float *fh, *fl, *ph, *pl;
   void* R[2];
@@ -732,10 +895,10 @@ MixedWork carve(const tpt_plan_s* p, void* work) {
     mw.A[pl] = (pl < static_cast<int>(z.np)) ? static_cast<void*>(w) : nullptr;
     if (pl < static_cast<int>(z.np)) w += align256(z.nab * z.eb);
   }
-  for (int pl = 0; pl < 2; ++pl) {
-    mw.B[pl] = (pl < static_cast<int>(z.np)) ? static_cast<void*>(w) : nullptr;
-    if (pl < static_cast<int>(z.np)) w += align256(z.nab * z.eb);
-  }
+  // B holds T2 as float32 (4 bytes an element) and later T4 in the operand
+  // format: two regions of nab 2-byte elements, plane 1 in the second
+  mw.B[0] = w;
+  mw.B[1] = (z.np == 2) ? static_cast<void*>(w + align256(z.nab * 2)) : nullptr;
   return mw;
 }
 
@@ -791,49 +954,119 @@ cudaError_t launch_prepare(const tpt_plan_s* p, const double* f, const MixedWork
   return cudaGetLastError();
 }
 
-template <int FMT, int M, bool FULL>
-cudaError_t launch_part_k(const tpt_plan_s* p, const MixedWork& w, cudaStream_t s) {
+// Tile width and segment length for Nz rows: 32-line tiles (16 segment slots)
+// up to Nz = 512, 16-line tiles (32 slots) above; M is the candidate whose
+// nseg = ceil(Nz / M) slots leave the fewest padding rows (ties: the smaller M).
+void thomas_shape(int nz, int* tlt, int* m_out) {
+  *tlt = nz <= 512 ? 32 : 16;
+  const int slots = kThomasThreads / *tlt;
+  static const int cand[] = {4, 8, 12, 16, 24, 32};
+  int best = 0, pad = 1 << 30;
+  for (int m : cand) {
+    const int nseg = (nz + m - 1) / m;
+    if (nseg > slots) continue;
+    if (nseg * m - nz < pad) {
+      pad = nseg * m - nz;
+      best = m;
+    }
+  }
+  *m_out = best;
+}
+
+// Stage geometry and ring size of thomas_tma_kernel; false when the shared
+// memory budget cannot hold two input stages and the output tile.
+bool thomas_geom(int nz, int m, int tlt, int out_npl, int out_eb, ThomasGeom* g) {
+  g->nseg = (nz + m - 1) / m;
+  const int r = g->nseg * m;
+  g->nb = (r + 255) / 256;
+  g->rb = (r + g->nb - 1) / g->nb;
+  g->sr = g->nb * g->rb;
+  g->in_bytes = g->sr * tlt * 4;
+  g->out_bytes = g->sr * tlt * out_eb * out_npl;
+  g->coef_bytes = (g->sr * static_cast<int>(sizeof(RowCoef)) + 1023) & ~1023;
+  g->stages = (kThomasSmemBudget - 1024 - g->coef_bytes - g->out_bytes) / g->in_bytes;
+  if (g->stages > kThomasMaxStages) g->stages = kThomasMaxStages;
+  return g->stages >= 2;
+}
+
+template <int FMT, int M, int TLT>
+cudaError_t launch_thomas_m(const tpt_plan_s* p, const MixedWork& w, cudaStream_t s) {
+  using O = T3Fmt<FMT>;
   const MixedTables& m = p->mixed;
-  const long long lines = static_cast<long long>(p->n[0]) * p->n[1];
+  const long long lines = static_cast<long long>(m.ldy) * p->n[0];
   const int nz = p->n[2];
+  const long long ntiles = (lines + TLT - 1) / TLT;
+  if (ntiles <= 0) return cudaSuccess;
+  if (lines + TLT > 0x7fffffffLL) return cudaErrorInvalidValue;   // int line indices and TMA coordinates
+  ThomasGeom geo;
+  if (!thomas_geom(nz, M, TLT, O::NPL, O::EB, &geo)) return cudaErrorInvalidConfiguration;
+  CUtensorMap mi, mo0, mo1;
+  if (!tc::make_plain_map(&mi, w.B[0], 4, lines, nz, lines * 4, TLT, geo.rb)) return cudaErrorInvalidValue;
+  if (!tc::make_plain_map(&mo0, w.A[0], O::EB, lines, nz, lines * O::EB, TLT, geo.rb)) return cudaErrorInvalidValue;
+  if (O::NPL == 2) {
+    if (!tc::make_plain_map(&mo1, w.A[1], O::EB, lines, nz, lines * O::EB, TLT, geo.rb))
+      return cudaErrorInvalidValue;
+  } else {
+    mo1 = mo0;
+  }
+  int* next_tile = reinterpret_cast<int*>(w.scal + 14);
+  cudaError_t e = cudaMemsetAsync(next_tile, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  const size_t smem = 1024 + static_cast<size_t>(geo.coef_bytes) + static_cast<size_t>(geo.stages) * geo.in_bytes +
+                      static_cast<size_t>(geo.out_bytes);
+  auto kern = thomas_tma_kernel<FMT, M, TLT>;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->dev);
+  const long long grid = ntiles < sms ? ntiles : sms;
   note_launch(1);
-  thomas_part_kernel<FMT, M, FULL><<<static_cast<unsigned>((lines + TL - 1) / TL), TL * NSEG, 0, s>>>(
-      p->n[0], p->n[1], nz, m.ldy, w.B[0], w.B[1], m.lam_f[0], m.lam_f[1], m.zrows_f,
-      m.zrows_f + nz, m.zrows_f + 2 * nz, static_cast<float>(p->alpha), static_cast<float>(p->beta),
-      p->singular ? 1 : 0);
+  kern<<<static_cast<unsigned>(grid), kThomasThreads, smem, s>>>(
+      mi, mo0, mo1, geo, p->n[0], p->n[1], nz, m.ldy, static_cast<int>(ntiles), next_tile, w.A[0], w.A[1],
+      m.lam_f[0], m.lam_f[1], m.zrows_f, m.zrows_f + nz, m.zrows_f + 2 * nz, static_cast<float>(p->alpha),
+      static_cast<float>(p->beta), p->singular ? 1 : 0, reinterpret_cast<int*>(w.scal + 15));
   return cudaGetLastError();
 }
 
-template <int FMT, int M>
-cudaError_t launch_part(const tpt_plan_s* p, const MixedWork& w, cudaStream_t s) {
-  // every segment full (Nz = NSEG * M): no padding predicates
-  if (p->n[2] == NSEG * M) return launch_part_k<FMT, M, true>(p, w, s);
-  return launch_part_k<FMT, M, false>(p, w, s);
-}
-
+// Step 2.3: T3 = modal Thomas solve of T2 (float32, in B) into A; the null
+// line of a singular problem on the second stream.
 template <int FMT>
 cudaError_t launch_thomas(const tpt_plan_s* p, const MixedWork& w, cudaStream_t s) {
   const MixedTables& m = p->mixed;
   const int nz = p->n[2];
-  cudaStream_t side = m.side;
+  const float* t2 = static_cast<const float*>(w.B[0]);
   if (p->singular) {   // fork: the float64 null line runs beside the partition kernel
     cudaError_t e = cudaEventRecord(m.fork, s);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(side, m.fork, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(m.side, m.fork, 0);
     if (e != cudaSuccess) return e;
-    const double* rz = p->d_rows[2];
     note_launch(1);
-    null_line_kernel<FMT><<<1, 32, static_cast<size_t>(nz) * sizeof(double), side>>>(
-        nz, static_cast<long long>(m.ldy) * p->n[0], w.B[0], w.B[1], rz, m.null_cp, m.null_invm,
+    null_line_kernel<FMT><<<1, 32, static_cast<size_t>(nz) * sizeof(double), m.side>>>(
+        nz, static_cast<long long>(m.ldy) * p->n[0], t2, w.A[0], w.A[1], p->d_rows[2], m.null_cp, m.null_invm,
         p->d_dxf[2], p->beta);
     e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaEventRecord(m.join, side);
+    if (e == cudaSuccess) e = cudaEventRecord(m.join, m.side);
     if (e != cudaSuccess) return e;
   }
   cudaError_t e = cudaErrorInvalidConfiguration;
-  if (nz <= NSEG * 4) e = launch_part<FMT, 4>(p, w, s);
-  else if (nz <= NSEG * 8) e = launch_part<FMT, 8>(p, w, s);
-  else if (nz <= NSEG * 16) e = launch_part<FMT, 16>(p, w, s);
-  else if (nz <= NSEG * 32) e = launch_part<FMT, 32>(p, w, s);
+  int tlt = 0, mm = 0;
+  thomas_shape(nz, &tlt, &mm);
+  if (tlt == 32) {
+    switch (mm) {
+      case 4: e = launch_thomas_m<FMT, 4, 32>(p, w, s); break;
+      case 8: e = launch_thomas_m<FMT, 8, 32>(p, w, s); break;
+      case 12: e = launch_thomas_m<FMT, 12, 32>(p, w, s); break;
+      case 16: e = launch_thomas_m<FMT, 16, 32>(p, w, s); break;
+      case 24: e = launch_thomas_m<FMT, 24, 32>(p, w, s); break;
+      case 32: e = launch_thomas_m<FMT, 32, 32>(p, w, s); break;
+      default: break;
+    }
+  } else {
+    switch (mm) {
+      case 24: e = launch_thomas_m<FMT, 24, 16>(p, w, s); break;
+      case 32: e = launch_thomas_m<FMT, 32, 16>(p, w, s); break;
+      default: break;
+    }
+  }
   if (e == cudaSuccess && p->singular) e = cudaStreamWaitEvent(s, m.join, 0);   // join
   return e;
 }
@@ -890,19 +1123,19 @@ StageGemm stage_gemm(const tpt_plan_s* p, const MixedWork& w, int i, bool accumu
       t.b = operand(m.q[0][0], nx, nx, m.ldx);
       t.g = gout(ny * nz, nx, nx, ny, static_cast<long long>(m.ldy) * nx, m.ldy, w.A[0], w.A[1], om, 0, 1, err);
       break;
-    case 1:   // A = Q_y^{-1} rows q, B = T1 rows (p,k) -> T2 (q, p, k)
+    case 1:   // A = Q_y^{-1} rows q, B = T1 rows (p,k) -> T2 (q, p, k), float32 in B
       t.a = operand(m.q[1][0], ny, ny, m.ldy);
       t.b = operand(w.A, nx * nz, ny, m.ldy);
-      t.g = gout(ny, nx * nz, ny, kBig, 0, m.ldy, w.B[0], w.B[1], om, 0, 0, err);
+      t.g = gout(ny, nx * nz, ny, kBig, 0, m.ldy, w.B[0], nullptr, tc::kOutF32, 0, 0, err);
       break;
-    case 2:   // A = T3 rows (p,k), B = Q_y rows j -> T4 (p, j, k)
-      t.a = operand(w.B, nx * nz, ny, m.ldy);
+    case 2:   // A = T3 rows (p,k) in A, B = Q_y rows j -> T4 (p, j, k) in B
+      t.a = operand(w.A, nx * nz, ny, m.ldy);
       t.b = operand(m.q[1][1], ny, ny, m.ldy);
-      t.g = gout(nx * nz, ny, ny, nx, static_cast<long long>(m.ldx) * ny, m.ldx, w.A[0], w.A[1], om, 0, 1, err);
+      t.g = gout(nx * nz, ny, ny, nx, static_cast<long long>(m.ldx) * ny, m.ldx, w.B[0], w.B[1], om, 0, 1, err);
       break;
     default:  // A = Q_x rows i, B = T4 rows (j,k) -> phi (float pair) (+)= result
       t.a = operand(m.q[0][1], nx, nx, m.ldx);
-      t.b = operand(w.A, ny * nz, nx, m.ldx);
+      t.b = operand(w.B, ny * nz, nx, m.ldx);
       t.g = gout(nx, ny * nz, nx, kBig, 0, nx, w.ph, w.pl, tc::kOutDF, accumulate ? 1 : 0, 0, err);
       break;
   }
@@ -1154,7 +1387,8 @@ size_t mixed_workspace_bytes(const tpt_plan_s* p) {
   size_t b = 256 + align256(2 * sizeof(double) * p->n[2]);
   b += 4 * align256(z.nf * sizeof(float));
   b += z.np * align256(z.nr * z.eb);
-  b += 2 * z.np * align256(z.nab * z.eb);
+  b += z.np * align256(z.nab * z.eb);   // A
+  b += 2 * align256(z.nab * 2);          // B: float32 T2, then T4
   return b;
 }
 

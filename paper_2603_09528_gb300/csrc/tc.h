@@ -1,6 +1,7 @@
 // Host interface of the tensor-core transform GEMM (gemm_tc.cu).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace tpt {
@@ -39,6 +40,13 @@ struct GemmOut {
 
 // Column tile width used when GemmOut::bn is 0.
 int default_bn(int N);
+
+// Unswizzled 2D tensor map over `outer` rows of `inner` elements (2-byte
+// bf16 or 4-byte float32), row stride in bytes, box of box_inner x
+// box_outer elements.  False when the driver entry point is missing or the
+// encoder rejects the layout (base or stride not 16-byte aligned, box too large).
+bool make_plain_map(CUtensorMap* map, const void* base, int elem_bytes, long long inner, long long outer,
+                    long long row_stride_bytes, int box_inner, int box_outer);
 
 cudaError_t gemm(int kind, int nplanes, const Operand& A, const Operand& B, const GemmOut& g,
                  cudaStream_t s);
