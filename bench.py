@@ -339,6 +339,13 @@ def run_ours(args):
         if not args.no_fp64:
             batch["fp64"] = batch_leg(tpt, local, stream, 0, args.steps)
 
+    serving = None
+    if not args.no_serving:
+        serving = {"mixed": serving_leg(tpt, local, prec if prec != 0 else 2, args.serve_requests,
+                                        args.serve_warmup)}
+        if not args.no_fp64:
+            serving["fp64"] = serving_leg(tpt, local, 0, args.serve_requests_fp64, 10)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         nslab = max(1, min(n[2], args.cpu_slabs))
@@ -366,6 +373,7 @@ def run_ours(args):
             "stages": stages,
             "fp64": fp64,
             "batch": batch,
+            "serving": serving,
             "gpu_launches": l1 - l0,
             "roofline": dom,
             "clocks": clk,
@@ -460,6 +468,86 @@ def batch_leg(tpt, device, stream, prec, steps, count=96, seed=5, nstreams=8):
     del fs, phis, work
     torch.cuda.empty_cache()
     return out
+
+
+def serving_leg(tpt, device, prec, count, warmup, rate_hz=200.0, slots=4, stretch_step=0.25):
+    """Open-loop serving (Poisson arrivals at rate_hz; sizes per dimension
+    uniform over {64, 96, ..., 512}; 70% Poisson / 30% Helmholtz; stretch
+    factors on [1, 3] in steps of stretch_step) through the continuous-batching
+    server.  Every request's right-hand side is the first N_x N_y N_z values of
+    one seeded pinned host field and its solution is copied back into one of a
+    ring of pinned host buffers (contents are not kept: timing only).  The
+    first `warmup` requests fill the eigenbasis cache and are not counted;
+    latency = completion - submission on the server's clock."""
+    import threading
+    import torch
+    import seeded_inputs as S
+    reqs = S.serving_requests(warmup + count, rate_hz=rate_hz, seed=6, stretch_step=stretch_step)
+    nmax = max(r["n"][0] * r["n"][1] * r["n"][2] for r in reqs)
+    gen = torch.Generator(device="cuda:%d" % device)
+    gen.manual_seed(6)
+    f_host = (torch.rand(nmax, generator=gen, dtype=torch.float64, device="cuda:%d" % device) * 2 - 1).cpu()
+    f_host = f_host.pin_memory()
+    ring = [torch.empty(nmax, dtype=torch.float64).pin_memory() for _ in range(slots + 4)]
+    srv = tpt.Server(device=device, slots=slots, setup_threads=min(8, max(2, (os.cpu_count() or 4) // 2)),
+                     memory_budget=96 << 30, cache_budget=16 << 30)
+    grids = {}
+
+    def spec(r):
+        gs = []
+        for a in range(3):
+            key = (r["n"][a], r["stretch"][a])
+            if key not in grids:
+                grids[key] = tpt.grid_tanh(r["n"][a], 1.0, r["stretch"][a])
+            gs.append(grids[key])
+        mixed = prec != 0
+        return dict(n=r["n"], dxf=[g[0] for g in gs], dxc=[g[1] for g in gs], bc=[(1, 1)] * 3,
+                    xform=(tpt.GEMM, tpt.GEMM), alpha=r["alpha"], beta=r["beta"], precision=prec,
+                    rtol=1e-10 if mixed else 0.0, max_refine=30 if mixed else 1)
+
+    specs = [spec(r) for r in reqs]
+    tickets = [None] * len(reqs)
+    results = [None] * len(reqs)
+    submitted = threading.Event()
+
+    def collector():
+        for i in range(len(reqs)):
+            while tickets[i] is None:
+                time.sleep(0.0005)
+            results[i] = srv.wait(tickets[i])
+
+    th = threading.Thread(target=collector, daemon=True)
+    th.start()
+    t0 = time.perf_counter()
+    for i, r in enumerate(reqs):
+        delay = r["t_arrival"] - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        tickets[i] = srv.submit(f_host, ring[i % len(ring)], **specs[i])
+    submitted.set()
+    th.join()
+    st = srv.stats()
+    srv.close()
+    meas = results[warmup:]
+    lat = np.array([(x["t_done"] - x["t_submit"]) * 1e3 for x in meas])
+    plan_ms = np.array([(x["t_planned"] - x["t_submit"]) * 1e3 for x in meas])
+    queue_ms = np.array([(x["t_admit"] - x["t_planned"]) * 1e3 for x in meas])
+    run_ms = np.array([(x["t_done"] - x["t_admit"]) * 1e3 for x in meas])
+    span = max(x["t_done"] for x in meas) - min(x["t_submit"] for x in meas)
+    pts = sum(r["n"][0] * r["n"][1] * r["n"][2] for r in reqs[warmup:])
+    bad = sum(1 for x in meas if x["status"] != 0)
+    return {"precision": {0: "fp64", 1: "mixed_bf16", 2: "mixed_bf16x3", 3: "mixed_tf32"}[prec],
+            "requests": count, "warmup_requests": warmup, "offered_rate_hz": rate_hz,
+            "slots": slots, "stretch_step": stretch_step,
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "mean": float(lat.mean()), "max": float(lat.max())},
+            "phase_ms_p50": {"plan": float(np.median(plan_ms)), "queue": float(np.median(queue_ms)),
+                             "h2d_solve_d2h": float(np.median(run_ms))},
+            "solves_per_s": count / span, "gpts_per_s": pts / span / 1e9,
+            "failed": bad, "max_rel_residual": float(max(x["rel_residual"] for x in meas)),
+            "cache": {"hits": int(st["cache_hits"]), "misses": int(st["cache_misses"]),
+                      "device_bytes": int(st["cache_bytes"])},
+            "peak_inflight": int(st["peak_inflight"]), "peak_device_bytes": int(st["peak_bytes"])}
 
 
 def stage_rooflines(ms, iters, n, prec):
@@ -559,6 +647,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched uneven-instances leg")
+    ap.add_argument("--no-serving", action="store_true", help="skip the open-loop serving leg")
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-warmup", type=int, default=200)
+    ap.add_argument("--serve-requests-fp64", type=int, default=40)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

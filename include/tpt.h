@@ -47,6 +47,7 @@ extern "C" {
 #define TPT_ERR_TIMEOUT        6  /* a bounded device-side wait gave up              */
 #define TPT_ERR_NONFINITE      7  /* NaN/Inf in the right-hand side or residual      */
 #define TPT_ERR_NUMERICAL      8  /* eigensolver failed or null pivot did not vanish */
+#define TPT_PENDING            9  /* a served request has not finished yet          */
 
 /* ---- enumerations ---------------------------------------------------- */
 /* Boundary rows of Sec. 2.2.1 ("modified as required by the boundary
@@ -294,6 +295,93 @@ int tpt_batch_infos(tpt_batch batch, tpt_info* infos, int* statuses);
 int tpt_batch_launches(tpt_batch batch, unsigned long long* count);
 
 int tpt_batch_destroy(tpt_batch batch);
+
+/* ---- shared eigenbases ---------------------------------------------------- */
+/* A cache of direction eigenbases on one device.  The eigendecomposition of a
+ * direction (Sec. 2.2.1) depends only on its cell widths, centre spacings,
+ * boundary pair and transform kind -- not on alpha, beta (Sec. 2.2.2) nor on
+ * the other directions -- so plans created through one cache share the
+ * eigenbasis and device tables of every direction they have in common, and
+ * the O(n^3) host eigendecomposition runs once per distinct direction.
+ * cuda_device < 0 makes a host-only cache (for host-only plans).
+ * budget_bytes: device memory the cache keeps for tables that no live plan
+ * uses (least recently used entries beyond it are freed).                  */
+typedef struct tpt_cache_s* tpt_cache;
+
+int tpt_cache_create(int cuda_device, size_t budget_bytes, tpt_cache* out);
+
+/* As tpt_plan_create on the cache's device, sharing eigenbases through the
+ * cache.  The plan's own tables are stream-ordered allocations from the
+ * cache's memory pool, so creating or destroying it does not synchronise the
+ * device; destroy it only after the solves that use it have completed, and
+ * before the cache.  Safe to call from several host threads at once.      */
+int tpt_plan_create_cached(const tpt_desc* desc, tpt_cache cache, tpt_plan* out);
+
+/* hits / misses of direction lookups, device bytes held, entries (each may
+ * be NULL).                                                                 */
+int tpt_cache_stats(tpt_cache cache, unsigned long long* hits, unsigned long long* misses,
+                    size_t* device_bytes, size_t* entries);
+int tpt_cache_destroy(tpt_cache cache);
+
+/* ---- serving ---------------------------------------------------------------- */
+/* A request server on one device with continuous batching: requests (a
+ * descriptor and a right-hand side in host memory) are queued as they arrive;
+ * `setup_threads` host threads build their plans ahead of admission through a
+ * shared eigenbasis cache; `slots` host threads each own a CUDA stream and
+ * admit the oldest planned request as soon as it fits in the device-memory
+ * budget (right-hand side, solution, workspace), copy its right-hand side in,
+ * solve it (adaptive refinement when the descriptor's rtol > 0) and copy the
+ * solution out.  Requests that arrive while others are on the device are
+ * admitted as slots and memory free up, and their work overlaps on the device
+ * through the slot streams.  cuda_device < 0 is a dry run on the host: plans
+ * are host-only and a solve is simulated as a sleep of dry_run_ns_per_point
+ * per grid point, which exercises queueing and admission without a GPU.    */
+typedef struct tpt_server_s* tpt_server;
+
+typedef struct {
+  int cuda_device;
+  int slots;                    /* concurrent requests on the device, >= 1          */
+  int setup_threads;            /* plan-building threads, >= 1                       */
+  size_t memory_budget;         /* device bytes for admitted requests' buffers       */
+  size_t cache_budget;          /* device bytes for unused cached eigenbases         */
+  double dry_run_ns_per_point;  /* simulated solve time (cuda_device < 0 only)       */
+} tpt_server_config;
+
+typedef struct {
+  int status;                   /* TPT_OK or the solve's / setup's error             */
+  tpt_info info;
+  double t_submit, t_planned, t_admit, t_done;   /* seconds on the server's clock    */
+  size_t device_bytes;          /* bytes charged to the memory budget                */
+} tpt_result;
+
+typedef struct {
+  unsigned long long submitted, completed, rejected;
+  unsigned long long cache_hits, cache_misses;
+  size_t cache_bytes, peak_bytes;
+  int peak_inflight;
+} tpt_serving_stats;
+
+int tpt_server_create(const tpt_server_config* cfg, tpt_server* out);
+
+/* Queue one solve.  desc (its spacing arrays included) is copied; f_host
+ * (Nx*Ny*Nz doubles) must stay valid and phi_host (as many) writable until
+ * the request has finished.  Pinned host memory gives full copy bandwidth.
+ * ticket receives the request's id.                                        */
+int tpt_server_submit(tpt_server s, const tpt_desc* desc, const double* f_host, double* phi_host,
+                      unsigned long long* ticket);
+
+/* Wait up to timeout_s seconds (< 0: no limit) for a request; on completion
+ * fills *result, forgets the ticket and returns TPT_OK (the request's own
+ * outcome is result->status); TPT_PENDING on timeout; INVALID_ARG for an
+ * unknown ticket.                                                           */
+int tpt_server_wait(tpt_server s, unsigned long long ticket, double timeout_s, tpt_result* result);
+
+/* Seconds on the server's steady clock (the clock of tpt_result).           */
+int tpt_server_now(tpt_server s, double* t);
+int tpt_server_stats(tpt_server s, tpt_serving_stats* out);
+
+/* Finishes every submitted request, then stops the threads.                 */
+int tpt_server_destroy(tpt_server s);
 
 /* ---- grid helper -------------------------------------------------------- */
 /* Cell widths and centre spacings of an n-cell grid on [0, L] whose faces are

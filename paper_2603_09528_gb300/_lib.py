@@ -20,6 +20,7 @@ TPT_ERR_NOT_CONVERGED = 5
 TPT_ERR_TIMEOUT = 6
 TPT_ERR_NONFINITE = 7
 TPT_ERR_NUMERICAL = 8
+TPT_PENDING = 9
 
 TPT_BC_PERIODIC, TPT_BC_NEUMANN, TPT_BC_DIRICHLET = 0, 1, 2
 TPT_XFORM_AUTO, TPT_XFORM_GEMM, TPT_XFORM_FFT = 0, 1, 2
@@ -49,6 +50,42 @@ class tpt_info(C.Structure):
         ("rel_residual", C.c_double),
         ("compat_defect", C.c_double),
         ("ms_stage", C.c_float * 8),
+    ]
+
+
+class tpt_server_config(C.Structure):
+    _fields_ = [
+        ("cuda_device", C.c_int),
+        ("slots", C.c_int),
+        ("setup_threads", C.c_int),
+        ("memory_budget", C.c_size_t),
+        ("cache_budget", C.c_size_t),
+        ("dry_run_ns_per_point", C.c_double),
+    ]
+
+
+class tpt_result(C.Structure):
+    _fields_ = [
+        ("status", C.c_int),
+        ("info", tpt_info),
+        ("t_submit", C.c_double),
+        ("t_planned", C.c_double),
+        ("t_admit", C.c_double),
+        ("t_done", C.c_double),
+        ("device_bytes", C.c_size_t),
+    ]
+
+
+class tpt_serving_stats(C.Structure):
+    _fields_ = [
+        ("submitted", C.c_ulonglong),
+        ("completed", C.c_ulonglong),
+        ("rejected", C.c_ulonglong),
+        ("cache_hits", C.c_ulonglong),
+        ("cache_misses", C.c_ulonglong),
+        ("cache_bytes", C.c_size_t),
+        ("peak_bytes", C.c_size_t),
+        ("peak_inflight", C.c_int),
     ]
 
 
@@ -89,6 +126,18 @@ SIGNATURES = [
     ("tpt_batch_infos", C.c_int, [C.c_void_p, C.POINTER(tpt_info), C.POINTER(C.c_int)]),
     ("tpt_batch_launches", C.c_int, [C.c_void_p, C.POINTER(C.c_ulonglong)]),
     ("tpt_batch_destroy", C.c_int, [C.c_void_p]),
+    ("tpt_cache_create", C.c_int, [C.c_int, C.c_size_t, C.POINTER(C.c_void_p)]),
+    ("tpt_plan_create_cached", C.c_int, [C.POINTER(tpt_desc), C.c_void_p, C.POINTER(C.c_void_p)]),
+    ("tpt_cache_stats", C.c_int, [C.c_void_p, C.POINTER(C.c_ulonglong), C.POINTER(C.c_ulonglong),
+                                  C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
+    ("tpt_cache_destroy", C.c_int, [C.c_void_p]),
+    ("tpt_server_create", C.c_int, [C.POINTER(tpt_server_config), C.POINTER(C.c_void_p)]),
+    ("tpt_server_submit", C.c_int, [C.c_void_p, C.POINTER(tpt_desc), C.c_void_p, C.c_void_p,
+                                    C.POINTER(C.c_ulonglong)]),
+    ("tpt_server_wait", C.c_int, [C.c_void_p, C.c_ulonglong, C.c_double, C.POINTER(tpt_result)]),
+    ("tpt_server_now", C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    ("tpt_server_stats", C.c_int, [C.c_void_p, C.POINTER(tpt_serving_stats)]),
+    ("tpt_server_destroy", C.c_int, [C.c_void_p]),
 ]
 
 LIB_PATH = _build.LIB

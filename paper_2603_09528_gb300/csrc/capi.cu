@@ -9,6 +9,7 @@
 #include <new>
 #include <vector>
 
+#include "cache.h"
 #include "tpt_internal.h"
 
 using tpt::Dir1D;
@@ -42,85 +43,29 @@ int cuda_status(cudaError_t e) {
 template <typename T>
 int upload(tpt_plan_s* p, const std::vector<T>& h, T** d) {
   void* ptr = nullptr;
-  const size_t bytes = h.size() * sizeof(T);
-  cudaError_t e = cudaMalloc(&ptr, bytes > 0 ? bytes : 16);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return TPT_ERR_OOM;
-  }
-  p->allocs.push_back(ptr);
+  TPT_TRY(p->arena.upload(h.data(), h.size() * sizeof(T), &ptr));
   *d = static_cast<T*>(ptr);
-  if (bytes) TPT_CUDA(cudaMemcpy(ptr, h.data(), bytes, cudaMemcpyHostToDevice));
   return TPT_OK;
 }
 
 void free_plan(tpt_plan_s* p) {
   if (!p) return;
-  if (p->dev >= 0 && (!p->allocs.empty() || p->h_ring)) {
+  if (p->dev >= 0) {
     DeviceGuard g(p->dev);
     for (cudaEvent_t e : p->ev)
       if (e) cudaEventDestroy(e);
     if (p->mixed.fork) cudaEventDestroy(p->mixed.fork);
     if (p->mixed.join) cudaEventDestroy(p->mixed.join);
     if (p->mixed.side) cudaStreamDestroy(p->mixed.side);
-    for (void* a : p->allocs) cudaFree(a);
+    p->arena.release();
+    if (p->own_stream && p->arena.stream) cudaStreamDestroy(p->arena.stream);
     if (p->h_ring) cudaFreeHost(p->h_ring);
+    cudaGetLastError();
   }
   delete p;
 }
 
 bool on_device(const tpt_plan_s* p) { return p && p->dev >= 0 && p->d_scal; }
-
-// Device matrices of one diagonalised direction for the float64 GEMM roles:
-//   x: C = A B with A = Q^{-1} (forward) or Q (inverse), column-major n x n;
-//   y: C_k = F_k B with B = (Q^{-1})^T (forward) or Q^T (inverse), column-major.
-int upload_basis(tpt_plan_s* p, int d) {
-  const int n = p->n[d];
-  const std::vector<double>& qt = p->eig[d].qt;   // Q~(i, p) at p*n + i
-  const std::vector<double>& dxf = p->dir[d].dxf;
-  std::vector<double> fwd(static_cast<size_t>(n) * n), inv(static_cast<size_t>(n) * n);
-  for (int m = 0; m < n; ++m) {        // mode
-    for (int i = 0; i < n; ++i) {      // grid point
-      const double s = std::sqrt(dxf[i]);
-      const double q = qt[static_cast<size_t>(m) * n + i];
-      const double qinv_mi = q * s;    // Q^{-1}(m, i) = Q~(i, m) sqrt(dx_i)
-      const double q_im = q / s;       // Q(i, m) = Q~(i, m) / sqrt(dx_i)
-      if (d == 0) {
-        fwd[m + static_cast<size_t>(n) * i] = qinv_mi;   // A(m, i), column-major
-        inv[i + static_cast<size_t>(n) * m] = q_im;      // A(i, m)
-      } else {
-        fwd[i + static_cast<size_t>(n) * m] = qinv_mi;   // B(k = i, n = m) = Q^{-1}(m, i)
-        inv[m + static_cast<size_t>(n) * i] = q_im;      // B(k = m, n = i) = Q(i, m)
-      }
-    }
-  }
-  TPT_TRY(upload(p, fwd, &p->ddir[d].fwd));
-  TPT_TRY(upload(p, inv, &p->ddir[d].inv));
-  TPT_TRY(upload(p, p->eig[d].lam, &p->ddir[d].lam));
-  return TPT_OK;
-}
-
-// Trigonometric tables of a Fourier-transformed direction and its eigenvalues.
-int upload_fft(tpt_plan_s* p, int d) {
-  const int n = p->n[d];
-  const long double pi = 3.141592653589793238462643383279502884L;
-  std::vector<double> twc(n / 2 > 0 ? n / 2 : 1, 1.0), tws(twc.size(), 0.0), hc(n), hs(n);
-  for (int m = 0; m < n / 2; ++m) {
-    twc[m] = static_cast<double>(std::cos(2.0L * pi * m / n));
-    tws[m] = static_cast<double>(std::sin(2.0L * pi * m / n));
-  }
-  for (int k = 0; k < n; ++k) {
-    hc[k] = static_cast<double>(std::cos(pi * k / (2.0L * n)));
-    hs[k] = static_cast<double>(std::sin(pi * k / (2.0L * n)));
-  }
-  tpt::FftTables& t = p->fft[d];
-  TPT_TRY(upload(p, twc, &t.twc));
-  TPT_TRY(upload(p, tws, &t.tws));
-  TPT_TRY(upload(p, hc, &t.hc));
-  TPT_TRY(upload(p, hs, &t.hs));
-  TPT_TRY(upload(p, p->eig[d].lam, &p->ddir[d].lam));
-  return TPT_OK;
-}
 
 int apply_transform(const tpt_plan_s* p, int d, bool inverse, const double* in, double* out,
                     bool accumulate, cudaStream_t s) {
@@ -242,6 +187,11 @@ int fp64_solve(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStre
       for (float& t : info->ms_stage) t = 0.0f;
     } else {
       std::memset(info, 0, sizeof(*info));
+      if (!p->h_ring) {   // pinned slots for asynchronous reports, made on first use
+        const size_t ring_bytes = static_cast<size_t>(kRingSlots) * kSlot * sizeof(double);
+        TPT_CUDA(cudaMallocHost(reinterpret_cast<void**>(&p->h_ring), ring_bytes));
+        std::memset(p->h_ring, 0, ring_bytes);
+      }
       double* slot = p->h_ring + static_cast<size_t>(p->ring_next) * kSlot;
       p->ring_next = (p->ring_next + 1) % kRingSlots;
       TPT_CUDA(cudaMemcpyAsync(slot, ds, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -251,6 +201,135 @@ int fp64_solve(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStre
     }
   }
   return status;
+}
+
+// Plan creation: host setup (1D operators, eigenbases), then the device
+// tables.  With a cache the eigenbases of x and y (and their device tables)
+// are shared with every plan that has the same direction, and the plan's own
+// tables are stream-ordered allocations from the cache's pool, so creating and
+// destroying plans does not synchronise the device.
+int create_plan_impl(const tpt_desc* desc, int cuda_device, tpt::BasisCache* cache, tpt_plan* out) {
+  if (!out) return TPT_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!desc) return TPT_ERR_INVALID_ARG;
+  for (int d = 0; d < 3; ++d)
+    if (desc->n[d] < 1 || !desc->dxf[d] || !desc->dxc[d]) return TPT_ERR_INVALID_ARG;
+  if (!std::isfinite(desc->alpha) || !std::isfinite(desc->beta)) return TPT_ERR_INVALID_ARG;
+  if (desc->alpha == 0.0 && desc->beta == 0.0) return TPT_ERR_INVALID_ARG;
+  if (desc->max_refine < 0 || desc->max_refine > 1000) return TPT_ERR_INVALID_ARG;
+  if (desc->precision < TPT_PREC_FP64 || desc->precision > TPT_PREC_MIXED_TF32)
+    return TPT_ERR_INVALID_ARG;
+  if (!std::isfinite(desc->rtol) || desc->rtol < 0.0) return TPT_ERR_INVALID_ARG;
+  for (int d = 0; d < 2; ++d)
+    if (desc->xform[d] < TPT_XFORM_AUTO || desc->xform[d] > TPT_XFORM_FFT) return TPT_ERR_INVALID_ARG;
+
+  tpt_plan_s* p = new (std::nothrow) tpt_plan_s();
+  if (!p) return TPT_ERR_OOM;
+  p->dev = cuda_device;
+  auto fail = [&](int st) {
+    free_plan(p);
+    return st;
+  };
+  for (int d = 0; d < 3; ++d) {
+    p->n[d] = desc->n[d];
+    int st = tpt::build_dir(desc->n[d], desc->dxf[d], desc->dxc[d], desc->bc[d], &p->dir[d]);
+    if (st != TPT_OK) return fail(st);
+  }
+  if (p->dir[2].periodic) return fail(TPT_ERR_UNSUPPORTED);
+  for (int d = 0; d < 2; ++d) {
+    // Fourier-based transforms: float64 path, uniform power-of-two directions
+    const bool ok = tpt::fft_supported(p->dir[d]) && desc->precision == TPT_PREC_FP64;
+    if (desc->xform[d] == TPT_XFORM_FFT && !ok) return fail(TPT_ERR_UNSUPPORTED);
+    p->xform[d] = (desc->xform[d] == TPT_XFORM_FFT || (desc->xform[d] == TPT_XFORM_AUTO && ok))
+                      ? TPT_XFORM_FFT
+                      : TPT_XFORM_GEMM;
+  }
+  p->alpha = desc->alpha;
+  p->beta = desc->beta;
+  p->precision = desc->precision;
+  p->rtol = desc->rtol;
+  p->max_refine = desc->max_refine;
+  for (int d = 0; d < 2; ++d) {
+    const bool fft = p->xform[d] == TPT_XFORM_FFT;
+    if (cache) {
+      int st = TPT_OK;
+      p->basis[d] = cache->get(p->dir[d], p->xform[d], &st);
+      if (!p->basis[d]) return fail(st);
+      p->eig[d].lam = p->basis[d]->eig.lam;   // the eigenvectors stay in the shared entry
+      p->eig[d].null_mode = p->basis[d]->eig.null_mode;
+      p->fft[d].kind = p->basis[d]->fft_kind;
+      p->null_g[d] = p->basis[d]->null_g;
+    } else {
+      int st = fft ? tpt::fft_dir(p->dir[d], &p->eig[d], &p->fft[d].kind) : tpt::eigen_dir(p->dir[d], &p->eig[d]);
+      if (st != TPT_OK) return fail(st);
+      p->null_g[d] = tpt::null_fhat(p->dir[d], p->eig[d], fft);
+    }
+  }
+  p->singular = (p->alpha == 0.0) && p->dir[0].has_null() && p->dir[1].has_null() &&
+                p->dir[2].has_null();
+  p->null_i = p->eig[0].null_mode;
+  p->null_j = p->eig[1].null_mode;
+  p->vol = 1.0;
+  for (int d = 0; d < 3; ++d) {
+    double L = 0.0;
+    for (double w : p->dir[d].dxf) L += w;
+    p->vol *= L;
+  }
+  if (cuda_device < 0) {   // host-only plan: setup tables for inspection, no device state
+    *out = p;
+    return TPT_OK;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(TPT_ERR_CUDA);
+  }
+  if (cuda_device >= ndev) return fail(TPT_ERR_INVALID_ARG);
+  DeviceGuard guard(cuda_device);
+  if (cache) {
+    p->arena.pool = cache->pool();
+    p->arena.stream = cache->stream();
+  } else {
+    if (cudaStreamCreateWithFlags(&p->arena.stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(TPT_ERR_CUDA);
+    }
+    p->own_stream = true;
+  }
+  for (int d = 0; d < 2; ++d) {
+    int st = TPT_OK;
+    if (cache) {
+      st = cache->device_fp64(*p->basis[d], d, &p->ddir[d], &p->fft[d]);
+    } else if (p->xform[d] == TPT_XFORM_FFT) {
+      st = tpt::upload_fft_tables(p->arena, p->n[d], p->eig[d], &p->fft[d], &p->ddir[d].lam);
+    } else {
+      st = tpt::upload_fp64_basis(p->arena, p->eig[d], p->dir[d].dxf, d, &p->ddir[d]);
+    }
+    if (st != TPT_OK) return fail(st);
+  }
+  for (int d = 0; d < 3; ++d) {
+    const Dir1D& dd = p->dir[d];
+    std::vector<double> rows(3 * static_cast<size_t>(dd.n));
+    std::copy(dd.a.begin(), dd.a.end(), rows.begin());
+    std::copy(dd.b.begin(), dd.b.end(), rows.begin() + dd.n);
+    std::copy(dd.c.begin(), dd.c.end(), rows.begin() + 2 * dd.n);
+    int st = upload(p, rows, &p->d_rows[d]);
+    if (st == TPT_OK) st = upload(p, dd.dxf, &p->d_dxf[d]);
+    if (st != TPT_OK) return fail(st);
+  }
+  std::vector<double> scal(16, 0.0);
+  int st = upload(p, scal, &p->d_scal);
+  if (st != TPT_OK) return fail(st);
+  if (p->precision != TPT_PREC_FP64) {
+    st = tpt::mixed_setup(p);
+    if (st != TPT_OK) return fail(st);
+  }
+  if (cudaStreamSynchronize(p->arena.stream) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(TPT_ERR_CUDA);
+  }
+  *out = p;
+  return TPT_OK;
 }
 
 }  // namespace
@@ -265,6 +344,10 @@ std::atomic<unsigned long long> g_launches{0};
 void note_launch(unsigned long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 void forget_launches(unsigned long long k) { g_launches.fetch_sub(k, std::memory_order_relaxed); }
+
+int create_plan(const tpt_desc* desc, int cuda_device, BasisCache* cache, tpt_plan* out) {
+  return create_plan_impl(desc, cuda_device, cache, out);
+}
 
 int solve_enqueue(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStream_t s) {
   if (p->precision != TPT_PREC_FP64) return mixed_enqueue(p, f, phi, work, s);
@@ -301,6 +384,7 @@ const char* tpt_status_string(int status) {
     case TPT_ERR_TIMEOUT: return "device wait timed out";
     case TPT_ERR_NONFINITE: return "non-finite value in right-hand side or residual";
     case TPT_ERR_NUMERICAL: return "numerical failure in setup";
+    case TPT_PENDING: return "request not finished";
     default: return "unknown status";
   }
 }
@@ -316,108 +400,52 @@ int tpt_grid_tanh(int n, double L, double stretch, double* dxf_out, double* dxc_
 }
 
 int tpt_plan_create(const tpt_desc* desc, int cuda_device, tpt_plan* out) {
+  return create_plan_impl(desc, cuda_device, nullptr, out);
+}
+
+int tpt_cache_create(int cuda_device, size_t budget_bytes, tpt_cache* out) {
   if (!out) return TPT_ERR_INVALID_ARG;
   *out = nullptr;
-  if (!desc) return TPT_ERR_INVALID_ARG;
-  for (int d = 0; d < 3; ++d)
-    if (desc->n[d] < 1 || !desc->dxf[d] || !desc->dxc[d]) return TPT_ERR_INVALID_ARG;
-  if (!std::isfinite(desc->alpha) || !std::isfinite(desc->beta)) return TPT_ERR_INVALID_ARG;
-  if (desc->alpha == 0.0 && desc->beta == 0.0) return TPT_ERR_INVALID_ARG;
-  if (desc->max_refine < 0 || desc->max_refine > 1000) return TPT_ERR_INVALID_ARG;
-  if (desc->precision < TPT_PREC_FP64 || desc->precision > TPT_PREC_MIXED_TF32)
-    return TPT_ERR_INVALID_ARG;
-  for (int d = 0; d < 2; ++d)
-    if (desc->xform[d] < TPT_XFORM_AUTO || desc->xform[d] > TPT_XFORM_FFT) return TPT_ERR_INVALID_ARG;
-
-  tpt_plan_s* p = new (std::nothrow) tpt_plan_s();
-  if (!p) return TPT_ERR_OOM;
-  p->dev = cuda_device;
-  auto fail = [&](int st) {
-    free_plan(p);
-    return st;
-  };
-  for (int d = 0; d < 3; ++d) {
-    p->n[d] = desc->n[d];
-    int st = tpt::build_dir(desc->n[d], desc->dxf[d], desc->dxc[d], desc->bc[d], &p->dir[d]);
-    if (st != TPT_OK) return fail(st);
-  }
-  if (p->dir[2].periodic) return fail(TPT_ERR_UNSUPPORTED);
-  for (int d = 0; d < 2; ++d) {
-    // Fourier-based transforms: float64 path, uniform power-of-two directions
-    const bool ok = tpt::fft_supported(p->dir[d]) && desc->precision == TPT_PREC_FP64;
-    if (desc->xform[d] == TPT_XFORM_FFT && !ok) return fail(TPT_ERR_UNSUPPORTED);
-    p->xform[d] = (desc->xform[d] == TPT_XFORM_FFT || (desc->xform[d] == TPT_XFORM_AUTO && ok))
-                      ? TPT_XFORM_FFT
-                      : TPT_XFORM_GEMM;
-  }
-  p->alpha = desc->alpha;
-  p->beta = desc->beta;
-  p->precision = desc->precision;
-  p->rtol = desc->rtol;
-  p->max_refine = desc->max_refine;
-  for (int d = 0; d < 2; ++d) {
-    int st = (p->xform[d] == TPT_XFORM_FFT) ? tpt::fft_dir(p->dir[d], &p->eig[d], &p->fft[d].kind)
-                                           : tpt::eigen_dir(p->dir[d], &p->eig[d]);
-    if (st != TPT_OK) return fail(st);
-    // f-hat of the constant 1 on the null mode: N for the Fourier transforms,
-    // sum_i Q~[i, null] sqrt(dx_i) for the eigenbasis
-    if (p->xform[d] == TPT_XFORM_FFT) {
-      p->null_g[d] = p->n[d];
-    } else {
-      double g = 0.0;
-      for (int i = 0; i < p->n[d]; ++i) g += p->eig[d].qt[i] * std::sqrt(p->dir[d].dxf[i]);
-      p->null_g[d] = g;
+  if (cuda_device >= 0) {
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+      cudaGetLastError();
+      return TPT_ERR_CUDA;
     }
+    if (cuda_device >= ndev) return TPT_ERR_INVALID_ARG;
   }
-  p->singular = (p->alpha == 0.0) && p->dir[0].has_null() && p->dir[1].has_null() &&
-                p->dir[2].has_null();
-  p->null_i = p->eig[0].null_mode;
-  p->null_j = p->eig[1].null_mode;
-  p->vol = 1.0;
-  for (int d = 0; d < 3; ++d) {
-    double L = 0.0;
-    for (double w : p->dir[d].dxf) L += w;
-    p->vol *= L;
+  tpt_cache c = new (std::nothrow) tpt_cache_s(cuda_device, budget_bytes);
+  if (!c) return TPT_ERR_OOM;
+  int st = TPT_OK;
+  {
+    DeviceGuard guard(cuda_device >= 0 ? cuda_device : 0);
+    st = c->impl.init();
   }
-  if (cuda_device < 0) {   // host-only plan: setup tables for inspection, no device state
-    *out = p;
-    return TPT_OK;
+  if (st != TPT_OK) {
+    delete c;
+    return st;
   }
-  int ndev = 0;
-  if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(TPT_ERR_CUDA);
-  }
-  if (cuda_device >= ndev) return fail(TPT_ERR_INVALID_ARG);
-  DeviceGuard guard(cuda_device);
-  for (int d = 0; d < 2; ++d) {
-    int st = (p->xform[d] == TPT_XFORM_FFT) ? upload_fft(p, d) : upload_basis(p, d);
-    if (st != TPT_OK) return fail(st);
-  }
-  for (int d = 0; d < 3; ++d) {
-    const Dir1D& dd = p->dir[d];
-    std::vector<double> rows(3 * static_cast<size_t>(dd.n));
-    std::copy(dd.a.begin(), dd.a.end(), rows.begin());
-    std::copy(dd.b.begin(), dd.b.end(), rows.begin() + dd.n);
-    std::copy(dd.c.begin(), dd.c.end(), rows.begin() + 2 * dd.n);
-    int st = upload(p, rows, &p->d_rows[d]);
-    if (st == TPT_OK) st = upload(p, dd.dxf, &p->d_dxf[d]);
-    if (st != TPT_OK) return fail(st);
-  }
-  std::vector<double> scal(16, 0.0);
-  int st = upload(p, scal, &p->d_scal);
-  if (st != TPT_OK) return fail(st);
-  const size_t ring_bytes = static_cast<size_t>(kRingSlots) * kSlot * sizeof(double);
-  if (cudaMallocHost(reinterpret_cast<void**>(&p->h_ring), ring_bytes) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(TPT_ERR_OOM);
-  }
-  std::memset(p->h_ring, 0, ring_bytes);
-  if (p->precision != TPT_PREC_FP64) {
-    st = tpt::mixed_setup(p);
-    if (st != TPT_OK) return fail(st);
-  }
-  *out = p;
+  *out = c;
+  return TPT_OK;
+}
+
+int tpt_plan_create_cached(const tpt_desc* desc, tpt_cache cache, tpt_plan* out) {
+  if (!cache) return TPT_ERR_INVALID_ARG;
+  const int st = create_plan_impl(desc, cache->impl.device(), &cache->impl, out);
+  cache->impl.trim();
+  return st;
+}
+
+int tpt_cache_stats(tpt_cache cache, unsigned long long* hits, unsigned long long* misses, size_t* device_bytes,
+                    size_t* entries) {
+  if (!cache) return TPT_ERR_INVALID_ARG;
+  cache->impl.stats(hits, misses, device_bytes, entries);
+  return TPT_OK;
+}
+
+int tpt_cache_destroy(tpt_cache cache) {
+  if (!cache) return TPT_ERR_INVALID_ARG;
+  delete cache;
   return TPT_OK;
 }
 

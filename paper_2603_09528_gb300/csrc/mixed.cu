@@ -25,6 +25,7 @@
 #include <cstring>
 #include <vector>
 
+#include "cache.h"
 #include "ptx.h"
 #include "tc.h"
 #include "tpt_internal.h"
@@ -819,23 +820,13 @@ int st_of(cudaError_t e) {
   } while (0)
 #define MX_CUDA(expr) MX_TRY(st_of(expr))
 
-int dev_alloc(tpt_plan_s* p, size_t bytes, void** out) {
-  void* ptr = nullptr;
-  if (cudaMalloc(&ptr, bytes ? bytes : 16) != cudaSuccess) {
-    cudaGetLastError();
-    return TPT_ERR_OOM;
-  }
-  p->allocs.push_back(ptr);
-  *out = ptr;
-  return TPT_OK;
-}
+int dev_alloc(tpt_plan_s* p, size_t bytes, void** out) { return p->arena.alloc(bytes, out); }
 
 template <typename T>
 int upload_vec(tpt_plan_s* p, const std::vector<T>& h, T** d) {
   void* ptr = nullptr;
-  MX_TRY(dev_alloc(p, h.size() * sizeof(T), &ptr));
+  MX_TRY(p->arena.upload(h.data(), h.size() * sizeof(T), &ptr));
   *d = static_cast<T*>(ptr);
-  if (!h.empty()) MX_CUDA(cudaMemcpy(ptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
   return TPT_OK;
 }
 
@@ -1281,36 +1272,51 @@ int solve_fmt(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStrea
 
 }  // namespace
 
+int mixed_pack_basis(DevArena& a, int fmt, const Eigen1D& e, const std::vector<double>& dxf, int dev,
+                     void* q[2][2], float** lam_f) {
+  const int n = static_cast<int>(dxf.size());
+  const int ld = (n + 7) & ~7;
+  const int np = nplanes(fmt);
+  const size_t eb = elem_bytes(fmt);
+  std::vector<double> fwd(static_cast<size_t>(n) * n), inv(static_cast<size_t>(n) * n);
+  for (int mode = 0; mode < n; ++mode)
+    for (int i = 0; i < n; ++i) {
+      const double s = std::sqrt(dxf[i]);
+      const double v = e.qt[static_cast<size_t>(mode) * n + i];
+      fwd[static_cast<size_t>(mode) * n + i] = v * s;   // Q^{-1}(mode, i), row-major
+      inv[static_cast<size_t>(i) * n + mode] = v / s;   // Q(i, mode), row-major
+    }
+  for (int role = 0; role < 2; ++role) {
+    const std::vector<double>& src = role == 0 ? fwd : inv;
+    void* stage = nullptr;
+    MX_TRY(a.upload(src.data(), src.size() * sizeof(double), &stage));
+    q[role][0] = q[role][1] = nullptr;
+    for (int pl = 0; pl < np; ++pl) {
+      MX_TRY(a.alloc(eb * static_cast<size_t>(n) * ld, &q[role][pl]));
+      MX_CUDA(cudaMemsetAsync(q[role][pl], 0, eb * static_cast<size_t>(n) * ld, a.stream));
+    }
+    MX_CUDA(pack_operand(fmt, n, n, ld, static_cast<const double*>(stage), q[role][0], q[role][1], dev, a.stream));
+  }
+  std::vector<float> lf(e.lam.begin(), e.lam.end());
+  void* lp = nullptr;
+  MX_TRY(a.upload(lf.data(), lf.size() * sizeof(float), &lp));
+  *lam_f = static_cast<float*>(lp);
+  // the host staging vectors die here
+  MX_CUDA(cudaStreamSynchronize(a.stream));
+  return TPT_OK;
+}
+
 int mixed_setup(tpt_plan_s* p) {
   MixedTables& m = p->mixed;
   m.fmt = fmt_of(p->precision);
   m.ldx = (p->n[0] + 7) & ~7;
   m.ldy = (p->n[1] + 7) & ~7;
-  const int np = nplanes(m.fmt);
-  const size_t eb = elem_bytes(m.fmt);
   for (int d = 0; d < 2; ++d) {
-    const int n = p->n[d];
-    const int ld = d == 0 ? m.ldx : m.ldy;
-    const std::vector<double>& qt = p->eig[d].qt;
-    const std::vector<double>& dxf = p->dir[d].dxf;
-    std::vector<double> fwd(static_cast<size_t>(n) * n), inv(static_cast<size_t>(n) * n);
-    for (int mode = 0; mode < n; ++mode)
-      for (int i = 0; i < n; ++i) {
-        const double s = std::sqrt(dxf[i]);
-        const double q = qt[static_cast<size_t>(mode) * n + i];
-        fwd[static_cast<size_t>(mode) * n + i] = q * s;   // Q^{-1}(mode, i), row-major
-        inv[static_cast<size_t>(i) * n + mode] = q / s;   // Q(i, mode), row-major
-      }
-    for (int role = 0; role < 2; ++role) {
-      double* stage = nullptr;
-      MX_TRY(upload_vec(p, role == 0 ? fwd : inv, &stage));
-      for (int pl = 0; pl < np; ++pl) MX_TRY(dev_alloc(p, eb * static_cast<size_t>(n) * ld, &m.q[d][role][pl]));
-      MX_CUDA(cudaMemset(m.q[d][role][0], 0, eb * static_cast<size_t>(n) * ld));
-      if (np == 2) MX_CUDA(cudaMemset(m.q[d][role][1], 0, eb * static_cast<size_t>(n) * ld));
-      MX_CUDA(pack_operand(m.fmt, n, n, ld, stage, m.q[d][role][0], m.q[d][role][1], p->dev, 0));
-    }
-    std::vector<float> lf(p->eig[d].lam.begin(), p->eig[d].lam.end());
-    MX_TRY(upload_vec(p, lf, &m.lam_f[d]));
+    void* q[2][2] = {};
+    if (p->basis[d]) MX_TRY(entry_mixed_tables(*p->basis[d], m.fmt, p->dev, q, &m.lam_f[d]));
+    else MX_TRY(mixed_pack_basis(p->arena, m.fmt, p->eig[d], p->dir[d].dxf, p->dev, q, &m.lam_f[d]));
+    for (int r = 0; r < 2; ++r)
+      for (int pl = 0; pl < 2; ++pl) m.q[d][r][pl] = q[r][pl];
   }
   {
     const Dir1D& z = p->dir[2];
@@ -1352,7 +1358,7 @@ int mixed_setup(tpt_plan_s* p) {
   MX_CUDA(cudaStreamCreateWithFlags(&m.side, cudaStreamNonBlocking));
   MX_CUDA(cudaEventCreateWithFlags(&m.fork, cudaEventDisableTiming));
   MX_CUDA(cudaEventCreateWithFlags(&m.join, cudaEventDisableTiming));
-  MX_CUDA(cudaDeviceSynchronize());
+  MX_CUDA(cudaStreamSynchronize(p->arena.stream));
   return TPT_OK;
 }
 
@@ -1376,7 +1382,9 @@ int mixed_set_beta(tpt_plan_s* p) {
       split_ld(beta * w, &t[4 * n + i], &t[5 * n + i]);
     }
     m.has_w[d] = hw;
-    MX_CUDA(cudaMemcpy(m.dfrows[d], t.data(), t.size() * sizeof(float), cudaMemcpyHostToDevice));
+    MX_CUDA(cudaMemcpyAsync(m.dfrows[d], t.data(), t.size() * sizeof(float), cudaMemcpyHostToDevice,
+                            p->arena.stream));
+    MX_CUDA(cudaStreamSynchronize(p->arena.stream));   // t dies here; the next solve may run on any stream
   }
   m.rows_beta = p->beta;
   return TPT_OK;

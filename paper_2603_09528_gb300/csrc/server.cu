@@ -1,0 +1,309 @@
+// Request server with continuous batching on one device.  Declarations and
+// contracts: include/tpt.h.
+//
+//   submit ──> setup queue ──(setup threads: plan through the eigenbasis
+//              cache)──> ready set (by arrival) ──(slot threads: admit the
+//              oldest ready request once it fits the memory budget)──> H2D,
+//              solve, D2H on the slot's stream ──> done
+//
+// Every slot owns a CUDA stream, so the solves of admitted requests overlap on
+// the device; a request that arrives while others run is admitted as soon as
+// a slot and enough of the budget are free.  Request buffers are
+// stream-ordered allocations from the cache's memory pool and plans are
+// created and destroyed without synchronising the device, so admitting or
+// retiring one request never stalls the others.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "cache.h"
+#include "tpt_internal.h"
+
+namespace {
+
+struct Request {
+  unsigned long long id = 0;
+  tpt_desc desc{};
+  std::vector<double> dxf[3], dxc[3];    // the descriptor's arrays, copied
+  const double* f_host = nullptr;
+  double* phi_host = nullptr;
+  tpt_plan plan = nullptr;
+  size_t npts = 0, work_bytes = 0, need = 0;
+  tpt_result res{};
+  bool done = false;
+};
+
+int cuda_st(cudaError_t e) {
+  if (e == cudaSuccess) return TPT_OK;
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? TPT_ERR_OOM : TPT_ERR_CUDA;
+}
+
+}  // namespace
+
+struct tpt_server_s {
+  tpt_server_config cfg{};
+  tpt::BasisCache cache;
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+  std::mutex mu;
+  std::condition_variable cv_setup, cv_ready, cv_done;
+  std::deque<Request*> setup_q;
+  std::map<unsigned long long, Request*> ready;   // planned, ordered by arrival
+  std::unordered_map<unsigned long long, std::unique_ptr<Request>> reqs;
+  unsigned long long next_id = 1;
+  size_t in_use = 0, peak = 0;
+  int inflight = 0, peak_inflight = 0;
+  unsigned long long submitted = 0, finished = 0, rejected = 0;
+  bool stop = false;
+  std::vector<std::thread> threads;
+
+  explicit tpt_server_s(const tpt_server_config& c) : cfg(c), cache(c.cuda_device, c.cache_budget) {}
+
+  double now() const {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+
+  // caller holds mu
+  void finish(Request* r, int status) {
+    r->res.status = status;
+    r->res.t_done = now();
+    r->done = true;
+    ++finished;
+    if (status != TPT_OK && status != TPT_ERR_NOT_CONVERGED && r->res.t_admit == 0.0) ++rejected;
+    cv_done.notify_all();
+  }
+
+  void setup_loop() {
+    if (cfg.cuda_device >= 0) cudaSetDevice(cfg.cuda_device);
+    for (;;) {
+      Request* r = nullptr;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv_setup.wait(lk, [&] { return stop || !setup_q.empty(); });
+        if (setup_q.empty()) return;   // stop with nothing left to plan
+        r = setup_q.front();
+        setup_q.pop_front();
+      }
+      tpt_plan p = nullptr;
+      int st = tpt::create_plan(&r->desc, cfg.cuda_device, &cache, &p);
+      size_t wb = 0;
+      if (st == TPT_OK) st = tpt_workspace_bytes(p, &wb);
+      std::lock_guard<std::mutex> g(mu);
+      r->res.t_planned = now();
+      if (st != TPT_OK) {
+        if (p) tpt_plan_destroy(p);
+        finish(r, st);
+        continue;
+      }
+      r->plan = p;
+      r->work_bytes = wb;
+      r->need = 2 * r->npts * sizeof(double) + wb + 3 * 256;
+      r->res.device_bytes = r->need;
+      if (r->need > cfg.memory_budget) {   // can never fit: reject rather than wait forever
+        tpt_plan_destroy(p);
+        r->plan = nullptr;
+        finish(r, TPT_ERR_OOM);
+        continue;
+      }
+      ready.emplace(r->id, r);
+      cv_ready.notify_all();
+    }
+  }
+
+  // H2D, solve, D2H on the slot's stream; returns the request's status.
+  int execute(Request* r, cudaStream_t s) {
+    if (cfg.cuda_device < 0) {   // dry run: the solve is a sleep
+      const double ns = cfg.dry_run_ns_per_point * static_cast<double>(r->npts);
+      std::this_thread::sleep_for(std::chrono::nanoseconds(static_cast<long long>(ns)));
+      return TPT_OK;
+    }
+    const size_t bytes = r->npts * sizeof(double);
+    void* buf[3] = {nullptr, nullptr, nullptr};
+    const size_t sz[3] = {bytes + 256, bytes + 256, r->work_bytes + 256};
+    int st = TPT_OK;
+    for (int i = 0; i < 3 && st == TPT_OK; ++i)
+      st = cuda_st(cudaMallocFromPoolAsync(&buf[i], sz[i], cache.pool(), s));
+    auto aligned = [](void* p) {
+      return reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(p) + 255) & ~static_cast<uintptr_t>(255));
+    };
+    if (st == TPT_OK) {
+      double* f = reinterpret_cast<double*>(aligned(buf[0]));
+      double* phi = reinterpret_cast<double*>(aligned(buf[1]));
+      void* work = aligned(buf[2]);
+      st = cuda_st(cudaMemcpyAsync(f, r->f_host, bytes, cudaMemcpyHostToDevice, s));
+      if (st == TPT_OK) {
+        st = tpt_solve(r->plan, f, phi, work, s, &r->res.info);
+        if (st == TPT_OK || st == TPT_ERR_NOT_CONVERGED) {
+          const int cs = cuda_st(cudaMemcpyAsync(r->phi_host, phi, bytes, cudaMemcpyDeviceToHost, s));
+          if (cs != TPT_OK) st = cs;
+        }
+      }
+    }
+    for (void* b : buf)
+      if (b) cudaFreeAsync(b, s);
+    const int ss = cuda_st(cudaStreamSynchronize(s));
+    return st != TPT_OK ? st : ss;
+  }
+
+  void slot_loop() {
+    cudaStream_t s = nullptr;
+    if (cfg.cuda_device >= 0) {
+      cudaSetDevice(cfg.cuda_device);
+      if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) cudaGetLastError();
+    }
+    for (;;) {
+      Request* r = nullptr;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv_ready.wait(lk, [&] {
+          if (!ready.empty() && in_use + ready.begin()->second->need <= cfg.memory_budget) return true;
+          return stop && ready.empty() && setup_q.empty();
+        });
+        if (ready.empty()) break;
+        r = ready.begin()->second;   // the oldest planned request
+        ready.erase(ready.begin());
+        in_use += r->need;
+        peak = in_use > peak ? in_use : peak;
+        ++inflight;
+        peak_inflight = inflight > peak_inflight ? inflight : peak_inflight;
+        r->res.t_admit = now();
+      }
+      const int st = (cfg.cuda_device >= 0 && !s) ? TPT_ERR_CUDA : execute(r, s);
+      tpt_plan p = r->plan;
+      r->plan = nullptr;
+      if (p) tpt_plan_destroy(p);   // stream-ordered frees: no device synchronisation
+      cache.trim();
+      {
+        std::lock_guard<std::mutex> g(mu);
+        in_use -= r->need;
+        --inflight;
+        finish(r, st);
+        cv_ready.notify_all();      // freed memory may admit the next request
+      }
+    }
+    if (s) cudaStreamDestroy(s);
+  }
+};
+
+extern "C" {
+
+int tpt_server_create(const tpt_server_config* cfg, tpt_server* out) {
+  if (!out) return TPT_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!cfg || cfg->slots < 1 || cfg->setup_threads < 1 || cfg->memory_budget == 0 || cfg->slots > 64 ||
+      cfg->setup_threads > 64 || !(cfg->dry_run_ns_per_point >= 0.0))
+    return TPT_ERR_INVALID_ARG;
+  if (cfg->cuda_device >= 0) {
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+      cudaGetLastError();
+      return TPT_ERR_CUDA;
+    }
+    if (cfg->cuda_device >= ndev) return TPT_ERR_INVALID_ARG;
+    cudaSetDevice(cfg->cuda_device);
+  }
+  tpt_server s = new (std::nothrow) tpt_server_s(*cfg);
+  if (!s) return TPT_ERR_OOM;
+  const int st = s->cache.init();
+  if (st != TPT_OK) {
+    delete s;
+    return st;
+  }
+  for (int i = 0; i < cfg->setup_threads; ++i) s->threads.emplace_back([s] { s->setup_loop(); });
+  for (int i = 0; i < cfg->slots; ++i) s->threads.emplace_back([s] { s->slot_loop(); });
+  *out = s;
+  return TPT_OK;
+}
+
+int tpt_server_submit(tpt_server s, const tpt_desc* desc, const double* f_host, double* phi_host,
+                      unsigned long long* ticket) {
+  if (!s || !desc || !f_host || !phi_host || !ticket) return TPT_ERR_INVALID_ARG;
+  auto r = std::unique_ptr<Request>(new (std::nothrow) Request);
+  if (!r) return TPT_ERR_OOM;
+  r->desc = *desc;
+  size_t npts = 1;
+  for (int d = 0; d < 3; ++d) {
+    if (desc->n[d] < 1 || !desc->dxf[d] || !desc->dxc[d]) return TPT_ERR_INVALID_ARG;
+    r->dxf[d].assign(desc->dxf[d], desc->dxf[d] + desc->n[d]);
+    r->dxc[d].assign(desc->dxc[d], desc->dxc[d] + desc->n[d] + 1);
+    r->desc.dxf[d] = r->dxf[d].data();
+    r->desc.dxc[d] = r->dxc[d].data();
+    npts *= static_cast<size_t>(desc->n[d]);
+  }
+  r->npts = npts;
+  r->f_host = f_host;
+  r->phi_host = phi_host;
+  std::lock_guard<std::mutex> g(s->mu);
+  if (s->stop) return TPT_ERR_INVALID_ARG;
+  r->id = s->next_id++;
+  r->res.t_submit = s->now();
+  *ticket = r->id;
+  s->setup_q.push_back(r.get());
+  s->reqs.emplace(r->id, std::move(r));
+  ++s->submitted;
+  s->cv_setup.notify_one();
+  return TPT_OK;
+}
+
+int tpt_server_wait(tpt_server s, unsigned long long ticket, double timeout_s, tpt_result* result) {
+  if (!s || !result) return TPT_ERR_INVALID_ARG;
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(ticket);
+  if (it == s->reqs.end()) return TPT_ERR_INVALID_ARG;
+  Request* r = it->second.get();
+  auto pred = [&] { return r->done; };
+  if (timeout_s < 0.0) {
+    s->cv_done.wait(lk, pred);
+  } else if (!s->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), pred)) {
+    return TPT_PENDING;
+  }
+  *result = r->res;
+  s->reqs.erase(it);
+  return TPT_OK;
+}
+
+int tpt_server_now(tpt_server s, double* t) {
+  if (!s || !t) return TPT_ERR_INVALID_ARG;
+  *t = s->now();
+  return TPT_OK;
+}
+
+int tpt_server_stats(tpt_server s, tpt_serving_stats* out) {
+  if (!s || !out) return TPT_ERR_INVALID_ARG;
+  std::memset(out, 0, sizeof(*out));
+  s->cache.stats(&out->cache_hits, &out->cache_misses, &out->cache_bytes, nullptr);
+  std::lock_guard<std::mutex> g(s->mu);
+  out->submitted = s->submitted;
+  out->completed = s->finished;
+  out->rejected = s->rejected;
+  out->peak_bytes = s->peak;
+  out->peak_inflight = s->peak_inflight;
+  return TPT_OK;
+}
+
+int tpt_server_destroy(tpt_server s) {
+  if (!s) return TPT_ERR_INVALID_ARG;
+  {
+    std::unique_lock<std::mutex> lk(s->mu);
+    s->cv_done.wait(lk, [&] { return s->finished == s->submitted; });
+    s->stop = true;
+  }
+  s->cv_setup.notify_all();
+  s->cv_ready.notify_all();
+  for (std::thread& t : s->threads) t.join();
+  if (s->cfg.cuda_device >= 0) cudaSetDevice(s->cfg.cuda_device);
+  delete s;
+  return TPT_OK;
+}
+
+}  // extern "C"

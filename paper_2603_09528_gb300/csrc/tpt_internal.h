@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
+#include <memory>
 #include <vector>
 
 #include "../../include/tpt.h"
@@ -44,6 +45,25 @@ bool fft_supported(const Dir1D& d);
 int fft_dir(const Dir1D& d, Eigen1D* out, int* kind);
 int eigen_dir(const Dir1D& d, Eigen1D* out);
 int grid_tanh(int n, double L, double stretch, double* dxf, double* dxc);
+
+// ----------------------------------------------------------------- device memory
+// Device tables of a plan or of a shared eigenbasis.  With a pool the tables
+// are stream-ordered allocations on `stream` (no device-wide synchronisation
+// when they are created or freed, so plans can come and go while other solves
+// run); otherwise plain cudaMalloc.  Uploads are asynchronous copies on
+// `stream`; the owner synchronises `stream` before the tables are used.
+struct DevArena {
+  cudaMemPool_t pool = nullptr;
+  cudaStream_t stream = nullptr;
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  int alloc(size_t n, void** out);
+  int upload(const void* h, size_t n, void** out);
+  void release();
+};
+
+struct DirEntry;      // shared eigenbasis of one direction (cache.cu)
+class BasisCache;
 
 // ----------------------------------------------------------------- device plan
 // operand formats of the low-precision path: bf16 hi/lo pair, bf16, float32
@@ -120,7 +140,9 @@ struct tpt_plan_s {
   int stage_timing = 0;           // record per-stage CUDA events in tpt_solve
   cudaEvent_t ev[12] = {};        // stage boundaries (created on first use)
   unsigned generation = 0;        // bumped when coefficients or tiles change
-  std::vector<void*> allocs;      // every device allocation owned by the plan
+  tpt::DevArena arena;            // every device table owned by the plan
+  bool own_stream = false;        // arena.stream was created for this plan
+  std::shared_ptr<tpt::DirEntry> basis[2];   // shared eigenbases of x and y (cached plans)
 };
 
 namespace tpt {

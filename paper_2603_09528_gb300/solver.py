@@ -86,11 +86,16 @@ class Plan:
     """tpt_plan_create / tpt_solve / tpt_plan_destroy on one CUDA device."""
 
     def __init__(self, n, dxf, dxc, bc, xform=(AUTO, AUTO), alpha=0.0, beta=1.0,
-                 precision=FP64, rtol=0.0, max_refine=1, device: int = 0):
-        self.device = int(device)
+                 precision=FP64, rtol=0.0, max_refine=1, device: int = 0, cache: "Cache" = None):
         desc, keep = make_desc(n, dxf, dxc, bc, xform, alpha, beta, precision, rtol, max_refine)
         h = C.c_void_p()
-        check(lib.tpt_plan_create(C.byref(desc), self.device, C.byref(h)), "tpt_plan_create")
+        if cache is not None:
+            self.device = cache.device
+            check(lib.tpt_plan_create_cached(C.byref(desc), cache._h, C.byref(h)), "tpt_plan_create_cached")
+            self._cache = cache          # the cache outlives its plans
+        else:
+            self.device = int(device)
+            check(lib.tpt_plan_create(C.byref(desc), self.device, C.byref(h)), "tpt_plan_create")
         del keep
         self._owned = True
         self._attach(h, n)
@@ -217,6 +222,98 @@ class Plan:
             if self._owned:
                 lib.tpt_plan_destroy(self._h)
             self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Cache:
+    """tpt_cache_*: shared direction eigenbases for plans created through it."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 1 << 30):
+        self.device = int(device)
+        h = C.c_void_p()
+        check(lib.tpt_cache_create(self.device, int(budget_bytes), C.byref(h)), "tpt_cache_create")
+        self._h = h
+
+    def stats(self):
+        hits, misses = C.c_ulonglong(), C.c_ulonglong()
+        nb, ne = C.c_size_t(), C.c_size_t()
+        check(lib.tpt_cache_stats(self._h, C.byref(hits), C.byref(misses), C.byref(nb), C.byref(ne)),
+              "tpt_cache_stats")
+        return dict(hits=int(hits.value), misses=int(misses.value), device_bytes=int(nb.value),
+                    entries=int(ne.value))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.tpt_cache_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """tpt_server_*: continuous-batching request server on one device.
+
+    ``submit`` takes Plan keyword arguments (n, dxf, dxc, bc, xform, alpha,
+    beta, precision, rtol, max_refine) and host tensors for f and phi (pinned
+    for full copy bandwidth); the tensors are kept alive until the request
+    is waited for.  ``device < 0`` runs the dry-run executor on the host."""
+
+    def __init__(self, device: int = 0, slots: int = 4, setup_threads: int = 4,
+                 memory_budget: int = 64 << 30, cache_budget: int = 4 << 30,
+                 dry_run_ns_per_point: float = 0.0):
+        cfg = _lib.tpt_server_config(int(device), int(slots), int(setup_threads), int(memory_budget),
+                                     int(cache_budget), float(dry_run_ns_per_point))
+        h = C.c_void_p()
+        check(lib.tpt_server_create(C.byref(cfg), C.byref(h)), "tpt_server_create")
+        self._h = h
+        self._held = {}
+
+    def submit(self, f_host, phi_host, **spec) -> int:
+        desc, keep = make_desc(**spec)
+        t = C.c_ulonglong()
+        fp = C.c_void_p(f_host.data_ptr() if hasattr(f_host, "data_ptr") else f_host.ctypes.data)
+        pp = C.c_void_p(phi_host.data_ptr() if hasattr(phi_host, "data_ptr") else phi_host.ctypes.data)
+        check(lib.tpt_server_submit(self._h, C.byref(desc), fp, pp, C.byref(t)), "tpt_server_submit")
+        del keep                        # the server copied the descriptor
+        self._held[int(t.value)] = (f_host, phi_host)
+        return int(t.value)
+
+    def wait(self, ticket: int, timeout: float = -1.0):
+        """The request's result dict, or None if it is still running after timeout."""
+        r = _lib.tpt_result()
+        st = lib.tpt_server_wait(self._h, int(ticket), float(timeout), C.byref(r))
+        if st == _lib.TPT_PENDING:
+            return None
+        check(st, "tpt_server_wait")
+        self._held.pop(int(ticket), None)
+        return dict(status=int(r.status), iters=r.info.iters, rel_residual=r.info.rel_residual,
+                    compat_defect=r.info.compat_defect, t_submit=r.t_submit, t_planned=r.t_planned,
+                    t_admit=r.t_admit, t_done=r.t_done, device_bytes=int(r.device_bytes))
+
+    def now(self) -> float:
+        t = C.c_double()
+        check(lib.tpt_server_now(self._h, C.byref(t)), "tpt_server_now")
+        return float(t.value)
+
+    def stats(self):
+        st = _lib.tpt_serving_stats()
+        check(lib.tpt_server_stats(self._h, C.byref(st)), "tpt_server_stats")
+        return {k: getattr(st, k) for k, _ in st._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.tpt_server_destroy(self._h)
+            self._h = None
+            self._held.clear()
 
     def __del__(self):
         try:

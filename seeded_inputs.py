@@ -88,10 +88,13 @@ def batch_instances(count: int = 96, seed: int = 5):
 
 
 def serving_requests(count: int, rate_hz: float = 200.0, seed: int = 6,
-                     nmin: int = 64, nmax: int = 512, step: int = 32, p_poisson: float = 0.7):
+                     nmin: int = 64, nmax: int = 512, step: int = 32, p_poisson: float = 0.7,
+                     stretch_step: float = 0.0):
     """Open-loop request stream: exponential inter-arrivals, sizes per dimension
     uniform over {nmin, nmin+step, ..., nmax}, 70% Poisson / 30% Helmholtz,
-    stretching factors uniform on [1, 3]."""
+    stretching factors uniform on [1, 3], rounded to multiples of stretch_step
+    above 1 when stretch_step > 0 (a finite set of grids, as a mesh library
+    of a serving deployment would have)."""
     rng = np.random.default_rng(seed)
     t = 0.0
     out = []
@@ -102,6 +105,8 @@ def serving_requests(count: int, rate_hz: float = 200.0, seed: int = 6,
         poisson = bool(rng.random() < p_poisson)
         dtnu = 0.0 if poisson else float(1e-2 * (1.0 - rng.random()))
         stretch = tuple(float(s) for s in rng.uniform(1.0, 3.0, size=3))
+        if stretch_step > 0.0:
+            stretch = tuple(1.0 + stretch_step * round((s - 1.0) / stretch_step) for s in stretch)
         out.append(dict(t_arrival=t, n=n, alpha=0.0 if poisson else 1.0,
                         beta=1.0 if poisson else -0.5 * dtnu, stretch=stretch, seed=20000 + r))
     return out

@@ -1,0 +1,111 @@
+"""Serving on GB300: requests of mixed sizes, kinds and precisions submitted
+together so that their solves overlap on the device must give the same
+result as each solved alone (same kernels and tables; only the atomic sums of
+the mean removal, gauge and residual norm differ in rounding order, so the
+bar is 1e-12 of the max norm for float64 and 1e-11 for refined mixed
+solves), and plans built through the eigenbasis cache must equal plans built
+on their own."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import seeded_inputs as S
+from _tpt import load
+
+pytestmark = pytest.mark.gpu
+tpt, L = load()
+
+NNN = [(1, 1)] * 3
+
+
+def _spec(n, stretch, alpha, beta, prec):
+    grids = [O.tanh_grid(n[a], 1.0, stretch[a]) for a in range(3)]
+    mixed = prec != L.TPT_PREC_FP64
+    return dict(n=n, dxf=[g[0] for g in grids], dxc=[g[1] for g in grids], bc=NNN, xform=(tpt.GEMM, tpt.GEMM),
+                alpha=alpha, beta=beta, precision=prec, rtol=1e-10 if mixed else 0.0,
+                max_refine=30 if mixed else 1)
+
+
+def _mix(count=14, seed=8):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = tuple(int(v) for v in rng.choice([48, 64, 96], size=3))
+        stretch = tuple(float(v) for v in rng.choice([1.0, 1.5, 2.0, 3.0], size=3))
+        helm = bool(rng.random() < 0.3)
+        alpha, beta = (1.0, -0.5 * 1e-2 * (1.0 - rng.random())) if helm else (0.0, 1.0)
+        prec = [L.TPT_PREC_FP64, L.TPT_PREC_MIXED_BF16X3, L.TPT_PREC_MIXED_TF32][i % 3]
+        out.append(_spec(n, stretch, alpha, beta, prec))
+    return out
+
+
+def _rhs(sp, seed):
+    f = S.uniform_rhs(sp["n"], seed)
+    if sp["alpha"] == 0.0:
+        f = S.remove_weighted_mean(f, sp["dxf"])
+    return f
+
+
+def _alone(sp, f):
+    plan = tpt.Plan(**sp)
+    phi, info = plan.solve(tpt.field_to_device(f))
+    return tpt.field_to_host(phi, sp["n"]), info
+
+
+def test_results_alone_equal_results_in_the_mix():
+    specs = _mix()
+    fs = [_rhs(sp, 50 + i) for i, sp in enumerate(specs)]
+    f_host = [torch.from_numpy(np.ascontiguousarray(f.ravel(order="F"))).pin_memory() for f in fs]
+    phi_host = [torch.empty_like(t).pin_memory() for t in f_host]
+    srv = tpt.Server(device=0, slots=3, setup_threads=6, memory_budget=8 << 30, cache_budget=1 << 30)
+    tickets = [srv.submit(f, p, **sp) for f, p, sp in zip(f_host, phi_host, specs)]
+    res = [srv.wait(t, timeout=300.0) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    assert st["peak_inflight"] >= 2, st                  # the requests did overlap
+    assert st["cache_hits"] > 0
+    for i, (sp, r) in enumerate(zip(specs, res)):
+        assert r is not None and r["status"] == L.TPT_OK, (i, r)
+        got = phi_host[i].numpy().reshape(sp["n"], order="F")
+        alone, info = _alone(sp, fs[i])
+        tol = 1e-12 if sp["precision"] == L.TPT_PREC_FP64 else 1e-11
+        assert np.abs(got - alone).max() <= tol * np.abs(alone).max(), (i, np.abs(got - alone).max())
+        if sp["precision"] != L.TPT_PREC_FP64:
+            assert r["rel_residual"] <= 1e-10 and r["iters"] == info["iters"]
+        assert r["t_submit"] <= r["t_planned"] <= r["t_admit"] <= r["t_done"]
+
+
+def test_served_float64_results_match_the_oracle():
+    sp = _spec((24, 32, 20), (1.5, 2.0, 2.5), 0.0, 1.0, L.TPT_PREC_FP64)
+    f = _rhs(sp, 77)
+    dirs = O.make_dirs(sp["n"], (1.5, 2.0, 2.5), NNN)
+    ref, _ = O.solve_tensor(f, dirs, 0.0, 1.0)
+    fh = torch.from_numpy(np.ascontiguousarray(f.ravel(order="F")))
+    ph = torch.empty_like(fh)
+    srv = tpt.Server(device=0, slots=2, setup_threads=1, memory_budget=1 << 30)
+    r = srv.wait(srv.submit(fh, ph, **sp))
+    srv.close()
+    assert r["status"] == L.TPT_OK
+    got = ph.numpy().reshape(sp["n"], order="F")
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("prec", [L.TPT_PREC_FP64, L.TPT_PREC_MIXED_BF16X3])
+def test_cached_device_plans_equal_standalone_plans(prec):
+    cache = tpt.Cache(device=0, budget_bytes=1 << 30)
+    outs = []
+    for n, stretch in [((40, 32, 24), (2.0, 1.5, 1.0)), ((32, 40, 24), (1.5, 2.0, 1.0))]:
+        sp = _spec(n, stretch, 0.0, 1.0, prec)
+        f = _rhs(sp, 5)
+        pc = tpt.Plan(cache=cache, **sp)
+        phi_c, _ = pc.solve(tpt.field_to_device(f))
+        alone, _ = _alone(sp, f)
+        got = tpt.field_to_host(phi_c, n)
+        assert np.abs(got - alone).max() <= 1e-12 * np.abs(alone).max()
+        outs.append(pc)
+    st = cache.stats()
+    assert st["hits"] == 2 and st["misses"] == 2 and st["device_bytes"] > 0
+    for p in outs:
+        p.close()
+    cache.close()
