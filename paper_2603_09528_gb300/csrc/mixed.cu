@@ -681,6 +681,176 @@ residual_df_kernel(int nx, int ny, int nz, int ldx, int kseg, const float* __res
   if ((threadIdx.x + blockDim.x * threadIdx.y) % 32 == 0) atomicAdd(&sums[0], s2);
 }
 
+// exact difference x - y of float pairs (hi parts by TwoSum, lo parts added)
+__device__ __forceinline__ df df_diff(df x, df y) {
+  df d = two_sum(x.hi, -y.hi);
+  d.lo += x.lo - y.lo;
+  return d;
+}
+// acc += coef * d with a float-pair coefficient and an exact pair difference d
+__device__ __forceinline__ void acc_term(df& acc, float ch, float cl, df d) {
+  const float pr = ch * d.hi;
+  float pe = fmaf(ch, d.hi, -pr);
+  pe = fmaf(ch, d.lo, pe);
+  pe = fmaf(cl, d.hi, pe);
+  const df t = two_sum(acc.hi, pr);
+  acc.hi = t.hi;
+  acc.lo += t.lo + pe;
+}
+
+template <int FMT>
+struct Elem2;   // two consecutive elements of R in one store
+template <>
+struct Elem2<kFmtSplit> {
+  static __device__ __forceinline__ void store(void* p0, void* p1, long long i, float a, float b) {
+    const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
+    __nv_bfloat162 h, l;
+    h.x = ha;
+    h.y = hb;
+    l.x = __float2bfloat16_rn(a - __bfloat162float(ha));
+    l.y = __float2bfloat16_rn(b - __bfloat162float(hb));
+    *reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(p0) + i) = h;
+    *reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(p1) + i) = l;
+  }
+};
+template <>
+struct Elem2<kFmtBF16> {
+  static __device__ __forceinline__ void store(void* p0, void*, long long i, float a, float b) {
+    __nv_bfloat162 h;
+    h.x = __float2bfloat16_rn(a);
+    h.y = __float2bfloat16_rn(b);
+    *reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(p0) + i) = h;
+  }
+};
+template <>
+struct Elem2<kFmtF32> {
+  static __device__ __forceinline__ void store(void* p0, void*, long long i, float a, float b) {
+    *reinterpret_cast<float2*>(static_cast<float*>(p0) + i) = make_float2(a, b);
+  }
+};
+
+// The residual of residual_df_kernel for even Nx, two neighbouring points
+// (i, i+1) per thread: float2 loads, the z-row coefficients read once for the
+// pair, the exact difference across the face between the two points computed
+// once, and the z-face difference carried from one plane to the next (the
+// difference up from plane k is, negated, the one down from plane k+1).  The
+// operations applied to each point, and their order, are those of
+// residual_df_kernel, so the result is the same to the bit.
+template <int FMT, int HAS_ALPHA, int WX, int WY, int WZ>
+__global__ void __launch_bounds__(128)
+residual_df2_kernel(int nx, int ny, int nz, int ldx, int kseg, const float* __restrict__ fh,
+                    const float* __restrict__ fl, const float* __restrict__ ph,
+                    const float* __restrict__ pl, void* r0, void* r1, BRows RX, BRows RY, BRows RZ,
+                    float alpha_h, float alpha_l, const double* __restrict__ fsums, double inv_vol,
+                    int singular, double* sums) {
+  const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x);   // points i and i + 1
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k0 = blockIdx.z * kseg;
+  const int k1 = min(nz, k0 + kseg);
+  float acc2 = 0.0f;
+  if (i < nx && j < ny && k0 < nz) {
+    const long long sz = static_cast<long long>(nx) * ny;
+    const long long base = i + static_cast<long long>(nx) * j;
+    const int dxm = (i == 0) ? nx - 1 : -1;                    // from point i
+    const int dxp = (i + 1 == nx - 1) ? -(nx - 2) : 2;         // from point i (to i + 2 or the wrap)
+    const int dym = (j == 0) ? (ny - 1) * nx : -nx, dyp = (j == ny - 1) ? -(ny - 1) * nx : nx;
+    const float axh0 = RX.ah[i], axl0 = RX.al[i], cxh0 = RX.ch[i], cxl0 = RX.cl[i];
+    const float axh1 = RX.ah[i + 1], axl1 = RX.al[i + 1], cxh1 = RX.ch[i + 1], cxl1 = RX.cl[i + 1];
+    const float ayh = RY.ah[j], ayl = RY.al[j], cyh = RY.ch[j], cyl = RY.cl[j];
+    df fshift = {0.0f, 0.0f};
+    if (singular) {
+      const double c = fsums[2] * inv_vol;
+      const float chi = static_cast<float>(c);
+      fshift = {chi, static_cast<float>(c - static_cast<double>(chi))};
+    }
+    const float* hk = ph + base + sz * k0;
+    const float* lk = pl + base + sz * k0;
+    const float* fhk = fh + base + sz * k0;
+    const float* flk = fl + base + sz * k0;
+    auto pair2 = [](const float* h, const float* l, df& a, df& b) {
+      const float2 vh = *reinterpret_cast<const float2*>(h);
+      const float2 vl = *reinterpret_cast<const float2*>(l);
+      a = {vh.x, vl.x};
+      b = {vh.y, vl.y};
+    };
+    const long long back = (k0 == 0) ? sz * (nz - 1) : -sz;
+    df p0a, p0b, pma, pmb;
+    pair2(hk, lk, p0a, p0b);
+    pair2(hk + back, lk + back, pma, pmb);
+    df dza = df_diff(pma, p0a), dzb = df_diff(pmb, p0b);        // down from plane k0
+    long long ro = i + static_cast<long long>(ldx) * (j + static_cast<long long>(ny) * k0);
+    const long long rstep = static_cast<long long>(ldx) * ny;
+    for (int k = k0; k < k1; ++k) {
+      const long long fwd = (k == nz - 1) ? -sz * (nz - 1) : sz;
+      df ppa, ppb, yma, ymb, ypa, ypb, fa, fb;
+      pair2(hk + fwd, lk + fwd, ppa, ppb);
+      pair2(hk + dym, lk + dym, yma, ymb);
+      pair2(hk + dyp, lk + dyp, ypa, ypb);
+      pair2(fhk, flk, fa, fb);
+      const df xm = {hk[dxm], lk[dxm]}, xp = {hk[dxp], lk[dxp]};
+      const float azh = RZ.ah[k], azl = RZ.al[k], czh = RZ.ch[k], czl = RZ.cl[k];
+      const df dmid = df_diff(p0b, p0a);                          // across the face between the pair
+      const df dupa = df_diff(ppa, p0a), dupb = df_diff(ppb, p0b);
+      df acc_a = {0.0f, 0.0f}, acc_b = {0.0f, 0.0f};
+      acc_term(acc_a, axh0, axl0, df_diff(xm, p0a));
+      acc_term(acc_a, cxh0, cxl0, dmid);
+      acc_term(acc_a, ayh, ayl, df_diff(yma, p0a));
+      acc_term(acc_a, cyh, cyl, df_diff(ypa, p0a));
+      acc_term(acc_a, azh, azl, dza);
+      acc_term(acc_a, czh, czl, dupa);
+      acc_term(acc_b, axh1, axl1, {-dmid.hi, -dmid.lo});
+      acc_term(acc_b, cxh1, cxl1, df_diff(xp, p0b));
+      acc_term(acc_b, ayh, ayl, df_diff(ymb, p0b));
+      acc_term(acc_b, cyh, cyl, df_diff(ypb, p0b));
+      acc_term(acc_b, azh, azl, dzb);
+      acc_term(acc_b, czh, czl, dupb);
+      if (WX) {
+        acc_mul(acc_a, -RX.wh[i], -RX.wl[i], p0a);
+        acc_mul(acc_b, -RX.wh[i + 1], -RX.wl[i + 1], p0b);
+      }
+      if (WY) {
+        acc_mul(acc_a, -RY.wh[j], -RY.wl[j], p0a);
+        acc_mul(acc_b, -RY.wh[j], -RY.wl[j], p0b);
+      }
+      if (WZ) {
+        acc_mul(acc_a, -RZ.wh[k], -RZ.wl[k], p0a);
+        acc_mul(acc_b, -RZ.wh[k], -RZ.wl[k], p0b);
+      }
+      if (HAS_ALPHA) {
+        acc_mul(acc_a, alpha_h, alpha_l, p0a);
+        acc_mul(acc_b, alpha_h, alpha_l, p0b);
+      }
+      float rv[2];
+      {
+        df r = two_sum(fa.hi, -fshift.hi);
+        r.lo += fa.lo - fshift.lo;
+        const df t = two_sum(r.hi, -acc_a.hi);
+        rv[0] = t.hi + (t.lo + (r.lo - acc_a.lo));
+      }
+      {
+        df r = two_sum(fb.hi, -fshift.hi);
+        r.lo += fb.lo - fshift.lo;
+        const df t = two_sum(r.hi, -acc_b.hi);
+        rv[1] = t.hi + (t.lo + (r.lo - acc_b.lo));
+      }
+      Elem2<FMT>::store(r0, r1, ro, rv[0], rv[1]);
+      acc2 = fmaf(rv[0], rv[0], acc2);
+      acc2 = fmaf(rv[1], rv[1], acc2);
+      dza = {-dupa.hi, -dupa.lo};                                 // down from plane k + 1
+      dzb = {-dupb.hi, -dupb.lo};
+      p0a = ppa;
+      p0b = ppb;
+      hk += sz;
+      lk += sz;
+      fhk += sz;
+      flk += sz;
+      ro += rstep;
+    }
+  }
+  double s2 = warp_sum_d(static_cast<double>(acc2));
+  if ((threadIdx.x + blockDim.x * threadIdx.y) % 32 == 0) atomicAdd(&sums[0], s2);
+}
+
 // sum of cell volume times phi (float pair) into *out, for the exact gauge;
 // work items are 256-point chunks of x-lines (one division per item)
 __global__ void __launch_bounds__(256)
@@ -1074,6 +1244,14 @@ cudaError_t launch_res(const tpt_plan_s* p, const MixedWork& w, cudaStream_t s) 
   const float ah = static_cast<float>(p->alpha);
   const float al = static_cast<float>(p->alpha - static_cast<double>(ah));
   note_launch(1);
+  if (nx % 2 == 0) {   // two points per thread
+    dim3 grid2((nx / 2 + 31) / 32, (ny + 3) / 4, (nz + kseg - 1) / kseg);
+    residual_df2_kernel<FMT, HA, WX, WY, WZ><<<grid2, block, 0, s>>>(
+        nx, ny, nz, p->mixed.ldx, kseg, w.fh, w.fl, w.ph, w.pl, w.R[0], w.R[1],
+        rows_of(p->mixed.dfrows[0], nx), rows_of(p->mixed.dfrows[1], ny), rows_of(p->mixed.dfrows[2], nz),
+        ah, al, w.scal + 5, 1.0 / p->vol, p->singular ? 1 : 0, w.scal + 1);
+    return cudaGetLastError();
+  }
   residual_df_kernel<FMT, HA, WX, WY, WZ><<<grid, block, 0, s>>>(
       nx, ny, nz, p->mixed.ldx, kseg, w.fh, w.fl, w.ph, w.pl, w.R[0], w.R[1],
       rows_of(p->mixed.dfrows[0], nx), rows_of(p->mixed.dfrows[1], ny), rows_of(p->mixed.dfrows[2], nz),
