@@ -918,6 +918,158 @@ df_to_f64_kernel(long long n, const float* __restrict__ h, const float* __restri
   }
 }
 
+// Vectorised forms of prepare_kernel, wsum_df_kernel and df_to_f64_kernel for
+// the common aligned case (Nx a multiple of the vector width): each thread
+// moves 2 or 4 consecutive points of an x-line with 16-byte loads and stores,
+// and the per-line weights and index divisions are shared by those points.
+// Same operations per point as the scalar kernels.
+template <int FMT>
+__global__ void __launch_bounds__(256)
+prepare2_kernel(int nx, int ny, int nz, int ldx, int nbi, const double* __restrict__ f, float* __restrict__ fh,
+                float* __restrict__ fl, void* r0, void* r1, const float* __restrict__ gx,
+                const float* __restrict__ gy, const float* __restrict__ gz, double* sums) {
+  // work item t: x-line (j, k) = t / nbi, points (t % nbi) * 512 + 2 * threadIdx.x + {0, 1}
+  const long long items = static_cast<long long>(nbi) * ny * nz;
+  float s2 = 0.0f, s1f = 0.0f;
+  df sv = {0.0f, 0.0f};
+  constexpr int U = 4;
+  for (long long t0 = blockIdx.x; t0 < items; t0 += static_cast<long long>(U) * gridDim.x) {
+    double2 v[U];
+    long long line[U];
+    int ii[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long t = t0 + static_cast<long long>(u) * gridDim.x;
+      line[u] = t / nbi;
+      ii[u] = static_cast<int>(t % nbi) * 512 + 2 * threadIdx.x;
+      const bool ok = t < items && ii[u] < nx;
+      if (!ok) ii[u] = -1;
+      v[u] = ok ? *reinterpret_cast<const double2*>(f + ii[u] + static_cast<long long>(nx) * line[u])
+                : make_double2(0.0, 0.0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = ii[u];
+      if (i < 0) continue;
+      const int j = static_cast<int>(line[u] % ny), k = static_cast<int>(line[u] / ny);
+      const long long o = i + static_cast<long long>(nx) * line[u];
+      const df d0 = split_double_int(v[u].x), d1 = split_double_int(v[u].y);
+      *reinterpret_cast<float2*>(fh + o) = make_float2(d0.hi, d1.hi);
+      *reinterpret_cast<float2*>(fl + o) = make_float2(d0.lo, d1.lo);
+      Elem2<FMT>::store(r0, r1, i + static_cast<long long>(ldx) * line[u], d0.hi + d0.lo, d1.hi + d1.lo);
+      s2 = fmaf(d0.hi, d0.hi, s2);
+      s2 = fmaf(d1.hi, d1.hi, s2);
+      s1f += d0.hi;
+      s1f += d1.hi;
+      const df wline = df_mul({gy[j], gy[ny + j]}, {gz[k], gz[nz + k]});
+      const float2 gxh = *reinterpret_cast<const float2*>(gx + i);
+      const float2 gxl = *reinterpret_cast<const float2*>(gx + nx + i);
+      acc_mul(sv, wline.hi, wline.lo, df_mul({gxh.x, gxl.x}, d0));
+      acc_mul(sv, wline.hi, wline.lo, df_mul({gxh.y, gxl.y}, d1));
+    }
+  }
+  df s1 = {s1f, 0.0f};
+  sv = fast_two_sum(sv.hi, sv.lo);
+  __shared__ float red[3][2][8];
+  const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    s1 = df_add(s1, {__shfl_xor_sync(0xffffffffu, s1.hi, o), __shfl_xor_sync(0xffffffffu, s1.lo, o)});
+    sv = df_add(sv, {__shfl_xor_sync(0xffffffffu, sv.hi, o), __shfl_xor_sync(0xffffffffu, sv.lo, o)});
+  }
+  if (lane == 0) {
+    red[0][0][w] = s2;
+    red[1][0][w] = s1.hi;
+    red[1][1][w] = s1.lo;
+    red[2][0][w] = sv.hi;
+    red[2][1][w] = sv.lo;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int q = 0; q < 8; ++q) {
+      a += red[0][0][q];
+      b += static_cast<double>(red[1][0][q]) + red[1][1][q];
+      c += static_cast<double>(red[2][0][q]) + red[2][1][q];
+    }
+    atomicAdd(&sums[0], a);
+    atomicAdd(&sums[1], b);
+    atomicAdd(&sums[2], c);
+  }
+}
+
+// sum of cell volume times phi, four points of an x-line per thread
+__global__ void __launch_bounds__(256)
+wsum4_kernel(int nx, int ny, int nz, const float* __restrict__ h, const float* __restrict__ l,
+             const float* __restrict__ gx, const float* __restrict__ gy, const float* __restrict__ gz,
+             double* out) {
+  const int nbi = (nx + 1023) / 1024;
+  const long long items = static_cast<long long>(nbi) * ny * nz;
+  df s = {0.0f, 0.0f};
+  constexpr int U = 2;
+  for (long long t0 = blockIdx.x; t0 < items; t0 += static_cast<long long>(U) * gridDim.x) {
+    float4 hh[U], ll[U];
+    long long line[U];
+    int ii[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long t = t0 + static_cast<long long>(u) * gridDim.x;
+      line[u] = t / nbi;
+      ii[u] = static_cast<int>(t % nbi) * 1024 + 4 * threadIdx.x;
+      const bool ok = t < items && ii[u] < nx;
+      if (!ok) ii[u] = -1;
+      const long long o = ok ? ii[u] + static_cast<long long>(nx) * line[u] : 0;
+      hh[u] = ok ? *reinterpret_cast<const float4*>(h + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+      ll[u] = ok ? *reinterpret_cast<const float4*>(l + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = ii[u];
+      if (i < 0) continue;
+      const int j = static_cast<int>(line[u] % ny), k = static_cast<int>(line[u] / ny);
+      const df wline = df_mul({gy[j], gy[ny + j]}, {gz[k], gz[nz + k]});
+      const float4 gh = *reinterpret_cast<const float4*>(gx + i);
+      const float4 gl = *reinterpret_cast<const float4*>(gx + nx + i);
+      acc_mul(s, wline.hi, wline.lo, df_mul({gh.x, gl.x}, {hh[u].x, ll[u].x}));
+      acc_mul(s, wline.hi, wline.lo, df_mul({gh.y, gl.y}, {hh[u].y, ll[u].y}));
+      acc_mul(s, wline.hi, wline.lo, df_mul({gh.z, gl.z}, {hh[u].z, ll[u].z}));
+      acc_mul(s, wline.hi, wline.lo, df_mul({gh.w, gl.w}, {hh[u].w, ll[u].w}));
+    }
+  }
+  s = fast_two_sum(s.hi, s.lo);
+  double v = static_cast<double>(s.hi) + s.lo;
+  v = warp_sum_d(v);
+  if (threadIdx.x % 32 == 0) atomicAdd(out, v);
+}
+
+// df_to_f64_kernel on groups of four points (n a multiple of 4, out 16-byte aligned)
+__global__ void __launch_bounds__(256)
+df_to_f64_v4_kernel(long long n4, const float4* __restrict__ h, const float4* __restrict__ l,
+                    const double* __restrict__ wsum, double inv_vol, double2* out) {
+  const df shift = df_from_double(wsum ? *wsum * inv_vol : 0.0);
+  constexpr int U = 2;
+  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+  for (long long g0 = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; g0 < n4; g0 += U * stride) {
+    float4 hh[U], ll[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long g = g0 + u * stride;
+      hh[u] = g < n4 ? h[g] : make_float4(0.f, 0.f, 0.f, 0.f);
+      ll[u] = g < n4 ? l[g] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long g = g0 + u * stride;
+      if (g >= n4) break;
+      const df a = df_sub({hh[u].x, ll[u].x}, shift), b = df_sub({hh[u].y, ll[u].y}, shift);
+      const df c = df_sub({hh[u].z, ll[u].z}, shift), d = df_sub({hh[u].w, ll[u].w}, shift);
+      out[2 * g] = make_double2(f2d_int(a.hi) + f2d_int(a.lo), f2d_int(b.hi) + f2d_int(b.lo));
+      out[2 * g + 1] = make_double2(f2d_int(c.hi) + f2d_int(c.lo), f2d_int(d.hi) + f2d_int(d.lo));
+    }
+  }
+}
+
 // rows x K float64 (row-major, stride K) -> operand planes with row stride ld
 template <int FMT>
 __global__ void __launch_bounds__(256)
@@ -1109,6 +1261,14 @@ cudaError_t launch_prepare(const tpt_plan_s* p, const double* f, const MixedWork
   const int nbi = (p->n[0] + 255) / 256;
   const long long items = static_cast<long long>(nbi) * p->n[1] * p->n[2];
   note_launch(1);
+  if (p->n[0] % 2 == 0 && reinterpret_cast<uintptr_t>(f) % 16 == 0) {   // two points per thread
+    const int nb2 = (p->n[0] + 511) / 512;
+    const long long items2 = static_cast<long long>(nb2) * p->n[1] * p->n[2];
+    prepare2_kernel<FMT><<<grid_for(items2 * 256, 256, p->dev), 256, 0, s>>>(
+        p->n[0], p->n[1], p->n[2], p->mixed.ldx, nb2, f, w.fh, w.fl, w.R[0], w.R[1], p->mixed.dfgeom[0],
+        p->mixed.dfgeom[1], p->mixed.dfgeom[2], w.scal + 5);
+    return cudaGetLastError();
+  }
   prepare_kernel<FMT><<<grid_for(items * 256, 256, p->dev), 256, 0, s>>>(
       p->n[0], p->n[1], p->n[2], p->mixed.ldx, nbi, f, w.fh, w.fl, w.R[0], w.R[1], p->mixed.dfgeom[0],
       p->mixed.dfgeom[1], p->mixed.dfgeom[2], w.scal + 5);
@@ -1414,14 +1574,24 @@ int solve_fmt(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStrea
   if (p->singular) {
     MX_CUDA(cudaMemsetAsync(w.scal + 2, 0, sizeof(double), s));
     note_launch(1);
-    wsum_df_kernel<<<grid_for(n, 256, p->dev), 256, 0, s>>>(p->n[0], p->n[1], p->n[2], w.ph, w.pl,
-                                                            p->mixed.dfgeom[0], p->mixed.dfgeom[1],
-                                                            p->mixed.dfgeom[2], w.scal + 2);
+    if (p->n[0] % 4 == 0)   // four points per thread
+      wsum4_kernel<<<grid_for(n / 4, 256, p->dev), 256, 0, s>>>(p->n[0], p->n[1], p->n[2], w.ph, w.pl,
+                                                               p->mixed.dfgeom[0], p->mixed.dfgeom[1],
+                                                               p->mixed.dfgeom[2], w.scal + 2);
+    else
+      wsum_df_kernel<<<grid_for(n, 256, p->dev), 256, 0, s>>>(p->n[0], p->n[1], p->n[2], w.ph, w.pl,
+                                                              p->mixed.dfgeom[0], p->mixed.dfgeom[1],
+                                                              p->mixed.dfgeom[2], w.scal + 2);
     MX_CUDA(cudaGetLastError());
   }
   note_launch(1);
-  df_to_f64_kernel<<<grid_for(n, 256, p->dev), 256, 0, s>>>(n, w.ph, w.pl, p->singular ? w.scal + 2 : nullptr,
-                                                            1.0 / p->vol, phi);
+  if (n % 4 == 0 && reinterpret_cast<uintptr_t>(phi) % 16 == 0)
+    df_to_f64_v4_kernel<<<grid_for(n / 4, 256, p->dev), 256, 0, s>>>(
+        n / 4, reinterpret_cast<const float4*>(w.ph), reinterpret_cast<const float4*>(w.pl),
+        p->singular ? w.scal + 2 : nullptr, 1.0 / p->vol, reinterpret_cast<double2*>(phi));
+  else
+    df_to_f64_kernel<<<grid_for(n, 256, p->dev), 256, 0, s>>>(n, w.ph, w.pl, p->singular ? w.scal + 2 : nullptr,
+                                                              1.0 / p->vol, phi);
   MX_CUDA(cudaGetLastError());
   if (timing) {
     cudaEventRecord(p->ev[11], s);
