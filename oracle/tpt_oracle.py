@@ -12,6 +12,10 @@ What it computes (paper sections cited per function):
   Sec. 2.2.1, with boundary rows (Neumann, periodic, Dirichlet);
 * the 3D Kronecker-sum operator of Sec. 2.2.2 applied as a 7-point stencil, and
   assembled densely for tiny grids;
+* the pressure projection of a staggered velocity field, Sec. 2.1 (the
+  pressure-correction equation Eq. poi_ns and the velocity correction that
+  follows it): divergence D, gradient G and u = u* - g G Phi with
+  L Phi = D u* / g;
 * the solve of (alpha I + beta L) phi = f:
     - ``solve_dense``: Gaussian elimination with partial pivoting on the
       assembled matrix (bordered when singular) -- the plain definition;
@@ -45,6 +49,14 @@ R6 the eigenvalue of the null mode is set to exactly 0.
 R7 eigenvalues are recomputed as Rayleigh quotients of the float64 eigenvectors
    in long double, in the energy form of the symmetric row-scaled operator, so
    that the smallest eigenvalues carry relative (not absolute) accuracy.
+R9 staggered velocity (projection): the x-velocity lives on the Nx + 1 x-faces
+   of each x-line (face i between cells i-1 and i), likewise v, w; D u is the
+   cell's net face flux over its width, (u_{i+1} - u_i)/dx_i summed over the
+   three directions, and (G phi) on face i is (phi_i - phi_{i-1})/dx_{i-1/2}
+   at interior faces and, on a periodic direction, across the wrap face 0 = N
+   with the wrap spacing; G is zero on wall faces (no penetration), so the wall
+   values of u are left as given.  With these, D o G is the operator of the
+   1D rows with Neumann walls.
 R8 the tensor solve is followed by ``refine`` steps of iterative refinement,
    each computing r = f - A phi with the stencil (float64 by default, long
    double on request) and adding the tensor solve of r.  A float64 eigensolver
@@ -379,3 +391,41 @@ def solve_tensor(f, dirs, alpha, beta, refine: int = 1, residual_dtype=np.float6
 def make_dirs(n, stretch, bcs, L=(1.0, 1.0, 1.0)):
     """Directions for sizes n, tanh factors ``stretch`` and boundary pairs ``bcs``."""
     return [Direction(*tanh_grid(n[a], L[a], stretch[a]), bcs[a]) for a in range(3)]
+
+
+# ------------------------------------- pressure projection (Sec. 2.1)
+
+def divergence(vel, dirs):
+    """D u on the cells (R9): vel = (u, v, w) with u of shape (Nx+1, Ny, Nz),
+    v (Nx, Ny+1, Nz), w (Nx, Ny, Nz+1)."""
+    out = 0.0
+    for ax, d in enumerate(dirs):
+        u = np.moveaxis(np.asarray(vel[ax], dtype=np.float64), ax, 0)
+        flux = (u[1:] - u[:-1]) / d.dxf.reshape((-1,) + (1,) * (u.ndim - 1))
+        out = out + np.moveaxis(flux, 0, ax)
+    return out
+
+
+def gradient(phi, dirs):
+    """G phi on the faces of each direction (R9): zero on wall faces, the wrap
+    difference on the shared boundary face of a periodic direction."""
+    out = []
+    for ax, d in enumerate(dirs):
+        p = np.moveaxis(np.asarray(phi, dtype=np.float64), ax, 0)
+        g = np.zeros((d.n + 1,) + p.shape[1:])
+        g[1:d.n] = (p[1:] - p[:-1]) / d.dxc[1:d.n].reshape((-1,) + (1,) * (p.ndim - 1))
+        if d.periodic:
+            g[0] = (p[0] - p[-1]) / d.dxc[0]
+            g[d.n] = g[0]
+        out.append(np.moveaxis(g, 0, ax))
+    return out
+
+
+def project(vel, dirs, gdt, refine: int = 1):
+    """The projection of Sec. 2.1 with g = gamma_k dt: Phi solves L Phi = D u / g
+    (Poisson, zero volume-weighted mean), and the result is u - g G Phi.
+    Returns (new velocity, Phi, the compatibility defect of D u / g)."""
+    rhs = divergence(vel, dirs) / gdt
+    phi, defect = solve_tensor(rhs, dirs, 0.0, 1.0, refine)
+    grad = gradient(phi, dirs)
+    return [np.asarray(vel[a], dtype=np.float64) - gdt * grad[a] for a in range(3)], phi, defect

@@ -319,3 +319,78 @@ def test_residual_is_at_round_off_in_long_double():
     r = O.residual(f, phi, dirs, 0.0, 1.0, np.longdouble)
     scale = max(d.b.__abs__().max() for d in dirs) * np.abs(phi).max()
     assert float(np.abs(r).max()) < 8 * np.finfo(float).eps * scale
+
+
+# ------------------------------------------------ pressure projection (N4)
+
+def _faces_of(d):
+    """Face coordinates of a direction from its cell widths (R1)."""
+    return np.concatenate([[0.0], np.cumsum(d.dxf)])
+
+
+def _random_velocity(n, dirs, seed):
+    rng = np.random.default_rng(seed)
+    vel = []
+    for ax, d in enumerate(dirs):
+        shp = list(n)
+        shp[ax] = d.n + 1
+        u = np.moveaxis(rng.uniform(-1, 1, shp), ax, 0)
+        if d.periodic:
+            u[d.n] = u[0]
+        else:
+            u[0] = 0.0
+            u[d.n] = 0.0
+        vel.append(np.moveaxis(u, 0, ax))
+    return vel
+
+
+def test_divergence_and_gradient_of_linear_fields_are_one():
+    # closed forms: D of u = x_face along x is 1 in every cell; G of p = x_centre
+    # is 1 on every interior face (R9), exactly up to rounding
+    n = (9, 7, 6)
+    dirs = O.make_dirs(n, (2.0, 1.3, 2.7), [(BC_N, BC_N)] * 3)
+    for ax, d in enumerate(dirs):
+        xf = _faces_of(d)
+        shp = [1, 1, 1]
+        shp[ax] = d.n + 1
+        vel = [np.zeros((n[0] + (a == 0), n[1] + (a == 1), n[2] + (a == 2))) for a in range(3)]
+        vel[ax] = np.broadcast_to(xf.reshape(shp), vel[ax].shape).copy()
+        assert np.allclose(O.divergence(vel, dirs), 1.0, rtol=0, atol=1e-13)
+        xc = 0.5 * (xf[1:] + xf[:-1])
+        shp2 = [1, 1, 1]
+        shp2[ax] = d.n
+        p = np.broadcast_to(xc.reshape(shp2), n).copy()
+        g = np.moveaxis(O.gradient(p, dirs)[ax], ax, 0)
+        assert np.allclose(g[1:d.n], 1.0, rtol=0, atol=1e-12)
+        assert np.all(g[0] == 0.0) and np.all(g[d.n] == 0.0)          # walls
+
+
+@pytest.mark.parametrize("bcs", [[(BC_N, BC_N)] * 3, [(BC_P, BC_P), (BC_N, BC_N), (BC_N, BC_N)]])
+def test_divergence_of_gradient_is_the_operator(bcs):
+    # D o G equals the 7-point operator of the paper's 1D rows (Eq. poisson-fd2)
+    n = (8, 7, 6)
+    dirs = O.make_dirs(n, (0.0 if bcs[0][0] == BC_P else 1.8, 2.4, 1.6), bcs)
+    phi = S.uniform_rhs(n, 31)
+    got = O.divergence(O.gradient(phi, dirs), dirs)
+    ref = O.apply_operator(phi, dirs, 0.0, 1.0)
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("bcx", [(BC_N, BC_N), (BC_P, BC_P)])
+def test_oracle_projection_is_divergence_free_and_idempotent(bcx):
+    n = (11, 9, 8)
+    dirs = O.make_dirs(n, (0.0 if bcx[0] == BC_P else 1.5, 2.5, 3.0), [bcx, (BC_N, BC_N), (BC_N, BC_N)])
+    vel = _random_velocity(n, dirs, 12)
+    gdt = 0.37
+    new, phi, defect = O.project(vel, dirs, gdt)
+    div0 = np.abs(O.divergence(vel, dirs)).max()
+    assert abs(defect) < 1e-12 * div0 / gdt
+    assert np.abs(O.divergence(new, dirs)).max() <= 1e-12 * div0
+    again, phi2, _ = O.project(new, dirs, gdt)
+    for a in range(3):
+        assert np.abs(again[a] - new[a]).max() <= 1e-12 * np.abs(new[a]).max()
+    # wall faces keep their (zero) values
+    for ax, d in enumerate(dirs):
+        if not d.periodic:
+            u = np.moveaxis(new[ax], ax, 0)
+            assert np.all(u[0] == 0.0) and np.all(u[d.n] == 0.0)
