@@ -333,6 +333,10 @@ def run_ours(args):
         e2e = {"value": solves / dt, "unit": "solves/s", "h2d_bytes_per_step": npts * 8,
                "d2h_bytes_per_step": npts * 8}
 
+    projection = None
+    if not args.no_projection and prec != 0:
+        projection = projection_leg(tpt, plan, n, stream, args.steps)
+
     batch = None
     if not args.no_batch:
         batch = {"mixed": batch_leg(tpt, local, stream, prec if prec != 0 else 2, args.steps)}
@@ -372,6 +376,7 @@ def run_ours(args):
             "solve_info": {k: v for k, v in (last or {}).items() if k != "ms_stage"},
             "stages": stages,
             "fp64": fp64,
+            "projection": projection,
             "batch": batch,
             "serving": serving,
             "gpu_launches": l1 - l0,
@@ -550,6 +555,54 @@ def serving_leg(tpt, device, prec, count, warmup, rate_hz=200.0, slots=4, stretc
             "peak_inflight": int(st["peak_inflight"]), "peak_device_bytes": int(st["peak_bytes"])}
 
 
+def projection_leg(tpt, plan, n, stream, steps):
+    """Pressure projection (Sec. 2.1) on the benchmark grid: D u* / g, the
+    refined Poisson solve, u -= g G Phi, with seeded uniform[-1, 1] face
+    velocities (zero normal velocity on the walls).  Each step restores the
+    starting velocity outside its timed region (CUDA events around
+    tpt_project only)."""
+    import torch
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(7)
+    shapes = [(n[0] + 1, n[1], n[2]), (n[0], n[1] + 1, n[2]), (n[0], n[1], n[2] + 1)]
+    start = []
+    for ax, shp in enumerate(shapes):
+        t = torch.rand(shp[::-1], generator=gen, dtype=torch.float64, device="cuda") * 2 - 1   # (z, y, x)
+        idx = [slice(None)] * 3
+        idx[2 - ax] = 0
+        t[tuple(idx)] = 0.0
+        idx[2 - ax] = -1
+        t[tuple(idx)] = 0.0
+        start.append(t.reshape(-1))
+    work = [t.clone() for t in start]
+    ws = plan.project_workspace()
+    phi = plan.new_field()
+    gdt = 0.125
+    for _ in range(2):
+        for w_, s_ in zip(work, start):
+            w_.copy_(s_)
+        plan.project(*work, gdt, phi=phi, work=ws, stream=stream)
+    times = []
+    for _ in range(max(3, steps)):
+        for w_, s_ in zip(work, start):
+            w_.copy_(s_)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        _, info = plan.project(*work, gdt, phi=phi, work=ws, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    npts = n[0] * n[1] * n[2]
+    ms = float(np.median(times))
+    del work, start, ws, phi
+    torch.cuda.empty_cache()
+    return {"workload": "projection_%dx%dx%d_tanh1.5-2.0-2.5_neumann" % n, "ms_per_projection": ms,
+            "projections_per_s": 1e3 / ms, "gpts_per_s": npts / (ms / 1e3) / 1e9, "steps": len(times),
+            "solve_iters": info["iters"], "rel_residual": info["rel_residual"],
+            "bytes_outside_solve_per_point": 32 + 56}
+
+
 def stage_rooflines(ms, iters, n, prec):
     """Per-stage achieved rates from the solve's own CUDA-event stage timings.
     Algorithmic work per point and launch: transforms 2*N_alpha flop per
@@ -648,6 +701,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched uneven-instances leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the open-loop serving leg")
+    ap.add_argument("--no-projection", action="store_true", help="skip the pressure-projection leg")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-warmup", type=int, default=200)
     ap.add_argument("--serve-requests-fp64", type=int, default=40)

@@ -229,6 +229,28 @@ int tpt_set_stage_timing(tpt_plan plan, int enable);
  * in tpt_desc).  Not to be called while a solve on this plan is in flight.  */
 int tpt_set_refinement(tpt_plan plan, double rtol, int max_refine);
 
+/* ---- pressure projection ------------------------------------------------- */
+/* The projection step of the fractional-step scheme (Sec. 2.1, the
+ * pressure-correction equation Eq. poi_ns and the velocity correction after
+ * it): with g = gamma_k dt,
+ *     L Phi = D u* / g ,    u = u* - g G Phi ,
+ * on the staggered grid of the plan.  u (Nx+1, Ny, Nz), v (Nx, Ny+1, Nz) and
+ * w (Nx, Ny, Nz+1) are the face-normal velocities on the x-, y- and z-faces
+ * (Fortran order; face i of a line lies between cells i-1 and i), updated in
+ * place.  (D u)_cell = sum over directions of (u_{i+1} - u_i) / dx_i;
+ * (G Phi) on interior face i is (Phi_i - Phi_{i-1}) / dx_{i-1/2}, on a
+ * periodic direction also across the shared boundary face (0 and N, which
+ * must hold equal values), and zero on wall faces, whose values are left as
+ * given (no penetration).  The plan must be the Poisson operator (alpha 0,
+ * beta 1) with periodic or Neumann directions; Phi (Nx*Ny*Nz doubles,
+ * phi_dev) gets zero volume-weighted mean, and a net wall flux is removed as
+ * the compatibility defect (info->compat_defect).  work_dev holds
+ * tpt_project_workspace_bytes() bytes.  Errors as tpt_solve, UNSUPPORTED for a
+ * Dirichlet direction, INVALID_ARG for other coefficients.                 */
+int tpt_project_workspace_bytes(tpt_plan plan, size_t* bytes);
+int tpt_project(tpt_plan plan, double* u, double* v, double* w, double gamma_dt, double* phi_dev,
+                void* work_dev, void* stream, tpt_info* info);
+
 /* ---- transform tiles ---------------------------------------------------- */
 /* Tile autotuner for the transform GEMMs of a TPT_PREC_MIXED_* plan (the
  * forward/inverse eigenbasis projections of Algorithm 1 steps 1, 3, 7, 9):

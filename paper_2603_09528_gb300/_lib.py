@@ -126,6 +126,9 @@ SIGNATURES = [
     ("tpt_batch_infos", C.c_int, [C.c_void_p, C.POINTER(tpt_info), C.POINTER(C.c_int)]),
     ("tpt_batch_launches", C.c_int, [C.c_void_p, C.POINTER(C.c_ulonglong)]),
     ("tpt_batch_destroy", C.c_int, [C.c_void_p]),
+    ("tpt_project_workspace_bytes", C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
+    ("tpt_project", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p,
+                              C.c_void_p, C.POINTER(tpt_info)]),
     ("tpt_cache_create", C.c_int, [C.c_int, C.c_size_t, C.POINTER(C.c_void_p)]),
     ("tpt_plan_create_cached", C.c_int, [C.POINTER(tpt_desc), C.c_void_p, C.POINTER(C.c_void_p)]),
     ("tpt_cache_stats", C.c_int, [C.c_void_p, C.POINTER(C.c_ulonglong), C.POINTER(C.c_ulonglong),

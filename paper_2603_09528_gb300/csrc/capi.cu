@@ -313,8 +313,13 @@ int create_plan_impl(const tpt_desc* desc, int cuda_device, tpt::BasisCache* cac
     std::copy(dd.a.begin(), dd.a.end(), rows.begin());
     std::copy(dd.b.begin(), dd.b.end(), rows.begin() + dd.n);
     std::copy(dd.c.begin(), dd.c.end(), rows.begin() + 2 * dd.n);
+    std::vector<double> ixf(dd.n), ixc(dd.n + 1);
+    for (int i = 0; i < dd.n; ++i) ixf[i] = 1.0 / dd.dxf[i];
+    for (int i = 0; i <= dd.n; ++i) ixc[i] = 1.0 / dd.dxc[i];
     int st = upload(p, rows, &p->d_rows[d]);
     if (st == TPT_OK) st = upload(p, dd.dxf, &p->d_dxf[d]);
+    if (st == TPT_OK) st = upload(p, ixf, &p->d_inv_dxf[d]);
+    if (st == TPT_OK) st = upload(p, ixc, &p->d_inv_dxc[d]);
     if (st != TPT_OK) return fail(st);
   }
   std::vector<double> scal(16, 0.0);

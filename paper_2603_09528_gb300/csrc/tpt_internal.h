@@ -132,6 +132,8 @@ struct tpt_plan_s {
   double null_g[2] = {1.0, 1.0};  // f-hat of a constant 1 on the null mode, per direction
   double* d_rows[3] = {nullptr, nullptr, nullptr};  // a|b|c per direction, 3n doubles
   double* d_dxf[3] = {nullptr, nullptr, nullptr};
+  double* d_inv_dxf[3] = {nullptr, nullptr, nullptr};   // 1 / cell widths (projection)
+  double* d_inv_dxc[3] = {nullptr, nullptr, nullptr};   // 1 / centre spacings, n + 1 each
   double* d_scal = nullptr;       // device scalars of the single-step entry points
   double* h_ring = nullptr;       // pinned host slots for asynchronous info reports
   int ring_next = 0;

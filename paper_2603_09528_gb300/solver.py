@@ -144,6 +144,27 @@ class Plan:
                          compat_defect=info.compat_defect, status=st,
                          ms_stage=[float(x) for x in info.ms_stage])
 
+    def project_workspace(self) -> torch.Tensor:
+        nb = C.c_size_t()
+        check(lib.tpt_project_workspace_bytes(self._h, C.byref(nb)), "tpt_project_workspace_bytes")
+        return torch.empty(int(nb.value), dtype=torch.uint8, device="cuda:%d" % self.device)
+
+    def project(self, u: torch.Tensor, v: torch.Tensor, w: torch.Tensor, gamma_dt: float,
+                phi: torch.Tensor = None, work: torch.Tensor = None, stream=None,
+                raise_not_converged: bool = True):
+        """tpt_project: u, v, w (face velocities, flat float64 CUDA tensors of
+        (Nx+1)NyNz, Nx(Ny+1)Nz, NxNy(Nz+1) values) are corrected in place;
+        returns (phi, info dict)."""
+        phi = self.new_field() if phi is None else phi
+        work = self.project_workspace() if work is None else work
+        info = _lib.tpt_info()
+        st = lib.tpt_project(self._h, _ptr(u), _ptr(v), _ptr(w), float(gamma_dt), _ptr(phi), _ptr(work),
+                             _stream(stream), C.byref(info))
+        if not (st == _lib.TPT_ERR_NOT_CONVERGED and not raise_not_converged):
+            check(st, "tpt_project")
+        (torch.cuda.current_stream() if stream is None else stream).synchronize()
+        return phi, _info_dict(info, st)
+
     def set_stage_timing(self, enable: bool):
         check(lib.tpt_set_stage_timing(self._h, int(bool(enable))), "tpt_set_stage_timing")
 
