@@ -9,6 +9,7 @@
 // reciprocal centre spacings, so no division runs on the device.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "tpt_internal.h"
@@ -21,11 +22,22 @@ int cuda_st(cudaError_t e) {
   return e == cudaErrorMemoryAllocation ? TPT_ERR_OOM : TPT_ERR_CUDA;
 }
 
-// rhs = (D u) / g on every cell; block (128, 1, 1) along x, grid (x, y, z)
+// Per-call coefficient tables with g folded in: tab[d][i] = (1/dx_i) / g for
+// the divergence (n entries) and tab[3+d][f] = -g / dx_{f-1/2} for the
+// gradient (n + 1 entries), so each cell and face costs one float64 multiply
+// or fused multiply-add less.
+__global__ void coef_kernel(int n, const double* __restrict__ ixf, const double* __restrict__ ixc, double g,
+                            double* __restrict__ div_tab, double* __restrict__ grad_tab) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) div_tab[i] = ixf[i] / g;
+  if (i <= n) grad_tab[i] = -g * ixc[i];
+}
+
+// rhs = (D u) / g on every cell; block 128 along x, grid (x, y, z)
 __global__ void __launch_bounds__(128)
-div_kernel(int nx, int ny, int nz, const double* __restrict__ u, const double* __restrict__ v,
+div_kernel(int nx, int ny, const double* __restrict__ u, const double* __restrict__ v,
            const double* __restrict__ w, const double* __restrict__ ix, const double* __restrict__ iy,
-           const double* __restrict__ iz, double inv_g, double* __restrict__ rhs) {
+           const double* __restrict__ iz, double* __restrict__ rhs) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y, k = blockIdx.z;
   if (i >= nx) return;
@@ -35,51 +47,53 @@ div_kernel(int nx, int ny, int nz, const double* __restrict__ u, const double* _
   const long long sz = static_cast<long long>(nx) * ny;
   double d = (u[ou + 1] - u[ou]) * ix[i];
   d = fma(v[ov + nx] - v[ov], iy[j], d);
-  d = fma(w[ow + sz] - w[ow], iz[k], d);
-  rhs[ow] = d * inv_g;
+  rhs[ow] = fma(w[ow + sz] - w[ow], iz[k], d);
 }
 
-// u -= g G Phi on the faces of direction `dir`: interior faces, and the
-// shared boundary face of a periodic direction (written at both ends).
-// Face (f, a, b) of the direction, f = 0..n, a/b the other two indices.
+// vel -= g G Phi on the faces of direction DIR: interior faces, and the shared
+// boundary face of a periodic direction (written at both ends).  Block 128
+// along x of the velocity's own shape, grid (x, y, z) over it.
+template <int DIR>
 __global__ void __launch_bounds__(128)
-grad_kernel(int dir, int nx, int ny, int nz, int periodic, const double* __restrict__ phi,
-            const double* __restrict__ ic, double g, double* __restrict__ vel) {
-  const int n[3] = {nx, ny, nz};
-  const int ext = n[dir] + 1;   // faces along dir
-  // thread index over the face array, x fastest in the velocity's own shape
-  const long long t = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
-  const int sx = (dir == 0) ? ext : nx, sy = (dir == 1) ? ext : ny, szz = (dir == 2) ? ext : nz;
-  const long long total = static_cast<long long>(sx) * sy * szz;
-  if (t >= total) return;
-  const int i = static_cast<int>(t % sx);
-  const int j = static_cast<int>((t / sx) % sy);
-  const int k = static_cast<int>(t / (static_cast<long long>(sx) * sy));
-  const int f = (dir == 0) ? i : (dir == 1 ? j : k);
-  const int nn = n[dir];
+grad_kernel(int nx, int ny, int nz, int periodic, const double* __restrict__ phi, const double* __restrict__ cg,
+            double* __restrict__ vel) {
+  const int sx = nx + (DIR == 0), sy = ny + (DIR == 1);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y, k = blockIdx.z;
+  if (i >= sx) return;
+  const int f = (DIR == 0) ? i : (DIR == 1 ? j : k);
+  const int nn = (DIR == 0) ? nx : (DIR == 1 ? ny : nz);
   int lo = f - 1, hi = f;   // cells on both sides of the face
   if (f == 0 || f == nn) {
-    if (!periodic) return;   // wall face: no penetration, value kept
+    if (!periodic) return;  // wall face: no penetration, value kept
     lo = nn - 1;
     hi = 0;
   }
-  const long long s[3] = {1, static_cast<long long>(nx), static_cast<long long>(nx) * ny};
-  const long long base = (dir == 0 ? 0 : i) + (dir == 1 ? 0 : static_cast<long long>(j) * nx) +
-                         (dir == 2 ? 0 : static_cast<long long>(k) * nx * ny);
-  const double dp = phi[base + hi * s[dir]] - phi[base + lo * s[dir]];
-  vel[t] = fma(-g * ic[f], dp, vel[t]);
+  const long long step = (DIR == 0) ? 1 : (DIR == 1 ? nx : static_cast<long long>(nx) * ny);
+  const long long base = (DIR == 0 ? 0 : i) + (DIR == 1 ? 0 : static_cast<long long>(j) * nx) +
+                         (DIR == 2 ? 0 : static_cast<long long>(k) * nx * ny);
+  const double dp = phi[base + hi * step] - phi[base + lo * step];
+  const long long o = i + static_cast<long long>(sx) * (j + static_cast<long long>(sy) * k);
+  vel[o] = fma(cg[f], dp, vel[o]);
 }
 
 }  // namespace
 
 extern "C" {
 
+size_t align256(size_t b) { return (b + 255) & ~static_cast<size_t>(255); }
+
+// Workspace: rhs field | coefficient tables (6 x (n + 1) doubles) | solve workspace.
+size_t tables_bytes(const tpt_plan_s* p) {
+  return align256(6 * sizeof(double) * (1 + std::max(p->n[0], std::max(p->n[1], p->n[2]))));
+}
+
 int tpt_project_workspace_bytes(tpt_plan p, size_t* bytes) {
   if (!p || !bytes) return TPT_ERR_INVALID_ARG;
   size_t ws = 0;
   const int st = tpt_workspace_bytes(p, &ws);
   if (st != TPT_OK) return st;
-  *bytes = ((tpt::npts(p) * sizeof(double) + 255) & ~static_cast<size_t>(255)) + ws;
+  *bytes = align256(tpt::npts(p) * sizeof(double)) + tables_bytes(p) + ws;
   return TPT_OK;
 }
 
@@ -95,14 +109,21 @@ int tpt_project(tpt_plan p, double* u, double* v, double* w, double gamma_dt, do
   cudaSetDevice(p->dev);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
+  const int nmax = 1 + std::max(nx, std::max(ny, nz));
   double* rhs = static_cast<double*>(work);
-  char* solve_work = static_cast<char*>(work) + ((tpt::npts(p) * sizeof(double) + 255) & ~static_cast<size_t>(255));
+  double* tab = reinterpret_cast<double*>(static_cast<char*>(work) + align256(tpt::npts(p) * sizeof(double)));
+  char* solve_work = reinterpret_cast<char*>(tab) + tables_bytes(p);
   int st = TPT_OK;
-  {
+  for (int d = 0; d < 3 && st == TPT_OK; ++d) {
+    tpt::note_launch(1);
+    coef_kernel<<<(p->n[d] + 1 + 127) / 128, 128, 0, s>>>(p->n[d], p->d_inv_dxf[d], p->d_inv_dxc[d], gamma_dt,
+                                                          tab + d * nmax, tab + (3 + d) * nmax);
+    st = cuda_st(cudaGetLastError());
+  }
+  if (st == TPT_OK) {
     dim3 grid((nx + 127) / 128, ny, nz);
     tpt::note_launch(1);
-    div_kernel<<<grid, 128, 0, s>>>(nx, ny, nz, u, v, w, p->d_inv_dxf[0], p->d_inv_dxf[1], p->d_inv_dxf[2],
-                                    1.0 / gamma_dt, rhs);
+    div_kernel<<<grid, 128, 0, s>>>(nx, ny, u, v, w, tab, tab + nmax, tab + 2 * nmax, rhs);
     st = cuda_st(cudaGetLastError());
   }
   bool converged = true;
@@ -115,10 +136,13 @@ int tpt_project(tpt_plan p, double* u, double* v, double* w, double gamma_dt, do
   }
   double* vel[3] = {u, v, w};
   for (int d = 0; d < 3 && st == TPT_OK; ++d) {
-    const long long faces = static_cast<long long>(nx + (d == 0)) * (ny + (d == 1)) * (nz + (d == 2));
+    const int per = p->dir[d].periodic ? 1 : 0;
+    const double* cg = tab + (3 + d) * nmax;
+    dim3 grid((nx + (d == 0) + 127) / 128, ny + (d == 1), nz + (d == 2));
     tpt::note_launch(1);
-    grad_kernel<<<static_cast<unsigned>((faces + 127) / 128), 128, 0, s>>>(
-        d, nx, ny, nz, p->dir[d].periodic ? 1 : 0, phi, p->d_inv_dxc[d], gamma_dt, vel[d]);
+    if (d == 0) grad_kernel<0><<<grid, 128, 0, s>>>(nx, ny, nz, per, phi, cg, vel[d]);
+    else if (d == 1) grad_kernel<1><<<grid, 128, 0, s>>>(nx, ny, nz, per, phi, cg, vel[d]);
+    else grad_kernel<2><<<grid, 128, 0, s>>>(nx, ny, nz, per, phi, cg, vel[d]);
     st = cuda_st(cudaGetLastError());
   }
   if (prev >= 0) cudaSetDevice(prev);
