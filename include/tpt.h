@@ -53,8 +53,19 @@ extern "C" {
 /* Boundary rows of Sec. 2.2.1 ("modified as required by the boundary
  * conditions"): Neumann drops the outside coupling; periodic keeps it as the
  * cyclic corner (set on both ends); homogeneous Dirichlet (zero wall value at
- * the face) drops it and adds 2/dx^2 to -b of that row.                    */
-enum { TPT_BC_PERIODIC = 0, TPT_BC_NEUMANN = 1, TPT_BC_DIRICHLET = 2 };
+ * the face) drops it and adds 2/dx^2 to -b of that row.  DIRICHLET_NODE is
+ * homogeneous Dirichlet with the zero value at the neighbouring node, a
+ * centre spacing away (dxc[0] below the first unknown, dxc[n] above the
+ * last): the coupling is dropped and its coefficient kept on the diagonal;
+ * this is the wall row of face-centred unknowns (the wall-normal velocity,
+ * see tpt_grid_faces).  NONE (on both ends of x and/or y) removes the
+ * direction from the operator: the implicit-diffusion options of Sec. 2.1 /
+ * Sec. 3 in which only y, z ("yz") or only z ("z") are implicit, so the
+ * problem decouples along the removed direction and no transform runs along
+ * it (its eigenbasis is the identity with zero eigenvalues); it needs
+ * alpha != 0 and never applies to z.                                       */
+enum { TPT_BC_PERIODIC = 0, TPT_BC_NEUMANN = 1, TPT_BC_DIRICHLET = 2, TPT_BC_DIRICHLET_NODE = 3,
+       TPT_BC_NONE = 4 };
 
 /* Transform of a diagonalised direction (x or y), Sec. 3: numerical eigenbasis
  * applied as a GEMM, or the Fourier-based transform of a uniform direction
@@ -411,6 +422,17 @@ int tpt_server_destroy(tpt_server s);
  * uniform grid.  dxf_out: n doubles; dxc_out: n+1 doubles with the wrap
  * spacing (dx_0 + dx_{n-1})/2 at both ends.                               */
 int tpt_grid_tanh(int n, double L, double stretch, double* dxf_out, double* dxc_out);
+
+/* Spacings of the face-centred unknowns of one direction (a velocity
+ * component normal to the faces, Sec. 2.1), from the cell-centred spacings:
+ * each unknown sits on a face and its control volume spans the two adjacent
+ * centres.  Walls (periodic = 0): the n - 1 interior faces are the unknowns,
+ * widths dxc[1..n-1], centre spacings dxf[0..n-1] (use TPT_BC_DIRICHLET_NODE,
+ * the wall faces being boundary nodes); periodic: the n faces 0..n-1, widths
+ * dxc[0..n-1], spacings dxf[n-1], dxf[0..n-2], dxf[n-1] (wrap at both ends).
+ * Outputs: *n_out, dxf_out (*n_out values), dxc_out (*n_out + 1 values).    */
+int tpt_grid_faces(int n, const double* dxf, const double* dxc, int periodic, int* n_out, double* dxf_out,
+                   double* dxc_out);
 
 #ifdef __cplusplus
 }

@@ -49,6 +49,13 @@ R6 the eigenvalue of the null mode is set to exactly 0.
 R7 eigenvalues are recomputed as Rayleigh quotients of the float64 eigenvectors
    in long double, in the energy form of the symmetric row-scaled operator, so
    that the smallest eigenvalues carry relative (not absolute) accuracy.
+R10 two more boundary kinds.  DIRICHLET_NODE: homogeneous Dirichlet with the
+   zero value at the neighbouring node a centre spacing away (dxc[0] below,
+   dxc[n] above): the coupling is dropped and its coefficient kept on the
+   diagonal -- the wall row of face-centred unknowns, whose wall face is a
+   boundary node.  NONE: the direction is not in the operator (the
+   implicit-diffusion options yz and z of Sec. 2.1): zero rows, so the
+   problem decouples along it.
 R9 staggered velocity (projection): the x-velocity lives on the Nx + 1 x-faces
    of each x-line (face i between cells i-1 and i), likewise v, w; D u is the
    cell's net face flux over its width, (u_{i+1} - u_i)/dx_i summed over the
@@ -68,8 +75,9 @@ from __future__ import annotations
 
 import numpy as np
 
-PERIODIC, NEUMANN, DIRICHLET = 0, 1, 2
-_BC_NAMES = {"periodic": PERIODIC, "neumann": NEUMANN, "dirichlet": DIRICHLET}
+PERIODIC, NEUMANN, DIRICHLET, DIRICHLET_NODE, NONE = 0, 1, 2, 3, 4
+_BC_NAMES = {"periodic": PERIODIC, "neumann": NEUMANN, "dirichlet": DIRICHLET,
+             "dirichlet_node": DIRICHLET_NODE, "none": NONE}
 
 
 def _bc(code):
@@ -122,18 +130,44 @@ def operator_1d(dxf, dxc, bc):
     lo, hi = _bc(bc[0]), _bc(bc[1])
     if (lo == PERIODIC) != (hi == PERIODIC):
         raise ValueError("periodic must be set on both ends")
-    a = 1.0 / (dxf * dxc[:n])        # a_i = 1/(dx_i dx_{i-1/2})
-    c = 1.0 / (dxf * dxc[1:n + 1])   # c_i = 1/(dx_i dx_{i+1/2})
+    if (lo == NONE) != (hi == NONE):
+        raise ValueError("a direction outside the operator is so on both ends")
+    if lo == NONE:                   # R10: the direction is not in the operator
+        return np.zeros(n), np.zeros(n), np.zeros(n)
+    with np.errstate(divide="ignore"):
+        a = 1.0 / (dxf * dxc[:n])        # a_i = 1/(dx_i dx_{i-1/2})
+        c = 1.0 / (dxf * dxc[1:n + 1])   # c_i = 1/(dx_i dx_{i+1/2})
     w = np.zeros(n)
     if lo != PERIODIC:
-        a[0] = 0.0
-        c[n - 1] = 0.0
         if lo == DIRICHLET:
             w[0] += 2.0 / (dxf[0] * dxf[0])
         if hi == DIRICHLET:
             w[n - 1] += 2.0 / (dxf[n - 1] * dxf[n - 1])
+        if lo == DIRICHLET_NODE:     # R10: zero value at the node dxc[0] below
+            w[0] += a[0]
+        if hi == DIRICHLET_NODE:     # and at the node dxc[n] above
+            w[n - 1] += c[n - 1]
+        a[0] = 0.0
+        c[n - 1] = 0.0
     b = -((a + c) + w)
     return a, b, c
+
+
+def face_grid(dxf, dxc, periodic: bool):
+    """Spacings of the face-centred unknowns of a direction (R10): each unknown
+    sits on a face, its control volume spans the two neighbouring centres and
+    its neighbours are the adjacent faces.  Returns (widths, centre spacings)
+    in the convention of ``tanh_grid``."""
+    dxf = np.asarray(dxf, dtype=np.float64)
+    dxc = np.asarray(dxc, dtype=np.float64)
+    n = dxf.size
+    if periodic:                     # faces 0..n-1, face n is face 0
+        w = dxc[:n].copy()
+        s = np.empty(n + 1)
+        s[1:n] = dxf[:n - 1]
+        s[0] = s[n] = dxf[n - 1]
+        return w, s
+    return dxc[1:n].copy(), dxf.copy()   # interior faces 1..n-1, walls are nodes
 
 
 def dense_1d(a, b, c, periodic: bool):
@@ -167,6 +201,10 @@ class Direction:
     def has_null_mode(self) -> bool:
         """Periodic and Neumann-Neumann rows sum to zero: constants are in the kernel."""
         return self.periodic or self.bc == (NEUMANN, NEUMANN)
+
+    @property
+    def excluded(self) -> bool:
+        return self.bc[0] == NONE
 
     def dense(self):
         return dense_1d(self.a, self.b, self.c, self.periodic)

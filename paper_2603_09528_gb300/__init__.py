@@ -6,7 +6,7 @@ ImportError when it has not been built (there is no CPU fallback); the
 ``build`` submodule works without it.
 """
 _EXPORTS = ("Plan", "Batch", "Cache", "Server", "make_desc", "grid_tanh", "field_to_device", "field_to_host", "AUTO", "GEMM", "FFT",
-            "PERIODIC", "NEUMANN", "DIRICHLET", "FP64", "MIXED_BF16", "MIXED_BF16X3", "MIXED_TF32")
+            "PERIODIC", "NEUMANN", "DIRICHLET", "DIRICHLET_NODE", "NONE", "grid_faces", "FP64", "MIXED_BF16", "MIXED_BF16X3", "MIXED_TF32")
 __all__ = list(_EXPORTS)
 
 

@@ -22,7 +22,7 @@ TPT_ERR_NONFINITE = 7
 TPT_ERR_NUMERICAL = 8
 TPT_PENDING = 9
 
-TPT_BC_PERIODIC, TPT_BC_NEUMANN, TPT_BC_DIRICHLET = 0, 1, 2
+TPT_BC_PERIODIC, TPT_BC_NEUMANN, TPT_BC_DIRICHLET, TPT_BC_DIRICHLET_NODE, TPT_BC_NONE = 0, 1, 2, 3, 4
 TPT_XFORM_AUTO, TPT_XFORM_GEMM, TPT_XFORM_FFT = 0, 1, 2
 TPT_PREC_FP64, TPT_PREC_MIXED_BF16, TPT_PREC_MIXED_BF16X3, TPT_PREC_MIXED_TF32 = 0, 1, 2, 3
 
@@ -111,6 +111,7 @@ SIGNATURES = [
     ("tpt_plan_transforms", C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     ("tpt_plan_rows", C.c_int, [C.c_void_p, C.c_int, _dp, _dp, _dp]),
     ("tpt_grid_tanh", C.c_int, [C.c_int, C.c_double, C.c_double, _dp, _dp]),
+    ("tpt_grid_faces", C.c_int, [C.c_int, _dp, _dp, C.c_int, C.POINTER(C.c_int), _dp, _dp]),
     ("tpt_kernel_launches", C.c_int, [C.POINTER(C.c_ulonglong)]),
     ("tpt_set_stage_timing", C.c_int, [C.c_void_p, C.c_int]),
     ("tpt_set_refinement", C.c_int, [C.c_void_p, C.c_double, C.c_int]),

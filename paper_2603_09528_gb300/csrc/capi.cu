@@ -69,6 +69,11 @@ bool on_device(const tpt_plan_s* p) { return p && p->dev >= 0 && p->d_scal; }
 
 int apply_transform(const tpt_plan_s* p, int d, bool inverse, const double* in, double* out,
                     bool accumulate, cudaStream_t s) {
+  if (p->dir[d].excluded()) {   // identity transform: no GEMM along a direction outside the operator
+    if (!accumulate) return cuda_status(cudaMemcpyAsync(out, in, tpt::npts(p) * sizeof(double),
+                                                        cudaMemcpyDeviceToDevice, s));
+    return cuda_status(tpt::add_fp64(static_cast<long long>(tpt::npts(p)), in, out, s));
+  }
   if (p->xform[d] == TPT_XFORM_FFT) return cuda_status(tpt::fft_fp64(p, d, inverse, in, out, accumulate, s));
   const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
   const double* mat = inverse ? p->ddir[d].inv : p->ddir[d].fwd;
@@ -235,7 +240,8 @@ int create_plan_impl(const tpt_desc* desc, int cuda_device, tpt::BasisCache* cac
     int st = tpt::build_dir(desc->n[d], desc->dxf[d], desc->dxc[d], desc->bc[d], &p->dir[d]);
     if (st != TPT_OK) return fail(st);
   }
-  if (p->dir[2].periodic) return fail(TPT_ERR_UNSUPPORTED);
+  if (p->dir[2].periodic || p->dir[2].excluded()) return fail(TPT_ERR_UNSUPPORTED);
+  if ((p->dir[0].excluded() || p->dir[1].excluded()) && desc->alpha == 0.0) return fail(TPT_ERR_INVALID_ARG);
   for (int d = 0; d < 2; ++d) {
     // Fourier-based transforms: float64 path, uniform power-of-two directions
     const bool ok = tpt::fft_supported(p->dir[d]) && desc->precision == TPT_PREC_FP64;
@@ -402,6 +408,11 @@ int tpt_kernel_launches(unsigned long long* count) {
 
 int tpt_grid_tanh(int n, double L, double stretch, double* dxf_out, double* dxc_out) {
   return tpt::grid_tanh(n, L, stretch, dxf_out, dxc_out);
+}
+
+int tpt_grid_faces(int n, const double* dxf, const double* dxc, int periodic, int* n_out, double* dxf_out,
+                   double* dxc_out) {
+  return tpt::grid_faces(n, dxf, dxc, periodic, n_out, dxf_out, dxc_out);
 }
 
 int tpt_plan_create(const tpt_desc* desc, int cuda_device, tpt_plan* out) {

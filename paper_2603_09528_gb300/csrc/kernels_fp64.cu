@@ -225,6 +225,22 @@ field_sums_kernel(int nx, int ny, int nz, const double* __restrict__ f, const do
 
 }  // namespace
 
+namespace {
+__global__ void __launch_bounds__(256) add_kernel(long long n, const double* __restrict__ in, double* __restrict__ out) {
+  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n; i += stride)
+    out[i] += in[i];
+}
+}  // namespace
+
+cudaError_t add_fp64(long long n, const double* in, double* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const long long blocks = (n + 255) / 256;
+  note_launch(1);
+  add_kernel<<<static_cast<unsigned>(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(n, in, out);
+  return cudaGetLastError();
+}
+
 cudaError_t field_sums(const tpt_plan_s* p, const double* f, double* sums, cudaStream_t s) {
   int dev_sms = 152;
   cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, p->dev);

@@ -16,6 +16,23 @@
 
 namespace tpt {
 
+int grid_faces(int n, const double* dxf, const double* dxc, int periodic, int* n_out, double* dxf_out,
+               double* dxc_out) {
+  if (n < 1 || !dxf || !dxc || !n_out || !dxf_out || !dxc_out) return TPT_ERR_INVALID_ARG;
+  if (periodic) {
+    for (int j = 0; j < n; ++j) dxf_out[j] = dxc[j];            // face j spans centres j-1 .. j
+    dxc_out[0] = dxc_out[n] = dxf[n - 1];                       // faces n-1 and n = 0 across the wrap
+    for (int j = 1; j < n; ++j) dxc_out[j] = dxf[j - 1];        // faces j-1 and j
+    *n_out = n;
+    return TPT_OK;
+  }
+  if (n < 2) return TPT_ERR_INVALID_ARG;
+  for (int j = 0; j < n - 1; ++j) dxf_out[j] = dxc[j + 1];      // interior face j + 1
+  for (int j = 0; j <= n - 1; ++j) dxc_out[j] = dxf[j];         // faces j and j + 1 (walls at the ends)
+  *n_out = n - 1;
+  return TPT_OK;
+}
+
 int grid_tanh(int n, double L, double stretch, double* dxf, double* dxc) {
   if (n < 1 || !(L > 0.0) || !(stretch >= 0.0) || !dxf || !dxc) return TPT_ERR_INVALID_ARG;
   std::vector<double> xf(n + 1);
@@ -38,9 +55,9 @@ int grid_tanh(int n, double L, double stretch, double* dxf, double* dxc) {
 int build_dir(int n, const double* dxf, const double* dxc, const int bc[2], Dir1D* out) {
   if (n < 1 || !dxf || !dxc) return TPT_ERR_INVALID_ARG;
   for (int e = 0; e < 2; ++e)
-    if (bc[e] != TPT_BC_PERIODIC && bc[e] != TPT_BC_NEUMANN && bc[e] != TPT_BC_DIRICHLET)
-      return TPT_ERR_INVALID_ARG;
+    if (bc[e] < TPT_BC_PERIODIC || bc[e] > TPT_BC_NONE) return TPT_ERR_INVALID_ARG;
   if ((bc[0] == TPT_BC_PERIODIC) != (bc[1] == TPT_BC_PERIODIC)) return TPT_ERR_INVALID_ARG;
+  if ((bc[0] == TPT_BC_NONE) != (bc[1] == TPT_BC_NONE)) return TPT_ERR_INVALID_ARG;
   Dir1D& d = *out;
   d.n = n;
   d.bc[0] = bc[0];
@@ -50,22 +67,31 @@ int build_dir(int n, const double* dxf, const double* dxc, const int bc[2], Dir1
   d.dxc.assign(dxc, dxc + n + 1);
   for (int i = 0; i < n; ++i)
     if (!(dxf[i] > 0.0) || !std::isfinite(dxf[i])) return TPT_ERR_INVALID_ARG;
-  const int c0 = d.periodic ? 0 : 1, c1 = d.periodic ? n : n - 1;
-  for (int i = c0; i <= c1; ++i)
-    if (!(dxc[i] > 0.0) || !std::isfinite(dxc[i])) return TPT_ERR_INVALID_ARG;
   d.a.assign(n, 0.0);
   d.b.assign(n, 0.0);
   d.c.assign(n, 0.0);
+  if (bc[0] == TPT_BC_NONE) {   // not in the operator: zero rows, spacings only for volumes
+    d.uniform = false;
+    return TPT_OK;
+  }
+  // centre spacings in use: interior ones, plus the ends of a periodic
+  // direction or of a node-Dirichlet wall
+  const int c0 = (d.periodic || bc[0] == TPT_BC_DIRICHLET_NODE) ? 0 : 1;
+  const int c1 = (d.periodic || bc[1] == TPT_BC_DIRICHLET_NODE) ? n : n - 1;
+  for (int i = c0; i <= c1; ++i)
+    if (!(dxc[i] > 0.0) || !std::isfinite(dxc[i])) return TPT_ERR_INVALID_ARG;
   std::vector<double> wall(n, 0.0);
   for (int i = 0; i < n; ++i) {
     d.a[i] = 1.0 / (dxf[i] * dxc[i]);       // 1/(dx_i dx_{i-1/2})
     d.c[i] = 1.0 / (dxf[i] * dxc[i + 1]);   // 1/(dx_i dx_{i+1/2})
   }
   if (!d.periodic) {
-    d.a[0] = 0.0;
-    d.c[n - 1] = 0.0;
     if (bc[0] == TPT_BC_DIRICHLET) wall[0] += 2.0 / (dxf[0] * dxf[0]);
     if (bc[1] == TPT_BC_DIRICHLET) wall[n - 1] += 2.0 / (dxf[n - 1] * dxf[n - 1]);
+    if (bc[0] == TPT_BC_DIRICHLET_NODE) wall[0] += d.a[0];        // zero value at the node below
+    if (bc[1] == TPT_BC_DIRICHLET_NODE) wall[n - 1] += d.c[n - 1];
+    d.a[0] = 0.0;
+    d.c[n - 1] = 0.0;
   }
   for (int i = 0; i < n; ++i) d.b[i] = -((d.a[i] + d.c[i]) + wall[i]);
   // a direction is uniform when every width and every used centre spacing
@@ -218,6 +244,13 @@ double rayleigh(const Dir1D& d, const double* q) {
 
 int eigen_dir(const Dir1D& d, Eigen1D* out) {
   const int n = d.n;
+  if (d.excluded()) {   // identity eigenbasis, zero eigenvalues: no transform along d
+    out->lam.assign(n, 0.0);
+    out->qt.assign(static_cast<size_t>(n) * n, 0.0);
+    for (int i = 0; i < n; ++i) out->qt[static_cast<size_t>(i) * n + i] = 1.0;
+    out->null_mode = -1;
+    return TPT_OK;
+  }
   std::vector<double> s(n);
   for (int i = 0; i < n; ++i) s[i] = std::sqrt(d.dxf[i]);
   std::vector<double> lam, vec;
@@ -271,6 +304,7 @@ int eigen_dir(const Dir1D& d, Eigen1D* out) {
 }
 
 bool fft_supported(const Dir1D& d) {
+  if (d.excluded()) return false;
   const int n = d.n;
   const bool pow2 = n >= 1 && (n & (n - 1)) == 0;
   const bool bcs = d.periodic || (d.bc[0] == TPT_BC_NEUMANN && d.bc[1] == TPT_BC_NEUMANN);

@@ -24,6 +24,7 @@ struct Dir1D {
   bool has_null() const {
     return periodic || (bc[0] == TPT_BC_NEUMANN && bc[1] == TPT_BC_NEUMANN);
   }
+  bool excluded() const { return bc[0] == TPT_BC_NONE; }   // not in the operator
 };
 
 // Eigenbasis of one diagonalised direction: T = Q Lambda Q^{-1} with
@@ -45,6 +46,8 @@ bool fft_supported(const Dir1D& d);
 int fft_dir(const Dir1D& d, Eigen1D* out, int* kind);
 int eigen_dir(const Dir1D& d, Eigen1D* out);
 int grid_tanh(int n, double L, double stretch, double* dxf, double* dxc);
+int grid_faces(int n, const double* dxf, const double* dxc, int periodic, int* n_out, double* dxf_out,
+               double* dxc_out);
 
 // ----------------------------------------------------------------- device memory
 // Device tables of a plan or of a shared eigenbasis.  With a pool the tables
@@ -172,6 +175,9 @@ cudaError_t fft_fp64(const tpt_plan_s* p, int d, bool inverse, const double* in,
 
 cudaError_t thomas_fp64(const tpt_plan_s* p, const double* fhat, double* phihat, double* scratch,
                         double* defect, cudaStream_t s);
+
+// out += in over n values
+cudaError_t add_fp64(long long n, const double* in, double* out, cudaStream_t s);
 
 // sums[0..2] += (sum f^2, sum f, sum vol*f) over the field
 cudaError_t field_sums(const tpt_plan_s* p, const double* f, double* sums, cudaStream_t s);

@@ -18,10 +18,12 @@ from ._lib import check, lib
 
 AUTO, GEMM, FFT = _lib.TPT_XFORM_AUTO, _lib.TPT_XFORM_GEMM, _lib.TPT_XFORM_FFT
 PERIODIC, NEUMANN, DIRICHLET = _lib.TPT_BC_PERIODIC, _lib.TPT_BC_NEUMANN, _lib.TPT_BC_DIRICHLET
+DIRICHLET_NODE, NONE = _lib.TPT_BC_DIRICHLET_NODE, _lib.TPT_BC_NONE
 FP64 = _lib.TPT_PREC_FP64
 MIXED_BF16, MIXED_BF16X3, MIXED_TF32 = (_lib.TPT_PREC_MIXED_BF16, _lib.TPT_PREC_MIXED_BF16X3,
                                         _lib.TPT_PREC_MIXED_TF32)
-_BC = {"periodic": PERIODIC, "neumann": NEUMANN, "dirichlet": DIRICHLET}
+_BC = {"periodic": PERIODIC, "neumann": NEUMANN, "dirichlet": DIRICHLET, "dirichlet_node": DIRICHLET_NODE,
+       "none": NONE}
 
 
 def _ptr(t) -> C.c_void_p:
@@ -41,6 +43,19 @@ def grid_tanh(n: int, L: float = 1.0, stretch: float = 0.0):
     check(lib.tpt_grid_tanh(n, L, stretch, dxf.ctypes.data_as(_lib._dp),
                             dxc.ctypes.data_as(_lib._dp)), "tpt_grid_tanh")
     return dxf, dxc
+
+
+def grid_faces(dxf, dxc, periodic: bool):
+    """tpt_grid_faces: (widths, centre spacings) of the face-centred unknowns."""
+    dxf = np.ascontiguousarray(dxf, dtype=np.float64)
+    dxc = np.ascontiguousarray(dxc, dtype=np.float64)
+    n = dxf.size
+    wf, sc = np.empty(n), np.empty(n + 1)
+    m = C.c_int()
+    check(lib.tpt_grid_faces(n, dxf.ctypes.data_as(_lib._dp), dxc.ctypes.data_as(_lib._dp), int(bool(periodic)),
+                             C.byref(m), wf.ctypes.data_as(_lib._dp), sc.ctypes.data_as(_lib._dp)),
+          "tpt_grid_faces")
+    return wf[:m.value].copy(), sc[:m.value + 1].copy()
 
 
 def field_to_device(f: np.ndarray, device="cuda") -> torch.Tensor:

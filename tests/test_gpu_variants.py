@@ -1,0 +1,70 @@
+"""Method variants on GB300 against the oracle: the implicit-diffusion options
+yz and z of Sec. 2.1 (x, or x and y, outside the operator: no transform along
+them), and face-centred unknowns between walls (node-Dirichlet rows on the
+face grid), each for the float64 path (1e-12) and the refined split-bf16
+path (residual 1e-10, error against the oracle 1e-7)."""
+import numpy as np
+import pytest
+
+import oracle as O
+import seeded_inputs as S
+from _tpt import load
+
+pytestmark = pytest.mark.gpu
+tpt, L = load()
+
+X = O.NONE
+
+
+def _solve(n, grids, bcs, alpha, beta, prec, f):
+    mixed = prec != L.TPT_PREC_FP64
+    plan = tpt.Plan(n, [g[0] for g in grids], [g[1] for g in grids], bcs, xform=(tpt.GEMM, tpt.GEMM),
+                    alpha=alpha, beta=beta, precision=prec, rtol=1e-10 if mixed else 0.0,
+                    max_refine=30 if mixed else 1)
+    phi, info = plan.solve(tpt.field_to_device(f))
+    return tpt.field_to_host(phi, n), info
+
+
+def _check(prec, got, info, f, dirs, alpha, beta):
+    ref, _ = O.solve_tensor(f, dirs, alpha, beta)
+    err = np.abs(got - ref).max() / np.abs(ref).max()
+    if prec == L.TPT_PREC_FP64:
+        assert err <= 1e-12, err
+    else:
+        r = O.residual(f, got, dirs, alpha, beta, np.longdouble)
+        rel = float(np.sqrt(np.sum(r ** 2) / np.sum(f ** 2)))
+        assert info["rel_residual"] <= 1e-10 and rel <= 2e-10, (info, rel)
+        assert err <= 1e-7, err
+
+
+PRECS = [L.TPT_PREC_FP64, L.TPT_PREC_MIXED_BF16X3]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("option", ["yz", "z"])
+def test_implicit_options(prec, option):
+    n = (40, 36, 48)
+    bcs = [(X, X), (1, 1), (1, 2)] if option == "yz" else [(X, X), (X, X), (1, 2)]
+    grids = [O.tanh_grid(n[a], 1.0, s) for a, s in enumerate((1.5, 2.0, 2.5))]
+    dirs = [O.Direction(g[0], g[1], b) for g, b in zip(grids, bcs)]
+    alpha, beta = 1.0, -0.5 * 4e-3
+    f = S.uniform_rhs(n, 61)
+    got, info = _solve(n, grids, bcs, alpha, beta, prec, f)
+    _check(prec, got, info, f, dirs, alpha, beta)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_face_centred_wall_normal_component(prec):
+    # the x-velocity of a channel with walls in x: unknowns on the interior x-faces
+    # (node-Dirichlet walls), cell-centred in y (periodic) and z (walls, Dirichlet)
+    nc = (33, 24, 40)
+    cx = O.tanh_grid(nc[0], 1.0, 2.0)
+    fx = tpt.grid_faces(cx[0], cx[1], periodic=False)
+    grids = [fx, O.tanh_grid(nc[1], 1.0, 0.0), O.tanh_grid(nc[2], 1.0, 1.8)]
+    n = (fx[0].size, nc[1], nc[2])
+    bcs = [(O.DIRICHLET_NODE, O.DIRICHLET_NODE), (0, 0), (2, 2)]
+    dirs = [O.Direction(g[0], g[1], b) for g, b in zip(grids, bcs)]
+    alpha, beta = 1.0, -0.5 * 2e-3
+    f = S.uniform_rhs(n, 62)
+    got, info = _solve(n, grids, bcs, alpha, beta, prec, f)
+    _check(prec, got, info, f, dirs, alpha, beta)

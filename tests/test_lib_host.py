@@ -206,3 +206,45 @@ def test_tile_setters_and_batch_argument_checks():
     n = C.c_size_t()
     assert L.lib.tpt_batch_workspace_bytes(None, C.byref(n)) == L.TPT_ERR_INVALID_ARG
     assert L.lib.tpt_batch_destroy(None) == L.TPT_ERR_INVALID_ARG
+
+
+def test_node_dirichlet_rows_and_face_grid_match_the_oracle():
+    dxf, dxc = O.tanh_grid(20, 1.0, 2.3)
+    for periodic in (False, True):
+        wf, sc = tpt.grid_faces(dxf, dxc, periodic)
+        rw, rs = O.face_grid(dxf, dxc, periodic)
+        assert np.array_equal(wf, rw) and np.array_equal(sc, rs)
+    wf, sc = O.face_grid(dxf, dxc, False)
+    m = wf.size
+    grids = [(wf, sc), O.tanh_grid(8, 1.0, 1.0), O.tanh_grid(6, 1.0, 1.0)]
+    bcs = [(O.DIRICHLET_NODE, O.DIRICHLET_NODE), (1, 1), (1, 2)]
+    d, keep = _desc((m, 8, 6), grids, bcs, alpha=1.0, beta=-1e-3)
+    h = C.c_void_p()
+    assert L.lib.tpt_plan_create(C.byref(d), -1, C.byref(h)) == L.TPT_OK
+    a, b, c = np.empty(m), np.empty(m), np.empty(m)
+    assert L.lib.tpt_plan_rows(h, 0, a.ctypes.data_as(L._dp), b.ctypes.data_as(L._dp),
+                               c.ctypes.data_as(L._dp)) == L.TPT_OK
+    ra, rb, rc = O.operator_1d(wf, sc, bcs[0])
+    assert np.array_equal(a, ra) and np.array_equal(b, rb) and np.array_equal(c, rc)
+    L.lib.tpt_plan_destroy(h)
+
+
+def test_excluded_direction_rules():
+    grids = [O.tanh_grid(8, 1.0, 1.0)] * 3
+    h = C.c_void_p()
+    X = O.NONE
+    d, keep = _desc((8, 8, 8), grids, [(X, X), (1, 1), (1, 1)], alpha=1.0, beta=-1e-3)
+    assert L.lib.tpt_plan_create(C.byref(d), -1, C.byref(h)) == L.TPT_OK       # yz option
+    lam = np.empty(8)
+    assert L.lib.tpt_plan_eigenvalues(h, 0, lam.ctypes.data_as(L._dp)) == L.TPT_OK
+    assert np.all(lam == 0.0)
+    L.lib.tpt_plan_destroy(h)
+    d, keep = _desc((8, 8, 8), grids, [(X, X), (X, X), (1, 1)], alpha=1.0, beta=-1e-3)
+    assert L.lib.tpt_plan_create(C.byref(d), -1, C.byref(h)) == L.TPT_OK       # z option
+    L.lib.tpt_plan_destroy(h)
+    d, keep = _desc((8, 8, 8), grids, [(X, X), (1, 1), (1, 1)])                 # Poisson: degenerate
+    assert L.lib.tpt_plan_create(C.byref(d), -1, C.byref(h)) == L.TPT_ERR_INVALID_ARG
+    d, keep = _desc((8, 8, 8), grids, [(X, 1), (1, 1), (1, 1)], alpha=1.0, beta=-1e-3)
+    assert L.lib.tpt_plan_create(C.byref(d), -1, C.byref(h)) == L.TPT_ERR_INVALID_ARG
+    d, keep = _desc((8, 8, 8), grids, [(1, 1), (1, 1), (X, X)], alpha=1.0, beta=-1e-3)
+    assert L.lib.tpt_plan_create(C.byref(d), -1, C.byref(h)) == L.TPT_ERR_UNSUPPORTED

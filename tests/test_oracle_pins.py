@@ -394,3 +394,69 @@ def test_oracle_projection_is_divergence_free_and_idempotent(bcx):
         if not d.periodic:
             u = np.moveaxis(new[ax], ax, 0)
             assert np.all(u[0] == 0.0) and np.all(u[d.n] == 0.0)
+
+
+# ------------------------------ N3: node Dirichlet, face grids, yz / z options
+
+BC_DN, BC_X = O.DIRICHLET_NODE, O.NONE
+
+
+def test_node_dirichlet_eigenvalues_closed_form():
+    # uniform face-centred unknowns between two walls: m = n - 1 interior faces
+    # of spacing h; the rows are tridiag(1, -2, 1)/h^2 whose eigenvalues are
+    # -4/h^2 sin^2(k pi / (2 (m + 1))), k = 1..m
+    n, L = 17, 1.0
+    dxf, dxc = O.uniform_grid(n, L)
+    wf, sf = O.face_grid(dxf, dxc, periodic=False)
+    d = O.Direction(wf, sf, (BC_DN, BC_DN))
+    lam = np.sort(np.linalg.eigvalsh(d.dense()))
+    m, h = n - 1, L / n
+    ref = np.sort(-4.0 / h ** 2 * np.sin(np.arange(1, m + 1) * np.pi / (2 * (m + 1))) ** 2)
+    assert np.abs(lam - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_face_grid_control_volumes():
+    dxf, dxc = O.tanh_grid(14, 1.0, 2.2)
+    w, s = O.face_grid(dxf, dxc, periodic=False)
+    # the face control volumes tile [centre 0, centre n-1]; neighbours are a cell apart
+    assert w.size == 13 and s.size == 14
+    assert abs(w.sum() - (1.0 - 0.5 * dxf[0] - 0.5 * dxf[-1])) <= 1e-14
+    assert np.array_equal(s, dxf)
+    wp, sp = O.face_grid(*O.uniform_grid(8), periodic=True)
+    assert wp.size == 8 and sp.size == 9 and abs(wp.sum() - 1.0) <= 1e-14
+
+
+def test_z_option_is_independent_line_solves():
+    # only z in the operator: every (i, j) line is alpha + beta T_z alone
+    n = (6, 5, 9)
+    dirs = O.make_dirs(n, (1.5, 2.0, 2.5), [(BC_X, BC_X), (BC_X, BC_X), (BC_N, BC_D)])
+    alpha, beta = 1.0, -7e-3
+    f = S.uniform_rhs(n, 41)
+    got, _ = O.solve_tensor(f, dirs, alpha, beta)
+    dz = dirs[2]
+    ab = np.zeros((3, n[2]))
+    ab[0, 1:] = beta * dz.c[:-1]
+    ab[1, :] = alpha + beta * dz.b
+    ab[2, :-1] = beta * dz.a[1:]
+    ref = np.empty(n)
+    for i in range(n[0]):
+        for j in range(n[1]):
+            ref[i, j] = sla.solve_banded((1, 1), ab, f[i, j])
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_yz_option_is_independent_plane_solves():
+    # y and z in the operator: every x-plane is a 2D problem alpha + beta (T_y + T_z)
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    n = (5, 7, 6)
+    dirs = O.make_dirs(n, (1.0, 2.0, 1.5), [(BC_X, BC_X), (BC_P, BC_P), (BC_N, BC_N)])
+    alpha, beta = 1.0, -3e-3
+    f = S.uniform_rhs(n, 43)
+    got, _ = O.solve_tensor(f, dirs, alpha, beta)
+    ty, tz = sp.csr_matrix(dirs[1].dense()), sp.csr_matrix(dirs[2].dense())
+    a2 = alpha * sp.identity(n[1] * n[2]) + beta * (sp.kron(sp.identity(n[2]), ty) + sp.kron(tz, sp.identity(n[1])))
+    ref = np.empty(n)
+    for i in range(n[0]):
+        ref[i] = spla.spsolve(a2.tocsc(), f[i].ravel(order="F")).reshape(n[1], n[2], order="F")
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
