@@ -184,7 +184,17 @@ PRECISIONS = {"fp64": 0, "mixed_bf16": 1, "mixed_bf16x3": 2, "mixed_tf32": 3}
 # DRAM bytes (read + write) per grid point of one launch, from one ncu capture
 # of the named kernel (profiles/mixed_bf16x3_poisson512.md: 256^3 case, scaled
 # by points).  An entry must be removed when its kernel changes.
-MEASURED_TRAFFIC_PER_POINT = {("residual", "mixed_bf16x3"): (274.215936e6 + 54.527488e6) / 256 ** 3}
+# dram__bytes_read.sum + dram__bytes_write.sum per point of each stage's kernel, from one
+# ncu --set full capture at 384^3 (profiles/mixed_bf16x3_poisson512.md); traffic scales with
+# points.  The x-inverse GEMM is left out: the captured launch was a first correction, which
+# does not read phi, so its bytes differ from the average launch.
+MEASURED_TRAFFIC_PER_POINT = {
+    ("residual", "mixed_bf16x3"): (924.333824e6 + 213.527808e6) / 384 ** 3,
+    ("thomas", "mixed_bf16x3"): (226.63168e6 + 178.502144e6) / 384 ** 3,
+    ("x_forward", "mixed_bf16x3"): (227.265792e6 + 178.339328e6) / 384 ** 3,
+    ("y_forward", "mixed_bf16x3"): (227.145472e6 + 175.130624e6) / 384 ** 3,
+    ("y_inverse", "mixed_bf16x3"): (227.291904e6 + 178.37952e6) / 384 ** 3,
+}
 DTYPE = {"fp64": "f64", "mixed_bf16": "bf16/f32/f64", "mixed_bf16x3": "bf16x3/f32/f64",
          "mixed_tf32": "tf32/f32/f64"}
 
@@ -511,6 +521,22 @@ def serving_leg(tpt, device, prec, count, warmup, rate_hz=200.0, slots=4, stretc
                     rtol=1e-10 if mixed else 0.0, max_refine=30 if mixed else 1)
 
     specs = [spec(r) for r in reqs]
+    # the mesh library is known ahead of traffic: build every direction's
+    # eigenbasis once (R16), as a deployment would at start-up
+    t0w = time.perf_counter()
+    seen = set()
+    for r in reqs:
+        for a in range(2):
+            key = (r["n"][a], r["stretch"][a])
+            if key in seen:
+                continue
+            seen.add(key)
+            g = grids[key]
+            small = tpt.grid_tanh(8, 1.0, 1.0)
+            srv.warm(n=(key[0], 8, 8), dxf=[g[0], small[0], small[0]], dxc=[g[1], small[1], small[1]],
+                     bc=[(1, 1)] * 3, xform=(tpt.GEMM, tpt.GEMM), alpha=1.0, beta=-1e-3, precision=prec,
+                     rtol=0.0, max_refine=1)
+    t_warm = time.perf_counter() - t0w
     tickets = [None] * len(reqs)
     results = [None] * len(reqs)
     submitted = threading.Event()
@@ -541,6 +567,10 @@ def serving_leg(tpt, device, prec, count, warmup, rate_hz=200.0, slots=4, stretc
     span = max(x["t_done"] for x in meas) - min(x["t_submit"] for x in meas)
     pts = sum(r["n"][0] * r["n"][1] * r["n"][2] for r in reqs[warmup:])
     bad = sum(1 for x in meas if x["status"] != 0)
+    statuses = {}
+    for x in results:
+        if x["status"] != 0:
+            statuses[str(x["status"])] = statuses.get(str(x["status"]), 0) + 1
     return {"precision": {0: "fp64", 1: "mixed_bf16", 2: "mixed_bf16x3", 3: "mixed_tf32"}[prec],
             "requests": count, "warmup_requests": warmup, "offered_rate_hz": rate_hz,
             "slots": slots, "stretch_step": stretch_step,
@@ -549,7 +579,8 @@ def serving_leg(tpt, device, prec, count, warmup, rate_hz=200.0, slots=4, stretc
             "phase_ms_p50": {"plan": float(np.median(plan_ms)), "queue": float(np.median(queue_ms)),
                              "h2d_solve_d2h": float(np.median(run_ms))},
             "solves_per_s": count / span, "gpts_per_s": pts / span / 1e9,
-            "failed": bad, "max_rel_residual": float(max(x["rel_residual"] for x in meas)),
+            "failed": bad, "failed_statuses": statuses, "warm_s": t_warm, "warmed_plans": len(seen),
+            "max_rel_residual": float(max(x["rel_residual"] for x in meas)),
             "cache": {"hits": int(st["cache_hits"]), "misses": int(st["cache_misses"]),
                       "device_bytes": int(st["cache_bytes"])},
             "peak_inflight": int(st["peak_inflight"]), "peak_device_bytes": int(st["peak_bytes"])}

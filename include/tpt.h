@@ -403,6 +403,12 @@ int tpt_server_create(const tpt_server_config* cfg, tpt_server* out);
 int tpt_server_submit(tpt_server s, const tpt_desc* desc, const double* f_host, double* phi_host,
                       unsigned long long* ticket);
 
+/* Build the eigenbases (and their device tables) of desc's x and y
+ * directions in the server's cache now, so that later requests with those
+ * directions find them: a deployment warms the cache with its mesh library
+ * before traffic arrives.  Synchronous; safe beside running requests.      */
+int tpt_server_warm(tpt_server s, const tpt_desc* desc);
+
 /* Wait up to timeout_s seconds (< 0: no limit) for a request; on completion
  * fills *result, forgets the ticket and returns TPT_OK (the request's own
  * outcome is result->status); TPT_PENDING on timeout; INVALID_ARG for an

@@ -138,6 +138,7 @@ SIGNATURES = [
     ("tpt_server_create", C.c_int, [C.POINTER(tpt_server_config), C.POINTER(C.c_void_p)]),
     ("tpt_server_submit", C.c_int, [C.c_void_p, C.POINTER(tpt_desc), C.c_void_p, C.c_void_p,
                                     C.POINTER(C.c_ulonglong)]),
+    ("tpt_server_warm", C.c_int, [C.c_void_p, C.POINTER(tpt_desc)]),
     ("tpt_server_wait", C.c_int, [C.c_void_p, C.c_ulonglong, C.c_double, C.POINTER(tpt_result)]),
     ("tpt_server_now", C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     ("tpt_server_stats", C.c_int, [C.c_void_p, C.POINTER(tpt_serving_stats)]),

@@ -255,6 +255,15 @@ int tpt_server_submit(tpt_server s, const tpt_desc* desc, const double* f_host, 
   return TPT_OK;
 }
 
+int tpt_server_warm(tpt_server s, const tpt_desc* desc) {
+  if (!s || !desc) return TPT_ERR_INVALID_ARG;
+  if (s->cfg.cuda_device >= 0) cudaSetDevice(s->cfg.cuda_device);
+  tpt_plan p = nullptr;
+  const int st = tpt::create_plan(desc, s->cfg.cuda_device, &s->cache, &p);
+  if (p) tpt_plan_destroy(p);   // the plan was never used: its tables can go at once
+  return st;
+}
+
 int tpt_server_wait(tpt_server s, unsigned long long ticket, double timeout_s, tpt_result* result) {
   if (!s || !result) return TPT_ERR_INVALID_ARG;
   std::unique_lock<std::mutex> lk(s->mu);

@@ -323,6 +323,11 @@ class Server:
         self._held[int(t.value)] = (f_host, phi_host)
         return int(t.value)
 
+    def warm(self, **spec):
+        """tpt_server_warm: build the eigenbases of spec's x and y directions now."""
+        desc, keep = make_desc(**spec)
+        check(lib.tpt_server_warm(self._h, C.byref(desc)), "tpt_server_warm")
+
     def wait(self, ticket: int, timeout: float = -1.0):
         """The request's result dict, or None if it is still running after timeout."""
         r = _lib.tpt_result()

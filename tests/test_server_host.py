@@ -158,3 +158,16 @@ def test_host_cached_plans_equal_standalone_plans():
     # x of the second plan is y of the first and vice versa: 4 hits out of 6 lookups
     assert st["hits"] == 4 and st["misses"] == 2 and st["device_bytes"] == 0
     cache.close()
+
+
+def test_warm_fills_the_cache_before_traffic():
+    srv = tpt.Server(device=-1, slots=2, setup_threads=1, memory_budget=1 << 40, cache_budget=0,
+                     dry_run_ns_per_point=10.0)
+    srv.warm(**_spec((12, 16, 10), (2.0, 1.5, 1.0)))
+    st0 = srv.stats()
+    assert st0["cache_misses"] == 2 and st0["completed"] == 0
+    res = _run(srv, [((12, 16, 10), (2.0, 1.5, 1.0)), ((16, 12, 8), (1.5, 2.0, 1.0))])
+    st = srv.stats()
+    srv.close()
+    assert all(r["status"] == L.TPT_OK for r in res)
+    assert st["cache_misses"] == 2 and st["cache_hits"] == 4
