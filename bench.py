@@ -281,6 +281,26 @@ def run_ours(args):
     else:
         dom = max(stages["per_stage"], key=lambda d: d["ms_per_launch"] * d["launches_per_solve"])
 
+    # end-to-end through the host-buffer entry point
+    e2e = None
+    if not args.no_e2e:
+        phi_pin = torch.empty_like(f_pin).pin_memory()
+        f2 = plan.new_field()
+        plan.solve_host(f_pin, phi_pin, f2, phi, work, stream=stream)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            plan.solve_host(f_pin, phi_pin, f2, phi, work, stream=stream)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": solves / dt, "unit": "solves/s", "h2d_bytes_per_step": npts * 8,
+               "d2h_bytes_per_step": npts * 8}
+
     # float64 path on the same workload, for the FP64-vs-mixed comparison
     fp64 = None
     if prec != 0 and not args.no_fp64:
@@ -322,26 +342,6 @@ def run_ours(args):
         del plan13, phi13
         del w64, phi64, plan64
         torch.cuda.empty_cache()
-
-    # end-to-end through the host-buffer entry point
-    e2e = None
-    if not args.no_e2e:
-        phi_pin = torch.empty_like(f_pin).pin_memory()
-        f2 = plan.new_field()
-        plan.solve_host(f_pin, phi_pin, f2, phi, work, stream=stream)
-        torch.cuda.synchronize()
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            plan.solve_host(f_pin, phi_pin, f2, phi, work, stream=stream)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": solves / dt, "unit": "solves/s", "h2d_bytes_per_step": npts * 8,
-               "d2h_bytes_per_step": npts * 8}
 
     projection = None
     if not args.no_projection and prec != 0:
