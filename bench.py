@@ -149,7 +149,7 @@ def _threads():
 
 def run_reference(args):
     rank = _env_int("RANK", 0)
-    if rank != 0:
+    if not runs_reference_leg(rank):
         return 0
     n, _ = workload(args.size)
     nslab = max(1, min(n[2], args.cpu_slabs))
@@ -199,6 +199,30 @@ DTYPE = {"fp64": "f64", "mixed_bf16": "bf16/f32/f64", "mixed_bf16x3": "bf16x3/f3
          "mixed_tf32": "tf32/f32/f64"}
 
 
+def max_over_ranks(x: float, world: int, device: str) -> float:
+    """The maximum of x over the ranks of the process group (x itself on one
+    rank): the job's time is its slowest rank's."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: int, world: int, t_max_s: float) -> float:
+    """Whole-job throughput: the units every rank processed (replicas: each rank
+    solves its own instances, no collective on the data path) over the slowest
+    rank's time."""
+    return units_per_rank * world / t_max_s
+
+
+def runs_reference_leg(rank: int) -> bool:
+    """Under torchrun only rank 0 times the CPU oracle; the others exit 0."""
+    return rank == 0
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -232,7 +256,9 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
+    tiles = None
     if prec != 0:
+        tiles = plan.autotune(work, stream=stream)   # transform GEMM column tiles per stage
         plan.set_stage_timing(True)
     # warm-up
     info = None
@@ -259,13 +285,9 @@ def run_ours(args):
     clk = clocks.stop()
     per = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
     total_ms = evs[0].elapsed_time(evs[-1])
-    t_max = total_ms
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = max_over_ranks(total_ms, world, "cuda")
     solves = world * args.steps
-    value = solves / (t_max / 1e3)
+    value = job_rate(args.steps, world, t_max / 1e3)
     npts = n[0] * n[1] * n[2]
     stages = None
     if prec != 0 and infos and infos[0]:
@@ -293,12 +315,8 @@ def run_ours(args):
         for _ in range(args.steps):
             plan.solve_host(f_pin, phi_pin, f2, phi, work, stream=stream)
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([dt], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": solves / dt, "unit": "solves/s", "h2d_bytes_per_step": npts * 8,
+        dt = max_over_ranks(time.perf_counter() - t0, world, "cuda")
+        e2e = {"value": job_rate(args.steps, world, dt), "unit": "solves/s", "h2d_bytes_per_step": npts * 8,
                "d2h_bytes_per_step": npts * 8}
 
     # float64 path on the same workload, for the FP64-vs-mixed comparison
@@ -379,6 +397,7 @@ def run_ours(args):
                        if args.size == 512 else "poisson_%dcube_tanh1.5-2.0-2.5_neumann" % args.size,
                        "size": list(n), "stretch": list(stretch), "precision": args.precision,
                        "rtol": rtol, "max_refine": refine, "parallelism": "replicas%d" % world,
+                       "gemm_tiles": tiles,
                        "l2": "inputs larger than L2 (%.2f GB field)" % (npts * 8 / 1e9)},
             "gpts_per_s": value * npts / 1e9,
             "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99)),
