@@ -207,10 +207,34 @@ int tpt_residual(tpt_plan plan, const double* f_dev, const double* phi_dev, doub
  * device, rounded to the operand format of `precision` (TPT_PREC_MIXED_*:
  * bf16, bf16 hi/lo pair with three products, tf32), multiplied with
  * tcgen05.mma in float32, and written to D column-major (element (m, n) at
- * m + M*n) as float64.  Runs on the current device; work_dev is 256-byte
- * aligned scratch of at least 8*(M+N)*(K+8) + 1024 bytes.                   */
+ * m + M*n) as float64.  tile: column-tile width (0 = default, else 32, 64,
+ * 128, 256); pair: two-CTA clusters sharing an operand tile (0 none, 1 pairs
+ * of m-tiles share B, 2 pairs of n-tiles share A; used for split bf16 with
+ * 128/256-column tiles and an even tile count, else ignored).  Runs on the
+ * current device; work_dev is 256-byte aligned scratch of at least
+ * 8*(M+N)*(K+8) + 1024 bytes.                                               */
 int tpt_tc_gemm(int precision, int M, int N, int K, const double* A_dev, const double* B_dev,
-                double* D_dev, void* work_dev, void* stream);
+                double* D_dev, void* work_dev, void* stream, int tile, int pair);
+
+/* The same GEMM writing one of the transforms' intermediate formats, for
+ * kernel tests of the output paths: element (m, n) of D goes to index
+ *   (m % rm) + (m / rm) * sm + n * sn
+ * of out0 (and of out1, the low part, for TPT_GEMM_OUT_SPLIT_BF16), as
+ * float32 (TPT_GEMM_OUT_F32), bf16 rounded to nearest (TPT_GEMM_OUT_BF16) or
+ * a bf16 hi/lo pair (TPT_GEMM_OUT_SPLIT_BF16: hi = bf16(d), lo = bf16(d - hi)).
+ * tma_out = 1 lets the kernel stage each 32 x 32 output chunk in shared
+ * memory and store it with a bulk tensor copy, where the layout allows it
+ * (128/256-column tiles; rm >= M, or rm a multiple of 32 dividing M; 16-byte
+ * aligned bases and strides); 0 forces per-thread stores.  Elements outside
+ * the index set are left untouched.  Output buffers are the caller's, on the
+ * current device; other arguments as tpt_tc_gemm.  TPT_ERR_INVALID_ARG for
+ * an unknown kind, a non-positive size or rm, or a null pointer.           */
+#define TPT_GEMM_OUT_F32 0
+#define TPT_GEMM_OUT_BF16 1
+#define TPT_GEMM_OUT_SPLIT_BF16 2
+int tpt_tc_gemm_out(int precision, int M, int N, int K, const double* A_dev, const double* B_dev,
+                    int out_kind, int rm, long long sm, long long sn, void* out0_dev, void* out1_dev,
+                    void* work_dev, void* stream, int tile, int tma_out);
 
 /* Host copies of the plan's tables, for inspection and tests.  lam: n[dir]
  * eigenvalues of direction dir (0 = x, 1 = y) in the plan's mode order;
@@ -280,6 +304,14 @@ int tpt_plan_autotune(tpt_plan plan, void* work_dev, void* stream, int* tiles_ou
  * Not to be called while a solve on this plan is in flight.                */
 int tpt_plan_set_tiles(tpt_plan plan, const int* tiles);
 int tpt_plan_get_tiles(tpt_plan plan, int* tiles_out);
+
+/* Two-CTA operand sharing of the four transform GEMMs (0 none; 1 pairs of
+ * m-tiles share the B tile, 2 pairs of n-tiles share the A tile, through
+ * TMA multicast in a cluster of two): chosen by tpt_plan_autotune, or set
+ * here (each 0, 1 or 2, else INVALID_ARG; a mode that does not apply to a
+ * GEMM falls back to one CTA per tile).                                     */
+int tpt_plan_set_pairing(tpt_plan plan, const int* pairs);
+int tpt_plan_get_pairing(tpt_plan plan, int* pairs_out);
 
 /* ---- batched solves ------------------------------------------------------ */
 /* A batch owns `count` plans of possibly different sizes and coefficients on

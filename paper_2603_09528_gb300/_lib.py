@@ -25,6 +25,7 @@ TPT_PENDING = 9
 TPT_BC_PERIODIC, TPT_BC_NEUMANN, TPT_BC_DIRICHLET, TPT_BC_DIRICHLET_NODE, TPT_BC_NONE = 0, 1, 2, 3, 4
 TPT_XFORM_AUTO, TPT_XFORM_GEMM, TPT_XFORM_FFT = 0, 1, 2
 TPT_PREC_FP64, TPT_PREC_MIXED_BF16, TPT_PREC_MIXED_BF16X3, TPT_PREC_MIXED_TF32 = 0, 1, 2, 3
+TPT_GEMM_OUT_F32, TPT_GEMM_OUT_BF16, TPT_GEMM_OUT_SPLIT_BF16 = 0, 1, 2
 
 _dp = C.POINTER(C.c_double)
 
@@ -106,7 +107,10 @@ SIGNATURES = [
     ("tpt_residual", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                C.c_void_p]),
     ("tpt_tc_gemm", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
-                              C.c_void_p, C.c_void_p]),
+                              C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
+    ("tpt_tc_gemm_out", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
+                                  C.c_longlong, C.c_longlong, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_int, C.c_int]),
     ("tpt_plan_eigenvalues", C.c_int, [C.c_void_p, C.c_int, _dp]),
     ("tpt_plan_transforms", C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     ("tpt_plan_rows", C.c_int, [C.c_void_p, C.c_int, _dp, _dp, _dp]),
@@ -118,6 +122,8 @@ SIGNATURES = [
     ("tpt_plan_autotune", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]),
     ("tpt_plan_set_tiles", C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     ("tpt_plan_get_tiles", C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    ("tpt_plan_set_pairing", C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    ("tpt_plan_get_pairing", C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     ("tpt_batch_create", C.c_int, [C.POINTER(tpt_desc), C.c_int, C.c_int, C.c_int, C.POINTER(C.c_void_p)]),
     ("tpt_batch_workspace_bytes", C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
     ("tpt_batch_plan", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),

@@ -228,18 +228,20 @@ int tpt_batch_autotune(tpt_batch b, void* work, void* stream) {
   for (int i = 0; i < b->count; ++i) {
     tpt_plan p = b->plans[i];
     if (p->precision == TPT_PREC_FP64) continue;
-    int tiles[4] = {0, 0, 0, 0};
+    int tiles[4] = {0, 0, 0, 0}, pairs[4] = {0, 0, 0, 0};
     bool found = false;
     for (int j : done) {
       const tpt_plan q = b->plans[j];
       if (q->precision == p->precision && q->n[0] == p->n[0] && q->n[1] == p->n[1] && q->n[2] == p->n[2]) {
         tpt_plan_get_tiles(q, tiles);
+        tpt_plan_get_pairing(q, pairs);
         found = true;
         break;
       }
     }
     if (found) {
       BT_TRY(tpt_plan_set_tiles(p, tiles));
+      BT_TRY(tpt_plan_set_pairing(p, pairs));
       continue;
     }
     BT_TRY(tpt_plan_autotune(p, work, stream, nullptr));   // the batch workspace holds any one plan's

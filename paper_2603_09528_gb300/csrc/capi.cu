@@ -517,6 +517,22 @@ int tpt_plan_set_tiles(tpt_plan p, const int* tiles) {
   return TPT_OK;
 }
 
+int tpt_plan_set_pairing(tpt_plan p, const int* pairs) {
+  if (!p || !pairs) return TPT_ERR_INVALID_ARG;
+  for (int i = 0; i < 4; ++i)
+    if (pairs[i] < 0 || pairs[i] > 2) return TPT_ERR_INVALID_ARG;
+  if (p->precision == TPT_PREC_FP64) return TPT_OK;
+  for (int i = 0; i < 4; ++i) p->mixed.gemm_pair[i] = pairs[i];
+  ++p->generation;
+  return TPT_OK;
+}
+
+int tpt_plan_get_pairing(tpt_plan p, int* pairs_out) {
+  if (!p || !pairs_out) return TPT_ERR_INVALID_ARG;
+  for (int i = 0; i < 4; ++i) pairs_out[i] = (p->precision == TPT_PREC_FP64) ? 0 : p->mixed.gemm_pair[i];
+  return TPT_OK;
+}
+
 int tpt_plan_get_tiles(tpt_plan p, int* tiles_out) {
   if (!p || !tiles_out) return TPT_ERR_INVALID_ARG;
   for (int i = 0; i < 4; ++i) tiles_out[i] = (p->precision == TPT_PREC_FP64) ? 0 : p->mixed.gemm_bn[i];
@@ -575,14 +591,30 @@ int tpt_residual(tpt_plan p, const double* f, const double* phi, double* r, doub
 }
 
 int tpt_tc_gemm(int precision, int M, int N, int K, const double* A, const double* B, double* D,
-                void* work, void* stream) {
+                void* work, void* stream, int tile, int pair) {
+  if (tile != 0 && tile != 32 && tile != 64 && tile != 128 && tile != 256) return TPT_ERR_INVALID_ARG;
+  if (pair < 0 || pair > 2) return TPT_ERR_INVALID_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
     return TPT_ERR_CUDA;
   }
   if (reinterpret_cast<uintptr_t>(work) % 256 != 0) return TPT_ERR_INVALID_ARG;
-  return tpt::tc_gemm_test(precision, M, N, K, A, B, D, work, dev, static_cast<cudaStream_t>(stream));
+  return tpt::tc_gemm_test(precision, M, N, K, A, B, D, work, dev, static_cast<cudaStream_t>(stream), tile, pair);
+}
+
+int tpt_tc_gemm_out(int precision, int M, int N, int K, const double* A, const double* B, int out_kind, int rm,
+                    long long sm, long long sn, void* out0, void* out1, void* work, void* stream, int tile,
+                    int tma_out) {
+  if (tile != 0 && tile != 32 && tile != 64 && tile != 128 && tile != 256) return TPT_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return TPT_ERR_CUDA;
+  }
+  if (reinterpret_cast<uintptr_t>(work) % 256 != 0) return TPT_ERR_INVALID_ARG;
+  return tpt::tc_gemm_out_test(precision, M, N, K, A, B, out_kind, rm, sm, sn, out0, out1, work, dev,
+                               static_cast<cudaStream_t>(stream), tile, tma_out != 0);
 }
 
 int tpt_set_stage_timing(tpt_plan p, int enable) {

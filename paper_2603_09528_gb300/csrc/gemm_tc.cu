@@ -60,6 +60,10 @@ struct Cfg {
   static constexpr int STAGES = (kSmemBudget / STAGE) > 4 ? 4 : (kSmemBudget / STAGE);
   static constexpr int TMEM_COLS = 2 * BN < 32 ? 32 : 2 * BN;   // two accumulator buffers
   static constexpr int SMEM = STAGES * STAGE + 1024 /* alignment */ + 256 /* barriers */;
+  // TMA-store epilogue: per epilogue warp two 32 x 32 chunks of up to 8 bytes
+  // an element (split bf16: two 2-byte planes; float32: one 4-byte plane)
+  static constexpr int OSTAGE = 4 * 2 * 32 * 32 * 4;
+  static constexpr int SMEM_TMAO = STAGES * STAGE + 1024 + OSTAGE + 1024;
   static constexpr int NPROD = (NPL == 2) ? 3 : 1;
 };
 
@@ -129,16 +133,41 @@ __device__ __forceinline__ void tile_coords(const GemmOut& g, int num_m, int num
   n0 = nt * BN;
 }
 
+// Tile of work unit q for CTA rank r of a pair.  PAIR 0: one CTA per tile
+// (q is the tile).  PAIR 1: the two CTAs of a cluster take the m-tiles 2mp and
+// 2mp + 1 of one n-tile and share its B tile; PAIR 2: the n-tiles 2np and
+// 2np + 1 of one m-tile, sharing its A tile.
+template <int BN, int PAIR>
+__device__ __forceinline__ void unit_coords(const GemmOut& g, int num_m, int num_n, long long q, int r, int& m0,
+                                            int& n0) {
+  if (PAIR == 0) {
+    tile_coords<BN>(g, num_m, num_n, q, m0, n0);
+  } else if (PAIR == 1) {
+    const int num_mp = num_m / 2;
+    const int nt = static_cast<int>(g.n_fastest ? q % num_n : q / num_mp);
+    const int mp = static_cast<int>(g.n_fastest ? q / num_n : q % num_mp);
+    m0 = (2 * mp + r) * BM;
+    n0 = nt * BN;
+  } else {
+    const int num_np = num_n / 2;
+    const int np = static_cast<int>(g.n_fastest ? q % num_np : q / num_m);
+    const int mt = static_cast<int>(g.n_fastest ? q / num_np : q % num_m);
+    m0 = mt * BM;
+    n0 = (2 * np + r) * BN;
+  }
+}
+
 // Persistent kernel: each CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x,
 // ...  The tensor-memory accumulator is double-buffered (2 x BN columns): the
 // MMA warp fills buffer b for tile t while the epilogue drains buffer b^1 of
 // tile t-1.  Barriers: full/empty per smem stage (TMA <-> MMA), acc_full[b]
 // (MMA -> epilogue, one commit) and acc_empty[b] (epilogue -> MMA, one arrive
 // per epilogue warp).
-template <int KIND, int NPL, int BN, int OUT>
+template <int KIND, int NPL, int BN, int OUT, int PAIR, int TMAO>
 __global__ void __launch_bounds__(kThreads, 1)
 gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
                const __grid_constant__ CUtensorMap tB0, const __grid_constant__ CUtensorMap tB1,
+               const __grid_constant__ CUtensorMap tO0, const __grid_constant__ CUtensorMap tO1,
                const GemmOut g) {
   using C = Cfg<KIND, NPL, BN>;
   static_assert(C::STAGES >= 2, "shared-memory ring needs two stages");
@@ -153,13 +182,21 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int num_m = (g.M + BM - 1) / BM, num_n = (g.N + BN - 1) / BN;
   const long long num_tiles = static_cast<long long>(num_m) * num_n;
+  // work units: tiles, or tile pairs of a two-CTA cluster (the host checks
+  // that the paired tile count is even)
+  const long long num_units = PAIR ? num_tiles / 2 : num_tiles;
+  const long long unit0 = PAIR ? blockIdx.x / 2 : blockIdx.x;
+  const long long unit_step = PAIR ? gridDim.x / 2 : gridDim.x;
+  const int rank = PAIR ? static_cast<int>(ptx::cluster_ctarank()) : 0;
+  constexpr uint16_t kPairMask = 0x3;
   const int nk = (g.K + C::BK - 1) / C::BK;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(g.err);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) {
       ptx::mbar_init(ptx::smem_u32(&bars[s]), 1);
-      ptx::mbar_init(ptx::smem_u32(&bars[C::STAGES + s]), 1);
+      // a stage is free once the MMA of every CTA that reads it has finished
+      ptx::mbar_init(ptx::smem_u32(&bars[C::STAGES + s]), PAIR ? 2 : 1);
     }
     for (int b = 0; b < 2; ++b) {
       ptx::mbar_init(ptx::smem_u32(&accf[b]), 1);
@@ -173,6 +210,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
   }
   ptx::tc_fence_before();
   __syncthreads();
+  if (PAIR) ptx::cluster_sync();   // the peer's barriers exist before any remote arrive
   ptx::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
@@ -186,9 +224,9 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
     }
     bool ok = true;
     long long it = 0;
-    for (long long tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
+    for (long long q = unit0; q < num_units && ok; q += unit_step) {
       int m0, n0;
-      tile_coords<BN>(g, num_m, num_n, tile, m0, n0);
+      unit_coords<BN, PAIR>(g, num_m, num_n, q, rank, m0, n0);
       for (int kc = 0; kc < nk; ++kc, ++it) {
         const int s = static_cast<int>(it % C::STAGES);
         const long long round = it / C::STAGES;
@@ -203,11 +241,32 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
         const uint32_t full = ptx::smem_u32(&bars[s]);
         ptx::mbar_arrive_expect_tx(full, C::STAGE);
         const int kx = kc * C::BK;
-        ptx::tma_load_2d(ptx::smem_u32(st), &tA0, full, kx, m0);
-        ptx::tma_load_2d(ptx::smem_u32(st + NPL * C::A_BYTES), &tB0, full, kx, n0);
-        if (NPL == 2) {
-          ptx::tma_load_2d(ptx::smem_u32(st + C::A_BYTES), &tA1, full, kx, m0);
-          ptx::tma_load_2d(ptx::smem_u32(st + NPL * C::A_BYTES + C::B_BYTES), &tB1, full, kx, n0);
+        if (PAIR == 1) {          // own A; half of the shared B tile, to both CTAs
+          const int hb = BN / 2;
+          ptx::tma_load_2d(ptx::smem_u32(st), &tA0, full, kx, m0);   // n0: the pair's common n-tile
+          ptx::tma_load_2d_mc(ptx::smem_u32(st + NPL * C::A_BYTES + rank * hb * 128), &tB0, full, kx,
+                              n0 + rank * hb, kPairMask);
+          if (NPL == 2) {
+            ptx::tma_load_2d(ptx::smem_u32(st + C::A_BYTES), &tA1, full, kx, m0);
+            ptx::tma_load_2d_mc(ptx::smem_u32(st + NPL * C::A_BYTES + C::B_BYTES + rank * hb * 128), &tB1, full,
+                                kx, n0 + rank * hb, kPairMask);
+          }
+        } else if (PAIR == 2) {   // half of the shared A tile, to both CTAs; own B
+          const int ha = BM / 2;
+          ptx::tma_load_2d_mc(ptx::smem_u32(st + rank * ha * 128), &tA0, full, kx, m0 + rank * ha, kPairMask);
+          ptx::tma_load_2d(ptx::smem_u32(st + NPL * C::A_BYTES), &tB0, full, kx, n0);
+          if (NPL == 2) {
+            ptx::tma_load_2d_mc(ptx::smem_u32(st + C::A_BYTES + rank * ha * 128), &tA1, full, kx, m0 + rank * ha,
+                                kPairMask);
+            ptx::tma_load_2d(ptx::smem_u32(st + NPL * C::A_BYTES + C::B_BYTES), &tB1, full, kx, n0);
+          }
+        } else {
+          ptx::tma_load_2d(ptx::smem_u32(st), &tA0, full, kx, m0);
+          ptx::tma_load_2d(ptx::smem_u32(st + NPL * C::A_BYTES), &tB0, full, kx, n0);
+          if (NPL == 2) {
+            ptx::tma_load_2d(ptx::smem_u32(st + C::A_BYTES), &tA1, full, kx, m0);
+            ptx::tma_load_2d(ptx::smem_u32(st + NPL * C::A_BYTES + C::B_BYTES), &tB1, full, kx, n0);
+          }
         }
       }
     }
@@ -222,7 +281,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
     bool ok = true;
     long long it = 0;
     int tcount = 0;
-    for (long long tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x, ++tcount) {
+    for (long long q = unit0; q < num_units && ok; q += unit_step, ++tcount) {
       const int b = tcount & 1, use = tcount >> 1;
       if (use > 0)
         ok = ptx::mbar_wait(ptx::smem_u32(&acce[b]), static_cast<uint32_t>((use - 1) & 1), g.err,
@@ -253,15 +312,25 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
               ptx::mma_tf32(d, ptx::smem_desc_k_sw128(a), ptx::smem_desc_k_sw128(bb), idesc, acc);
           }
         }
-        ptx::mma_commit(ptx::smem_u32(&bars[C::STAGES + s]));   // frees the stage
+        if (PAIR) ptx::mma_commit_mc(ptx::smem_u32(&bars[C::STAGES + s]), kPairMask);   // frees the stage
+        else ptx::mma_commit(ptx::smem_u32(&bars[C::STAGES + s]));                  // in both CTAs
       }
       ptx::mma_commit(ptx::smem_u32(&accf[b]));                 // accumulator b ready
     }
   } else if (warp >= 2) {
     // ---------------------------------------------------------- epilogue
     const int quarter = warp % 4;                  // tensor-memory lanes 32*quarter ..
+    // TMA-store epilogue: each 32-row x 32-column chunk is written to a
+    // shared-memory staging buffer (column-major, rows contiguous, as in the
+    // output) and stored by one lane with a 3D bulk tensor store, two chunks
+    // in flight per warp
+    constexpr int OEB = (OUT == kOutF32) ? 4 : 2;
+    constexpr int ONPL = (OUT == kOutSplitBF16) ? 2 : 1;
+    constexpr int CHUNK = 32 * 32 * OEB;           // one plane of a chunk
+    uint8_t* ostage = smem + C::STAGES * C::STAGE + 1024 + quarter * (2 * ONPL * CHUNK);
+    int chunk_i = 0;
     int tcount = 0;
-    for (long long tile = blockIdx.x; tile < num_tiles; tile += gridDim.x, ++tcount) {
+    for (long long q = unit0; q < num_units; q += unit_step, ++tcount) {
       const int b = tcount & 1, use = tcount >> 1;
       const bool ok = ptx::mbar_wait(ptx::smem_u32(&accf[b]), static_cast<uint32_t>(use & 1), g.err,
                                      ptx::kErrWaitAccum);
@@ -270,7 +339,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
       // tcgen05.ld is warp-collective: decide for the whole warp
       if (!__all_sync(0xffffffffu, ok && !flagged)) break;
       int m0, n0;
-      tile_coords<BN>(g, num_m, num_n, tile, m0, n0);
+      unit_coords<BN, PAIR>(g, num_m, num_n, q, rank, m0, n0);
       const int m = m0 + quarter * 32 + lane;
       const bool mvalid = m < g.M;
       const long long mterm =
@@ -281,15 +350,54 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
         ptx::tmem_ld_32x32b_x32(tmem + (static_cast<uint32_t>(quarter * 32) << 16) +
                                     static_cast<uint32_t>(b * BN + c0), r);
         ptx::tmem_ld_wait();
-        if (mvalid) store_chunk<OUT>(g, mterm, n0 + c0, r);
+        if (TMAO) {
+          if (chunk_i >= 2) {                      // the store of chunk i-2 has left its buffer
+            if (lane == 0) ptx::bulk_wait_read<1>();
+            __syncwarp();
+          }
+          uint8_t* sb = ostage + (chunk_i & 1) * ONPL * CHUNK;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const float v = __uint_as_float(r[j]);
+            const int e = j * 32 + lane;
+            if (OUT == kOutSplitBF16) {
+              __nv_bfloat16 hi, lo;
+              split_bf16(v, hi, lo);
+              reinterpret_cast<__nv_bfloat16*>(sb)[e] = hi;
+              reinterpret_cast<__nv_bfloat16*>(sb + CHUNK)[e] = lo;
+            } else if (OUT == kOutBF16) {
+              reinterpret_cast<__nv_bfloat16*>(sb)[e] = __float2bfloat16_rn(v);
+            } else {
+              reinterpret_cast<float*>(sb)[e] = v;
+            }
+          }
+          ptx::fence_proxy_async_smem();
+          __syncwarp();
+          const int mc = m0 + quarter * 32;        // first row of the chunk
+          if (lane == 0 && mc < g.M && n0 + c0 < g.N) {
+            // boxes start inside the tensor; the TMA unit clips their far
+            // edges.  x stays a multiple of 32 elements: rm is a multiple of
+            // 32, or the output is one block of rows (x = m, z = 0)
+            const bool flat = g.rm >= g.M;
+            const int x = flat ? mc : mc % g.rm, z = flat ? 0 : mc / g.rm;
+            ptx::tma_store_3d(&tO0, ptx::smem_u32(sb), x, n0 + c0, z);
+            if (ONPL == 2) ptx::tma_store_3d(&tO1, ptx::smem_u32(sb + CHUNK), x, n0 + c0, z);
+            ptx::bulk_commit();
+          }
+          ++chunk_i;
+        } else if (mvalid) {
+          store_chunk<OUT>(g, mterm, n0 + c0, r);
+        }
       }
       ptx::tc_fence_before();
       __syncwarp();
       if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&acce[b]));   // buffer b may be refilled
     }
+    if (TMAO && lane == 0) ptx::bulk_wait_all();   // staging buffers stay until the stores are done
   }
   ptx::tc_fence_before();
   __syncthreads();
+  if (PAIR) ptx::cluster_sync();   // no CTA leaves while its peer may still signal it
   if (warp == 1) ptx::tmem_dealloc(tmem, C::TMEM_COLS);
 }
 
@@ -330,22 +438,57 @@ bool make_map(CUtensorMap* map, const void* base, int kind, int rows, int K, int
   return r == CUDA_SUCCESS;
 }
 
-template <int KIND, int NPL, int BN, int OUT>
+// Output tensor of the TMA-store epilogue: element (m, n) at (m % rm) +
+// (m / rm) sm + n sn is the 3D tensor {rm, N, M / rm} with strides (sn, sm)
+// (a single block of rows when rm >= M), box 32 x 32 x 1.
+bool make_out_map(CUtensorMap* map, void* base, int eb, const GemmOut& g) {
+  auto fn = encode_fn();
+  if (!fn || !base) return false;
+  const bool flat = g.rm >= g.M;
+  cuuint64_t dims[3] = {static_cast<cuuint64_t>(flat ? g.M : g.rm), static_cast<cuuint64_t>(g.N),
+                        static_cast<cuuint64_t>(flat ? 1 : g.M / g.rm)};
+  cuuint64_t strides[2] = {static_cast<cuuint64_t>(g.sn) * eb,
+                           static_cast<cuuint64_t>(flat ? g.sn * g.N : g.sm) * eb};
+  cuuint32_t box[3] = {32, 32, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || strides[0] % 16 != 0 || strides[1] % 16 != 0) return false;
+  std::memset(map, 0, sizeof(*map));
+  CUresult r = fn(map, eb == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims,
+                  strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int KIND, int NPL, int BN, int OUT, int PAIR, int TMAO = 0>
 cudaError_t launch(const Operand& A, const Operand& B, const GemmOut& g, cudaStream_t s) {
   using C = Cfg<KIND, NPL, BN>;
-  CUtensorMap m[4];
+  CUtensorMap m[6];
   std::memset(m, 0, sizeof(m));
-  if (!make_map(&m[0], A.plane[0], KIND, A.rows, A.K, A.ld, BM)) return cudaErrorInvalidValue;
-  if (!make_map(&m[2], B.plane[0], KIND, B.rows, B.K, B.ld, BN)) return cudaErrorInvalidValue;
+  if (TMAO) {
+    // layouts the tensor map cannot describe (unaligned base or strides) take
+    // the direct-store epilogue
+    const int eb = (OUT == kOutF32) ? 4 : 2;
+    if (!make_out_map(&m[4], g.out0, eb, g)) return launch<KIND, NPL, BN, OUT, PAIR, 0>(A, B, g, s);
+    if (OUT == kOutSplitBF16) {
+      if (!make_out_map(&m[5], g.out1, eb, g)) return launch<KIND, NPL, BN, OUT, PAIR, 0>(A, B, g, s);
+    } else {
+      m[5] = m[4];
+    }
+  }
+  // the shared operand of a pair is loaded in halves (one per CTA)
+  const int a_rows = PAIR == 2 ? BM / 2 : BM, b_rows = PAIR == 1 ? BN / 2 : BN;
+  if (!make_map(&m[0], A.plane[0], KIND, A.rows, A.K, A.ld, a_rows)) return cudaErrorInvalidValue;
+  if (!make_map(&m[2], B.plane[0], KIND, B.rows, B.K, B.ld, b_rows)) return cudaErrorInvalidValue;
   if (NPL == 2) {
-    if (!make_map(&m[1], A.plane[1], KIND, A.rows, A.K, A.ld, BM)) return cudaErrorInvalidValue;
-    if (!make_map(&m[3], B.plane[1], KIND, B.rows, B.K, B.ld, BN)) return cudaErrorInvalidValue;
+    if (!make_map(&m[1], A.plane[1], KIND, A.rows, A.K, A.ld, a_rows)) return cudaErrorInvalidValue;
+    if (!make_map(&m[3], B.plane[1], KIND, B.rows, B.K, B.ld, b_rows)) return cudaErrorInvalidValue;
   } else {
     m[1] = m[0];
     m[3] = m[2];
   }
-  auto kern = gemm_tc_kernel<KIND, NPL, BN, OUT>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+  auto kern = gemm_tc_kernel<KIND, NPL, BN, OUT, PAIR, TMAO>;
+  const int smem_bytes = TMAO ? C::SMEM_TMAO : C::SMEM;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
   if (e != cudaSuccess) return e;
   const long long tiles = static_cast<long long>((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN);
   if (tiles <= 0) return cudaSuccess;
@@ -353,19 +496,64 @@ cudaError_t launch(const Operand& A, const Operand& B, const GemmOut& g, cudaStr
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const long long cap = (g.max_ctas > 0 && g.max_ctas < sms) ? g.max_ctas : sms;
-  const long long ctas = tiles < cap ? tiles : cap;   // persistent: one CTA per SM
+  if (PAIR == 0) {
+    const long long ctas = tiles < cap ? tiles : cap;   // persistent: one CTA per SM
+    note_launch(1);
+    kern<<<static_cast<unsigned>(ctas), kThreads, smem_bytes, s>>>(m[0], m[1], m[2], m[3], m[4], m[5], g);
+    return cudaGetLastError();
+  }
+  // clusters of two CTAs, as many as can be resident at once (one CTA per SM)
+  cudaLaunchConfig_t cfg;
+  std::memset(&cfg, 0, sizeof(cfg));
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem_bytes;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  long long pairs = (cap / 2 < tiles / 2) ? cap / 2 : tiles / 2;
+  cfg.gridDim = dim3(static_cast<unsigned>(2 * pairs), 1, 1);
+  int resident = 0;
+  if (cudaOccupancyMaxActiveClusters(&resident, kern, &cfg) == cudaSuccess && resident > 0 && resident < pairs)
+    pairs = resident;
+  cudaGetLastError();
+  cfg.gridDim = dim3(static_cast<unsigned>(2 * pairs), 1, 1);
   note_launch(1);
-  kern<<<static_cast<unsigned>(ctas), kThreads, C::SMEM, s>>>(m[0], m[1], m[2], m[3], g);
+  e = cudaLaunchKernelEx(&cfg, kern, m[0], m[1], m[2], m[3], m[4], m[5], g);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
+}
+
+// Pair mode g.pair when it applies (split bf16 operands, 128- or 256-column
+// tiles, an even number of m-tiles (pair 1) or n-tiles (pair 2), an output
+// mode instantiated for it), else a single CTA per tile.
+template <int KIND, int NPL, int BN, int OUT>
+cudaError_t launch_pair(const Operand& A, const Operand& B, const GemmOut& g, cudaStream_t s) {
+  const int num_m = (g.M + BM - 1) / BM, num_n = (g.N + BN - 1) / BN;
+  constexpr bool can1 = NPL == 2 && BN >= 128 &&
+                        (OUT == kOutSplitBF16 || OUT == kOutBF16 || OUT == kOutF32 || OUT == kOutF64);
+  constexpr bool can2 = NPL == 2 && BN >= 128 && (OUT == kOutF32 || OUT == kOutDF || OUT == kOutF64);
+  if (g.pair == 1 && can1 && num_m % 2 == 0) return launch<KIND, NPL, BN, OUT, can1 ? 1 : 0>(A, B, g, s);
+  if (g.pair == 2 && can2 && num_n % 2 == 0) return launch<KIND, NPL, BN, OUT, can2 ? 2 : 0>(A, B, g, s);
+  // TMA-store epilogue when the output is a plain block of rows or whole
+  // 32-row chunks of rm-row blocks
+  constexpr bool cant = OUT == kOutSplitBF16 || OUT == kOutBF16 || OUT == kOutF32;
+  if (cant && g.tma_out && (g.rm >= g.M || (g.rm % 32 == 0 && g.M % g.rm == 0)))
+    return launch<KIND, NPL, BN, OUT, 0, cant ? 1 : 0>(A, B, g, s);
+  return launch<KIND, NPL, BN, OUT, 0>(A, B, g, s);
 }
 
 template <int KIND, int NPL, int OUT>
 cudaError_t launch_bn(const Operand& A, const Operand& B, const GemmOut& g, cudaStream_t s) {
   switch (g.bn ? g.bn : default_bn(g.N)) {
-    case 32: return launch<KIND, NPL, 32, OUT>(A, B, g, s);
-    case 64: return launch<KIND, NPL, 64, OUT>(A, B, g, s);
-    case 128: return launch<KIND, NPL, 128, OUT>(A, B, g, s);
-    case 256: return launch<KIND, NPL, 256, OUT>(A, B, g, s);
+    case 32: return launch<KIND, NPL, 32, OUT, 0>(A, B, g, s);
+    case 64: return launch<KIND, NPL, 64, OUT, 0>(A, B, g, s);
+    case 128: return launch_pair<KIND, NPL, 128, OUT>(A, B, g, s);
+    case 256: return launch_pair<KIND, NPL, 256, OUT>(A, B, g, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -1251,6 +1251,7 @@ tc::GemmOut gout(int M, int N, int K, int rm, long long sm, long long sn, void* 
 tc::GemmOut tuned(tc::GemmOut g, const MixedTables& m, int i) {
   g.bn = m.gemm_bn[i];
   g.max_ctas = m.gemm_ctas[i];
+  g.pair = m.gemm_pair[i];
   return g;
 }
 
@@ -1778,12 +1779,20 @@ int autotune_gemms(tpt_plan_s* p, void* work, cudaStream_t s) {
   for (int i = 0; i < 4 && status == TPT_OK; ++i) {
     const StageGemm t = stage_gemm(p, w, i, false);
     const int top = tc::default_bn(t.g.N);
+    // the operand common to neighbouring tiles: the transform matrix, which
+    // is B for the x forward and y inverse stages and A for the other two
+    const int share = (i == 0 || i == 2) ? 1 : 2;
     float best = 0.0f;
-    int best_bn = top;
-    for (int bn = 32; bn <= top && status == TPT_OK; bn *= 2) {
+    int best_bn = top, best_pair = 0;
+    bool first = true;
+    for (int cand = 0; cand < 8 && status == TPT_OK; ++cand) {
+      const int bn = 32 << (cand / 2), pair = (cand % 2) ? share : 0;
+      if (bn > top) break;
+      if (pair && (m.fmt != kFmtSplit || bn < 128)) continue;
       tc::GemmOut g = t.g;
       g.bn = bn;
       g.max_ctas = 0;
+      g.pair = pair;
       cudaError_t e = tc::gemm(kind, npl, t.a, t.b, g, s);   // warm-up
       if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
       for (int r = 0; r < kReps && e == cudaSuccess; ++r) e = tc::gemm(kind, npl, t.a, t.b, g, s);
@@ -1795,13 +1804,16 @@ int autotune_gemms(tpt_plan_s* p, void* work, cudaStream_t s) {
         status = TPT_ERR_CUDA;
         break;
       }
-      if (bn == 32 || ms < best) {
+      if (first || ms < best) {
         best = ms;
         best_bn = bn;
+        best_pair = pair;
+        first = false;
       }
     }
     m.gemm_bn[i] = best_bn;
     m.gemm_ctas[i] = 0;
+    m.gemm_pair[i] = best_pair;
   }
   for (cudaEvent_t& e : ev)
     if (e) cudaEventDestroy(e);
@@ -1810,7 +1822,11 @@ int autotune_gemms(tpt_plan_s* p, void* work, cudaStream_t s) {
   MX_CUDA(cudaMemcpyAsync(&errflag, w.scal + 15, sizeof(int), cudaMemcpyDeviceToHost, s));
   MX_CUDA(cudaStreamSynchronize(s));
   ++p->generation;
-  return errflag ? TPT_ERR_TIMEOUT : TPT_OK;
+  if (errflag) {   // a timed-out candidate aborts the ones after it, which then look fast
+    for (int i = 0; i < 4; ++i) m.gemm_bn[i] = m.gemm_pair[i] = 0;
+    return TPT_ERR_TIMEOUT;
+  }
+  return TPT_OK;
 }
 
 int mixed_info(const tpt_plan_s* p, const double* h, tpt_info* info) {
@@ -1832,7 +1848,7 @@ int mixed_info(const tpt_plan_s* p, const double* h, tpt_info* info) {
 }
 
 int tc_gemm_test(int precision, int M, int N, int K, const double* A, const double* B, double* D,
-                 void* work, int dev, cudaStream_t s) {
+                 void* work, int dev, cudaStream_t s, int tile, int pair) {
   if (M <= 0 || N <= 0 || K <= 0 || !A || !B || !D || !work) return TPT_ERR_INVALID_ARG;
   if (precision < TPT_PREC_MIXED_BF16 || precision > TPT_PREC_MIXED_TF32) return TPT_ERR_INVALID_ARG;
   const int fmt = fmt_of(precision);
@@ -1848,8 +1864,43 @@ int tc_gemm_test(int precision, int M, int N, int K, const double* A, const doub
   }
   MX_CUDA(pack_operand(fmt, M, K, ld, A, pa[0], pa[1], dev, s));
   MX_CUDA(pack_operand(fmt, N, K, ld, B, pb[0], pb[1], dev, s));
-  MX_CUDA(tc::gemm(kind_of(fmt), nplanes(fmt), operand(pa, M, K, ld), operand(pb, N, K, ld),
-                   gout(M, N, K, kBig, 0, M, D, nullptr, tc::kOutF64, 0, 0, nullptr), s));
+  tc::GemmOut g = gout(M, N, K, kBig, 0, M, D, nullptr, tc::kOutF64, 0, 0, nullptr);
+  g.bn = tile;
+  g.pair = pair;
+  MX_CUDA(tc::gemm(kind_of(fmt), nplanes(fmt), operand(pa, M, K, ld), operand(pb, N, K, ld), g, s));
+  return TPT_OK;
+}
+
+int tc_gemm_out_test(int precision, int M, int N, int K, const double* A, const double* B, int out_kind,
+                     int rm, long long sm, long long sn, void* out0, void* out1, void* work, int dev,
+                     cudaStream_t s, int tile, int tma_out) {
+  if (M <= 0 || N <= 0 || K <= 0 || rm <= 0 || !A || !B || !out0 || !work) return TPT_ERR_INVALID_ARG;
+  if (precision < TPT_PREC_MIXED_BF16 || precision > TPT_PREC_MIXED_TF32) return TPT_ERR_INVALID_ARG;
+  int mode;
+  switch (out_kind) {
+    case TPT_GEMM_OUT_F32: mode = tc::kOutF32; break;
+    case TPT_GEMM_OUT_BF16: mode = tc::kOutBF16; break;
+    case TPT_GEMM_OUT_SPLIT_BF16: mode = tc::kOutSplitBF16; break;
+    default: return TPT_ERR_INVALID_ARG;
+  }
+  if (mode == tc::kOutSplitBF16 && !out1) return TPT_ERR_INVALID_ARG;
+  const int fmt = fmt_of(precision);
+  const int ld = (K + 7) & ~7;
+  const size_t eb = elem_bytes(fmt);
+  char* w = static_cast<char*>(work);
+  void* pa[2] = {w, w + align256(eb * static_cast<size_t>(M) * ld)};
+  char* wb = w + 2 * align256(eb * static_cast<size_t>(M) * ld);
+  void* pb[2] = {wb, wb + align256(eb * static_cast<size_t>(N) * ld)};
+  if (nplanes(fmt) == 1) {
+    pa[1] = nullptr;
+    pb[1] = nullptr;
+  }
+  MX_CUDA(pack_operand(fmt, M, K, ld, A, pa[0], pa[1], dev, s));
+  MX_CUDA(pack_operand(fmt, N, K, ld, B, pb[0], pb[1], dev, s));
+  tc::GemmOut g = gout(M, N, K, rm, sm, sn, out0, out1, mode, 0, 0, nullptr);
+  g.bn = tile;
+  g.tma_out = tma_out;
+  MX_CUDA(tc::gemm(kind_of(fmt), nplanes(fmt), operand(pa, M, K, ld), operand(pb, N, K, ld), g, s));
   return TPT_OK;
 }
 

@@ -36,6 +36,10 @@ struct GemmOut {
   int* err;         // device flag for timed-out waits (may be null)
   int bn = 0;       // column tile width 32/64/128/256; 0 picks the smallest >= N
   int max_ctas = 0; // cap on the persistent CTAs; 0 = one per SM
+  int pair = 0;     // two-CTA clusters sharing an operand tile by TMA multicast:
+                    // 1 = pairs of m-tiles share B, 2 = pairs of n-tiles share A
+  int tma_out = 1;  // TMA-store epilogue where the output layout allows (split bf16,
+                    // bf16 or float32 out, 128/256-column tiles, one CTA per tile)
 };
 
 // Column tile width used when GemmOut::bn is 0.

@@ -91,6 +91,7 @@ struct MixedTables {
   // inverse): column tile width (0 = default) and persistent-CTA cap (0 = all)
   int gemm_bn[4] = {0, 0, 0, 0};
   int gemm_ctas[4] = {0, 0, 0, 0};
+  int gemm_pair[4] = {0, 0, 0, 0};  // two-CTA operand sharing (0 none, 1 share B, 2 share A)
 };
 
 struct FftTables {    // device tables of a Fourier-transformed direction
@@ -106,15 +107,6 @@ struct DevDir {       // device tables of a diagonalised direction (float64)
   double* inv = nullptr;  // inverse transform operand
   double* lam = nullptr;  // eigenvalues in mode order
 };
-
-// mixed-precision path (mixed.cu)
-int mixed_setup(tpt_plan_s* p);
-int mixed_set_beta(tpt_plan_s* p);   // rescale the residual tables after a coefficient change
-size_t mixed_workspace_bytes(const tpt_plan_s* p);
-int mixed_solve(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStream_t s,
-                tpt_info* info);
-int tc_gemm_test(int precision, int M, int N, int K, const double* A, const double* B, double* D,
-                 void* work, int dev, cudaStream_t s);
 
 }  // namespace tpt
 
@@ -193,7 +185,10 @@ size_t mixed_workspace_bytes(const tpt_plan_s* p);
 int mixed_solve(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStream_t s,
                 tpt_info* info);
 int tc_gemm_test(int precision, int M, int N, int K, const double* A, const double* B, double* D,
-                 void* work, int dev, cudaStream_t s);
+                 void* work, int dev, cudaStream_t s, int tile = 0, int pair = 0);
+int tc_gemm_out_test(int precision, int M, int N, int K, const double* A, const double* B, int out_kind,
+                     int rm, long long sm, long long sn, void* out0, void* out1, void* work, int dev,
+                     cudaStream_t s, int tile, int tma_out);
 
 // Capturable solves: 1 + max_refine corrections and a final residual, no host
 // synchronisation; the residual sums are left in the first 16 doubles of the

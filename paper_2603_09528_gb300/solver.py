@@ -253,6 +253,15 @@ class Plan:
         check(lib.tpt_plan_get_tiles(self._h, t), "tpt_plan_get_tiles")
         return tuple(int(v) for v in t)
 
+    def set_pairing(self, pairs):
+        t = (C.c_int * 4)(*[int(v) for v in pairs])
+        check(lib.tpt_plan_set_pairing(self._h, t), "tpt_plan_set_pairing")
+
+    def pairing(self):
+        t = (C.c_int * 4)()
+        check(lib.tpt_plan_get_pairing(self._h, t), "tpt_plan_get_pairing")
+        return tuple(int(v) for v in t)
+
     def close(self):
         if getattr(self, "_h", None):
             if self._owned:

@@ -16,7 +16,7 @@ tpt, L = load()
 PRECS = {"bf16": L.TPT_PREC_MIXED_BF16, "bf16x3": L.TPT_PREC_MIXED_BF16X3, "tf32": L.TPT_PREC_MIXED_TF32}
 
 
-def _tc_gemm(prec, A, B):
+def _tc_gemm(prec, A, B, tile=0, pair=0):
     M, K = A.shape
     N = B.shape[0]
     a = torch.from_numpy(np.ascontiguousarray(A)).cuda()
@@ -25,7 +25,7 @@ def _tc_gemm(prec, A, B):
     work = torch.empty(8 * (M + N) * (K + 8) + 1024, dtype=torch.uint8, device="cuda")
     st = L.lib.tpt_tc_gemm(PRECS[prec], M, N, K, C.c_void_p(a.data_ptr()), C.c_void_p(b.data_ptr()),
                            C.c_void_p(d.data_ptr()), C.c_void_p(work.data_ptr()),
-                           C.c_void_p(torch.cuda.current_stream().cuda_stream))
+                           C.c_void_p(torch.cuda.current_stream().cuda_stream), tile, pair)
     assert st == L.TPT_OK, L.lib.tpt_status_string(st)
     torch.cuda.synchronize()
     return d.cpu().numpy().T          # column-major D -> (M, N)
@@ -155,3 +155,99 @@ def test_mixed_refined_to_float64_accuracy_matches_oracle(prec):
     err = np.abs(tpt.field_to_host(phi, n) - ref).max() / np.abs(ref).max()
     print("fp64-accurate", prec, "iters", info["iters"], "err", err)
     assert err <= 1e-12
+
+
+PAIR_CASES = [((512, 512, 128), 256, 1), ((512, 512, 128), 256, 2), ((1024, 256, 96), 128, 1),
+              ((256, 768, 200), 128, 2), ((384, 512, 64), 256, 1),      # odd m-tile count: one CTA per tile
+              ((512, 640, 64), 256, 2)]                                # odd n-tile count: one CTA per tile
+
+
+@pytest.mark.parametrize("shape,tile,pair", PAIR_CASES)
+def test_tc_gemm_two_cta_pairs_exact(shape, tile, pair):
+    # clusters of two CTAs sharing an operand tile by TMA multicast must give
+    # exactly the products of small integers, as the single-CTA kernel does
+    M, N, K = shape
+    rng = np.random.default_rng(M + 3 * N + 7 * K + pair)
+    A = rng.integers(-8, 9, size=(M, K)).astype(np.float64)
+    B = rng.integers(-8, 9, size=(N, K)).astype(np.float64)
+    got = _tc_gemm("bf16x3", A, B, tile=tile, pair=pair)
+    assert np.array_equal(got, A @ B.T), (shape, tile, pair, np.abs(got - A @ B.T).max())
+
+
+def test_mixed_solve_with_two_cta_pairs_equals_default():
+    n = (256, 128, 64)
+    dirs = _dirs(n, (1.5, 2.0, 2.5), [(1, 1)] * 3)
+    f = S.remove_weighted_mean(S.uniform_rhs(n, 23), [d.dxf for d in dirs])
+    kw = dict(xform=(tpt.GEMM, tpt.GEMM), alpha=0.0, beta=1.0, precision=PRECS["bf16x3"], rtol=0.0, max_refine=3)
+    ref_plan = tpt.Plan(n, [d.dxf for d in dirs], [d.dxc for d in dirs], [(1, 1)] * 3, **kw)
+    ref, _ = ref_plan.solve(tpt.field_to_device(f))
+    plan = tpt.Plan(n, [d.dxf for d in dirs], [d.dxc for d in dirs], [(1, 1)] * 3, **kw)
+    plan.set_tiles((256, 128, 128, 256))
+    plan.set_pairing((1, 2, 1, 2))
+    assert plan.pairing() == (1, 2, 1, 2)
+    got, info = plan.solve(tpt.field_to_device(f))
+    a, r = got.cpu().numpy(), ref.cpu().numpy()
+    assert np.abs(a - r).max() <= 1e-12 * np.abs(r).max()
+
+
+def _tc_gemm_out(prec, A, B, kind, rm, sm, sn, size, tile, tma_out):
+    M, K = A.shape
+    N = B.shape[0]
+    a = torch.from_numpy(np.ascontiguousarray(A)).cuda()
+    b = torch.from_numpy(np.ascontiguousarray(B)).cuda()
+    dt = torch.float32 if kind == L.TPT_GEMM_OUT_F32 else torch.bfloat16
+    # sentinel everywhere: elements outside the index set must stay untouched
+    o0 = torch.full((size,), -7.25, dtype=dt, device="cuda")
+    o1 = torch.full((size,), -7.25, dtype=dt, device="cuda")
+    work = torch.empty(8 * (M + N) * (K + 8) + 1024, dtype=torch.uint8, device="cuda")
+    st = L.lib.tpt_tc_gemm_out(PRECS[prec], M, N, K, C.c_void_p(a.data_ptr()), C.c_void_p(b.data_ptr()), kind,
+                               rm, sm, sn, C.c_void_p(o0.data_ptr()), C.c_void_p(o1.data_ptr()),
+                               C.c_void_p(work.data_ptr()), C.c_void_p(torch.cuda.current_stream().cuda_stream),
+                               tile, tma_out)
+    assert st == L.TPT_OK, L.lib.tpt_status_string(st)
+    torch.cuda.synchronize()
+    return o0.float().cpu().numpy(), o1.float().cpu().numpy()
+
+
+# (M, N, K), rm, sm, sn: one block of rows (rm >= M), blocks of 32/64/96 rows
+# with padded block strides (the transforms' T1/T3 layouts), ragged M and N
+# edges, and a column stride that is not 16-byte aligned (direct stores)
+OUT_CASES = [((384, 512, 64), 1 << 30, 0, 400), ((200, 300, 72), 1 << 30, 0, 208),
+             ((256, 384, 96), 64, 64 * 384 + 32, 64), ((384, 256, 64), 96, 96 * 256 + 32, 96),
+             ((192, 200, 40), 32, 32 * 200 + 32, 32), ((160, 140, 64), 1 << 30, 0, 161)]
+
+
+@pytest.mark.parametrize("kind", ["f32", "bf16", "split"])
+@pytest.mark.parametrize("case", OUT_CASES)
+@pytest.mark.parametrize("tile", [128, 256])
+def test_tc_gemm_output_formats_and_layouts(kind, case, tile):
+    # the bulk-tensor-store epilogue and the per-thread stores must write the
+    # same values to the same indices and nothing else; the values are the
+    # exact integer products, rounded once to the output format
+    (M, N, K), rm, sm, sn = case
+    k = {"f32": L.TPT_GEMM_OUT_F32, "bf16": L.TPT_GEMM_OUT_BF16, "split": L.TPT_GEMM_OUT_SPLIT_BF16}[kind]
+    rng = np.random.default_rng(M + N + K + tile)
+    A = rng.integers(-40, 41, size=(M, K)).astype(np.float64)
+    B = rng.integers(-40, 41, size=(N, K)).astype(np.float64)
+    m = np.arange(M)[:, None]
+    n = np.arange(N)[None, :]
+    idx = (m % rm) + (m // rm) * sm + n * sn
+    size = int(idx.max()) + 1 + 64
+    outs = [_tc_gemm_out("bf16x3", A, B, k, rm, sm, sn, size, tile, t) for t in (1, 0)]
+    (t0, t1), (d0, d1) = outs
+    assert np.array_equal(t0, d0) and (kind != "split" or np.array_equal(t1, d1)), (kind, case, tile)
+    hi, lo = outs[0]
+    D = A @ B.T                                     # exact: |D| < 2^24
+    if kind == "f32":
+        assert np.array_equal(hi[idx], D)
+    else:
+        hb = torch.from_numpy(D).to(torch.bfloat16)
+        assert np.array_equal(hi[idx], hb.float().numpy())
+        if kind == "split":
+            lb = torch.from_numpy(D - hb.double().numpy()).to(torch.bfloat16)
+            assert np.array_equal(lo[idx], lb.float().numpy())
+    untouched = np.ones(size, bool)
+    untouched[idx.ravel()] = False
+    assert np.all(hi[untouched] == -7.25)
+    if kind == "split":
+        assert np.all(lo[untouched] == -7.25)
