@@ -313,6 +313,15 @@ int tpt_plan_get_tiles(tpt_plan plan, int* tiles_out);
 int tpt_plan_set_pairing(tpt_plan plan, const int* pairs);
 int tpt_plan_get_pairing(tpt_plan plan, int* pairs_out);
 
+/* Residual kernel of a TPT_PREC_MIXED_* plan (Sec. 4.1 residual in float
+ * pairs): 0 automatic (plane tiles staged in shared memory by TMA when Nx is
+ * a multiple of 4, else direct loads), 1 direct loads, 2 TMA-staged tiles
+ * where Nx allows.  Both compute every point with the same operations in the
+ * same order, so R is the same to the bit; only the summation order of the
+ * residual norm differs.  For kernel tests and measurements.  INVALID_ARG
+ * for another value; a no-op on float64 plans.                              */
+int tpt_plan_set_residual_kernel(tpt_plan plan, int variant);
+
 /* ---- batched solves ------------------------------------------------------ */
 /* A batch owns `count` plans of possibly different sizes and coefficients on
  * one device (Sec. 2.2: each instance is an independent tensor-product-Thomas

@@ -527,6 +527,14 @@ int tpt_plan_set_pairing(tpt_plan p, const int* pairs) {
   return TPT_OK;
 }
 
+int tpt_plan_set_residual_kernel(tpt_plan p, int variant) {
+  if (!p || variant < 0 || variant > 2) return TPT_ERR_INVALID_ARG;
+  if (p->precision == TPT_PREC_FP64) return TPT_OK;
+  p->mixed.res_kernel = variant;
+  ++p->generation;
+  return TPT_OK;
+}
+
 int tpt_plan_get_pairing(tpt_plan p, int* pairs_out) {
   if (!p || !pairs_out) return TPT_ERR_INVALID_ARG;
   for (int i = 0; i < 4; ++i) pairs_out[i] = (p->precision == TPT_PREC_FP64) ? 0 : p->mixed.gemm_pair[i];

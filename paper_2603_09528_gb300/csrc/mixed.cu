@@ -606,18 +606,19 @@ struct BRows {
 };
 
 // r = (f - fshift) - alpha phi - beta L phi in float-pair arithmetic, written
-// to R (operand format, rows of ldx), and sum r^2 -> sums[0].  Block (32, 4)
+// to R (operand format, rows of ldx), and sum r^2 -> sums[0]; fshift (the
+// volume-weighted mean of f) only for a singular problem (SING).  Block (32, 4)
 // over (i, j); blockIdx.z picks a segment of kseg planes that the thread
 // marches through with pointer increments (neighbour offsets are fixed per
 // thread; a neighbour past a non-periodic wall is the wrapped index and meets a
 // zero coefficient).
-template <int FMT, int HAS_ALPHA, int WX, int WY, int WZ>
+template <int FMT, int HAS_ALPHA, int WX, int WY, int WZ, int SING>
 __global__ void __launch_bounds__(128)
 residual_df_kernel(int nx, int ny, int nz, int ldx, int kseg, const float* __restrict__ fh,
                    const float* __restrict__ fl, const float* __restrict__ ph,
                    const float* __restrict__ pl, void* r0, void* r1, BRows RX, BRows RY, BRows RZ,
                    float alpha_h, float alpha_l, const double* __restrict__ fsums, double inv_vol,
-                   int singular, double* sums) {
+                   double* sums) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k0 = blockIdx.z * kseg;
@@ -631,7 +632,7 @@ residual_df_kernel(int nx, int ny, int nz, int ldx, int kseg, const float* __res
     const float axh = RX.ah[i], axl = RX.al[i], cxh = RX.ch[i], cxl = RX.cl[i];
     const float ayh = RY.ah[j], ayl = RY.al[j], cyh = RY.ch[j], cyl = RY.cl[j];
     df fshift = {0.0f, 0.0f};
-    if (singular) {
+    if (SING) {
       const double c = fsums[2] * inv_vol;
       const float chi = static_cast<float>(c);
       fshift = {chi, static_cast<float>(c - static_cast<double>(chi))};
@@ -651,21 +652,24 @@ residual_df_kernel(int nx, int ny, int nz, int ldx, int kseg, const float* __res
       const df xm = {hk[dxm], lk[dxm]}, xp = {hk[dxp], lk[dxp]};
       const df ym = {hk[dym], lk[dym]}, yp = {hk[dyp], lk[dyp]};
       const df fv = {*fhk, *flk};
-      df acc = {0.0f, 0.0f};
-      acc_flux(acc, axh, axl, xm, p0);
-      acc_flux(acc, cxh, cxl, xp, p0);
-      acc_flux(acc, ayh, ayl, ym, p0);
-      acc_flux(acc, cyh, cyl, yp, p0);
-      acc_flux(acc, RZ.ah[k], RZ.al[k], pm, p0);
-      acc_flux(acc, RZ.ch[k], RZ.cl[k], pp, p0);
-      if (WX) acc_mul(acc, -RX.wh[i], -RX.wl[i], p0);
-      if (WY) acc_mul(acc, -RY.wh[j], -RY.wl[j], p0);
-      if (WZ) acc_mul(acc, -RZ.wh[k], -RZ.wl[k], p0);
-      if (HAS_ALPHA) acc_mul(acc, alpha_h, alpha_l, p0);
-      df r = two_sum(fv.hi, -fshift.hi);
-      r.lo += fv.lo - fshift.lo;
-      const df t = two_sum(r.hi, -acc.hi);
-      const float rv = t.hi + (t.lo + (r.lo - acc.lo));
+      // r starts as f (less the compatibility shift of a singular problem)
+      // and each operator term is subtracted from it
+      df acc = fv;
+      if (SING) {
+        acc = two_sum(fv.hi, -fshift.hi);
+        acc.lo += fv.lo - fshift.lo;
+      }
+      acc_flux(acc, -axh, -axl, xm, p0);
+      acc_flux(acc, -cxh, -cxl, xp, p0);
+      acc_flux(acc, -ayh, -ayl, ym, p0);
+      acc_flux(acc, -cyh, -cyl, yp, p0);
+      acc_flux(acc, -RZ.ah[k], -RZ.al[k], pm, p0);
+      acc_flux(acc, -RZ.ch[k], -RZ.cl[k], pp, p0);
+      if (WX) acc_mul(acc, RX.wh[i], RX.wl[i], p0);
+      if (WY) acc_mul(acc, RY.wh[j], RY.wl[j], p0);
+      if (WZ) acc_mul(acc, RZ.wh[k], RZ.wl[k], p0);
+      if (HAS_ALPHA) acc_mul(acc, -alpha_h, -alpha_l, p0);
+      const float rv = acc.hi + acc.lo;
       Elem<FMT>::store(r0, r1, ro, rv);
       acc2 = fmaf(rv, rv, acc2);
       pm = p0;
@@ -729,20 +733,114 @@ struct Elem2<kFmtF32> {
   }
 };
 
+// Coefficients of the two points (i, i+1) of a thread that do not change
+// along z: the x rows of both points, the y row, and the wall diagonals.
+struct PairCoefs {
+  float axh0, axl0, cxh0, cxl0, axh1, axl1, cxh1, cxl1;
+  float ayh, ayl, cyh, cyl;
+  float wxh0, wxl0, wxh1, wxl1, wyh, wyl;
+};
+
+template <int WX, int WY>
+__device__ __forceinline__ PairCoefs pair_coefs(const BRows& RX, const BRows& RY, int i, int j) {
+  PairCoefs c;
+  c.axh0 = RX.ah[i];
+  c.axl0 = RX.al[i];
+  c.cxh0 = RX.ch[i];
+  c.cxl0 = RX.cl[i];
+  c.axh1 = RX.ah[i + 1];
+  c.axl1 = RX.al[i + 1];
+  c.cxh1 = RX.ch[i + 1];
+  c.cxl1 = RX.cl[i + 1];
+  c.ayh = RY.ah[j];
+  c.ayl = RY.al[j];
+  c.cyh = RY.ch[j];
+  c.cyl = RY.cl[j];
+  c.wxh0 = WX ? RX.wh[i] : 0.0f;
+  c.wxl0 = WX ? RX.wl[i] : 0.0f;
+  c.wxh1 = WX ? RX.wh[i + 1] : 0.0f;
+  c.wxl1 = WX ? RX.wl[i + 1] : 0.0f;
+  c.wyh = WY ? RY.wh[j] : 0.0f;
+  c.wyl = WY ? RY.wl[j] : 0.0f;
+  return c;
+}
+
+// z row of one plane: (a hi, a lo, c hi, c lo) and the wall diagonal
+struct ZCoef {
+  float ah, al, ch, cl, wh, wl;
+};
+
+// One plane of the residual of residual_df_kernel at the points a = (i, j, k)
+// and b = (i+1, j, k), from their neighbours (float pairs): the face between
+// a and b is differenced once, and dza / dzb hold the differences down from
+// plane k (carried from plane k - 1) and leave holding those down from plane
+// k + 1.  The operations applied to each point, and their order, are those
+// of residual_df_kernel, so the results are the same to the bit.
+template <int HAS_ALPHA, int WX, int WY, int WZ, int SING>
+__device__ __forceinline__ void residual_pair(const PairCoefs& c, const ZCoef& z, float alpha_h, float alpha_l,
+                                              df fshift, df p0a, df p0b, df ppa, df ppb, df xm, df xp, df yma,
+                                              df ymb, df ypa, df ypb, df fa, df fb, df& dza, df& dzb,
+                                              float rv[2]) {
+  const df dmid = df_diff(p0b, p0a);                          // across the face between the pair
+  const df dupa = df_diff(ppa, p0a), dupb = df_diff(ppb, p0b);
+  df acc_a = fa, acc_b = fb;
+  if (SING) {
+    acc_a = two_sum(fa.hi, -fshift.hi);
+    acc_a.lo += fa.lo - fshift.lo;
+    acc_b = two_sum(fb.hi, -fshift.hi);
+    acc_b.lo += fb.lo - fshift.lo;
+  }
+  acc_term(acc_a, -c.axh0, -c.axl0, df_diff(xm, p0a));
+  acc_term(acc_a, -c.cxh0, -c.cxl0, dmid);
+  acc_term(acc_a, -c.ayh, -c.ayl, df_diff(yma, p0a));
+  acc_term(acc_a, -c.cyh, -c.cyl, df_diff(ypa, p0a));
+  acc_term(acc_a, -z.ah, -z.al, dza);
+  acc_term(acc_a, -z.ch, -z.cl, dupa);
+  acc_term(acc_b, -c.axh1, -c.axl1, {-dmid.hi, -dmid.lo});
+  acc_term(acc_b, -c.cxh1, -c.cxl1, df_diff(xp, p0b));
+  acc_term(acc_b, -c.ayh, -c.ayl, df_diff(ymb, p0b));
+  acc_term(acc_b, -c.cyh, -c.cyl, df_diff(ypb, p0b));
+  acc_term(acc_b, -z.ah, -z.al, dzb);
+  acc_term(acc_b, -z.ch, -z.cl, dupb);
+  if (WX) {
+    acc_mul(acc_a, c.wxh0, c.wxl0, p0a);
+    acc_mul(acc_b, c.wxh1, c.wxl1, p0b);
+  }
+  if (WY) {
+    acc_mul(acc_a, c.wyh, c.wyl, p0a);
+    acc_mul(acc_b, c.wyh, c.wyl, p0b);
+  }
+  if (WZ) {
+    acc_mul(acc_a, z.wh, z.wl, p0a);
+    acc_mul(acc_b, z.wh, z.wl, p0b);
+  }
+  if (HAS_ALPHA) {
+    acc_mul(acc_a, -alpha_h, -alpha_l, p0a);
+    acc_mul(acc_b, -alpha_h, -alpha_l, p0b);
+  }
+  rv[0] = acc_a.hi + acc_a.lo;
+  rv[1] = acc_b.hi + acc_b.lo;
+  dza = {-dupa.hi, -dupa.lo};                                 // down from plane k + 1
+  dzb = {-dupb.hi, -dupb.lo};
+}
+
+__device__ __forceinline__ df fshift_of(const double* fsums, double inv_vol) {
+  const double c = fsums[2] * inv_vol;
+  const float chi = static_cast<float>(c);
+  return {chi, static_cast<float>(c - static_cast<double>(chi))};
+}
+
 // The residual of residual_df_kernel for even Nx, two neighbouring points
-// (i, i+1) per thread: float2 loads, the z-row coefficients read once for the
-// pair, the exact difference across the face between the two points computed
-// once, and the z-face difference carried from one plane to the next (the
-// difference up from plane k is, negated, the one down from plane k+1).  The
-// operations applied to each point, and their order, are those of
-// residual_df_kernel, so the result is the same to the bit.
-template <int FMT, int HAS_ALPHA, int WX, int WY, int WZ>
-__global__ void __launch_bounds__(128)
+// (i, i+1) per thread (residual_pair), marching through a segment of kseg
+// planes with the loads of plane k + 1 issued before the arithmetic of plane
+// k.  Used where the plane rows cannot be described by a tensor map.
+template <int FMT, int HAS_ALPHA, int WX, int WY, int WZ, int SING>
+__global__ void __launch_bounds__(128, 5)
 residual_df2_kernel(int nx, int ny, int nz, int ldx, int kseg, const float* __restrict__ fh,
                     const float* __restrict__ fl, const float* __restrict__ ph,
                     const float* __restrict__ pl, void* r0, void* r1, BRows RX, BRows RY, BRows RZ,
                     float alpha_h, float alpha_l, const double* __restrict__ fsums, double inv_vol,
-                    int singular, double* sums) {
+                    double* sums) {
   const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x);   // points i and i + 1
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k0 = blockIdx.z * kseg;
@@ -754,15 +852,8 @@ residual_df2_kernel(int nx, int ny, int nz, int ldx, int kseg, const float* __re
     const int dxm = (i == 0) ? nx - 1 : -1;                    // from point i
     const int dxp = (i + 1 == nx - 1) ? -(nx - 2) : 2;         // from point i (to i + 2 or the wrap)
     const int dym = (j == 0) ? (ny - 1) * nx : -nx, dyp = (j == ny - 1) ? -(ny - 1) * nx : nx;
-    const float axh0 = RX.ah[i], axl0 = RX.al[i], cxh0 = RX.ch[i], cxl0 = RX.cl[i];
-    const float axh1 = RX.ah[i + 1], axl1 = RX.al[i + 1], cxh1 = RX.ch[i + 1], cxl1 = RX.cl[i + 1];
-    const float ayh = RY.ah[j], ayl = RY.al[j], cyh = RY.ch[j], cyl = RY.cl[j];
-    df fshift = {0.0f, 0.0f};
-    if (singular) {
-      const double c = fsums[2] * inv_vol;
-      const float chi = static_cast<float>(c);
-      fshift = {chi, static_cast<float>(c - static_cast<double>(chi))};
-    }
+    const PairCoefs c = pair_coefs<WX, WY>(RX, RY, i, j);
+    const df fshift = SING ? fshift_of(fsums, inv_vol) : df{0.0f, 0.0f};
     const float* hk = ph + base + sz * k0;
     const float* lk = pl + base + sz * k0;
     const float* fhk = fh + base + sz * k0;
@@ -780,64 +871,41 @@ residual_df2_kernel(int nx, int ny, int nz, int ldx, int kseg, const float* __re
     df dza = df_diff(pma, p0a), dzb = df_diff(pmb, p0b);        // down from plane k0
     long long ro = i + static_cast<long long>(ldx) * (j + static_cast<long long>(ny) * k0);
     const long long rstep = static_cast<long long>(ldx) * ny;
-    for (int k = k0; k < k1; ++k) {
+    struct Loads {
+      float2 pph, ppl, ymh, yml, yph, ypl, fh, fl;
+      float xmh, xml, xph, xpl;
+      ZCoef z;
+    };
+    auto fetch = [&](int k, const float* h, const float* l, const float* f0, const float* f1, Loads& L) {
       const long long fwd = (k == nz - 1) ? -sz * (nz - 1) : sz;
-      df ppa, ppb, yma, ymb, ypa, ypb, fa, fb;
-      pair2(hk + fwd, lk + fwd, ppa, ppb);
-      pair2(hk + dym, lk + dym, yma, ymb);
-      pair2(hk + dyp, lk + dyp, ypa, ypb);
-      pair2(fhk, flk, fa, fb);
-      const df xm = {hk[dxm], lk[dxm]}, xp = {hk[dxp], lk[dxp]};
-      const float azh = RZ.ah[k], azl = RZ.al[k], czh = RZ.ch[k], czl = RZ.cl[k];
-      const df dmid = df_diff(p0b, p0a);                          // across the face between the pair
-      const df dupa = df_diff(ppa, p0a), dupb = df_diff(ppb, p0b);
-      df acc_a = {0.0f, 0.0f}, acc_b = {0.0f, 0.0f};
-      acc_term(acc_a, axh0, axl0, df_diff(xm, p0a));
-      acc_term(acc_a, cxh0, cxl0, dmid);
-      acc_term(acc_a, ayh, ayl, df_diff(yma, p0a));
-      acc_term(acc_a, cyh, cyl, df_diff(ypa, p0a));
-      acc_term(acc_a, azh, azl, dza);
-      acc_term(acc_a, czh, czl, dupa);
-      acc_term(acc_b, axh1, axl1, {-dmid.hi, -dmid.lo});
-      acc_term(acc_b, cxh1, cxl1, df_diff(xp, p0b));
-      acc_term(acc_b, ayh, ayl, df_diff(ymb, p0b));
-      acc_term(acc_b, cyh, cyl, df_diff(ypb, p0b));
-      acc_term(acc_b, azh, azl, dzb);
-      acc_term(acc_b, czh, czl, dupb);
-      if (WX) {
-        acc_mul(acc_a, -RX.wh[i], -RX.wl[i], p0a);
-        acc_mul(acc_b, -RX.wh[i + 1], -RX.wl[i + 1], p0b);
-      }
-      if (WY) {
-        acc_mul(acc_a, -RY.wh[j], -RY.wl[j], p0a);
-        acc_mul(acc_b, -RY.wh[j], -RY.wl[j], p0b);
-      }
-      if (WZ) {
-        acc_mul(acc_a, -RZ.wh[k], -RZ.wl[k], p0a);
-        acc_mul(acc_b, -RZ.wh[k], -RZ.wl[k], p0b);
-      }
-      if (HAS_ALPHA) {
-        acc_mul(acc_a, alpha_h, alpha_l, p0a);
-        acc_mul(acc_b, alpha_h, alpha_l, p0b);
-      }
+      L.pph = *reinterpret_cast<const float2*>(h + fwd);
+      L.ppl = *reinterpret_cast<const float2*>(l + fwd);
+      L.ymh = *reinterpret_cast<const float2*>(h + dym);
+      L.yml = *reinterpret_cast<const float2*>(l + dym);
+      L.yph = *reinterpret_cast<const float2*>(h + dyp);
+      L.ypl = *reinterpret_cast<const float2*>(l + dyp);
+      L.fh = *reinterpret_cast<const float2*>(f0);
+      L.fl = *reinterpret_cast<const float2*>(f1);
+      L.xmh = h[dxm];
+      L.xml = l[dxm];
+      L.xph = h[dxp];
+      L.xpl = l[dxp];
+      L.z = {RZ.ah[k], RZ.al[k], RZ.ch[k], RZ.cl[k], WZ ? RZ.wh[k] : 0.0f, WZ ? RZ.wl[k] : 0.0f};
+    };
+    Loads nxt;
+    fetch(k0, hk, lk, fhk, flk, nxt);
+    for (int k = k0; k < k1; ++k) {
+      const Loads L = nxt;
+      if (k + 1 < k1) fetch(k + 1, hk + sz, lk + sz, fhk + sz, flk + sz, nxt);
+      const df ppa = {L.pph.x, L.ppl.x}, ppb = {L.pph.y, L.ppl.y};
       float rv[2];
-      {
-        df r = two_sum(fa.hi, -fshift.hi);
-        r.lo += fa.lo - fshift.lo;
-        const df t = two_sum(r.hi, -acc_a.hi);
-        rv[0] = t.hi + (t.lo + (r.lo - acc_a.lo));
-      }
-      {
-        df r = two_sum(fb.hi, -fshift.hi);
-        r.lo += fb.lo - fshift.lo;
-        const df t = two_sum(r.hi, -acc_b.hi);
-        rv[1] = t.hi + (t.lo + (r.lo - acc_b.lo));
-      }
+      residual_pair<HAS_ALPHA, WX, WY, WZ, SING>(c, L.z, alpha_h, alpha_l, fshift, p0a, p0b, ppa, ppb,
+                                                 {L.xmh, L.xml}, {L.xph, L.xpl}, {L.ymh.x, L.yml.x},
+                                                 {L.ymh.y, L.yml.y}, {L.yph.x, L.ypl.x}, {L.yph.y, L.ypl.y},
+                                                 {L.fh.x, L.fl.x}, {L.fh.y, L.fl.y}, dza, dzb, rv);
       Elem2<FMT>::store(r0, r1, ro, rv[0], rv[1]);
       acc2 = fmaf(rv[0], rv[0], acc2);
       acc2 = fmaf(rv[1], rv[1], acc2);
-      dza = {-dupa.hi, -dupa.lo};                                 // down from plane k + 1
-      dzb = {-dupb.hi, -dupb.lo};
       p0a = ppa;
       p0b = ppb;
       hk += sz;
@@ -849,6 +917,182 @@ residual_df2_kernel(int nx, int ny, int nz, int ldx, int kseg, const float* __re
   }
   double s2 = warp_sum_d(static_cast<double>(acc2));
   if ((threadIdx.x + blockDim.x * threadIdx.y) % 32 == 0) atomicAdd(&sums[0], s2);
+}
+
+// ---------------------------------------------------------------------------
+// TMA-staged residual.  A block owns a tile of kResTX x kResTY points of the
+// (x, y) plane and a segment of up to kResKseg planes; a producer warp
+// streams, plane by plane, the phi pair with a halo (x from i0 - 4 to
+// i0 + kResTX + 4, rows j0 - 1 to j0 + kResTY) and the f pair of the tile into
+// a ring of shared-memory stages.  The tensor maps are 2D over the rows
+// (j + Ny k) of the field, so a halo row past a tile's y edge is a row of the
+// neighbouring plane, or outside the tensor and zero; either meets a zero
+// coefficient unless the direction is periodic, where the edge points load
+// the wrapped neighbour directly.  Each consumer warp takes one row of the
+// tile, two points per lane, and applies residual_pair, so the results equal
+// residual_df2_kernel's.
+constexpr int kResTX = 64, kResTY = 8, kResStages = 5, kResKseg = 64;
+constexpr int kResPW = kResTX + 8;                         // phi row: 4 halo columns each side
+constexpr int kResPBytes = ((kResPW * (kResTY + 2) * 4 + 127) / 128) * 128;
+constexpr int kResFBytes = kResTX * kResTY * 4;
+constexpr int kResStage = 2 * kResPBytes + 2 * kResFBytes;
+constexpr int kResZBytes = kResKseg * static_cast<int>(sizeof(ZCoef));
+constexpr int kResSmem = kResStages * kResStage + 2 * kResStages * 8 + kResZBytes + 128;
+constexpr int kResThreads = 32 * (kResTY + 1);
+
+template <int FMT, int HAS_ALPHA, int WX, int WY, int WZ, int SING>
+__global__ void __launch_bounds__(kResThreads, 3)
+residual_tma_kernel(const __grid_constant__ CUtensorMap tPH, const __grid_constant__ CUtensorMap tPL,
+                    const __grid_constant__ CUtensorMap tFH, const __grid_constant__ CUtensorMap tFL, int nx,
+                    int ny, int nz, int ldx, int px, int py, const float* __restrict__ ph,
+                    const float* __restrict__ pl, void* r0, void* r1, BRows RX, BRows RY, BRows RZ,
+                    float alpha_h, float alpha_l, const double* __restrict__ fsums, double inv_vol,
+                    double* sums, int* err) {
+  extern __shared__ __align__(128) uint8_t res_smem_raw[];
+  uint8_t* smem = res_smem_raw + ((128u - (ptx::smem_u32(res_smem_raw) & 127u)) & 127u);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kResStages * kResStage);
+  uint64_t* empty = full + kResStages;
+  ZCoef* zc = reinterpret_cast<ZCoef*>(empty + kResStages);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int i0 = blockIdx.x * kResTX, j0 = blockIdx.y * kResTY;
+  const int k0 = blockIdx.z * kResKseg;
+  const int k1 = min(nz, k0 + kResKseg);
+  const int nplanes = k1 - k0 + 2;                           // planes k0 - 1 .. k1
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kResStages; ++s) {
+      ptx::mbar_init(ptx::smem_u32(&full[s]), 1);
+      ptx::mbar_init(ptx::smem_u32(&empty[s]), kResTY);
+    }
+    ptx::fence_mbar_init();
+  }
+  for (int t = threadIdx.x; t < k1 - k0; t += kResThreads) {
+    const int k = k0 + t;
+    zc[t] = {RZ.ah[k], RZ.al[k], RZ.ch[k], RZ.cl[k], WZ ? RZ.wh[k] : 0.0f, WZ ? RZ.wl[k] : 0.0f};
+  }
+  __syncthreads();
+  if (warp == kResTY) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      ptx::prefetch_tmap(&tPH);
+      ptx::prefetch_tmap(&tPL);
+      ptx::prefetch_tmap(&tFH);
+      ptx::prefetch_tmap(&tFL);
+      int s = 0;
+      uint32_t par = 0;
+      for (int q = 0; q < nplanes; ++q) {
+        if (q >= kResStages && !ptx::mbar_wait(ptx::smem_u32(&empty[s]), par ^ 1u, err, ptx::kErrWaitEmpty)) break;
+        const int kk = (k0 - 1 + q + nz) % nz;               // wrapped plane
+        const bool with_f = q >= 1 && q < nplanes - 1;
+        uint8_t* st = smem + s * kResStage;
+        const uint32_t bar = ptx::smem_u32(&full[s]);
+        ptx::mbar_arrive_expect_tx(bar, 2 * kResPW * (kResTY + 2) * 4 + (with_f ? 2 * kResFBytes : 0));
+        const int yrow = j0 - 1 + ny * kk;
+        ptx::tma_load_2d(ptx::smem_u32(st), &tPH, bar, i0 - 4, yrow);
+        ptx::tma_load_2d(ptx::smem_u32(st + kResPBytes), &tPL, bar, i0 - 4, yrow);
+        if (with_f) {
+          ptx::tma_load_2d(ptx::smem_u32(st + 2 * kResPBytes), &tFH, bar, i0, j0 + ny * kk);
+          ptx::tma_load_2d(ptx::smem_u32(st + 2 * kResPBytes + kResFBytes), &tFL, bar, i0, j0 + ny * kk);
+        }
+        if (++s == kResStages) {
+          s = 0;
+          par ^= 1u;
+        }
+      }
+    }
+    return;
+  }
+  // -------------------------------------------------------------- consumers
+  const int i = i0 + 2 * lane, j = j0 + warp;
+  const bool active = i < nx && j < ny;
+  // periodic directions: the edge points load their wrapped neighbours
+  const bool edge = active && ((px && (i == 0 || i + 2 == nx)) || (py && (j == 0 || j == ny - 1)));
+  const PairCoefs c = pair_coefs<WX, WY>(RX, RY, active ? i : 0, active ? j : 0);
+  const df fshift = SING ? fshift_of(fsums, inv_vol) : df{0.0f, 0.0f};
+  const int pc = (warp + 1) * kResPW + 4 + 2 * lane;          // centre of the pair in a phi stage
+  const int fc = warp * kResTX + 2 * lane;
+  const long long sz = static_cast<long long>(nx) * ny;
+  auto pair_at = [&](const uint8_t* st, int e, df& a, df& b) {
+    const float2 h = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(st) + e);
+    const float2 l = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(st + kResPBytes) + e);
+    a = {h.x, l.x};
+    b = {h.y, l.y};
+  };
+  auto release = [&](int s) {
+    __syncwarp();
+    if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&empty[s]));
+  };
+  float acc2 = 0.0f;
+  df pma = {0.0f, 0.0f}, pmb = {0.0f, 0.0f}, p0a = {0.0f, 0.0f}, p0b = {0.0f, 0.0f};
+  bool ok = ptx::mbar_wait(ptx::smem_u32(&full[0]), 0, err, ptx::kErrWaitFull);
+  if (ok) {
+    pair_at(smem, pc, pma, pmb);
+    release(0);
+    ok = ptx::mbar_wait(ptx::smem_u32(&full[1]), 0, err, ptx::kErrWaitFull);
+  }
+  if (ok) pair_at(smem + kResStage, pc, p0a, p0b);
+  df dza = df_diff(pma, p0a), dzb = df_diff(pmb, p0b);        // down from plane k0
+  long long ro = i + static_cast<long long>(ldx) * (j + static_cast<long long>(ny) * k0);
+  const long long rstep = static_cast<long long>(ldx) * ny;
+  int s = 1, sn = 2;                                           // stages of planes k and k + 1
+  uint32_t parn = 0;                                           // phase parity of stage sn
+  for (int k = k0; ok && k < k1; ++k) {
+    const ZCoef z = zc[k - k0];
+    if (!ptx::mbar_wait(ptx::smem_u32(&full[sn]), parn, err, ptx::kErrWaitFull)) break;
+    df ppa, ppb;
+    pair_at(smem + sn * kResStage, pc, ppa, ppb);
+    const uint8_t* st = smem + s * kResStage;
+    df xma, xmb, xpa, xpb, yma, ymb, ypa, ypb;
+    pair_at(st, pc - 2, xma, xmb);                             // xmb: the -x neighbour of a
+    pair_at(st, pc + 2, xpa, xpb);                             // xpa: the +x neighbour of b
+    pair_at(st, pc - kResPW, yma, ymb);
+    pair_at(st, pc + kResPW, ypa, ypb);
+    const float2 fhv = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(st + 2 * kResPBytes) + fc);
+    const float2 flv =
+        *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(st + 2 * kResPBytes + kResFBytes) + fc);
+    df xm = xmb, xp = xpa;
+    if (edge) {
+      const long long plane = sz * k;
+      if (px && i == 0) {
+        const long long o = plane + static_cast<long long>(nx) * j + (nx - 1);
+        xm = {ph[o], pl[o]};
+      }
+      if (px && i + 2 == nx) {
+        const long long o = plane + static_cast<long long>(nx) * j;
+        xp = {ph[o], pl[o]};
+      }
+      if (py && j == 0) {
+        const long long o = plane + static_cast<long long>(nx) * (ny - 1) + i;
+        const float2 h = *reinterpret_cast<const float2*>(ph + o), l = *reinterpret_cast<const float2*>(pl + o);
+        yma = {h.x, l.x};
+        ymb = {h.y, l.y};
+      }
+      if (py && j == ny - 1) {
+        const long long o = plane + i;
+        const float2 h = *reinterpret_cast<const float2*>(ph + o), l = *reinterpret_cast<const float2*>(pl + o);
+        ypa = {h.x, l.x};
+        ypb = {h.y, l.y};
+      }
+    }
+    if (active) {
+      float rv[2];
+      residual_pair<HAS_ALPHA, WX, WY, WZ, SING>(c, z, alpha_h, alpha_l, fshift, p0a, p0b, ppa, ppb, xm, xp, yma,
+                                                 ymb, ypa, ypb, {fhv.x, flv.x}, {fhv.y, flv.y}, dza, dzb, rv);
+      Elem2<FMT>::store(r0, r1, ro, rv[0], rv[1]);
+      acc2 = fmaf(rv[0], rv[0], acc2);
+      acc2 = fmaf(rv[1], rv[1], acc2);
+    }
+    release(s);
+    p0a = ppa;
+    p0b = ppb;
+    ro += rstep;
+    s = sn;
+    if (++sn == kResStages) {
+      sn = 0;
+      parn ^= 1u;
+    }
+  }
+  double s2 = warp_sum_d(static_cast<double>(acc2));
+  if (lane == 0) atomicAdd(&sums[0], s2);
 }
 
 // sum of cell volume times phi (float pair) into *out, for the exact gauge;
@@ -1397,7 +1641,7 @@ BRows rows_of(const float* t, int n) {
   return BRows{t, t + n, t + 2 * n, t + 3 * n, t + 4 * n, t + 5 * n};
 }
 
-template <int FMT, int HA, int WX, int WY, int WZ>
+template <int FMT, int HA, int WX, int WY, int WZ, int SING>
 cudaError_t launch_res(const tpt_plan_s* p, const MixedWork& w, cudaStream_t s) {
   const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
   const int kseg = 32;
@@ -1405,18 +1649,38 @@ cudaError_t launch_res(const tpt_plan_s* p, const MixedWork& w, cudaStream_t s) 
   const float ah = static_cast<float>(p->alpha);
   const float al = static_cast<float>(p->alpha - static_cast<double>(ah));
   note_launch(1);
+  if (nx % 4 == 0 && p->mixed.res_kernel != 1) {   // TMA-staged tiles (rows of 16-byte multiples)
+    CUtensorMap m[4];
+    const long long rows = static_cast<long long>(ny) * nz;
+    bool maps = tc::make_plain_map(&m[0], w.ph, 4, nx, rows, 4LL * nx, kResPW, kResTY + 2) &&
+                tc::make_plain_map(&m[1], w.pl, 4, nx, rows, 4LL * nx, kResPW, kResTY + 2) &&
+                tc::make_plain_map(&m[2], w.fh, 4, nx, rows, 4LL * nx, kResTX, kResTY) &&
+                tc::make_plain_map(&m[3], w.fl, 4, nx, rows, 4LL * nx, kResTX, kResTY);
+    if (maps) {
+      auto kern = residual_tma_kernel<FMT, HA, WX, WY, WZ, SING>;
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kResSmem);
+      if (e != cudaSuccess) return e;
+      dim3 gt((nx + kResTX - 1) / kResTX, (ny + kResTY - 1) / kResTY, (nz + kResKseg - 1) / kResKseg);
+      kern<<<gt, kResThreads, kResSmem, s>>>(
+          m[0], m[1], m[2], m[3], nx, ny, nz, p->mixed.ldx, p->dir[0].periodic ? 1 : 0,
+          p->dir[1].periodic ? 1 : 0, w.ph, w.pl, w.R[0], w.R[1], rows_of(p->mixed.dfrows[0], nx),
+          rows_of(p->mixed.dfrows[1], ny), rows_of(p->mixed.dfrows[2], nz), ah, al, w.scal + 5, 1.0 / p->vol,
+          w.scal + 1, reinterpret_cast<int*>(w.scal + 15));
+      return cudaGetLastError();
+    }
+  }
   if (nx % 2 == 0) {   // two points per thread
     dim3 grid2((nx / 2 + 31) / 32, (ny + 3) / 4, (nz + kseg - 1) / kseg);
-    residual_df2_kernel<FMT, HA, WX, WY, WZ><<<grid2, block, 0, s>>>(
+    residual_df2_kernel<FMT, HA, WX, WY, WZ, SING><<<grid2, block, 0, s>>>(
         nx, ny, nz, p->mixed.ldx, kseg, w.fh, w.fl, w.ph, w.pl, w.R[0], w.R[1],
         rows_of(p->mixed.dfrows[0], nx), rows_of(p->mixed.dfrows[1], ny), rows_of(p->mixed.dfrows[2], nz),
-        ah, al, w.scal + 5, 1.0 / p->vol, p->singular ? 1 : 0, w.scal + 1);
+        ah, al, w.scal + 5, 1.0 / p->vol, w.scal + 1);
     return cudaGetLastError();
   }
-  residual_df_kernel<FMT, HA, WX, WY, WZ><<<grid, block, 0, s>>>(
+  residual_df_kernel<FMT, HA, WX, WY, WZ, SING><<<grid, block, 0, s>>>(
       nx, ny, nz, p->mixed.ldx, kseg, w.fh, w.fl, w.ph, w.pl, w.R[0], w.R[1],
       rows_of(p->mixed.dfrows[0], nx), rows_of(p->mixed.dfrows[1], ny), rows_of(p->mixed.dfrows[2], nz),
-      ah, al, w.scal + 5, 1.0 / p->vol, p->singular ? 1 : 0, w.scal + 1);
+      ah, al, w.scal + 5, 1.0 / p->vol, w.scal + 1);
   return cudaGetLastError();
 }
 
@@ -1424,14 +1688,17 @@ template <int FMT>
 cudaError_t launch_residual(const tpt_plan_s* p, const MixedWork& w, cudaStream_t s) {
   const int* hw = p->mixed.has_w;
   const int code = (p->alpha != 0.0 ? 8 : 0) | (hw[0] ? 4 : 0) | (hw[1] ? 2 : 0) | (hw[2] ? 1 : 0);
+  // a singular problem (alpha = 0, every direction periodic or Neumann-Neumann)
+  // has no wall with a diagonal remainder, so code is 0 there
+  if (p->singular) return launch_res<FMT, 0, 0, 0, 0, 1>(p, w, s);
   switch (code) {
-    case 0: return launch_res<FMT, 0, 0, 0, 0>(p, w, s);
-    case 8: return launch_res<FMT, 1, 0, 0, 0>(p, w, s);
+    case 0: return launch_res<FMT, 0, 0, 0, 0, 0>(p, w, s);
+    case 8: return launch_res<FMT, 1, 0, 0, 0, 0>(p, w, s);
     default: break;
   }
   // walls with a diagonal remainder (Dirichlet): one general instantiation
-  if (p->alpha != 0.0) return launch_res<FMT, 1, 1, 1, 1>(p, w, s);
-  return launch_res<FMT, 0, 1, 1, 1>(p, w, s);
+  if (p->alpha != 0.0) return launch_res<FMT, 1, 1, 1, 1, 0>(p, w, s);
+  return launch_res<FMT, 0, 1, 1, 1, 0>(p, w, s);
 }
 
 // Operands and output of transform stage i of one correction (Algorithm 1

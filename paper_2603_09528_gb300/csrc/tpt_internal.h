@@ -91,7 +91,8 @@ struct MixedTables {
   // inverse): column tile width (0 = default) and persistent-CTA cap (0 = all)
   int gemm_bn[4] = {0, 0, 0, 0};
   int gemm_ctas[4] = {0, 0, 0, 0};
-  int gemm_pair[4] = {0, 0, 0, 0};  // two-CTA operand sharing (0 none, 1 share B, 2 share A)
+  int gemm_pair[4] = {0, 0, 0, 0};
+  int res_kernel = 0;               // residual: 0 automatic, 1 direct loads, 2 TMA-staged tiles  // two-CTA operand sharing (0 none, 1 share B, 2 share A)
 };
 
 struct FftTables {    // device tables of a Fourier-transformed direction

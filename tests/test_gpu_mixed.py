@@ -251,3 +251,55 @@ def test_tc_gemm_output_formats_and_layouts(kind, case, tile):
     assert np.all(hi[untouched] == -7.25)
     if kind == "split":
         assert np.all(lo[untouched] == -7.25)
+
+
+# (n, boundaries, (alpha, beta)): full 64 x 8 tiles with three z segments
+# (64 + 64 + 2 planes); periodic x and y (edge points load the wrapped
+# neighbours) with ragged x and y tiles; Dirichlet walls (diagonal remainder)
+# with Helmholtz; a grid narrower than one tile in every direction
+RES_CASES = [((128, 64, 130), [(1, 1)] * 3, (0.0, 1.0)),
+             ((132, 44, 70), [(0, 0), (0, 0), (1, 1)], (0.0, 1.0)),
+             ((100, 36, 66), [(2, 1), (1, 2), (2, 2)], (1.0, -5e-4)),
+             ((4, 9, 3), [(0, 0), (0, 0), (2, 1)], (1.0, -1e-3))]
+
+
+@pytest.mark.parametrize("case", RES_CASES, ids=["full", "periodic-xy", "walls-helmholtz", "tiny"])
+def test_tma_residual_equals_direct_loads_and_the_oracle(case):
+    # both residual kernels apply the same float-pair operations to every
+    # point, so three fixed corrections give the same phi (to the bit where
+    # the problem is not singular); the TMA-staged solve refined to 1e-10 must
+    # then match the oracle
+    n, bcs, coef = case
+    dirs = _dirs(n, (1.5, 2.0, 2.5), bcs)
+    f = S.uniform_rhs(n, 31)
+    if O.is_singular(dirs, coef[0]):
+        f = S.remove_weighted_mean(f, [d.dxf for d in dirs])
+    kw = dict(xform=(tpt.GEMM, tpt.GEMM), alpha=coef[0], beta=coef[1], precision=PRECS["bf16x3"])
+    out = []
+    for variant in (1, 2):
+        plan = tpt.Plan(n, [d.dxf for d in dirs], [d.dxc for d in dirs], bcs, rtol=0.0, max_refine=3, **kw)
+        plan.set_residual_kernel(variant)
+        phi, info = plan.solve(tpt.field_to_device(f))
+        out.append((phi.cpu().numpy(), info))
+    (a, ia), (b, ib) = out
+    assert ia["iters"] == ib["iters"]
+    if O.is_singular(dirs, coef[0]):
+        # the mean removal and the gauge sum with float64 atomics, whose order
+        # changes from run to run: equal to rounding of those sums (the
+        # residual, near the float-pair floor, to a few of its digits)
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max(), np.abs(a - b).max()
+        assert abs(ia["rel_residual"] - ib["rel_residual"]) <= 1e-3 * ia["rel_residual"] + 1e-16
+    else:
+        assert np.array_equal(a, b)
+        # r^2 is summed in float32 per thread over its plane segment (64
+        # planes for the tiles, 32 for direct loads), then in float64
+        assert abs(ia["rel_residual"] - ib["rel_residual"]) <= 1e-5 * ia["rel_residual"]
+    plan = tpt.Plan(n, [d.dxf for d in dirs], [d.dxc for d in dirs], bcs, rtol=1e-10, max_refine=40, **kw)
+    plan.set_residual_kernel(2)
+    phi, info = plan.solve(tpt.field_to_device(f))
+    got = tpt.field_to_host(phi, n)
+    r = O.residual(f, got, dirs, *coef, np.longdouble)
+    rel = float(np.sqrt(np.sum(r ** 2) / np.sum(f ** 2)))
+    ref, _ = O.solve_tensor(f, dirs, *coef)
+    assert info["rel_residual"] <= 1e-10 and rel <= 2e-10, (info, rel)
+    assert np.abs(got - ref).max() <= 1e-7 * np.abs(ref).max()
