@@ -34,7 +34,18 @@ namespace tc {
 namespace {
 
 constexpr int BM = 128;
-constexpr int kThreads = 192;
+// Threads of a CTA: a producer warp, an MMA warp and the epilogue warps.
+// Epilogue warps: eight for the float-pair update (two warps per tensor-memory
+// lane quarter, alternate 32-column chunks), so that twice as many
+// read-modify-write loads are in flight; four otherwise.
+template <int OUT>
+__host__ __device__ constexpr int epi_warps() {
+  return OUT == kOutDF ? 8 : 4;
+}
+template <int OUT>
+__host__ __device__ constexpr int threads_of() {
+  return 32 * (2 + epi_warps<OUT>());
+}
 constexpr int kSmemBudget = 200 * 1024;
 
 __device__ __forceinline__ void split_bf16(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
@@ -164,15 +175,18 @@ __device__ __forceinline__ void unit_coords(const GemmOut& g, int num_m, int num
 // (MMA -> epilogue, one commit) and acc_empty[b] (epilogue -> MMA, one arrive
 // per epilogue warp).
 template <int KIND, int NPL, int BN, int OUT, int PAIR, int TMAO>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(threads_of<OUT>(), 1)
 gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
                const __grid_constant__ CUtensorMap tB0, const __grid_constant__ CUtensorMap tB1,
                const __grid_constant__ CUtensorMap tO0, const __grid_constant__ CUtensorMap tO1,
                const GemmOut g) {
   using C = Cfg<KIND, NPL, BN>;
   static_assert(C::STAGES >= 2, "shared-memory ring needs two stages");
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  extern __shared__ __align__(128) uint8_t smem_raw[];
+  // 1024-byte aligned start, offset on the shared pointer itself so that the
+  // epilogue's staging accesses stay shared-memory (not generic) accesses
+  uint8_t* smem = smem_raw + ((1024u - (ptx::smem_u32(smem_raw) & 1023u)) & 1023u);
+  constexpr int EPI = epi_warps<OUT>();
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE);
   // bars[0..S) full, [S..2S) empty, [2S, 2S+2) acc_full, [2S+2, 2S+4) acc_empty
   uint64_t* accf = bars + 2 * C::STAGES;
@@ -200,7 +214,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
     }
     for (int b = 0; b < 2; ++b) {
       ptx::mbar_init(ptx::smem_u32(&accf[b]), 1);
-      ptx::mbar_init(ptx::smem_u32(&acce[b]), 4);
+      ptx::mbar_init(ptx::smem_u32(&acce[b]), EPI);
     }
     ptx::fence_mbar_init();
   }
@@ -320,6 +334,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
   } else if (warp >= 2) {
     // ---------------------------------------------------------- epilogue
     const int quarter = warp % 4;                  // tensor-memory lanes 32*quarter ..
+    const int half = (warp - 2) / 4;               // eight warps: chunks of parity `half`
     // TMA-store epilogue: each 32-row x 32-column chunk is written to a
     // shared-memory staging buffer (column-major, rows contiguous, as in the
     // output) and stored by one lane with a 3D bulk tensor store, two chunks
@@ -345,7 +360,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
       const long long mterm =
           mvalid ? (static_cast<long long>(m % g.rm) + static_cast<long long>(m / g.rm) * g.sm) : 0;
 #pragma unroll 1
-      for (int c0 = 0; c0 < BN; c0 += 32) {
+      for (int c0 = 32 * half; c0 < BN; c0 += 32 * (EPI / 4)) {
         uint32_t r[32];
         ptx::tmem_ld_32x32b_x32(tmem + (static_cast<uint32_t>(quarter * 32) << 16) +
                                     static_cast<uint32_t>(b * BN + c0), r);
@@ -499,7 +514,7 @@ cudaError_t launch(const Operand& A, const Operand& B, const GemmOut& g, cudaStr
   if (PAIR == 0) {
     const long long ctas = tiles < cap ? tiles : cap;   // persistent: one CTA per SM
     note_launch(1);
-    kern<<<static_cast<unsigned>(ctas), kThreads, smem_bytes, s>>>(m[0], m[1], m[2], m[3], m[4], m[5], g);
+    kern<<<static_cast<unsigned>(ctas), threads_of<OUT>(), smem_bytes, s>>>(m[0], m[1], m[2], m[3], m[4], m[5], g);
     return cudaGetLastError();
   }
   // clusters of two CTAs, as many as can be resident at once (one CTA per SM)
@@ -510,7 +525,7 @@ cudaError_t launch(const Operand& A, const Operand& B, const GemmOut& g, cudaStr
   attr[0].val.clusterDim.x = 2;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
-  cfg.blockDim = dim3(kThreads, 1, 1);
+  cfg.blockDim = dim3(threads_of<OUT>(), 1, 1);
   cfg.dynamicSmemBytes = smem_bytes;
   cfg.stream = s;
   cfg.attrs = attr;

@@ -2042,40 +2042,57 @@ int autotune_gemms(tpt_plan_s* p, void* work, cudaStream_t s) {
   for (cudaEvent_t& e : ev)
     if (cudaEventCreate(&e) != cudaSuccess) status = TPT_ERR_CUDA;
   const int kind = kind_of(m.fmt), npl = nplanes(m.fmt);
-  constexpr int kReps = 3;
+  constexpr int kReps = 3, kRounds = 3;
   for (int i = 0; i < 4 && status == TPT_OK; ++i) {
     const StageGemm t = stage_gemm(p, w, i, false);
     const int top = tc::default_bn(t.g.N);
     // the operand common to neighbouring tiles: the transform matrix, which
     // is B for the x forward and y inverse stages and A for the other two
     const int share = (i == 0 || i == 2) ? 1 : 2;
-    float best = 0.0f;
-    int best_bn = top, best_pair = 0;
-    bool first = true;
-    for (int cand = 0; cand < 8 && status == TPT_OK; ++cand) {
+    int cbn[8], cpair[8], nc = 0;
+    for (int cand = 0; cand < 8; ++cand) {
       const int bn = 32 << (cand / 2), pair = (cand % 2) ? share : 0;
       if (bn > top) break;
       if (pair && (m.fmt != kFmtSplit || bn < 128)) continue;
-      tc::GemmOut g = t.g;
-      g.bn = bn;
-      g.max_ctas = 0;
-      g.pair = pair;
-      cudaError_t e = tc::gemm(kind, npl, t.a, t.b, g, s);   // warm-up
-      if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
-      for (int r = 0; r < kReps && e == cudaSuccess; ++r) e = tc::gemm(kind, npl, t.a, t.b, g, s);
-      if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
-      if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
-      float ms = 0.0f;
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
-      if (e != cudaSuccess) {
-        status = TPT_ERR_CUDA;
-        break;
+      cbn[nc] = bn;
+      cpair[nc++] = pair;
+    }
+    // rounds over all candidates, keeping each candidate's fastest round, so
+    // that a slow moment of the device does not decide for one candidate
+    float tbest[8];
+    for (int c = 0; c < nc; ++c) tbest[c] = -1.0f;
+    for (int round = 0; round < kRounds && status == TPT_OK; ++round) {
+      for (int c = 0; c < nc && status == TPT_OK; ++c) {
+        tc::GemmOut g = t.g;
+        g.bn = cbn[c];
+        g.max_ctas = 0;
+        g.pair = cpair[c];
+        cudaError_t e = cudaSuccess;
+        if (round == 0) e = tc::gemm(kind, npl, t.a, t.b, g, s);   // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
+        for (int r = 0; r < kReps && e == cudaSuccess; ++r) e = tc::gemm(kind, npl, t.a, t.b, g, s);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        if (e != cudaSuccess) {
+          status = TPT_ERR_CUDA;
+          break;
+        }
+        if (tbest[c] < 0.0f || ms < tbest[c]) tbest[c] = ms;
       }
-      if (first || ms < best) {
-        best = ms;
-        best_bn = bn;
-        best_pair = pair;
-        first = false;
+    }
+    // the default (widest tile, one CTA per tile) unless another candidate is
+    // faster by more than 1 %
+    int best_bn = top, best_pair = 0;
+    float best = -1.0f;
+    for (int c = 0; c < nc; ++c)
+      if (cbn[c] == top && cpair[c] == 0) best = tbest[c];
+    for (int c = 0; c < nc; ++c) {
+      if (best < 0.0f || tbest[c] < 0.99f * best) {
+        best = tbest[c];
+        best_bn = cbn[c];
+        best_pair = cpair[c];
       }
     }
     m.gemm_bn[i] = best_bn;
