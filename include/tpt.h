@@ -124,7 +124,8 @@ typedef struct {
  * For a TPT_PREC_MIXED_* plan the transform matrices are also rounded to
  * the operand format on the device.
  * Synchronous.  Errors: INVALID_ARG (bad descriptor), UNSUPPORTED (FFT on a
- * non-uniform direction, periodic z), NUMERICAL (eigensolver did not
+ * non-uniform direction, periodic z, a product of two sizes of 2^31 or
+ * more), NUMERICAL (eigensolver did not
  * converge), OOM, CUDA.  On error *out is set to NULL.                    */
 int tpt_plan_create(const tpt_desc* desc, int cuda_device, tpt_plan* out);
 

@@ -227,6 +227,11 @@ int create_plan_impl(const tpt_desc* desc, int cuda_device, tpt::BasisCache* cac
   if (!std::isfinite(desc->rtol) || desc->rtol < 0.0) return TPT_ERR_INVALID_ARG;
   for (int d = 0; d < 2; ++d)
     if (desc->xform[d] < TPT_XFORM_AUTO || desc->xform[d] > TPT_XFORM_FFT) return TPT_ERR_INVALID_ARG;
+  // lines of a plane and planes of a field are indexed with 32-bit integers
+  if (static_cast<long long>(desc->n[0]) * desc->n[1] >= (1LL << 31) ||
+      static_cast<long long>(desc->n[1]) * desc->n[2] >= (1LL << 31) ||
+      static_cast<long long>(desc->n[0]) * desc->n[2] >= (1LL << 31))
+    return TPT_ERR_UNSUPPORTED;
 
   tpt_plan_s* p = new (std::nothrow) tpt_plan_s();
   if (!p) return TPT_ERR_OOM;

@@ -40,7 +40,7 @@ constexpr int BM = 128;
 // read-modify-write loads are in flight; four otherwise.
 template <int OUT>
 __host__ __device__ constexpr int epi_warps() {
-  return OUT == kOutDF ? 8 : 4;
+  return 8;
 }
 template <int OUT>
 __host__ __device__ constexpr int threads_of() {
@@ -342,7 +342,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
     constexpr int OEB = (OUT == kOutF32) ? 4 : 2;
     constexpr int ONPL = (OUT == kOutSplitBF16) ? 2 : 1;
     constexpr int CHUNK = 32 * 32 * OEB;           // one plane of a chunk
-    uint8_t* ostage = smem + C::STAGES * C::STAGE + 1024 + quarter * (2 * ONPL * CHUNK);
+    uint8_t* ostage = smem + C::STAGES * C::STAGE + 1024 + (warp - 2) * (ONPL * CHUNK);
     int chunk_i = 0;
     int tcount = 0;
     for (long long q = unit0; q < num_units; q += unit_step, ++tcount) {
@@ -366,11 +366,11 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
                                     static_cast<uint32_t>(b * BN + c0), r);
         ptx::tmem_ld_wait();
         if (TMAO) {
-          if (chunk_i >= 2) {                      // the store of chunk i-2 has left its buffer
-            if (lane == 0) ptx::bulk_wait_read<1>();
+          if (chunk_i >= 1) {                      // the store of chunk i-1 has left the buffer
+            if (lane == 0) ptx::bulk_wait_read<0>();
             __syncwarp();
           }
-          uint8_t* sb = ostage + (chunk_i & 1) * ONPL * CHUNK;
+          uint8_t* sb = ostage;
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             const float v = __uint_as_float(r[j]);

@@ -1169,47 +1169,63 @@ df_to_f64_kernel(long long n, const float* __restrict__ h, const float* __restri
 // Same operations per point as the scalar kernels.
 template <int FMT>
 __global__ void __launch_bounds__(256)
-prepare2_kernel(int nx, int ny, int nz, int ldx, int nbi, const double* __restrict__ f, float* __restrict__ fh,
+prepare2_kernel(int nx, int ny, int nz, int ldx, const double* __restrict__ f, float* __restrict__ fh,
                 float* __restrict__ fl, void* r0, void* r1, const float* __restrict__ gx,
                 const float* __restrict__ gy, const float* __restrict__ gz, double* sums) {
-  // work item t: x-line (j, k) = t / nbi, points (t % nbi) * 512 + 2 * threadIdx.x + {0, 1}
-  const long long items = static_cast<long long>(nbi) * ny * nz;
+  // block b takes the x-lines (j, k) = b, b + G, b + 2G, ... (G blocks), U of
+  // them per step, whose (j, k) advance by U G lines without a division; its
+  // threads cover a line 512 points at a time, two points each
+  const int lines = ny * nz;
+  constexpr int U = 4;
+  const int G = gridDim.x, step = U * G;
+  const int sj = step % ny, sk = step / ny;
+  int jj[U], kk[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int L = blockIdx.x + u * G;
+    jj[u] = L % ny;
+    kk[u] = L / ny;
+  }
   float s2 = 0.0f, s1f = 0.0f;
   df sv = {0.0f, 0.0f};
-  constexpr int U = 4;
-  for (long long t0 = blockIdx.x; t0 < items; t0 += static_cast<long long>(U) * gridDim.x) {
-    double2 v[U];
-    long long line[U];
-    int ii[U];
+  for (int L0 = blockIdx.x; L0 < lines; L0 += step) {
+    for (int i = 2 * threadIdx.x; i < nx; i += 512) {
+      double2 v[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const long long t = t0 + static_cast<long long>(u) * gridDim.x;
-      line[u] = t / nbi;
-      ii[u] = static_cast<int>(t % nbi) * 512 + 2 * threadIdx.x;
-      const bool ok = t < items && ii[u] < nx;
-      if (!ok) ii[u] = -1;
-      v[u] = ok ? *reinterpret_cast<const double2*>(f + ii[u] + static_cast<long long>(nx) * line[u])
-                : make_double2(0.0, 0.0);
+      for (int u = 0; u < U; ++u) {
+        const int L = L0 + u * G;
+        v[u] = L < lines ? *reinterpret_cast<const double2*>(f + i + static_cast<long long>(nx) * L)
+                         : make_double2(0.0, 0.0);
+      }
+      const float2 gxh = *reinterpret_cast<const float2*>(gx + i);
+      const float2 gxl = *reinterpret_cast<const float2*>(gx + nx + i);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int L = L0 + u * G;
+        if (L >= lines) break;
+        const long long o = i + static_cast<long long>(nx) * L;
+        const df d0 = split_double_int(v[u].x), d1 = split_double_int(v[u].y);
+        *reinterpret_cast<float2*>(fh + o) = make_float2(d0.hi, d1.hi);
+        *reinterpret_cast<float2*>(fl + o) = make_float2(d0.lo, d1.lo);
+        Elem2<FMT>::store(r0, r1, i + static_cast<long long>(ldx) * L, d0.hi + d0.lo, d1.hi + d1.lo);
+        s2 = fmaf(d0.hi, d0.hi, s2);
+        s2 = fmaf(d1.hi, d1.hi, s2);
+        s1f += d0.hi;
+        s1f += d1.hi;
+        const int j = jj[u], k = kk[u];
+        const df wline = df_mul({gy[j], gy[ny + j]}, {gz[k], gz[nz + k]});
+        acc_mul(sv, wline.hi, wline.lo, df_mul({gxh.x, gxl.x}, d0));
+        acc_mul(sv, wline.hi, wline.lo, df_mul({gxh.y, gxl.y}, d1));
+      }
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int i = ii[u];
-      if (i < 0) continue;
-      const int j = static_cast<int>(line[u] % ny), k = static_cast<int>(line[u] / ny);
-      const long long o = i + static_cast<long long>(nx) * line[u];
-      const df d0 = split_double_int(v[u].x), d1 = split_double_int(v[u].y);
-      *reinterpret_cast<float2*>(fh + o) = make_float2(d0.hi, d1.hi);
-      *reinterpret_cast<float2*>(fl + o) = make_float2(d0.lo, d1.lo);
-      Elem2<FMT>::store(r0, r1, i + static_cast<long long>(ldx) * line[u], d0.hi + d0.lo, d1.hi + d1.lo);
-      s2 = fmaf(d0.hi, d0.hi, s2);
-      s2 = fmaf(d1.hi, d1.hi, s2);
-      s1f += d0.hi;
-      s1f += d1.hi;
-      const df wline = df_mul({gy[j], gy[ny + j]}, {gz[k], gz[nz + k]});
-      const float2 gxh = *reinterpret_cast<const float2*>(gx + i);
-      const float2 gxl = *reinterpret_cast<const float2*>(gx + nx + i);
-      acc_mul(sv, wline.hi, wline.lo, df_mul({gxh.x, gxl.x}, d0));
-      acc_mul(sv, wline.hi, wline.lo, df_mul({gxh.y, gxl.y}, d1));
+      jj[u] += sj;
+      kk[u] += sk;
+      if (jj[u] >= ny) {
+        jj[u] -= ny;
+        ++kk[u];
+      }
     }
   }
   df s1 = {s1f, 0.0f};
@@ -1243,42 +1259,55 @@ prepare2_kernel(int nx, int ny, int nz, int ldx, int nbi, const double* __restri
   }
 }
 
-// sum of cell volume times phi, four points of an x-line per thread
+// sum of cell volume times phi, four points of an x-line per thread; lines
+// are distributed over blocks as in prepare2_kernel
 __global__ void __launch_bounds__(256)
 wsum4_kernel(int nx, int ny, int nz, const float* __restrict__ h, const float* __restrict__ l,
              const float* __restrict__ gx, const float* __restrict__ gy, const float* __restrict__ gz,
              double* out) {
-  const int nbi = (nx + 1023) / 1024;
-  const long long items = static_cast<long long>(nbi) * ny * nz;
-  df s = {0.0f, 0.0f};
+  const int lines = ny * nz;
   constexpr int U = 2;
-  for (long long t0 = blockIdx.x; t0 < items; t0 += static_cast<long long>(U) * gridDim.x) {
-    float4 hh[U], ll[U];
-    long long line[U];
-    int ii[U];
+  const int G = gridDim.x, step = U * G;
+  const int sj = step % ny, sk = step / ny;
+  int jj[U], kk[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const long long t = t0 + static_cast<long long>(u) * gridDim.x;
-      line[u] = t / nbi;
-      ii[u] = static_cast<int>(t % nbi) * 1024 + 4 * threadIdx.x;
-      const bool ok = t < items && ii[u] < nx;
-      if (!ok) ii[u] = -1;
-      const long long o = ok ? ii[u] + static_cast<long long>(nx) * line[u] : 0;
-      hh[u] = ok ? *reinterpret_cast<const float4*>(h + o) : make_float4(0.f, 0.f, 0.f, 0.f);
-      ll[u] = ok ? *reinterpret_cast<const float4*>(l + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int u = 0; u < U; ++u) {
+    const int L = blockIdx.x + u * G;
+    jj[u] = L % ny;
+    kk[u] = L / ny;
+  }
+  df s = {0.0f, 0.0f};
+  for (int L0 = blockIdx.x; L0 < lines; L0 += step) {
+    for (int i = 4 * threadIdx.x; i < nx; i += 1024) {
+      float4 hh[U], ll[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int L = L0 + u * G;
+        const long long o = i + static_cast<long long>(nx) * (L < lines ? L : 0);
+        hh[u] = L < lines ? *reinterpret_cast<const float4*>(h + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+        ll[u] = L < lines ? *reinterpret_cast<const float4*>(l + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      const float4 gh = *reinterpret_cast<const float4*>(gx + i);
+      const float4 gl = *reinterpret_cast<const float4*>(gx + nx + i);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (L0 + u * G >= lines) break;
+        const int j = jj[u], k = kk[u];
+        const df wline = df_mul({gy[j], gy[ny + j]}, {gz[k], gz[nz + k]});
+        acc_mul(s, wline.hi, wline.lo, df_mul({gh.x, gl.x}, {hh[u].x, ll[u].x}));
+        acc_mul(s, wline.hi, wline.lo, df_mul({gh.y, gl.y}, {hh[u].y, ll[u].y}));
+        acc_mul(s, wline.hi, wline.lo, df_mul({gh.z, gl.z}, {hh[u].z, ll[u].z}));
+        acc_mul(s, wline.hi, wline.lo, df_mul({gh.w, gl.w}, {hh[u].w, ll[u].w}));
+      }
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int i = ii[u];
-      if (i < 0) continue;
-      const int j = static_cast<int>(line[u] % ny), k = static_cast<int>(line[u] / ny);
-      const df wline = df_mul({gy[j], gy[ny + j]}, {gz[k], gz[nz + k]});
-      const float4 gh = *reinterpret_cast<const float4*>(gx + i);
-      const float4 gl = *reinterpret_cast<const float4*>(gx + nx + i);
-      acc_mul(s, wline.hi, wline.lo, df_mul({gh.x, gl.x}, {hh[u].x, ll[u].x}));
-      acc_mul(s, wline.hi, wline.lo, df_mul({gh.y, gl.y}, {hh[u].y, ll[u].y}));
-      acc_mul(s, wline.hi, wline.lo, df_mul({gh.z, gl.z}, {hh[u].z, ll[u].z}));
-      acc_mul(s, wline.hi, wline.lo, df_mul({gh.w, gl.w}, {hh[u].w, ll[u].w}));
+      jj[u] += sj;
+      kk[u] += sk;
+      if (jj[u] >= ny) {
+        jj[u] -= ny;
+        ++kk[u];
+      }
     }
   }
   s = fast_two_sum(s.hi, s.lo);
@@ -1507,10 +1536,9 @@ cudaError_t launch_prepare(const tpt_plan_s* p, const double* f, const MixedWork
   const long long items = static_cast<long long>(nbi) * p->n[1] * p->n[2];
   note_launch(1);
   if (p->n[0] % 2 == 0 && reinterpret_cast<uintptr_t>(f) % 16 == 0) {   // two points per thread
-    const int nb2 = (p->n[0] + 511) / 512;
-    const long long items2 = static_cast<long long>(nb2) * p->n[1] * p->n[2];
-    prepare2_kernel<FMT><<<grid_for(items2 * 256, 256, p->dev), 256, 0, s>>>(
-        p->n[0], p->n[1], p->n[2], p->mixed.ldx, nb2, f, w.fh, w.fl, w.R[0], w.R[1], p->mixed.dfgeom[0],
+    const long long lines = static_cast<long long>(p->n[1]) * p->n[2];
+    prepare2_kernel<FMT><<<grid_for(lines * 256, 256, p->dev), 256, 0, s>>>(
+        p->n[0], p->n[1], p->n[2], p->mixed.ldx, f, w.fh, w.fl, w.R[0], w.R[1], p->mixed.dfgeom[0],
         p->mixed.dfgeom[1], p->mixed.dfgeom[2], w.scal + 5);
     return cudaGetLastError();
   }
@@ -1843,7 +1871,8 @@ int solve_fmt(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStrea
     MX_CUDA(cudaMemsetAsync(w.scal + 2, 0, sizeof(double), s));
     note_launch(1);
     if (p->n[0] % 4 == 0)   // four points per thread
-      wsum4_kernel<<<grid_for(n / 4, 256, p->dev), 256, 0, s>>>(p->n[0], p->n[1], p->n[2], w.ph, w.pl,
+      wsum4_kernel<<<grid_for(static_cast<long long>(p->n[1]) * p->n[2] * 256, 256, p->dev), 256, 0, s>>>(
+          p->n[0], p->n[1], p->n[2], w.ph, w.pl,
                                                                p->mixed.dfgeom[0], p->mixed.dfgeom[1],
                                                                p->mixed.dfgeom[2], w.scal + 2);
     else
