@@ -181,19 +181,17 @@ def run_reference(args):
 
 PRECISIONS = {"fp64": 0, "mixed_bf16": 1, "mixed_bf16x3": 2, "mixed_tf32": 3}
 
-# DRAM bytes (read + write) per grid point of one launch, from one ncu capture
-# of the named kernel (profiles/mixed_bf16x3_poisson512.md: 256^3 case, scaled
-# by points).  An entry must be removed when its kernel changes.
 # dram__bytes_read.sum + dram__bytes_write.sum per point of each stage's kernel, from one
-# ncu --set full capture at 384^3 (profiles/mixed_bf16x3_poisson512.md); traffic scales with
-# points.  The x-inverse GEMM is left out: the captured launch was a first correction, which
-# does not read phi, so its bytes differ from the average launch.
+# ncu --set full capture at 384^3 (summarised under profiles/); traffic scales with points.
+# An entry must be removed when its kernel changes.  The x-inverse GEMM is left out: the
+# captured launch was a first correction, which does not read phi, so its bytes differ
+# from the average launch.
 MEASURED_TRAFFIC_PER_POINT = {
-    ("residual", "mixed_bf16x3"): (924.333824e6 + 213.527808e6) / 384 ** 3,
-    ("thomas", "mixed_bf16x3"): (226.63168e6 + 178.502144e6) / 384 ** 3,
-    ("x_forward", "mixed_bf16x3"): (227.265792e6 + 178.339328e6) / 384 ** 3,
-    ("y_forward", "mixed_bf16x3"): (227.145472e6 + 175.130624e6) / 384 ** 3,
-    ("y_inverse", "mixed_bf16x3"): (227.291904e6 + 178.37952e6) / 384 ** 3,
+    ("residual", "mixed_bf16x3"): (921.18272e6 + 212.572416e6) / 384 ** 3,
+    ("thomas", "mixed_bf16x3"): (226.610688e6 + 178.848768e6) / 384 ** 3,
+    ("x_forward", "mixed_bf16x3"): (227.2256e6 + 179.54304e6) / 384 ** 3,
+    ("y_forward", "mixed_bf16x3"): (227.148032e6 + 176.46592e6) / 384 ** 3,
+    ("y_inverse", "mixed_bf16x3"): (227.151104e6 + 180.143104e6) / 384 ** 3,
 }
 DTYPE = {"fp64": "f64", "mixed_bf16": "bf16/f32/f64", "mixed_bf16x3": "bf16x3/f32/f64",
          "mixed_tf32": "tf32/f32/f64"}
@@ -258,7 +256,10 @@ def run_ours(args):
 
     tiles = None
     if prec != 0:
-        tiles = plan.autotune(work, stream=stream)   # transform GEMM column tiles per stage
+        if args.no_autotune:   # default tiles (for profiling runs: no tuning launches)
+            tiles = plan.tiles()
+        else:
+            tiles = plan.autotune(work, stream=stream)   # transform GEMM column tiles per stage
         plan.set_stage_timing(True)
     # warm-up
     info = None
@@ -725,7 +726,7 @@ def dominant_kernel(plan, prec, n, f_dev, steps, stream):
     flops = 2.0 * n[0] * n[0] * n[1] * n[2]
     achieved = flops / (ms / 1e3) / 1e12
     if prec == 0:
-        peak = 1.25   # GB300 float64 (FMA = DMMA), nominal; see the design doc
+        peak = 1.25   # GB300 float64 rate in TFLOP/s, nominal (an FMA counts two flops)
         return {"kernel": "dgemm_cm_kernel (x forward transform)", "bound": "alu",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_source": "nominal GB300 float64 rate (MEASURED_PEAKS.json has no float64 entry)",
@@ -752,6 +753,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched uneven-instances leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the open-loop serving leg")
     ap.add_argument("--no-projection", action="store_true", help="skip the pressure-projection leg")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default GEMM tiles of the headline plan (profiling runs)")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-warmup", type=int, default=200)
     ap.add_argument("--serve-requests-fp64", type=int, default=40)

@@ -23,7 +23,7 @@ What it computes (paper sections cited per function):
       solution 2.1-2.5) with plain numpy matmuls and a scalar-recurrence Thomas
       sweep, followed by iterative refinement against the assembled stencil.
 
-Readings of points the paper leaves open (each is also listed in the design doc):
+Readings of points the paper leaves open:
 
 R1 grid: faces at x(k/N), k = 0..N, from Eq. (tanh_stretching); cell widths are
    face spacings, centres are face midpoints, centre spacings are the

@@ -1172,28 +1172,30 @@ __global__ void __launch_bounds__(256)
 prepare2_kernel(int nx, int ny, int nz, int ldx, const double* __restrict__ f, float* __restrict__ fh,
                 float* __restrict__ fl, void* r0, void* r1, const float* __restrict__ gx,
                 const float* __restrict__ gy, const float* __restrict__ gz, double* sums) {
-  // block b takes the x-lines (j, k) = b, b + G, b + 2G, ... (G blocks), U of
-  // them per step, whose (j, k) advance by U G lines without a division; its
-  // threads cover a line 512 points at a time, two points each
+  // a block is blockDim.y rows of threads, one x-line (j, k) each, two
+  // points per thread; block b takes the line groups b, b + G, b + 2G, ...
+  // (G blocks), U of them per step, whose (j, k) advance by constant steps
+  // without a division
   const int lines = ny * nz;
-  constexpr int U = 4;
-  const int G = gridDim.x, step = U * G;
+  constexpr int U = 2;
+  const int G = gridDim.x, ty = blockDim.y;
+  const int step = U * G * ty;
   const int sj = step % ny, sk = step / ny;
   int jj[U], kk[U];
 #pragma unroll
   for (int u = 0; u < U; ++u) {
-    const int L = blockIdx.x + u * G;
+    const int L = (blockIdx.x + u * G) * ty + threadIdx.y;
     jj[u] = L % ny;
     kk[u] = L / ny;
   }
   float s2 = 0.0f, s1f = 0.0f;
   df sv = {0.0f, 0.0f};
-  for (int L0 = blockIdx.x; L0 < lines; L0 += step) {
-    for (int i = 2 * threadIdx.x; i < nx; i += 512) {
+  for (int L0 = blockIdx.x * ty + threadIdx.y; L0 < lines; L0 += step) {
+    for (int i = 2 * threadIdx.x; i < nx; i += 2 * blockDim.x) {
       double2 v[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int L = L0 + u * G;
+        const int L = L0 + u * G * ty;
         v[u] = L < lines ? *reinterpret_cast<const double2*>(f + i + static_cast<long long>(nx) * L)
                          : make_double2(0.0, 0.0);
       }
@@ -1201,7 +1203,7 @@ prepare2_kernel(int nx, int ny, int nz, int ldx, const double* __restrict__ f, f
       const float2 gxl = *reinterpret_cast<const float2*>(gx + nx + i);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int L = L0 + u * G;
+        const int L = L0 + u * G * ty;
         if (L >= lines) break;
         const long long o = i + static_cast<long long>(nx) * L;
         const df d0 = split_double_int(v[u].x), d1 = split_double_int(v[u].y);
@@ -1231,7 +1233,8 @@ prepare2_kernel(int nx, int ny, int nz, int ldx, const double* __restrict__ f, f
   df s1 = {s1f, 0.0f};
   sv = fast_two_sum(sv.hi, sv.lo);
   __shared__ float red[3][2][8];
-  const int lane = threadIdx.x % 32, w = threadIdx.x / 32;
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int lane = tid % 32, w = tid / 32;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     s2 += __shfl_xor_sync(0xffffffffu, s2, o);
@@ -1246,9 +1249,10 @@ prepare2_kernel(int nx, int ny, int nz, int ldx, const double* __restrict__ f, f
     red[2][1][w] = sv.lo;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     double a = 0.0, b = 0.0, c = 0.0;
-    for (int q = 0; q < 8; ++q) {
+    const int nw = (blockDim.x * blockDim.y + 31) / 32;   // warps of this block (at most 8)
+    for (int q = 0; q < nw; ++q) {
       a += red[0][0][q];
       b += static_cast<double>(red[1][0][q]) + red[1][1][q];
       c += static_cast<double>(red[2][0][q]) + red[2][1][q];
@@ -1261,28 +1265,29 @@ prepare2_kernel(int nx, int ny, int nz, int ldx, const double* __restrict__ f, f
 
 // sum of cell volume times phi, four points of an x-line per thread; lines
 // are distributed over blocks as in prepare2_kernel
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 wsum4_kernel(int nx, int ny, int nz, const float* __restrict__ h, const float* __restrict__ l,
              const float* __restrict__ gx, const float* __restrict__ gy, const float* __restrict__ gz,
              double* out) {
   const int lines = ny * nz;
   constexpr int U = 2;
-  const int G = gridDim.x, step = U * G;
+  const int G = gridDim.x, ty = blockDim.y;
+  const int step = U * G * ty;
   const int sj = step % ny, sk = step / ny;
   int jj[U], kk[U];
 #pragma unroll
   for (int u = 0; u < U; ++u) {
-    const int L = blockIdx.x + u * G;
+    const int L = (blockIdx.x + u * G) * ty + threadIdx.y;
     jj[u] = L % ny;
     kk[u] = L / ny;
   }
   df s = {0.0f, 0.0f};
-  for (int L0 = blockIdx.x; L0 < lines; L0 += step) {
-    for (int i = 4 * threadIdx.x; i < nx; i += 1024) {
+  for (int L0 = blockIdx.x * ty + threadIdx.y; L0 < lines; L0 += step) {
+    for (int i = 4 * threadIdx.x; i < nx; i += 4 * blockDim.x) {
       float4 hh[U], ll[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int L = L0 + u * G;
+        const int L = L0 + u * G * ty;
         const long long o = i + static_cast<long long>(nx) * (L < lines ? L : 0);
         hh[u] = L < lines ? *reinterpret_cast<const float4*>(h + o) : make_float4(0.f, 0.f, 0.f, 0.f);
         ll[u] = L < lines ? *reinterpret_cast<const float4*>(l + o) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1291,7 +1296,7 @@ wsum4_kernel(int nx, int ny, int nz, const float* __restrict__ h, const float* _
       const float4 gl = *reinterpret_cast<const float4*>(gx + nx + i);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        if (L0 + u * G >= lines) break;
+        if (L0 + u * G * ty >= lines) break;
         const int j = jj[u], k = kk[u];
         const df wline = df_mul({gy[j], gy[ny + j]}, {gz[k], gz[nz + k]});
         acc_mul(s, wline.hi, wline.lo, df_mul({gh.x, gl.x}, {hh[u].x, ll[u].x}));
@@ -1313,7 +1318,7 @@ wsum4_kernel(int nx, int ny, int nz, const float* __restrict__ h, const float* _
   s = fast_two_sum(s.hi, s.lo);
   double v = static_cast<double>(s.hi) + s.lo;
   v = warp_sum_d(v);
-  if (threadIdx.x % 32 == 0) atomicAdd(out, v);
+  if ((threadIdx.x + blockDim.x * threadIdx.y) % 32 == 0) atomicAdd(out, v);
 }
 
 // df_to_f64_kernel on groups of four points (n a multiple of 4, out 16-byte aligned)
@@ -1365,6 +1370,14 @@ pack_kernel(int rows, int K, int ld, const double* __restrict__ src, void* d0, v
       static_cast<float*>(d0)[di] = static_cast<float>(v);
     }
   }
+}
+
+// Block of 256 threads as rows of one x-line each: blockDim.x covers Nx with
+// `per` points per thread (a multiple of 32, at most 256), blockDim.y lines.
+dim3 line_block(int nx, int per) {
+  int tx = ((nx + per - 1) / per + 31) / 32 * 32;
+  if (tx > 256) tx = 256;
+  return dim3(tx, 256 / tx, 1);
 }
 
 int grid_for(long long n, int bs, int dev) {
@@ -1537,7 +1550,8 @@ cudaError_t launch_prepare(const tpt_plan_s* p, const double* f, const MixedWork
   note_launch(1);
   if (p->n[0] % 2 == 0 && reinterpret_cast<uintptr_t>(f) % 16 == 0) {   // two points per thread
     const long long lines = static_cast<long long>(p->n[1]) * p->n[2];
-    prepare2_kernel<FMT><<<grid_for(lines * 256, 256, p->dev), 256, 0, s>>>(
+    const dim3 blk = line_block(p->n[0], 2);
+    prepare2_kernel<FMT><<<grid_for(lines * blk.x, blk.x * blk.y, p->dev), blk, 0, s>>>(
         p->n[0], p->n[1], p->n[2], p->mixed.ldx, f, w.fh, w.fl, w.R[0], w.R[1], p->mixed.dfgeom[0],
         p->mixed.dfgeom[1], p->mixed.dfgeom[2], w.scal + 5);
     return cudaGetLastError();
@@ -1871,7 +1885,9 @@ int solve_fmt(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStrea
     MX_CUDA(cudaMemsetAsync(w.scal + 2, 0, sizeof(double), s));
     note_launch(1);
     if (p->n[0] % 4 == 0)   // four points per thread
-      wsum4_kernel<<<grid_for(static_cast<long long>(p->n[1]) * p->n[2] * 256, 256, p->dev), 256, 0, s>>>(
+      wsum4_kernel<<<grid_for(static_cast<long long>(p->n[1]) * p->n[2] * line_block(p->n[0], 4).x,
+                              256, p->dev),
+                     line_block(p->n[0], 4), 0, s>>>(
           p->n[0], p->n[1], p->n[2], w.ph, w.pl,
                                                                p->mixed.dfgeom[0], p->mixed.dfgeom[1],
                                                                p->mixed.dfgeom[2], w.scal + 2);
