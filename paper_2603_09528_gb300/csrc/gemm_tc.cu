@@ -63,10 +63,13 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 template <int KIND, int NPL, int BN>
 struct Cfg {
   static constexpr int EB = (KIND == kKindBF16) ? 2 : 4;     // element bytes
-  static constexpr int BK = 128 / EB;                         // elements per 128-byte row
+  // bytes of a K-row of a stage: 64 (64-byte swizzle) for the split-bf16
+  // 256-column tile, so that four stages fit instead of two; 128 otherwise
+  static constexpr int SW = (NPL == 2 && BN == 256) ? 64 : 128;
+  static constexpr int BK = SW / EB;                          // elements per row
   static constexpr int KI = (KIND == kKindBF16) ? 16 : 8;     // K of one MMA instruction
-  static constexpr int A_BYTES = BM * 128;                    // one plane of A per stage
-  static constexpr int B_BYTES = BN * 128;
+  static constexpr int A_BYTES = BM * SW;                     // one plane of A per stage
+  static constexpr int B_BYTES = BN * SW;
   static constexpr int STAGE = NPL * (A_BYTES + B_BYTES);
   static constexpr int STAGES = (kSmemBudget / STAGE) > 4 ? 4 : (kSmemBudget / STAGE);
   static constexpr int TMEM_COLS = 2 * BN < 32 ? 32 : 2 * BN;   // two accumulator buffers
@@ -258,19 +261,19 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
         if (PAIR == 1) {          // own A; half of the shared B tile, to both CTAs
           const int hb = BN / 2;
           ptx::tma_load_2d(ptx::smem_u32(st), &tA0, full, kx, m0);   // n0: the pair's common n-tile
-          ptx::tma_load_2d_mc(ptx::smem_u32(st + NPL * C::A_BYTES + rank * hb * 128), &tB0, full, kx,
+          ptx::tma_load_2d_mc(ptx::smem_u32(st + NPL * C::A_BYTES + rank * hb * C::SW), &tB0, full, kx,
                               n0 + rank * hb, kPairMask);
           if (NPL == 2) {
             ptx::tma_load_2d(ptx::smem_u32(st + C::A_BYTES), &tA1, full, kx, m0);
-            ptx::tma_load_2d_mc(ptx::smem_u32(st + NPL * C::A_BYTES + C::B_BYTES + rank * hb * 128), &tB1, full,
+            ptx::tma_load_2d_mc(ptx::smem_u32(st + NPL * C::A_BYTES + C::B_BYTES + rank * hb * C::SW), &tB1, full,
                                 kx, n0 + rank * hb, kPairMask);
           }
         } else if (PAIR == 2) {   // half of the shared A tile, to both CTAs; own B
           const int ha = BM / 2;
-          ptx::tma_load_2d_mc(ptx::smem_u32(st + rank * ha * 128), &tA0, full, kx, m0 + rank * ha, kPairMask);
+          ptx::tma_load_2d_mc(ptx::smem_u32(st + rank * ha * C::SW), &tA0, full, kx, m0 + rank * ha, kPairMask);
           ptx::tma_load_2d(ptx::smem_u32(st + NPL * C::A_BYTES), &tB0, full, kx, n0);
           if (NPL == 2) {
-            ptx::tma_load_2d_mc(ptx::smem_u32(st + C::A_BYTES + rank * ha * 128), &tA1, full, kx, m0 + rank * ha,
+            ptx::tma_load_2d_mc(ptx::smem_u32(st + C::A_BYTES + rank * ha * C::SW), &tA1, full, kx, m0 + rank * ha,
                                 kPairMask);
             ptx::tma_load_2d(ptx::smem_u32(st + NPL * C::A_BYTES + C::B_BYTES), &tB1, full, kx, n0);
           }
@@ -321,9 +324,9 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
             const uint32_t bb = sb + (p == 1 ? C::B_BYTES : 0) + off;
             const uint32_t acc = (kc > 0 || kk > 0 || p > 0) ? 1u : 0u;
             if (KIND == kKindBF16)
-              ptx::mma_bf16(d, ptx::smem_desc_k_sw128(a), ptx::smem_desc_k_sw128(bb), idesc, acc);
+              ptx::mma_bf16(d, ptx::smem_desc_k_sw<C::SW>(a), ptx::smem_desc_k_sw<C::SW>(bb), idesc, acc);
             else
-              ptx::mma_tf32(d, ptx::smem_desc_k_sw128(a), ptx::smem_desc_k_sw128(bb), idesc, acc);
+              ptx::mma_tf32(d, ptx::smem_desc_k_sw<C::SW>(a), ptx::smem_desc_k_sw<C::SW>(bb), idesc, acc);
           }
         }
         if (PAIR) ptx::mma_commit_mc(ptx::smem_u32(&bars[C::STAGES + s]), kPairMask);   // frees the stage
@@ -435,20 +438,20 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // K-major operand plane: rows x K elements, row stride ld elements; box of
-// (128-byte row) x box_rows with the 128-byte swizzle.
-bool make_map(CUtensorMap* map, const void* base, int kind, int rows, int K, int ld, int box_rows) {
+// (sw-byte row) x box_rows with the sw-byte swizzle (sw = 64 or 128).
+bool make_map(CUtensorMap* map, const void* base, int kind, int rows, int K, int ld, int box_rows, int sw) {
   auto fn = encode_fn();
   if (!fn || !base) return false;
   const int eb = (kind == kKindBF16) ? 2 : 4;
   if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || (static_cast<long long>(ld) * eb) % 16 != 0) return false;
   cuuint64_t dims[2] = {static_cast<cuuint64_t>(K), static_cast<cuuint64_t>(rows)};
   cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * eb};
-  cuuint32_t box[2] = {static_cast<cuuint32_t>(128 / eb), static_cast<cuuint32_t>(box_rows)};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(sw / eb), static_cast<cuuint32_t>(box_rows)};
   cuuint32_t estr[2] = {1, 1};
   const CUtensorMapDataType dt =
       (kind == kKindBF16) ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   CUresult r = fn(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, sw == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -492,11 +495,11 @@ cudaError_t launch(const Operand& A, const Operand& B, const GemmOut& g, cudaStr
   }
   // the shared operand of a pair is loaded in halves (one per CTA)
   const int a_rows = PAIR == 2 ? BM / 2 : BM, b_rows = PAIR == 1 ? BN / 2 : BN;
-  if (!make_map(&m[0], A.plane[0], KIND, A.rows, A.K, A.ld, a_rows)) return cudaErrorInvalidValue;
-  if (!make_map(&m[2], B.plane[0], KIND, B.rows, B.K, B.ld, b_rows)) return cudaErrorInvalidValue;
+  if (!make_map(&m[0], A.plane[0], KIND, A.rows, A.K, A.ld, a_rows, C::SW)) return cudaErrorInvalidValue;
+  if (!make_map(&m[2], B.plane[0], KIND, B.rows, B.K, B.ld, b_rows, C::SW)) return cudaErrorInvalidValue;
   if (NPL == 2) {
-    if (!make_map(&m[1], A.plane[1], KIND, A.rows, A.K, A.ld, a_rows)) return cudaErrorInvalidValue;
-    if (!make_map(&m[3], B.plane[1], KIND, B.rows, B.K, B.ld, b_rows)) return cudaErrorInvalidValue;
+    if (!make_map(&m[1], A.plane[1], KIND, A.rows, A.K, A.ld, a_rows, C::SW)) return cudaErrorInvalidValue;
+    if (!make_map(&m[3], B.plane[1], KIND, B.rows, B.K, B.ld, b_rows, C::SW)) return cudaErrorInvalidValue;
   } else {
     m[1] = m[0];
     m[3] = m[2];

@@ -217,6 +217,22 @@ __device__ __forceinline__ uint64_t smem_desc_k_sw128(uint32_t saddr) {
   return d;
 }
 
+// The same for rows of 64 bytes with the 64-byte swizzle (8-row atoms 512
+// bytes apart, swizzle mode 4); SW selects the layout.
+__device__ __forceinline__ uint64_t smem_desc_k_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+  d |= static_cast<uint64_t>(1u) << 16;
+  d |= static_cast<uint64_t>(512u >> 4) << 32;
+  d |= static_cast<uint64_t>(1u) << 46;
+  d |= static_cast<uint64_t>(4u) << 61;
+  return d;
+}
+template <int SW>
+__device__ __forceinline__ uint64_t smem_desc_k_sw(uint32_t saddr) {
+  return SW == 64 ? smem_desc_k_sw64(saddr) : smem_desc_k_sw128(saddr);
+}
+
 // Instruction descriptor: D in f32, A and B of format `fmt` (1 = bf16 for
 // kind::f16, 2 = tf32 for kind::tf32), both K-major, shape M x N.
 __host__ __device__ constexpr uint32_t instr_desc(uint32_t fmt, uint32_t M, uint32_t N) {
