@@ -260,7 +260,6 @@ def run_ours(args):
             tiles = plan.tiles()
         else:
             tiles = plan.autotune(work, stream=stream)   # transform GEMM column tiles per stage
-        plan.set_stage_timing(True)
     # warm-up
     info = None
     for _ in range(args.warmup):
@@ -291,12 +290,18 @@ def run_ours(args):
     value = job_rate(args.steps, world, t_max / 1e3)
     npts = n[0] * n[1] * n[2]
     stages = None
-    if prec != 0 and infos and infos[0]:
-        ms = np.mean([i["ms_stage"] for i in infos], axis=0)
-        its = float(np.mean([i["iters"] for i in infos]))
-        stages = stage_rooflines(ms, its, n, prec)
-        stages["per_solve_ms"] = {"input_conversion": float(ms[0]), "gauge_and_output": float(ms[7])}
+    if prec != 0:
+        # per-stage kernel times: the same solves again with CUDA events around
+        # every stage (that mode synchronises once per correction, so it is kept
+        # out of the timed region above)
+        plan.set_stage_timing(True)
+        tinfos = [plan.solve(f_dev, phi, work, stream=stream, want_info=True)[1] for _ in range(args.steps)]
         plan.set_stage_timing(False)
+        ms = np.mean([i["ms_stage"] for i in tinfos], axis=0)
+        its = float(np.mean([i["iters"] for i in tinfos]))
+        stages = stage_rooflines(ms, its, n, prec)
+        stages["per_solve_ms"] = {"input_conversion": float(ms[0]), "gauge_and_output": float(ms[7]),
+                                  "stage_sum": float(np.sum(ms[0:8]))}
 
     # roofline of the dominant kernel
     if prec == 0:
@@ -317,8 +322,21 @@ def run_ours(args):
             plan.solve_host(f_pin, phi_pin, f2, phi, work, stream=stream)
         torch.cuda.synchronize()
         dt = max_over_ranks(time.perf_counter() - t0, world, "cuda")
-        e2e = {"value": job_rate(args.steps, world, dt), "unit": "solves/s", "h2d_bytes_per_step": npts * 8,
-               "d2h_bytes_per_step": npts * 8}
+        one_at_a_time = {"value": job_rate(args.steps, world, dt), "api": "tpt_solve_host, one call after another"}
+        spec = dict(n=n, dxf=[g[0] for g in grids], dxc=[g[1] for g in grids], bc=[(1, 1)] * 3,
+                    xform=(tpt.GEMM, tpt.GEMM), alpha=0.0, beta=1.0, precision=prec, rtol=rtol,
+                    max_refine=refine)
+        # a stream of requests long enough that filling and draining the
+        # copy/solve pipeline does not dominate the rate
+        nreq = max(args.steps, 20)
+        srv = e2e_server(tpt, local, spec, f_pin, nreq, args.warmup, phi, barrier)
+        dt_srv = max_over_ranks(srv.pop("seconds"), world, "cuda")
+        e2e = {"value": job_rate(nreq, world, dt_srv), "unit": "solves/s", "h2d_bytes_per_step": npts * 8,
+               "d2h_bytes_per_step": npts * 8,
+               "api": "tpt_server_submit / tpt_server_wait: consecutive solves from pinned host buffers, "
+                      "each request's host-to-device copy, solve and device-to-host copy overlapping "
+                      "those of its neighbours on %d slots" % srv["slots"],
+               "server": srv, "one_call_at_a_time": one_at_a_time}
 
     # float64 path on the same workload, for the FP64-vs-mixed comparison
     fp64 = None
@@ -700,6 +718,43 @@ def stage_rooflines(ms, iters, n, prec):
         if key in MEASURED_TRAFFIC_PER_POINT:
             d["traffic"] = MEASURED_TRAFFIC_PER_POINT[key] * npts
     return {"per_stage": out, "iters": iters, "peak_source": "MEASURED_PEAKS.json (burst)"}
+
+
+def e2e_server(tpt, device, spec, f_pin, steps, warmup, phi_ref, barrier, slots=3):
+    """End to end through the serving API: `steps` solves of the headline
+    workload submitted back to back with pinned host buffers (f read from
+    host memory, phi written back to host memory by every request), timed from
+    the first submission to the last completion; the server overlaps each
+    request's copies with its neighbours' solves.  The last result is checked
+    against the solve of the same right-hand side on the device."""
+    import torch
+    npts = f_pin.numel()
+    ring = [torch.empty(npts, dtype=torch.float64).pin_memory() for _ in range(2 * slots + 2)]
+    srv = tpt.Server(device=device, slots=slots, setup_threads=2, memory_budget=64 << 30,
+                     cache_budget=8 << 30)
+    try:
+        srv.warm(**spec)
+        for t in [srv.submit(f_pin, ring[i % len(ring)], **spec) for i in range(warmup)]:
+            r = srv.wait(t, timeout=300.0)
+            if r is None or r["status"] != 0:
+                raise RuntimeError("e2e warm-up request failed: %r" % (r,))
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        tickets = [srv.submit(f_pin, ring[i % len(ring)], **spec) for i in range(steps)]
+        res = [srv.wait(t, timeout=300.0) for t in tickets]
+        seconds = time.perf_counter() - t0
+    finally:
+        srv.close()
+    bad = [r for r in res if r is None or r["status"] != 0]
+    if bad:
+        raise RuntimeError("e2e request failed: %r" % (bad[0],))
+    ref = phi_ref.cpu()
+    last = ring[(steps - 1) % len(ring)]
+    diff = float((last - ref).abs().max() / ref.abs().max())
+    return {"seconds": seconds, "slots": slots, "requests": steps,
+            "max_rel_residual": max(r["rel_residual"] for r in res),
+            "max_rel_diff_vs_device_solve": diff}
 
 
 def dominant_kernel(plan, prec, n, f_dev, steps, stream):

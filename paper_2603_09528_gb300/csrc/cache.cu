@@ -16,11 +16,61 @@
 #include <functional>
 #include <mutex>
 #include <unordered_map>
+#include <vector>
 
 #include "cache.h"
 #include "tpt_internal.h"
 
 namespace tpt {
+
+namespace {
+struct PinnedSlots {
+  std::mutex mu;
+  std::vector<std::pair<double*, double*>> free;   // (host, device)
+  std::unordered_map<double*, double*> dev_of;
+};
+PinnedSlots& pinned_slots() {
+  static PinnedSlots* s = new PinnedSlots();   // lives to process exit
+  return *s;
+}
+}  // namespace
+
+double* pinned_slot_acquire(double** dev) {
+  PinnedSlots& ps = pinned_slots();
+  std::lock_guard<std::mutex> g(ps.mu);
+  if (ps.free.empty()) {
+    constexpr int kSlots = 256, kDoubles = 16;
+    void* blk = nullptr;
+    if (cudaHostAlloc(&blk, kSlots * kDoubles * sizeof(double), cudaHostAllocMapped | cudaHostAllocPortable) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    void* dblk = nullptr;
+    if (cudaHostGetDevicePointer(&dblk, blk, 0) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;   // the block stays allocated (never freed), unused
+    }
+    std::memset(blk, 0, kSlots * kDoubles * sizeof(double));
+    for (int i = kSlots - 1; i >= 0; --i)
+      ps.free.emplace_back(static_cast<double*>(blk) + i * kDoubles, static_cast<double*>(dblk) + i * kDoubles);
+  }
+  const auto slot = ps.free.back();
+  ps.free.pop_back();
+  ps.dev_of[slot.first] = slot.second;
+  *dev = slot.second;
+  return slot.first;
+}
+
+void pinned_slot_release(double* host) {
+  if (!host) return;
+  PinnedSlots& ps = pinned_slots();
+  std::lock_guard<std::mutex> g(ps.mu);
+  auto it = ps.dev_of.find(host);
+  if (it == ps.dev_of.end()) return;
+  ps.free.emplace_back(host, it->second);
+  ps.dev_of.erase(it);
+}
 
 namespace {
 
@@ -157,6 +207,13 @@ int BasisCache::init() {
   if (st != TPT_OK) return st;
   uint64_t keep = ~0ULL;   // keep freed memory in the pool: no release to the driver
   st = st_of(cudaMemPoolSetAttribute(pool_, cudaMemPoolAttrReleaseThreshold, &keep));
+  if (st != TPT_OK) return st;
+  // an allocation on one stream must not reuse a block freed on another
+  // stream by waiting for that stream (requests on different slots would
+  // then run one after another); it reuses blocks whose free has completed
+  // and grows the pool otherwise
+  int no = 0;
+  st = st_of(cudaMemPoolSetAttribute(pool_, cudaMemPoolReuseAllowInternalDependencies, &no));
   if (st != TPT_OK) return st;
   return st_of(cudaStreamCreateWithFlags(&stream_, cudaStreamNonBlocking));
 }

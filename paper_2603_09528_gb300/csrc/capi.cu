@@ -60,6 +60,9 @@ void free_plan(tpt_plan_s* p) {
     p->arena.release();
     if (p->own_stream && p->arena.stream) cudaStreamDestroy(p->arena.stream);
     if (p->h_ring) cudaFreeHost(p->h_ring);
+    if (p->solve_exec) cudaGraphExecDestroy(p->solve_exec);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    tpt::pinned_slot_release(p->h_scal);
     cudaGetLastError();
   }
   delete p;

@@ -183,6 +183,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
                const __grid_constant__ CUtensorMap tB0, const __grid_constant__ CUtensorMap tB1,
                const __grid_constant__ CUtensorMap tO0, const __grid_constant__ CUtensorMap tO1,
                const GemmOut g) {
+  if (g.skip && *g.skip) return;   // uniform over the grid: no barrier or TMEM is touched
   using C = Cfg<KIND, NPL, BN>;
   static_assert(C::STAGES >= 2, "shared-memory ring needs two stages");
   extern __shared__ __align__(128) uint8_t smem_raw[];

@@ -21,6 +21,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <shared_mutex>
 #include <new>
 #include <thread>
 #include <unordered_map>
@@ -56,6 +57,12 @@ struct tpt_server_s {
   tpt::BasisCache cache;
   std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
   std::mutex mu;
+  std::mutex h2d_mu;   // one input copy at a time (see execute)
+  // Solves of large requests (each fills the GPU) run one at a time, so that
+  // the solve in progress has the device to itself while other slots copy;
+  // smaller ones share the device
+  std::shared_mutex compute_mu;
+  static constexpr size_t kExclusivePoints = size_t(1) << 24;
   std::condition_variable cv_setup, cv_ready, cv_done;
   std::deque<Request*> setup_q;
   std::map<unsigned long long, Request*> ready;   // planned, ordered by arrival
@@ -140,9 +147,22 @@ struct tpt_server_s {
       double* f = reinterpret_cast<double*>(aligned(buf[0]));
       double* phi = reinterpret_cast<double*>(aligned(buf[1]));
       void* work = aligned(buf[2]);
-      st = cuda_st(cudaMemcpyAsync(f, r->f_host, bytes, cudaMemcpyHostToDevice, s));
+      {
+        // input copies take turns (in about admission order) instead of
+        // sharing the host link, so that the oldest admitted request's solve
+        // starts as early as possible and the next copy overlaps it
+        std::lock_guard<std::mutex> g(h2d_mu);
+        st = cuda_st(cudaMemcpyAsync(f, r->f_host, bytes, cudaMemcpyHostToDevice, s));
+        if (st == TPT_OK) st = cuda_st(cudaStreamSynchronize(s));
+      }
       if (st == TPT_OK) {
-        st = tpt_solve(r->plan, f, phi, work, s, &r->res.info);
+        if (r->npts >= kExclusivePoints) {
+          std::unique_lock<std::shared_mutex> g(compute_mu);
+          st = tpt_solve(r->plan, f, phi, work, s, &r->res.info);
+        } else {
+          std::shared_lock<std::shared_mutex> g(compute_mu);
+          st = tpt_solve(r->plan, f, phi, work, s, &r->res.info);
+        }
         if (st == TPT_OK || st == TPT_ERR_NOT_CONVERGED) {
           const int cs = cuda_st(cudaMemcpyAsync(r->phi_host, phi, bytes, cudaMemcpyDeviceToHost, s));
           if (cs != TPT_OK) st = cs;

@@ -40,6 +40,7 @@ struct GemmOut {
                     // 1 = pairs of m-tiles share B, 2 = pairs of n-tiles share A
   int tma_out = 1;  // TMA-store epilogue where the output layout allows (split bf16,
                     // bf16 or float32 out, 128/256-column tiles, one CTA per tile)
+  const int* skip = nullptr;   // device flag: the kernel returns at entry when it is nonzero
 };
 
 // Column tile width used when GemmOut::bn is 0.

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <memory>
@@ -119,6 +120,20 @@ struct tpt_plan_s {
   int precision = TPT_PREC_FP64;
   double rtol = 0.0;
   int max_refine = 1;
+  std::atomic<int> last_iters{0};   // corrections the last adaptive mixed solve used (0: none yet)
+  // The adaptive mixed solve as one CUDA graph, captured on the second call with
+  // the same (f, phi, work, planned corrections, generation) and replayed after;
+  // taken by one caller at a time (graph_busy).
+  cudaGraphExec_t solve_exec = nullptr;
+  const void* gkey[3] = {nullptr, nullptr, nullptr};
+  const void* gprev[3] = {nullptr, nullptr, nullptr};
+  int gkey_planned = 0, gprev_planned = 0;
+  unsigned gkey_gen = 0, gprev_gen = 0;
+  unsigned long long graph_launches = 0;   // kernels in the captured solve
+  cudaStream_t cap_stream = nullptr;
+  double* h_scal = nullptr;                // pinned, mapped slot for the workspace scalars
+  double* d_hscal = nullptr;               // its device address
+  std::atomic<bool> graph_busy{false};
   bool singular = false;
   int null_i = 0, null_j = 0;     // mode indices of the null line when singular
   tpt::Dir1D dir[3];
@@ -146,6 +161,14 @@ struct tpt_plan_s {
 namespace tpt {
 
 size_t npts(const tpt_plan_s* p);
+
+// Process-wide pool of 16-double host slots in pinned, device-mapped memory,
+// for scalars a kernel writes straight into host memory (no copy engine, so
+// they do not queue behind large host transfers of other streams).  Blocks
+// are never returned to the driver (freeing pinned memory synchronises the
+// device).  `dev` receives the slot's device address; nullptr on failure.
+double* pinned_slot_acquire(double** dev);
+void pinned_slot_release(double* host);
 
 // Count of kernels this library has launched (all devices, all threads).
 void note_launch(unsigned long long k = 1);

@@ -303,3 +303,41 @@ def test_tma_residual_equals_direct_loads_and_the_oracle(case):
     ref, _ = O.solve_tensor(f, dirs, *coef)
     assert info["rel_residual"] <= 1e-10 and rel <= 2e-10, (info, rel)
     assert np.abs(got - ref).max() <= 1e-7 * np.abs(ref).max()
+
+
+def test_adaptive_solve_replayed_as_graph_and_continued_past_the_planned_corrections():
+    # the adaptive solve stops on the device (converge_kernel) and is replayed
+    # from a CUDA graph once the same call repeats: repeated calls must give
+    # the first call's result, a new right-hand side in the same buffer must
+    # give that right-hand side's solution, and a plan whose previous solve
+    # needed one correction must continue past it when the next one needs more
+    n = (64, 48, 40)
+    dirs = _dirs(n, (1.5, 2.0, 2.5), [(1, 1)] * 3)
+    kw = dict(xform=(tpt.GEMM, tpt.GEMM), alpha=0.0, beta=1.0, precision=PRECS["bf16x3"], rtol=1e-10,
+              max_refine=8)
+    plan = tpt.Plan(n, [d.dxf for d in dirs], [d.dxc for d in dirs], [(1, 1)] * 3, **kw)
+    f1 = S.remove_weighted_mean(S.uniform_rhs(n, 41), [d.dxf for d in dirs])
+    f2 = S.remove_weighted_mean(S.uniform_rhs(n, 42), [d.dxf for d in dirs])
+    f_dev = tpt.field_to_device(f1)
+    phi = plan.new_field()
+    work = plan.new_workspace()
+    outs = []
+    for _ in range(4):                      # direct, direct + capture, replay, replay
+        _, info = plan.solve(f_dev, phi, work)
+        outs.append((phi.cpu().numpy().copy(), info))
+    for o, inf in outs[1:]:
+        assert np.abs(o - outs[0][0]).max() <= 1e-12 * np.abs(outs[0][0]).max()
+        assert inf["iters"] == outs[0][1]["iters"] and inf["rel_residual"] <= 1e-10
+    f_dev.copy_(tpt.field_to_device(f2))
+    _, info2 = plan.solve(f_dev, phi, work)
+    ref2, _ = O.solve_tensor(f2, dirs, 0.0, 1.0)
+    got2 = tpt.field_to_host(phi, n)
+    assert info2["rel_residual"] <= 1e-10
+    assert np.abs(got2 - ref2).max() <= 1e-7 * np.abs(ref2).max()
+    # a zero right-hand side converges at once (one correction); the next,
+    # non-zero one must then run past that plan
+    plan0 = tpt.Plan(n, [d.dxf for d in dirs], [d.dxc for d in dirs], [(1, 1)] * 3, **kw)
+    _, i0 = plan0.solve(tpt.field_to_device(np.zeros(n)))
+    assert i0["iters"] == 1
+    _, i1 = plan0.solve(tpt.field_to_device(f1))
+    assert i1["iters"] > 1 and i1["rel_residual"] <= 1e-10
