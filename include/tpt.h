@@ -226,8 +226,9 @@ int tpt_tc_gemm(int precision, int M, int N, int K, const double* A_dev, const d
  * tma_out = 1 lets the kernel stage each 32 x 32 output chunk in shared
  * memory and store it with a bulk tensor copy, where the layout allows it
  * (128/256-column tiles; rm >= M, or rm a multiple of 32 dividing M; 16-byte
- * aligned bases and strides); 0 forces per-thread stores.  Elements outside
- * the index set are left untouched.  Output buffers are the caller's, on the
+ * aligned bases and strides); 0 forces per-thread stores.  pair: two-CTA
+ * clusters as in tpt_tc_gemm.  Elements outside the index set are left
+ * untouched.  Output buffers are the caller's, on the
  * current device; other arguments as tpt_tc_gemm.  TPT_ERR_INVALID_ARG for
  * an unknown kind, a non-positive size or rm, or a null pointer.           */
 #define TPT_GEMM_OUT_F32 0
@@ -235,7 +236,7 @@ int tpt_tc_gemm(int precision, int M, int N, int K, const double* A_dev, const d
 #define TPT_GEMM_OUT_SPLIT_BF16 2
 int tpt_tc_gemm_out(int precision, int M, int N, int K, const double* A_dev, const double* B_dev,
                     int out_kind, int rm, long long sm, long long sn, void* out0_dev, void* out1_dev,
-                    void* work_dev, void* stream, int tile, int tma_out);
+                    void* work_dev, void* stream, int tile, int tma_out, int pair);
 
 /* Host copies of the plan's tables, for inspection and tests.  lam: n[dir]
  * eigenvalues of direction dir (0 = x, 1 = y) in the plan's mode order;

@@ -110,7 +110,7 @@ SIGNATURES = [
                               C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
     ("tpt_tc_gemm_out", C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_int,
                                   C.c_longlong, C.c_longlong, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
-                                  C.c_int, C.c_int]),
+                                  C.c_int, C.c_int, C.c_int]),
     ("tpt_plan_eigenvalues", C.c_int, [C.c_void_p, C.c_int, _dp]),
     ("tpt_plan_transforms", C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     ("tpt_plan_rows", C.c_int, [C.c_void_p, C.c_int, _dp, _dp, _dp]),

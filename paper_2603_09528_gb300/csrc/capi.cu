@@ -621,8 +621,9 @@ int tpt_tc_gemm(int precision, int M, int N, int K, const double* A, const doubl
 
 int tpt_tc_gemm_out(int precision, int M, int N, int K, const double* A, const double* B, int out_kind, int rm,
                     long long sm, long long sn, void* out0, void* out1, void* work, void* stream, int tile,
-                    int tma_out) {
+                    int tma_out, int pair) {
   if (tile != 0 && tile != 32 && tile != 64 && tile != 128 && tile != 256) return TPT_ERR_INVALID_ARG;
+  if (pair < 0 || pair > 2) return TPT_ERR_INVALID_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
@@ -630,7 +631,7 @@ int tpt_tc_gemm_out(int precision, int M, int N, int K, const double* A, const d
   }
   if (reinterpret_cast<uintptr_t>(work) % 256 != 0) return TPT_ERR_INVALID_ARG;
   return tpt::tc_gemm_out_test(precision, M, N, K, A, B, out_kind, rm, sm, sn, out0, out1, work, dev,
-                               static_cast<cudaStream_t>(stream), tile, tma_out != 0);
+                               static_cast<cudaStream_t>(stream), tile, tma_out != 0, pair);
 }
 
 int tpt_set_stage_timing(tpt_plan p, int enable) {

@@ -556,13 +556,17 @@ cudaError_t launch_pair(const Operand& A, const Operand& B, const GemmOut& g, cu
   constexpr bool can1 = NPL == 2 && BN >= 128 &&
                         (OUT == kOutSplitBF16 || OUT == kOutBF16 || OUT == kOutF32 || OUT == kOutF64);
   constexpr bool can2 = NPL == 2 && BN >= 128 && (OUT == kOutF32 || OUT == kOutDF || OUT == kOutF64);
-  if (g.pair == 1 && can1 && num_m % 2 == 0) return launch<KIND, NPL, BN, OUT, can1 ? 1 : 0>(A, B, g, s);
-  if (g.pair == 2 && can2 && num_n % 2 == 0) return launch<KIND, NPL, BN, OUT, can2 ? 2 : 0>(A, B, g, s);
   // TMA-store epilogue when the output is a plain block of rows or whole
   // 32-row chunks of rm-row blocks
   constexpr bool cant = OUT == kOutSplitBF16 || OUT == kOutBF16 || OUT == kOutF32;
-  if (cant && g.tma_out && (g.rm >= g.M || (g.rm % 32 == 0 && g.M % g.rm == 0)))
-    return launch<KIND, NPL, BN, OUT, 0, cant ? 1 : 0>(A, B, g, s);
+  const bool tma = cant && g.tma_out && (g.rm >= g.M || (g.rm % 32 == 0 && g.M % g.rm == 0));
+  if (g.pair == 1 && can1 && num_m % 2 == 0)
+    return tma ? launch<KIND, NPL, BN, OUT, can1 ? 1 : 0, cant ? 1 : 0>(A, B, g, s)
+               : launch<KIND, NPL, BN, OUT, can1 ? 1 : 0>(A, B, g, s);
+  if (g.pair == 2 && can2 && num_n % 2 == 0)
+    return tma ? launch<KIND, NPL, BN, OUT, can2 ? 2 : 0, cant ? 1 : 0>(A, B, g, s)
+               : launch<KIND, NPL, BN, OUT, can2 ? 2 : 0>(A, B, g, s);
+  if (tma) return launch<KIND, NPL, BN, OUT, 0, cant ? 1 : 0>(A, B, g, s);
   return launch<KIND, NPL, BN, OUT, 0>(A, B, g, s);
 }
 

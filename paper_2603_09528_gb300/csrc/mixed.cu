@@ -2425,7 +2425,7 @@ int tc_gemm_test(int precision, int M, int N, int K, const double* A, const doub
 
 int tc_gemm_out_test(int precision, int M, int N, int K, const double* A, const double* B, int out_kind,
                      int rm, long long sm, long long sn, void* out0, void* out1, void* work, int dev,
-                     cudaStream_t s, int tile, int tma_out) {
+                     cudaStream_t s, int tile, int tma_out, int pair) {
   if (M <= 0 || N <= 0 || K <= 0 || rm <= 0 || !A || !B || !out0 || !work) return TPT_ERR_INVALID_ARG;
   if (precision < TPT_PREC_MIXED_BF16 || precision > TPT_PREC_MIXED_TF32) return TPT_ERR_INVALID_ARG;
   int mode;
@@ -2452,6 +2452,7 @@ int tc_gemm_out_test(int precision, int M, int N, int K, const double* A, const 
   tc::GemmOut g = gout(M, N, K, rm, sm, sn, out0, out1, mode, 0, 0, nullptr);
   g.bn = tile;
   g.tma_out = tma_out;
+  g.pair = pair;
   MX_CUDA(tc::gemm(kind_of(fmt), nplanes(fmt), operand(pa, M, K, ld), operand(pb, N, K, ld), g, s));
   return TPT_OK;
 }

@@ -212,7 +212,7 @@ int tc_gemm_test(int precision, int M, int N, int K, const double* A, const doub
                  void* work, int dev, cudaStream_t s, int tile = 0, int pair = 0);
 int tc_gemm_out_test(int precision, int M, int N, int K, const double* A, const double* B, int out_kind,
                      int rm, long long sm, long long sn, void* out0, void* out1, void* work, int dev,
-                     cudaStream_t s, int tile, int tma_out);
+                     cudaStream_t s, int tile, int tma_out, int pair);
 
 // Capturable solves: 1 + max_refine corrections and a final residual, no host
 // synchronisation; the residual sums are left in the first 16 doubles of the

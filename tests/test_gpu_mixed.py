@@ -190,7 +190,7 @@ def test_mixed_solve_with_two_cta_pairs_equals_default():
     assert np.abs(a - r).max() <= 1e-12 * np.abs(r).max()
 
 
-def _tc_gemm_out(prec, A, B, kind, rm, sm, sn, size, tile, tma_out):
+def _tc_gemm_out(prec, A, B, kind, rm, sm, sn, size, tile, tma_out, pair=0):
     M, K = A.shape
     N = B.shape[0]
     a = torch.from_numpy(np.ascontiguousarray(A)).cuda()
@@ -203,7 +203,7 @@ def _tc_gemm_out(prec, A, B, kind, rm, sm, sn, size, tile, tma_out):
     st = L.lib.tpt_tc_gemm_out(PRECS[prec], M, N, K, C.c_void_p(a.data_ptr()), C.c_void_p(b.data_ptr()), kind,
                                rm, sm, sn, C.c_void_p(o0.data_ptr()), C.c_void_p(o1.data_ptr()),
                                C.c_void_p(work.data_ptr()), C.c_void_p(torch.cuda.current_stream().cuda_stream),
-                               tile, tma_out)
+                               tile, tma_out, pair)
     assert st == L.TPT_OK, L.lib.tpt_status_string(st)
     torch.cuda.synchronize()
     return o0.float().cpu().numpy(), o1.float().cpu().numpy()
@@ -220,7 +220,8 @@ OUT_CASES = [((384, 512, 64), 1 << 30, 0, 400), ((200, 300, 72), 1 << 30, 0, 208
 @pytest.mark.parametrize("kind", ["f32", "bf16", "split"])
 @pytest.mark.parametrize("case", OUT_CASES)
 @pytest.mark.parametrize("tile", [128, 256])
-def test_tc_gemm_output_formats_and_layouts(kind, case, tile):
+@pytest.mark.parametrize("pair", [0, 1, 2])
+def test_tc_gemm_output_formats_and_layouts(kind, case, tile, pair):
     # the bulk-tensor-store epilogue and the per-thread stores must write the
     # same values to the same indices and nothing else; the values are the
     # exact integer products, rounded once to the output format
@@ -233,7 +234,9 @@ def test_tc_gemm_output_formats_and_layouts(kind, case, tile):
     n = np.arange(N)[None, :]
     idx = (m % rm) + (m // rm) * sm + n * sn
     size = int(idx.max()) + 1 + 64
-    outs = [_tc_gemm_out("bf16x3", A, B, k, rm, sm, sn, size, tile, t) for t in (1, 0)]
+    # pair 1: clusters of two m-tiles share B (even m-tile count), pair 2: two
+    # n-tiles share A (even n-tile count, float32 out); otherwise one CTA per tile
+    outs = [_tc_gemm_out("bf16x3", A, B, k, rm, sm, sn, size, tile, t, pair) for t in (1, 0)]
     (t0, t1), (d0, d1) = outs
     assert np.array_equal(t0, d0) and (kind != "split" or np.array_equal(t1, d1)), (kind, case, tile)
     hi, lo = outs[0]
