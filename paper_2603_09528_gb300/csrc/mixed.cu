@@ -1930,6 +1930,7 @@ int enqueue_adaptive(tpt_plan_s* p, const MixedWork& w, const double* f, double*
     MX_CUDA(cudaGetLastError());
   }
   MX_CUDA(launch_output(p, w, phi, s));
+  if (!d_hdst) return TPT_OK;   // the caller gathers the scalars itself
   note_launch(1);
   scal_to_host_kernel<<<1, 32, 0, s>>>(w.scal, d_hdst);   // no copy engine: see pinned_slot_acquire
   return cudaGetLastError() == cudaSuccess ? TPT_OK : TPT_ERR_CUDA;
@@ -2293,6 +2294,15 @@ int mixed_solve(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStr
 }
 
 int mixed_enqueue(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStream_t s) {
+  if (p->rtol > 0.0) {   // every correction enqueued; those past convergence return at entry
+    const MixedWork w = carve(p, work);
+    const int corrections = 1 + p->max_refine;
+    switch (p->mixed.fmt) {
+      case kFmtSplit: return enqueue_adaptive<kFmtSplit>(p, w, f, phi, 0, corrections, true, nullptr, s);
+      case kFmtBF16: return enqueue_adaptive<kFmtBF16>(p, w, f, phi, 0, corrections, true, nullptr, s);
+      default: return enqueue_adaptive<kFmtF32>(p, w, f, phi, 0, corrections, true, nullptr, s);
+    }
+  }
   switch (p->mixed.fmt) {
     case kFmtSplit: return solve_fmt<kFmtSplit>(p, f, phi, work, s, nullptr, true);
     case kFmtBF16: return solve_fmt<kFmtBF16>(p, f, phi, work, s, nullptr, true);
@@ -2382,6 +2392,20 @@ int autotune_gemms(tpt_plan_s* p, void* work, cudaStream_t s) {
 }
 
 int mixed_info(const tpt_plan_s* p, const double* h, tpt_info* info) {
+  int flags[2] = {0, 0};
+  std::memcpy(flags, &h[8], sizeof(flags));
+  if (flags[1] > 0) {   // decided on the device (converge_kernel): its count and sums
+    const double rel = h[12] > 0.0 ? std::sqrt(h[11] / h[12]) : std::sqrt(h[11]);
+    if (info) {
+      std::memset(info, 0, sizeof(*info));
+      info->iters = flags[1];
+      info->rel_residual = rel;
+      info->compat_defect = p->singular ? h[7] / p->vol : 0.0;
+    }
+    if (flags[0] == 3) return TPT_ERR_TIMEOUT;
+    if (flags[0] == 2) return TPT_ERR_NONFINITE;
+    return flags[0] == 1 ? TPT_OK : TPT_ERR_NOT_CONVERGED;
+  }
   int errflag = 0;
   std::memcpy(&errflag, &h[15], sizeof(int));
   const double np = static_cast<double>(npts(p));

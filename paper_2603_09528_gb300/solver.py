@@ -411,16 +411,20 @@ class Batch:
         return [p.tiles() for p in self.plans]
 
     def calibrate(self, fs, phis, work: torch.Tensor, rtol: float = 1e-10, max_refine: int = 40,
-                  stream=None):
-        """Fix each instance's number of corrections for capture: one adaptive
-        solve to ``rtol`` per instance, then max_refine = corrections used - 1.
-        Returns the corrections per instance."""
+                  stream=None, spare: int = 1):
+        """Size each instance's corrections for capture: one adaptive solve to
+        ``rtol`` per instance, then room for the corrections it used plus
+        ``spare``.  In the captured batch the stopping test runs on the
+        device, so an instance stops as soon as it reaches rtol; a spare
+        correction only computes for a right-hand side that needs it (past
+        convergence its kernels return at entry, at the cost of their
+        launches).  Returns the corrections per instance."""
         used = []
         for p, f, phi in zip(self.plans, fs, phis):
             p.set_refinement(rtol, max_refine)
             _, info = p.solve(f, phi, work, stream=stream, raise_not_converged=False)
             used.append(int(info["iters"]))
-            p.set_refinement(rtol, max(0, used[-1] - 1))
+            p.set_refinement(rtol, min(max_refine, max(0, used[-1] - 1 + int(spare))))
         return used
 
     def solve(self, fs, phis, work: torch.Tensor, stream=None, want_info: bool = True,
