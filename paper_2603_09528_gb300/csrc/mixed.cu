@@ -241,8 +241,8 @@ __device__ __forceinline__ void copy_elem(const void* s0, const void* s1, int i,
   }
 }
 
-template <int FMT, int M, int TLT>
-__global__ void __launch_bounds__(kThomasThreads, 1)
+template <int FMT, int M, int TLT, int NT>
+__global__ void __launch_bounds__(NT, kThomasThreads / NT)
 thomas_tma_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ CUtensorMap map_o0,
                   const __grid_constant__ CUtensorMap map_o1, ThomasGeom geo, int nx, int ny, int nz, int ldy,
                   int ntiles, int* next_tile, void* t3_0, void* t3_1, const float* __restrict__ lamx,
@@ -251,7 +251,7 @@ thomas_tma_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_const
                   const int* skip) {
   if (skip && *skip) return;   // the refinement has stopped
   using O = T3Fmt<FMT>;
-  constexpr int NSEG = kThomasThreads / TLT;   // segment slots per line (16 or 32)
+  constexpr int NSEG = NT / TLT;   // segment slots per line (16 or 32)
   extern __shared__ __align__(128) uint8_t dsm_raw[];
   // 1024-byte aligned start, offset on the shared pointer itself so that every
   // access below stays a shared-memory (not generic) access
@@ -261,17 +261,17 @@ thomas_tma_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_const
   uint8_t* ot = in_base + static_cast<size_t>(geo.stages) * geo.in_bytes;
   void* o0 = ot;
   void* o1 = ot + (O::NPL == 2 ? geo.out_bytes / 2 : 0);
-  __shared__ float red[7 * kThomasThreads];
+  __shared__ float red[7 * NT];
   __shared__ __align__(8) uint64_t full[kThomasMaxStages];
   __shared__ int tile_of[kThomasMaxStages];   // tile loaded into each stage, -1: none left
   __shared__ int go;
   float* G0 = red;                       // [slot][TLT] g_0, u_0, v_0 of each segment
-  float* U0 = G0 + kThomasThreads;
-  float* V0 = U0 + kThomasThreads;
-  float* RA = V0 + kThomasThreads;       // reduced rows
-  float* RB = RA + kThomasThreads;
-  float* RC = RB + kThomasThreads;
-  float* RD = RC + kThomasThreads;       // right-hand side, then y
+  float* U0 = G0 + NT;
+  float* V0 = U0 + NT;
+  float* RA = V0 + NT;                   // reduced rows
+  float* RB = RA + NT;
+  float* RC = RB + NT;
+  float* RD = RC + NT;                   // right-hand side, then y
   const int tid = threadIdx.x;
   const int l = tid % TLT, s = tid / TLT;
   const int s0 = s * M;
@@ -1526,7 +1526,7 @@ void thomas_shape(int nz, int* tlt, int* m_out) {
 
 // Stage geometry and ring size of thomas_tma_kernel; false when the shared
 // memory budget cannot hold two input stages and the output tile.
-bool thomas_geom(int nz, int m, int tlt, int out_npl, int out_eb, ThomasGeom* g) {
+bool thomas_geom(int nz, int m, int tlt, int out_npl, int out_eb, ThomasGeom* g, int budget = kThomasSmemBudget) {
   g->nseg = (nz + m - 1) / m;
   const int r = g->nseg * m;
   g->nb = (r + 255) / 256;
@@ -1535,13 +1535,14 @@ bool thomas_geom(int nz, int m, int tlt, int out_npl, int out_eb, ThomasGeom* g)
   g->in_bytes = g->sr * tlt * 4;
   g->out_bytes = g->sr * tlt * out_eb * out_npl;
   g->coef_bytes = (g->sr * static_cast<int>(sizeof(RowCoef)) + 1023) & ~1023;
-  g->stages = (kThomasSmemBudget - 1024 - g->coef_bytes - g->out_bytes) / g->in_bytes;
+  g->stages = (budget - 1024 - g->coef_bytes - g->out_bytes) / g->in_bytes;
   if (g->stages > kThomasMaxStages) g->stages = kThomasMaxStages;
   return g->stages >= 2;
 }
 
-template <int FMT, int M, int TLT>
+template <int FMT, int M, int TLT, int NT = kThomasThreads>
 cudaError_t launch_thomas_m(const tpt_plan_s* p, const MixedWork& w, cudaStream_t s) {
+  constexpr int kPerSm = kThomasThreads / NT;   // CTAs resident on one SM
   using O = T3Fmt<FMT>;
   const MixedTables& m = p->mixed;
   const long long lines = static_cast<long long>(m.ldy) * p->n[0];
@@ -1550,7 +1551,7 @@ cudaError_t launch_thomas_m(const tpt_plan_s* p, const MixedWork& w, cudaStream_
   if (ntiles <= 0) return cudaSuccess;
   if (lines + TLT > 0x7fffffffLL) return cudaErrorInvalidValue;   // int line indices and TMA coordinates
   ThomasGeom geo;
-  if (!thomas_geom(nz, M, TLT, O::NPL, O::EB, &geo)) return cudaErrorInvalidConfiguration;
+  if (!thomas_geom(nz, M, TLT, O::NPL, O::EB, &geo, kThomasSmemBudget / kPerSm)) return cudaErrorInvalidConfiguration;
   CUtensorMap mi, mo0, mo1;
   if (!tc::make_plain_map(&mi, w.B[0], 4, lines, nz, lines * 4, TLT, geo.rb)) return cudaErrorInvalidValue;
   if (!tc::make_plain_map(&mo0, w.A[0], O::EB, lines, nz, lines * O::EB, TLT, geo.rb)) return cudaErrorInvalidValue;
@@ -1565,14 +1566,14 @@ cudaError_t launch_thomas_m(const tpt_plan_s* p, const MixedWork& w, cudaStream_
   if (e != cudaSuccess) return e;
   const size_t smem = 1024 + static_cast<size_t>(geo.coef_bytes) + static_cast<size_t>(geo.stages) * geo.in_bytes +
                       static_cast<size_t>(geo.out_bytes);
-  auto kern = thomas_tma_kernel<FMT, M, TLT>;
+  auto kern = thomas_tma_kernel<FMT, M, TLT, NT>;
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->dev);
-  const long long grid = ntiles < sms ? ntiles : sms;
+  const long long grid = ntiles < kPerSm * sms ? ntiles : kPerSm * sms;
   note_launch(1);
-  kern<<<static_cast<unsigned>(grid), kThomasThreads, smem, s>>>(
+  kern<<<static_cast<unsigned>(grid), NT, smem, s>>>(
       mi, mo0, mo1, geo, p->n[0], p->n[1], nz, m.ldy, static_cast<int>(ntiles), next_tile, w.A[0], w.A[1],
       m.lam_f[0], m.lam_f[1], m.zrows_f, m.zrows_f + nz, m.zrows_f + 2 * nz, static_cast<float>(p->alpha),
       static_cast<float>(p->beta), p->singular ? 1 : 0, reinterpret_cast<int*>(w.scal + 15), w.skip);
