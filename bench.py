@@ -754,9 +754,12 @@ def e2e_server(tpt, device, spec, f_pin, steps, warmup, phi_ref, barrier, slots=
     ref = phi_ref.cpu()
     last = ring[(steps - 1) % len(ring)]
     diff = float((last - ref).abs().max() / ref.abs().max())
+    t0s = res[0]["t_submit"]
     return {"seconds": seconds, "slots": slots, "requests": steps,
             "max_rel_residual": max(r["rel_residual"] for r in res),
-            "max_rel_diff_vs_device_solve": diff}
+            "max_rel_diff_vs_device_solve": diff,
+            "timeline_ms": {k: [round((r[key] - t0s) * 1e3, 2) for r in res]
+                            for k, key in (("planned", "t_planned"), ("admitted", "t_admit"), ("done", "t_done"))}}
 
 
 def dominant_kernel(plan, prec, n, f_dev, steps, stream):

@@ -14,6 +14,7 @@
 // retiring one request never stalls the others.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -279,9 +280,38 @@ int tpt_server_warm(tpt_server s, const tpt_desc* desc) {
   if (!s || !desc) return TPT_ERR_INVALID_ARG;
   if (s->cfg.cuda_device >= 0) cudaSetDevice(s->cfg.cuda_device);
   tpt_plan p = nullptr;
-  const int st = tpt::create_plan(desc, s->cfg.cuda_device, &s->cache, &p);
+  int st = tpt::create_plan(desc, s->cfg.cuda_device, &s->cache, &p);
+  size_t wb = 0;
+  if (st == TPT_OK && p && s->cfg.cuda_device >= 0) st = tpt_workspace_bytes(p, &wb);
   if (p) tpt_plan_destroy(p);   // the plan was never used: its tables can go at once
-  return st;
+  if (st != TPT_OK || s->cfg.cuda_device < 0) return st;
+  // grow the memory pool to hold `slots` requests of this shape (the
+  // buffers execute() takes), so that the first requests do not wait for the
+  // driver to map memory; the pool keeps what is freed
+  const size_t npts = static_cast<size_t>(desc->n[0]) * desc->n[1] * desc->n[2];
+  const size_t sz[3] = {npts * sizeof(double) + 256, npts * sizeof(double) + 256, wb + 256};
+  const size_t need = sz[0] + sz[1] + sz[2];
+  const int sets = static_cast<int>(std::min<size_t>(static_cast<size_t>(s->cfg.slots), s->cfg.memory_budget / need));
+  cudaStream_t ws = nullptr;
+  if (cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return TPT_OK;   // only a warm-up: requests will grow the pool themselves
+  }
+  std::vector<void*> bufs;
+  for (int k = 0; k < sets; ++k)
+    for (size_t b : sz) {
+      void* ptr = nullptr;
+      if (cudaMallocFromPoolAsync(&ptr, b, s->cache.pool(), ws) != cudaSuccess) {
+        cudaGetLastError();
+        break;
+      }
+      bufs.push_back(ptr);
+    }
+  for (void* b : bufs) cudaFreeAsync(b, ws);
+  cudaStreamSynchronize(ws);
+  cudaStreamDestroy(ws);
+  cudaGetLastError();
+  return TPT_OK;
 }
 
 int tpt_server_wait(tpt_server s, unsigned long long ticket, double timeout_s, tpt_result* result) {
