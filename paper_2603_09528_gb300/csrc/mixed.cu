@@ -1587,7 +1587,9 @@ cudaError_t launch_thomas(const tpt_plan_s* p, const MixedWork& w, cudaStream_t 
   const MixedTables& m = p->mixed;
   const int nz = p->n[2];
   const float* t2 = static_cast<const float*>(w.B[0]);
+  std::unique_lock<std::mutex> side_lock(const_cast<tpt_plan_s*>(p)->side_mu, std::defer_lock);
   if (p->singular) {   // fork: the float64 null line runs beside the partition kernel
+    side_lock.lock();
     cudaError_t e = cudaEventRecord(m.fork, s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(m.side, m.fork, 0);
     if (e != cudaSuccess) return e;

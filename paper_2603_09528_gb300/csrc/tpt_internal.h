@@ -6,6 +6,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <memory>
+#include <mutex>
 #include <vector>
 
 #include "../../include/tpt.h"
@@ -134,6 +135,10 @@ struct tpt_plan_s {
   double* h_scal = nullptr;                // pinned, mapped slot for the workspace scalars
   double* d_hscal = nullptr;               // its device address
   std::atomic<bool> graph_busy{false};
+  // The null line runs on the plan's second stream between a fork and a join
+  // event shared by all solves of the plan: solves enqueued from several host
+  // threads take turns for that sequence, so no solve waits on another's event.
+  std::mutex side_mu;
   bool singular = false;
   int null_i = 0, null_j = 0;     // mode indices of the null line when singular
   tpt::Dir1D dir[3];

@@ -344,3 +344,40 @@ def test_adaptive_solve_replayed_as_graph_and_continued_past_the_planned_correct
     assert i0["iters"] == 1
     _, i1 = plan0.solve(tpt.field_to_device(f1))
     assert i1["iters"] > 1 and i1["rel_residual"] <= 1e-10
+
+
+def test_concurrent_solves_on_one_plan_from_two_threads():
+    # two host threads solve on one plan with their own workspaces and
+    # streams: the shared null-line fork/join and the plan's graph are taken
+    # in turn, so every result equals the same solve made alone
+    import threading
+    n = (64, 48, 40)
+    dirs = _dirs(n, (1.5, 2.0, 2.5), [(1, 1)] * 3)
+    plan = tpt.Plan(n, [d.dxf for d in dirs], [d.dxc for d in dirs], [(1, 1)] * 3, xform=(tpt.GEMM, tpt.GEMM),
+                    alpha=0.0, beta=1.0, precision=PRECS["bf16x3"], rtol=1e-10, max_refine=8)
+    fs = [tpt.field_to_device(S.remove_weighted_mean(S.uniform_rhs(n, 60 + t), [d.dxf for d in dirs]))
+          for t in range(2)]
+    refs = [plan.solve(f)[0].cpu().numpy() for f in fs]
+    errors = []
+
+    def worker(t):
+        try:
+            stream = torch.cuda.Stream()
+            work = plan.new_workspace()
+            phi = plan.new_field()
+            for _ in range(6):
+                _, info = plan.solve(fs[t], phi, work, stream=stream)
+                stream.synchronize()
+                got = phi.cpu().numpy()
+                if not (np.abs(got - refs[t]).max() <= 1e-12 * np.abs(refs[t]).max() and
+                        info["rel_residual"] <= 1e-10):
+                    errors.append((t, float(np.abs(got - refs[t]).max()), info))
+        except Exception as e:   # noqa: BLE001 (reported below)
+            errors.append((t, repr(e)))
+
+    threads = [threading.Thread(target=worker, args=(t,)) for t in range(2)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    assert not errors, errors
