@@ -45,21 +45,27 @@ def _env_int(name, default):
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clocks and throttle reasons sampled every 20 ms from before
+    the warm-up (so that the sampler is running when the timed region starts)
+    to after the timed region; stop() keeps the samples taken inside the
+    timed window (its start and end marked with mark()), widened by one
+    sampling period, and counts the rest separately."""
+    QUERY = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_S = 0.02
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
         self.lines = []
         self._t = None
+        self.window = [None, None]
 
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(int(self.PERIOD_S * 1000))],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -71,7 +77,12 @@ class ClockSampler:
         for ln in self.proc.stdout:
             self.lines.append(ln.strip())
 
+    def mark(self, i):
+        import datetime
+        self.window[i] = datetime.datetime.now()
+
     def stop(self):
+        import datetime
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -80,24 +91,30 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self._t.join(timeout=2)
-        sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        t0, t1 = self.window
+        pad = datetime.timedelta(seconds=self.PERIOD_S)
+        inside, outside = [], 0
         for ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f")
+                row = (float(parts[2]), float(parts[3]), float(parts[4]) if parts[4] else float("nan"),
+                       {nm for nm, v in zip(names, parts[6:10]) if v.lower() == "active"})
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        if not sm:
+            if t0 is not None and t1 is not None and t0 - pad <= ts <= t1 + pad:
+                inside.append(row)
+            else:
+                outside += 1
+        if not inside:
             return None
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return {"sm_mhz": float(np.median([r[0] for r in inside])), "sm_max_mhz": float(max(r[1] for r in inside)),
+                "power_w": float(np.median([r[2] for r in inside])),
+                "reasons": sorted(set().union(*[r[3] for r in inside])), "samples": len(inside),
+                "period_ms": self.PERIOD_S * 1e3, "samples_outside_window": outside}
 
 
 # ------------------------------------------------------------------ inputs
@@ -260,6 +277,8 @@ def run_ours(args):
             tiles = plan.tiles()
         else:
             tiles = plan.autotune(work, stream=stream)   # transform GEMM column tiles per stage
+    clocks = ClockSampler(local)
+    clocks.start()
     # warm-up
     info = None
     for _ in range(args.warmup):
@@ -268,8 +287,7 @@ def run_ours(args):
     barrier()
     torch.cuda.synchronize()
 
-    clocks = ClockSampler(local)
-    clocks.start()
+    clocks.mark(0)
     l0 = _lib.kernel_launches()
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     evs[0].record(stream)
@@ -279,6 +297,7 @@ def run_ours(args):
         infos.append(inf)
         evs[k + 1].record(stream)
     torch.cuda.synchronize()
+    clocks.mark(1)
     l1 = _lib.kernel_launches()
     barrier()
     torch.cuda.synchronize()
