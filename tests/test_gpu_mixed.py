@@ -381,3 +381,31 @@ def test_concurrent_solves_on_one_plan_from_two_threads():
     for th in threads:
         th.join()
     assert not errors, errors
+
+
+def test_device_stopping_test_reports_misses_and_continues_after_a_graph_replay():
+    # a plan allowed one correction reports NOT_CONVERGED with its residual;
+    # a plan whose solve was captured as a graph for a zero right-hand side
+    # (one correction) replays that graph for a random one in the same
+    # buffer and continues with further corrections until rtol
+    n = (48, 40, 32)
+    bcs = [(2, 1), (1, 2), (2, 2)]            # walls: not singular
+    dirs = _dirs(n, (1.5, 2.0, 2.5), bcs)
+    kw = dict(xform=(tpt.GEMM, tpt.GEMM), alpha=0.0, beta=1.0, precision=PRECS["bf16x3"])
+    f = S.uniform_rhs(n, 71)
+    one = tpt.Plan(n, [d.dxf for d in dirs], [d.dxc for d in dirs], bcs, rtol=1e-10, max_refine=0, **kw)
+    _, info = one.solve(tpt.field_to_device(f), raise_not_converged=False)
+    assert info["iters"] == 1 and info["rel_residual"] > 1e-10 and info["status"] == L.TPT_ERR_NOT_CONVERGED
+
+    plan = tpt.Plan(n, [d.dxf for d in dirs], [d.dxc for d in dirs], bcs, rtol=1e-10, max_refine=8, **kw)
+    f_dev = tpt.field_to_device(np.zeros(n))
+    phi = plan.new_field()
+    work = plan.new_workspace()
+    easy = [plan.solve(f_dev, phi, work)[1]["iters"] for _ in range(4)]   # captured, then replayed
+    assert easy == [1, 1, 1, 1], easy
+    f_dev.copy_(tpt.field_to_device(f))
+    _, info = plan.solve(f_dev, phi, work)
+    ref, _ = O.solve_tensor(f, dirs, 0.0, 1.0)
+    got = tpt.field_to_host(phi, n)
+    assert info["status"] == L.TPT_OK and info["rel_residual"] <= 1e-10 and info["iters"] > 1, info
+    assert np.abs(got - ref).max() <= 1e-7 * np.abs(ref).max()
