@@ -645,12 +645,9 @@ struct Elem2;   // two consecutive elements of R in one store
 template <>
 struct Elem2<kFmtSplit> {
   static __device__ __forceinline__ void store(void* p0, void* p1, long long i, float a, float b) {
-    const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
-    __nv_bfloat162 h, l;
-    h.x = ha;
-    h.y = hb;
-    l.x = __float2bfloat16_rn(a - __bfloat162float(ha));
-    l.y = __float2bfloat16_rn(b - __bfloat162float(hb));
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
     *reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(p0) + i) = h;
     *reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(p1) + i) = l;
   }
@@ -975,6 +972,7 @@ residual_tma_kernel(const __grid_constant__ CUtensorMap tPH, const __grid_consta
   const long long rstep = static_cast<long long>(ldx) * ny;
   int s = 1, sn = 2;                                           // stages of planes k and k + 1
   uint32_t parn = 0;                                           // phase parity of stage sn
+#pragma unroll 2
   for (int k = k0; ok && k < k1; ++k) {
     const ZCoef z = zc[k - k0];
     if (!ptx::mbar_wait(ptx::smem_u32(&full[sn]), parn, err, ptx::kErrWaitFull)) break;
