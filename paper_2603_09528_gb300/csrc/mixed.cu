@@ -867,7 +867,7 @@ residual_df2_kernel(int nx, int ny, int nz, int ldx, int kseg, const float* __re
 // the wrapped neighbour directly.  Each consumer warp takes one row of the
 // tile, two points per lane, and applies residual_pair, so the results equal
 // residual_df2_kernel's.
-constexpr int kResTX = 64, kResTY = 8, kResStages = 5, kResKseg = 64;
+constexpr int kResTX = 64, kResTY = 8, kResStages = 6, kResKseg = 64;
 constexpr int kResPW = kResTX + 8;                         // phi row: 4 halo columns each side
 constexpr int kResPBytes = ((kResPW * (kResTY + 2) * 4 + 127) / 128) * 128;
 constexpr int kResFBytes = kResTX * kResTY * 4;
