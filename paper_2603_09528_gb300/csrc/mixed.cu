@@ -1585,7 +1585,7 @@ cudaError_t launch_thomas(const tpt_plan_s* p, const MixedWork& w, cudaStream_t 
   const MixedTables& m = p->mixed;
   const int nz = p->n[2];
   const float* t2 = static_cast<const float*>(w.B[0]);
-  std::unique_lock<std::mutex> side_lock(const_cast<tpt_plan_s*>(p)->side_mu, std::defer_lock);
+  std::unique_lock<std::recursive_mutex> side_lock(const_cast<tpt_plan_s*>(p)->side_mu, std::defer_lock);
   if (p->singular) {   // fork: the float64 null line runs beside the partition kernel
     side_lock.lock();
     cudaError_t e = cudaEventRecord(m.fork, s);
@@ -1879,6 +1879,9 @@ int capture_adaptive(tpt_plan_s* p, const MixedWork& w, const double* f, double*
     p->solve_exec = nullptr;
   }
   if (!p->cap_stream) MX_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+  // the plan's second stream belongs to the capture until it ends: other
+  // threads' solves on this plan wait to use it (see tpt_plan_s::side_mu)
+  std::lock_guard<std::recursive_mutex> side_guard(p->side_mu);
   const unsigned long long before = launch_count();
   MX_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeRelaxed));
   const int st = enqueue_adaptive<FMT>(p, w, f, phi, 0, planned, true, p->d_hscal, p->cap_stream);

@@ -137,8 +137,10 @@ struct tpt_plan_s {
   std::atomic<bool> graph_busy{false};
   // The null line runs on the plan's second stream between a fork and a join
   // event shared by all solves of the plan: solves enqueued from several host
-  // threads take turns for that sequence, so no solve waits on another's event.
-  std::mutex side_mu;
+  // threads take turns for that sequence, so no solve waits on another's
+  // event; a graph capture holds it throughout, since the second stream is
+  // part of the capture until it ends.
+  std::recursive_mutex side_mu;
   bool singular = false;
   int null_i = 0, null_j = 0;     // mode indices of the null line when singular
   tpt::Dir1D dir[3];
