@@ -449,9 +449,10 @@ int tpt_server_submit(tpt_server s, const tpt_desc* desc, const double* f_host, 
 /* Build the eigenbases (and their device tables) of desc's x and y
  * directions in the server's cache now, so that later requests with those
  * directions find them: a deployment warms the cache with its mesh library
- * before traffic arrives.  Also grows the server's device memory pool to
- * hold `slots` requests of desc's shape (as far as the memory budget
- * allows), so the first ones do not wait for the driver to map memory.
+ * before traffic arrives.  Also grows the server's pool of request buffers
+ * (fields and workspaces; plan tables come from a separate pool) to hold
+ * `slots` requests of desc's shape (as far as the memory budget allows), so
+ * the first ones do not wait for the driver to map memory.
  * Synchronous; safe beside running requests.                               */
 int tpt_server_warm(tpt_server s, const tpt_desc* desc);
 

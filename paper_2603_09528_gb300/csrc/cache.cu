@@ -203,18 +203,20 @@ int BasisCache::init() {
   props.allocType = cudaMemAllocationTypePinned;
   props.location.type = cudaMemLocationTypeDevice;
   props.location.id = dev_;
-  int st = st_of(cudaMemPoolCreate(&pool_, &props));
-  if (st != TPT_OK) return st;
-  uint64_t keep = ~0ULL;   // keep freed memory in the pool: no release to the driver
-  st = st_of(cudaMemPoolSetAttribute(pool_, cudaMemPoolAttrReleaseThreshold, &keep));
-  if (st != TPT_OK) return st;
-  // an allocation on one stream must not reuse a block freed on another
-  // stream by waiting for that stream (requests on different slots would
-  // then run one after another); it reuses blocks whose free has completed
-  // and grows the pool otherwise
-  int no = 0;
-  st = st_of(cudaMemPoolSetAttribute(pool_, cudaMemPoolReuseAllowInternalDependencies, &no));
-  if (st != TPT_OK) return st;
+  for (cudaMemPool_t* pl : {&pool_, &buf_pool_}) {
+    int st = st_of(cudaMemPoolCreate(pl, &props));
+    if (st != TPT_OK) return st;
+    uint64_t keep = ~0ULL;   // keep freed memory in the pool: no release to the driver
+    st = st_of(cudaMemPoolSetAttribute(*pl, cudaMemPoolAttrReleaseThreshold, &keep));
+    if (st != TPT_OK) return st;
+    // an allocation on one stream must not reuse a block freed on another
+    // stream by waiting for that stream (requests on different slots would
+    // then run one after another); it reuses blocks whose free has completed
+    // and grows the pool otherwise
+    int no = 0;
+    st = st_of(cudaMemPoolSetAttribute(*pl, cudaMemPoolReuseAllowInternalDependencies, &no));
+    if (st != TPT_OK) return st;
+  }
   return st_of(cudaStreamCreateWithFlags(&stream_, cudaStreamNonBlocking));
 }
 
@@ -230,6 +232,7 @@ BasisCache::~BasisCache() {
       cudaStreamDestroy(stream_);
     }
     if (pool_) cudaMemPoolDestroy(pool_);
+    if (buf_pool_) cudaMemPoolDestroy(buf_pool_);
     cudaGetLastError();
     if (prev >= 0) cudaSetDevice(prev);
   }

@@ -42,6 +42,10 @@ class BasisCache {
   int init();
   int device() const { return dev_; }
   cudaMemPool_t pool() const { return pool_; }
+  // Pool of the request buffers (fields and workspaces): kept apart from the
+  // tables so that a small table never splits a freed field-sized block and
+  // same-shape requests reuse whole blocks.
+  cudaMemPool_t buffer_pool() const { return buf_pool_; }
   cudaStream_t stream() const { return stream_; }
   // The entry of direction d with transform kind xform; computed on a miss.
   std::shared_ptr<DirEntry> get(const Dir1D& d, int xform, int* status);
@@ -54,6 +58,7 @@ class BasisCache {
   int dev_;
   size_t budget_;
   cudaMemPool_t pool_ = nullptr;
+  cudaMemPool_t buf_pool_ = nullptr;
   cudaStream_t stream_ = nullptr;
   std::mutex mu_;
   std::unordered_multimap<size_t, std::shared_ptr<DirEntry>> map_;

@@ -9,7 +9,8 @@
 // Every slot owns a CUDA stream, so the solves of admitted requests overlap on
 // the device; a request that arrives while others run is admitted as soon as
 // a slot and enough of the budget are free.  Request buffers are
-// stream-ordered allocations from the cache's memory pool and plans are
+// stream-ordered allocations from a memory pool of their own (plan tables
+// come from another, so small tables never split the big blocks) and plans are
 // created and destroyed without synchronising the device, so admitting or
 // retiring one request never stalls the others.
 #include <cuda_runtime.h>
@@ -140,7 +141,7 @@ struct tpt_server_s {
     const size_t sz[3] = {bytes + 256, bytes + 256, r->work_bytes + 256};
     int st = TPT_OK;
     for (int i = 0; i < 3 && st == TPT_OK; ++i)
-      st = cuda_st(cudaMallocFromPoolAsync(&buf[i], sz[i], cache.pool(), s));
+      st = cuda_st(cudaMallocFromPoolAsync(&buf[i], sz[i], cache.buffer_pool(), s));
     auto aligned = [](void* p) {
       return reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(p) + 255) & ~static_cast<uintptr_t>(255));
     };
@@ -301,7 +302,7 @@ int tpt_server_warm(tpt_server s, const tpt_desc* desc) {
   for (int k = 0; k < sets; ++k)
     for (size_t b : sz) {
       void* ptr = nullptr;
-      if (cudaMallocFromPoolAsync(&ptr, b, s->cache.pool(), ws) != cudaSuccess) {
+      if (cudaMallocFromPoolAsync(&ptr, b, s->cache.buffer_pool(), ws) != cudaSuccess) {
         cudaGetLastError();
         break;
       }
