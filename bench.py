@@ -199,16 +199,18 @@ def run_reference(args):
 PRECISIONS = {"fp64": 0, "mixed_bf16": 1, "mixed_bf16x3": 2, "mixed_tf32": 3}
 
 # dram__bytes_read.sum + dram__bytes_write.sum per point of each stage's kernel, from one
-# ncu --set full capture at 384^3 (summarised under profiles/); traffic scales with points.
-# An entry must be removed when its kernel changes.  The x-inverse GEMM is left out: the
-# captured launch was a first correction, which does not read phi, so its bytes differ
-# from the average launch.
+# ncu capture at 384^3 (second correction of a solve; summarised under profiles/);
+# traffic scales with points.  An entry must be removed when its kernel changes.  The
+# x-inverse GEMM of a solve's first correction writes phi without reading it, so it has
+# its own entry ("x_inverse_first").
 MEASURED_TRAFFIC_PER_POINT = {
-    ("residual", "mixed_bf16x3"): (921.18272e6 + 212.572416e6) / 384 ** 3,
-    ("thomas", "mixed_bf16x3"): (226.610688e6 + 178.848768e6) / 384 ** 3,
-    ("x_forward", "mixed_bf16x3"): (227.2256e6 + 179.54304e6) / 384 ** 3,
-    ("y_forward", "mixed_bf16x3"): (227.148032e6 + 176.46592e6) / 384 ** 3,
-    ("y_inverse", "mixed_bf16x3"): (227.151104e6 + 180.143104e6) / 384 ** 3,
+    ("residual", "mixed_bf16x3"): (919.794176e6 + 208.527616e6) / 384 ** 3,
+    ("thomas", "mixed_bf16x3"): (226.578432e6 + 175.845888e6) / 384 ** 3,
+    ("x_forward", "mixed_bf16x3"): (227.178240e6 + 177.789440e6) / 384 ** 3,
+    ("y_forward", "mixed_bf16x3"): (227.145472e6 + 173.730048e6) / 384 ** 3,
+    ("y_inverse", "mixed_bf16x3"): (227.169024e6 + 178.160384e6) / 384 ** 3,
+    ("x_inverse", "mixed_bf16x3"): (681.375488e6 + 389.430528e6) / 384 ** 3,
+    ("x_inverse_first", "mixed_bf16x3"): (227.432448e6 + 387.996672e6) / 384 ** 3,
 }
 DTYPE = {"fp64": "f64", "mixed_bf16": "bf16/f32/f64", "mixed_bf16x3": "bf16x3/f32/f64",
          "mixed_tf32": "tf32/f32/f64"}
@@ -718,7 +720,10 @@ def stage_rooflines(ms, iters, n, prec):
         if nm in ("x_forward", "y_forward", "y_inverse", "x_inverse"):
             na = n[0] if nm.startswith("x") else n[1]
             flops = 2.0 * na * npts * prods
-            byts = npts * (eb + (16 if nm == "x_inverse" else eb))
+            # the x inverse updates the float-pair phi: read and write (16 B/pt), except
+            # in a solve's first correction, which only writes it (8 B/pt)
+            first = 1.0 / max(iters, 1)
+            byts = npts * (eb + (16.0 - 8.0 * first if nm == "x_inverse" else eb))
             t_tensor = flops / (tflops * 1e12)
             t_hbm = byts / (hbm * 1e9)
             if t_tensor >= t_hbm:
@@ -734,9 +739,16 @@ def stage_rooflines(ms, iters, n, prec):
                   "bytes_per_launch": byts, "traffic": None})
         d["frac"] = d["achieved"] / d["peak"]
         out.append(d)
+    fmt = {1: "mixed_bf16", 2: "mixed_bf16x3", 3: "mixed_tf32"}[prec]
     for d in out:
-        key = (d["kernel"], {1: "mixed_bf16", 2: "mixed_bf16x3", 3: "mixed_tf32"}[prec])
-        if key in MEASURED_TRAFFIC_PER_POINT:
+        key = (d["kernel"], fmt)
+        if d["kernel"] == "x_inverse":   # average launch: one first correction per solve
+            k1 = ("x_inverse_first", fmt)
+            if key in MEASURED_TRAFFIC_PER_POINT and k1 in MEASURED_TRAFFIC_PER_POINT:
+                first = 1.0 / max(iters, 1)
+                d["traffic"] = npts * (first * MEASURED_TRAFFIC_PER_POINT[k1] +
+                                       (1.0 - first) * MEASURED_TRAFFIC_PER_POINT[key])
+        elif key in MEASURED_TRAFFIC_PER_POINT:
             d["traffic"] = MEASURED_TRAFFIC_PER_POINT[key] * npts
     return {"per_stage": out, "iters": iters, "peak_source": "MEASURED_PEAKS.json (burst)"}
 
