@@ -405,6 +405,10 @@ def run_ours(args):
     if not args.no_projection and prec != 0:
         projection = projection_leg(tpt, plan, n, stream, args.steps)
 
+    fft = None
+    if not args.no_fft:
+        fft = fft_leg(tpt, n, stream, args.steps)
+
     batch = None
     if not args.no_batch:
         batch = {"mixed": batch_leg(tpt, local, stream, prec if prec != 0 else 2, args.steps)}
@@ -446,6 +450,7 @@ def run_ours(args):
             "stages": stages,
             "fp64": fp64,
             "projection": projection,
+            "fft": fft,
             "batch": batch,
             "serving": serving,
             "gpu_launches": l1 - l0,
@@ -647,6 +652,65 @@ def serving_leg(tpt, device, prec, count, warmup, rate_hz=200.0, slots=4, stretc
             "peak_inflight": int(st["peak_inflight"]), "peak_device_bytes": int(st["peak_bytes"])}
 
 
+def fft_leg(tpt, n, stream, steps):
+    """float64 path with Fourier-based x and y transforms (Sec. 2.2.1, uniform
+    grids): uniform x and y (Neumann walls: DCT-II / DCT-III; periodic: real
+    DFT), z stretched 2.0 and solved by Thomas, Helmholtz (1, -5e-4).  Each
+    transform is timed alone with CUDA events (seeded uniform[0, 1) input),
+    then the whole solve.  Algorithmic work per point and transform: 16 bytes
+    (one float64 read, one write) and 5 log2(N) + 6 float64 flops (radix-2
+    complex FFT of length N plus the pre/post rotation)."""
+    import torch
+    out = {}
+    npts = n[0] * n[1] * n[2]
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(11)
+    for kind, bc in (("neumann_dct", (1, 1)), ("periodic_dft", (0, 0))):
+        if any(n[a] & (n[a] - 1) for a in (0, 1)):
+            return None   # power-of-two x and y only
+        grids = [tpt.grid_tanh(n[a], 1.0, 0.0 if a < 2 else 2.0) for a in range(3)]
+        plan = tpt.Plan(n, [g[0] for g in grids], [g[1] for g in grids], [bc, bc, (1, 1)],
+                        xform=(tpt.FFT, tpt.FFT), alpha=1.0, beta=-5e-4, precision=0, max_refine=1)
+        f = torch.rand(npts, generator=gen, dtype=torch.float64, device="cuda")
+        y = plan.new_field()
+        rec = {}
+        for d in (0, 1):
+            N = n[d]
+            flops = npts * (5.0 * np.log2(N) + 6.0)
+            for inv in (False, True):
+                for _ in range(2):
+                    plan.transform(f, d, inv, out=y, stream=stream)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                reps = max(3, steps)
+                e0.record(stream)
+                for _ in range(reps):
+                    plan.transform(f, d, inv, out=y, stream=stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / reps
+                rec["%s_%s" % ("xy"[d], "inverse" if inv else "forward")] = {
+                    "ms": ms, "gb_per_s": 16.0 * npts / (ms / 1e3) / 1e9,
+                    "fp64_gflop_per_s": flops / (ms / 1e3) / 1e9}
+        phi, work = plan.new_field(), plan.new_workspace()
+        plan.solve(f, phi, work, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = max(2, min(steps, 3))
+        e0.record(stream)
+        for _ in range(reps):
+            _, info = plan.solve(f, phi, work, stream=stream, want_info=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rec["solve"] = {"ms": e0.elapsed_time(e1) / reps, "iters": info["iters"],
+                        "rel_residual": info["rel_residual"]}
+        out[kind] = rec
+        del plan, f, y, phi, work
+        torch.cuda.empty_cache()
+    out["workload"] = "helmholtz_%dx%dx%d_uniform_xy_tanh2.0_z_fp64_fft" % tuple(n)
+    return out
+
+
 def projection_leg(tpt, plan, n, stream, steps):
     """Pressure projection (Sec. 2.1) on the benchmark grid: D u* / g, the
     refined Poisson solve, u -= g G Phi, with seeded uniform[-1, 1] face
@@ -840,6 +904,7 @@ def main():
     ap.add_argument("--max-refine", type=int, default=None)
     ap.add_argument("--cpu-slabs", type=int, default=128)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fft", action="store_true", help="skip the float64 FFT/DCT-transform leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched uneven-instances leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the open-loop serving leg")
