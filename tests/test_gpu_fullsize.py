@@ -1,0 +1,69 @@
+"""The 512^3 stretched Poisson problem (x, y, z stretched 1.5 / 2.0 / 2.5,
+Neumann walls) at its full size, solved in the launch configuration the
+benchmark times: split-bf16 transforms with autotuned tiles, refinement to a
+relative residual of 1e-10 decided on the device, repeated solves of one right
+side replayed as a CUDA graph.  The oracle cannot solve this size, so every
+check is a property that holds at any size, computed by oracle code on the
+host: the float64 residual of the returned phi, the zero volume-weighted mean
+of the canonical gauge, and the distance to the float64 path (which matches the
+oracle to 1e-12 at the sizes the oracle solves)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import seeded_inputs as S
+from _tpt import load
+
+pytestmark = pytest.mark.gpu
+tpt, L = load()
+
+N = (512, 512, 512)
+STRETCH = (1.5, 2.0, 2.5)
+BCS = [(1, 1)] * 3
+
+
+def _rel_residual(f, phi, dirs):
+    r = O.residual(f, phi, dirs, 0.0, 1.0)
+    return float(np.sqrt(np.sum(r * r) / np.sum(f * f)))
+
+
+def test_512cube_split_bf16_in_the_benchmark_configuration():
+    dirs = O.make_dirs(N, STRETCH, BCS)
+    f = S.remove_weighted_mean(S.uniform_rhs(N, 4), [d.dxf for d in dirs])
+    f_dev = tpt.field_to_device(f)
+    plan = tpt.Plan(N, [d.dxf for d in dirs], [d.dxc for d in dirs], BCS, xform=(tpt.GEMM, tpt.GEMM),
+                    alpha=0.0, beta=1.0, precision=L.TPT_PREC_MIXED_BF16X3, rtol=1e-10, max_refine=8)
+    phi, work = plan.new_field(), plan.new_workspace()
+    stream = torch.cuda.current_stream()
+    plan.autotune(work, stream=stream)
+    outs = []
+    for _ in range(3):   # eager, captured, replayed
+        _, info = plan.solve(f_dev, phi, work, stream=stream, want_info=True)
+        assert info["rel_residual"] <= 1e-10, info
+        assert info["iters"] <= 4, info
+        outs.append(phi.clone())
+    torch.cuda.synchronize()
+    ref = outs[0].abs().max().item()
+    for o in outs[1:]:
+        # the gauge and norm sums use float64 atomics, whose order varies
+        assert (o - outs[0]).abs().max().item() <= 1e-12 * ref
+    got = tpt.field_to_host(outs[-1], N)
+    del outs, work
+    torch.cuda.empty_cache()
+
+    rel = _rel_residual(f, got, dirs)
+    assert rel <= 2e-10, rel
+    assert abs(O.weighted_mean(got, dirs)) <= 1e-12 * np.abs(got).max()
+
+    plan64 = tpt.Plan(N, [d.dxf for d in dirs], [d.dxc for d in dirs], BCS, xform=(tpt.GEMM, tpt.GEMM),
+                      alpha=0.0, beta=1.0, precision=L.TPT_PREC_FP64, max_refine=1)
+    phi64, _ = plan64.solve(f_dev)
+    ref64 = tpt.field_to_host(phi64, N)
+    del phi64, plan64, f_dev
+    torch.cuda.empty_cache()
+    assert _rel_residual(f, ref64, dirs) <= 1e-12
+    err = np.abs(got - ref64).max() / np.abs(ref64).max()
+    print("512^3 split bf16: iters", info["iters"], "rel residual (gpu)", info["rel_residual"],
+          "(oracle stencil)", rel, "max rel diff vs float64 path", err)
+    assert err <= 1e-9, err
