@@ -67,3 +67,54 @@ def test_512cube_split_bf16_in_the_benchmark_configuration():
     print("512^3 split bf16: iters", info["iters"], "rel residual (gpu)", info["rel_residual"],
           "(oracle stencil)", rel, "max rel diff vs float64 path", err)
     assert err <= 1e-9, err
+
+
+def test_batch_of_96_uneven_instances_in_the_benchmark_configuration():
+    # the batched workload at its full size (96 instances, 4.65e8 points) as the
+    # benchmark runs it: corrections calibrated without spare, autotuned tiles,
+    # every instance in one captured graph; each instance's device-reported
+    # residual, and for a sample (the first instance of each size and every
+    # twelfth) the float64 residual by the oracle's stencil and the gauge, on
+    # seeded right-hand sides
+    bcs = [(1, 1)] * 3
+    inst = S.batch_instances(96, 5)
+    first = {}
+    for t, it in enumerate(inst):
+        first.setdefault(it["n"], t)
+    sample = set(first.values()) | set(range(0, 96, 12))
+    specs, fs, host = [], [], {}
+    gen = torch.Generator(device="cuda")
+    for t, it in enumerate(inst):
+        n = it["n"]
+        dirs = O.make_dirs(n, it["stretch"], bcs)
+        specs.append(dict(n=n, dxf=[d.dxf for d in dirs], dxc=[d.dxc for d in dirs], bc=bcs,
+                          xform=(tpt.GEMM, tpt.GEMM), alpha=it["alpha"], beta=it["beta"],
+                          precision=L.TPT_PREC_MIXED_BF16X3, rtol=1e-10, max_refine=8))
+        if t in sample:
+            f = S.uniform_rhs(n, it["seed"])
+            if it["alpha"] == 0.0:
+                f = S.remove_weighted_mean(f, [d.dxf for d in dirs])
+            host[t] = (f, dirs)
+            fs.append(tpt.field_to_device(f))
+        else:
+            gen.manual_seed(it["seed"])
+            fs.append(torch.rand(n[0] * n[1] * n[2], generator=gen, dtype=torch.float64, device="cuda") * 2 - 1)
+    b = tpt.Batch(specs, nstreams=8)
+    phis = [torch.empty_like(f) for f in fs]
+    work = b.new_workspace()
+    stream = torch.cuda.current_stream()
+    b.calibrate(fs, phis, work, rtol=1e-10, spare=0)
+    b.autotune(work, stream)
+    b.solve(fs, phis, work, stream=stream)            # eager run and capture
+    infos = b.solve(fs, phis, work, stream=stream)    # graph replay
+    assert len(infos) == 96
+    for t, inf in enumerate(infos):
+        assert inf["status"] == 0 and inf["rel_residual"] <= 1e-10, (t, inf)
+    for t in sorted(sample):
+        f, dirs = host[t]
+        got = tpt.field_to_host(phis[t], inst[t]["n"])
+        r = O.residual(f, got, dirs, inst[t]["alpha"], inst[t]["beta"])
+        rel = float(np.sqrt(np.sum(r * r) / np.sum(f * f)))
+        assert rel <= 2e-10, (t, rel, infos[t])
+        if O.is_singular(dirs, inst[t]["alpha"]):
+            assert abs(O.weighted_mean(got, dirs)) <= 1e-12 * np.abs(got).max()
