@@ -124,6 +124,12 @@ def workload(size):
     return n, STRETCH
 
 
+def workload_name(size):
+    if size == 512:
+        return "poisson_512cube_tanh1.5-2.0-2.5_neumann_GG_thomas"
+    return "poisson_%dcube_tanh1.5-2.0-2.5_neumann" % size
+
+
 def rhs_host(n, grids):
     import seeded_inputs as S
     f = S.uniform_rhs(n, SEED)
@@ -176,14 +182,14 @@ def run_reference(args):
     s_per_solve = float(np.mean(times))
     val = 1.0 / s_per_solve
     sample = ("oracle (numpy float64) correction pass + residual on a %dx%dx%d slab of the "
-              "512^3 stretched Neumann grid, scaled by points to one refined solve "
-              "(2 passes + 2 residuals)" % (n[0], n[1], nslab))
+              "%d^3 stretched Neumann grid, scaled by points to one refined solve "
+              "(2 passes + 2 residuals)" % (n[0], n[1], nslab, n[2]))
     out = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": "solves/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": s_per_solve * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "poisson_512cube_tanh1.5-2.0-2.5_neumann_GG_thomas", "size": list(n),
+        "config": {"workload": workload_name(args.size), "size": list(n),
                    "sample": "z-slab of %d" % nslab},
         "gpts_per_s": val * n[0] * n[1] * n[2] / 1e9,
         "cpu_baseline": {"value": val, "unit": "solves/s", "cores": _threads(), "kind": "oracle",
@@ -437,8 +443,7 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": DTYPE[args.precision], "data": "synthetic",
-            "config": {"workload": "poisson_512cube_tanh1.5-2.0-2.5_neumann_GG_thomas"
-                       if args.size == 512 else "poisson_%dcube_tanh1.5-2.0-2.5_neumann" % args.size,
+            "config": {"workload": workload_name(args.size),
                        "size": list(n), "stretch": list(stretch), "precision": args.precision,
                        "rtol": rtol, "max_refine": refine, "parallelism": "replicas%d" % world,
                        "gemm_tiles": tiles,
