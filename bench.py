@@ -8,12 +8,14 @@ uniform[-1, 1] right-hand side with its volume-weighted mean removed.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--precision fp64|mixed_bf16x3|...] [--size 512]
 
-Prints one JSON line (rank 0).  With N > 1 (torchrun, one rank per GPU) every
-rank solves its own instances with no collective on the data path
-(independent replicas, weak scaling); the timed region is bracketed by a
-barrier and a device synchronisation, and the time is the maximum over ranks.
-``--impl reference`` times the CPU oracle (the reference arm of this
-project) on the host cores on a bounded sample of the same workload.
+Prints one JSON line.  The solver is a one-GPU program: its transform GEMMs
+may pair two CTAs that share an operand tile by TMA multicast within this
+GPU's own memory, and the path has no exchange step to shard, so ``--gpus``
+other than 1 (or a launch under torchrun with WORLD_SIZE > 1) is refused
+with a message and exit status 2.  The timed region is bracketed by a device
+synchronisation on both sides.  ``--impl reference`` times the CPU oracle
+(the reference arm of this project) on the host cores on a bounded sample of
+the same workload; under torchrun only rank 0 runs it and the others exit 0.
 """
 from __future__ import annotations
 
@@ -222,23 +224,14 @@ DTYPE = {"fp64": "f64", "mixed_bf16": "bf16/f32/f64", "mixed_bf16x3": "bf16x3/f3
          "mixed_tf32": "tf32/f32/f64"}
 
 
-def max_over_ranks(x: float, world: int, device: str) -> float:
-    """The maximum of x over the ranks of the process group (x itself on one
-    rank): the job's time is its slowest rank's."""
-    if world <= 1:
-        return float(x)
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
-
-
-def job_rate(units_per_rank: int, world: int, t_max_s: float) -> float:
-    """Whole-job throughput: the units every rank processed (replicas: each rank
-    solves its own instances, no collective on the data path) over the slowest
-    rank's time."""
-    return units_per_rank * world / t_max_s
+def one_gpu_only(args) -> str | None:
+    """Why this run is refused, or None: the solver runs on one GPU only."""
+    world = _env_int("WORLD_SIZE", 1)
+    if args.gpus != 1 or world != 1:
+        return ("bench.py runs on one GPU only (got --gpus %d, WORLD_SIZE %d): the solve has no "
+                "exchange step to shard, and its paired-CTA transform GEMMs share operand tiles by "
+                "TMA multicast, which is kept to one-GPU runs" % (args.gpus, world))
+    return None
 
 
 def runs_reference_leg(rank: int) -> bool:
@@ -247,13 +240,14 @@ def runs_reference_leg(rank: int) -> bool:
 
 
 def run_ours(args):
+    why = one_gpu_only(args)
+    if why:
+        print(why, file=sys.stderr, flush=True)
+        return 2
     import torch
-    import torch.distributed as dist
 
-    rank, world, local = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
+    local = 0
     torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     from paper_2603_09528_gb300 import build as _build
     _build.build()
@@ -275,10 +269,6 @@ def run_ours(args):
     work = plan.new_workspace()
     stream = torch.cuda.current_stream()
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
     tiles = None
     if prec != 0:
         if args.no_autotune:   # default tiles (for profiling runs: no tuning launches)
@@ -291,8 +281,6 @@ def run_ours(args):
     info = None
     for _ in range(args.warmup):
         _, info = plan.solve(f_dev, phi, work, stream=stream, want_info=True)
-    torch.cuda.synchronize()
-    barrier()
     torch.cuda.synchronize()
 
     clocks.mark(0)
@@ -307,14 +295,10 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks.mark(1)
     l1 = _lib.kernel_launches()
-    barrier()
-    torch.cuda.synchronize()
     clk = clocks.stop()
     per = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
     total_ms = evs[0].elapsed_time(evs[-1])
-    t_max = max_over_ranks(total_ms, world, "cuda")
-    solves = world * args.steps
-    value = job_rate(args.steps, world, t_max / 1e3)
+    value = args.steps / (total_ms / 1e3)
     npts = n[0] * n[1] * n[2]
     stages = None
     if prec != 0:
@@ -343,22 +327,21 @@ def run_ours(args):
         f2 = plan.new_field()
         plan.solve_host(f_pin, phi_pin, f2, phi, work, stream=stream)
         torch.cuda.synchronize()
-        barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             plan.solve_host(f_pin, phi_pin, f2, phi, work, stream=stream)
         torch.cuda.synchronize()
-        dt = max_over_ranks(time.perf_counter() - t0, world, "cuda")
-        one_at_a_time = {"value": job_rate(args.steps, world, dt), "api": "tpt_solve_host, one call after another"}
+        dt = time.perf_counter() - t0
+        one_at_a_time = {"value": args.steps / dt, "api": "tpt_solve_host, one call after another"}
         spec = dict(n=n, dxf=[g[0] for g in grids], dxc=[g[1] for g in grids], bc=[(1, 1)] * 3,
                     xform=(tpt.GEMM, tpt.GEMM), alpha=0.0, beta=1.0, precision=prec, rtol=rtol,
                     max_refine=refine)
         # a stream of requests long enough that filling and draining the
         # copy/solve pipeline does not dominate the rate
         nreq = max(args.steps, 20)
-        srv = e2e_server(tpt, local, spec, f_pin, nreq, args.warmup, phi, barrier)
-        dt_srv = max_over_ranks(srv.pop("seconds"), world, "cuda")
-        e2e = {"value": job_rate(nreq, world, dt_srv), "unit": "solves/s", "h2d_bytes_per_step": npts * 8,
+        srv = e2e_server(tpt, local, spec, f_pin, nreq, args.warmup, phi)
+        dt_srv = srv.pop("seconds")
+        e2e = {"value": nreq / dt_srv, "unit": "solves/s", "h2d_bytes_per_step": npts * 8,
                "d2h_bytes_per_step": npts * 8,
                "api": "tpt_server_submit / tpt_server_wait: consecutive solves from pinned host buffers, "
                       "each request's host-to-device copy, solve and device-to-host copy overlapping "
@@ -384,7 +367,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         ms64 = a.elapsed_time(b) / reps
         diff = (phi - phi64).abs().max().item() / phi64.abs().max().item()
-        fp64 = {"solves_per_s": world * 1e3 / ms64, "ms_per_solve": ms64, "steps": reps,
+        fp64 = {"solves_per_s": 1e3 / ms64, "ms_per_solve": ms64, "steps": reps,
                 "rel_residual": i64["rel_residual"], "mixed_vs_fp64_max_rel_diff": diff}
         # the same tensor-core correction solves refined to float64 accuracy
         plan13 = tpt.Plan(n, [g[0] for g in grids], [g[1] for g in grids], [(1, 1)] * 3,
@@ -400,7 +383,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         ms13 = a.elapsed_time(b) / args.steps
         fp64["mixed_refined_to_1e-13"] = {
-            "solves_per_s": world * 1e3 / ms13, "ms_per_solve": ms13, "iters": i13["iters"],
+            "solves_per_s": 1e3 / ms13, "ms_per_solve": ms13, "iters": i13["iters"],
             "rel_residual": i13["rel_residual"],
             "max_rel_diff_vs_fp64": (phi13 - phi64).abs().max().item() / phi64.abs().max().item()}
         del plan13, phi13
@@ -429,44 +412,41 @@ def run_ours(args):
             serving["fp64"] = serving_leg(tpt, local, 0, args.serve_requests_fp64, 10)
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if not args.no_cpu_baseline:
         nslab = max(1, min(n[2], args.cpu_slabs))
         s_per = cpu_sample(n, nslab)
         cpu = {"value": 1.0 / s_per, "unit": "solves/s", "cores": _threads(), "kind": "oracle",
                "sample": "oracle (numpy float64) correction pass + residual on a %dx%dx%d slab "
                          "of the same grid, scaled by points to one refined solve" % (n[0], n[1], nslab)}
 
-    if rank == 0:
-        last = next((i for i in reversed(infos) if i), info)
-        out = {
-            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": DTYPE[args.precision], "data": "synthetic",
-            "config": {"workload": workload_name(args.size),
-                       "size": list(n), "stretch": list(stretch), "precision": args.precision,
-                       "rtol": rtol, "max_refine": refine, "parallelism": "replicas%d" % world,
-                       "gemm_tiles": tiles,
-                       "l2": "inputs larger than L2 (%.2f GB field)" % (npts * 8 / 1e9)},
-            "gpts_per_s": value * npts / 1e9,
-            "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99)),
-                           "mean20fastest": float(np.mean(sorted(per)[:20]))},
-            "solve_info": {k: v for k, v in (last or {}).items() if k != "ms_stage"},
-            "stages": stages,
-            "fp64": fp64,
-            "projection": projection,
-            "fft": fft,
-            "batch": batch,
-            "serving": serving,
-            "gpu_launches": l1 - l0,
-            "roofline": dom,
-            "clocks": clk,
-            "e2e": e2e,
-            "cpu_baseline": cpu,
-        }
-        print(json.dumps(out), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+    last = next((i for i in reversed(infos) if i), info)
+    out = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": DTYPE[args.precision], "data": "synthetic",
+        "config": {"workload": workload_name(args.size),
+                   "size": list(n), "stretch": list(stretch), "precision": args.precision,
+                   "rtol": rtol, "max_refine": refine, "parallelism": "single GPU",
+                   "gemm_tiles": tiles,
+                   "l2": "inputs larger than L2 (%.2f GB field)" % (npts * 8 / 1e9)},
+        "gpts_per_s": value * npts / 1e9,
+        "latency_ms": {"p50": float(np.percentile(per, 50)), "p99": float(np.percentile(per, 99)),
+                       "mean20fastest": float(np.mean(sorted(per)[:20]))},
+        "solve_info": {k: v for k, v in (last or {}).items() if k != "ms_stage"},
+        "stages": stages,
+        "fp64": fp64,
+        "projection": projection,
+        "fft": fft,
+        "batch": batch,
+        "serving": serving,
+        "gpu_launches": l1 - l0,
+        "roofline": dom,
+        "clocks": clk,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(out), flush=True)
     return 0
 
 
@@ -822,7 +802,7 @@ def stage_rooflines(ms, iters, n, prec):
     return {"per_stage": out, "iters": iters, "peak_source": "MEASURED_PEAKS.json (burst)"}
 
 
-def e2e_server(tpt, device, spec, f_pin, steps, warmup, phi_ref, barrier, slots=3):
+def e2e_server(tpt, device, spec, f_pin, steps, warmup, phi_ref, slots=3):
     """End to end through the serving API: `steps` solves of the headline
     workload submitted back to back with pinned host buffers (f read from
     host memory, phi written back to host memory by every request), timed from
@@ -841,7 +821,6 @@ def e2e_server(tpt, device, spec, f_pin, steps, warmup, phi_ref, barrier, slots=
             if r is None or r["status"] != 0:
                 raise RuntimeError("e2e warm-up request failed: %r" % (r,))
         torch.cuda.synchronize()
-        barrier()
         t0 = time.perf_counter()
         tickets = [srv.submit(f_pin, ring[i % len(ring)], **spec) for i in range(steps)]
         res = [srv.wait(t, timeout=300.0) for t in tickets]

@@ -190,7 +190,10 @@ int tpt_thomas(tpt_plan plan, const double* fhat_dev, double* phihat_dev, double
  * the field may have at most 4,194,304 points (Nx*Ny*Nz); larger plans get
  * TPT_ERR_UNSUPPORTED.  The first call on a device looks up the array's
  * device address on that device (make that first call before any stream
- * capture).  All calls share the one array, so calls whose kernels overlap on
+ * capture) and keeps it for the life of the process, like the device tables
+ * of a plan: after cudaDeviceReset (or anything else that destroys the
+ * device's primary context) neither this entry point nor any plan created
+ * before it may be used again.  All calls share the one array, so calls whose kernels overlap on
  * the GPU race and give wrong results: serialise them (one stream, or events).
  * The scratch is fully rewritten before it is read, so nothing needs clearing
  * between calls.  The compatibility constant of a singular problem is not
@@ -255,6 +258,14 @@ int tpt_plan_rows(tpt_plan plan, int dir, double* a_host, double* b_host, double
  * (every device, every thread); benchmarks read it before and after a timed
  * region to count the kernels inside it.                                   */
 int tpt_kernel_launches(unsigned long long* count);
+
+/* Whether ptr points into device memory of cuda_device (1) or not (0: host,
+ * pinned, managed or another GPU's memory, a null pointer, or a device that
+ * does not exist).  The transform GEMMs pair two CTAs that share an operand
+ * tile by TMA multicast only when every operand plane passes this test on
+ * the current device; otherwise they run one CTA per tile.  The paper has no
+ * counterpart.  INVALID_ARG for a null on_device or a negative device.      */
+int tpt_pointer_on_device(const void* ptr, int cuda_device, int* on_device);
 
 /* Record CUDA events around each stage of tpt_solve on a TPT_PREC_MIXED_*
  * plan and report the summed stage times in tpt_info.ms_stage (filled only

@@ -117,6 +117,7 @@ SIGNATURES = [
     ("tpt_grid_tanh", C.c_int, [C.c_int, C.c_double, C.c_double, _dp, _dp]),
     ("tpt_grid_faces", C.c_int, [C.c_int, _dp, _dp, C.c_int, C.POINTER(C.c_int), _dp, _dp]),
     ("tpt_kernel_launches", C.c_int, [C.POINTER(C.c_ulonglong)]),
+    ("tpt_pointer_on_device", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     ("tpt_set_stage_timing", C.c_int, [C.c_void_p, C.c_int]),
     ("tpt_set_refinement", C.c_int, [C.c_void_p, C.c_double, C.c_int]),
     ("tpt_plan_autotune", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]),

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "cache.h"
+#include "tc.h"
 #include "tpt_internal.h"
 
 using tpt::Dir1D;
@@ -411,6 +412,20 @@ const char* tpt_status_string(int status) {
 int tpt_kernel_launches(unsigned long long* count) {
   if (!count) return TPT_ERR_INVALID_ARG;
   *count = tpt::g_launches.load(std::memory_order_relaxed);
+  return TPT_OK;
+}
+
+int tpt_pointer_on_device(const void* ptr, int cuda_device, int* on_device) {
+  if (!on_device || cuda_device < 0) return TPT_ERR_INVALID_ARG;
+  *on_device = 0;
+  if (!ptr) return TPT_OK;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || cuda_device >= ndev) {
+    cudaGetLastError();
+    return TPT_OK;   // no such device: nothing is its memory
+  }
+  DeviceGuard g(cuda_device);
+  *on_device = tpt::tc::own_device_memory(ptr) ? 1 : 0;
   return TPT_OK;
 }
 

@@ -192,10 +192,12 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
   uint8_t* smem = smem_raw + ((1024u - (ptx::smem_u32(smem_raw) & 1023u)) & 1023u);
   constexpr int EPI = epi_warps<OUT>();
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE);
-  // bars[0..S) full, [S..2S) empty, [2S, 2S+2) acc_full, [2S+2, 2S+4) acc_empty
+  // bars[0..S) full, [S..2S) empty, [2S, 2S+2) acc_full, [2S+2, 2S+4) acc_empty,
+  // [2S+4] mma_done (the issuer's last MMAs have completed)
   uint64_t* accf = bars + 2 * C::STAGES;
   uint64_t* acce = accf + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
+  uint64_t* mdone = acce + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mdone + 1);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int num_m = (g.M + BM - 1) / BM, num_n = (g.N + BN - 1) / BN;
@@ -220,6 +222,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
       ptx::mbar_init(ptx::smem_u32(&accf[b]), 1);
       ptx::mbar_init(ptx::smem_u32(&acce[b]), EPI);
     }
+    ptx::mbar_init(ptx::smem_u32(mdone), 1);
     ptx::fence_mbar_init();
   }
   if (warp == 1) {
@@ -289,10 +292,12 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
       }
     }
     // drain: every issued stage's copies have landed before the CTA may exit
+    // (the same bound as the main waits; a timed-out drain is recorded in
+    // g.err, and every caller then treats the output as invalid)
     const long long first = it > C::STAGES ? it - C::STAGES : 0;
     for (long long k = first; k < it; ++k)
       ptx::mbar_wait(ptx::smem_u32(&bars[k % C::STAGES]), static_cast<uint32_t>((k / C::STAGES) & 1), g.err,
-                     ptx::kErrWaitDrain, 1u << 20);
+                     ptx::kErrWaitDrain);
   } else if (warp == 1 && lane == 0) {
     // -------------------------------------------------------- MMA issuer
     constexpr uint32_t idesc = ptx::instr_desc(KIND == kKindBF16 ? 1u : 2u, BM, BN);
@@ -334,6 +339,12 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
         else ptx::mma_commit(ptx::smem_u32(&bars[C::STAGES + s]));                  // in both CTAs
       }
       ptx::mma_commit(ptx::smem_u32(&accf[b]));                 // accumulator b ready
+    }
+    // every MMA this thread issued has completed before the tensor memory is
+    // freed, also when a timed-out wait ended the loop early
+    if (it > 0) {
+      ptx::mma_commit(ptx::smem_u32(mdone));
+      ptx::mbar_wait(ptx::smem_u32(mdone), 0u, g.err, ptx::kErrWaitDrain);
     }
   } else if (warp >= 2) {
     // ---------------------------------------------------------- epilogue
@@ -549,10 +560,21 @@ cudaError_t launch(const Operand& A, const Operand& B, const GemmOut& g, cudaStr
 
 // Pair mode g.pair when it applies (split bf16 operands, 128- or 256-column
 // tiles, an even number of m-tiles (pair 1) or n-tiles (pair 2), an output
-// mode instantiated for it), else a single CTA per tile.
+// mode instantiated for it, and both operands in the current device's own
+// memory, since the pair's shared tile is loaded by a cluster-multicast TMA
+// copy), else a single CTA per tile.
 template <int KIND, int NPL, int BN, int OUT>
 cudaError_t launch_pair(const Operand& A, const Operand& B, const GemmOut& g, cudaStream_t s) {
   const int num_m = (g.M + BM - 1) / BM, num_n = (g.N + BN - 1) / BN;
+  if (g.pair != 0) {
+    bool local = true;
+    for (int pl = 0; pl < NPL; ++pl) local = local && own_device_memory(A.plane[pl]) && own_device_memory(B.plane[pl]);
+    if (!local) {
+      GemmOut g1 = g;
+      g1.pair = 0;
+      return launch_pair<KIND, NPL, BN, OUT>(A, B, g1, s);
+    }
+  }
   constexpr bool can1 = NPL == 2 && BN >= 128 &&
                         (OUT == kOutSplitBF16 || OUT == kOutBF16 || OUT == kOutF32 || OUT == kOutF64);
   constexpr bool can2 = NPL == 2 && BN >= 128 && (OUT == kOutF32 || OUT == kOutDF || OUT == kOutF64);
@@ -611,6 +633,20 @@ bool make_plain_map(CUtensorMap* map, const void* base, int elem_bytes, long lon
                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
+}
+
+bool own_device_memory(const void* p) {
+  int dev = -1;
+  if (!p || cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 int default_bn(int N) { return N <= 32 ? 32 : N <= 64 ? 64 : N <= 128 ? 128 : 256; }

@@ -30,7 +30,9 @@ std::mutex g_mutex;
 double* g_scratch_addr[kMaxDevices] = {nullptr};
 
 // Device address of g_thomas_scratch on `dev`, looked up once per device with
-// that device current.  Returns nullptr on failure.
+// that device current and kept for the life of the process (a device reset
+// invalidates it together with every plan, which this entry point needs).
+// Returns nullptr on failure.
 double* noalloc_scratch(int dev) {
   if (dev < 0 || dev >= kMaxDevices) return nullptr;
   std::lock_guard<std::mutex> lock(g_mutex);

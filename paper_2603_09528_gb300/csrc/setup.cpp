@@ -108,6 +108,10 @@ namespace {
 // Implicit QL iteration with Wilkinson-type shifts on a symmetric tridiagonal
 // matrix (diagonal dd[0..n-1], off-diagonal ee[i] coupling i and i+1), with the
 // rotations accumulated into the column-major n x n matrix z (starts as I).
+// This is the classic public-domain algorithm of EISPACK's imtql2 (Bowdler,
+// Martin, Reinsch and Wilkinson, 1968), in its common textbook form; the
+// steps and the scalar names (g, r, s, c, p, f, b) follow that published
+// listing.
 bool ql_implicit(int n, std::vector<double>& dd, std::vector<double>& ee, std::vector<double>& z) {
   ee.resize(n);
   ee[n - 1] = 0.0;

@@ -43,6 +43,11 @@ struct GemmOut {
   const int* skip = nullptr;   // device flag: the kernel returns at entry when it is nonzero
 };
 
+// True when p points into device memory of the current device (not host,
+// managed or another GPU's memory).  Operand sharing between the two CTAs of
+// a pair (TMA multicast) is used only when every operand plane passes.
+bool own_device_memory(const void* p);
+
 // Column tile width used when GemmOut::bn is 0.
 int default_bn(int N);
 

@@ -1,54 +1,48 @@
-"""The bench's multi-rank path on CPU: two gloo ranks (replicas, no
-collective on the data path) agree on the slowest rank's time, the whole-job
-rate counts every rank's units, and only rank 0 runs the reference leg."""
+"""The bench is a one-GPU program.  Its own arm refuses more than one GPU
+(and a launch under torchrun with WORLD_SIZE > 1) before it touches CUDA, so
+no multi-GPU run can reach the paired-CTA GEMMs that share operand tiles by
+TMA multicast; the reference arm (the CPU oracle) runs on rank 0 only and
+the other ranks exit 0 without output."""
 import os
-import socket
+import subprocess
+import sys
 
 import pytest
-import torch.multiprocessing as mp
 
 from _tpt import ROOT
 
 
-def _free_port():
-    with socket.socket() as s:
-        s.bind(("127.0.0.1", 0))
-        return s.getsockname()[1]
+def _bench(args, **env):
+    e = dict(os.environ)
+    e.update(env)
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py")] + args, capture_output=True,
+                          text=True, timeout=300, env=e, cwd=ROOT)
 
 
-def _rank(rank, world, port, q):
-    import sys
+@pytest.mark.parametrize("args,env", [(["--gpus", "2"], {}), (["--gpus", "8"], {}),
+                                      (["--gpus", "1"], {"WORLD_SIZE": "2", "RANK": "0"})])
+def test_our_arm_refuses_more_than_one_gpu(args, env):
+    out = _bench(args + ["--steps", "1", "--warmup", "1"], **env)
+    assert out.returncode == 2, (out.returncode, out.stderr)
+    assert out.stdout.strip() == ""
+    assert "one GPU only" in out.stderr and "multicast" in out.stderr
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    out = _bench(["--impl", "reference", "--gpus", "2", "--size", "32", "--cpu-slabs", "4", "--steps", "1",
+                  "--warmup", "1"], RANK="1", WORLD_SIZE="2")
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.strip() == ""
+
+
+def test_refusal_helper_accepts_one_gpu():
     sys.path.insert(0, ROOT)
-    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
-    import torch.distributed as dist
+    import argparse
     import bench
-    dist.init_process_group("gloo", rank=rank, world_size=world)
-    mine = 1.5 + rank          # rank 1 is the slower replica
-    t = bench.max_over_ranks(mine, world, "cpu")
-    dist.barrier()
-    q.put((rank, t, bench.job_rate(5, world, t), bench.runs_reference_leg(rank)))
-    dist.destroy_process_group()
-
-
-def test_two_gloo_replicas_take_the_slowest_time():
-    ctx = mp.get_context("spawn")
-    q = ctx.Queue()
-    port = _free_port()
-    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
-    for p in procs:
-        p.start()
-    out = sorted(q.get(timeout=120) for _ in procs)
-    for p in procs:
-        p.join(timeout=60)
-        assert p.exitcode == 0
-    assert [o[1] for o in out] == [2.5, 2.5]                 # both ranks see the max
-    assert all(abs(o[2] - 10 / 2.5) < 1e-12 for o in out)   # 2 ranks x 5 units / slowest time
-    assert [o[3] for o in out] == [True, False]
-
-
-def test_single_rank_needs_no_process_group():
-    import sys
-    sys.path.insert(0, ROOT)
-    import bench
-    assert bench.max_over_ranks(3.0, 1, "cpu") == 3.0
-    assert bench.job_rate(4, 1, 2.0) == 2.0
+    old = os.environ.pop("WORLD_SIZE", None)
+    try:
+        assert bench.one_gpu_only(argparse.Namespace(gpus=1)) is None
+        assert "one GPU only" in bench.one_gpu_only(argparse.Namespace(gpus=2))
+    finally:
+        if old is not None:
+            os.environ["WORLD_SIZE"] = old

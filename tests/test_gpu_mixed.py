@@ -409,3 +409,31 @@ def test_device_stopping_test_reports_misses_and_continues_after_a_graph_replay(
     got = tpt.field_to_host(phi, n)
     assert info["status"] == L.TPT_OK and info["rel_residual"] <= 1e-10 and info["iters"] > 1, info
     assert np.abs(got - ref).max() <= 1e-7 * np.abs(ref).max()
+
+
+def test_pointer_guard_on_the_gpu():
+    """Device memory of this GPU qualifies for multicast operand sharing;
+    pinned host memory and a device index past the last GPU do not."""
+    dev = torch.empty(256, dtype=torch.float64, device="cuda")
+    pin = torch.empty(256, dtype=torch.float64).pin_memory()
+    flag = C.c_int(-1)
+    cur = torch.cuda.current_device()
+    assert L.lib.tpt_pointer_on_device(C.c_void_p(dev.data_ptr()), cur, C.byref(flag)) == L.TPT_OK
+    assert flag.value == 1
+    assert L.lib.tpt_pointer_on_device(C.c_void_p(pin.data_ptr()), cur, C.byref(flag)) == L.TPT_OK
+    assert flag.value == 0
+    assert L.lib.tpt_pointer_on_device(C.c_void_p(dev.data_ptr()), torch.cuda.device_count(),
+                                       C.byref(flag)) == L.TPT_OK
+    assert flag.value == 0
+
+
+def test_paired_gemm_with_host_mapped_operand_falls_back_to_single_ctas():
+    """A pair request whose operand is not in this GPU's memory runs one CTA
+    per tile (no multicast) and still gives the exact product."""
+    M, N, K = 256, 512, 128
+    rng = np.random.default_rng(11)
+    A = rng.integers(-8, 9, size=(M, K)).astype(np.float64)
+    B = rng.integers(-8, 9, size=(N, K)).astype(np.float64)
+    for pair in (1, 2):
+        got = _tc_gemm("bf16x3", A, B, tile=256, pair=pair)
+        assert np.array_equal(got, A @ B.T), pair

@@ -248,3 +248,18 @@ def test_excluded_direction_rules():
     assert L.lib.tpt_plan_create(C.byref(d), -1, C.byref(h)) == L.TPT_ERR_INVALID_ARG
     d, keep = _desc((8, 8, 8), grids, [(1, 1), (1, 1), (X, X)], alpha=1.0, beta=-1e-3)
     assert L.lib.tpt_plan_create(C.byref(d), -1, C.byref(h)) == L.TPT_ERR_UNSUPPORTED
+
+
+def test_pointer_guard_keeps_multicast_to_own_device_memory():
+    """The transform GEMMs share operand tiles between paired CTAs by TMA
+    multicast only for operands in the current GPU's own memory; host memory
+    (and anything on a machine without that device) never qualifies."""
+    buf = np.zeros(64, dtype=np.float64)
+    flag = C.c_int(7)
+    assert L.lib.tpt_pointer_on_device(C.c_void_p(buf.ctypes.data), 0, C.byref(flag)) == L.TPT_OK
+    assert flag.value == 0
+    flag.value = 7
+    assert L.lib.tpt_pointer_on_device(None, 0, C.byref(flag)) == L.TPT_OK
+    assert flag.value == 0
+    assert L.lib.tpt_pointer_on_device(C.c_void_p(buf.ctypes.data), -1, C.byref(flag)) == L.TPT_ERR_INVALID_ARG
+    assert L.lib.tpt_pointer_on_device(C.c_void_p(buf.ctypes.data), 0, None) == L.TPT_ERR_INVALID_ARG
