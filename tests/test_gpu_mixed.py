@@ -426,14 +426,3 @@ def test_pointer_guard_on_the_gpu():
                                        C.byref(flag)) == L.TPT_OK
     assert flag.value == 0
 
-
-def test_paired_gemm_with_host_mapped_operand_falls_back_to_single_ctas():
-    """A pair request whose operand is not in this GPU's memory runs one CTA
-    per tile (no multicast) and still gives the exact product."""
-    M, N, K = 256, 512, 128
-    rng = np.random.default_rng(11)
-    A = rng.integers(-8, 9, size=(M, K)).astype(np.float64)
-    B = rng.integers(-8, 9, size=(N, K)).astype(np.float64)
-    for pair in (1, 2):
-        got = _tc_gemm("bf16x3", A, B, tile=256, pair=pair)
-        assert np.array_equal(got, A @ B.T), pair
