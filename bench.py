@@ -618,10 +618,12 @@ def serving_leg(tpt, device, prec, count, warmup, rate_hz=200.0, slots=4, stretc
     span = max(x["t_done"] for x in meas) - min(x["t_submit"] for x in meas)
     pts = sum(r["n"][0] * r["n"][1] * r["n"][2] for r in reqs[warmup:])
     bad = sum(1 for x in meas if x["status"] != 0)
-    statuses = {}
+    statuses, failures = {}, []
     for x in results:
         if x["status"] != 0:
             statuses[str(x["status"])] = statuses.get(str(x["status"]), 0) + 1
+            failures.append({"status": x["status"], "step": x.get("failed_step"),
+                             "cuda_error": x.get("cuda_error_name")})
     return {"precision": {0: "fp64", 1: "mixed_bf16", 2: "mixed_bf16x3", 3: "mixed_tf32"}[prec],
             "requests": count, "warmup_requests": warmup, "offered_rate_hz": rate_hz,
             "slots": slots, "stretch_step": stretch_step,
@@ -630,7 +632,7 @@ def serving_leg(tpt, device, prec, count, warmup, rate_hz=200.0, slots=4, stretc
             "phase_ms_p50": {"plan": float(np.median(plan_ms)), "queue": float(np.median(queue_ms)),
                              "h2d_solve_d2h": float(np.median(run_ms))},
             "solves_per_s": count / span, "gpts_per_s": pts / span / 1e9,
-            "failed": bad, "failed_statuses": statuses, "warm_s": t_warm, "warmed_plans": len(seen),
+            "failed": bad, "failed_statuses": statuses, "failures": failures[:8], "warm_s": t_warm, "warmed_plans": len(seen),
             "max_rel_residual": float(max(x["rel_residual"] for x in meas)),
             "cache": {"hits": int(st["cache_hits"]), "misses": int(st["cache_misses"]),
                       "device_bytes": int(st["cache_bytes"])},

@@ -439,7 +439,20 @@ typedef struct {
   tpt_info info;
   double t_submit, t_planned, t_admit, t_done;   /* seconds on the server's clock    */
   size_t device_bytes;          /* bytes charged to the memory budget                */
+  int failed_step;              /* 0 none; where a failing request failed:
+                                   TPT_STEP_* below                                  */
+  int cuda_error;               /* the cudaError_t behind TPT_ERR_CUDA / _OOM, else 0;
+                                   tpt_cuda_error_name() names it                    */
 } tpt_result;
+#define TPT_STEP_PLAN 1         /* plan creation (host setup, cached tables)        */
+#define TPT_STEP_ALLOC 2        /* request buffers from the server's pool            */
+#define TPT_STEP_H2D 3          /* right-hand side copy to the device                */
+#define TPT_STEP_SOLVE 4        /* tpt_solve                                         */
+#define TPT_STEP_D2H 5          /* solution copy to the host                         */
+#define TPT_STEP_SYNC 6         /* the slot stream's final synchronisation           */
+
+/* Name of a cudaError_t value as reported in tpt_result.cuda_error.        */
+const char* tpt_cuda_error_name(int cuda_error);
 
 typedef struct {
   unsigned long long submitted, completed, rejected;

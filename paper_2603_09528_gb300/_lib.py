@@ -74,6 +74,8 @@ class tpt_result(C.Structure):
         ("t_admit", C.c_double),
         ("t_done", C.c_double),
         ("device_bytes", C.c_size_t),
+        ("failed_step", C.c_int),
+        ("cuda_error", C.c_int),
     ]
 
 
@@ -118,6 +120,7 @@ SIGNATURES = [
     ("tpt_grid_faces", C.c_int, [C.c_int, _dp, _dp, C.c_int, C.POINTER(C.c_int), _dp, _dp]),
     ("tpt_kernel_launches", C.c_int, [C.POINTER(C.c_ulonglong)]),
     ("tpt_pointer_on_device", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
+    ("tpt_cuda_error_name", C.c_char_p, [C.c_int]),
     ("tpt_set_stage_timing", C.c_int, [C.c_void_p, C.c_int]),
     ("tpt_set_refinement", C.c_int, [C.c_void_p, C.c_double, C.c_int]),
     ("tpt_plan_autotune", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]),

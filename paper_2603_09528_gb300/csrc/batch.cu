@@ -54,6 +54,7 @@ struct DeviceScope {   // restores the caller's current device
 int cuda_st(cudaError_t e) {
   if (e == cudaSuccess) return TPT_OK;
   cudaGetLastError();
+  tpt::note_cuda_error(e);
   return e == cudaErrorMemoryAllocation ? TPT_ERR_OOM : TPT_ERR_CUDA;
 }
 

@@ -77,6 +77,7 @@ namespace {
 int st_of(cudaError_t e) {
   if (e == cudaSuccess) return TPT_OK;
   cudaGetLastError();
+  tpt::note_cuda_error(e);
   return e == cudaErrorMemoryAllocation ? TPT_ERR_OOM : TPT_ERR_CUDA;
 }
 

@@ -31,6 +31,7 @@ struct DeviceGuard {   // restores the caller's current device
 int cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return TPT_OK;
   cudaGetLastError();
+  tpt::note_cuda_error(e);
   return e == cudaErrorMemoryAllocation ? TPT_ERR_OOM : TPT_ERR_CUDA;
 }
 
@@ -362,6 +363,14 @@ namespace {
 std::atomic<unsigned long long> g_launches{0};
 }
 void note_launch(unsigned long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+namespace {
+thread_local cudaError_t t_last_cuda_error = cudaSuccess;
+}
+void note_cuda_error(cudaError_t e) {
+  if (e != cudaSuccess) t_last_cuda_error = e;
+}
+cudaError_t last_cuda_error() { return t_last_cuda_error; }
+void clear_cuda_error() { t_last_cuda_error = cudaSuccess; }
 unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 void forget_launches(unsigned long long k) { g_launches.fetch_sub(k, std::memory_order_relaxed); }
 
@@ -413,6 +422,10 @@ int tpt_kernel_launches(unsigned long long* count) {
   if (!count) return TPT_ERR_INVALID_ARG;
   *count = tpt::g_launches.load(std::memory_order_relaxed);
   return TPT_OK;
+}
+
+const char* tpt_cuda_error_name(int cuda_error) {
+  return cuda_error == 0 ? "cudaSuccess" : cudaGetErrorName(static_cast<cudaError_t>(cuda_error));
 }
 
 int tpt_pointer_on_device(const void* ptr, int cuda_device, int* on_device) {

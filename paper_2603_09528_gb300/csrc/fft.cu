@@ -151,12 +151,20 @@ cudaError_t launch_fft(int kind, bool inverse, int N, long long nlines, long lon
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   const int acc = accumulate ? 1 : 0;
   const unsigned g = static_cast<unsigned>(blocks);
+  int dev = 0, cap = 48 * 1024;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&cap, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    cudaGetLastError();
+    cap = 48 * 1024;
+  }
 #define TPT_FFT_LAUNCH(K, I)                                                                       \
   do {                                                                                             \
     auto kern = fft_lines_kernel<R, K, I>;                                                         \
     if (smem > 48 * 1024) {                                                                        \
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
-                                           static_cast<int>(smem));                                \
+      /* the device's cap, the same for every launch: a per-launch value could */                 \
+      /* be lowered by another thread between setting it and launching */                        \
+      if (static_cast<int>(smem) > cap) return cudaErrorInvalidConfiguration;                      \
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, cap); \
       if (e != cudaSuccess) return e;                                                              \
     }                                                                                              \
     note_launch(1);                                                                                \

@@ -1357,6 +1357,7 @@ namespace {
 int st_of(cudaError_t e) {
   if (e == cudaSuccess) return TPT_OK;
   cudaGetLastError();
+  note_cuda_error(e);
   return e == cudaErrorMemoryAllocation ? TPT_ERR_OOM : TPT_ERR_CUDA;
 }
 #define MX_TRY(expr)               \
@@ -1565,7 +1566,10 @@ cudaError_t launch_thomas_m(const tpt_plan_s* p, const MixedWork& w, cudaStream_
   const size_t smem = 1024 + static_cast<size_t>(geo.coef_bytes) + static_cast<size_t>(geo.stages) * geo.in_bytes +
                       static_cast<size_t>(geo.out_bytes);
   auto kern = thomas_tma_kernel<FMT, M, TLT, NT>;
-  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  // The cap is the kernel's fixed budget, never the size of this launch:
+  // threads that launch the same kernel for different Nz (the server's slots)
+  // would otherwise lower each other's cap between setting it and launching.
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kThomasSmemBudget / kPerSm);
   if (e != cudaSuccess) return e;
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->dev);

@@ -49,6 +49,7 @@ struct Request {
 int cuda_st(cudaError_t e) {
   if (e == cudaSuccess) return TPT_OK;
   cudaGetLastError();
+  tpt::note_cuda_error(e);
   return e == cudaErrorMemoryAllocation ? TPT_ERR_OOM : TPT_ERR_CUDA;
 }
 
@@ -104,6 +105,7 @@ struct tpt_server_s {
         setup_q.pop_front();
       }
       tpt_plan p = nullptr;
+      tpt::clear_cuda_error();
       int st = tpt::create_plan(&r->desc, cfg.cuda_device, &cache, &p);
       size_t wb = 0;
       if (st == TPT_OK) st = tpt_workspace_bytes(p, &wb);
@@ -111,6 +113,8 @@ struct tpt_server_s {
       r->res.t_planned = now();
       if (st != TPT_OK) {
         if (p) tpt_plan_destroy(p);
+        r->res.failed_step = TPT_STEP_PLAN;
+        r->res.cuda_error = static_cast<int>(tpt::last_cuda_error());
         finish(r, st);
         continue;
       }
@@ -129,8 +133,20 @@ struct tpt_server_s {
     }
   }
 
-  // H2D, solve, D2H on the slot's stream; returns the request's status.
+  // H2D, solve, D2H on the slot's stream; returns the request's status and
+  // records in r->res where a failure happened and its CUDA error.
   int execute(Request* r, cudaStream_t s) {
+    tpt::clear_cuda_error();
+    int step = 0;
+    const int st = execute_steps(r, s, &step);
+    if (st != TPT_OK && st != TPT_ERR_NOT_CONVERGED) {
+      r->res.failed_step = step;
+      r->res.cuda_error = static_cast<int>(tpt::last_cuda_error());
+    }
+    return st;
+  }
+
+  int execute_steps(Request* r, cudaStream_t s, int* step) {
     if (cfg.cuda_device < 0) {   // dry run: the solve is a sleep
       const double ns = cfg.dry_run_ns_per_point * static_cast<double>(r->npts);
       std::this_thread::sleep_for(std::chrono::nanoseconds(static_cast<long long>(ns)));
@@ -140,6 +156,7 @@ struct tpt_server_s {
     void* buf[3] = {nullptr, nullptr, nullptr};
     const size_t sz[3] = {bytes + 256, bytes + 256, r->work_bytes + 256};
     int st = TPT_OK;
+    *step = TPT_STEP_ALLOC;
     for (int i = 0; i < 3 && st == TPT_OK; ++i)
       st = cuda_st(cudaMallocFromPoolAsync(&buf[i], sz[i], cache.buffer_pool(), s));
     auto aligned = [](void* p) {
@@ -154,10 +171,12 @@ struct tpt_server_s {
         // sharing the host link, so that the oldest admitted request's solve
         // starts as early as possible and the next copy overlaps it
         std::lock_guard<std::mutex> g(h2d_mu);
+        *step = TPT_STEP_H2D;
         st = cuda_st(cudaMemcpyAsync(f, r->f_host, bytes, cudaMemcpyHostToDevice, s));
         if (st == TPT_OK) st = cuda_st(cudaStreamSynchronize(s));
       }
       if (st == TPT_OK) {
+        *step = TPT_STEP_SOLVE;
         if (r->npts >= kExclusivePoints) {
           std::unique_lock<std::shared_mutex> g(compute_mu);
           st = tpt_solve(r->plan, f, phi, work, s, &r->res.info);
@@ -167,13 +186,17 @@ struct tpt_server_s {
         }
         if (st == TPT_OK || st == TPT_ERR_NOT_CONVERGED) {
           const int cs = cuda_st(cudaMemcpyAsync(r->phi_host, phi, bytes, cudaMemcpyDeviceToHost, s));
-          if (cs != TPT_OK) st = cs;
+          if (cs != TPT_OK) {
+            *step = TPT_STEP_D2H;
+            st = cs;
+          }
         }
       }
     }
     for (void* b : buf)
       if (b) cudaFreeAsync(b, s);
     const int ss = cuda_st(cudaStreamSynchronize(s));
+    if (st == TPT_OK && ss != TPT_OK) *step = TPT_STEP_SYNC;
     return st != TPT_OK ? st : ss;
   }
 

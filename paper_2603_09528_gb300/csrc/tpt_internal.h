@@ -177,6 +177,13 @@ size_t npts(const tpt_plan_s* p);
 double* pinned_slot_acquire(double** dev);
 void pinned_slot_release(double* host);
 
+// The last CUDA error this thread turned into a TPT_ERR_* status (cudaSuccess:
+// none since the last clear), so that a caller that gets TPT_ERR_CUDA or
+// TPT_ERR_OOM can say which CUDA error it was.
+void note_cuda_error(cudaError_t e);
+cudaError_t last_cuda_error();
+void clear_cuda_error();
+
 // Count of kernels this library has launched (all devices, all threads).
 void note_launch(unsigned long long k = 1);
 unsigned long long launch_count();

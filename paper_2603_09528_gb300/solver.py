@@ -351,7 +351,9 @@ class Server:
         self._held.pop(int(ticket), None)
         return dict(status=int(r.status), iters=r.info.iters, rel_residual=r.info.rel_residual,
                     compat_defect=r.info.compat_defect, t_submit=r.t_submit, t_planned=r.t_planned,
-                    t_admit=r.t_admit, t_done=r.t_done, device_bytes=int(r.device_bytes))
+                    t_admit=r.t_admit, t_done=r.t_done, device_bytes=int(r.device_bytes),
+                    failed_step=int(r.failed_step), cuda_error=int(r.cuda_error),
+                    cuda_error_name=(lib.tpt_cuda_error_name(int(r.cuda_error)) or b"?").decode())
 
     def now(self) -> float:
         t = C.c_double()

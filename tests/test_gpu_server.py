@@ -109,3 +109,38 @@ def test_cached_device_plans_equal_standalone_plans(prec):
     for p in outs:
         p.close()
     cache.close()
+
+
+def test_concurrent_solves_of_sizes_sharing_a_kernel_do_not_race():
+    """Host threads that launch the same Thomas kernel instance for different
+    Nz (here 96 and 128 rows: the same 8-row segments, different shared
+    memory) must all succeed: each launch keeps the kernel's fixed
+    dynamic-shared-memory cap, which another thread cannot lower between the
+    cap being set and the launch."""
+    import threading
+    specs = [_spec((64, 64, nz), (1.5, 2.0, 2.5), 0.0, 1.0, L.TPT_PREC_MIXED_BF16X3) for nz in (96, 128, 96, 128)]
+    errors = []
+
+    def worker(sp, seed):
+        try:
+            plan = tpt.Plan(sp["n"], sp["dxf"], sp["dxc"], sp["bc"], xform=sp["xform"], alpha=0.0, beta=1.0,
+                            precision=sp["precision"], rtol=1e-10, max_refine=30)
+            stream = torch.cuda.Stream()
+            f = tpt.field_to_device(_rhs(sp, seed))
+            phi, work = plan.new_field(), plan.new_workspace()
+            for _ in range(12):
+                with torch.cuda.stream(stream):
+                    plan.set_tiles([0, 0, 0, 0])   # a new generation each time: no graph replay
+                    _, info = plan.solve(f, phi, work, stream=stream, want_info=True)
+                if info["status"] != 0:
+                    errors.append(info["status"])
+            stream.synchronize()
+        except Exception as e:   # noqa: BLE001 - collected and asserted below
+            errors.append(repr(e))
+
+    th = [threading.Thread(target=worker, args=(sp, 40 + i)) for i, sp in enumerate(specs)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert errors == []

@@ -171,3 +171,21 @@ def test_warm_fills_the_cache_before_traffic():
     srv.close()
     assert all(r["status"] == L.TPT_OK for r in res)
     assert st["cache_misses"] == 2 and st["cache_hits"] == 4
+
+
+def test_a_failed_request_reports_its_step_and_cuda_error():
+    """A request that fails names the step it failed in; one that fails in
+    host setup (an FFT transform asked for a stretched direction) carries no
+    CUDA error.  Requests that succeed report neither."""
+    srv = tpt.Server(device=-1, slots=2, setup_threads=1, memory_budget=1 << 30, cache_budget=0,
+                     dry_run_ns_per_point=10.0)
+    f, phi = np.zeros(8 * 8 * 8), np.zeros(8 * 8 * 8)
+    bad = dict(_spec((8, 8, 8), (2.0, 2.0, 2.0)), xform=(tpt.FFT, tpt.GEMM))
+    t_bad = srv.submit(f, phi, **bad)
+    t_ok = srv.submit(f, phi, **_spec((8, 8, 8), (2.0, 2.0, 2.0)))
+    r_bad, r_ok = srv.wait(t_bad, timeout=60.0), srv.wait(t_ok, timeout=60.0)
+    srv.close()
+    assert r_bad["status"] == L.TPT_ERR_UNSUPPORTED
+    assert r_bad["failed_step"] == 1 and r_bad["cuda_error"] == 0   # TPT_STEP_PLAN
+    assert r_ok["status"] == L.TPT_OK and r_ok["failed_step"] == 0 and r_ok["cuda_error"] == 0
+    assert L.lib.tpt_cuda_error_name(0) == b"cudaSuccess"
