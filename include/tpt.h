@@ -335,6 +335,31 @@ int tpt_plan_get_pairing(tpt_plan plan, int* pairs_out);
  * for another value; a no-op on float64 plans.                              */
 int tpt_plan_set_residual_kernel(tpt_plan plan, int variant);
 
+/* Modal Thomas kernel of a TPT_PREC_MIXED_* plan (Sec. 2.2.2 solution step
+ * 2.3 / Algorithm 1 step 5 in float32, by the partition method): 0
+ * automatic, 1 one modal line per thread (segments of up to 32 rows, 16 per
+ * line), 2 two neighbouring lines per thread (segments of up to 16 rows, 32
+ * per line; Nz <= 512).  Automatic takes 2 for 192 < Nz <= 512.  The two
+ * partition the lines differently, so results agree to float32 rounding,
+ * not to the bit.  For kernel tests and measurements.  INVALID_ARG for
+ * another value; a no-op on float64 plans.                                 */
+int tpt_plan_set_thomas_kernel(tpt_plan plan, int variant);
+
+/* That Thomas step alone, for kernel tests: t2_dev holds the modal right
+ * sides f-hat in float32, element (x mode p, y mode q, row k) at
+ * q + ldy (p + Nx k) with ldy = Ny rounded up to a multiple of 8 (entries
+ * with q >= Ny are padding and are solved as dummy lines); the solution
+ * phi-hat is written in the same layout in the plan's operand format:
+ * float32 (TPT_PREC_MIXED_TF32), bf16 (TPT_PREC_MIXED_BF16), or bf16 hi in
+ * t3_dev and lo in t3_lo_dev (TPT_PREC_MIXED_BF16X3).  A singular plan
+ * solves the null line (0, 0) in float64 on its second stream (the
+ * compatibility part of that line removed, zero dz-weighted mean).  work_dev
+ * is a workspace of tpt_workspace_bytes (its scalars are overwritten).
+ * Synchronises `stream`.  Errors: INVALID_ARG (float64 plan, null pointer),
+ * CUDA, TIMEOUT.                                                           */
+int tpt_mixed_thomas(tpt_plan plan, const float* t2_dev, void* t3_dev, void* t3_lo_dev, void* work_dev,
+                     void* stream);
+
 /* ---- batched solves ------------------------------------------------------ */
 /* A batch owns `count` plans of possibly different sizes and coefficients on
  * one device (Sec. 2.2: each instance is an independent tensor-product-Thomas

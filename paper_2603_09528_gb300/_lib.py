@@ -128,6 +128,8 @@ SIGNATURES = [
     ("tpt_plan_get_tiles", C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     ("tpt_plan_set_pairing", C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     ("tpt_plan_set_residual_kernel", C.c_int, [C.c_void_p, C.c_int]),
+    ("tpt_plan_set_thomas_kernel", C.c_int, [C.c_void_p, C.c_int]),
+    ("tpt_mixed_thomas", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     ("tpt_plan_get_pairing", C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     ("tpt_batch_create", C.c_int, [C.POINTER(tpt_desc), C.c_int, C.c_int, C.c_int, C.POINTER(C.c_void_p)]),
     ("tpt_batch_workspace_bytes", C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),

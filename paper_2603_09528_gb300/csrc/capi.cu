@@ -571,6 +571,21 @@ int tpt_plan_set_residual_kernel(tpt_plan p, int variant) {
   return TPT_OK;
 }
 
+int tpt_plan_set_thomas_kernel(tpt_plan p, int variant) {
+  if (!p || variant < 0 || variant > 2) return TPT_ERR_INVALID_ARG;
+  if (p->precision == TPT_PREC_FP64) return TPT_OK;
+  p->mixed.thomas_kernel = variant;
+  ++p->generation;
+  return TPT_OK;
+}
+
+int tpt_mixed_thomas(tpt_plan p, const float* t2_dev, void* t3_dev, void* t3_lo_dev, void* work_dev,
+                     void* stream) {
+  if (!p) return TPT_ERR_INVALID_ARG;
+  DeviceGuard g(p->dev);
+  return tpt::mixed_thomas_test(p, t2_dev, t3_dev, t3_lo_dev, work_dev, static_cast<cudaStream_t>(stream));
+}
+
 int tpt_plan_get_pairing(tpt_plan p, int* pairs_out) {
   if (!p || !pairs_out) return TPT_ERR_INVALID_ARG;
   for (int i = 0; i < 4; ++i) pairs_out[i] = (p->precision == TPT_PREC_FP64) ? 0 : p->mixed.gemm_pair[i];

@@ -480,7 +480,314 @@ thomas_tma_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_const
     if (!ok)   // the loads of local tiles i .. issued - 1 may still be landing
       for (long long k = i; k < issued; ++k)
         ptx::mbar_wait(ptx::smem_u32(&full[k % S]), static_cast<uint32_t>((k / S) & 1), err,
-                       ptx::kErrWaitDrain, 1u << 20);
+                       ptx::kErrWaitDrain);
+    ptx::bulk_wait_all();
+  }
+}
+
+// Two adjacent lines per thread (thomas2_kernel).  The same partition method
+// as thomas_tma_kernel on the same tiles (32 consecutive lines x all rows,
+// streamed by TMA, solved into an output tile stored by TMA), but each thread
+// carries two neighbouring lines through its segment, so every recurrence of
+// the sweeps runs as two independent dependency chains (the one-line kernel
+// spends most cycles waiting on its single chain of reciprocals and shared
+// loads), their inputs arrive as one 8-byte shared load and their outputs
+// leave as packed pairs.  A line has up to 32 segments of M <= 16 rows
+// (segment slot s = 2 * warp + lane / 16, lines 2 (lane % 16) and
+// 2 (lane % 16) + 1); a half-warp reads one 128-byte row of the tile, so the
+// 8-byte accesses are free of bank conflicts.  The reduced system has 32
+// interface rows per line; warp w solves lines 2w and 2w + 1 by parallel
+// cyclic reduction over all 32 lanes (lane r = interface row r), the rows
+// kept in a shared buffer with a row pitch of 33 floats so that a warp's
+// column reads are free of bank conflicts.  The second forward pass keeps its
+// values in registers for the back substitution instead of rewriting the
+// input tile.
+constexpr int kT2Slots = 32;                    // segment slots per line
+constexpr int kT2Pitch = kT2Slots + 1;          // row pitch of the reduced-system buffer
+constexpr int kT2SmemBudget = 210 * 1024;       // dynamic shared memory (16.5 KB static beside it)
+
+// Elements i and i + 1 (i even) of an output tile in the T3 format.
+template <int FMT>
+__device__ __forceinline__ void store_pair(void* o0, void* o1, int i, float x0, float x1) {
+  if (FMT == kFmtF32) {
+    *reinterpret_cast<float2*>(static_cast<float*>(o0) + i) = make_float2(x0, x1);
+  } else {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+    *reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(o0) + i) = h;
+    if (FMT == kFmtSplit) {
+      const float2 hf = __bfloat1622float2(h);
+      *reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(o1) + i) =
+          __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+    }
+  }
+}
+
+template <int FMT, int M>
+__global__ void __launch_bounds__(kThomasThreads, 1)
+thomas2_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ CUtensorMap map_o0,
+               const __grid_constant__ CUtensorMap map_o1, ThomasGeom geo, int nx, int ny, int nz, int ldy,
+               int ntiles, int* next_tile, void* t3_0, void* t3_1, const float* __restrict__ lamx,
+               const float* __restrict__ lamy, const float* __restrict__ az, const float* __restrict__ bz,
+               const float* __restrict__ cz, float alpha, float beta, int singular, int* err, const int* skip) {
+  if (skip && *skip) return;   // the refinement has stopped
+  using O = T3Fmt<FMT>;
+  constexpr int TLT = 32;
+  static_assert(M >= 2 && M <= 16, "segments of 2 to 16 rows");
+  extern __shared__ __align__(128) uint8_t dsm_raw[];
+  uint8_t* dsm = dsm_raw + ((1024u - (ptx::smem_u32(dsm_raw) & 1023u)) & 1023u);
+  RowCoef* coef = reinterpret_cast<RowCoef*>(dsm);
+  uint8_t* in_base = dsm + geo.coef_bytes;
+  uint8_t* ot = in_base + static_cast<size_t>(geo.stages) * geo.in_bytes;
+  void* o0 = ot;
+  void* o1 = ot + (O::NPL == 2 ? geo.out_bytes / 2 : 0);
+  // reduced-system buffer: first g_0, u_0, v_0 of every segment, then the
+  // interface rows A, B, C, D (D overwritten by the interface values y)
+  __shared__ float X[4][kT2Slots * kT2Pitch];
+  __shared__ __align__(8) uint64_t full[kThomasMaxStages];
+  __shared__ int tile_of[kThomasMaxStages];
+  __shared__ int go;
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  const int s = 2 * warp + lane / 16;    // segment slot
+  const int l0 = 2 * (lane % 16);        // first of the thread's two lines in the tile
+  const int s0 = s * M;
+  const bool active = s < geo.nseg;
+  const int xo = s * kT2Pitch + l0;      // the thread's entries in X
+  const int lines = ldy * nx;
+  const int S = geo.stages;
+  long long issued = 0;
+  bool exhausted = false;
+  int claim = -1;
+
+  auto issue = [&](long long i, int tile) {
+    const int st = static_cast<int>(i % S);
+    const uint32_t bar = ptx::smem_u32(&full[st]);
+    ++issued;
+    if (tile >= ntiles) {
+      exhausted = true;
+      tile_of[st] = -1;
+      ptx::mbar_arrive(bar);
+      return;
+    }
+    tile_of[st] = tile;
+    ptx::mbar_arrive_expect_tx(bar, static_cast<uint32_t>(geo.in_bytes));
+    uint8_t* base = in_base + static_cast<size_t>(st) * geo.in_bytes;
+    for (int b = 0; b < geo.nb; ++b)
+      ptx::tma_load_2d(ptx::smem_u32(base + b * geo.rb * TLT * 4), &map_in, bar, tile * TLT, b * geo.rb);
+  };
+
+  for (int k = tid; k < geo.sr; k += blockDim.x) {
+    RowCoef rc{0.0f, 1.0f, 0.0f, 0.0f};
+    if (k < nz) {
+      rc.a = k > 0 ? beta * az[k] : 0.0f;
+      rc.b = beta * bz[k];
+      rc.c = k < nz - 1 ? beta * cz[k] : 0.0f;
+      rc.m = 1.0f;
+    }
+    coef[k] = rc;
+  }
+  if (tid == 0) {
+    for (int i = 0; i < S; ++i) ptx::mbar_init(ptx::smem_u32(&full[i]), 1);
+    ptx::fence_mbar_init();
+    ptx::prefetch_tmap(&map_in);
+    ptx::prefetch_tmap(&map_o0);
+    if (O::NPL == 2) ptx::prefetch_tmap(&map_o1);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (long long i = 0; i < S && !exhausted; ++i) issue(i, atomicAdd(next_tile, 1));
+    if (!exhausted) claim = atomicAdd(next_tile, 1);
+  }
+
+  long long i = 0;
+  bool ok = true;
+  for (;; ++i) {
+    const int st = static_cast<int>(i % S);
+    const uint32_t bar = ptx::smem_u32(&full[st]);
+    const uint32_t par = static_cast<uint32_t>((i / S) & 1);
+    if (tid == 0) go = ptx::mbar_wait(bar, par, err, ptx::kErrWaitFull) ? 1 : 0;
+    __syncthreads();
+    if (!go) {
+      ok = false;
+      break;
+    }
+    const int tile = tile_of[st];
+    if (tile < 0) break;
+    for (int k = 0; k < 64 && !ptx::mbar_try_wait(bar, par); ++k) {
+    }   // the phase is complete: this acquires the TMA writes for every thread
+    const float* in = reinterpret_cast<const float*>(in_base + static_cast<size_t>(st) * geo.in_bytes);
+
+    float shift[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int L = tile * TLT + l0 + j;
+      int q = L % ldy, p = L / ldy;
+      if (L >= lines || q >= ny) q = p = 0;   // padding line: dummy shift
+      shift[j] = alpha + beta * (lamx[p] + lamy[q]);
+    }
+
+    // forward elimination of the interior rows (as in thomas_tma_kernel),
+    // two lines at a time
+    float inv[2][M - 1];
+    float cprev[2] = {0.0f, 0.0f}, gprev[2] = {0.0f, 0.0f}, uprev[2] = {0.0f, 0.0f};
+    if (active) {
+      float P[2] = {1.0f, 1.0f}, Gs[2] = {0.0f, 0.0f}, Us[2] = {0.0f, 0.0f};
+#pragma unroll
+      for (int t = 0; t < M - 1; ++t) {
+        const RowCoef rc = coef[s0 + t];
+        const float2 d = *reinterpret_cast<const float2*>(in + (s0 + t) * TLT + l0);
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const float m = fmaf(-rc.a, cprev[j], fmaf(rc.m, shift[j], rc.b));
+          const float iv = __fdividef(1.0f, m);
+          inv[j][t] = iv;
+          const float cp = rc.c * iv;
+          const float g = fmaf(-rc.a, gprev[j], j ? d.y : d.x) * iv;
+          const float u = (t == 0 ? -rc.a : -rc.a * uprev[j]) * iv;
+          Gs[j] = fmaf(P[j], g, Gs[j]);
+          Us[j] = fmaf(P[j], u, Us[j]);
+          P[j] *= -cp;
+          cprev[j] = cp;
+          gprev[j] = g;
+          uprev[j] = u;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        X[0][xo + j] = Gs[j];
+        X[1][xo + j] = Us[j];
+        X[2][xo + j] = P[j];
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        X[0][xo + j] = 0.0f;
+        X[1][xo + j] = 0.0f;
+        X[2][xo + j] = 0.0f;
+      }
+    }
+    __syncthreads();
+    // interface row of the segment (its last row), coupled to the first row of
+    // the next segment through g_0, u_0, v_0 of that segment
+    float ra[2] = {0.0f, 0.0f}, rb[2] = {1.0f, 1.0f}, rcc[2] = {0.0f, 0.0f}, rd[2] = {0.0f, 0.0f};
+    if (active) {
+      const int k = s0 + M - 1;
+      const RowCoef rc = coef[k];
+      const float2 d = *reinterpret_cast<const float2*>(in + k * TLT + l0);
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        ra[j] = rc.a * uprev[j];
+        rb[j] = fmaf(-rc.a, cprev[j], fmaf(rc.m, shift[j], rc.b));
+        rd[j] = fmaf(-rc.a, gprev[j], j ? d.y : d.x);
+        if (s + 1 < kT2Slots) {
+          const int on = xo + kT2Pitch + j;
+          rb[j] = fmaf(rc.c, X[1][on], rb[j]);
+          rcc[j] = rc.c * X[2][on];
+          rd[j] = fmaf(-rc.c, X[0][on], rd[j]);
+        }
+      }
+    }
+    __syncthreads();                     // every g_0, u_0, v_0 has been read
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      X[0][xo + j] = ra[j];
+      X[1][xo + j] = rb[j];
+      X[2][xo + j] = rcc[j];
+      X[3][xo + j] = rd[j];
+    }
+    __syncthreads();
+    // reduced systems: warp w takes lines 2w and 2w + 1, lane r interface row r
+    {
+      const int r = lane;
+      float A[2], B[2], Cc[2], D[2];
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int ix = r * kT2Pitch + 2 * warp + j;
+        A[j] = X[0][ix];
+        B[j] = X[1][ix];
+        Cc[j] = X[2][ix];
+        D[j] = X[3][ix];
+      }
+#pragma unroll
+      for (int dlt = 1; dlt < kT2Slots; dlt <<= 1) {
+        const bool hasm = r >= dlt, hasp = r + dlt < kT2Slots;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const float Am = __shfl_up_sync(0xffffffffu, A[j], dlt), Bm = __shfl_up_sync(0xffffffffu, B[j], dlt);
+          const float Cm = __shfl_up_sync(0xffffffffu, Cc[j], dlt), Dm = __shfl_up_sync(0xffffffffu, D[j], dlt);
+          const float Ap = __shfl_down_sync(0xffffffffu, A[j], dlt), Bp = __shfl_down_sync(0xffffffffu, B[j], dlt);
+          const float Cp = __shfl_down_sync(0xffffffffu, Cc[j], dlt), Dp = __shfl_down_sync(0xffffffffu, D[j], dlt);
+          const float k1 = hasm ? __fdividef(A[j], Bm) : 0.0f;
+          const float k2 = hasp ? __fdividef(Cc[j], Bp) : 0.0f;
+          const float nA = hasm ? -Am * k1 : 0.0f;
+          const float nC = hasp ? -Cp * k2 : 0.0f;
+          B[j] = B[j] - (hasm ? Cm * k1 : 0.0f) - (hasp ? Ap * k2 : 0.0f);
+          D[j] = D[j] - (hasm ? Dm * k1 : 0.0f) - (hasp ? Dp * k2 : 0.0f);
+          A[j] = nA;
+          Cc[j] = nC;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 2; ++j) X[3][r * kT2Pitch + 2 * warp + j] = __fdividef(D[j], B[j]);
+    }
+    if (tid == 0) ptx::bulk_wait_read<0>();   // the output tile of tile i-1 has been stored
+    __syncthreads();
+    if (active) {
+      // Thomas on the segment with boundary values y_{s-1} and y_s
+      float gp[2], x[2], gv[2][M - 1];
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        x[j] = X[3][xo + j];
+        gp[j] = (s > 0) ? X[3][xo - kT2Pitch + j] : 0.0f;
+      }
+#pragma unroll
+      for (int t = 0; t < M - 1; ++t) {
+        const float a = coef[s0 + t].a;
+        const float2 d = *reinterpret_cast<const float2*>(in + (s0 + t) * TLT + l0);
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          gp[j] = fmaf(-a, gp[j], j ? d.y : d.x) * inv[j][t];
+          gv[j][t] = gp[j];
+        }
+      }
+      store_pair<FMT>(o0, o1, (s0 + M - 1) * TLT + l0, x[0], x[1]);
+#pragma unroll
+      for (int t = M - 2; t >= 0; --t) {
+        const float c = coef[s0 + t].c;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) x[j] = fmaf(-c * inv[j][t], x[j], gv[j][t]);
+        store_pair<FMT>(o0, o1, (s0 + t) * TLT + l0, x[0], x[1]);
+      }
+    }
+    ptx::fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0 && !exhausted) {        // the input stage is free: refill it
+      issue(i + S, claim);
+      if (!exhausted) claim = atomicAdd(next_tile, 1);
+    }
+    if (!(singular && tile == 0)) {
+      if (tid == 0) {
+        for (int b = 0; b < geo.nb; ++b) {
+          const int off = b * geo.rb * TLT * O::EB;
+          ptx::tma_store_2d(&map_o0, ptx::smem_u32(static_cast<uint8_t*>(o0) + off), tile * TLT, b * geo.rb);
+          if (O::NPL == 2)
+            ptx::tma_store_2d(&map_o1, ptx::smem_u32(static_cast<uint8_t*>(o1) + off), tile * TLT, b * geo.rb);
+        }
+        ptx::bulk_commit();
+      }
+    } else {                             // the null line is not ours to write
+      for (int e = tid; e < TLT * nz; e += blockDim.x) {
+        const int ll = e % TLT, k = e / TLT;
+        if (ll == 0 || ll >= lines) continue;
+        copy_elem<FMT>(o0, o1, e, t3_0, t3_1, ll + static_cast<long long>(k) * lines);
+      }
+      __syncthreads();                   // the output tile is rewritten by the next tile
+    }
+  }
+  if (tid == 0) {
+    if (!ok)   // the loads of local tiles i .. issued - 1 may still be landing
+      for (long long k = i; k < issued; ++k)
+        ptx::mbar_wait(ptx::smem_u32(&full[k % S]), static_cast<uint32_t>((k / S) & 1), err,
+                       ptx::kErrWaitDrain);
     ptx::bulk_wait_all();
   }
 }
@@ -1582,6 +1889,77 @@ cudaError_t launch_thomas_m(const tpt_plan_s* p, const MixedWork& w, cudaStream_
   return cudaGetLastError();
 }
 
+// Segment length of thomas2_kernel for Nz rows: the candidate M <= 16 whose
+// ceil(Nz / M) <= 32 segments leave the fewest padding rows (ties: the
+// smaller M); 0 when Nz > 512.
+int thomas2_m(int nz) {
+  static const int cand[] = {4, 8, 12, 16};
+  int best = 0, pad = 1 << 30;
+  for (int m : cand) {
+    const int nseg = (nz + m - 1) / m;
+    if (nseg > kT2Slots) continue;
+    if (nseg * m - nz < pad) {
+      pad = nseg * m - nz;
+      best = m;
+    }
+  }
+  return best;
+}
+
+template <int FMT, int M>
+cudaError_t launch_thomas2_m(const tpt_plan_s* p, const MixedWork& w, cudaStream_t s) {
+  using O = T3Fmt<FMT>;
+  constexpr int TLT = 32;
+  const MixedTables& m = p->mixed;
+  const long long lines = static_cast<long long>(m.ldy) * p->n[0];
+  const int nz = p->n[2];
+  const long long ntiles = (lines + TLT - 1) / TLT;
+  if (ntiles <= 0) return cudaSuccess;
+  if (lines + TLT > 0x7fffffffLL) return cudaErrorInvalidValue;
+  ThomasGeom geo;
+  if (!thomas_geom(nz, M, TLT, O::NPL, O::EB, &geo, kT2SmemBudget)) return cudaErrorInvalidConfiguration;
+  if (geo.nseg > kT2Slots) return cudaErrorInvalidConfiguration;
+  CUtensorMap mi, mo0, mo1;
+  if (!tc::make_plain_map(&mi, w.B[0], 4, lines, nz, lines * 4, TLT, geo.rb)) return cudaErrorInvalidValue;
+  if (!tc::make_plain_map(&mo0, w.A[0], O::EB, lines, nz, lines * O::EB, TLT, geo.rb)) return cudaErrorInvalidValue;
+  if (O::NPL == 2) {
+    if (!tc::make_plain_map(&mo1, w.A[1], O::EB, lines, nz, lines * O::EB, TLT, geo.rb))
+      return cudaErrorInvalidValue;
+  } else {
+    mo1 = mo0;
+  }
+  int* next_tile = reinterpret_cast<int*>(w.scal + 14);
+  cudaError_t e = cudaMemsetAsync(next_tile, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  const size_t smem = 1024 + static_cast<size_t>(geo.coef_bytes) + static_cast<size_t>(geo.stages) * geo.in_bytes +
+                      static_cast<size_t>(geo.out_bytes);
+  auto kern = thomas2_kernel<FMT, M>;
+  // a fixed cap (see launch_thomas_m)
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kT2SmemBudget);
+  if (e != cudaSuccess) return e;
+  if (smem > static_cast<size_t>(kT2SmemBudget)) return cudaErrorInvalidConfiguration;
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->dev);
+  const long long grid = ntiles < sms ? ntiles : sms;
+  note_launch(1);
+  kern<<<static_cast<unsigned>(grid), kThomasThreads, smem, s>>>(
+      mi, mo0, mo1, geo, p->n[0], p->n[1], nz, m.ldy, static_cast<int>(ntiles), next_tile, w.A[0], w.A[1],
+      m.lam_f[0], m.lam_f[1], m.zrows_f, m.zrows_f + nz, m.zrows_f + 2 * nz, static_cast<float>(p->alpha),
+      static_cast<float>(p->beta), p->singular ? 1 : 0, reinterpret_cast<int*>(w.scal + 15), w.skip);
+  return cudaGetLastError();
+}
+
+// Thomas kernel for a plan: 1 one line per thread (thomas_tma_kernel), 2 two
+// lines per thread (thomas2_kernel); `variant` 0 picks the two-line kernel
+// where its segments are at least 8 rows long (Nz from 193 to 512), where it
+// has work for all but a few of its threads.
+int thomas_variant(int nz, int variant) {
+  if (variant == 1) return 1;
+  const int m2 = thomas2_m(nz);
+  if (variant == 2) return m2 > 0 ? 2 : 1;
+  return (m2 >= 8 && nz > 192) ? 2 : 1;
+}
+
 // Step 2.3: T3 = modal Thomas solve of T2 (float32, in B) into A; the null
 // line of a singular problem on the second stream.
 template <int FMT>
@@ -1606,7 +1984,15 @@ cudaError_t launch_thomas(const tpt_plan_s* p, const MixedWork& w, cudaStream_t 
   cudaError_t e = cudaErrorInvalidConfiguration;
   int tlt = 0, mm = 0;
   thomas_shape(nz, &tlt, &mm);
-  if (tlt == 32) {
+  if (thomas_variant(nz, m.thomas_kernel) == 2) {
+    switch (thomas2_m(nz)) {
+      case 4: e = launch_thomas2_m<FMT, 4>(p, w, s); break;
+      case 8: e = launch_thomas2_m<FMT, 8>(p, w, s); break;
+      case 12: e = launch_thomas2_m<FMT, 12>(p, w, s); break;
+      case 16: e = launch_thomas2_m<FMT, 16>(p, w, s); break;
+      default: break;
+    }
+  } else if (tlt == 32) {
     switch (mm) {
       case 4: e = launch_thomas_m<FMT, 4, 32>(p, w, s); break;
       case 8: e = launch_thomas_m<FMT, 8, 32>(p, w, s); break;
@@ -2362,6 +2748,27 @@ int mixed_info(const tpt_plan_s* p, const double* h, tpt_info* info) {
   if (!std::isfinite(rel)) return TPT_ERR_NONFINITE;
   if (p->rtol > 0.0 && !(rel <= p->rtol)) return TPT_ERR_NOT_CONVERGED;
   return TPT_OK;
+}
+
+int mixed_thomas_test(tpt_plan_s* p, const float* t2, void* t3_0, void* t3_1, void* work, cudaStream_t s) {
+  if (!p || p->precision == TPT_PREC_FP64 || !t2 || !t3_0 || !work) return TPT_ERR_INVALID_ARG;
+  if (p->mixed.fmt == kFmtSplit && !t3_1) return TPT_ERR_INVALID_ARG;
+  MixedWork w = carve(p, work);
+  MX_CUDA(cudaMemsetAsync(w.scal, 0, 256, s));   // stop flag, tile counter and error flag cleared
+  w.B[0] = const_cast<float*>(t2);
+  w.A[0] = t3_0;
+  w.A[1] = t3_1;
+  cudaError_t e;
+  switch (p->mixed.fmt) {
+    case kFmtSplit: e = launch_thomas<kFmtSplit>(p, w, s); break;
+    case kFmtBF16: e = launch_thomas<kFmtBF16>(p, w, s); break;
+    default: e = launch_thomas<kFmtF32>(p, w, s); break;
+  }
+  MX_CUDA(e);
+  int errflag = 0;
+  MX_CUDA(cudaMemcpyAsync(&errflag, w.scal + 15, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MX_CUDA(cudaStreamSynchronize(s));
+  return errflag ? TPT_ERR_TIMEOUT : TPT_OK;
 }
 
 int tc_gemm_test(int precision, int M, int N, int K, const double* A, const double* B, double* D,

@@ -94,7 +94,8 @@ struct MixedTables {
   int gemm_bn[4] = {0, 0, 0, 0};
   int gemm_ctas[4] = {0, 0, 0, 0};
   int gemm_pair[4] = {0, 0, 0, 0};
-  int res_kernel = 0;               // residual: 0 automatic, 1 direct loads, 2 TMA-staged tiles  // two-CTA operand sharing (0 none, 1 share B, 2 share A)
+  int res_kernel = 0;               // residual: 0 automatic, 1 direct loads, 2 TMA-staged tiles
+  int thomas_kernel = 0;            // modal Thomas: 0 automatic, 1 one line per thread, 2 two lines
 };
 
 struct FftTables {    // device tables of a Fourier-transformed direction
@@ -222,6 +223,9 @@ int mixed_set_beta(tpt_plan_s* p);   // rescale the residual tables after a coef
 size_t mixed_workspace_bytes(const tpt_plan_s* p);
 int mixed_solve(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStream_t s,
                 tpt_info* info);
+// The modal Thomas step of a mixed plan on its own (kernel tests): T2 float32
+// in the (q, p, k) layout with rows of ldy, T3 planes in the operand format.
+int mixed_thomas_test(tpt_plan_s* p, const float* t2, void* t3_0, void* t3_1, void* work, cudaStream_t s);
 int tc_gemm_test(int precision, int M, int N, int K, const double* A, const double* B, double* D,
                  void* work, int dev, cudaStream_t s, int tile = 0, int pair = 0);
 int tc_gemm_out_test(int precision, int M, int N, int K, const double* A, const double* B, int out_kind,

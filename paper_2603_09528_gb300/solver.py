@@ -257,6 +257,9 @@ class Plan:
         t = (C.c_int * 4)(*[int(v) for v in pairs])
         check(lib.tpt_plan_set_pairing(self._h, t), "tpt_plan_set_pairing")
 
+    def set_thomas_kernel(self, variant):
+        check(lib.tpt_plan_set_thomas_kernel(self._h, int(variant)), "tpt_plan_set_thomas_kernel")
+
     def set_residual_kernel(self, variant):
         """0 automatic, 1 direct loads, 2 TMA-staged plane tiles (mixed plans)."""
         check(lib.tpt_plan_set_residual_kernel(self._h, int(variant)), "tpt_plan_set_residual_kernel")

@@ -426,3 +426,96 @@ def test_pointer_guard_on_the_gpu():
                                        C.byref(flag)) == L.TPT_OK
     assert flag.value == 0
 
+
+
+def _thomas_f32_sequential(fh, lx, ly, dz, alpha, beta):
+    """The plain Thomas recurrence in float32 (numpy, vectorised over lines):
+    the accuracy a float32 modal solve can be expected to reach per line."""
+    f32 = np.float32
+    shift = (f32(alpha) + f32(beta) * (lx.astype(f32)[:, None] + ly.astype(f32)[None, :])).astype(f32)
+    a, b, c = (f32(beta) * dz.a.astype(f32)), (f32(beta) * dz.b.astype(f32)), (f32(beta) * dz.c.astype(f32))
+    nz = fh.shape[2]
+    cp = np.zeros(fh.shape, f32)
+    dp = np.zeros(fh.shape, f32)
+    m = b[0] + shift
+    cp[:, :, 0] = c[0] / m
+    dp[:, :, 0] = fh[:, :, 0] / m
+    for k in range(1, nz):
+        m = (b[k] + shift) - a[k] * cp[:, :, k - 1]
+        cp[:, :, k] = c[k] / m
+        dp[:, :, k] = (fh[:, :, k] - a[k] * dp[:, :, k - 1]) / m
+    x = np.zeros(fh.shape, f32)
+    x[:, :, -1] = dp[:, :, -1]
+    for k in range(nz - 2, -1, -1):
+        x[:, :, k] = dp[:, :, k] - cp[:, :, k] * x[:, :, k + 1]
+    return x.astype(np.float64)
+
+
+def _line_errors(got, ref):
+    scale = np.abs(ref).max(axis=2)
+    return np.abs(got - ref).max(axis=2) / np.where(scale > 0, scale, 1.0)
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("nz", [33, 200, 256, 387, 512])
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
+@pytest.mark.parametrize("coef", [(1.0, -5e-4), (0.0, 1.0)])
+def test_mixed_thomas_kernels_match_the_oracle_recurrence(variant, nz, prec, coef):
+    """The float32 modal Thomas step of the mixed path (partition method, both
+    kernels) against the oracle's float64 recurrence on the same float32
+    inputs: every line within a small multiple of what a plain sequential
+    float32 Thomas sweep reaches on that line (near-singular Poisson lines
+    lose digits in any float32 solve), and the bulk near float32 rounding.
+    Nx = 20 with Ny = 12 (padded to 16 operand rows) gives 10 tiles of 32
+    lines with dummy padding lines; Nz = 33, 200 and 387 leave padding rows."""
+    n = (20, 12, nz)
+    bcs = [(1, 1)] * 3
+    dirs = O.make_dirs(n, (1.5, 2.0, 2.5), bcs)
+    plan = tpt.Plan(n, [d.dxf for d in dirs], [d.dxc for d in dirs], bcs, xform=(tpt.GEMM, tpt.GEMM),
+                    alpha=coef[0], beta=coef[1], precision=PRECS[prec], rtol=1e-10, max_refine=30)
+    plan.set_thomas_kernel(variant)
+    lx, ly = plan.eigenvalues(0), plan.eigenvalues(1)
+    fh = S.uniform_rhs(n, 31).astype(np.float32).astype(np.float64)
+    sing = O.is_singular(dirs, coef[0])
+    nx, ny = n[0], n[1]
+    ldy = (ny + 7) // 8 * 8
+    t2 = np.zeros((nz, nx, ldy), np.float32)
+    t2[:, :, :ny] = fh.transpose(2, 0, 1)
+    t2d = torch.from_numpy(t2.ravel()).cuda()
+    if prec == "bf16x3":
+        o0 = torch.zeros(t2.size, dtype=torch.int16, device="cuda")
+        o1 = torch.zeros(t2.size, dtype=torch.int16, device="cuda")
+    else:
+        o0 = torch.zeros(t2.size, dtype=torch.float32, device="cuda")
+        o1 = None
+    work = plan.new_workspace()
+    st = L.lib.tpt_mixed_thomas(plan._h, C.c_void_p(t2d.data_ptr()), C.c_void_p(o0.data_ptr()),
+                                C.c_void_p(o1.data_ptr() if o1 is not None else 0), C.c_void_p(work.data_ptr()),
+                                C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == L.TPT_OK, L.lib.tpt_status_string(st)
+    if prec == "bf16x3":
+        def bf(t):
+            u = t.cpu().numpy().view(np.uint16).astype(np.uint32) << 16
+            return u.view(np.float32).astype(np.float64)
+        out = bf(o0) + bf(o1)
+    else:
+        out = o0.cpu().numpy().astype(np.float64)
+    got = out.reshape(nz, nx, ldy)[:, :, :ny].transpose(1, 2, 0)
+    ref_in = fh.copy()
+    if sing:   # the kernel projects the null line; give the references the projected line
+        w = dirs[2].dxf
+        ref_in[0, 0, :] -= np.sum(w * ref_in[0, 0, :]) / np.sum(w)
+    ref = O.thomas_modal(ref_in, lx, ly, dirs[2], coef[0], coef[1], (0, 0) if sing else None)
+    seq = _thomas_f32_sequential(ref_in, lx, ly, dirs[2], coef[0], coef[1])
+    if sing:
+        w = dirs[2].dxf
+        ref[0, 0, :] -= np.sum(w * ref[0, 0, :]) / np.sum(w)
+        seq[0, 0, :] = ref[0, 0, :]       # the null line is solved in float64 by its own kernel
+    e_got, e_seq = _line_errors(got, ref), _line_errors(seq, ref)
+    print("thomas", variant, nz, prec, coef, "max", e_got.max(), "median", np.median(e_got),
+          "seq max", e_seq.max(), "seq median", np.median(e_seq))
+    # the T3 format rounds each value once more: a bf16 hi/lo pair keeps ~16
+    # significant bits (2^-17 relative), float32 (the tf32 path) all 24
+    fmt = 2.0 ** -16 if prec == "bf16x3" else 0.0
+    assert np.all(e_got <= 16.0 * e_seq + 4e-6 + fmt), (e_got.max(), e_seq.max())
+    assert np.median(e_got) <= 2.0 * np.median(e_seq) + 1e-6 + fmt / 2
