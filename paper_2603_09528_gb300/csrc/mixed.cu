@@ -617,12 +617,16 @@ thomas2_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_constant
     const float* in = reinterpret_cast<const float*>(in_base + static_cast<size_t>(st) * geo.in_bytes);
 
     float shift[2];
+    {
+      // one division per tile: ldy is even and l0 is even, so the thread's
+      // second line L + 1 lies in the same row p of modes as its first
+      const int L = tile * TLT + l0;
+      const int p = L / ldy, q = L - p * ldy;
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int L = tile * TLT + l0 + j;
-      int q = L % ldy, p = L / ldy;
-      if (L >= lines || q >= ny) q = p = 0;   // padding line: dummy shift
-      shift[j] = alpha + beta * (lamx[p] + lamy[q]);
+      for (int j = 0; j < 2; ++j) {
+        const bool real = L + j < lines && q + j < ny;   // else a padding line: dummy shift
+        shift[j] = alpha + beta * (lamx[real ? p : 0] + lamy[real ? q + j : 0]);
+      }
     }
 
     // forward elimination of the interior rows (as in thomas_tma_kernel),
@@ -695,39 +699,44 @@ thomas2_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_constant
       X[3][xo + j] = rd[j];
     }
     __syncthreads();
-    // reduced systems: warp w takes lines 2w and 2w + 1, lane r interface row r
+    // reduced systems: warp w takes lines 2w and 2w + 1, lane r interface row
+    // r.  Parallel cyclic reduction on rows scaled to a unit diagonal
+    // (a x_{r-d} + x_r + c x_{r+d} = d): eliminating both neighbours gives
+    //   a' = -a a_{r-d},  c' = -c c_{r+d},  b' = 1 - a c_{r-d} - c a_{r+d},
+    //   d' = d - a d_{r-d} - c d_{r+d},  then the row is scaled by 1 / b'.
+    // Row 0 has a = 0 and row 31 has c = 0, and that stays so for every row
+    // whose neighbour at distance d lies outside (its a or c is a product
+    // with such a zero), so the shuffles that fall off an end (which return
+    // the lane's own values) are always multiplied by zero.
     {
       const int r = lane;
-      float A[2], B[2], Cc[2], D[2];
+      float A[2], Cc[2], D[2];
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         const int ix = r * kT2Pitch + 2 * warp + j;
-        A[j] = X[0][ix];
-        B[j] = X[1][ix];
-        Cc[j] = X[2][ix];
-        D[j] = X[3][ix];
+        const float ib = __fdividef(1.0f, X[1][ix]);
+        A[j] = X[0][ix] * ib;
+        Cc[j] = X[2][ix] * ib;
+        D[j] = X[3][ix] * ib;
       }
 #pragma unroll
       for (int dlt = 1; dlt < kT2Slots; dlt <<= 1) {
-        const bool hasm = r >= dlt, hasp = r + dlt < kT2Slots;
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-          const float Am = __shfl_up_sync(0xffffffffu, A[j], dlt), Bm = __shfl_up_sync(0xffffffffu, B[j], dlt);
-          const float Cm = __shfl_up_sync(0xffffffffu, Cc[j], dlt), Dm = __shfl_up_sync(0xffffffffu, D[j], dlt);
-          const float Ap = __shfl_down_sync(0xffffffffu, A[j], dlt), Bp = __shfl_down_sync(0xffffffffu, B[j], dlt);
-          const float Cp = __shfl_down_sync(0xffffffffu, Cc[j], dlt), Dp = __shfl_down_sync(0xffffffffu, D[j], dlt);
-          const float k1 = hasm ? __fdividef(A[j], Bm) : 0.0f;
-          const float k2 = hasp ? __fdividef(Cc[j], Bp) : 0.0f;
-          const float nA = hasm ? -Am * k1 : 0.0f;
-          const float nC = hasp ? -Cp * k2 : 0.0f;
-          B[j] = B[j] - (hasm ? Cm * k1 : 0.0f) - (hasp ? Ap * k2 : 0.0f);
-          D[j] = D[j] - (hasm ? Dm * k1 : 0.0f) - (hasp ? Dp * k2 : 0.0f);
-          A[j] = nA;
-          Cc[j] = nC;
+          const float Am = __shfl_up_sync(0xffffffffu, A[j], dlt), Cm = __shfl_up_sync(0xffffffffu, Cc[j], dlt);
+          const float Dm = __shfl_up_sync(0xffffffffu, D[j], dlt);
+          const float Ap = __shfl_down_sync(0xffffffffu, A[j], dlt), Cp = __shfl_down_sync(0xffffffffu, Cc[j], dlt);
+          const float Dp = __shfl_down_sync(0xffffffffu, D[j], dlt);
+          const float b = fmaf(-A[j], Cm, fmaf(-Cc[j], Ap, 1.0f));
+          const float d = fmaf(-A[j], Dm, fmaf(-Cc[j], Dp, D[j]));
+          const float ib = __fdividef(1.0f, b);
+          A[j] = -A[j] * Am * ib;
+          Cc[j] = -Cc[j] * Cp * ib;
+          D[j] = d * ib;
         }
       }
 #pragma unroll
-      for (int j = 0; j < 2; ++j) X[3][r * kT2Pitch + 2 * warp + j] = __fdividef(D[j], B[j]);
+      for (int j = 0; j < 2; ++j) X[3][r * kT2Pitch + 2 * warp + j] = D[j];
     }
     if (tid == 0) ptx::bulk_wait_read<0>();   // the output tile of tile i-1 has been stored
     __syncthreads();
