@@ -142,7 +142,10 @@ int tpt_workspace_bytes(tpt_plan plan, size_t* bytes);
  * solution with zero cell-volume-weighted mean after removing that mean from
  * f.  `info` may be NULL; it is filled when the call returns if rtol > 0,
  * else after `stream` is synchronised.  Errors: INVALID_ARG, CUDA,
- * NOT_CONVERGED (phi holds the last iterate), NONFINITE, TIMEOUT.          */
+ * NOT_CONVERGED (phi holds the last iterate), NONFINITE (a NaN or Inf in f
+ * or in a residual; the float64 path reports it as a status when rtol > 0,
+ * otherwise as a non-finite info->rel_residual once `stream` is
+ * synchronised), TIMEOUT.                                                  */
 int tpt_solve(tpt_plan plan, const double* f_dev, double* phi_dev, void* work_dev,
               void* stream, tpt_info* info);
 
@@ -475,6 +478,23 @@ typedef struct {
 #define TPT_STEP_SOLVE 4        /* tpt_solve                                         */
 #define TPT_STEP_D2H 5          /* solution copy to the host                         */
 #define TPT_STEP_SYNC 6         /* the slot stream's final synchronisation           */
+
+/* ---- failure-detection tests (no GPU fault involved) --------------------- */
+/* Allocation-failure injection: after `after` (>= 0) more device
+ * allocations of the library (plan and cache tables, server request
+ * buffers) succeed, every later one fails as if the device were out of
+ * memory, and the calls that made them return TPT_ERR_OOM (a server result
+ * records cudaErrorMemoryAllocation and the step); after < 0 turns the
+ * injection off.  Process-wide.  The paper has no counterpart.            */
+int tpt_test_fail_allocations(long long after);
+
+/* A 256 x 256 x 64 bf16 transform GEMM on the current device whose TMA
+ * producer issues no loads, with `polls` polls for every bounded
+ * mbarrier wait (about 0.1 ms for 1024): the waits run out, the kernel frees
+ * its tensor memory and returns, and the call reports TPT_ERR_TIMEOUT.  The
+ * context stays usable.  work_dev: at least 1 MiB of device scratch.  The
+ * paper has no counterpart.                                                */
+int tpt_test_gemm_timeout(unsigned polls, void* work_dev, size_t work_bytes, void* stream);
 
 /* Name of a cudaError_t value as reported in tpt_result.cuda_error.        */
 const char* tpt_cuda_error_name(int cuda_error);

@@ -121,6 +121,8 @@ SIGNATURES = [
     ("tpt_kernel_launches", C.c_int, [C.POINTER(C.c_ulonglong)]),
     ("tpt_pointer_on_device", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     ("tpt_cuda_error_name", C.c_char_p, [C.c_int]),
+    ("tpt_test_fail_allocations", C.c_int, [C.c_longlong]),
+    ("tpt_test_gemm_timeout", C.c_int, [C.c_uint, C.c_void_p, C.c_size_t, C.c_void_p]),
     ("tpt_set_stage_timing", C.c_int, [C.c_void_p, C.c_int]),
     ("tpt_set_refinement", C.c_int, [C.c_void_p, C.c_double, C.c_int]),
     ("tpt_plan_autotune", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]),

@@ -94,6 +94,7 @@ size_t hash_bytes(const void* p, size_t n, size_t h) {
 int DevArena::alloc(size_t n, void** out) {
   void* ptr = nullptr;
   const size_t sz = n ? n : 16;
+  if (injected_alloc_failure()) return TPT_ERR_OOM;
   cudaError_t e = pool ? cudaMallocFromPoolAsync(&ptr, sz, pool, stream) : cudaMalloc(&ptr, sz);
   if (e != cudaSuccess) {
     cudaGetLastError();

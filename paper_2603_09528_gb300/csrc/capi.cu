@@ -188,6 +188,11 @@ int fp64_solve(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStre
     TPT_TRY(inner_fp64(p, r, phi, true, t1, t2, ds, s));
     ++iters;
   }
+  // the canonical gauge: phi shifted to zero volume-weighted mean in physical
+  // space (the null line's gauge fixes it only up to the eigenvectors'
+  // rounding, ~1e-12 of phi on 512-point stretched grids); the final residual
+  // above is unaffected, a constant being in the operator's null space
+  if (p->singular) TPT_CUDA(tpt::remove_weighted_mean(p, phi, r, rb, ds + 9, s));
   if (adaptive && !converged) status = TPT_ERR_NOT_CONVERGED;
   if (info && !enqueue_only) {
     if (adaptive) {
@@ -370,6 +375,19 @@ void note_cuda_error(cudaError_t e) {
   if (e != cudaSuccess) t_last_cuda_error = e;
 }
 cudaError_t last_cuda_error() { return t_last_cuda_error; }
+namespace {
+std::atomic<long long> g_alloc_budget{-1};   // < 0: no injection
+}
+bool injected_alloc_failure() {
+  long long b = g_alloc_budget.load(std::memory_order_relaxed);
+  while (b > 0 && !g_alloc_budget.compare_exchange_weak(b, b - 1, std::memory_order_relaxed)) {
+  }
+  if (b == 0) {
+    note_cuda_error(cudaErrorMemoryAllocation);
+    return true;
+  }
+  return false;
+}
 void clear_cuda_error() { t_last_cuda_error = cudaSuccess; }
 unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 void forget_launches(unsigned long long k) { g_launches.fetch_sub(k, std::memory_order_relaxed); }
@@ -422,6 +440,18 @@ int tpt_kernel_launches(unsigned long long* count) {
   if (!count) return TPT_ERR_INVALID_ARG;
   *count = tpt::g_launches.load(std::memory_order_relaxed);
   return TPT_OK;
+}
+
+int tpt_test_fail_allocations(long long after) {
+  tpt::g_alloc_budget.store(after < 0 ? -1 : after, std::memory_order_relaxed);
+  return TPT_OK;
+}
+
+int tpt_test_gemm_timeout(unsigned polls, void* work_dev, size_t work_bytes, void* stream) {
+  if (!work_dev || polls == 0 || work_bytes < (1u << 20)) return TPT_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return cuda_status(cudaGetLastError());
+  return tpt::gemm_timeout_test(polls, work_dev, dev, static_cast<cudaStream_t>(stream));
 }
 
 const char* tpt_cuda_error_name(int cuda_error) {

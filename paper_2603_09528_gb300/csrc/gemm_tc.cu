@@ -211,6 +211,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
   constexpr uint16_t kPairMask = 0x3;
   const int nk = (g.K + C::BK - 1) / C::BK;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(g.err);
+  const uint32_t polls = g.polls ? g.polls : (1u << 22);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) {
@@ -253,8 +254,12 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
         const long long round = it / C::STAGES;
         if (round > 0)
           ok = ptx::mbar_wait(ptx::smem_u32(&bars[C::STAGES + s]), static_cast<uint32_t>((round - 1) & 1), g.err,
-                              ptx::kErrWaitEmpty);
+                              ptx::kErrWaitEmpty, polls);
         if (!ok || (abort_flag && *abort_flag)) {
+          ok = false;
+          break;
+        }
+        if (g.drop_loads) {      // failure-detection test: no stage ever fills
           ok = false;
           break;
         }
@@ -297,7 +302,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
     const long long first = it > C::STAGES ? it - C::STAGES : 0;
     for (long long k = first; k < it; ++k)
       ptx::mbar_wait(ptx::smem_u32(&bars[k % C::STAGES]), static_cast<uint32_t>((k / C::STAGES) & 1), g.err,
-                     ptx::kErrWaitDrain);
+                     ptx::kErrWaitDrain, polls);
   } else if (warp == 1 && lane == 0) {
     // -------------------------------------------------------- MMA issuer
     constexpr uint32_t idesc = ptx::instr_desc(KIND == kKindBF16 ? 1u : 2u, BM, BN);
@@ -308,14 +313,14 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
       const int b = tcount & 1, use = tcount >> 1;
       if (use > 0)
         ok = ptx::mbar_wait(ptx::smem_u32(&acce[b]), static_cast<uint32_t>((use - 1) & 1), g.err,
-                            ptx::kErrWaitAccum);
+                            ptx::kErrWaitAccum, polls);
       if (!ok || (abort_flag && *abort_flag)) break;
       ptx::tc_fence_after();
       const uint32_t d = tmem + static_cast<uint32_t>(b * BN);
       for (int kc = 0; kc < nk; ++kc, ++it) {
         const int s = static_cast<int>(it % C::STAGES);
         ok = ptx::mbar_wait(ptx::smem_u32(&bars[s]), static_cast<uint32_t>((it / C::STAGES) & 1), g.err,
-                            ptx::kErrWaitFull);
+                            ptx::kErrWaitFull, polls);
         if (!ok) break;
         ptx::tc_fence_after();
         const uint32_t sa = ptx::smem_u32(smem + s * C::STAGE);
@@ -344,7 +349,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
     // freed, also when a timed-out wait ended the loop early
     if (it > 0) {
       ptx::mma_commit(ptx::smem_u32(mdone));
-      ptx::mbar_wait(ptx::smem_u32(mdone), 0u, g.err, ptx::kErrWaitDrain);
+      ptx::mbar_wait(ptx::smem_u32(mdone), 0u, g.err, ptx::kErrWaitDrain, polls);
     }
   } else if (warp >= 2) {
     // ---------------------------------------------------------- epilogue
@@ -363,7 +368,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
     for (long long q = unit0; q < num_units; q += unit_step, ++tcount) {
       const int b = tcount & 1, use = tcount >> 1;
       const bool ok = ptx::mbar_wait(ptx::smem_u32(&accf[b]), static_cast<uint32_t>(use & 1), g.err,
-                                     ptx::kErrWaitAccum);
+                                     ptx::kErrWaitAccum, polls);
       ptx::tc_fence_after();
       const bool flagged = abort_flag && *abort_flag;
       // tcgen05.ld is warp-collective: decide for the whole warp

@@ -223,6 +223,84 @@ field_sums_kernel(int nx, int ny, int nz, const double* __restrict__ f, const do
   }
 }
 
+// Canonical gauge (reading R4): the volume-weighted mean of phi, summed
+// with error-free additions (TwoSum) so that the mean is exact to a few ulps
+// of the sum of |vol phi| whatever the cancellation, in two deterministic
+// levels: block partial sums as (hi, lo) pairs, then one block over them.
+__device__ __forceinline__ void two_sum_d(double a, double b, double& s, double& e) {
+  s = a + b;
+  const double bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void pair_add_d(double& hi, double& lo, double h2, double l2) {
+  double s, e;
+  two_sum_d(hi, h2, s, e);
+  hi = s;
+  lo += e + l2;
+}
+
+__global__ void __launch_bounds__(256)
+wsum_partial_fp64_kernel(int nx, int ny, int nz, const double* __restrict__ phi, const double* __restrict__ dxf,
+                         const double* __restrict__ dyf, const double* __restrict__ dzf, double2* partial) {
+  const long long lines = static_cast<long long>(ny) * nz;
+  double hi = 0.0, lo = 0.0;
+  for (long long L = blockIdx.x; L < lines; L += gridDim.x) {   // x-line (j, k) = L
+    const int j = static_cast<int>(L % ny), k = static_cast<int>(L / ny);
+    const double wyz = dyf[j] * dzf[k];
+    const double* row = phi + static_cast<long long>(nx) * L;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+      const double v = (dxf[i] * wyz) * row[i];
+      double s, e;
+      two_sum_d(hi, v, s, e);
+      hi = s;
+      lo += e;
+    }
+  }
+  __shared__ double sh[2][256];
+  sh[0][threadIdx.x] = hi;
+  sh[1][threadIdx.x] = lo;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      double h = sh[0][threadIdx.x], l = sh[1][threadIdx.x];
+      pair_add_d(h, l, sh[0][threadIdx.x + w], sh[1][threadIdx.x + w]);
+      sh[0][threadIdx.x] = h;
+      sh[1][threadIdx.x] = l;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = make_double2(sh[0][0], sh[1][0]);
+}
+
+// mean = (sum of the partial pairs) / volume, one block
+__global__ void __launch_bounds__(256)
+wsum_final_fp64_kernel(int nb, const double2* __restrict__ partial, double inv_vol, double* mean) {
+  double hi = 0.0, lo = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) pair_add_d(hi, lo, partial[b].x, partial[b].y);
+  __shared__ double sh[2][256];
+  sh[0][threadIdx.x] = hi;
+  sh[1][threadIdx.x] = lo;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      double h = sh[0][threadIdx.x], l = sh[1][threadIdx.x];
+      pair_add_d(h, l, sh[0][threadIdx.x + w], sh[1][threadIdx.x + w]);
+      sh[0][threadIdx.x] = h;
+      sh[1][threadIdx.x] = l;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *mean = (sh[0][0] + sh[1][0]) * inv_vol;
+}
+
+__global__ void __launch_bounds__(256) sub_scalar_kernel(long long n, const double* __restrict__ c,
+                                                          double* __restrict__ x) {
+  const double v = *c;
+  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n; i += stride)
+    x[i] -= v;
+}
+
 }  // namespace
 
 namespace {
@@ -238,6 +316,27 @@ cudaError_t add_fp64(long long n, const double* in, double* out, cudaStream_t s)
   const long long blocks = (n + 255) / 256;
   note_launch(1);
   add_kernel<<<static_cast<unsigned>(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(n, in, out);
+  return cudaGetLastError();
+}
+
+cudaError_t remove_weighted_mean(const tpt_plan_s* p, double* phi, void* scratch, size_t scratch_bytes,
+                                 double* mean, cudaStream_t s) {
+  int dev_sms = 152;
+  cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, p->dev);
+  const long long lines = static_cast<long long>(p->n[1]) * p->n[2];
+  long long cap = static_cast<long long>(scratch_bytes / sizeof(double2));
+  if (cap > 4LL * dev_sms) cap = 4LL * dev_sms;
+  if (cap < 1) return cudaErrorInvalidValue;
+  const int nb = static_cast<int>(lines < cap ? lines : cap);
+  double2* partial = static_cast<double2*>(scratch);
+  note_launch(3);
+  wsum_partial_fp64_kernel<<<nb, 256, 0, s>>>(p->n[0], p->n[1], p->n[2], phi, p->d_dxf[0], p->d_dxf[1],
+                                              p->d_dxf[2], partial);
+  wsum_final_fp64_kernel<<<1, 256, 0, s>>>(nb, partial, 1.0 / p->vol, mean);
+  const long long n = static_cast<long long>(p->n[0]) * p->n[1] * p->n[2];
+  long long g = (n + 255) / 256;
+  if (g > 16LL * dev_sms) g = 16LL * dev_sms;
+  sub_scalar_kernel<<<static_cast<unsigned>(g), 256, 0, s>>>(n, mean, phi);
   return cudaGetLastError();
 }
 

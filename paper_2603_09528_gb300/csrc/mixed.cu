@@ -2804,6 +2804,30 @@ int tc_gemm_test(int precision, int M, int N, int K, const double* A, const doub
   return TPT_OK;
 }
 
+int gemm_timeout_test(unsigned polls, void* work, int dev, cudaStream_t s) {
+  if (!work || polls == 0) return TPT_ERR_INVALID_ARG;
+  // a 256 x 256 x 64 bf16 GEMM whose producer issues no loads: the MMA
+  // warp's and the epilogue's bounded waits run out, record their codes in
+  // the error flag and return; nothing is read from the (valid) operands
+  constexpr int M = 256, N = 256, K = 64;
+  char* w = static_cast<char*>(work);
+  int* err = reinterpret_cast<int*>(w);
+  void* pa[2] = {w + 256, nullptr};
+  void* pb[2] = {w + 256 + align256(2 * M * K), nullptr};
+  void* out = w + 256 + align256(2 * M * K) + align256(2 * N * K);
+  MX_CUDA(cudaMemsetAsync(work, 0, 256, s));
+  tc::GemmOut g = gout(M, N, K, kBig, 0, M, out, nullptr, tc::kOutF32, 0, 0, err);
+  g.polls = polls;
+  g.drop_loads = 1;
+  g.tma_out = 0;
+  MX_CUDA(tc::gemm(tc::kKindBF16, 1, operand(pa, M, K, K), operand(pb, N, K, K), g, s));
+  int h = 0;
+  MX_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MX_CUDA(cudaStreamSynchronize(s));
+  (void)dev;
+  return h ? TPT_ERR_TIMEOUT : TPT_OK;
+}
+
 int tc_gemm_out_test(int precision, int M, int N, int K, const double* A, const double* B, int out_kind,
                      int rm, long long sm, long long sn, void* out0, void* out1, void* work, int dev,
                      cudaStream_t s, int tile, int tma_out, int pair) {

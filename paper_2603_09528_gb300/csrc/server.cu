@@ -158,7 +158,8 @@ struct tpt_server_s {
     int st = TPT_OK;
     *step = TPT_STEP_ALLOC;
     for (int i = 0; i < 3 && st == TPT_OK; ++i)
-      st = cuda_st(cudaMallocFromPoolAsync(&buf[i], sz[i], cache.buffer_pool(), s));
+      st = tpt::injected_alloc_failure() ? TPT_ERR_OOM
+                                         : cuda_st(cudaMallocFromPoolAsync(&buf[i], sz[i], cache.buffer_pool(), s));
     auto aligned = [](void* p) {
       return reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(p) + 255) & ~static_cast<uintptr_t>(255));
     };

@@ -41,6 +41,11 @@ struct GemmOut {
   int tma_out = 1;  // TMA-store epilogue where the output layout allows (split bf16,
                     // bf16 or float32 out, 128/256-column tiles, one CTA per tile)
   const int* skip = nullptr;   // device flag: the kernel returns at entry when it is nonzero
+  // Failure-detection tests only: polls of every bounded wait (0 = the
+  // default, about 2^22) and a producer that issues no loads, so that the
+  // waits run out and the kernel returns with TPT_ERR_TIMEOUT in *err.
+  unsigned polls = 0;
+  int drop_loads = 0;
 };
 
 // True when p points into device memory of the current device (not host,

@@ -185,6 +185,11 @@ void note_cuda_error(cudaError_t e);
 cudaError_t last_cuda_error();
 void clear_cuda_error();
 
+// Failure-detection tests: true when an armed allocation-failure injection
+// makes this device allocation fail (tpt_test_fail_allocations); the caller
+// then returns TPT_ERR_OOM exactly as for a real failed allocation.
+bool injected_alloc_failure();
+
 // Count of kernels this library has launched (all devices, all threads).
 void note_launch(unsigned long long k = 1);
 unsigned long long launch_count();
@@ -213,6 +218,12 @@ cudaError_t add_fp64(long long n, const double* in, double* out, cudaStream_t s)
 // sums[0..2] += (sum f^2, sum f, sum vol*f) over the field
 cudaError_t field_sums(const tpt_plan_s* p, const double* f, double* sums, cudaStream_t s);
 
+// phi -= its volume-weighted mean (the canonical gauge of a singular
+// problem, reading R4), summed exactly to a few ulps; scratch (16-byte
+// aligned) holds the block partial sums, *mean (device) receives the mean.
+cudaError_t remove_weighted_mean(const tpt_plan_s* p, double* phi, void* scratch, size_t scratch_bytes,
+                                 double* mean, cudaStream_t s);
+
 // r = (f - fshift) - (alpha I + beta L) phi; fshift (device scalar) may be NULL.
 cudaError_t residual_fp64(const tpt_plan_s* p, const double* f, const double* phi, double* r,
                           double* sums, const double* fshift, cudaStream_t s);
@@ -226,6 +237,9 @@ int mixed_solve(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStr
 // The modal Thomas step of a mixed plan on its own (kernel tests): T2 float32
 // in the (q, p, k) layout with rows of ldy, T3 planes in the operand format.
 int mixed_thomas_test(tpt_plan_s* p, const float* t2, void* t3_0, void* t3_1, void* work, cudaStream_t s);
+// A transform GEMM whose producer issues no loads, with `polls` polls per
+// bounded wait: TPT_ERR_TIMEOUT when the waits ran out and said so.
+int gemm_timeout_test(unsigned polls, void* work, int dev, cudaStream_t s);
 int tc_gemm_test(int precision, int M, int N, int K, const double* A, const double* B, double* D,
                  void* work, int dev, cudaStream_t s, int tile = 0, int pair = 0);
 int tc_gemm_out_test(int precision, int M, int N, int K, const double* A, const double* B, int out_kind,

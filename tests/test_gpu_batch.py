@@ -15,6 +15,15 @@ from _tpt import load
 pytestmark = pytest.mark.gpu
 tpt, L = load()
 
+# Bars of the refined mixed path: its own float-pair residual stops the
+# refinement at <= 1e-10 (relative 2-norm); the oracle's long-double residual
+# of the returned phi differs from it by float-pair rounding of r (~1e-13 of
+# |f| per point, measured below 2e-15 in the relative norm), hence 1e-10 plus
+# 1e-14.  The element-wise distance to the oracle's float64 solution is at
+# most ~1.2e-10 in these cases (measured), bounded here at 1e-9.
+RES_BAR = 1e-10 + 1e-14
+ERR_BAR = 1e-9
+
 NNN = [(1, 1)] * 3
 DND = [(2, 1), (1, 2), (2, 2)]
 PNN = [(0, 0), (1, 1), (1, 1)]
@@ -100,7 +109,7 @@ def _check_instances(specs, dirs, fs, phis, infos):
             r = O.residual(f, got, d, alpha, beta, np.longdouble)
             rel = float(np.sqrt(np.sum(r ** 2) / np.sum(f ** 2)))
             assert infos[i]["status"] == L.TPT_OK, infos[i]
-            assert infos[i]["rel_residual"] <= 1e-10 and rel <= 2e-10, (i, rel, infos[i])
+            assert infos[i]["rel_residual"] <= 1e-10 and rel <= RES_BAR, (i, rel, infos[i])
 
 
 def test_batch_instances_equal_standalone_and_oracle(batch):
@@ -184,7 +193,7 @@ def test_calibrated_batch_stops_on_the_device_and_reports_misses():
             assert infos[i]["status"] == L.TPT_OK and infos[i]["iters"] == used[i], (infos[i], used)
             r = O.residual(fs[i], tpt.field_to_host(phis[i], cases[i][0]), dirs[i], cases[i][3], cases[i][4],
                            np.longdouble)
-            assert float(np.sqrt(np.sum(r ** 2) / np.sum(fs[i] ** 2))) <= 2e-10
+            assert float(np.sqrt(np.sum(r ** 2) / np.sum(fs[i] ** 2))) <= RES_BAR
         zeros = [torch.zeros_like(t) for t in fs_dev]
         assert b.calibrate(zeros, phis, work) == [1, 1]
         infos = b.solve(fs_dev, phis, work, raise_errors=False)

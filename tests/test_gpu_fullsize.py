@@ -2,11 +2,12 @@
 Neumann walls) at its full size, solved in the launch configuration the
 benchmark times: split-bf16 transforms with autotuned tiles, refinement to a
 relative residual of 1e-10 decided on the device, repeated solves of one right
-side replayed as a CUDA graph.  The oracle cannot solve this size, so every
-check is a property that holds at any size, computed by oracle code on the
-host: the float64 residual of the returned phi, the zero volume-weighted mean
-of the canonical gauge, and the distance to the float64 path (which matches the
-oracle to 1e-12 at the sizes the oracle solves)."""
+side replayed as a CUDA graph.  The mixed solve is checked by properties that
+hold at any size, computed by oracle code on the host (the float64 residual
+of the returned phi, the zero volume-weighted mean of the canonical gauge, the
+distance to the float64 path); the float64 path itself is compared with the
+oracle's tensor solve element by element at this size (slow: the oracle
+takes about a minute on the host cores)."""
 import numpy as np
 import pytest
 import torch
@@ -19,6 +20,10 @@ pytestmark = pytest.mark.gpu
 tpt, L = load()
 
 N = (512, 512, 512)
+# the device stops the refinement at a float-pair residual <= 1e-10; the
+# oracle's float64 stencil of the returned phi differs by rounding (its own
+# floor is ~4e-15 relative at this size)
+RES_BAR = 1e-10 + 1e-13
 STRETCH = (1.5, 2.0, 2.5)
 BCS = [(1, 1)] * 3
 
@@ -53,7 +58,7 @@ def test_512cube_split_bf16_in_the_benchmark_configuration():
     torch.cuda.empty_cache()
 
     rel = _rel_residual(f, got, dirs)
-    assert rel <= 2e-10, rel
+    assert rel <= RES_BAR, rel
     assert abs(O.weighted_mean(got, dirs)) <= 1e-12 * np.abs(got).max()
 
     plan64 = tpt.Plan(N, [d.dxf for d in dirs], [d.dxc for d in dirs], BCS, xform=(tpt.GEMM, tpt.GEMM),
@@ -115,6 +120,25 @@ def test_batch_of_96_uneven_instances_in_the_benchmark_configuration():
         got = tpt.field_to_host(phis[t], inst[t]["n"])
         r = O.residual(f, got, dirs, inst[t]["alpha"], inst[t]["beta"])
         rel = float(np.sqrt(np.sum(r * r) / np.sum(f * f)))
-        assert rel <= 2e-10, (t, rel, infos[t])
+        assert rel <= RES_BAR, (t, rel, infos[t])
         if O.is_singular(dirs, inst[t]["alpha"]):
             assert abs(O.weighted_mean(got, dirs)) <= 1e-12 * np.abs(got).max()
+
+
+@pytest.mark.slow
+def test_512cube_float64_path_matches_the_oracle_elementwise():
+    """The float64 path at the benchmark's full size against the oracle's
+    tensor solve (Sec. 2.2.2 steps with one float64 refinement step, reading
+    R8), element by element, at the 1e-12 relative max-norm bar."""
+    dirs = O.make_dirs(N, STRETCH, BCS)
+    f = S.remove_weighted_mean(S.uniform_rhs(N, 4), [d.dxf for d in dirs])
+    plan64 = tpt.Plan(N, [d.dxf for d in dirs], [d.dxc for d in dirs], BCS, xform=(tpt.GEMM, tpt.GEMM),
+                      alpha=0.0, beta=1.0, precision=L.TPT_PREC_FP64, max_refine=1)
+    phi64, info = plan64.solve(tpt.field_to_device(f))
+    got = tpt.field_to_host(phi64, N)
+    del phi64, plan64
+    torch.cuda.empty_cache()
+    ref, _ = O.solve_tensor(f, dirs, 0.0, 1.0)
+    err = np.abs(got - ref).max() / np.abs(ref).max()
+    print("512^3 float64 path vs oracle: max rel err", err, "gpu rel residual", info["rel_residual"])
+    assert err <= 1e-12, err

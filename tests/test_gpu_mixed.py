@@ -13,6 +13,15 @@ from _tpt import load
 pytestmark = pytest.mark.gpu
 tpt, L = load()
 
+# Bars of the refined mixed path: its own float-pair residual stops the
+# refinement at <= 1e-10 (relative 2-norm); the oracle's long-double residual
+# of the returned phi differs from it by float-pair rounding of r (~1e-13 of
+# |f| per point, measured below 2e-15 in the relative norm), hence 1e-10 plus
+# 1e-14.  The element-wise distance to the oracle's float64 solution is at
+# most ~1.2e-10 in these cases (measured), bounded here at 1e-9.
+RES_BAR = 1e-10 + 1e-14
+ERR_BAR = 1e-9
+
 PRECS = {"bf16": L.TPT_PREC_MIXED_BF16, "bf16x3": L.TPT_PREC_MIXED_BF16X3, "tf32": L.TPT_PREC_MIXED_TF32}
 
 
@@ -87,8 +96,8 @@ def test_mixed_solve_reaches_rtol(prec, case):
     print("mixed", prec, case, "iters", info["iters"], "rel_res(gpu)", info["rel_residual"],
           "rel_res(oracle)", rel, "err vs fp64", err)
     assert info["rel_residual"] <= 1e-10
-    assert rel <= 2e-10
-    assert err <= 1e-7, err
+    assert rel <= RES_BAR
+    assert err <= ERR_BAR, err
 
 
 @pytest.mark.parametrize("prec", list(PRECS))
@@ -136,8 +145,8 @@ def test_mixed_ragged_sizes_and_boundaries(prec, bcs, coef):
     ref, _ = O.solve_tensor(f, dirs, *coef)
     err = np.abs(got - ref).max() / np.abs(ref).max()
     print("ragged", prec, bcs, coef, "iters", info["iters"], "rel_res", rel, "err", err)
-    assert info["rel_residual"] <= 1e-10 and rel <= 2e-10
-    assert err <= 1e-7
+    assert info["rel_residual"] <= 1e-10 and rel <= RES_BAR
+    assert err <= ERR_BAR, err
 
 
 @pytest.mark.parametrize("prec", ["bf16x3", "tf32"])
@@ -304,8 +313,9 @@ def test_tma_residual_equals_direct_loads_and_the_oracle(case):
     r = O.residual(f, got, dirs, *coef, np.longdouble)
     rel = float(np.sqrt(np.sum(r ** 2) / np.sum(f ** 2)))
     ref, _ = O.solve_tensor(f, dirs, *coef)
-    assert info["rel_residual"] <= 1e-10 and rel <= 2e-10, (info, rel)
-    assert np.abs(got - ref).max() <= 1e-7 * np.abs(ref).max()
+    print("tma-res", case, "rel", rel, "gpu", info["rel_residual"], "err", np.abs(got - ref).max() / np.abs(ref).max())
+    assert info["rel_residual"] <= 1e-10 and rel <= RES_BAR, (info, rel)
+    assert np.abs(got - ref).max() <= ERR_BAR * np.abs(ref).max()
 
 
 def test_adaptive_solve_replayed_as_graph_and_continued_past_the_planned_corrections():
@@ -335,8 +345,9 @@ def test_adaptive_solve_replayed_as_graph_and_continued_past_the_planned_correct
     _, info2 = plan.solve(f_dev, phi, work)
     ref2, _ = O.solve_tensor(f2, dirs, 0.0, 1.0)
     got2 = tpt.field_to_host(phi, n)
+    print("graph-rhs2 err", np.abs(got2 - ref2).max() / np.abs(ref2).max(), "gpu", info2["rel_residual"])
     assert info2["rel_residual"] <= 1e-10
-    assert np.abs(got2 - ref2).max() <= 1e-7 * np.abs(ref2).max()
+    assert np.abs(got2 - ref2).max() <= ERR_BAR * np.abs(ref2).max()
     # a zero right-hand side converges at once (one correction); the next,
     # non-zero one must then run past that plan
     plan0 = tpt.Plan(n, [d.dxf for d in dirs], [d.dxc for d in dirs], [(1, 1)] * 3, **kw)
@@ -407,8 +418,9 @@ def test_device_stopping_test_reports_misses_and_continues_after_a_graph_replay(
     _, info = plan.solve(f_dev, phi, work)
     ref, _ = O.solve_tensor(f, dirs, 0.0, 1.0)
     got = tpt.field_to_host(phi, n)
+    print("stop-test err", np.abs(got - ref).max() / np.abs(ref).max(), "gpu", info["rel_residual"])
     assert info["status"] == L.TPT_OK and info["rel_residual"] <= 1e-10 and info["iters"] > 1, info
-    assert np.abs(got - ref).max() <= 1e-7 * np.abs(ref).max()
+    assert np.abs(got - ref).max() <= ERR_BAR * np.abs(ref).max()
 
 
 def test_pointer_guard_on_the_gpu():

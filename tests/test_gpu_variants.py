@@ -2,7 +2,7 @@
 yz and z of Sec. 2.1 (x, or x and y, outside the operator: no transform along
 them), and face-centred unknowns between walls (node-Dirichlet rows on the
 face grid), each for the float64 path (1e-12) and the refined split-bf16
-path (residual 1e-10, error against the oracle 1e-7)."""
+path (residual 1e-10, error against the oracle 1e-9)."""
 import numpy as np
 import pytest
 
@@ -12,6 +12,15 @@ from _tpt import load
 
 pytestmark = pytest.mark.gpu
 tpt, L = load()
+
+# Bars of the refined mixed path: its own float-pair residual stops the
+# refinement at <= 1e-10 (relative 2-norm); the oracle's long-double residual
+# of the returned phi differs from it by float-pair rounding of r (~1e-13 of
+# |f| per point, measured below 2e-15 in the relative norm), hence 1e-10 plus
+# 1e-14.  The element-wise distance to the oracle's float64 solution is at
+# most ~1.2e-10 in these cases (measured), bounded here at 1e-9.
+RES_BAR = 1e-10 + 1e-14
+ERR_BAR = 1e-9
 
 X = O.NONE
 
@@ -33,8 +42,9 @@ def _check(prec, got, info, f, dirs, alpha, beta):
     else:
         r = O.residual(f, got, dirs, alpha, beta, np.longdouble)
         rel = float(np.sqrt(np.sum(r ** 2) / np.sum(f ** 2)))
-        assert info["rel_residual"] <= 1e-10 and rel <= 2e-10, (info, rel)
-        assert err <= 1e-7, err
+        print("variant rel", rel, "gpu", info["rel_residual"], "err", err)
+        assert info["rel_residual"] <= 1e-10 and rel <= RES_BAR, (info, rel)
+        assert err <= ERR_BAR, err
 
 
 PRECS = [L.TPT_PREC_FP64, L.TPT_PREC_MIXED_BF16X3]
