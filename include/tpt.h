@@ -471,6 +471,8 @@ typedef struct {
                                    TPT_STEP_* below                                  */
   int cuda_error;               /* the cudaError_t behind TPT_ERR_CUDA / _OOM, else 0;
                                    tpt_cuda_error_name() names it                    */
+  double t_copied, t_solved;    /* when the input copy and the solve had finished
+                                   (server clock; 0 if not reached)                  */
 } tpt_result;
 #define TPT_STEP_PLAN 1         /* plan creation (host setup, cached tables)        */
 #define TPT_STEP_ALLOC 2        /* request buffers from the server's pool            */

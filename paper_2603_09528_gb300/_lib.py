@@ -76,6 +76,8 @@ class tpt_result(C.Structure):
         ("device_bytes", C.c_size_t),
         ("failed_step", C.c_int),
         ("cuda_error", C.c_int),
+        ("t_copied", C.c_double),
+        ("t_solved", C.c_double),
     ]
 
 

@@ -176,6 +176,7 @@ struct tpt_server_s {
         st = cuda_st(cudaMemcpyAsync(f, r->f_host, bytes, cudaMemcpyHostToDevice, s));
         if (st == TPT_OK) st = cuda_st(cudaStreamSynchronize(s));
       }
+      r->res.t_copied = now();
       if (st == TPT_OK) {
         *step = TPT_STEP_SOLVE;
         if (r->npts >= kExclusivePoints) {
@@ -185,6 +186,7 @@ struct tpt_server_s {
           std::shared_lock<std::shared_mutex> g(compute_mu);
           st = tpt_solve(r->plan, f, phi, work, s, &r->res.info);
         }
+        r->res.t_solved = now();
         if (st == TPT_OK || st == TPT_ERR_NOT_CONVERGED) {
           const int cs = cuda_st(cudaMemcpyAsync(r->phi_host, phi, bytes, cudaMemcpyDeviceToHost, s));
           if (cs != TPT_OK) {

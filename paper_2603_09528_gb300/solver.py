@@ -356,6 +356,7 @@ class Server:
                     compat_defect=r.info.compat_defect, t_submit=r.t_submit, t_planned=r.t_planned,
                     t_admit=r.t_admit, t_done=r.t_done, device_bytes=int(r.device_bytes),
                     failed_step=int(r.failed_step), cuda_error=int(r.cuda_error),
+                    t_copied=r.t_copied, t_solved=r.t_solved,
                     cuda_error_name=(lib.tpt_cuda_error_name(int(r.cuda_error)) or b"?").decode())
 
     def now(self) -> float:
