@@ -177,13 +177,19 @@ __device__ __forceinline__ void unit_coords(const GemmOut& g, int num_m, int num
 // tile t-1.  Barriers: full/empty per smem stage (TMA <-> MMA), acc_full[b]
 // (MMA -> epilogue, one commit) and acc_empty[b] (epilogue -> MMA, one arrive
 // per epilogue warp).
-template <int KIND, int NPL, int BN, int OUT, int PAIR, int TMAO>
+//
+// Grouped launches (MULTI = 1, one CTA per tile): the units are the tiles of
+// every job of a device job table, in job order; a unit's job supplies its
+// tensor maps, sizes, output and stop flag, and the units of a stopped job
+// are passed over by all three roles alike.
+template <int KIND, int NPL, int BN, int OUT, int PAIR, int TMAO, int MULTI = 0>
 __global__ void __launch_bounds__(threads_of<OUT>(), 1)
 gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1,
                const __grid_constant__ CUtensorMap tB0, const __grid_constant__ CUtensorMap tB1,
                const __grid_constant__ CUtensorMap tO0, const __grid_constant__ CUtensorMap tO1,
-               const GemmOut g) {
-  if (g.skip && *g.skip) return;   // uniform over the grid: no barrier or TMEM is touched
+               const GemmOut g, const GemmJob* __restrict__ jobs, int njobs, long long total_units) {
+  static_assert(!MULTI || PAIR == 0, "grouped launches run one CTA per tile");
+  if (!MULTI && g.skip && *g.skip) return;   // uniform over the grid: no barrier or TMEM is touched
   using C = Cfg<KIND, NPL, BN>;
   static_assert(C::STAGES >= 2, "shared-memory ring needs two stages");
   extern __shared__ __align__(128) uint8_t smem_raw[];
@@ -204,7 +210,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
   const long long num_tiles = static_cast<long long>(num_m) * num_n;
   // work units: tiles, or tile pairs of a two-CTA cluster (the host checks
   // that the paired tile count is even)
-  const long long num_units = PAIR ? num_tiles / 2 : num_tiles;
+  const long long num_units = MULTI ? total_units : (PAIR ? num_tiles / 2 : num_tiles);
   const long long unit0 = PAIR ? blockIdx.x / 2 : blockIdx.x;
   const long long unit_step = PAIR ? gridDim.x / 2 : gridDim.x;
   const int rank = PAIR ? static_cast<int>(ptx::cluster_ctarank()) : 0;
@@ -212,6 +218,31 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
   const int nk = (g.K + C::BK - 1) / C::BK;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(g.err);
   const uint32_t polls = g.polls ? g.polls : (1u << 22);
+  // unit q: its tile origin, K chunks, output description and tensor maps
+  // (A0, A1, B0, B1, O0, O1); false when its job has stopped
+  auto resolve = [&](long long q, int& m0, int& n0, int& nkq, const GemmOut*& gq,
+                     const CUtensorMap*& mq) -> bool {
+    if constexpr (MULTI) {
+      int lo = 0, hi = njobs - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (jobs[mid].first <= q) lo = mid;
+        else hi = mid - 1;
+      }
+      const GemmJob& jb = jobs[lo];
+      gq = &jb.g;
+      mq = jb.map;
+      if (gq->skip && *gq->skip) return false;
+      tile_coords<BN>(*gq, jb.num_m, jb.num_n, q - jb.first, m0, n0);
+      nkq = (gq->K + C::BK - 1) / C::BK;
+    } else {
+      gq = &g;
+      mq = nullptr;
+      unit_coords<BN, PAIR>(g, num_m, num_n, q, rank, m0, n0);
+      nkq = nk;
+    }
+    return true;
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) {
@@ -238,24 +269,35 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
 
   if (warp == 0 && lane == 0) {
     // ------------------------------------------------------- TMA producer
-    ptx::prefetch_tmap(&tA0);
-    ptx::prefetch_tmap(&tB0);
-    if (NPL == 2) {
-      ptx::prefetch_tmap(&tA1);
-      ptx::prefetch_tmap(&tB1);
+    if (!MULTI) {
+      ptx::prefetch_tmap(&tA0);
+      ptx::prefetch_tmap(&tB0);
+      if (NPL == 2) {
+        ptx::prefetch_tmap(&tA1);
+        ptx::prefetch_tmap(&tB1);
+      }
     }
     bool ok = true;
     long long it = 0;
+    int* last_err = g.err;
     for (long long q = unit0; q < num_units && ok; q += unit_step) {
-      int m0, n0;
-      unit_coords<BN, PAIR>(g, num_m, num_n, q, rank, m0, n0);
-      for (int kc = 0; kc < nk; ++kc, ++it) {
+      int m0, n0, nkq;
+      const GemmOut* gq;
+      const CUtensorMap* mq;
+      if (!resolve(q, m0, n0, nkq, gq, mq)) continue;
+      const CUtensorMap* mA0 = MULTI ? &mq[0] : &tA0;
+      const CUtensorMap* mA1 = MULTI ? &mq[1] : &tA1;
+      const CUtensorMap* mB0 = MULTI ? &mq[2] : &tB0;
+      const CUtensorMap* mB1 = MULTI ? &mq[3] : &tB1;
+      volatile int* abort_q = MULTI ? reinterpret_cast<volatile int*>(gq->err) : abort_flag;
+      last_err = gq->err;
+      for (int kc = 0; kc < nkq; ++kc, ++it) {
         const int s = static_cast<int>(it % C::STAGES);
         const long long round = it / C::STAGES;
         if (round > 0)
-          ok = ptx::mbar_wait(ptx::smem_u32(&bars[C::STAGES + s]), static_cast<uint32_t>((round - 1) & 1), g.err,
+          ok = ptx::mbar_wait(ptx::smem_u32(&bars[C::STAGES + s]), static_cast<uint32_t>((round - 1) & 1), gq->err,
                               ptx::kErrWaitEmpty, polls);
-        if (!ok || (abort_flag && *abort_flag)) {
+        if (!ok || (abort_q && *abort_q)) {
           ok = false;
           break;
         }
@@ -269,29 +311,29 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
         const int kx = kc * C::BK;
         if (PAIR == 1) {          // own A; half of the shared B tile, to both CTAs
           const int hb = BN / 2;
-          ptx::tma_load_2d(ptx::smem_u32(st), &tA0, full, kx, m0);   // n0: the pair's common n-tile
-          ptx::tma_load_2d_mc(ptx::smem_u32(st + NPL * C::A_BYTES + rank * hb * C::SW), &tB0, full, kx,
+          ptx::tma_load_2d(ptx::smem_u32(st), mA0, full, kx, m0);   // n0: the pair's common n-tile
+          ptx::tma_load_2d_mc(ptx::smem_u32(st + NPL * C::A_BYTES + rank * hb * C::SW), mB0, full, kx,
                               n0 + rank * hb, kPairMask);
           if (NPL == 2) {
-            ptx::tma_load_2d(ptx::smem_u32(st + C::A_BYTES), &tA1, full, kx, m0);
-            ptx::tma_load_2d_mc(ptx::smem_u32(st + NPL * C::A_BYTES + C::B_BYTES + rank * hb * C::SW), &tB1, full,
+            ptx::tma_load_2d(ptx::smem_u32(st + C::A_BYTES), mA1, full, kx, m0);
+            ptx::tma_load_2d_mc(ptx::smem_u32(st + NPL * C::A_BYTES + C::B_BYTES + rank * hb * C::SW), mB1, full,
                                 kx, n0 + rank * hb, kPairMask);
           }
         } else if (PAIR == 2) {   // half of the shared A tile, to both CTAs; own B
           const int ha = BM / 2;
-          ptx::tma_load_2d_mc(ptx::smem_u32(st + rank * ha * C::SW), &tA0, full, kx, m0 + rank * ha, kPairMask);
-          ptx::tma_load_2d(ptx::smem_u32(st + NPL * C::A_BYTES), &tB0, full, kx, n0);
+          ptx::tma_load_2d_mc(ptx::smem_u32(st + rank * ha * C::SW), mA0, full, kx, m0 + rank * ha, kPairMask);
+          ptx::tma_load_2d(ptx::smem_u32(st + NPL * C::A_BYTES), mB0, full, kx, n0);
           if (NPL == 2) {
-            ptx::tma_load_2d_mc(ptx::smem_u32(st + C::A_BYTES + rank * ha * C::SW), &tA1, full, kx, m0 + rank * ha,
+            ptx::tma_load_2d_mc(ptx::smem_u32(st + C::A_BYTES + rank * ha * C::SW), mA1, full, kx, m0 + rank * ha,
                                 kPairMask);
-            ptx::tma_load_2d(ptx::smem_u32(st + NPL * C::A_BYTES + C::B_BYTES), &tB1, full, kx, n0);
+            ptx::tma_load_2d(ptx::smem_u32(st + NPL * C::A_BYTES + C::B_BYTES), mB1, full, kx, n0);
           }
         } else {
-          ptx::tma_load_2d(ptx::smem_u32(st), &tA0, full, kx, m0);
-          ptx::tma_load_2d(ptx::smem_u32(st + NPL * C::A_BYTES), &tB0, full, kx, n0);
+          ptx::tma_load_2d(ptx::smem_u32(st), mA0, full, kx, m0);
+          ptx::tma_load_2d(ptx::smem_u32(st + NPL * C::A_BYTES), mB0, full, kx, n0);
           if (NPL == 2) {
-            ptx::tma_load_2d(ptx::smem_u32(st + C::A_BYTES), &tA1, full, kx, m0);
-            ptx::tma_load_2d(ptx::smem_u32(st + NPL * C::A_BYTES + C::B_BYTES), &tB1, full, kx, n0);
+            ptx::tma_load_2d(ptx::smem_u32(st + C::A_BYTES), mA1, full, kx, m0);
+            ptx::tma_load_2d(ptx::smem_u32(st + NPL * C::A_BYTES + C::B_BYTES), mB1, full, kx, n0);
           }
         }
       }
@@ -301,7 +343,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
     // g.err, and every caller then treats the output as invalid)
     const long long first = it > C::STAGES ? it - C::STAGES : 0;
     for (long long k = first; k < it; ++k)
-      ptx::mbar_wait(ptx::smem_u32(&bars[k % C::STAGES]), static_cast<uint32_t>((k / C::STAGES) & 1), g.err,
+      ptx::mbar_wait(ptx::smem_u32(&bars[k % C::STAGES]), static_cast<uint32_t>((k / C::STAGES) & 1), last_err,
                      ptx::kErrWaitDrain, polls);
   } else if (warp == 1 && lane == 0) {
     // -------------------------------------------------------- MMA issuer
@@ -309,17 +351,25 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
     bool ok = true;
     long long it = 0;
     int tcount = 0;
-    for (long long q = unit0; q < num_units && ok; q += unit_step, ++tcount) {
+    int* last_err = g.err;
+    for (long long q = unit0; q < num_units && ok; q += unit_step) {
+      int m0, n0, nkq;
+      const GemmOut* gq;
+      const CUtensorMap* mq;
+      if (!resolve(q, m0, n0, nkq, gq, mq)) continue;
+      volatile int* abort_q = MULTI ? reinterpret_cast<volatile int*>(gq->err) : abort_flag;
+      last_err = gq->err;
       const int b = tcount & 1, use = tcount >> 1;
+      ++tcount;
       if (use > 0)
-        ok = ptx::mbar_wait(ptx::smem_u32(&acce[b]), static_cast<uint32_t>((use - 1) & 1), g.err,
+        ok = ptx::mbar_wait(ptx::smem_u32(&acce[b]), static_cast<uint32_t>((use - 1) & 1), gq->err,
                             ptx::kErrWaitAccum, polls);
-      if (!ok || (abort_flag && *abort_flag)) break;
+      if (!ok || (abort_q && *abort_q)) break;
       ptx::tc_fence_after();
       const uint32_t d = tmem + static_cast<uint32_t>(b * BN);
-      for (int kc = 0; kc < nk; ++kc, ++it) {
+      for (int kc = 0; kc < nkq; ++kc, ++it) {
         const int s = static_cast<int>(it % C::STAGES);
-        ok = ptx::mbar_wait(ptx::smem_u32(&bars[s]), static_cast<uint32_t>((it / C::STAGES) & 1), g.err,
+        ok = ptx::mbar_wait(ptx::smem_u32(&bars[s]), static_cast<uint32_t>((it / C::STAGES) & 1), gq->err,
                             ptx::kErrWaitFull, polls);
         if (!ok) break;
         ptx::tc_fence_after();
@@ -349,7 +399,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
     // freed, also when a timed-out wait ended the loop early
     if (it > 0) {
       ptx::mma_commit(ptx::smem_u32(mdone));
-      ptx::mbar_wait(ptx::smem_u32(mdone), 0u, g.err, ptx::kErrWaitDrain, polls);
+      ptx::mbar_wait(ptx::smem_u32(mdone), 0u, last_err, ptx::kErrWaitDrain, polls);
     }
   } else if (warp >= 2) {
     // ---------------------------------------------------------- epilogue
@@ -365,20 +415,27 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
     uint8_t* ostage = smem + C::STAGES * C::STAGE + 1024 + (warp - 2) * (ONPL * CHUNK);
     int chunk_i = 0;
     int tcount = 0;
-    for (long long q = unit0; q < num_units; q += unit_step, ++tcount) {
+    for (long long q = unit0; q < num_units; q += unit_step) {
+      int m0, n0, nkq;
+      const GemmOut* gq;
+      const CUtensorMap* mq;
+      if (!resolve(q, m0, n0, nkq, gq, mq)) continue;
+      const GemmOut& gu = *gq;
+      const CUtensorMap* mO0 = MULTI ? &mq[4] : &tO0;
+      const CUtensorMap* mO1 = MULTI ? &mq[5] : &tO1;
+      volatile int* abort_q = MULTI ? reinterpret_cast<volatile int*>(gu.err) : abort_flag;
       const int b = tcount & 1, use = tcount >> 1;
-      const bool ok = ptx::mbar_wait(ptx::smem_u32(&accf[b]), static_cast<uint32_t>(use & 1), g.err,
+      ++tcount;
+      const bool ok = ptx::mbar_wait(ptx::smem_u32(&accf[b]), static_cast<uint32_t>(use & 1), gu.err,
                                      ptx::kErrWaitAccum, polls);
       ptx::tc_fence_after();
-      const bool flagged = abort_flag && *abort_flag;
+      const bool flagged = abort_q && *abort_q;
       // tcgen05.ld is warp-collective: decide for the whole warp
       if (!__all_sync(0xffffffffu, ok && !flagged)) break;
-      int m0, n0;
-      unit_coords<BN, PAIR>(g, num_m, num_n, q, rank, m0, n0);
       const int m = m0 + quarter * 32 + lane;
-      const bool mvalid = m < g.M;
+      const bool mvalid = m < gu.M;
       const long long mterm =
-          mvalid ? (static_cast<long long>(m % g.rm) + static_cast<long long>(m / g.rm) * g.sm) : 0;
+          mvalid ? (static_cast<long long>(m % gu.rm) + static_cast<long long>(m / gu.rm) * gu.sm) : 0;
 #pragma unroll 1
       for (int c0 = 32 * half; c0 < BN; c0 += 32 * (EPI / 4)) {
         uint32_t r[32];
@@ -409,19 +466,19 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
           ptx::fence_proxy_async_smem();
           __syncwarp();
           const int mc = m0 + quarter * 32;        // first row of the chunk
-          if (lane == 0 && mc < g.M && n0 + c0 < g.N) {
+          if (lane == 0 && mc < gu.M && n0 + c0 < gu.N) {
             // boxes start inside the tensor; the TMA unit clips their far
             // edges.  x stays a multiple of 32 elements: rm is a multiple of
             // 32, or the output is one block of rows (x = m, z = 0)
-            const bool flat = g.rm >= g.M;
-            const int x = flat ? mc : mc % g.rm, z = flat ? 0 : mc / g.rm;
-            ptx::tma_store_3d(&tO0, ptx::smem_u32(sb), x, n0 + c0, z);
-            if (ONPL == 2) ptx::tma_store_3d(&tO1, ptx::smem_u32(sb + CHUNK), x, n0 + c0, z);
+            const bool flat = gu.rm >= gu.M;
+            const int x = flat ? mc : mc % gu.rm, z = flat ? 0 : mc / gu.rm;
+            ptx::tma_store_3d(mO0, ptx::smem_u32(sb), x, n0 + c0, z);
+            if (ONPL == 2) ptx::tma_store_3d(mO1, ptx::smem_u32(sb + CHUNK), x, n0 + c0, z);
             ptx::bulk_commit();
           }
           ++chunk_i;
         } else if (mvalid) {
-          store_chunk<OUT>(g, mterm, n0 + c0, r);
+          store_chunk<OUT>(gu, mterm, n0 + c0, r);
         }
       }
       ptx::tc_fence_before();
@@ -534,7 +591,8 @@ cudaError_t launch(const Operand& A, const Operand& B, const GemmOut& g, cudaStr
   if (PAIR == 0) {
     const long long ctas = tiles < cap ? tiles : cap;   // persistent: one CTA per SM
     note_launch(1);
-    kern<<<static_cast<unsigned>(ctas), threads_of<OUT>(), smem_bytes, s>>>(m[0], m[1], m[2], m[3], m[4], m[5], g);
+    kern<<<static_cast<unsigned>(ctas), threads_of<OUT>(), smem_bytes, s>>>(m[0], m[1], m[2], m[3], m[4], m[5], g,
+                                                                           nullptr, 0, 0LL);
     return cudaGetLastError();
   }
   // clusters of two CTAs, as many as can be resident at once (one CTA per SM)
@@ -558,7 +616,8 @@ cudaError_t launch(const Operand& A, const Operand& B, const GemmOut& g, cudaStr
   cudaGetLastError();
   cfg.gridDim = dim3(static_cast<unsigned>(2 * pairs), 1, 1);
   note_launch(1);
-  e = cudaLaunchKernelEx(&cfg, kern, m[0], m[1], m[2], m[3], m[4], m[5], g);
+  e = cudaLaunchKernelEx(&cfg, kern, m[0], m[1], m[2], m[3], m[4], m[5], g, static_cast<const GemmJob*>(nullptr), 0,
+                         0LL);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
@@ -638,6 +697,75 @@ bool make_plain_map(CUtensorMap* map, const void* base, int elem_bytes, long lon
                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
+}
+
+namespace {
+
+template <int OUT, int TMAO>
+cudaError_t launch_grouped(const GemmJob* d_jobs, int njobs, long long units, cudaStream_t s) {
+  using C = Cfg<kKindBF16, 2, 256>;
+  auto kern = gemm_tc_kernel<kKindBF16, 2, 256, OUT, 0, TMAO, 1>;
+  const int smem_bytes = TMAO ? C::SMEM_TMAO : C::SMEM;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+  if (e != cudaSuccess) return e;
+  if (units <= 0 || njobs <= 0) return cudaSuccess;
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long ctas = units < sms ? units : sms;
+  CUtensorMap none;
+  std::memset(&none, 0, sizeof(none));
+  GemmOut g0;
+  std::memset(&g0, 0, sizeof(g0));
+  note_launch(1);
+  kern<<<static_cast<unsigned>(ctas), threads_of<OUT>(), smem_bytes, s>>>(none, none, none, none, none, none, g0,
+                                                                         d_jobs, njobs, units);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+long long job_units(const GemmOut& g) {
+  return static_cast<long long>((g.M + BM - 1) / BM) * ((g.N + 255) / 256);
+}
+
+bool make_job(const Operand& A, const Operand& B, const GemmOut& g, bool tma_out, GemmJob* job, long long first) {
+  using C = Cfg<kKindBF16, 2, 256>;
+  std::memset(job, 0, sizeof(*job));
+  if (A.K != B.K || A.rows != g.M || B.rows != g.N || g.M <= 0 || g.N <= 0 || A.K <= 0 || g.rm <= 0) return false;
+  if (!make_map(&job->map[0], A.plane[0], kKindBF16, A.rows, A.K, A.ld, BM, C::SW)) return false;
+  if (!make_map(&job->map[1], A.plane[1], kKindBF16, A.rows, A.K, A.ld, BM, C::SW)) return false;
+  if (!make_map(&job->map[2], B.plane[0], kKindBF16, B.rows, B.K, B.ld, 256, C::SW)) return false;
+  if (!make_map(&job->map[3], B.plane[1], kKindBF16, B.rows, B.K, B.ld, 256, C::SW)) return false;
+  if (tma_out) {
+    const int eb = (g.mode == kOutF32) ? 4 : 2;
+    if (!(g.rm >= g.M || (g.rm % 32 == 0 && g.M % g.rm == 0))) return false;
+    if (!make_out_map(&job->map[4], g.out0, eb, g)) return false;
+    if (g.mode == kOutSplitBF16) {
+      if (!make_out_map(&job->map[5], g.out1, eb, g)) return false;
+    } else {
+      job->map[5] = job->map[4];
+    }
+  }
+  job->g = g;
+  job->first = first;
+  job->num_m = (g.M + BM - 1) / BM;
+  job->num_n = (g.N + 255) / 256;
+  return true;
+}
+
+cudaError_t gemm_grouped(int mode, bool tma_out, const GemmJob* d_jobs, int njobs, long long units,
+                         cudaStream_t s) {
+  switch (mode) {
+    case kOutSplitBF16:
+      return tma_out ? launch_grouped<kOutSplitBF16, 1>(d_jobs, njobs, units, s)
+                     : launch_grouped<kOutSplitBF16, 0>(d_jobs, njobs, units, s);
+    case kOutF32:
+      return tma_out ? launch_grouped<kOutF32, 1>(d_jobs, njobs, units, s)
+                     : launch_grouped<kOutF32, 0>(d_jobs, njobs, units, s);
+    case kOutDF: return launch_grouped<kOutDF, 0>(d_jobs, njobs, units, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 bool own_device_memory(const void* p) {

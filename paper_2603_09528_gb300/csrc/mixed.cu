@@ -522,24 +522,37 @@ __device__ __forceinline__ void store_pair(void* o0, void* o1, int i, float x0, 
   }
 }
 
-template <int FMT, int M>
+// The data of one instance for thomas2_kernel: tensor maps of T2 (in) and
+// T3 (out planes), its stage geometry, sizes, tables and flags.  A grouped
+// launch reads these from a device table (`first` = the instance's first
+// tile in the launch); a single solve passes one as a kernel parameter.
+struct ThomasJob {
+  CUtensorMap map_in, map_o0, map_o1;
+  ThomasGeom geo;
+  int nx, ny, nz, ldy, ntiles, first;
+  void *t3_0, *t3_1;
+  const float *lamx, *lamy, *az, *bz, *cz;
+  float alpha, beta;
+  int singular;
+  int* err;
+  const int* skip;
+};
+
+// lg: the shared-memory layout of the launch (stage count and the largest
+// stage, output tile and row table over its instances).
+template <int FMT, int M, int MULTI>
 __global__ void __launch_bounds__(kThomasThreads, 1)
-thomas2_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ CUtensorMap map_o0,
-               const __grid_constant__ CUtensorMap map_o1, ThomasGeom geo, int nx, int ny, int nz, int ldy,
-               int ntiles, int* next_tile, void* t3_0, void* t3_1, const float* __restrict__ lamx,
-               const float* __restrict__ lamy, const float* __restrict__ az, const float* __restrict__ bz,
-               const float* __restrict__ cz, float alpha, float beta, int singular, int* err, const int* skip) {
-  if (skip && *skip) return;   // the refinement has stopped
+thomas2_kernel(const __grid_constant__ ThomasJob job0, ThomasGeom lg, int* next_tile, int total_tiles,
+               const ThomasJob* __restrict__ jobs, int njobs) {
+  if (!MULTI && job0.skip && *job0.skip) return;   // the refinement has stopped
   using O = T3Fmt<FMT>;
   constexpr int TLT = 32;
   static_assert(M >= 2 && M <= 16, "segments of 2 to 16 rows");
   extern __shared__ __align__(128) uint8_t dsm_raw[];
   uint8_t* dsm = dsm_raw + ((1024u - (ptx::smem_u32(dsm_raw) & 1023u)) & 1023u);
   RowCoef* coef = reinterpret_cast<RowCoef*>(dsm);
-  uint8_t* in_base = dsm + geo.coef_bytes;
-  uint8_t* ot = in_base + static_cast<size_t>(geo.stages) * geo.in_bytes;
-  void* o0 = ot;
-  void* o1 = ot + (O::NPL == 2 ? geo.out_bytes / 2 : 0);
+  uint8_t* in_base = dsm + lg.coef_bytes;
+  uint8_t* ot = in_base + static_cast<size_t>(lg.stages) * lg.in_bytes;
   // reduced-system buffer: first g_0, u_0, v_0 of every segment, then the
   // interface rows A, B, C, D (D overwritten by the interface values y)
   __shared__ float X[4][kT2Slots * kT2Pitch];
@@ -550,52 +563,70 @@ thomas2_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_constant
   const int s = 2 * warp + lane / 16;    // segment slot
   const int l0 = 2 * (lane % 16);        // first of the thread's two lines in the tile
   const int s0 = s * M;
-  const bool active = s < geo.nseg;
   const int xo = s * kT2Pitch + l0;      // the thread's entries in X
-  const int lines = ldy * nx;
-  const int S = geo.stages;
+  const int S = lg.stages;
   long long issued = 0;
   bool exhausted = false;
   int claim = -1;
+  int cur = -1;                          // instance whose rows are in `coef`
+  int* err0 = MULTI ? nullptr : job0.err;
 
+  // instance of global tile t (its first tile <= t)
+  auto job_of = [&](int t) -> const ThomasJob* {
+    if constexpr (MULTI) {
+      int lo = 0, hi = njobs - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if (jobs[mid].first <= t) lo = mid;
+        else hi = mid - 1;
+      }
+      return &jobs[lo];
+    } else {
+      (void)t;
+      return &job0;
+    }
+  };
+  // next tile from the counter, passing over the tiles of stopped instances
+  auto next = [&]() -> int {
+    for (;;) {
+      const int t = atomicAdd(next_tile, 1);
+      if (!MULTI || t >= total_tiles) return t;
+      const ThomasJob& J = *job_of(t);
+      if (!(J.skip && *J.skip)) return t;
+    }
+  };
   auto issue = [&](long long i, int tile) {
     const int st = static_cast<int>(i % S);
     const uint32_t bar = ptx::smem_u32(&full[st]);
     ++issued;
-    if (tile >= ntiles) {
+    if (tile >= total_tiles) {
       exhausted = true;
       tile_of[st] = -1;
       ptx::mbar_arrive(bar);
       return;
     }
+    const ThomasJob& J = *job_of(tile);
     tile_of[st] = tile;
-    ptx::mbar_arrive_expect_tx(bar, static_cast<uint32_t>(geo.in_bytes));
-    uint8_t* base = in_base + static_cast<size_t>(st) * geo.in_bytes;
-    for (int b = 0; b < geo.nb; ++b)
-      ptx::tma_load_2d(ptx::smem_u32(base + b * geo.rb * TLT * 4), &map_in, bar, tile * TLT, b * geo.rb);
+    ptx::mbar_arrive_expect_tx(bar, static_cast<uint32_t>(J.geo.in_bytes));
+    uint8_t* base = in_base + static_cast<size_t>(st) * lg.in_bytes;
+    const int lt = tile - J.first;
+    for (int b = 0; b < J.geo.nb; ++b)
+      ptx::tma_load_2d(ptx::smem_u32(base + b * J.geo.rb * TLT * 4), &J.map_in, bar, lt * TLT, b * J.geo.rb);
   };
 
-  for (int k = tid; k < geo.sr; k += blockDim.x) {
-    RowCoef rc{0.0f, 1.0f, 0.0f, 0.0f};
-    if (k < nz) {
-      rc.a = k > 0 ? beta * az[k] : 0.0f;
-      rc.b = beta * bz[k];
-      rc.c = k < nz - 1 ? beta * cz[k] : 0.0f;
-      rc.m = 1.0f;
-    }
-    coef[k] = rc;
-  }
   if (tid == 0) {
     for (int i = 0; i < S; ++i) ptx::mbar_init(ptx::smem_u32(&full[i]), 1);
     ptx::fence_mbar_init();
-    ptx::prefetch_tmap(&map_in);
-    ptx::prefetch_tmap(&map_o0);
-    if (O::NPL == 2) ptx::prefetch_tmap(&map_o1);
+    if (!MULTI) {
+      ptx::prefetch_tmap(&job0.map_in);
+      ptx::prefetch_tmap(&job0.map_o0);
+      if (O::NPL == 2) ptx::prefetch_tmap(&job0.map_o1);
+    }
   }
   __syncthreads();
   if (tid == 0) {
-    for (long long i = 0; i < S && !exhausted; ++i) issue(i, atomicAdd(next_tile, 1));
-    if (!exhausted) claim = atomicAdd(next_tile, 1);
+    for (long long i = 0; i < S && !exhausted; ++i) issue(i, next());
+    if (!exhausted) claim = next();
   }
 
   long long i = 0;
@@ -604,7 +635,11 @@ thomas2_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_constant
     const int st = static_cast<int>(i % S);
     const uint32_t bar = ptx::smem_u32(&full[st]);
     const uint32_t par = static_cast<uint32_t>((i / S) & 1);
-    if (tid == 0) go = ptx::mbar_wait(bar, par, err, ptx::kErrWaitFull) ? 1 : 0;
+    if (tid == 0) {
+      const int t = tile_of[st];
+      int* e = MULTI ? (t >= 0 && t < total_tiles ? job_of(t)->err : nullptr) : err0;
+      go = ptx::mbar_wait(bar, par, e, ptx::kErrWaitFull) ? 1 : 0;
+    }
     __syncthreads();
     if (!go) {
       ok = false;
@@ -614,21 +649,42 @@ thomas2_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_constant
     if (tile < 0) break;
     for (int k = 0; k < 64 && !ptx::mbar_try_wait(bar, par); ++k) {
     }   // the phase is complete: this acquires the TMA writes for every thread
-    const float* in = reinterpret_cast<const float*>(in_base + static_cast<size_t>(st) * geo.in_bytes);
+    const ThomasJob& J = *job_of(tile);
+    const int jid = MULTI ? static_cast<int>(&J - jobs) : 0;
+    if (jid != cur) {                    // this instance's beta-scaled z rows into the table
+      if (cur >= 0) __syncthreads();     // the previous tile is done with them
+      for (int k = tid; k < J.geo.sr; k += blockDim.x) {
+        RowCoef rc{0.0f, 1.0f, 0.0f, 0.0f};
+        if (k < J.nz) {
+          rc.a = k > 0 ? J.beta * J.az[k] : 0.0f;
+          rc.b = J.beta * J.bz[k];
+          rc.c = k < J.nz - 1 ? J.beta * J.cz[k] : 0.0f;
+          rc.m = 1.0f;
+        }
+        coef[k] = rc;
+      }
+      cur = jid;
+      __syncthreads();
+    }
+    const int lt = tile - J.first;
+    const int lines = J.ldy * J.nx;
+    const bool active = s < J.geo.nseg;
+    void* o0 = ot;
+    void* o1 = ot + (O::NPL == 2 ? J.geo.out_bytes / 2 : 0);
+    const float* in = reinterpret_cast<const float*>(in_base + static_cast<size_t>(st) * lg.in_bytes);
 
     float shift[2];
     {
       // one division per tile: ldy is even and l0 is even, so the thread's
       // second line L + 1 lies in the same row p of modes as its first
-      const int L = tile * TLT + l0;
-      const int p = L / ldy, q = L - p * ldy;
+      const int L = lt * TLT + l0;
+      const int p = L / J.ldy, q = L - p * J.ldy;
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
-        const bool real = L + j < lines && q + j < ny;   // else a padding line: dummy shift
-        shift[j] = alpha + beta * (lamx[real ? p : 0] + lamy[real ? q + j : 0]);
+        const bool real = L + j < lines && q + j < J.ny;   // else a padding line: dummy shift
+        shift[j] = J.alpha + J.beta * (J.lamx[real ? p : 0] + J.lamy[real ? q + j : 0]);
       }
     }
-
     // forward elimination of the interior rows (as in thomas_tma_kernel),
     // two lines at a time
     float inv[2][M - 1];
@@ -771,32 +827,34 @@ thomas2_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_constant
     __syncthreads();
     if (tid == 0 && !exhausted) {        // the input stage is free: refill it
       issue(i + S, claim);
-      if (!exhausted) claim = atomicAdd(next_tile, 1);
+      if (!exhausted) claim = next();
     }
-    if (!(singular && tile == 0)) {
+    if (!(J.singular && lt == 0)) {
       if (tid == 0) {
-        for (int b = 0; b < geo.nb; ++b) {
-          const int off = b * geo.rb * TLT * O::EB;
-          ptx::tma_store_2d(&map_o0, ptx::smem_u32(static_cast<uint8_t*>(o0) + off), tile * TLT, b * geo.rb);
+        for (int b = 0; b < J.geo.nb; ++b) {
+          const int off = b * J.geo.rb * TLT * O::EB;
+          ptx::tma_store_2d(&J.map_o0, ptx::smem_u32(static_cast<uint8_t*>(o0) + off), lt * TLT, b * J.geo.rb);
           if (O::NPL == 2)
-            ptx::tma_store_2d(&map_o1, ptx::smem_u32(static_cast<uint8_t*>(o1) + off), tile * TLT, b * geo.rb);
+            ptx::tma_store_2d(&J.map_o1, ptx::smem_u32(static_cast<uint8_t*>(o1) + off), lt * TLT, b * J.geo.rb);
         }
         ptx::bulk_commit();
       }
     } else {                             // the null line is not ours to write
-      for (int e = tid; e < TLT * nz; e += blockDim.x) {
+      for (int e = tid; e < TLT * J.nz; e += blockDim.x) {
         const int ll = e % TLT, k = e / TLT;
         if (ll == 0 || ll >= lines) continue;
-        copy_elem<FMT>(o0, o1, e, t3_0, t3_1, ll + static_cast<long long>(k) * lines);
+        copy_elem<FMT>(o0, o1, e, J.t3_0, J.t3_1, ll + static_cast<long long>(k) * lines);
       }
       __syncthreads();                   // the output tile is rewritten by the next tile
     }
   }
   if (tid == 0) {
     if (!ok)   // the loads of local tiles i .. issued - 1 may still be landing
-      for (long long k = i; k < issued; ++k)
-        ptx::mbar_wait(ptx::smem_u32(&full[k % S]), static_cast<uint32_t>((k / S) & 1), err,
-                       ptx::kErrWaitDrain);
+      for (long long k = i; k < issued; ++k) {
+        const int t = tile_of[k % S];
+        int* e = MULTI ? (t >= 0 && t < total_tiles ? job_of(t)->err : nullptr) : err0;
+        ptx::mbar_wait(ptx::smem_u32(&full[k % S]), static_cast<uint32_t>((k / S) & 1), e, ptx::kErrWaitDrain);
+      }
     ptx::bulk_wait_all();
   }
 }
@@ -1915,46 +1973,71 @@ int thomas2_m(int nz) {
   return best;
 }
 
+// The job record of a plan's Thomas step on workspace w (tile numbers from
+// `first`); false when T2 or T3 cannot be described by tensor maps or the
+// segments do not fit.
 template <int FMT, int M>
-cudaError_t launch_thomas2_m(const tpt_plan_s* p, const MixedWork& w, cudaStream_t s) {
+bool thomas2_job(const tpt_plan_s* p, const MixedWork& w, int first, ThomasJob* J) {
   using O = T3Fmt<FMT>;
   constexpr int TLT = 32;
   const MixedTables& m = p->mixed;
   const long long lines = static_cast<long long>(m.ldy) * p->n[0];
   const int nz = p->n[2];
-  const long long ntiles = (lines + TLT - 1) / TLT;
-  if (ntiles <= 0) return cudaSuccess;
-  if (lines + TLT > 0x7fffffffLL) return cudaErrorInvalidValue;
-  ThomasGeom geo;
-  if (!thomas_geom(nz, M, TLT, O::NPL, O::EB, &geo, kT2SmemBudget)) return cudaErrorInvalidConfiguration;
-  if (geo.nseg > kT2Slots) return cudaErrorInvalidConfiguration;
-  CUtensorMap mi, mo0, mo1;
-  if (!tc::make_plain_map(&mi, w.B[0], 4, lines, nz, lines * 4, TLT, geo.rb)) return cudaErrorInvalidValue;
-  if (!tc::make_plain_map(&mo0, w.A[0], O::EB, lines, nz, lines * O::EB, TLT, geo.rb)) return cudaErrorInvalidValue;
+  if (lines + TLT > 0x7fffffffLL) return false;   // int line indices and TMA coordinates
+  std::memset(J, 0, sizeof(*J));
+  if (!thomas_geom(nz, M, TLT, O::NPL, O::EB, &J->geo, kT2SmemBudget) || J->geo.nseg > kT2Slots) return false;
+  if (!tc::make_plain_map(&J->map_in, w.B[0], 4, lines, nz, lines * 4, TLT, J->geo.rb)) return false;
+  if (!tc::make_plain_map(&J->map_o0, w.A[0], O::EB, lines, nz, lines * O::EB, TLT, J->geo.rb)) return false;
   if (O::NPL == 2) {
-    if (!tc::make_plain_map(&mo1, w.A[1], O::EB, lines, nz, lines * O::EB, TLT, geo.rb))
-      return cudaErrorInvalidValue;
+    if (!tc::make_plain_map(&J->map_o1, w.A[1], O::EB, lines, nz, lines * O::EB, TLT, J->geo.rb)) return false;
   } else {
-    mo1 = mo0;
+    J->map_o1 = J->map_o0;
   }
+  J->nx = p->n[0];
+  J->ny = p->n[1];
+  J->nz = nz;
+  J->ldy = m.ldy;
+  J->ntiles = static_cast<int>((lines + TLT - 1) / TLT);
+  J->first = first;
+  J->t3_0 = w.A[0];
+  J->t3_1 = w.A[1];
+  J->lamx = m.lam_f[0];
+  J->lamy = m.lam_f[1];
+  J->az = m.zrows_f;
+  J->bz = m.zrows_f + nz;
+  J->cz = m.zrows_f + 2 * nz;
+  J->alpha = static_cast<float>(p->alpha);
+  J->beta = static_cast<float>(p->beta);
+  J->singular = p->singular ? 1 : 0;
+  J->err = reinterpret_cast<int*>(w.scal + 15);
+  J->skip = w.skip;
+  return true;
+}
+
+size_t thomas2_smem(const ThomasGeom& g) {
+  return 1024 + static_cast<size_t>(g.coef_bytes) + static_cast<size_t>(g.stages) * g.in_bytes +
+         static_cast<size_t>(g.out_bytes);
+}
+
+template <int FMT, int M>
+cudaError_t launch_thomas2_m(const tpt_plan_s* p, const MixedWork& w, cudaStream_t s) {
+  ThomasJob J;
+  if (!thomas2_job<FMT, M>(p, w, 0, &J)) return cudaErrorInvalidValue;
+  if (J.ntiles <= 0) return cudaSuccess;
   int* next_tile = reinterpret_cast<int*>(w.scal + 14);
   cudaError_t e = cudaMemsetAsync(next_tile, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
-  const size_t smem = 1024 + static_cast<size_t>(geo.coef_bytes) + static_cast<size_t>(geo.stages) * geo.in_bytes +
-                      static_cast<size_t>(geo.out_bytes);
-  auto kern = thomas2_kernel<FMT, M>;
+  const size_t smem = thomas2_smem(J.geo);
+  auto kern = thomas2_kernel<FMT, M, 0>;
   // a fixed cap (see launch_thomas_m)
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kT2SmemBudget);
   if (e != cudaSuccess) return e;
   if (smem > static_cast<size_t>(kT2SmemBudget)) return cudaErrorInvalidConfiguration;
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->dev);
-  const long long grid = ntiles < sms ? ntiles : sms;
+  const int grid = J.ntiles < sms ? J.ntiles : sms;
   note_launch(1);
-  kern<<<static_cast<unsigned>(grid), kThomasThreads, smem, s>>>(
-      mi, mo0, mo1, geo, p->n[0], p->n[1], nz, m.ldy, static_cast<int>(ntiles), next_tile, w.A[0], w.A[1],
-      m.lam_f[0], m.lam_f[1], m.zrows_f, m.zrows_f + nz, m.zrows_f + 2 * nz, static_cast<float>(p->alpha),
-      static_cast<float>(p->beta), p->singular ? 1 : 0, reinterpret_cast<int*>(w.scal + 15), w.skip);
+  kern<<<static_cast<unsigned>(grid), kThomasThreads, smem, s>>>(J, J.geo, next_tile, J.ntiles, nullptr, 0);
   return cudaGetLastError();
 }
 

@@ -48,6 +48,17 @@ struct GemmOut {
   int drop_loads = 0;
 };
 
+// One GEMM of a grouped launch: its tensor maps (A0, A1, B0, B1, O0, O1; the
+// output maps only for the TMA-store epilogue), its output description, its
+// first unit in the launch's list of tiles and its tile counts.  Kept in
+// device memory.
+struct GemmJob {
+  CUtensorMap map[6];
+  GemmOut g;
+  long long first;
+  int num_m, num_n;
+};
+
 // True when p points into device memory of the current device (not host,
 // managed or another GPU's memory).  Operand sharing between the two CTAs of
 // a pair (TMA multicast) is used only when every operand plane passes.
@@ -65,6 +76,18 @@ bool make_plain_map(CUtensorMap* map, const void* base, int elem_bytes, long lon
 
 cudaError_t gemm(int kind, int nplanes, const Operand& A, const Operand& B, const GemmOut& g,
                  cudaStream_t s);
+
+// Grouped launches of split-bf16 GEMMs (two planes, three products) with
+// 256-column tiles: make_job fills one job on the host (false if an operand
+// or the output cannot be described by tensor maps); gemm_grouped launches
+// one persistent kernel over the tiles of `njobs` jobs already copied to
+// device memory (`d_jobs`), whose units are claimed round-robin.  The output
+// mode (g.mode) and tma_out must be the same for every job of a launch.
+bool make_job(const Operand& A, const Operand& B, const GemmOut& g, bool tma_out, GemmJob* job,
+              long long first);
+long long job_units(const GemmOut& g);
+cudaError_t gemm_grouped(int mode, bool tma_out, const GemmJob* d_jobs, int njobs, long long units,
+                         cudaStream_t s);
 
 }  // namespace tc
 }  // namespace tpt
