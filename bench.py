@@ -487,20 +487,38 @@ def batch_leg(tpt, device, stream, prec, steps, count=96, seed=5, nstreams=8):
     t0 = time.perf_counter()
     tiles = b.autotune(work, stream) if prec != 0 else None
     t_tune = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    b.solve(fs, phis, work, stream=stream)            # eager run + graph capture
-    t_capture = time.perf_counter() - t0
-    for _ in range(2):
-        b.solve(fs, phis, work, stream=stream, want_info=False)
-    torch.cuda.synchronize()
     reps = max(2, steps) if prec != 0 else 2
+
+    def timed(work):
+        t0 = time.perf_counter()
+        b.solve(fs, phis, work, stream=stream)        # eager run + graph capture
+        t_cap = time.perf_counter() - t0
+        for _ in range(2):
+            b.solve(fs, phis, work, stream=stream, want_info=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            b.solve(fs, phis, work, stream=stream, want_info=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, t_cap
+
+    grouped = b.grouped
+    streams_mode = None
+    if grouped:
+        # the capture streams on the same instances, for comparison
+        b.set_grouped(False)
+        ws = b.new_workspace()
+        ms_s, _ = timed(ws)
+        streams_mode = {"ms_per_batch": ms_s, "gpts_per_s": sum(it["n"][0] * it["n"][1] * it["n"][2]
+                                                                for it in inst) / (ms_s / 1e3) / 1e9,
+                        "launches_per_replay": b.launches_per_replay(), "nstreams": nstreams}
+        del ws
+        b.set_grouped(True)
+        work = b.new_workspace()
+    ms, t_capture = timed(work)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
-        b.solve(fs, phis, work, stream=stream, want_info=False)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / reps
     infos = b.solve(fs, phis, work, stream=stream)
     # the same instances one after another on one stream, without the graph
     for p, inf in zip(b.plans, infos):
@@ -515,7 +533,9 @@ def batch_leg(tpt, device, stream, prec, steps, count=96, seed=5, nstreams=8):
     res = [i["rel_residual"] for i in infos]
     out = {"instances": count, "points": pts, "precision": {0: "fp64", 1: "mixed_bf16", 2: "mixed_bf16x3",
                                                               3: "mixed_tf32"}[prec],
-           "nstreams": nstreams, "ms_per_batch": ms, "steps": reps,
+           "mode": "grouped launches (one kernel per stage over all instances)" if grouped
+           else "capture streams", "nstreams": None if grouped else nstreams, "ms_per_batch": ms, "steps": reps,
+           "capture_streams_mode": streams_mode,
            "solves_per_s": count * 1e3 / ms, "gpts_per_s": pts / (ms / 1e3) / 1e9,
            "sequential_ms": ms_seq, "graph_speedup_vs_sequential": ms_seq / ms,
            "launches_per_replay": b.launches_per_replay(), "graph_launches_per_batch": 1,

@@ -409,6 +409,25 @@ int tpt_batch_infos(tpt_batch batch, tpt_info* infos, int* statuses);
 /* Kernels one graph replay launches (0 before the first capture).           */
 int tpt_batch_launches(tpt_batch batch, unsigned long long* count);
 
+/* Grouped mode of a batch (the default where it applies): every stage of
+ * every correction is one kernel over all instances (one per Thomas segment
+ * length and per residual variant), whose CTAs take their units -- GEMM
+ * tiles, tiles of modal lines, plane tiles -- from all instances at once
+ * through device job tables; an instance that has met its rtol stops and its
+ * units are passed over by the later kernels.  A batch of ~100 instances
+ * then replays O(10) kernels per correction instead of ~10 per instance.  It
+ * applies when every instance is TPT_PREC_MIXED_BF16X3 with rtol > 0, Nx a
+ * multiple of 4 and Nz <= 512, and the fields are 16-byte aligned; each
+ * instance then runs until it meets rtol or the largest 1 + max_refine of the
+ * batch, and has its own region of the workspace (tpt_batch_workspace_bytes
+ * reports the mode's size: query it after switching).  grouped = 0 selects
+ * the capture streams; UNSUPPORTED when grouped mode does not apply (a solve
+ * whose buffers it cannot take also returns UNSUPPORTED and switches the
+ * batch back to streams).  The paper's closest analogue is the autotuned
+ * decomposition of its GPU runs (Sec. 3, Sec. 4.2.2).                      */
+int tpt_batch_set_grouped(tpt_batch batch, int grouped);
+int tpt_batch_get_grouped(tpt_batch batch, int* grouped);
+
 int tpt_batch_destroy(tpt_batch batch);
 
 /* ---- shared eigenbases ---------------------------------------------------- */

@@ -143,6 +143,8 @@ SIGNATURES = [
                                   C.c_void_p, C.POINTER(tpt_info), C.POINTER(C.c_int)]),
     ("tpt_batch_infos", C.c_int, [C.c_void_p, C.POINTER(tpt_info), C.POINTER(C.c_int)]),
     ("tpt_batch_launches", C.c_int, [C.c_void_p, C.POINTER(C.c_ulonglong)]),
+    ("tpt_batch_set_grouped", C.c_int, [C.c_void_p, C.c_int]),
+    ("tpt_batch_get_grouped", C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     ("tpt_batch_destroy", C.c_int, [C.c_void_p]),
     ("tpt_project_workspace_bytes", C.c_int, [C.c_void_p, C.POINTER(C.c_size_t)]),
     ("tpt_project", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p,

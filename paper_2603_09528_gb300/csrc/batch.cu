@@ -34,6 +34,12 @@ struct tpt_batch_s {
   std::vector<unsigned> gens;            // plan generations at capture
   unsigned long long launches = 0;       // kernels per replay
   bool solved = false;
+  // grouped mode: one kernel per stage over every instance (when the plans
+  // qualify; see tpt::group_create), instead of per-instance kernels spread
+  // over the capture streams
+  tpt::GroupSolve* group = nullptr;
+  bool grouped = false;
+  size_t ws_streams = 0;                 // workspace of the stream mode
 };
 
 namespace {
@@ -69,6 +75,7 @@ size_t align256(size_t b) { return (b + 255) & ~static_cast<size_t>(255); }
 
 void release(tpt_batch b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
+  tpt::group_destroy(b->group);
   for (cudaStream_t s : b->streams)
     if (s) cudaStreamDestroy(s);
   for (cudaEvent_t e : b->joins)
@@ -90,8 +97,15 @@ double cost_of(const tpt_plan_s* p) {
 }
 
 // Fork onto the capture streams, solve every instance, join, and copy the
-// per-instance sums to the pinned host array.
+// per-instance sums to the pinned host array (grouped mode: the grouped
+// launches on s).
 int enqueue(tpt_batch b, const double* const* f, double* const* phi, char* work, cudaStream_t s) {
+  if (b->grouped) {
+    BT_TRY(tpt::group_enqueue(b->group, b->d_scal, s));
+    BT_CUDA(cudaMemcpyAsync(b->h_scal, b->d_scal, static_cast<size_t>(b->count) * kScal * sizeof(double),
+                            cudaMemcpyDeviceToHost, s));
+    return TPT_OK;
+  }
   BT_CUDA(cudaEventRecord(b->fork, s));
   for (cudaStream_t ls : b->streams) BT_CUDA(cudaStreamWaitEvent(ls, b->fork, 0));
   for (size_t k = 0; k < b->lanes.size(); ++k) {
@@ -207,7 +221,36 @@ int tpt_batch_create(const tpt_desc* descs, int count, int cuda_device, int nstr
     return st;
   }
   std::memset(b->h_scal, 0, sb);
+  b->ws_streams = b->ws_bytes;
+  b->group = tpt::group_create(b->plans.data(), count);
+  if (b->group) {
+    b->grouped = true;
+    b->ws_bytes = tpt::group_workspace_bytes(b->group);
+  }
   *out = b;
+  return TPT_OK;
+}
+
+int tpt_batch_set_grouped(tpt_batch b, int grouped) {
+  if (!b || grouped < 0 || grouped > 1) return TPT_ERR_INVALID_ARG;
+  if (grouped && !b->group) {
+    // the plans' refinement settings may have changed since creation
+    b->group = tpt::group_create(b->plans.data(), b->count);
+    if (!b->group) return TPT_ERR_UNSUPPORTED;
+  }
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  b->key.clear();
+  b->grouped = grouped != 0;
+  b->ws_bytes = b->grouped ? tpt::group_workspace_bytes(b->group) : b->ws_streams;
+  return TPT_OK;
+}
+
+int tpt_batch_get_grouped(tpt_batch b, int* grouped) {
+  if (!b || !grouped) return TPT_ERR_INVALID_ARG;
+  *grouped = b->grouped ? 1 : 0;
   return TPT_OK;
 }
 
@@ -279,6 +322,14 @@ int tpt_batch_solve(tpt_batch b, const double* const* f, double* const* phi, voi
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   char* w = static_cast<char*>(work);
   b->solved = false;
+  if (b->grouped) {
+    const int st = tpt::group_prepare(b->group, f, phi, work, s);   // tables for these buffers
+    if (st == TPT_ERR_UNSUPPORTED) {
+      BT_TRY(tpt_batch_set_grouped(b, 0));   // buffers the grouped kernels cannot take
+      return TPT_ERR_UNSUPPORTED;
+    }
+    BT_TRY(st);
+  }
   if (same_key(b, key)) {
     BT_CUDA(cudaGraphLaunch(b->exec, s));
     tpt::note_launch(b->launches);

@@ -866,12 +866,10 @@ thomas2_kernel(const __grid_constant__ ThomasJob job0, ThomasGeom lg, int* next_
 // the line of T3.  One warp; it touches no other line, so it runs beside
 // thomas_tma_kernel on a second stream.
 template <int FMT>
-__global__ void __launch_bounds__(32)
-null_line_kernel(int nz, long long stride, const float* __restrict__ t2, void* t3_0, void* t3_1,
-                 const double* __restrict__ az, const double* __restrict__ ncp,
-                 const double* __restrict__ ninvm, const double* __restrict__ dz, double beta,
-                 const int* skip) {
-  if (skip && *skip) return;   // the refinement has stopped
+__device__ __forceinline__ void null_line_body(int nz, long long stride, const float* __restrict__ t2, void* t3_0,
+                                               void* t3_1, const double* __restrict__ az,
+                                               const double* __restrict__ ncp, const double* __restrict__ ninvm,
+                                               const double* __restrict__ dz, double beta) {
   extern __shared__ double line[];
   const int lane = threadIdx.x;
   double s = 0.0, w = 0.0;
@@ -905,6 +903,16 @@ null_line_kernel(int nz, long long stride, const float* __restrict__ t2, void* t
   const double mean = xs / w;
   for (int k = lane; k < nz; k += 32)
     Elem<FMT>::store(t3_0, t3_1, static_cast<long long>(k) * stride, static_cast<float>((line[k] - mean) / beta));
+}
+
+template <int FMT>
+__global__ void __launch_bounds__(32)
+null_line_kernel(int nz, long long stride, const float* __restrict__ t2, void* t3_0, void* t3_1,
+                 const double* __restrict__ az, const double* __restrict__ ncp,
+                 const double* __restrict__ ninvm, const double* __restrict__ dz, double beta,
+                 const int* skip) {
+  if (skip && *skip) return;   // the refinement has stopped
+  null_line_body<FMT>(nz, stride, t2, t3_0, t3_1, az, ncp, ninvm, dz, beta);
 }
 
 // ------------------------------------------------------------- residual
@@ -1250,23 +1258,48 @@ constexpr int kResZBytes = kResKseg * static_cast<int>(sizeof(ZCoef));
 constexpr int kResSmem = kResStages * kResStage + 2 * kResStages * 8 + kResZBytes + 128;
 constexpr int kResThreads = 32 * (kResTY + 1);
 
+// The residual of one instance for residual_tma_kernel: tensor maps of the
+// phi pair (with halo boxes) and of the f pair, sizes, rows and outputs.  A
+// grouped launch reads these from a device table, its block b taking tile
+// b - first of instance `job` (tiles x fastest, then y, then z segments).
+struct ResJob {
+  CUtensorMap tPH, tPL, tFH, tFL;
+  int nx, ny, nz, ldx, px, py;
+  const float *ph, *pl;
+  void *r0, *r1;
+  BRows RX, RY, RZ;
+  float alpha_h, alpha_l;
+  const double* fsums;
+  double inv_vol;
+  double* sums;
+  int* err;
+  const int* skip;
+  int first, tx, ty, tz;   // first block and tile counts of the instance
+};
+
 template <int FMT, int HAS_ALPHA, int WX, int WY, int WZ, int SING>
-__global__ void __launch_bounds__(kResThreads, 3)
-residual_tma_kernel(const __grid_constant__ CUtensorMap tPH, const __grid_constant__ CUtensorMap tPL,
-                    const __grid_constant__ CUtensorMap tFH, const __grid_constant__ CUtensorMap tFL, int nx,
-                    int ny, int nz, int ldx, int px, int py, const float* __restrict__ ph,
-                    const float* __restrict__ pl, void* r0, void* r1, BRows RX, BRows RY, BRows RZ,
-                    float alpha_h, float alpha_l, const double* __restrict__ fsums, double inv_vol,
-                    double* sums, int* err, const int* skip) {
-  if (skip && *skip) return;   // the refinement has stopped
+__device__ __forceinline__ void residual_tma_body(const ResJob& J, int bx, int by, int bz) {
+  const CUtensorMap& tPH = J.tPH;
+  const CUtensorMap& tPL = J.tPL;
+  const CUtensorMap& tFH = J.tFH;
+  const CUtensorMap& tFL = J.tFL;
+  const int nx = J.nx, ny = J.ny, nz = J.nz, ldx = J.ldx, px = J.px, py = J.py;
+  const float* __restrict__ ph = J.ph;
+  const float* __restrict__ pl = J.pl;
+  void* r0 = J.r0;
+  void* r1 = J.r1;
+  const BRows RX = J.RX, RY = J.RY, RZ = J.RZ;
+  const float alpha_h = J.alpha_h, alpha_l = J.alpha_l;
+  double* sums = J.sums;
+  int* err = J.err;
   extern __shared__ __align__(128) uint8_t res_smem_raw[];
   uint8_t* smem = res_smem_raw + ((128u - (ptx::smem_u32(res_smem_raw) & 127u)) & 127u);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kResStages * kResStage);
   uint64_t* empty = full + kResStages;
   ZCoef* zc = reinterpret_cast<ZCoef*>(empty + kResStages);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int i0 = blockIdx.x * kResTX, j0 = blockIdx.y * kResTY;
-  const int k0 = blockIdx.z * kResKseg;
+  const int i0 = bx * kResTX, j0 = by * kResTY;
+  const int k0 = bz * kResKseg;
   const int k1 = min(nz, k0 + kResKseg);
   const int nplanes = k1 - k0 + 2;                           // planes k0 - 1 .. k1
   if (threadIdx.x == 0) {
@@ -1318,7 +1351,7 @@ residual_tma_kernel(const __grid_constant__ CUtensorMap tPH, const __grid_consta
   // periodic directions: the edge points load their wrapped neighbours
   const bool edge = active && ((px && (i == 0 || i + 2 == nx)) || (py && (j == 0 || j == ny - 1)));
   const PairCoefs c = pair_coefs<WX, WY>(RX, RY, active ? i : 0, active ? j : 0);
-  const df fshift = SING ? fshift_of(fsums, inv_vol) : df{0.0f, 0.0f};
+  const df fshift = SING ? fshift_of(J.fsums, J.inv_vol) : df{0.0f, 0.0f};
   const int pc = (warp + 1) * kResPW + 4 + 2 * lane;          // centre of the pair in a phi stage
   const int fc = warp * kResTX + 2 * lane;
   const long long sz = static_cast<long long>(nx) * ny;
@@ -1407,6 +1440,35 @@ residual_tma_kernel(const __grid_constant__ CUtensorMap tPH, const __grid_consta
   if (lane == 0) atomicAdd(&sums[0], s2);
 }
 
+template <int FMT, int HAS_ALPHA, int WX, int WY, int WZ, int SING>
+__global__ void __launch_bounds__(kResThreads, 3)
+residual_tma_kernel(const __grid_constant__ ResJob J) {
+  if (J.skip && *J.skip) return;   // the refinement has stopped
+  residual_tma_body<FMT, HAS_ALPHA, WX, WY, WZ, SING>(J, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// index of the job whose first unit is the largest one <= u (jobs sorted by first)
+template <typename Job>
+__device__ __forceinline__ int job_index(const Job* __restrict__ jobs, int njobs, long long u) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (jobs[mid].first <= u) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Grouped residual: block b is a tile of the instance whose range holds it.
+template <int FMT, int HAS_ALPHA, int WX, int WY, int WZ, int SING>
+__global__ void __launch_bounds__(kResThreads, 3)
+residual_tma_group_kernel(const ResJob* __restrict__ jobs, int njobs) {
+  const ResJob& J = jobs[job_index(jobs, njobs, blockIdx.x)];
+  if (J.skip && *J.skip) return;
+  const int t = blockIdx.x - J.first;
+  residual_tma_body<FMT, HAS_ALPHA, WX, WY, WZ, SING>(J, t % J.tx, (t / J.tx) % J.ty, t / (J.tx * J.ty));
+}
+
 // sum of cell volume times phi (float pair) into *out, for the exact gauge;
 // work items are 256-point chunks of x-lines (one division per item)
 __global__ void __launch_bounds__(256)
@@ -1480,29 +1542,30 @@ df_to_f64_kernel(long long n, const float* __restrict__ h, const float* __restri
 // and the per-line weights and index divisions are shared by those points.
 // Same operations per point as the scalar kernels.
 template <int FMT>
-__global__ void __launch_bounds__(256)
-prepare2_kernel(int nx, int ny, int nz, int ldx, const double* __restrict__ f, float* __restrict__ fh,
-                float* __restrict__ fl, void* r0, void* r1, const float* __restrict__ gx,
-                const float* __restrict__ gy, const float* __restrict__ gz, double* sums) {
+__device__ __forceinline__ void prepare2_body(int bx, int G, int nx, int ny, int nz, int ldx,
+                                              const double* __restrict__ f, float* __restrict__ fh,
+                                              float* __restrict__ fl, void* r0, void* r1,
+                                              const float* __restrict__ gx, const float* __restrict__ gy,
+                                              const float* __restrict__ gz, double* sums) {
   // a block is blockDim.y rows of threads, one x-line (j, k) each, two
-  // points per thread; block b takes the line groups b, b + G, b + 2G, ...
-  // (G blocks), U of them per step, whose (j, k) advance by constant steps
-  // without a division
+  // points per thread; block bx takes the line groups bx, bx + G, bx + 2G,
+  // ... (G blocks), U of them per step, whose (j, k) advance by constant
+  // steps without a division
   const int lines = ny * nz;
   constexpr int U = 2;
-  const int G = gridDim.x, ty = blockDim.y;
+  const int ty = blockDim.y;
   const int step = U * G * ty;
   const int sj = step % ny, sk = step / ny;
   int jj[U], kk[U];
 #pragma unroll
   for (int u = 0; u < U; ++u) {
-    const int L = (blockIdx.x + u * G) * ty + threadIdx.y;
+    const int L = (bx + u * G) * ty + threadIdx.y;
     jj[u] = L % ny;
     kk[u] = L / ny;
   }
   float s2 = 0.0f, s1f = 0.0f;
   df sv = {0.0f, 0.0f};
-  for (int L0 = blockIdx.x * ty + threadIdx.y; L0 < lines; L0 += step) {
+  for (int L0 = bx * ty + threadIdx.y; L0 < lines; L0 += step) {
     for (int i = 2 * threadIdx.x; i < nx; i += 2 * blockDim.x) {
       double2 v[U];
 #pragma unroll
@@ -1575,26 +1638,34 @@ prepare2_kernel(int nx, int ny, int nz, int ldx, const double* __restrict__ f, f
   }
 }
 
+template <int FMT>
+__global__ void __launch_bounds__(256)
+prepare2_kernel(int nx, int ny, int nz, int ldx, const double* __restrict__ f, float* __restrict__ fh,
+                float* __restrict__ fl, void* r0, void* r1, const float* __restrict__ gx,
+                const float* __restrict__ gy, const float* __restrict__ gz, double* sums) {
+  prepare2_body<FMT>(blockIdx.x, gridDim.x, nx, ny, nz, ldx, f, fh, fl, r0, r1, gx, gy, gz, sums);
+}
+
 // sum of cell volume times phi, four points of an x-line per thread; lines
 // are distributed over blocks as in prepare2_kernel
-__global__ void __launch_bounds__(256, 4)
-wsum4_kernel(int nx, int ny, int nz, const float* __restrict__ h, const float* __restrict__ l,
-             const float* __restrict__ gx, const float* __restrict__ gy, const float* __restrict__ gz,
-             double* out) {
+__device__ __forceinline__ void wsum4_body(int bx, int G, int nx, int ny, int nz, const float* __restrict__ h,
+                                           const float* __restrict__ l, const float* __restrict__ gx,
+                                           const float* __restrict__ gy, const float* __restrict__ gz,
+                                           double* out) {
   const int lines = ny * nz;
   constexpr int U = 2;
-  const int G = gridDim.x, ty = blockDim.y;
+  const int ty = blockDim.y;
   const int step = U * G * ty;
   const int sj = step % ny, sk = step / ny;
   int jj[U], kk[U];
 #pragma unroll
   for (int u = 0; u < U; ++u) {
-    const int L = (blockIdx.x + u * G) * ty + threadIdx.y;
+    const int L = (bx + u * G) * ty + threadIdx.y;
     jj[u] = L % ny;
     kk[u] = L / ny;
   }
   df s = {0.0f, 0.0f};
-  for (int L0 = blockIdx.x * ty + threadIdx.y; L0 < lines; L0 += step) {
+  for (int L0 = bx * ty + threadIdx.y; L0 < lines; L0 += step) {
     for (int i = 4 * threadIdx.x; i < nx; i += 4 * blockDim.x) {
       float4 hh[U], ll[U];
 #pragma unroll
@@ -1633,14 +1704,21 @@ wsum4_kernel(int nx, int ny, int nz, const float* __restrict__ h, const float* _
   if ((threadIdx.x + blockDim.x * threadIdx.y) % 32 == 0) atomicAdd(out, v);
 }
 
+__global__ void __launch_bounds__(256, 4)
+wsum4_kernel(int nx, int ny, int nz, const float* __restrict__ h, const float* __restrict__ l,
+             const float* __restrict__ gx, const float* __restrict__ gy, const float* __restrict__ gz,
+             double* out) {
+  wsum4_body(blockIdx.x, gridDim.x, nx, ny, nz, h, l, gx, gy, gz, out);
+}
+
 // df_to_f64_kernel on groups of four points (n a multiple of 4, out 16-byte aligned)
-__global__ void __launch_bounds__(256)
-df_to_f64_v4_kernel(long long n4, const float4* __restrict__ h, const float4* __restrict__ l,
-                    const double* __restrict__ wsum, double inv_vol, double2* out) {
+__device__ __forceinline__ void df_to_f64_v4_body(int bx, int G, long long n4, const float4* __restrict__ h,
+                                                  const float4* __restrict__ l, const double* __restrict__ wsum,
+                                                  double inv_vol, double2* out) {
   const df shift = df_from_double(wsum ? *wsum * inv_vol : 0.0);
   constexpr int U = 2;
-  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
-  for (long long g0 = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; g0 < n4; g0 += U * stride) {
+  const long long stride = static_cast<long long>(G) * blockDim.x;
+  for (long long g0 = bx * static_cast<long long>(blockDim.x) + threadIdx.x; g0 < n4; g0 += U * stride) {
     float4 hh[U], ll[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -1658,6 +1736,12 @@ df_to_f64_v4_kernel(long long n4, const float4* __restrict__ h, const float4* __
       out[2 * g + 1] = make_double2(f2d_int(c.hi) + f2d_int(c.lo), f2d_int(d.hi) + f2d_int(d.lo));
     }
   }
+}
+
+__global__ void __launch_bounds__(256)
+df_to_f64_v4_kernel(long long n4, const float4* __restrict__ h, const float4* __restrict__ l,
+                    const double* __restrict__ wsum, double inv_vol, double2* out) {
+  df_to_f64_v4_body(blockIdx.x, gridDim.x, n4, h, l, wsum, inv_vol, out);
 }
 
 // rows x K float64 (row-major, stride K) -> operand planes with row stride ld
@@ -2109,6 +2193,52 @@ BRows rows_of(const float* t, int n) {
   return BRows{t, t + n, t + 2 * n, t + 3 * n, t + 4 * n, t + 5 * n};
 }
 
+// The residual job of a plan on workspace w with tensor maps m (phi pair,
+// f pair), its blocks numbered from `first`.
+ResJob res_job(const tpt_plan_s* p, const MixedWork& w, const CUtensorMap m[4], int first) {
+  const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
+  ResJob J;
+  std::memset(&J, 0, sizeof(J));
+  J.tPH = m[0];
+  J.tPL = m[1];
+  J.tFH = m[2];
+  J.tFL = m[3];
+  J.nx = nx;
+  J.ny = ny;
+  J.nz = nz;
+  J.ldx = p->mixed.ldx;
+  J.px = p->dir[0].periodic ? 1 : 0;
+  J.py = p->dir[1].periodic ? 1 : 0;
+  J.ph = w.ph;
+  J.pl = w.pl;
+  J.r0 = w.R[0];
+  J.r1 = w.R[1];
+  J.RX = rows_of(p->mixed.dfrows[0], nx);
+  J.RY = rows_of(p->mixed.dfrows[1], ny);
+  J.RZ = rows_of(p->mixed.dfrows[2], nz);
+  J.alpha_h = static_cast<float>(p->alpha);
+  J.alpha_l = static_cast<float>(p->alpha - static_cast<double>(J.alpha_h));
+  J.fsums = w.scal + 5;
+  J.inv_vol = 1.0 / p->vol;
+  J.sums = w.scal + 1;
+  J.err = reinterpret_cast<int*>(w.scal + 15);
+  J.skip = w.skip;
+  J.first = first;
+  J.tx = (nx + kResTX - 1) / kResTX;
+  J.ty = (ny + kResTY - 1) / kResTY;
+  J.tz = (nz + kResKseg - 1) / kResKseg;
+  return J;
+}
+
+bool res_maps(const tpt_plan_s* p, const MixedWork& w, CUtensorMap m[4]) {
+  const int nx = p->n[0];
+  const long long rows = static_cast<long long>(p->n[1]) * p->n[2];
+  return nx % 4 == 0 && tc::make_plain_map(&m[0], w.ph, 4, nx, rows, 4LL * nx, kResPW, kResTY + 2) &&
+         tc::make_plain_map(&m[1], w.pl, 4, nx, rows, 4LL * nx, kResPW, kResTY + 2) &&
+         tc::make_plain_map(&m[2], w.fh, 4, nx, rows, 4LL * nx, kResTX, kResTY) &&
+         tc::make_plain_map(&m[3], w.fl, 4, nx, rows, 4LL * nx, kResTX, kResTY);
+}
+
 template <int FMT, int HA, int WX, int WY, int WZ, int SING>
 cudaError_t launch_res(const tpt_plan_s* p, const MixedWork& w, cudaStream_t s) {
   const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
@@ -2128,12 +2258,8 @@ cudaError_t launch_res(const tpt_plan_s* p, const MixedWork& w, cudaStream_t s) 
       auto kern = residual_tma_kernel<FMT, HA, WX, WY, WZ, SING>;
       cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kResSmem);
       if (e != cudaSuccess) return e;
-      dim3 gt((nx + kResTX - 1) / kResTX, (ny + kResTY - 1) / kResTY, (nz + kResKseg - 1) / kResKseg);
-      kern<<<gt, kResThreads, kResSmem, s>>>(
-          m[0], m[1], m[2], m[3], nx, ny, nz, p->mixed.ldx, p->dir[0].periodic ? 1 : 0,
-          p->dir[1].periodic ? 1 : 0, w.ph, w.pl, w.R[0], w.R[1], rows_of(p->mixed.dfrows[0], nx),
-          rows_of(p->mixed.dfrows[1], ny), rows_of(p->mixed.dfrows[2], nz), ah, al, w.scal + 5, 1.0 / p->vol,
-          w.scal + 1, reinterpret_cast<int*>(w.scal + 15), w.skip);
+      const ResJob J = res_job(p, w, m, 0);
+      kern<<<dim3(J.tx, J.ty, J.tz), kResThreads, kResSmem, s>>>(J);
       return cudaGetLastError();
     }
   }
@@ -2239,8 +2365,7 @@ int correction(tpt_plan_s* p, const MixedWork& w, bool accumulate, cudaStream_t 
 // wait, and from then on every kernel of a later correction returns at entry;
 // scal[8] + 4 bytes counts the corrections applied; scal[11], scal[12] keep
 // the last r^2 and f^2 sums; otherwise r's sum is cleared for the next residual.
-__global__ void converge_kernel(double* scal, double npts, double vol, int singular, double rtol) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ __forceinline__ void converge_body(double* scal, double npts, double vol, int singular, double rtol) {
   int* flags = reinterpret_cast<int*>(scal + 8);
   if (flags[0]) return;
   flags[1] += 1;
@@ -2269,9 +2394,103 @@ __global__ void converge_kernel(double* scal, double npts, double vol, int singu
   scal[2] = 0.0;
 }
 
+__global__ void converge_kernel(double* scal, double npts, double vol, int singular, double rtol) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  converge_body(scal, npts, vol, singular, rtol);
+}
+
 // The 16 workspace scalars into a pinned, device-mapped host slot.
 __global__ void scal_to_host_kernel(const double* __restrict__ scal, double* host) {
   if (threadIdx.x < 16) host[threadIdx.x] = scal[threadIdx.x];
+}
+
+// ------------------------------------------------------- grouped launches
+// The per-instance data of the grouped stage kernels of a batch: each of
+// those kernels runs once over all instances, a block (or thread) finding its
+// instance from the block ranges `first[...]` (ascending).
+struct InstJob {
+  int nx, ny, nz, ldx;
+  const double* f;
+  double* phi;
+  float *fh, *fl, *ph, *pl;
+  void *r0, *r1;
+  const float *gx, *gy, *gz;   // cell widths as float pairs
+  double* scal;                // the instance's 16 workspace scalars
+  int singular;
+  double npts, vol, rtol;
+  // the float64 null line of a singular instance
+  long long nl_stride;
+  const float* t2;
+  void *t3_0, *t3_1;
+  const double *az, *ncp, *ninvm, *dz;
+  double beta;
+  const int* skip;
+  int first[3], blocks[3];     // block ranges of the prepare, gauge-sum and output kernels
+};
+
+__device__ __forceinline__ int inst_of(const InstJob* __restrict__ jobs, int njobs, int range, int b) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (jobs[mid].first[range] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// every instance's workspace scalars cleared (one block of 32 per instance)
+__global__ void group_clear_kernel(const InstJob* __restrict__ jobs) {
+  if (threadIdx.x < 16) jobs[blockIdx.x].scal[threadIdx.x] = 0.0;
+}
+
+template <int FMT>
+__global__ void __launch_bounds__(256) group_prepare_kernel(const InstJob* __restrict__ jobs, int njobs) {
+  const InstJob& J = jobs[inst_of(jobs, njobs, 0, blockIdx.x)];
+  prepare2_body<FMT>(blockIdx.x - J.first[0], J.blocks[0], J.nx, J.ny, J.nz, J.ldx, J.f, J.fh, J.fl, J.r0, J.r1,
+                     J.gx, J.gy, J.gz, J.scal + 5);
+}
+
+// the float64 null lines of the singular instances in `ids` (one block each)
+template <int FMT>
+__global__ void __launch_bounds__(32)
+group_null_line_kernel(const InstJob* __restrict__ jobs, const int* __restrict__ ids) {
+  const InstJob& J = jobs[ids[blockIdx.x]];
+  if (J.skip && *J.skip) return;
+  null_line_body<FMT>(J.nz, J.nl_stride, J.t2, J.t3_0, J.t3_1, J.az, J.ncp, J.ninvm, J.dz, J.beta);
+}
+
+// stopping test of every instance (one thread each)
+__global__ void group_converge_kernel(const InstJob* __restrict__ jobs, int njobs) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= njobs) return;
+  const InstJob& J = jobs[i];
+  converge_body(J.scal, J.npts, J.vol, J.singular, J.rtol);
+}
+
+// gauge sums of the singular instances (scal[2] cleared beforehand)
+__global__ void __launch_bounds__(256, 4) group_wsum_kernel(const InstJob* __restrict__ jobs, int njobs) {
+  const InstJob& J = jobs[inst_of(jobs, njobs, 1, blockIdx.x)];
+  if (!J.singular || J.blocks[1] == 0) return;
+  wsum4_body(blockIdx.x - J.first[1], J.blocks[1], J.nx, J.ny, J.nz, J.ph, J.pl, J.gx, J.gy, J.gz, J.scal + 2);
+}
+
+__global__ void __launch_bounds__(256) group_output_kernel(const InstJob* __restrict__ jobs, int njobs) {
+  const InstJob& J = jobs[inst_of(jobs, njobs, 2, blockIdx.x)];
+  const long long n4 = static_cast<long long>(J.npts) / 4;
+  df_to_f64_v4_body(blockIdx.x - J.first[2], J.blocks[2], n4, reinterpret_cast<const float4*>(J.ph),
+                    reinterpret_cast<const float4*>(J.pl), J.singular ? J.scal + 2 : nullptr, 1.0 / J.vol,
+                    reinterpret_cast<double2*>(J.phi));
+}
+
+// every instance's gauge sum cleared (one thread each)
+__global__ void group_clear2_kernel(const InstJob* __restrict__ jobs, int njobs) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < njobs) jobs[i].scal[2] = 0.0;
+}
+
+// every instance's 16 scalars into out[16 i .. 16 i + 15] (one block of 32 each)
+__global__ void group_gather_kernel(const InstJob* __restrict__ jobs, double* out) {
+  if (threadIdx.x < 16) out[16 * blockIdx.x + threadIdx.x] = jobs[blockIdx.x].scal[threadIdx.x];
 }
 
 double proj_norm2(const double* h, double npts, double vol, bool singular) {
@@ -2727,6 +2946,376 @@ int mixed_enqueue(tpt_plan_s* p, const double* f, double* phi, void* work, cudaS
     case kFmtBF16: return solve_fmt<kFmtBF16>(p, f, phi, work, s, nullptr, true);
     default: return solve_fmt<kFmtF32>(p, f, phi, work, s, nullptr, true);
   }
+}
+
+// ------------------------------------------------------ grouped batch solve
+// Every instance of a batch solved by grouped launches: one kernel per stage
+// over all instances (per Thomas segment length and per residual variant),
+// each taking its units (tiles of a GEMM, line tiles of the Thomas sweep,
+// plane tiles of the residual, blocks of the elementwise stages) from the
+// whole batch; an instance that has met its rtol stops, its units passed
+// over by every later kernel.  Qualifying batches: split-bf16 plans with
+// rtol > 0, Nx a multiple of 4, Nz <= 512.
+struct GroupSolve {
+  int n = 0, dev = 0;
+  std::vector<tpt_plan_s*> plans;
+  std::vector<size_t> ws_off;          // workspace of instance i at work + ws_off[i]
+  size_t ws_bytes = 0;
+  // device tables: instances, GEMM jobs of the four stages (x inverse: first
+  // correction and later ones), Thomas jobs per segment length, residual jobs
+  // per variant, ids of the singular instances, Thomas tile counters
+  void* dmem = nullptr;
+  size_t dmem_bytes = 0;
+  InstJob* d_inst = nullptr;
+  tc::GemmJob* d_gemm[5] = {};
+  long long gemm_units[5] = {};
+  bool gemm_tma[5] = {};
+  struct TGroup { int m = 0; int njobs = 0; int tiles = 0; ThomasGeom lg{}; ThomasJob* d = nullptr; };
+  std::vector<TGroup> tg;
+  struct RGroup { int code = 0; int njobs = 0; int blocks = 0; ResJob* d = nullptr; };
+  std::vector<RGroup> rg;
+  int* d_null_ids = nullptr;
+  int nnull = 0;
+  int* d_counters = nullptr;           // one per Thomas group and correction
+  int max_nz = 0;
+  int blocks[3] = {0, 0, 0};           // prepare, gauge sum, output
+  std::vector<const void*> key;        // buffers the tables were built for
+  std::vector<unsigned> gens;
+  unsigned long long kernels = 0;      // kernels of the last enqueue
+};
+
+namespace {
+
+int res_code(const tpt_plan_s* p) {
+  if (p->singular) return 1;
+  const int* hw = p->mixed.has_w;
+  if (!hw[0] && !hw[1] && !hw[2]) return p->alpha != 0.0 ? 2 : 0;
+  return p->alpha != 0.0 ? 3 : 4;
+}
+
+template <int HA, int WX, int WY, int WZ, int SING>
+cudaError_t launch_res_group(const GroupSolve::RGroup& r, cudaStream_t s) {
+  auto kern = residual_tma_group_kernel<kFmtSplit, HA, WX, WY, WZ, SING>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kResSmem);
+  if (e != cudaSuccess) return e;
+  note_launch(1);
+  kern<<<r.blocks, kResThreads, kResSmem, s>>>(r.d, r.njobs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_res_code(const GroupSolve::RGroup& r, cudaStream_t s) {
+  switch (r.code) {
+    case 0: return launch_res_group<0, 0, 0, 0, 0>(r, s);
+    case 1: return launch_res_group<0, 0, 0, 0, 1>(r, s);
+    case 2: return launch_res_group<1, 0, 0, 0, 0>(r, s);
+    case 3: return launch_res_group<1, 1, 1, 1, 0>(r, s);
+    default: return launch_res_group<0, 1, 1, 1, 0>(r, s);
+  }
+}
+
+template <int M>
+cudaError_t launch_thomas_group(const GroupSolve::TGroup& t, int* counter, int dev, cudaStream_t s) {
+  auto kern = thomas2_kernel<kFmtSplit, M, 1>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kT2SmemBudget);
+  if (e != cudaSuccess) return e;
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = t.tiles < sms ? t.tiles : sms;
+  ThomasJob none;
+  std::memset(&none, 0, sizeof(none));
+  note_launch(1);
+  kern<<<grid, kThomasThreads, thomas2_smem(t.lg), s>>>(none, t.lg, counter, t.tiles, t.d, t.njobs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_thomas_m_group(const GroupSolve::TGroup& t, int* counter, int dev, cudaStream_t s) {
+  switch (t.m) {
+    case 4: return launch_thomas_group<4>(t, counter, dev, s);
+    case 8: return launch_thomas_group<8>(t, counter, dev, s);
+    case 12: return launch_thomas_group<12>(t, counter, dev, s);
+    case 16: return launch_thomas_group<16>(t, counter, dev, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int M>
+bool thomas_job_m(const tpt_plan_s* p, const MixedWork& w, int first, ThomasJob* J) {
+  return thomas2_job<kFmtSplit, M>(p, w, first, J);
+}
+
+bool thomas_job_any(int m, const tpt_plan_s* p, const MixedWork& w, int first, ThomasJob* J) {
+  switch (m) {
+    case 4: return thomas_job_m<4>(p, w, first, J);
+    case 8: return thomas_job_m<8>(p, w, first, J);
+    case 12: return thomas_job_m<12>(p, w, first, J);
+    case 16: return thomas_job_m<16>(p, w, first, J);
+    default: return false;
+  }
+}
+
+}  // namespace
+
+GroupSolve* group_create(tpt_plan_s* const* plans, int n) {
+  if (n <= 0) return nullptr;
+  for (int i = 0; i < n; ++i) {
+    const tpt_plan_s* p = plans[i];
+    if (p->precision != TPT_PREC_MIXED_BF16X3 || p->mixed.fmt != kFmtSplit || !(p->rtol > 0.0)) return nullptr;
+    if (p->n[0] % 4 != 0 || thomas2_m(p->n[2]) == 0 || p->dev != plans[0]->dev) return nullptr;
+  }
+  GroupSolve* g = new (std::nothrow) GroupSolve;
+  if (!g) return nullptr;
+  g->n = n;
+  g->dev = plans[0]->dev;
+  g->plans.assign(plans, plans + n);
+  for (int i = 0; i < n; ++i) {
+    g->ws_off.push_back(g->ws_bytes);
+    g->ws_bytes += align256(mixed_workspace_bytes(plans[i]));
+    g->max_nz = std::max(g->max_nz, plans[i]->n[2]);
+  }
+  return g;
+}
+
+void group_destroy(GroupSolve* g) {
+  if (!g) return;
+  if (g->dmem) cudaFree(g->dmem);
+  delete g;
+}
+
+size_t group_workspace_bytes(const GroupSolve* g) { return g ? g->ws_bytes : 0; }
+unsigned long long group_kernels(const GroupSolve* g) { return g ? g->kernels : 0; }
+
+// Builds the job tables for these buffers and copies them to the device
+// (synchronously, so that the launches may be captured afterwards).
+int group_prepare(GroupSolve* g, const double* const* f, double* const* phi, void* work, cudaStream_t s) {
+  for (int i = 0; i < g->n; ++i)   // 16-byte vector loads of f and stores of phi
+    if (reinterpret_cast<uintptr_t>(f[i]) % 16 != 0 || reinterpret_cast<uintptr_t>(phi[i]) % 16 != 0)
+      return TPT_ERR_UNSUPPORTED;
+  std::vector<const void*> key;
+  std::vector<unsigned> gens;
+  for (int i = 0; i < g->n; ++i) {
+    key.push_back(f[i]);
+    key.push_back(phi[i]);
+    gens.push_back(g->plans[i]->generation);
+  }
+  key.push_back(work);
+  if (g->dmem && key == g->key && gens == g->gens) return TPT_OK;
+  const int n = g->n;
+  std::vector<MixedWork> ws(n);
+  for (int i = 0; i < n; ++i) ws[i] = carve(g->plans[i], static_cast<char*>(work) + g->ws_off[i]);
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->dev);
+  // instances and the block ranges of the elementwise stages
+  std::vector<InstJob> inst(n);
+  int nb[3] = {0, 0, 0};
+  std::vector<int> null_ids;
+  for (int i = 0; i < n; ++i) {
+    const tpt_plan_s* p = g->plans[i];
+    const MixedWork& w = ws[i];
+    InstJob& J = inst[i];
+    std::memset(&J, 0, sizeof(J));
+    J.nx = p->n[0];
+    J.ny = p->n[1];
+    J.nz = p->n[2];
+    J.ldx = p->mixed.ldx;
+    J.f = f[i];
+    J.phi = phi[i];
+    J.fh = w.fh;
+    J.fl = w.fl;
+    J.ph = w.ph;
+    J.pl = w.pl;
+    J.r0 = w.R[0];
+    J.r1 = w.R[1];
+    J.gx = p->mixed.dfgeom[0];
+    J.gy = p->mixed.dfgeom[1];
+    J.gz = p->mixed.dfgeom[2];
+    J.scal = w.scal;
+    J.singular = p->singular ? 1 : 0;
+    J.npts = static_cast<double>(npts(p));
+    J.vol = p->vol;
+    J.rtol = p->rtol;
+    J.nl_stride = static_cast<long long>(p->mixed.ldy) * p->n[0];
+    J.t2 = static_cast<const float*>(w.B[0]);
+    J.t3_0 = w.A[0];
+    J.t3_1 = w.A[1];
+    J.az = p->d_rows[2];
+    J.ncp = p->mixed.null_cp;
+    J.ninvm = p->mixed.null_invm;
+    J.dz = p->d_dxf[2];
+    J.beta = p->beta;
+    J.skip = w.skip;
+    const long long lines = static_cast<long long>(p->n[1]) * p->n[2];
+    const int per_block = 8;                    // lines of a 32 x 8 block
+    const int b0 = static_cast<int>(std::min<long long>((lines + per_block - 1) / per_block, 2LL * sms));
+    const int b2 = static_cast<int>(std::min<long long>((npts(p) / 4 + 255) / 256, 2LL * sms));
+    J.first[0] = nb[0];
+    J.blocks[0] = b0;
+    nb[0] += b0;
+    J.first[1] = nb[1];
+    J.blocks[1] = p->singular ? b0 : 0;
+    nb[1] += J.blocks[1];
+    J.first[2] = nb[2];
+    J.blocks[2] = b2;
+    nb[2] += b2;
+    if (p->singular) null_ids.push_back(i);
+  }
+  for (int r = 0; r < 3; ++r) g->blocks[r] = nb[r];
+  // GEMM jobs: x forward, y forward, y inverse, x inverse (first, later)
+  std::vector<tc::GemmJob> gj[5];
+  for (int st = 0; st < 5; ++st) {
+    const int stage = st < 4 ? st : 3;
+    long long units = 0;
+    bool tma = (stage == 0 || stage == 2 || stage == 1);
+    for (int pass = 0; pass < 2; ++pass) {   // with the TMA-store epilogue if every job allows it
+      gj[st].assign(n, tc::GemmJob{});
+      units = 0;
+      bool ok = true;
+      for (int i = 0; i < n && ok; ++i) {
+        const StageGemm t = stage_gemm(g->plans[i], ws[i], stage, st == 4);
+        tc::GemmOut go = t.g;
+        go.skip = ws[i].skip;
+        go.bn = 256;
+        ok = tc::make_job(t.a, t.b, go, tma, &gj[st][i], units);
+        units += tc::job_units(go);
+      }
+      if (ok) break;
+      if (!tma) return TPT_ERR_UNSUPPORTED;
+      tma = false;
+    }
+    g->gemm_units[st] = units;
+    g->gemm_tma[st] = tma;
+  }
+  // Thomas jobs grouped by segment length, residual jobs by variant
+  std::vector<std::vector<ThomasJob>> tj;
+  std::vector<GroupSolve::TGroup> tg;
+  std::vector<std::vector<ResJob>> rj;
+  std::vector<GroupSolve::RGroup> rg;
+  for (int i = 0; i < n; ++i) {
+    const tpt_plan_s* p = g->plans[i];
+    const int m = thomas2_m(p->n[2]);
+    size_t k = 0;
+    while (k < tg.size() && tg[k].m != m) ++k;
+    if (k == tg.size()) {
+      tg.push_back(GroupSolve::TGroup{});
+      tg[k].m = m;
+      tg[k].lg.stages = 2;
+      tj.emplace_back();
+    }
+    ThomasJob J;
+    if (!thomas_job_any(m, p, ws[i], tg[k].tiles, &J)) return TPT_ERR_UNSUPPORTED;
+    tg[k].tiles += J.ntiles;
+    tg[k].lg.in_bytes = std::max(tg[k].lg.in_bytes, J.geo.in_bytes);
+    tg[k].lg.out_bytes = std::max(tg[k].lg.out_bytes, J.geo.out_bytes);
+    tg[k].lg.coef_bytes = std::max(tg[k].lg.coef_bytes, J.geo.coef_bytes);
+    tj[k].push_back(J);
+    const int code = res_code(p);
+    size_t r = 0;
+    while (r < rg.size() && rg[r].code != code) ++r;
+    if (r == rg.size()) {
+      rg.push_back(GroupSolve::RGroup{});
+      rg[r].code = code;
+      rj.emplace_back();
+    }
+    CUtensorMap m4[4];
+    if (!res_maps(p, ws[i], m4)) return TPT_ERR_UNSUPPORTED;
+    const ResJob R = res_job(p, ws[i], m4, rg[r].blocks);
+    rg[r].blocks += R.tx * R.ty * R.tz;
+    rj[r].push_back(R);
+  }
+  for (auto& t : tg) {   // as many stages as the budget holds beside the output tile and rows
+    const long long room = static_cast<long long>(kT2SmemBudget) - 1024 - t.lg.coef_bytes - t.lg.out_bytes;
+    t.lg.stages = static_cast<int>(std::min<long long>(kThomasMaxStages, room / std::max(1, t.lg.in_bytes)));
+    if (t.lg.stages < 2) return TPT_ERR_UNSUPPORTED;
+    t.njobs = 0;
+  }
+  // one device block for every table
+  size_t bytes = align256(sizeof(InstJob) * n);
+  for (int st = 0; st < 5; ++st) bytes += align256(sizeof(tc::GemmJob) * n);
+  for (auto& v : tj) bytes += align256(sizeof(ThomasJob) * v.size());
+  for (auto& v : rj) bytes += align256(sizeof(ResJob) * v.size());
+  bytes += align256(sizeof(int) * std::max<size_t>(1, null_ids.size()));
+  const int max_corr = 64;
+  bytes += align256(sizeof(int) * tg.size() * max_corr);
+  if (bytes > g->dmem_bytes) {
+    MX_CUDA(cudaStreamSynchronize(s));
+    if (g->dmem) cudaFree(g->dmem);
+    g->dmem = nullptr;
+    g->dmem_bytes = 0;
+    MX_CUDA(cudaMalloc(&g->dmem, bytes));
+    g->dmem_bytes = bytes;
+  }
+  std::vector<char> host(bytes, 0);
+  size_t off = 0;
+  auto put = [&](const void* src, size_t sz) {   // src null: a region left zero
+    if (sz && src) std::memcpy(host.data() + off, src, sz);
+    void* dptr = static_cast<char*>(g->dmem) + off;
+    off += align256(sz ? sz : 1);
+    return dptr;
+  };
+  g->d_inst = static_cast<InstJob*>(put(inst.data(), sizeof(InstJob) * n));
+  for (int st = 0; st < 5; ++st) g->d_gemm[st] = static_cast<tc::GemmJob*>(put(gj[st].data(), sizeof(tc::GemmJob) * n));
+  for (size_t k = 0; k < tg.size(); ++k) {
+    tg[k].njobs = static_cast<int>(tj[k].size());
+    tg[k].d = static_cast<ThomasJob*>(put(tj[k].data(), sizeof(ThomasJob) * tj[k].size()));
+  }
+  for (size_t r = 0; r < rg.size(); ++r) {
+    rg[r].njobs = static_cast<int>(rj[r].size());
+    rg[r].d = static_cast<ResJob*>(put(rj[r].data(), sizeof(ResJob) * rj[r].size()));
+  }
+  g->d_null_ids = static_cast<int*>(put(null_ids.data(), sizeof(int) * null_ids.size()));
+  g->nnull = static_cast<int>(null_ids.size());
+  g->d_counters = static_cast<int*>(put(nullptr, sizeof(int) * tg.size() * max_corr));
+  // a solve still in flight on s may be reading the previous tables
+  MX_CUDA(cudaStreamSynchronize(s));
+  MX_CUDA(cudaMemcpy(g->dmem, host.data(), bytes, cudaMemcpyHostToDevice));
+  g->tg = tg;
+  g->rg = rg;
+  g->key = key;
+  g->gens = gens;
+  return TPT_OK;
+}
+
+// The grouped solve on stream s (tables from group_prepare): every instance's
+// scalars cleared, f converted, corrections until each instance's rtol or the
+// largest 1 + max_refine of the batch, the gauge and the float64 output, and
+// the 16 scalars of instance i gathered into d_scal[16 i ..].
+int group_enqueue(GroupSolve* g, double* d_scal, cudaStream_t s) {
+  int corrections = 1;
+  for (tpt_plan_s* p : g->plans) corrections = std::max(corrections, 1 + p->max_refine);
+  if (corrections > 64) return TPT_ERR_UNSUPPORTED;
+  const unsigned long long before = launch_count();
+  const int n = g->n;
+  note_launch(2);
+  group_clear_kernel<<<n, 32, 0, s>>>(g->d_inst);
+  group_prepare_kernel<kFmtSplit><<<g->blocks[0], dim3(32, 8), 0, s>>>(g->d_inst, n);
+  MX_CUDA(cudaGetLastError());
+  MX_CUDA(cudaMemsetAsync(g->d_counters, 0, sizeof(int) * g->tg.size() * 64, s));
+  const size_t null_smem = static_cast<size_t>(g->max_nz) * sizeof(double);
+  for (int c = 0; c < corrections; ++c) {
+    for (int st : {0, 1}) MX_CUDA(tc::gemm_grouped(st == 1 ? tc::kOutF32 : tc::kOutSplitBF16, g->gemm_tma[st],
+                                                  g->d_gemm[st], n, g->gemm_units[st], s));
+    for (size_t k = 0; k < g->tg.size(); ++k)
+      MX_CUDA(launch_thomas_m_group(g->tg[k], g->d_counters + 64 * k + c, g->dev, s));
+    if (g->nnull > 0) {
+      note_launch(1);
+      group_null_line_kernel<kFmtSplit><<<g->nnull, 32, null_smem, s>>>(g->d_inst, g->d_null_ids);
+      MX_CUDA(cudaGetLastError());
+    }
+    MX_CUDA(tc::gemm_grouped(tc::kOutSplitBF16, g->gemm_tma[2], g->d_gemm[2], n, g->gemm_units[2], s));
+    const int xi = c == 0 ? 3 : 4;
+    MX_CUDA(tc::gemm_grouped(tc::kOutDF, false, g->d_gemm[xi], n, g->gemm_units[xi], s));
+    for (const auto& r : g->rg) MX_CUDA(launch_res_code(r, s));
+    note_launch(1);
+    group_converge_kernel<<<(n + 127) / 128, 128, 0, s>>>(g->d_inst, n);
+    MX_CUDA(cudaGetLastError());
+  }
+  note_launch(4);
+  group_clear2_kernel<<<(n + 127) / 128, 128, 0, s>>>(g->d_inst, n);
+  if (g->blocks[1] > 0) group_wsum_kernel<<<g->blocks[1], dim3(64, 4), 0, s>>>(g->d_inst, n);
+  group_output_kernel<<<g->blocks[2], 256, 0, s>>>(g->d_inst, n);
+  group_gather_kernel<<<n, 32, 0, s>>>(g->d_inst, d_scal);
+  MX_CUDA(cudaGetLastError());
+  g->kernels = launch_count() - before;
+  return TPT_OK;
 }
 
 int autotune_gemms(tpt_plan_s* p, void* work, cudaStream_t s) {

@@ -254,6 +254,21 @@ int mixed_enqueue(tpt_plan_s* p, const double* f, double* phi, void* work, cudaS
 int mixed_info(const tpt_plan_s* p, const double* h, tpt_info* info);
 int solve_enqueue(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStream_t s);
 int solve_info(const tpt_plan_s* p, const double* h, tpt_info* info);
+// Grouped batch solve (mixed.cu): one kernel per stage over every instance.
+// group_create returns null unless every plan qualifies (split bf16, rtol > 0,
+// Nx a multiple of 4, Nz <= 512, one device).  group_prepare builds the
+// device job tables for the buffers (synchronising s first; a no-op when
+// they are unchanged), instance i using work + its offset; group_enqueue then issues
+// the launches on s (capturable) and gathers the 16 scalars of instance i
+// into d_scal[16 i ..].
+struct GroupSolve;
+GroupSolve* group_create(tpt_plan_s* const* plans, int n);
+void group_destroy(GroupSolve* g);
+size_t group_workspace_bytes(const GroupSolve* g);
+unsigned long long group_kernels(const GroupSolve* g);
+int group_prepare(GroupSolve* g, const double* const* f, double* const* phi, void* work, cudaStream_t s);
+int group_enqueue(GroupSolve* g, double* d_scal, cudaStream_t s);
+
 // Times the transform GEMMs of a mixed plan over the candidate tiles and keeps
 // the fastest per stage (gemm_tune.cu).
 int autotune_gemms(tpt_plan_s* p, void* work, cudaStream_t s);

@@ -412,6 +412,20 @@ class Batch:
     def new_workspace(self) -> torch.Tensor:
         return torch.empty(self.workspace_bytes, dtype=torch.uint8, device="cuda:%d" % self.device)
 
+    @property
+    def grouped(self) -> bool:
+        v = C.c_int()
+        check(lib.tpt_batch_get_grouped(self._h, C.byref(v)), "tpt_batch_get_grouped")
+        return bool(v.value)
+
+    def set_grouped(self, on: bool):
+        """tpt_batch_set_grouped: grouped launches (True) or capture streams
+        (False); the workspace size follows the mode."""
+        check(lib.tpt_batch_set_grouped(self._h, int(bool(on))), "tpt_batch_set_grouped")
+        nb = C.c_size_t()
+        check(lib.tpt_batch_workspace_bytes(self._h, C.byref(nb)), "tpt_batch_workspace_bytes")
+        self.workspace_bytes = int(nb.value)
+
     def autotune(self, work: torch.Tensor, stream=None):
         check(lib.tpt_batch_autotune(self._h, _ptr(work), _stream(stream)), "tpt_batch_autotune")
         return [p.tiles() for p in self.plans]
