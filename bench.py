@@ -409,6 +409,8 @@ def run_ours(args):
     if not args.no_serving:
         serving = {"mixed": serving_leg(tpt, local, prec if prec != 0 else 2, args.serve_requests,
                                         args.serve_warmup)}
+        serving["same_shape_bursts"] = [merge_leg(tpt, local, count=96, n=(64, 64, 64), slots=2),
+                                        merge_leg(tpt, local, count=64, n=(96, 96, 96), slots=4)]
         if not args.no_fp64:
             serving["fp64"] = serving_leg(tpt, local, 0, args.serve_requests_fp64, 10)
 
@@ -653,11 +655,55 @@ def serving_leg(tpt, device, prec, count, warmup, rate_hz=200.0, slots=4, stretc
             "phase_ms_p50": {"plan": float(np.median(plan_ms)), "queue": float(np.median(queue_ms)),
                              "h2d_solve_d2h": float(np.median(run_ms))},
             "solves_per_s": count / span, "gpts_per_s": pts / span / 1e9,
+            "same_shape_batching": {"merge": 8, "merged_fraction": float(np.mean([x.get("merged", 1) > 1
+                                                                                 for x in meas])),
+                                    "max_merged": int(max(x.get("merged", 1) for x in meas))},
             "failed": bad, "failed_statuses": statuses, "failures": failures[:8], "warm_s": t_warm, "warmed_plans": len(seen),
             "max_rel_residual": float(max(x["rel_residual"] for x in meas)),
             "cache": {"hits": int(st["cache_hits"]), "misses": int(st["cache_misses"]),
                       "device_bytes": int(st["cache_bytes"])},
             "peak_inflight": int(st["peak_inflight"]), "peak_device_bytes": int(st["peak_bytes"])}
+
+
+def merge_leg(tpt, device, count=64, n=(96, 96, 96), slots=4):
+    """Same-shape batching: `count` requests of one grid size (split bf16
+    Poisson, rtol 1e-10, stretching varied per request so each has its own
+    eigenbases) submitted at once, served with merging off and with up to 8
+    requests solved together; solves/s from the first submission to the last
+    completion, and p50/p99 of the request latency."""
+    import torch
+    npts = n[0] * n[1] * n[2]
+    f = (torch.rand(npts, dtype=torch.float64) * 2 - 1).pin_memory()
+    outs = [torch.empty(npts, dtype=torch.float64).pin_memory() for _ in range(count)]
+    specs = []
+    for i in range(count):
+        st = (1.0 + 0.25 * (i % 5), 1.25 + 0.25 * (i % 4), 1.5 + 0.25 * (i % 3))
+        gs = [tpt.grid_tanh(n[a], 1.0, st[a]) for a in range(3)]
+        specs.append(dict(n=n, dxf=[g[0] for g in gs], dxc=[g[1] for g in gs], bc=[(1, 1)] * 3,
+                          xform=(tpt.GEMM, tpt.GEMM), alpha=1.0, beta=-5e-4, precision=2, rtol=1e-10,
+                          max_refine=30))
+    out = {"requests": count, "grid": list(n), "slots": slots}
+    for merge in (1, 8):
+        srv = tpt.Server(device=device, slots=slots, setup_threads=4, memory_budget=32 << 30,
+                         cache_budget=4 << 30, merge=merge)
+        try:
+            for sp in specs:
+                srv.warm(**sp)
+            for t in [srv.submit(f, outs[i], **specs[i]) for i in range(8)]:   # warm-up
+                srv.wait(t, timeout=300.0)
+            t0 = time.perf_counter()
+            tickets = [srv.submit(f, outs[i], **specs[i]) for i in range(count)]
+            res = [srv.wait(t, timeout=300.0) for t in tickets]
+            dt = time.perf_counter() - t0
+        finally:
+            srv.close()
+        lat = np.array([(r["t_done"] - r["t_submit"]) * 1e3 for r in res])
+        out["merge%d" % merge] = {"solves_per_s": count / dt, "p50_ms": float(np.percentile(lat, 50)),
+                                  "p99_ms": float(np.percentile(lat, 99)),
+                                  "mean_merged": float(np.mean([r["merged"] for r in res])),
+                                  "failed": sum(1 for r in res if r["status"] != 0),
+                                  "max_rel_residual": float(max(r["rel_residual"] for r in res))}
+    return out
 
 
 def fft_leg(tpt, n, stream, steps):

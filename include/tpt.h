@@ -467,7 +467,15 @@ int tpt_cache_destroy(tpt_cache cache);
  * solve it (adaptive refinement when the descriptor's rtol > 0) and copy the
  * solution out.  Requests that arrive while others are on the device are
  * admitted as slots and memory free up, and their work overlaps on the device
- * through the slot streams.  cuda_device < 0 is a dry run on the host: plans
+ * through the slot streams.  Same-shape batching (config.merge > 1): a slot
+ * that admits a request of fewer than 2^24 points also takes the other ready
+ * requests of the same grid size and precision (up to `merge` in all, within
+ * the budget; only when at least three are ready, smaller groups being
+ * served faster one by one) and solves them together as one grouped batch (see
+ * tpt_batch_set_grouped; split-bf16 requests with rtol > 0, Nx a multiple of
+ * 4, Nz <= 512): one set of grouped kernels for all of them, their buffers and
+ * job tables from the server's memory pool.  Each result is that of its own
+ * solve to within the refinement target.  cuda_device < 0 is a dry run on the host: plans
  * are host-only and a solve is simulated as a sleep of dry_run_ns_per_point
  * per grid point, which exercises queueing and admission without a GPU.    */
 typedef struct tpt_server_s* tpt_server;
@@ -479,6 +487,8 @@ typedef struct {
   size_t memory_budget;         /* device bytes for admitted requests' buffers       */
   size_t cache_budget;          /* device bytes for unused cached eigenbases         */
   double dry_run_ns_per_point;  /* simulated solve time (cuda_device < 0 only)       */
+  int merge;                    /* same-shape batching: up to `merge` ready requests
+                                   of one shape solved together (0 or 1: each alone) */
 } tpt_server_config;
 
 typedef struct {
@@ -492,6 +502,7 @@ typedef struct {
                                    tpt_cuda_error_name() names it                    */
   double t_copied, t_solved;    /* when the input copy and the solve had finished
                                    (server clock; 0 if not reached)                  */
+  int merged;                   /* requests solved together with this one (1: alone) */
 } tpt_result;
 #define TPT_STEP_PLAN 1         /* plan creation (host setup, cached tables)        */
 #define TPT_STEP_ALLOC 2        /* request buffers from the server's pool            */

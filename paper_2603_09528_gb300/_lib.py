@@ -62,6 +62,7 @@ class tpt_server_config(C.Structure):
         ("memory_budget", C.c_size_t),
         ("cache_budget", C.c_size_t),
         ("dry_run_ns_per_point", C.c_double),
+        ("merge", C.c_int),
     ]
 
 
@@ -78,6 +79,7 @@ class tpt_result(C.Structure):
         ("cuda_error", C.c_int),
         ("t_copied", C.c_double),
         ("t_solved", C.c_double),
+        ("merged", C.c_int),
     ]
 
 

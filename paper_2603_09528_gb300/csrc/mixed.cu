@@ -2606,14 +2606,12 @@ int capture_adaptive(tpt_plan_s* p, const MixedWork& w, const double* f, double*
   return TPT_OK;
 }
 
-template <int FMT>
-int solve_adaptive(tpt_plan_s* p, const MixedWork& w, const double* f, double* phi, void* work, cudaStream_t s,
-                   tpt_info* info) {
+// Corrections an adaptive solve enqueues before its first look at the stop
+// flags: what the plan's last solve needed, else an estimate from the
+// residual reduction one correction of this operand format typically gives
+// (measured on stretched grids: ~3.5e-4 split bf16, ~2e-3 tf32, ~8e-3 bf16).
+int planned_corrections(const tpt_plan_s* p) {
   const int corrections = 1 + p->max_refine;
-  // corrections to enqueue before the first look at the flags: what the
-  // plan's last solve needed, else an estimate from the residual reduction
-  // one correction of this operand format typically gives (measured on
-  // stretched grids: ~3.5e-4 split bf16, ~2e-3 tf32, ~8e-3 bf16)
   int planned = corrections;
   const int li = p->last_iters.load();
   if (li > 0) {
@@ -2623,6 +2621,14 @@ int solve_adaptive(tpt_plan_s* p, const MixedWork& w, const double* f, double* p
     const double est = std::ceil(std::log(p->rtol) / std::log(c));
     if (est >= 1.0 && est < corrections) planned = static_cast<int>(est);
   }
+  return planned;
+}
+
+template <int FMT>
+int solve_adaptive(tpt_plan_s* p, const MixedWork& w, const double* f, double* phi, void* work, cudaStream_t s,
+                   tpt_info* info) {
+  const int corrections = 1 + p->max_refine;
+  const int planned = planned_corrections(p);
   int enq = 0;
   bool own = !p->graph_busy.exchange(true);   // this caller may use and update the plan's graph
   // the scalars come back through a pinned slot: the plan's own, or one of
@@ -2982,6 +2988,7 @@ struct GroupSolve {
   std::vector<const void*> key;        // buffers the tables were built for
   std::vector<unsigned> gens;
   unsigned long long kernels = 0;      // kernels of the last enqueue
+  bool external = false;               // dmem belongs to the caller
 };
 
 namespace {
@@ -3055,13 +3062,15 @@ bool thomas_job_any(int m, const tpt_plan_s* p, const MixedWork& w, int first, T
 
 }  // namespace
 
+bool group_eligible(const tpt_plan_s* p) {
+  return p->dev >= 0 && p->precision == TPT_PREC_MIXED_BF16X3 && p->mixed.fmt == kFmtSplit && p->rtol > 0.0 &&
+         p->n[0] % 4 == 0 && thomas2_m(p->n[2]) != 0;
+}
+
 GroupSolve* group_create(tpt_plan_s* const* plans, int n) {
   if (n <= 0) return nullptr;
-  for (int i = 0; i < n; ++i) {
-    const tpt_plan_s* p = plans[i];
-    if (p->precision != TPT_PREC_MIXED_BF16X3 || p->mixed.fmt != kFmtSplit || !(p->rtol > 0.0)) return nullptr;
-    if (p->n[0] % 4 != 0 || thomas2_m(p->n[2]) == 0 || p->dev != plans[0]->dev) return nullptr;
-  }
+  for (int i = 0; i < n; ++i)
+    if (!group_eligible(plans[i]) || plans[i]->dev != plans[0]->dev) return nullptr;
   GroupSolve* g = new (std::nothrow) GroupSolve;
   if (!g) return nullptr;
   g->n = n;
@@ -3077,8 +3086,25 @@ GroupSolve* group_create(tpt_plan_s* const* plans, int n) {
 
 void group_destroy(GroupSolve* g) {
   if (!g) return;
-  if (g->dmem) cudaFree(g->dmem);
+  if (g->dmem && !g->external) cudaFree(g->dmem);
   delete g;
+}
+
+size_t group_table_bytes(const GroupSolve* g) {
+  // an upper bound of group_prepare's layout: at most 4 Thomas groups (one per
+  // segment length) and 5 residual variants, each rounded up to 256 bytes
+  const size_t n = g ? static_cast<size_t>(g->n) : 0;
+  return align256(sizeof(InstJob) * n) + 5 * align256(sizeof(tc::GemmJob) * n) + sizeof(ThomasJob) * n +
+         4 * 256 + sizeof(ResJob) * n + 5 * 256 + align256(sizeof(int) * std::max<size_t>(1, n)) +
+         align256(sizeof(int) * 4 * 64);
+}
+
+void group_set_memory(GroupSolve* g, void* mem, size_t bytes) {
+  if (g->dmem && !g->external) cudaFree(g->dmem);
+  g->dmem = mem;
+  g->dmem_bytes = bytes;
+  g->external = true;
+  g->key.clear();
 }
 
 size_t group_workspace_bytes(const GroupSolve* g) { return g ? g->ws_bytes : 0; }
@@ -3236,6 +3262,7 @@ int group_prepare(GroupSolve* g, const double* const* f, double* const* phi, voi
   const int max_corr = 64;
   bytes += align256(sizeof(int) * tg.size() * max_corr);
   if (bytes > g->dmem_bytes) {
+    if (g->external) return TPT_ERR_INVALID_ARG;   // group_table_bytes bounds the layout
     MX_CUDA(cudaStreamSynchronize(s));
     if (g->dmem) cudaFree(g->dmem);
     g->dmem = nullptr;
@@ -3266,7 +3293,8 @@ int group_prepare(GroupSolve* g, const double* const* f, double* const* phi, voi
   g->d_counters = static_cast<int*>(put(nullptr, sizeof(int) * tg.size() * max_corr));
   // a solve still in flight on s may be reading the previous tables
   MX_CUDA(cudaStreamSynchronize(s));
-  MX_CUDA(cudaMemcpy(g->dmem, host.data(), bytes, cudaMemcpyHostToDevice));
+  MX_CUDA(cudaMemcpyAsync(g->dmem, host.data(), bytes, cudaMemcpyHostToDevice, s));
+  MX_CUDA(cudaStreamSynchronize(s));
   g->tg = tg;
   g->rg = rg;
   g->key = key;
@@ -3278,19 +3306,28 @@ int group_prepare(GroupSolve* g, const double* const* f, double* const* phi, voi
 // scalars cleared, f converted, corrections until each instance's rtol or the
 // largest 1 + max_refine of the batch, the gauge and the float64 output, and
 // the 16 scalars of instance i gathered into d_scal[16 i ..].
-int group_enqueue(GroupSolve* g, double* d_scal, cudaStream_t s) {
+int group_corrections(const GroupSolve* g) {
   int corrections = 1;
   for (tpt_plan_s* p : g->plans) corrections = std::max(corrections, 1 + p->max_refine);
-  if (corrections > 64) return TPT_ERR_UNSUPPORTED;
-  const unsigned long long before = launch_count();
+  return corrections;
+}
+
+// Corrections c0 .. c1 - 1 of the grouped solve, after the clearing and the
+// conversion of f when `prepare`, followed by the gauge and the float64
+// output when `output`; the 16 scalars of every instance are gathered into
+// d_scal at the end either way.
+int group_enqueue_part(GroupSolve* g, double* d_scal, cudaStream_t s, int c0, int c1, bool prepare, bool output) {
+  if (c1 > 64) return TPT_ERR_UNSUPPORTED;
   const int n = g->n;
-  note_launch(2);
-  group_clear_kernel<<<n, 32, 0, s>>>(g->d_inst);
-  group_prepare_kernel<kFmtSplit><<<g->blocks[0], dim3(32, 8), 0, s>>>(g->d_inst, n);
-  MX_CUDA(cudaGetLastError());
-  MX_CUDA(cudaMemsetAsync(g->d_counters, 0, sizeof(int) * g->tg.size() * 64, s));
+  if (prepare) {
+    note_launch(2);
+    group_clear_kernel<<<n, 32, 0, s>>>(g->d_inst);
+    group_prepare_kernel<kFmtSplit><<<g->blocks[0], dim3(32, 8), 0, s>>>(g->d_inst, n);
+    MX_CUDA(cudaGetLastError());
+    MX_CUDA(cudaMemsetAsync(g->d_counters, 0, sizeof(int) * g->tg.size() * 64, s));
+  }
   const size_t null_smem = static_cast<size_t>(g->max_nz) * sizeof(double);
-  for (int c = 0; c < corrections; ++c) {
+  for (int c = c0; c < c1; ++c) {
     for (int st : {0, 1}) MX_CUDA(tc::gemm_grouped(st == 1 ? tc::kOutF32 : tc::kOutSplitBF16, g->gemm_tma[st],
                                                   g->d_gemm[st], n, g->gemm_units[st], s));
     for (size_t k = 0; k < g->tg.size(); ++k)
@@ -3308,14 +3345,51 @@ int group_enqueue(GroupSolve* g, double* d_scal, cudaStream_t s) {
     group_converge_kernel<<<(n + 127) / 128, 128, 0, s>>>(g->d_inst, n);
     MX_CUDA(cudaGetLastError());
   }
-  note_launch(4);
-  group_clear2_kernel<<<(n + 127) / 128, 128, 0, s>>>(g->d_inst, n);
-  if (g->blocks[1] > 0) group_wsum_kernel<<<g->blocks[1], dim3(64, 4), 0, s>>>(g->d_inst, n);
-  group_output_kernel<<<g->blocks[2], 256, 0, s>>>(g->d_inst, n);
+  if (output) {
+    note_launch(3);
+    group_clear2_kernel<<<(n + 127) / 128, 128, 0, s>>>(g->d_inst, n);
+    if (g->blocks[1] > 0) group_wsum_kernel<<<g->blocks[1], dim3(64, 4), 0, s>>>(g->d_inst, n);
+    group_output_kernel<<<g->blocks[2], 256, 0, s>>>(g->d_inst, n);
+  }
+  note_launch(1);
   group_gather_kernel<<<n, 32, 0, s>>>(g->d_inst, d_scal);
   MX_CUDA(cudaGetLastError());
-  g->kernels = launch_count() - before;
   return TPT_OK;
+}
+
+int group_enqueue(GroupSolve* g, double* d_scal, cudaStream_t s) {
+  const unsigned long long before = launch_count();
+  const int st = group_enqueue_part(g, d_scal, s, 0, group_corrections(g), true, true);
+  g->kernels = launch_count() - before;
+  return st;
+}
+
+int group_solve_adaptive(GroupSolve* g, double* d_scal, double* h_scal, cudaStream_t s) {
+  const int n = g->n;
+  const int corrections = std::min(64, group_corrections(g));
+  int planned = 1;
+  for (tpt_plan_s* p : g->plans) planned = std::max(planned, planned_corrections(p));
+  planned = std::min(planned, corrections);
+  auto fetch = [&]() -> int {
+    MX_CUDA(cudaMemcpyAsync(h_scal, d_scal, sizeof(double) * 16 * n, cudaMemcpyDeviceToHost, s));
+    MX_CUDA(cudaStreamSynchronize(s));
+    return TPT_OK;
+  };
+  auto running = [&]() {
+    for (int i = 0; i < n; ++i)
+      if (reinterpret_cast<const int*>(h_scal + 16 * i + 8)[0] == 0) return true;
+    return false;
+  };
+  MX_TRY(group_enqueue_part(g, d_scal, s, 0, planned, true, false));
+  MX_TRY(fetch());
+  int c = planned;
+  while (c < corrections && running()) {   // the rest, one correction at a time
+    MX_TRY(group_enqueue_part(g, d_scal, s, c, c + 1, false, false));
+    MX_TRY(fetch());
+    ++c;
+  }
+  MX_TRY(group_enqueue_part(g, d_scal, s, c, c, false, true));
+  return fetch();
 }
 
 int autotune_gemms(tpt_plan_s* p, void* work, cudaStream_t s) {

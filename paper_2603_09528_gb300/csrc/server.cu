@@ -137,6 +137,7 @@ struct tpt_server_s {
   // records in r->res where a failure happened and its CUDA error.
   int execute(Request* r, cudaStream_t s) {
     tpt::clear_cuda_error();
+    r->res.merged = 1;
     int step = 0;
     const int st = execute_steps(r, s, &step);
     if (st != TPT_OK && st != TPT_ERR_NOT_CONVERGED) {
@@ -203,6 +204,123 @@ struct tpt_server_s {
     return st != TPT_OK ? st : ss;
   }
 
+  // Same-shape batching: requests that may join a group led by r.
+  bool mergeable(const Request* r) const {
+    if (cfg.merge <= 1 || r->npts >= kExclusivePoints || !r->plan) return false;
+    const tpt_desc& d = r->desc;   // the grouped kernels' conditions (see tpt::group_eligible)
+    if (d.precision != TPT_PREC_MIXED_BF16X3 || !(d.rtol > 0.0) || d.n[0] % 4 != 0 || d.n[2] > 512) return false;
+    return cfg.cuda_device < 0 || tpt::group_eligible(r->plan);
+  }
+  static bool same_shape(const Request* a, const Request* b) {
+    return a->desc.n[0] == b->desc.n[0] && a->desc.n[1] == b->desc.n[1] && a->desc.n[2] == b->desc.n[2] &&
+           a->desc.precision == b->desc.precision;
+  }
+  static constexpr size_t kGroupExtra = 16384;   // per request: job tables and scalars of a group
+  static constexpr size_t kMinGroup = 3;          // smallest group worth solving together
+
+  // The requests of `grp` solved together as one grouped batch on stream s;
+  // fills each request's result times and info, returns their statuses.
+  std::vector<int> execute_group(const std::vector<Request*>& grp, cudaStream_t s) {
+    const int n = static_cast<int>(grp.size());
+    std::vector<int> st(n, TPT_OK);
+    for (Request* r : grp) r->res.merged = n;
+    if (cfg.cuda_device < 0) {   // dry run: one sleep for all their points
+      double pts = 0.0;
+      for (Request* r : grp) pts += static_cast<double>(r->npts);
+      std::this_thread::sleep_for(std::chrono::nanoseconds(static_cast<long long>(cfg.dry_run_ns_per_point * pts)));
+      return st;
+    }
+    std::vector<tpt_plan_s*> plans;
+    for (Request* r : grp) plans.push_back(r->plan);
+    tpt::GroupSolve* g = tpt::group_create(plans.data(), n);
+    if (!g) {   // cannot be grouped after all: one after another
+      for (int i = 0; i < n; ++i) st[i] = execute(grp[i], s);
+      return st;   // (execute records each as solved alone)
+    }
+    tpt::clear_cuda_error();
+    int step = TPT_STEP_ALLOC;
+    std::vector<void*> bufs;
+    auto alloc = [&](size_t bytes, void** out) -> int {
+      if (tpt::injected_alloc_failure()) return TPT_ERR_OOM;
+      const int e = cuda_st(cudaMallocFromPoolAsync(out, bytes + 256, cache.buffer_pool(), s));
+      if (e == TPT_OK) bufs.push_back(*out);
+      return e;
+    };
+    auto aligned = [](void* p) {
+      return reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(p) + 255) & ~static_cast<uintptr_t>(255));
+    };
+    std::vector<const double*> fs(n);
+    std::vector<double*> phis(n);
+    void* work = nullptr;
+    void* tables = nullptr;
+    void* scal = nullptr;
+    int gs = TPT_OK;
+    for (int i = 0; i < n && gs == TPT_OK; ++i) {
+      void* a = nullptr;
+      void* b = nullptr;
+      gs = alloc(grp[i]->npts * sizeof(double), &a);
+      if (gs == TPT_OK) gs = alloc(grp[i]->npts * sizeof(double), &b);
+      if (gs == TPT_OK) {
+        fs[i] = reinterpret_cast<const double*>(aligned(a));
+        phis[i] = reinterpret_cast<double*>(aligned(b));
+      }
+    }
+    if (gs == TPT_OK) gs = alloc(tpt::group_workspace_bytes(g), &work);
+    if (gs == TPT_OK) gs = alloc(tpt::group_table_bytes(g), &tables);
+    if (gs == TPT_OK) gs = alloc(static_cast<size_t>(n) * 16 * sizeof(double), &scal);
+    if (gs == TPT_OK) {
+      std::lock_guard<std::mutex> lk(h2d_mu);   // input copies take turns (see execute)
+      step = TPT_STEP_H2D;
+      for (int i = 0; i < n && gs == TPT_OK; ++i)
+        gs = cuda_st(cudaMemcpyAsync(const_cast<double*>(fs[i]), grp[i]->f_host, grp[i]->npts * sizeof(double),
+                                     cudaMemcpyHostToDevice, s));
+      if (gs == TPT_OK) gs = cuda_st(cudaStreamSynchronize(s));
+    }
+    const double tc = now();
+    for (Request* r : grp) r->res.t_copied = tc;
+    std::vector<double> h(static_cast<size_t>(n) * 16, 0.0);
+    if (gs == TPT_OK) {
+      std::shared_lock<std::shared_mutex> lk(compute_mu);
+      step = TPT_STEP_SOLVE;
+      tpt::group_set_memory(g, aligned(tables), tpt::group_table_bytes(g));
+      gs = tpt::group_prepare(g, fs.data(), phis.data(), aligned(work), s);
+      if (gs == TPT_OK) gs = tpt::group_solve_adaptive(g, reinterpret_cast<double*>(aligned(scal)), h.data(), s);
+    }
+    const double ts = now();
+    for (int i = 0; i < n; ++i) {
+      Request* r = grp[i];
+      if (gs != TPT_OK) {
+        st[i] = gs;
+        continue;
+      }
+      r->res.t_solved = ts;
+      st[i] = tpt::solve_info(r->plan, h.data() + 16 * i, &r->res.info);
+      if (st[i] == TPT_OK || st[i] == TPT_ERR_NOT_CONVERGED) {
+        const int cs = cuda_st(cudaMemcpyAsync(r->phi_host, phis[i], r->npts * sizeof(double),
+                                               cudaMemcpyDeviceToHost, s));
+        if (cs != TPT_OK) {
+          st[i] = cs;
+          r->res.failed_step = TPT_STEP_D2H;
+          r->res.cuda_error = static_cast<int>(tpt::last_cuda_error());
+        }
+      }
+    }
+    for (void* b : bufs) cudaFreeAsync(b, s);
+    const int ss = cuda_st(cudaStreamSynchronize(s));
+    tpt::group_destroy(g);
+    for (int i = 0; i < n; ++i) {
+      if (st[i] == TPT_OK && ss != TPT_OK) {
+        st[i] = ss;
+        grp[i]->res.failed_step = TPT_STEP_SYNC;
+      }
+      if (gs != TPT_OK) {
+        grp[i]->res.failed_step = step;
+        grp[i]->res.cuda_error = static_cast<int>(tpt::last_cuda_error());
+      }
+    }
+    return st;
+  }
+
   void slot_loop() {
     cudaStream_t s = nullptr;
     if (cfg.cuda_device >= 0) {
@@ -210,7 +328,8 @@ struct tpt_server_s {
       if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) cudaGetLastError();
     }
     for (;;) {
-      Request* r = nullptr;
+      std::vector<Request*> grp;
+      size_t charged = 0;
       {
         std::unique_lock<std::mutex> lk(mu);
         cv_ready.wait(lk, [&] {
@@ -218,24 +337,53 @@ struct tpt_server_s {
           return stop && ready.empty() && setup_q.empty();
         });
         if (ready.empty()) break;
-        r = ready.begin()->second;   // the oldest planned request
+        Request* r = ready.begin()->second;   // the oldest planned request
         ready.erase(ready.begin());
-        in_use += r->need;
+        grp.push_back(r);
+        charged = r->need;
+        if (mergeable(r)) {   // other ready requests of its shape join it
+          for (auto it = ready.begin(); it != ready.end() && static_cast<int>(grp.size()) < cfg.merge;) {
+            Request* q = it->second;
+            const size_t add = q->need + kGroupExtra;
+            if (same_shape(q, r) && mergeable(q) && in_use + charged + add + kGroupExtra <= cfg.memory_budget) {
+              grp.push_back(q);
+              charged += add;
+              it = ready.erase(it);
+            } else {
+              ++it;
+            }
+          }
+          // a pair gains less than the grouped path's set-up costs (measured:
+          // groups of two served slower than the requests alone on four slots)
+          if (grp.size() > 1 && grp.size() < kMinGroup) {
+            for (size_t k = 1; k < grp.size(); ++k) ready.emplace(grp[k]->id, grp[k]);
+            grp.resize(1);
+            charged = r->need;
+          }
+          if (grp.size() > 1) charged += kGroupExtra;
+        }
+        in_use += charged;
         peak = in_use > peak ? in_use : peak;
-        ++inflight;
+        inflight += static_cast<int>(grp.size());
         peak_inflight = inflight > peak_inflight ? inflight : peak_inflight;
-        r->res.t_admit = now();
+        const double ta = now();
+        for (Request* q : grp) q->res.t_admit = ta;
       }
-      const int st = (cfg.cuda_device >= 0 && !s) ? TPT_ERR_CUDA : execute(r, s);
-      tpt_plan p = r->plan;
-      r->plan = nullptr;
-      if (p) tpt_plan_destroy(p);   // stream-ordered frees: no device synchronisation
+      std::vector<int> st;
+      if (cfg.cuda_device >= 0 && !s) st.assign(grp.size(), TPT_ERR_CUDA);
+      else if (grp.size() == 1) st.push_back(execute(grp[0], s));
+      else st = execute_group(grp, s);
+      for (Request* q : grp) {
+        tpt_plan p = q->plan;
+        q->plan = nullptr;
+        if (p) tpt_plan_destroy(p);   // stream-ordered frees: no device synchronisation
+      }
       cache.trim();
       {
         std::lock_guard<std::mutex> g(mu);
-        in_use -= r->need;
-        --inflight;
-        finish(r, st);
+        in_use -= charged;
+        inflight -= static_cast<int>(grp.size());
+        for (size_t i = 0; i < grp.size(); ++i) finish(grp[i], st[i]);
         cv_ready.notify_all();      // freed memory may admit the next request
       }
     }
@@ -249,7 +397,7 @@ int tpt_server_create(const tpt_server_config* cfg, tpt_server* out) {
   if (!out) return TPT_ERR_INVALID_ARG;
   *out = nullptr;
   if (!cfg || cfg->slots < 1 || cfg->setup_threads < 1 || cfg->memory_budget == 0 || cfg->slots > 64 ||
-      cfg->setup_threads > 64 || !(cfg->dry_run_ns_per_point >= 0.0))
+      cfg->setup_threads > 64 || !(cfg->dry_run_ns_per_point >= 0.0) || cfg->merge < 0 || cfg->merge > 256)
     return TPT_ERR_INVALID_ARG;
   if (cfg->cuda_device >= 0) {
     int ndev = 0;

@@ -262,12 +262,23 @@ int solve_info(const tpt_plan_s* p, const double* h, tpt_info* info);
 // the launches on s (capturable) and gathers the 16 scalars of instance i
 // into d_scal[16 i ..].
 struct GroupSolve;
+bool group_eligible(const tpt_plan_s* p);
 GroupSolve* group_create(tpt_plan_s* const* plans, int n);
+// Device memory for the job tables from the caller (at least
+// group_table_bytes, 256-byte aligned, kept by the caller), so that a
+// grouped solve allocates nothing itself.
+size_t group_table_bytes(const GroupSolve* g);
+void group_set_memory(GroupSolve* g, void* mem, size_t bytes);
 void group_destroy(GroupSolve* g);
 size_t group_workspace_bytes(const GroupSolve* g);
 unsigned long long group_kernels(const GroupSolve* g);
 int group_prepare(GroupSolve* g, const double* const* f, double* const* phi, void* work, cudaStream_t s);
 int group_enqueue(GroupSolve* g, double* d_scal, cudaStream_t s);
+// The same solve decided on the host: the corrections the instances are
+// expected to need, then one at a time while any instance is short of its
+// rtol (reading the 16 scalars of every instance back into h_scal, host
+// memory of 16 n doubles, after each step); synchronises s.
+int group_solve_adaptive(GroupSolve* g, double* d_scal, double* h_scal, cudaStream_t s);
 
 // Times the transform GEMMs of a mixed plan over the candidate tiles and keeps
 // the fastest per stage (gemm_tune.cu).

@@ -321,9 +321,9 @@ class Server:
 
     def __init__(self, device: int = 0, slots: int = 4, setup_threads: int = 4,
                  memory_budget: int = 64 << 30, cache_budget: int = 4 << 30,
-                 dry_run_ns_per_point: float = 0.0):
+                 dry_run_ns_per_point: float = 0.0, merge: int = 8):
         cfg = _lib.tpt_server_config(int(device), int(slots), int(setup_threads), int(memory_budget),
-                                     int(cache_budget), float(dry_run_ns_per_point))
+                                     int(cache_budget), float(dry_run_ns_per_point), int(merge))
         h = C.c_void_p()
         check(lib.tpt_server_create(C.byref(cfg), C.byref(h)), "tpt_server_create")
         self._h = h
@@ -356,7 +356,7 @@ class Server:
                     compat_defect=r.info.compat_defect, t_submit=r.t_submit, t_planned=r.t_planned,
                     t_admit=r.t_admit, t_done=r.t_done, device_bytes=int(r.device_bytes),
                     failed_step=int(r.failed_step), cuda_error=int(r.cuda_error),
-                    t_copied=r.t_copied, t_solved=r.t_solved,
+                    t_copied=r.t_copied, t_solved=r.t_solved, merged=int(r.merged),
                     cuda_error_name=(lib.tpt_cuda_error_name(int(r.cuda_error)) or b"?").decode())
 
     def now(self) -> float:

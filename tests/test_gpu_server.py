@@ -58,7 +58,7 @@ def test_results_alone_equal_results_in_the_mix():
     fs = [_rhs(sp, 50 + i) for i, sp in enumerate(specs)]
     f_host = [torch.from_numpy(np.ascontiguousarray(f.ravel(order="F"))).pin_memory() for f in fs]
     phi_host = [torch.empty_like(t).pin_memory() for t in f_host]
-    srv = tpt.Server(device=0, slots=3, setup_threads=6, memory_budget=8 << 30, cache_budget=1 << 30)
+    srv = tpt.Server(device=0, slots=3, setup_threads=6, memory_budget=8 << 30, cache_budget=1 << 30, merge=1)
     tickets = [srv.submit(f, p, **sp) for f, p, sp in zip(f_host, phi_host, specs)]
     res = [srv.wait(t, timeout=300.0) for t in tickets]
     st = srv.stats()
@@ -144,3 +144,36 @@ def test_concurrent_solves_of_sizes_sharing_a_kernel_do_not_race():
     for t in th:
         t.join()
     assert errors == []
+
+
+def test_requests_of_one_shape_merged_equal_their_own_solves():
+    """Same-shape batching: ready requests of one grid size queued behind a
+    busy slot are solved together as one grouped batch; each result equals the
+    request solved on its own with the same Thomas kernel (1e-11, refined
+    mixed) and reaches the refinement target in the oracle's stencil."""
+    n = (64, 48, 40)
+    specs = []
+    for i in range(10):
+        stretch = (1.0 + 0.2 * (i % 4), 1.5 + 0.1 * (i % 3), 2.0)
+        alpha, beta = (0.0, 1.0) if i % 3 else (1.0, -0.5 * 5e-3)
+        specs.append(_spec(n, stretch, alpha, beta, L.TPT_PREC_MIXED_BF16X3))
+    fs = [_rhs(sp, 90 + i) for i, sp in enumerate(specs)]
+    f_pin = [torch.from_numpy(np.ascontiguousarray(f.ravel(order="F"))).pin_memory() for f in fs]
+    outs = [torch.empty_like(t).pin_memory() for t in f_pin]
+    srv = tpt.Server(device=0, slots=1, setup_threads=2, memory_budget=8 << 30, cache_budget=1 << 30, merge=8)
+    try:
+        tickets = [srv.submit(f, o, **sp) for f, o, sp in zip(f_pin, outs, specs)]
+        res = [srv.wait(t, timeout=120.0) for t in tickets]
+    finally:
+        srv.close()
+    assert all(r["status"] == L.TPT_OK for r in res), res
+    assert max(r["merged"] for r in res) > 1, [r["merged"] for r in res]
+    for i, (sp, f, r) in enumerate(zip(specs, fs, res)):
+        got = outs[i].numpy().reshape(n, order="F")
+        plan = tpt.Plan(**sp)
+        plan.set_thomas_kernel(2)
+        alone = tpt.field_to_host(plan.solve(tpt.field_to_device(f))[0], n)
+        assert np.abs(got - alone).max() <= 1e-11 * np.abs(alone).max(), (i, r["merged"])
+        dirs = [O.Direction(sp["dxf"][a], sp["dxc"][a], NNN[a]) for a in range(3)]
+        rr = O.residual(f, got, dirs, sp["alpha"], sp["beta"], np.longdouble)
+        assert float(np.sqrt(np.sum(rr ** 2) / np.sum(f ** 2))) <= 1e-10 + 1e-14, i

@@ -189,3 +189,33 @@ def test_a_failed_request_reports_its_step_and_cuda_error():
     assert r_bad["failed_step"] == 1 and r_bad["cuda_error"] == 0   # TPT_STEP_PLAN
     assert r_ok["status"] == L.TPT_OK and r_ok["failed_step"] == 0 and r_ok["cuda_error"] == 0
     assert L.lib.tpt_cuda_error_name(0) == b"cudaSuccess"
+
+
+def test_dry_run_merges_ready_requests_of_one_shape():
+    """Same-shape batching on the host: with one slot busy, requests of one
+    grid size that queue up are admitted together (at most `merge`, within
+    the budget), others one at a time; every request completes and reports
+    how many were solved with it."""
+    mixed = dict(precision=L.TPT_PREC_MIXED_BF16X3, rtol=1e-10, max_refine=8)
+    shapes = [(16, 12, 8)] * 9 + [(12, 16, 8)] * 2 + [(18, 12, 8)] * 2   # Nx = 18: not grouped
+    srv = tpt.Server(device=-1, slots=1, setup_threads=1, memory_budget=1 << 40, cache_budget=0,
+                     dry_run_ns_per_point=4000.0, merge=4)
+    bufs, tickets = [], []
+    for i, n in enumerate(shapes):
+        f, phi = np.zeros(n[0] * n[1] * n[2]), np.zeros(n[0] * n[1] * n[2])
+        bufs.append((f, phi))
+        tickets.append(srv.submit(f, phi, **dict(_spec(n, (1.5, 2.0, 1.0)), **mixed)))
+    res = [srv.wait(t, timeout=60.0) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    assert all(r["status"] == L.TPT_OK for r in res)
+    merged = [r["merged"] for r in res]
+    assert max(merged) >= 3 and max(merged) <= 4, merged
+    assert all(m == 1 or m >= 3 for m in merged), merged     # no pairs
+    assert all(m == 1 for m, n in zip(merged, shapes) if n[0] == 18)
+    # requests solved together were admitted and finished at the same moment
+    for r in res:
+        if r["merged"] > 1:
+            same = [q for q in res if q["t_admit"] == r["t_admit"]]
+            assert len(same) == r["merged"] and all(abs(q["t_done"] - r["t_done"]) < 1e-3 for q in same)
+    assert st["completed"] == len(shapes)
