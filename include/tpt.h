@@ -78,9 +78,16 @@ enum { TPT_XFORM_AUTO = 0, TPT_XFORM_GEMM = 1, TPT_XFORM_FFT = 2 };
  * throughout.  MIXED_*: correction solves with the transforms on the tensor
  * cores (BF16, split BF16 with three products, or TF32; FP32 accumulation),
  * FP32 Thomas except the singular null line (float64), and a float64
- * residual driving iterative refinement to `rtol`.                          */
+ * residual driving iterative refinement to `rtol`.  FP64_OZAKI: the float64
+ * solve with its eigenbasis-transform GEMMs on the bf16 tensor cores by the
+ * Ozaki scheme (each operand row split into seven bf16 slices of six bits,
+ * slice products summed exactly in float32 level by level and the levels in
+ * float64; ~1e-13 of sum |a||b| per product) -- float64-accurate after the
+ * plan's float64 refinement steps, everything else as FP64; GEMM directions
+ * of at most 576 points (else UNSUPPORTED).  Reported as TPT_PREC_FP64 by the
+ * plan's inspection calls.                                                   */
 enum { TPT_PREC_FP64 = 0, TPT_PREC_MIXED_BF16 = 1, TPT_PREC_MIXED_BF16X3 = 2,
-       TPT_PREC_MIXED_TF32 = 3 };
+       TPT_PREC_MIXED_TF32 = 3, TPT_PREC_FP64_OZAKI = 4 };
 
 /* ---- plan ------------------------------------------------------------ */
 typedef struct tpt_plan_s* tpt_plan;

@@ -24,7 +24,7 @@ TPT_PENDING = 9
 
 TPT_BC_PERIODIC, TPT_BC_NEUMANN, TPT_BC_DIRICHLET, TPT_BC_DIRICHLET_NODE, TPT_BC_NONE = 0, 1, 2, 3, 4
 TPT_XFORM_AUTO, TPT_XFORM_GEMM, TPT_XFORM_FFT = 0, 1, 2
-TPT_PREC_FP64, TPT_PREC_MIXED_BF16, TPT_PREC_MIXED_BF16X3, TPT_PREC_MIXED_TF32 = 0, 1, 2, 3
+TPT_PREC_FP64, TPT_PREC_MIXED_BF16, TPT_PREC_MIXED_BF16X3, TPT_PREC_MIXED_TF32, TPT_PREC_FP64_OZAKI = 0, 1, 2, 3, 4
 TPT_GEMM_OUT_F32, TPT_GEMM_OUT_BF16, TPT_GEMM_OUT_SPLIT_BF16 = 0, 1, 2
 
 _dp = C.POINTER(C.c_double)

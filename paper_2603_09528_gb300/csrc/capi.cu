@@ -64,6 +64,7 @@ void free_plan(tpt_plan_s* p) {
     if (p->h_ring) cudaFreeHost(p->h_ring);
     if (p->solve_exec) cudaGraphExecDestroy(p->solve_exec);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    if (p->oz_scratch) cudaFree(p->oz_scratch);
     tpt::pinned_slot_release(p->h_scal);
     cudaGetLastError();
   }
@@ -73,13 +74,14 @@ void free_plan(tpt_plan_s* p) {
 bool on_device(const tpt_plan_s* p) { return p && p->dev >= 0 && p->d_scal; }
 
 int apply_transform(const tpt_plan_s* p, int d, bool inverse, const double* in, double* out,
-                    bool accumulate, cudaStream_t s) {
+                    bool accumulate, void* oz, int* err, cudaStream_t s) {
   if (p->dir[d].excluded()) {   // identity transform: no GEMM along a direction outside the operator
     if (!accumulate) return cuda_status(cudaMemcpyAsync(out, in, tpt::npts(p) * sizeof(double),
                                                         cudaMemcpyDeviceToDevice, s));
     return cuda_status(tpt::add_fp64(static_cast<long long>(tpt::npts(p)), in, out, s));
   }
   if (p->xform[d] == TPT_XFORM_FFT) return cuda_status(tpt::fft_fp64(p, d, inverse, in, out, accumulate, s));
+  if (p->ozaki) return cuda_status(tpt::ozaki_transform(p, d, inverse, in, out, accumulate, oz, err, s));
   const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
   const double* mat = inverse ? p->ddir[d].inv : p->ddir[d].fwd;
   if (d == 0) {
@@ -102,12 +104,12 @@ size_t region_bytes(const tpt_plan_s* p) {
 
 // One correction solve: out (=|+=) Q_x Q_y (Thomas) Q_y^{-1} Q_x^{-1} rhs.
 int inner_fp64(const tpt_plan_s* p, const double* rhs, double* out, bool accumulate, double* t1,
-               double* t2, double* defect, cudaStream_t s) {
-  TPT_TRY(apply_transform(p, 0, false, rhs, t1, false, s));               // step 2.1
-  TPT_TRY(apply_transform(p, 1, false, t1, t2, false, s));                // step 2.2
+               double* t2, double* defect, void* oz, int* err, cudaStream_t s) {
+  TPT_TRY(apply_transform(p, 0, false, rhs, t1, false, oz, err, s));      // step 2.1
+  TPT_TRY(apply_transform(p, 1, false, t1, t2, false, oz, err, s));       // step 2.2
   TPT_CUDA(tpt::thomas_fp64(p, t2, t2, t1, defect, s));                   // step 2.3
-  TPT_TRY(apply_transform(p, 1, true, t2, t1, false, s));                 // step 2.4
-  TPT_TRY(apply_transform(p, 0, true, t1, out, accumulate, s));           // step 2.5
+  TPT_TRY(apply_transform(p, 1, true, t2, t1, false, oz, err, s));        // step 2.4
+  TPT_TRY(apply_transform(p, 0, true, t1, out, accumulate, oz, err, s));  // step 2.5
   return TPT_OK;
 }
 
@@ -157,14 +159,17 @@ int fp64_solve(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStre
   }
   TPT_CUDA(cudaMemsetAsync(ds, 0, 16 * sizeof(double), s));
   TPT_CUDA(tpt::field_sums(p, fu, ds + 5, s));
-  TPT_TRY(inner_fp64(p, fu, phi, false, t1, t2, ds + 4, s));
+  void* oz = p->ozaki ? static_cast<void*>(w + 4 * rb) : nullptr;   // Ozaki scratch after fcopy
+  int* oz_err = reinterpret_cast<int*>(ds + 10);
+  TPT_TRY(inner_fp64(p, fu, phi, false, t1, t2, ds + 4, oz, oz_err, s));
   int iters = 1;
   const double np = static_cast<double>(tpt::npts(p));
   double fn2 = -1.0, rel = -1.0;
   double h[kSlot] = {0.0};
   auto read_residual = [&]() -> int {
-    TPT_CUDA(cudaMemcpyAsync(h, ds, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    TPT_CUDA(cudaMemcpyAsync(h, ds, 16 * sizeof(double), cudaMemcpyDeviceToHost, s));
     TPT_CUDA(cudaStreamSynchronize(s));
+    if (reinterpret_cast<const int*>(h + 10)[0]) return TPT_ERR_TIMEOUT;   // a bounded GEMM wait ran out
     fn2 = projected_norm2(h[5], h[6], h[7], np, p->vol, p->singular);
     if (!std::isfinite(h[1]) || !std::isfinite(fn2)) return TPT_ERR_NONFINITE;
     rel = (fn2 > 0.0) ? std::sqrt(h[1] / fn2) : std::sqrt(h[1]);
@@ -185,7 +190,7 @@ int fp64_solve(tpt_plan_s* p, const double* f, double* phi, void* work, cudaStre
       }
     }
     if (iters >= corrections) break;
-    TPT_TRY(inner_fp64(p, r, phi, true, t1, t2, ds, s));
+    TPT_TRY(inner_fp64(p, r, phi, true, t1, t2, ds, oz, oz_err, s));
     ++iters;
   }
   // the canonical gauge: phi shifted to zero volume-weighted mean in physical
@@ -232,7 +237,7 @@ int create_plan_impl(const tpt_desc* desc, int cuda_device, tpt::BasisCache* cac
   if (!std::isfinite(desc->alpha) || !std::isfinite(desc->beta)) return TPT_ERR_INVALID_ARG;
   if (desc->alpha == 0.0 && desc->beta == 0.0) return TPT_ERR_INVALID_ARG;
   if (desc->max_refine < 0 || desc->max_refine > 1000) return TPT_ERR_INVALID_ARG;
-  if (desc->precision < TPT_PREC_FP64 || desc->precision > TPT_PREC_MIXED_TF32)
+  if (desc->precision < TPT_PREC_FP64 || desc->precision > TPT_PREC_FP64_OZAKI)
     return TPT_ERR_INVALID_ARG;
   if (!std::isfinite(desc->rtol) || desc->rtol < 0.0) return TPT_ERR_INVALID_ARG;
   for (int d = 0; d < 2; ++d)
@@ -259,7 +264,8 @@ int create_plan_impl(const tpt_desc* desc, int cuda_device, tpt::BasisCache* cac
   if ((p->dir[0].excluded() || p->dir[1].excluded()) && desc->alpha == 0.0) return fail(TPT_ERR_INVALID_ARG);
   for (int d = 0; d < 2; ++d) {
     // Fourier-based transforms: float64 path, uniform power-of-two directions
-    const bool ok = tpt::fft_supported(p->dir[d]) && desc->precision == TPT_PREC_FP64;
+    const bool ok = tpt::fft_supported(p->dir[d]) &&
+                    (desc->precision == TPT_PREC_FP64 || desc->precision == TPT_PREC_FP64_OZAKI);
     if (desc->xform[d] == TPT_XFORM_FFT && !ok) return fail(TPT_ERR_UNSUPPORTED);
     p->xform[d] = (desc->xform[d] == TPT_XFORM_FFT || (desc->xform[d] == TPT_XFORM_AUTO && ok))
                       ? TPT_XFORM_FFT
@@ -267,7 +273,8 @@ int create_plan_impl(const tpt_desc* desc, int cuda_device, tpt::BasisCache* cac
   }
   p->alpha = desc->alpha;
   p->beta = desc->beta;
-  p->precision = desc->precision;
+  // an Ozaki plan is a float64 plan whose GEMM transforms run on the tensor cores
+  p->precision = desc->precision == TPT_PREC_FP64_OZAKI ? TPT_PREC_FP64 : desc->precision;
   p->rtol = desc->rtol;
   p->max_refine = desc->max_refine;
   for (int d = 0; d < 2; ++d) {
@@ -353,6 +360,14 @@ int create_plan_impl(const tpt_desc* desc, int cuda_device, tpt::BasisCache* cac
   if (cudaStreamSynchronize(p->arena.stream) != cudaSuccess) {
     cudaGetLastError();
     return fail(TPT_ERR_CUDA);
+  }
+  if (desc->precision == TPT_PREC_FP64_OZAKI && p->dev >= 0) {   // slices of the transform matrices
+    st = tpt::ozaki_setup(p);
+    if (st != TPT_OK) return fail(st);
+    if (cudaStreamSynchronize(p->arena.stream) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(TPT_ERR_CUDA);
+    }
   }
   *out = p;
   return TPT_OK;
@@ -630,7 +645,9 @@ int tpt_plan_get_tiles(tpt_plan p, int* tiles_out) {
 
 int tpt_workspace_bytes(tpt_plan p, size_t* bytes) {
   if (!p || !bytes) return TPT_ERR_INVALID_ARG;
-  *bytes = (p->precision == TPT_PREC_FP64) ? 256 + 4 * region_bytes(p) : tpt::mixed_workspace_bytes(p);
+  *bytes = (p->precision == TPT_PREC_FP64)
+               ? 256 + 4 * region_bytes(p) + (p->ozaki ? tpt::ozaki_scratch_bytes(p) : 0)
+               : tpt::mixed_workspace_bytes(p);
   return TPT_OK;
 }
 
@@ -660,7 +677,10 @@ int tpt_solve_host(tpt_plan p, const double* f_host, double* phi_host, double* f
 int tpt_transform(tpt_plan p, int dir, int inverse, const double* in, double* out, void* stream) {
   if (!on_device(p) || !in || !out || in == out || (dir != 0 && dir != 1)) return TPT_ERR_INVALID_ARG;
   DeviceGuard guard(p->dev);
-  return apply_transform(p, dir, inverse != 0, in, out, false, static_cast<cudaStream_t>(stream));
+  if (p->ozaki && !p->oz_scratch)   // this entry point's own scratch, kept by the plan
+    TPT_CUDA(cudaMalloc(&p->oz_scratch, tpt::ozaki_scratch_bytes(p)));
+  return apply_transform(p, dir, inverse != 0, in, out, false, p->oz_scratch, nullptr,
+                         static_cast<cudaStream_t>(stream));
 }
 
 int tpt_thomas(tpt_plan p, const double* fhat, double* phihat, double* scratch, void* stream) {

@@ -111,6 +111,24 @@ __device__ __forceinline__ void store_chunk(const GemmOut& g, long long mterm, i
     }
     return;
   }
+  if (OUT == kOutF64 && g.accumulate) {
+    // float64 read-modify-write (the levels of an Ozaki product): every load
+    // of the chunk is issued before the first store, so the 32 loads overlap
+    double* o = static_cast<double*>(g.out0);
+    double old[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int n = nb + j;
+      old[j] = n < g.N ? o[mterm + static_cast<long long>(n) * g.sn] : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int n = nb + j;
+      if (n >= g.N) break;
+      o[mterm + static_cast<long long>(n) * g.sn] = old[j] + static_cast<double>(__uint_as_float(r[j]));
+    }
+    return;
+  }
 #pragma unroll
   for (int j = 0; j < 32; ++j) {
     const int n = nb + j;

@@ -31,7 +31,7 @@ struct GemmOut {
   void* out0;
   void* out1;
   int mode;
-  int accumulate;   // float-pair mode: add into (out0, out1) instead of writing
+  int accumulate;   // float-pair and float64 modes: add into the output instead of writing
   int n_fastest;    // tile order: n fastest (A tile reused by consecutive CTAs)
   int* err;         // device flag for timed-out waits (may be null)
   int bn = 0;       // column tile width 32/64/128/256; 0 picks the smallest >= N

@@ -158,6 +158,13 @@ struct tpt_plan_s {
   int ring_next = 0;
   double vol = 1.0;               // domain volume Lx Ly Lz
   tpt::MixedTables mixed;
+  // float64 transforms by the Ozaki scheme (TPT_PREC_FP64_OZAKI; ozaki.cu):
+  // bf16 slices of the four transform matrices (x forward, x inverse, y
+  // forward, y inverse) and the padded contraction lengths of x and y
+  bool ozaki = false;
+  void* oz_tab[4] = {nullptr, nullptr, nullptr, nullptr};
+  int oz_kp[2] = {0, 0};
+  void* oz_scratch = nullptr;      // scratch of the single-step transform entry point
   int stage_timing = 0;           // record per-stage CUDA events in tpt_solve
   cudaEvent_t ev[12] = {};        // stage boundaries (created on first use)
   unsigned generation = 0;        // bumped when coefficients or tiles change
@@ -279,6 +286,15 @@ int group_enqueue(GroupSolve* g, double* d_scal, cudaStream_t s);
 // rtol (reading the 16 scalars of every instance back into h_scal, host
 // memory of 16 n doubles, after each step); synchronises s.
 int group_solve_adaptive(GroupSolve* g, double* d_scal, double* h_scal, cudaStream_t s);
+
+// Ozaki-scheme transforms (ozaki.cu): tables built at plan creation (the
+// float64 transform matrices must be on the device), scratch of one transform,
+// and the transform itself: out (+)= the float64-accurate transform of in.
+bool ozaki_supported(const tpt_plan_s* p);
+int ozaki_setup(tpt_plan_s* p);
+size_t ozaki_scratch_bytes(const tpt_plan_s* p);
+cudaError_t ozaki_transform(const tpt_plan_s* p, int d, bool inverse, const double* in, double* out,
+                            bool accumulate, void* scratch, int* err, cudaStream_t s);
 
 // Times the transform GEMMs of a mixed plan over the candidate tiles and keeps
 // the fastest per stage (gemm_tune.cu).
