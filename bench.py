@@ -212,13 +212,13 @@ PRECISIONS = {"fp64": 0, "mixed_bf16": 1, "mixed_bf16x3": 2, "mixed_tf32": 3}
 # x-inverse GEMM of a solve's first correction writes phi without reading it, so it has
 # its own entry ("x_inverse_first").
 MEASURED_TRAFFIC_PER_POINT = {
-    ("residual", "mixed_bf16x3"): (919.794176e6 + 208.527616e6) / 384 ** 3,
-    ("thomas", "mixed_bf16x3"): (226.578432e6 + 175.845888e6) / 384 ** 3,
-    ("x_forward", "mixed_bf16x3"): (227.178240e6 + 177.789440e6) / 384 ** 3,
-    ("y_forward", "mixed_bf16x3"): (227.145472e6 + 173.730048e6) / 384 ** 3,
-    ("y_inverse", "mixed_bf16x3"): (227.169024e6 + 178.160384e6) / 384 ** 3,
-    ("x_inverse", "mixed_bf16x3"): (681.375488e6 + 389.430528e6) / 384 ** 3,
-    ("x_inverse_first", "mixed_bf16x3"): (227.432448e6 + 387.996672e6) / 384 ** 3,
+    ("residual", "mixed_bf16x3"): (919.583e6 + 208.553e6) / 384 ** 3,
+    ("thomas", "mixed_bf16x3"): (226.602e6 + 175.457e6) / 384 ** 3,
+    ("x_forward", "mixed_bf16x3"): (227.166e6 + 177.864e6) / 384 ** 3,
+    ("y_forward", "mixed_bf16x3"): (227.126e6 + 174.007e6) / 384 ** 3,
+    ("y_inverse", "mixed_bf16x3"): (227.184e6 + 178.220e6) / 384 ** 3,
+    ("x_inverse", "mixed_bf16x3"): (681.377e6 + 389.205e6) / 384 ** 3,
+    ("x_inverse_first", "mixed_bf16x3"): (227.420e6 + 388.045e6) / 384 ** 3,
 }
 DTYPE = {"fp64": "f64", "mixed_bf16": "bf16/f32/f64", "mixed_bf16x3": "bf16x3/f32/f64",
          "mixed_tf32": "tf32/f32/f64"}
