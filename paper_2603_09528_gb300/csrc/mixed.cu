@@ -504,7 +504,7 @@ thomas_tma_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_const
 // input tile.
 constexpr int kT2Slots = 32;                    // segment slots per line
 constexpr int kT2Pitch = kT2Slots + 1;          // row pitch of the reduced-system buffer
-constexpr int kT2SmemBudget = 210 * 1024;       // dynamic shared memory (16.5 KB static beside it)
+constexpr int kT2SmemBudget = 209 * 1024;       // dynamic shared memory (17.1 KB static beside it)
 
 // Elements i and i + 1 (i even) of an output tile in the T3 format.
 template <int FMT>
@@ -530,13 +530,94 @@ struct ThomasJob {
   CUtensorMap map_in, map_o0, map_o1;
   ThomasGeom geo;
   int nx, ny, nz, ldy, ntiles, first;
+  unsigned ldy_magic;   // L / ldy = (L * ldy_magic) >> ldy_shift for 0 <= L < 2^31
+  int ldy_shift;
   void *t3_0, *t3_1;
   const float *lamx, *lamy, *az, *bz, *cz;
   float alpha, beta;
   int singular;
   int* err;
   const int* skip;
+  // singular problems: the null line (q, p) = (0, 0) in float64 from T2
+  // (element k at t2[k * nstride]) with the float64 z rows, the precomputed
+  // factorisation of T_z (c', 1 / pivot), the z cell widths and beta
+  const float* t2;
+  const double *naz, *ncp, *ninvm, *ndz;
+  double nbeta;
+  long long nstride;
 };
+
+// The singular null line of a thomas2_kernel tile, solved in float64 by the
+// whole block (one row per thread, Nz <= blockDim.x) into column 0 of the
+// output tile: the line is projected to compatible form (dz-weighted mean
+// removed), solved with the factorisation of T_z whose last pivot vanishes
+// (the last modal unknown set to zero) and shifted to zero dz-weighted mean.
+// Both sweeps are first-order linear recurrences, evaluated as block-wide
+// scans of affine maps (warp shuffles, then the 16 warp totals in order).
+// scr: 64 doubles of shared memory.  Every thread of the block calls it.
+template <int FMT>
+__device__ void null_line_block(const ThomasJob& J, void* o0, void* o1, double* scr) {
+  constexpr int TLT = 32;
+  const int k = threadIdx.x, lane = k % 32, warp = k / 32, nw = blockDim.x / 32;
+  const int nz = J.nz;
+  const bool row = k < nz, elim = k < nz - 1;
+  const double f = row ? static_cast<double>(J.t2[static_cast<long long>(k) * J.nstride]) : 0.0;
+  const double dzk = row ? J.ndz[k] : 0.0;
+  // block sums, the same in every thread
+  auto sum2 = [&](double a, double b, double& sa, double& sb) {
+    a = warp_sum_d(a);
+    b = warp_sum_d(b);
+    if (lane == 0) {
+      scr[warp] = a;
+      scr[32 + warp] = b;
+    }
+    __syncthreads();
+    sa = 0.0;
+    sb = 0.0;
+    for (int v = 0; v < nw; ++v) {
+      sa += scr[v];
+      sb += scr[32 + v];
+    }
+    __syncthreads();
+  };
+  // x -> A x + B per row, composed in row order (up) or reverse row order;
+  // returns this row's composed map applied to the value entering the line (0)
+  auto scan = [&](double A, double B, bool up) -> double {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const double Ap = up ? __shfl_up_sync(0xffffffffu, A, d) : __shfl_down_sync(0xffffffffu, A, d);
+      const double Bp = up ? __shfl_up_sync(0xffffffffu, B, d) : __shfl_down_sync(0xffffffffu, B, d);
+      if (up ? lane >= d : lane + d < 32) {
+        B = fma(A, Bp, B);
+        A *= Ap;
+      }
+    }
+    if (lane == (up ? 31 : 0)) {         // the map of the whole warp
+      scr[warp] = A;
+      scr[32 + warp] = B;
+    }
+    __syncthreads();
+    double v = 0.0;                      // the value entering this warp
+    if (up) {
+      for (int u = 0; u < warp; ++u) v = fma(scr[u], v, scr[32 + u]);
+    } else {
+      for (int u = nw - 1; u > warp; --u) v = fma(scr[u], v, scr[32 + u]);
+    }
+    __syncthreads();
+    return fma(A, v, B);
+  };
+  double sf, w;
+  sum2(dzk * f, dzk, sf, w);
+  const double fshift = sf / w;
+  // forward: dp_k = (f_k - fshift - a_k dp_{k-1}) / m_k, dp_{-1} = 0
+  const double iv = elim ? J.ninvm[k] : 0.0;
+  const double dp = scan(elim ? -J.naz[k] * iv : 1.0, elim ? (f - fshift) * iv : 0.0, true);
+  // backward: x_k = dp_k - c'_k x_{k+1}, x_{nz-1} = 0
+  const double x = scan(elim ? -J.ncp[k] : 1.0, elim ? dp : 0.0, false);
+  double xs, w2;
+  sum2(dzk * x, 0.0, xs, w2);
+  if (row) Elem<FMT>::store(o0, o1, static_cast<long long>(k) * TLT, static_cast<float>((x - xs / w) / J.nbeta));
+}
 
 // lg: the shared-memory layout of the launch (stage count and the largest
 // stage, output tile and row table over its instances).
@@ -553,12 +634,13 @@ thomas2_kernel(const __grid_constant__ ThomasJob job0, ThomasGeom lg, int* next_
   RowCoef* coef = reinterpret_cast<RowCoef*>(dsm);
   uint8_t* in_base = dsm + lg.coef_bytes;
   uint8_t* ot = in_base + static_cast<size_t>(lg.stages) * lg.in_bytes;
-  // reduced-system buffer: first g_0, u_0, v_0 of every segment, then the
-  // interface rows A, B, C, D (D overwritten by the interface values y)
-  __shared__ float X[4][kT2Slots * kT2Pitch];
+  // reduced-system buffer: first g_0, u_0, v_0 of segment s in slot s, then
+  // the interface row of segment s (A, B, C, D; D overwritten by the interface
+  // value y_s) in slot s + 1.  The thread of segment s is the only reader of
+  // slot s + 1 before it writes it, so no barrier separates the two uses.
+  __shared__ __align__(16) float X[4][(kT2Slots + 1) * kT2Pitch];
   __shared__ __align__(8) uint64_t full[kThomasMaxStages];
   __shared__ int tile_of[kThomasMaxStages];
-  __shared__ int go;
   const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
   const int s = 2 * warp + lane / 16;    // segment slot
   const int l0 = 2 * (lane % 16);        // first of the thread's two lines in the tile
@@ -628,27 +710,24 @@ thomas2_kernel(const __grid_constant__ ThomasJob job0, ThomasGeom lg, int* next_
     for (long long i = 0; i < S && !exhausted; ++i) issue(i, next());
     if (!exhausted) claim = next();
   }
+  __syncthreads();                       // tile_of of the first stages
 
+  // Block barriers per tile: after the forward sweeps (which also agrees
+  // whether every thread saw its stage land), after the interface rows, after
+  // the reduced systems and after the output tile.  tile_of[st] is written by
+  // thread 0 when it issues the stage, at least one tile (S >= 2 stages) and
+  // so at least one barrier before it is read here.
   long long i = 0;
   bool ok = true;
   for (;; ++i) {
     const int st = static_cast<int>(i % S);
     const uint32_t bar = ptx::smem_u32(&full[st]);
     const uint32_t par = static_cast<uint32_t>((i / S) & 1);
-    if (tid == 0) {
-      const int t = tile_of[st];
-      int* e = MULTI ? (t >= 0 && t < total_tiles ? job_of(t)->err : nullptr) : err0;
-      go = ptx::mbar_wait(bar, par, e, ptx::kErrWaitFull) ? 1 : 0;
-    }
-    __syncthreads();
-    if (!go) {
-      ok = false;
-      break;
-    }
     const int tile = tile_of[st];
     if (tile < 0) break;
-    for (int k = 0; k < 64 && !ptx::mbar_try_wait(bar, par); ++k) {
-    }   // the phase is complete: this acquires the TMA writes for every thread
+    // every thread waits for the stage itself (bounded); a wait that runs out
+    // is agreed on at the first barrier below
+    const bool landed = ptx::mbar_wait(bar, par, nullptr, 0);
     const ThomasJob& J = *job_of(tile);
     const int jid = MULTI ? static_cast<int>(&J - jobs) : 0;
     if (jid != cur) {                    // this instance's beta-scaled z rows into the table
@@ -671,14 +750,15 @@ thomas2_kernel(const __grid_constant__ ThomasJob job0, ThomasGeom lg, int* next_
     const bool active = s < J.geo.nseg;
     void* o0 = ot;
     void* o1 = ot + (O::NPL == 2 ? J.geo.out_bytes / 2 : 0);
-    const float* in = reinterpret_cast<const float*>(in_base + static_cast<size_t>(st) * lg.in_bytes);
+    float* in = reinterpret_cast<float*>(in_base + static_cast<size_t>(st) * lg.in_bytes);
 
     float shift[2];
     {
       // one division per tile: ldy is even and l0 is even, so the thread's
       // second line L + 1 lies in the same row p of modes as its first
       const int L = lt * TLT + l0;
-      const int p = L / J.ldy, q = L - p * J.ldy;
+      const int p = static_cast<int>((static_cast<unsigned long long>(L) * J.ldy_magic) >> J.ldy_shift);
+      const int q = L - p * J.ldy;
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
         const bool real = L + j < lines && q + j < J.ny;   // else a padding line: dummy shift
@@ -686,8 +766,10 @@ thomas2_kernel(const __grid_constant__ ThomasJob job0, ThomasGeom lg, int* next_
       }
     }
     // forward elimination of the interior rows (as in thomas_tma_kernel),
-    // two lines at a time
-    float inv[2][M - 1];
+    // two lines at a time.  g (zero left boundary) replaces d in the input
+    // stage; c' and the spike u (the response to a unit left boundary) stay in
+    // registers, so that the final values are x_t = g_t + u_t y_{s-1} - c'_t x_{t+1}.
+    float cpv[2][M - 1], uv[2][M - 1];
     float cprev[2] = {0.0f, 0.0f}, gprev[2] = {0.0f, 0.0f}, uprev[2] = {0.0f, 0.0f};
     if (active) {
       float P[2] = {1.0f, 1.0f}, Gs[2] = {0.0f, 0.0f}, Us[2] = {0.0f, 0.0f};
@@ -699,10 +781,11 @@ thomas2_kernel(const __grid_constant__ ThomasJob job0, ThomasGeom lg, int* next_
         for (int j = 0; j < 2; ++j) {
           const float m = fmaf(-rc.a, cprev[j], fmaf(rc.m, shift[j], rc.b));
           const float iv = __fdividef(1.0f, m);
-          inv[j][t] = iv;
           const float cp = rc.c * iv;
           const float g = fmaf(-rc.a, gprev[j], j ? d.y : d.x) * iv;
           const float u = (t == 0 ? -rc.a : -rc.a * uprev[j]) * iv;
+          cpv[j][t] = cp;
+          uv[j][t] = u;
           Gs[j] = fmaf(P[j], g, Gs[j]);
           Us[j] = fmaf(P[j], u, Us[j]);
           P[j] *= -cp;
@@ -710,6 +793,7 @@ thomas2_kernel(const __grid_constant__ ThomasJob job0, ThomasGeom lg, int* next_
           gprev[j] = g;
           uprev[j] = u;
         }
+        *reinterpret_cast<float2*>(in + (s0 + t) * TLT + l0) = make_float2(gprev[0], gprev[1]);
       }
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
@@ -725,9 +809,14 @@ thomas2_kernel(const __grid_constant__ ThomasJob job0, ThomasGeom lg, int* next_
         X[2][xo + j] = 0.0f;
       }
     }
-    __syncthreads();
+    if (__syncthreads_or(!landed)) {     // a stage did not land in time
+      if (tid == 0 && J.err) atomicOr(J.err, ptx::kErrWaitFull);
+      ok = false;
+      break;
+    }
     // interface row of the segment (its last row), coupled to the first row of
-    // the next segment through g_0, u_0, v_0 of that segment
+    // the next segment through g_0, u_0, v_0 of that segment (slot s + 1),
+    // written over those in slot s + 1
     float ra[2] = {0.0f, 0.0f}, rb[2] = {1.0f, 1.0f}, rcc[2] = {0.0f, 0.0f}, rd[2] = {0.0f, 0.0f};
     if (active) {
       const int k = s0 + M - 1;
@@ -746,82 +835,92 @@ thomas2_kernel(const __grid_constant__ ThomasJob job0, ThomasGeom lg, int* next_
         }
       }
     }
-    __syncthreads();                     // every g_0, u_0, v_0 has been read
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
-      X[0][xo + j] = ra[j];
-      X[1][xo + j] = rb[j];
-      X[2][xo + j] = rcc[j];
-      X[3][xo + j] = rd[j];
+      X[0][xo + kT2Pitch + j] = ra[j];
+      X[1][xo + kT2Pitch + j] = rb[j];
+      X[2][xo + kT2Pitch + j] = rcc[j];
+      X[3][xo + kT2Pitch + j] = rd[j];
     }
     __syncthreads();
-    // reduced systems: warp w takes lines 2w and 2w + 1, lane r interface row
-    // r.  Parallel cyclic reduction on rows scaled to a unit diagonal
-    // (a x_{r-d} + x_r + c x_{r+d} = d): eliminating both neighbours gives
+    // reduced systems: warp w takes lines 2w (lanes 0-15) and 2w + 1 (lanes
+    // 16-31); lane q of a half holds interface rows 2q and 2q + 1, scaled to a
+    // unit diagonal (a x_{r-1} + x_r + c x_{r+1} = d).  One odd-even step
+    // eliminates the odd rows from the even ones (the odd row below comes from
+    // lane q - 1), parallel cyclic reduction solves the 16 even rows, and each
+    // odd row is then recovered from its two even neighbours.  Eliminating both
+    // neighbours at distance d gives
     //   a' = -a a_{r-d},  c' = -c c_{r+d},  b' = 1 - a c_{r-d} - c a_{r+d},
     //   d' = d - a d_{r-d} - c d_{r+d},  then the row is scaled by 1 / b'.
     // Row 0 has a = 0 and row 31 has c = 0, and that stays so for every row
     // whose neighbour at distance d lies outside (its a or c is a product
-    // with such a zero), so the shuffles that fall off an end (which return
-    // the lane's own values) are always multiplied by zero.
+    // with such a zero), so the shuffles that fall off an end of a half (which
+    // return the lane's own values) are always multiplied by zero.
     {
-      const int r = lane;
-      float A[2], Cc[2], D[2];
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        const int ix = r * kT2Pitch + 2 * warp + j;
-        const float ib = __fdividef(1.0f, X[1][ix]);
-        A[j] = X[0][ix] * ib;
-        Cc[j] = X[2][ix] * ib;
-        D[j] = X[3][ix] * ib;
+      const int q = lane % 16;
+      const int col = 2 * warp + lane / 16;
+      const int ie = (2 * q + 1) * kT2Pitch + col, io = ie + kT2Pitch;   // rows 2q, 2q + 1
+      float ae, ce, de, ao, co, dO;
+      {
+        const float ibe = __fdividef(1.0f, X[1][ie]), ibo = __fdividef(1.0f, X[1][io]);
+        ae = X[0][ie] * ibe;
+        ce = X[2][ie] * ibe;
+        de = X[3][ie] * ibe;
+        ao = X[0][io] * ibo;
+        co = X[2][io] * ibo;
+        dO = X[3][io] * ibo;
+      }
+      {
+        // the odd row 2q - 1 (lane q - 1) and 2q + 1 (this lane)
+        const float am = __shfl_up_sync(0xffffffffu, ao, 1, 16), cm = __shfl_up_sync(0xffffffffu, co, 1, 16);
+        const float dm = __shfl_up_sync(0xffffffffu, dO, 1, 16);
+        const float b = fmaf(-ae, cm, fmaf(-ce, ao, 1.0f));
+        const float d = fmaf(-ae, dm, fmaf(-ce, dO, de));
+        const float ib = __fdividef(1.0f, b);
+        ae = -ae * am * ib;
+        ce = -ce * co * ib;
+        de = d * ib;
       }
 #pragma unroll
-      for (int dlt = 1; dlt < kT2Slots; dlt <<= 1) {
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          const float Am = __shfl_up_sync(0xffffffffu, A[j], dlt), Cm = __shfl_up_sync(0xffffffffu, Cc[j], dlt);
-          const float Dm = __shfl_up_sync(0xffffffffu, D[j], dlt);
-          const float Ap = __shfl_down_sync(0xffffffffu, A[j], dlt), Cp = __shfl_down_sync(0xffffffffu, Cc[j], dlt);
-          const float Dp = __shfl_down_sync(0xffffffffu, D[j], dlt);
-          const float b = fmaf(-A[j], Cm, fmaf(-Cc[j], Ap, 1.0f));
-          const float d = fmaf(-A[j], Dm, fmaf(-Cc[j], Dp, D[j]));
-          const float ib = __fdividef(1.0f, b);
-          A[j] = -A[j] * Am * ib;
-          Cc[j] = -Cc[j] * Cp * ib;
-          D[j] = d * ib;
-        }
+      for (int dlt = 1; dlt < 16; dlt <<= 1) {
+        const float Am = __shfl_up_sync(0xffffffffu, ae, dlt, 16), Cm = __shfl_up_sync(0xffffffffu, ce, dlt, 16);
+        const float Dm = __shfl_up_sync(0xffffffffu, de, dlt, 16);
+        const float Ap = __shfl_down_sync(0xffffffffu, ae, dlt, 16), Cp = __shfl_down_sync(0xffffffffu, ce, dlt, 16);
+        const float Dp = __shfl_down_sync(0xffffffffu, de, dlt, 16);
+        const float b = fmaf(-ae, Cm, fmaf(-ce, Ap, 1.0f));
+        const float d = fmaf(-ae, Dm, fmaf(-ce, Dp, de));
+        const float ib = __fdividef(1.0f, b);
+        ae = -ae * Am * ib;
+        ce = -ce * Cp * ib;
+        de = d * ib;
       }
-#pragma unroll
-      for (int j = 0; j < 2; ++j) X[3][r * kT2Pitch + 2 * warp + j] = D[j];
+      // de = x_{2q}; the odd row from x_{2q} and x_{2q+2} (lane q + 1)
+      const float xn = __shfl_down_sync(0xffffffffu, de, 1, 16);
+      X[3][ie] = de;
+      X[3][io] = fmaf(-ao, de, fmaf(-co, xn, dO));
     }
     if (tid == 0) ptx::bulk_wait_read<0>();   // the output tile of tile i-1 has been stored
     __syncthreads();
     if (active) {
-      // Thomas on the segment with boundary values y_{s-1} and y_s
-      float gp[2], x[2], gv[2][M - 1];
+      // back substitution on the segment with boundary values y_{s-1}, y_s
+      float yl[2], x[2];
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
-        x[j] = X[3][xo + j];
-        gp[j] = (s > 0) ? X[3][xo - kT2Pitch + j] : 0.0f;
-      }
-#pragma unroll
-      for (int t = 0; t < M - 1; ++t) {
-        const float a = coef[s0 + t].a;
-        const float2 d = *reinterpret_cast<const float2*>(in + (s0 + t) * TLT + l0);
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          gp[j] = fmaf(-a, gp[j], j ? d.y : d.x) * inv[j][t];
-          gv[j][t] = gp[j];
-        }
+        x[j] = X[3][xo + kT2Pitch + j];
+        yl[j] = (s > 0) ? X[3][xo + j] : 0.0f;
       }
       store_pair<FMT>(o0, o1, (s0 + M - 1) * TLT + l0, x[0], x[1]);
 #pragma unroll
       for (int t = M - 2; t >= 0; --t) {
-        const float c = coef[s0 + t].c;
-#pragma unroll
-        for (int j = 0; j < 2; ++j) x[j] = fmaf(-c * inv[j][t], x[j], gv[j][t]);
+        const float2 g = *reinterpret_cast<const float2*>(in + (s0 + t) * TLT + l0);
+        x[0] = fmaf(-cpv[0][t], x[0], fmaf(uv[0][t], yl[0], g.x));
+        x[1] = fmaf(-cpv[1][t], x[1], fmaf(uv[1][t], yl[1], g.y));
         store_pair<FMT>(o0, o1, (s0 + t) * TLT + l0, x[0], x[1]);
       }
+    }
+    if (J.singular && lt == 0) {         // the null line, in float64, over column 0
+      __syncthreads();                   // every back substitution has read X
+      null_line_block<FMT>(J, o0, o1, reinterpret_cast<double*>(&X[0][0]));
     }
     ptx::fence_proxy_async_smem();
     __syncthreads();
@@ -829,23 +928,14 @@ thomas2_kernel(const __grid_constant__ ThomasJob job0, ThomasGeom lg, int* next_
       issue(i + S, claim);
       if (!exhausted) claim = next();
     }
-    if (!(J.singular && lt == 0)) {
-      if (tid == 0) {
-        for (int b = 0; b < J.geo.nb; ++b) {
-          const int off = b * J.geo.rb * TLT * O::EB;
-          ptx::tma_store_2d(&J.map_o0, ptx::smem_u32(static_cast<uint8_t*>(o0) + off), lt * TLT, b * J.geo.rb);
-          if (O::NPL == 2)
-            ptx::tma_store_2d(&J.map_o1, ptx::smem_u32(static_cast<uint8_t*>(o1) + off), lt * TLT, b * J.geo.rb);
-        }
-        ptx::bulk_commit();
+    if (tid == 0) {
+      for (int b = 0; b < J.geo.nb; ++b) {
+        const int off = b * J.geo.rb * TLT * O::EB;
+        ptx::tma_store_2d(&J.map_o0, ptx::smem_u32(static_cast<uint8_t*>(o0) + off), lt * TLT, b * J.geo.rb);
+        if (O::NPL == 2)
+          ptx::tma_store_2d(&J.map_o1, ptx::smem_u32(static_cast<uint8_t*>(o1) + off), lt * TLT, b * J.geo.rb);
       }
-    } else {                             // the null line is not ours to write
-      for (int e = tid; e < TLT * J.nz; e += blockDim.x) {
-        const int ll = e % TLT, k = e / TLT;
-        if (ll == 0 || ll >= lines) continue;
-        copy_elem<FMT>(o0, o1, e, J.t3_0, J.t3_1, ll + static_cast<long long>(k) * lines);
-      }
-      __syncthreads();                   // the output tile is rewritten by the next tile
+      ptx::bulk_commit();
     }
   }
   if (tid == 0) {
@@ -882,20 +972,57 @@ __device__ __forceinline__ void null_line_body(int nz, long long stride, const f
   s = warp_sum_d(s);
   w = warp_sum_d(w);
   __syncwarp();
-  if (lane == 0) {
-    const double fshift = s / w;
-    double dp = 0.0;
-    for (int k = 0; k < nz - 1; ++k) {
-      dp = fma(-az[k], dp, line[k] - fshift) * ninvm[k];
-      line[k] = dp;
-    }
-    double x = 0.0;
-    line[nz - 1] = 0.0;
-    for (int k = nz - 2; k >= 0; --k) {
-      x = fma(-ncp[k], x, line[k]);
-      line[k] = x;
+  // The two sweeps are first-order linear recurrences, run as scans: lane L
+  // takes rows [k0, k1) of the nz - 1 eliminated rows, composes its rows'
+  // affine maps, the warp scans the 32 maps (5 shuffle steps), and each lane
+  // reruns its rows from its incoming value.
+  const double fshift = s / w;
+  const int n1 = nz - 1, chunk = (n1 + 31) / 32;
+  const int k0 = min(lane * chunk, n1), k1 = min(k0 + chunk, n1);
+  // forward: dp_k = (f_k - fshift - a_k dp_{k-1}) / m_k, dp_{-1} = 0
+  double A = 1.0, B = 0.0;
+  for (int k = k0; k < k1; ++k) {
+    const double al = -az[k] * ninvm[k];
+    B = fma(al, B, (line[k] - fshift) * ninvm[k]);
+    A *= al;
+  }
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {   // inclusive scan, lanes in row order
+    const double Ap = __shfl_up_sync(0xffffffffu, A, d), Bp = __shfl_up_sync(0xffffffffu, B, d);
+    if (lane >= d) {
+      B = fma(A, Bp, B);
+      A *= Ap;
     }
   }
+  double dp = __shfl_up_sync(0xffffffffu, B, 1);
+  if (lane == 0) dp = 0.0;
+  for (int k = k0; k < k1; ++k) {
+    dp = fma(-az[k], dp, line[k] - fshift) * ninvm[k];
+    line[k] = dp;
+  }
+  // backward: x_k = dp_k - c'_k x_{k+1}, x_{nz-1} = 0 (the vanishing pivot)
+  A = 1.0;
+  B = 0.0;
+  for (int k = k1 - 1; k >= k0; --k) {
+    const double g = -ncp[k];
+    B = fma(g, B, line[k]);
+    A *= g;
+  }
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {   // inclusive scan, lanes in reverse row order
+    const double Ap = __shfl_down_sync(0xffffffffu, A, d), Bp = __shfl_down_sync(0xffffffffu, B, d);
+    if (lane + d < 32) {
+      B = fma(A, Bp, B);
+      A *= Ap;
+    }
+  }
+  double x = __shfl_down_sync(0xffffffffu, B, 1);
+  if (lane == 31) x = 0.0;
+  for (int k = k1 - 1; k >= k0; --k) {
+    x = fma(-ncp[k], x, line[k]);
+    line[k] = x;
+  }
+  if (lane == 0) line[nz - 1] = 0.0;
   __syncwarp();
   double xs = 0.0;
   for (int k = lane; k < nz; k += 32) xs = fma(dz[k], line[k], xs);
@@ -2057,6 +2184,17 @@ int thomas2_m(int nz) {
   return best;
 }
 
+// Division by d (1 <= d < 2^31) of any 0 <= n < 2^31 as n * magic >> shift:
+// with 2^(s-1) < d <= 2^s, magic = floor(2^(31+s) / d) + 1 < 2^32 exceeds
+// 2^(31+s) / d by e / d with 0 < e <= d <= 2^s, so n * e < 2^(31+s) and the
+// quotient floor(n * magic / 2^(31+s)) is floor(n / d).
+void div_magic(unsigned d, unsigned* magic, int* shift) {
+  int s = 0;
+  while ((1ull << s) < d) ++s;
+  *magic = static_cast<unsigned>((1ull << (31 + s)) / d + 1);
+  *shift = 31 + s;
+}
+
 // The job record of a plan's Thomas step on workspace w (tile numbers from
 // `first`); false when T2 or T3 cannot be described by tensor maps or the
 // segments do not fit.
@@ -2083,6 +2221,7 @@ bool thomas2_job(const tpt_plan_s* p, const MixedWork& w, int first, ThomasJob* 
   J->ldy = m.ldy;
   J->ntiles = static_cast<int>((lines + TLT - 1) / TLT);
   J->first = first;
+  div_magic(static_cast<unsigned>(m.ldy), &J->ldy_magic, &J->ldy_shift);
   J->t3_0 = w.A[0];
   J->t3_1 = w.A[1];
   J->lamx = m.lam_f[0];
@@ -2095,6 +2234,13 @@ bool thomas2_job(const tpt_plan_s* p, const MixedWork& w, int first, ThomasJob* 
   J->singular = p->singular ? 1 : 0;
   J->err = reinterpret_cast<int*>(w.scal + 15);
   J->skip = w.skip;
+  J->t2 = static_cast<const float*>(w.B[0]);
+  J->naz = p->d_rows[2];
+  J->ncp = m.null_cp;
+  J->ninvm = m.null_invm;
+  J->ndz = p->d_dxf[2];
+  J->nbeta = p->beta;
+  J->nstride = lines;
   return true;
 }
 
@@ -2136,15 +2282,17 @@ int thomas_variant(int nz, int variant) {
   return (m2 >= 8 && nz > 192) ? 2 : 1;
 }
 
-// Step 2.3: T3 = modal Thomas solve of T2 (float32, in B) into A; the null
-// line of a singular problem on the second stream.
+// Step 2.3: T3 = modal Thomas solve of T2 (float32, in B) into A.  The null
+// line of a singular problem: inside thomas2_kernel, else on the second stream.
 template <int FMT>
 cudaError_t launch_thomas(const tpt_plan_s* p, const MixedWork& w, cudaStream_t s) {
   const MixedTables& m = p->mixed;
   const int nz = p->n[2];
   const float* t2 = static_cast<const float*>(w.B[0]);
+  const bool two = thomas_variant(nz, m.thomas_kernel) == 2;
+  const bool fork = p->singular && !two;
   std::unique_lock<std::recursive_mutex> side_lock(const_cast<tpt_plan_s*>(p)->side_mu, std::defer_lock);
-  if (p->singular) {   // fork: the float64 null line runs beside the partition kernel
+  if (fork) {   // fork: the float64 null line runs beside the partition kernel
     side_lock.lock();
     cudaError_t e = cudaEventRecord(m.fork, s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(m.side, m.fork, 0);
@@ -2160,7 +2308,7 @@ cudaError_t launch_thomas(const tpt_plan_s* p, const MixedWork& w, cudaStream_t 
   cudaError_t e = cudaErrorInvalidConfiguration;
   int tlt = 0, mm = 0;
   thomas_shape(nz, &tlt, &mm);
-  if (thomas_variant(nz, m.thomas_kernel) == 2) {
+  if (two) {
     switch (thomas2_m(nz)) {
       case 4: e = launch_thomas2_m<FMT, 4>(p, w, s); break;
       case 8: e = launch_thomas2_m<FMT, 8>(p, w, s); break;
@@ -2185,7 +2333,7 @@ cudaError_t launch_thomas(const tpt_plan_s* p, const MixedWork& w, cudaStream_t 
       default: break;
     }
   }
-  if (e == cudaSuccess && p->singular) e = cudaStreamWaitEvent(s, m.join, 0);   // join
+  if (e == cudaSuccess && fork) e = cudaStreamWaitEvent(s, m.join, 0);   // join
   return e;
 }
 
@@ -2418,12 +2566,6 @@ struct InstJob {
   double* scal;                // the instance's 16 workspace scalars
   int singular;
   double npts, vol, rtol;
-  // the float64 null line of a singular instance
-  long long nl_stride;
-  const float* t2;
-  void *t3_0, *t3_1;
-  const double *az, *ncp, *ninvm, *dz;
-  double beta;
   const int* skip;
   int first[3], blocks[3];     // block ranges of the prepare, gauge-sum and output kernels
 };
@@ -2448,15 +2590,6 @@ __global__ void __launch_bounds__(256) group_prepare_kernel(const InstJob* __res
   const InstJob& J = jobs[inst_of(jobs, njobs, 0, blockIdx.x)];
   prepare2_body<FMT>(blockIdx.x - J.first[0], J.blocks[0], J.nx, J.ny, J.nz, J.ldx, J.f, J.fh, J.fl, J.r0, J.r1,
                      J.gx, J.gy, J.gz, J.scal + 5);
-}
-
-// the float64 null lines of the singular instances in `ids` (one block each)
-template <int FMT>
-__global__ void __launch_bounds__(32)
-group_null_line_kernel(const InstJob* __restrict__ jobs, const int* __restrict__ ids) {
-  const InstJob& J = jobs[ids[blockIdx.x]];
-  if (J.skip && *J.skip) return;
-  null_line_body<FMT>(J.nz, J.nl_stride, J.t2, J.t3_0, J.t3_1, J.az, J.ncp, J.ninvm, J.dz, J.beta);
 }
 
 // stopping test of every instance (one thread each)
@@ -2980,8 +3113,6 @@ struct GroupSolve {
   std::vector<TGroup> tg;
   struct RGroup { int code = 0; int njobs = 0; int blocks = 0; ResJob* d = nullptr; };
   std::vector<RGroup> rg;
-  int* d_null_ids = nullptr;
-  int nnull = 0;
   int* d_counters = nullptr;           // one per Thomas group and correction
   int max_nz = 0;
   int blocks[3] = {0, 0, 0};           // prepare, gauge sum, output
@@ -3133,7 +3264,6 @@ int group_prepare(GroupSolve* g, const double* const* f, double* const* phi, voi
   // instances and the block ranges of the elementwise stages
   std::vector<InstJob> inst(n);
   int nb[3] = {0, 0, 0};
-  std::vector<int> null_ids;
   for (int i = 0; i < n; ++i) {
     const tpt_plan_s* p = g->plans[i];
     const MixedWork& w = ws[i];
@@ -3159,15 +3289,6 @@ int group_prepare(GroupSolve* g, const double* const* f, double* const* phi, voi
     J.npts = static_cast<double>(npts(p));
     J.vol = p->vol;
     J.rtol = p->rtol;
-    J.nl_stride = static_cast<long long>(p->mixed.ldy) * p->n[0];
-    J.t2 = static_cast<const float*>(w.B[0]);
-    J.t3_0 = w.A[0];
-    J.t3_1 = w.A[1];
-    J.az = p->d_rows[2];
-    J.ncp = p->mixed.null_cp;
-    J.ninvm = p->mixed.null_invm;
-    J.dz = p->d_dxf[2];
-    J.beta = p->beta;
     J.skip = w.skip;
     const long long lines = static_cast<long long>(p->n[1]) * p->n[2];
     const int per_block = 8;                    // lines of a 32 x 8 block
@@ -3182,7 +3303,6 @@ int group_prepare(GroupSolve* g, const double* const* f, double* const* phi, voi
     J.first[2] = nb[2];
     J.blocks[2] = b2;
     nb[2] += b2;
-    if (p->singular) null_ids.push_back(i);
   }
   for (int r = 0; r < 3; ++r) g->blocks[r] = nb[r];
   // GEMM jobs: x forward, y forward, y inverse, x inverse (first, later)
@@ -3258,7 +3378,6 @@ int group_prepare(GroupSolve* g, const double* const* f, double* const* phi, voi
   for (int st = 0; st < 5; ++st) bytes += align256(sizeof(tc::GemmJob) * n);
   for (auto& v : tj) bytes += align256(sizeof(ThomasJob) * v.size());
   for (auto& v : rj) bytes += align256(sizeof(ResJob) * v.size());
-  bytes += align256(sizeof(int) * std::max<size_t>(1, null_ids.size()));
   const int max_corr = 64;
   bytes += align256(sizeof(int) * tg.size() * max_corr);
   if (bytes > g->dmem_bytes) {
@@ -3288,8 +3407,6 @@ int group_prepare(GroupSolve* g, const double* const* f, double* const* phi, voi
     rg[r].njobs = static_cast<int>(rj[r].size());
     rg[r].d = static_cast<ResJob*>(put(rj[r].data(), sizeof(ResJob) * rj[r].size()));
   }
-  g->d_null_ids = static_cast<int*>(put(null_ids.data(), sizeof(int) * null_ids.size()));
-  g->nnull = static_cast<int>(null_ids.size());
   g->d_counters = static_cast<int*>(put(nullptr, sizeof(int) * tg.size() * max_corr));
   // a solve still in flight on s may be reading the previous tables
   MX_CUDA(cudaStreamSynchronize(s));
@@ -3326,17 +3443,11 @@ int group_enqueue_part(GroupSolve* g, double* d_scal, cudaStream_t s, int c0, in
     MX_CUDA(cudaGetLastError());
     MX_CUDA(cudaMemsetAsync(g->d_counters, 0, sizeof(int) * g->tg.size() * 64, s));
   }
-  const size_t null_smem = static_cast<size_t>(g->max_nz) * sizeof(double);
   for (int c = c0; c < c1; ++c) {
     for (int st : {0, 1}) MX_CUDA(tc::gemm_grouped(st == 1 ? tc::kOutF32 : tc::kOutSplitBF16, g->gemm_tma[st],
                                                   g->d_gemm[st], n, g->gemm_units[st], s));
     for (size_t k = 0; k < g->tg.size(); ++k)
       MX_CUDA(launch_thomas_m_group(g->tg[k], g->d_counters + 64 * k + c, g->dev, s));
-    if (g->nnull > 0) {
-      note_launch(1);
-      group_null_line_kernel<kFmtSplit><<<g->nnull, 32, null_smem, s>>>(g->d_inst, g->d_null_ids);
-      MX_CUDA(cudaGetLastError());
-    }
     MX_CUDA(tc::gemm_grouped(tc::kOutSplitBF16, g->gemm_tma[2], g->d_gemm[2], n, g->gemm_units[2], s));
     const int xi = c == 0 ? 3 : 4;
     MX_CUDA(tc::gemm_grouped(tc::kOutDF, false, g->d_gemm[xi], n, g->gemm_units[xi], s));

@@ -531,3 +531,5 @@ def test_mixed_thomas_kernels_match_the_oracle_recurrence(variant, nz, prec, coe
     fmt = 2.0 ** -16 if prec == "bf16x3" else 0.0
     assert np.all(e_got <= 16.0 * e_seq + 4e-6 + fmt), (e_got.max(), e_seq.max())
     assert np.median(e_got) <= 2.0 * np.median(e_seq) + 1e-6 + fmt / 2
+    if sing:   # the float64 null line: only the output format's rounding
+        assert e_got[0, 0] <= 1e-7 + fmt, e_got[0, 0]
