@@ -79,18 +79,48 @@ dgemm_cm_kernel(int M, int N, int K, const double* __restrict__ A, int lda, long
   }
 }
 
+// 1 / m in float64 without a division: the float32 reciprocal as the seed
+// (relative error below 2^-21) and two Newton steps r <- r + r (1 - m r), each
+// of which squares the relative error (2^-42, then below the float64
+// rounding).  Pivots outside the float32 range take the division.
+__device__ __forceinline__ double recip_fp64(double m) {
+  const float rf = __fdividef(1.0f, static_cast<float>(m));
+  if (!(fabsf(rf) < 1.0e37f && fabsf(rf) > 1.0e-37f)) return 1.0 / m;
+  double r = static_cast<double>(rf);
+  r = fma(r, fma(-m, r, 1.0), r);
+  return fma(r, fma(-m, r, 1.0), r);
+}
+
 // One thread per (i, j) line.  Forward elimination keeps c' in `scratch`
 // and d' in `out`; back substitution overwrites `out`.  The singular line
 // (null_i, null_j) is first projected to compatible form (its dz-weighted
 // mean removed, recorded in *defect), its last modal unknown is set to zero,
-// and the result is shifted to zero dz-weighted mean.
+// and the result is shifted to zero dz-weighted mean.  The beta-scaled z rows
+// are staged in shared memory once per block (3 Nz doubles, dynamic) when
+// ROWS is set; the pipe that bounds the kernel is GB300's float64 pipe, so
+// the per-point work is kept to two DFMA, the reciprocal and two multiplies
+// forward and one DFMA back.  f may alias out (each element is read before
+// the same thread writes it).
+template <bool ROWS>
 __global__ void __launch_bounds__(128)
-thomas_fp64_kernel(int nx, int ny, int nz, const double* __restrict__ f, double* out,
+thomas_fp64_kernel(int nx, int ny, int nz, const double* f, double* out,
                    double* __restrict__ scratch, const double* __restrict__ lamx,
                    const double* __restrict__ lamy, const double* __restrict__ az,
                    const double* __restrict__ bz, const double* __restrict__ cz,
                    const double* __restrict__ dz, double alpha, double beta, int null_i,
                    int null_j, double null_scale, double* defect) {
+  extern __shared__ double zrow[];   // beta a, beta b, beta c (ROWS)
+  if (ROWS) {
+    for (int k = threadIdx.x; k < nz; k += blockDim.x) {
+      zrow[k] = k > 0 ? beta * az[k] : 0.0;
+      zrow[nz + k] = beta * bz[k];
+      zrow[2 * nz + k] = k < nz - 1 ? beta * cz[k] : 0.0;
+    }
+    __syncthreads();
+  }
+  auto ra = [&](int k) { return ROWS ? zrow[k] : (k > 0 ? beta * az[k] : 0.0); };
+  auto rb = [&](int k) { return ROWS ? zrow[nz + k] : beta * bz[k]; };
+  auto rc = [&](int k) { return ROWS ? zrow[2 * nz + k] : (k < nz - 1 ? beta * cz[k] : 0.0); };
   const long long lines = static_cast<long long>(nx) * ny;
   const long long line = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
   if (line >= lines) return;
@@ -110,29 +140,33 @@ thomas_fp64_kernel(int nx, int ny, int nz, const double* __restrict__ f, double*
   double cp = 0.0, dp = 0.0;
   for (int k = 0; k < nz; ++k) {
     const long long o = line + k * lines;
-    const double sub = (k > 0) ? beta * az[k] : 0.0;
-    const double m = (beta * bz[k] + shift) - sub * cp;
-    const double rhs = (f[o] - fshift) - sub * dp;
+    const double sub = ra(k);
+    const double m = fma(-sub, cp, rb(k) + shift);
+    double fo = f[o];
+    if (is_null) fo -= fshift;
+    const double rhs = fma(-sub, dp, fo);
     if (is_null && k == nz - 1) {
       dp = 0.0;   // vanishing final pivot: the modal unknown is set to zero
     } else {
-      const double inv = 1.0 / m;
-      cp = (k < nz - 1) ? beta * cz[k] * inv : 0.0;
+      const double inv = recip_fp64(m);
+      cp = rc(k) * inv;
       dp = rhs * inv;
     }
     scratch[o] = cp;
     out[o] = dp;
   }
   double x = dp;
-  double xs = dz[nz - 1] * x, w = dz[nz - 1];
   for (int k = nz - 2; k >= 0; --k) {
     const long long o = line + k * lines;
-    x = out[o] - scratch[o] * x;
+    x = fma(-scratch[o], x, out[o]);
     out[o] = x;
-    xs = fma(dz[k], x, xs);
-    w += dz[k];
   }
   if (is_null) {
+    double xs = 0.0, w = 0.0;
+    for (int k = 0; k < nz; ++k) {
+      xs = fma(dz[k], out[line + k * lines], xs);
+      w += dz[k];
+    }
     const double mean = xs / w;
     for (int k = 0; k < nz; ++k) out[line + k * lines] -= mean;
   }
@@ -382,8 +416,11 @@ cudaError_t thomas_fp64(const tpt_plan_s* p, const double* fhat, double* phihat,
   const double* rz = p->d_rows[2];
   // f-hat of the null line equals (g_x g_y) times the physical constant
   const double null_scale = p->singular ? 1.0 / (p->null_g[0] * p->null_g[1]) : 0.0;
+  const size_t rows_bytes = 3 * static_cast<size_t>(nz) * sizeof(double);
+  const bool rows = rows_bytes <= 48 * 1024;   // within the default dynamic limit
   note_launch();
-  thomas_fp64_kernel<<<static_cast<unsigned>(nb), bs, 0, s>>>(
+  auto kern = rows ? thomas_fp64_kernel<true> : thomas_fp64_kernel<false>;
+  kern<<<static_cast<unsigned>(nb), bs, rows ? rows_bytes : 0, s>>>(
       nx, ny, nz, fhat, phihat, scratch, p->ddir[0].lam, p->ddir[1].lam, rz, rz + nz, rz + 2 * nz,
       p->d_dxf[2], p->alpha, p->beta, p->singular ? p->null_i : -1, p->singular ? p->null_j : -1,
       null_scale, p->singular ? defect : nullptr);
