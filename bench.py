@@ -163,6 +163,55 @@ def cpu_sample(n, nslab, reps=1):
     return 2.0 * per_point * n[0] * n[1] * nz_full
 
 
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name:"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.lower().startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def cpu_single_thread(size, nslab):
+    """cpu_sample in a child process with one BLAS/OpenMP thread; seconds per
+    full-size refined solve, or None if the child fails."""
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, os.path.abspath(__file__), "--size", str(size),
+                              "--cpu-sample-only", str(nslab)], capture_output=True, text=True, env=env,
+                             timeout=600)
+        return float(out.stdout.strip().splitlines()[-1])
+    except Exception:
+        return None
+
+
+def cpu_baseline_record(n, size, nslab, s_per_solve):
+    """The cpu_baseline object: the oracle at the host's BLAS threads on an
+    nslab-plane slab, plus the same sample on one thread (a 1/16 slab)."""
+    rec = {"value": 1.0 / s_per_solve, "unit": "solves/s", "cores": _threads(), "kind": "oracle",
+           "cpu": cpu_model(),
+           "sample": "oracle (numpy float64) correction pass + residual on a %dx%dx%d slab of the "
+                     "%d^3 stretched Neumann grid, scaled by points to one refined solve "
+                     "(2 passes + 2 residuals)" % (n[0], n[1], nslab, n[2])}
+    slab1 = max(1, nslab // 16)
+    t1 = cpu_single_thread(size, slab1)
+    if t1:
+        rec["single_thread"] = {"value": 1.0 / t1, "unit": "solves/s", "cores": 1,
+                                "sample": "the same on a %dx%dx%d slab, one BLAS thread" % (n[0], n[1], slab1)}
+    return rec
+
+
 def _threads():
     try:
         import threadpoolctl
@@ -186,6 +235,7 @@ def run_reference(args):
     sample = ("oracle (numpy float64) correction pass + residual on a %dx%dx%d slab of the "
               "%d^3 stretched Neumann grid, scaled by points to one refined solve "
               "(2 passes + 2 residuals)" % (n[0], n[1], nslab, n[2]))
+    cpu = cpu_baseline_record(n, args.size, nslab, s_per_solve)
     out = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": "solves/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -194,8 +244,7 @@ def run_reference(args):
         "config": {"workload": workload_name(args.size), "size": list(n),
                    "sample": "z-slab of %d" % nslab},
         "gpts_per_s": val * n[0] * n[1] * n[2] / 1e9,
-        "cpu_baseline": {"value": val, "unit": "solves/s", "cores": _threads(), "kind": "oracle",
-                         "sample": sample},
+        "cpu_baseline": dict(cpu, sample=sample),
         "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
@@ -436,10 +485,7 @@ def run_ours(args):
     cpu = None
     if not args.no_cpu_baseline:
         nslab = max(1, min(n[2], args.cpu_slabs))
-        s_per = cpu_sample(n, nslab)
-        cpu = {"value": 1.0 / s_per, "unit": "solves/s", "cores": _threads(), "kind": "oracle",
-               "sample": "oracle (numpy float64) correction pass + residual on a %dx%dx%d slab "
-                         "of the same grid, scaled by points to one refined solve" % (n[0], n[1], nslab)}
+        cpu = cpu_baseline_record(n, args.size, nslab, cpu_sample(n, nslab))
 
     last = next((i for i in reversed(infos) if i), info)
     out = {
@@ -990,7 +1036,11 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-warmup", type=int, default=200)
     ap.add_argument("--serve-requests-fp64", type=int, default=40)
+    ap.add_argument("--cpu-sample-only", type=int, default=0, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.cpu_sample_only:   # child of cpu_single_thread: seconds per solve, no GPU
+        print(cpu_sample(workload(args.size)[0], args.cpu_sample_only))
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
