@@ -1365,6 +1365,141 @@ residual_df2_kernel(int nx, int ny, int nz, int ldx, int kseg, const float* __re
 }
 
 // ---------------------------------------------------------------------------
+// Paired float32 arithmetic: the float pairs of two points side by side, hi
+// and lo parts as float2 (.x point a, .y point b), operated on by the paired
+// instructions of sm_100 and later (__fadd2_rn, __fmul2_rn, __ffma2_rn: two
+// IEEE round-to-nearest operations per instruction).  Every component goes
+// through the operations of the scalar helpers above (two_sum, df_diff,
+// acc_term) in the same order, so results are the same to the bit.  A
+// subtraction is a fused multiply-add by -1 (exact product, one rounding);
+// negated operands are passed in precomputed.
+struct dfx2 {
+  float2 hi, lo;
+};
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p_sub(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 p_dup(float v) { return make_float2(v, v); }
+
+// x - y of both points (df_diff): TwoSum of x.hi and -y.hi, whose error
+// RN(-y.hi - bb) enters as -RN(y.hi + bb), then the lo parts
+__device__ __forceinline__ dfx2 p_diff(const dfx2& x, const dfx2& y) {
+  const float2 s = p_sub(x.hi, y.hi);
+  const float2 bb = p_sub(s, x.hi);
+  const float2 e = p_sub(p_sub(x.hi, p_sub(s, bb)), p_add(y.hi, bb));
+  return {s, p_add(e, p_sub(x.lo, y.lo))};
+}
+// acc += (ch, cl) * d of both points (acc_term; acc_mul with d = x), given
+// nch = -ch and ncl = -cl: the product's error chain runs negated
+// (RN(pr - ch dh) = -RN(ch dh - pr), and so on) and is subtracted at the end
+__device__ __forceinline__ void p_term(dfx2& acc, float2 ch, float2 nch, float2 ncl, const dfx2& d) {
+  const float2 pr = p_mul(ch, d.hi);
+  float2 ne = p_fma(nch, d.hi, pr);
+  ne = p_fma(nch, d.lo, ne);
+  ne = p_fma(ncl, d.hi, ne);
+  const float2 s = p_add(acc.hi, pr);
+  const float2 bb = p_sub(s, acc.hi);
+  const float2 e = p_add(p_sub(acc.hi, p_sub(s, bb)), p_sub(pr, bb));
+  acc.hi = s;
+  acc.lo = p_add(acc.lo, p_sub(e, ne));
+}
+
+// Coefficients of two x or y terms of residual_pair_x2 (as applied to
+// points a and b): the coefficient (ch), its negation (nch) and the negated
+// lo part (ncl).  The x pair is term 1 (-x face of a; of b the face shared
+// with a) and term 2 (the face shared with b for a; +x face of b), the y pair
+// the -y and +y faces.  They live in shared memory (one x pair per lane, one y
+// pair per row of the tile) and are read for every plane, which keeps the
+// registers of the consumer threads within three blocks per SM.
+struct TermCoefs2 {
+  float2 ch0, ch1, nch0, nch1, ncl0, ncl1;
+};
+// rows d and d + off of one direction's float-pair rows (a at d, c at d + off)
+__device__ __forceinline__ TermCoefs2 term_coefs2(const BRows& R, int d0, int d1) {
+  // residual_pair's acc_term coefficients are the negated rows
+  TermCoefs2 t;
+  t.ch0 = make_float2(-R.ah[d0], -R.ah[d1]);
+  t.ch1 = make_float2(-R.ch[d0], -R.ch[d1]);
+  t.nch0 = make_float2(R.ah[d0], R.ah[d1]);
+  t.nch1 = make_float2(R.ch[d0], R.ch[d1]);
+  t.ncl0 = make_float2(R.al[d0], R.al[d1]);
+  t.ncl1 = make_float2(R.cl[d0], R.cl[d1]);
+  return t;
+}
+__device__ __forceinline__ TermCoefs2 lds_terms(const TermCoefs2* p) {
+  TermCoefs2 t;
+  const uint32_t a = ptx::smem_u32(p);
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(t.ch0.x), "=f"(t.ch0.y), "=f"(t.ch1.x), "=f"(t.ch1.y) : "r"(a));
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4 + 16];"
+               : "=f"(t.nch0.x), "=f"(t.nch0.y), "=f"(t.nch1.x), "=f"(t.nch1.y) : "r"(a));
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4 + 32];"
+               : "=f"(t.ncl0.x), "=f"(t.ncl0.y), "=f"(t.ncl1.x), "=f"(t.ncl1.y) : "r"(a));
+  return t;
+}
+// wall diagonals of the pair (Dirichlet walls only)
+struct WallCoefs2 {
+  float2 wxh, nwxh, nwxl, wyh, nwyh, nwyl;
+};
+template <int WX, int WY>
+__device__ __forceinline__ WallCoefs2 wall_coefs2(const BRows& RX, const BRows& RY, int i, int j) {
+  WallCoefs2 c;
+  const float wx0 = WX ? RX.wh[i] : 0.0f, wx1 = WX ? RX.wh[i + 1] : 0.0f;
+  const float wl0 = WX ? RX.wl[i] : 0.0f, wl1 = WX ? RX.wl[i + 1] : 0.0f;
+  c.wxh = make_float2(wx0, wx1);
+  c.nwxh = make_float2(-wx0, -wx1);
+  c.nwxl = make_float2(-wl0, -wl1);
+  const float wy = WY ? RY.wh[j] : 0.0f, wyl = WY ? RY.wl[j] : 0.0f;
+  c.wyh = p_dup(wy);
+  c.nwyh = p_dup(-wy);
+  c.nwyl = p_dup(-wyl);
+  return c;
+}
+
+// z coefficients of one plane for residual_pair_x2, duplicated for the two
+// points: term 5 (the face below, applied to -dz with the row's own sign),
+// term 6 (the face above, negated row), the wall diagonal
+struct ZCoef2 {
+  float2 ch5, nch5, ncl5, ch6, nch6, ncl6, wh, nwh, nwl;
+};
+__device__ __forceinline__ ZCoef2 zcoef2(float ah, float al, float ch, float cl, float wh, float wl) {
+  return {p_dup(ah), p_dup(-ah), p_dup(-al), p_dup(-ch), p_dup(ch), p_dup(cl), p_dup(wh), p_dup(-wh), p_dup(-wl)};
+}
+
+// residual_pair with paired instructions: P0 = (phi_a, phi_b), PP the plane
+// above, XL = (phi_{i-1}, phi_a), XR = (phi_b, phi_{i+2}), YM / YP the -y / +y
+// neighbours, F = (f_a, f_b), FS the duplicated fshift.  du holds on entry
+// phi(k) - phi(k-1) (the negated face difference below) and leaves holding
+// phi(k+1) - phi(k).  Term by term the operations are residual_pair's: the
+// -dmid of point b is the difference p0a - p0b, the z difference below enters
+// with the opposite sign and the row's own sign (the same products).
+template <int HAS_ALPHA, int WX, int WY, int WZ, int SING>
+__device__ __forceinline__ float2 residual_pair_x2(const TermCoefs2& cx, const TermCoefs2& cy,
+                                                   const WallCoefs2& c, const ZCoef2& z, float2 ach,
+                                                   float2 anch, float2 ancl, const dfx2& FS,
+                                                   const dfx2& P0, const dfx2& PP, const dfx2& XL,
+                                                   const dfx2& XR, const dfx2& YM, const dfx2& YP,
+                                                   const dfx2& F, dfx2& du) {
+  const dfx2 dup = p_diff(PP, P0);
+  dfx2 acc = SING ? p_diff(F, FS) : F;
+  p_term(acc, cx.ch0, cx.nch0, cx.ncl0, p_diff(XL, P0));
+  p_term(acc, cx.ch1, cx.nch1, cx.ncl1, p_diff(XR, P0));
+  p_term(acc, cy.ch0, cy.nch0, cy.ncl0, p_diff(YM, P0));
+  p_term(acc, cy.ch1, cy.nch1, cy.ncl1, p_diff(YP, P0));
+  p_term(acc, z.ch5, z.nch5, z.ncl5, du);
+  p_term(acc, z.ch6, z.nch6, z.ncl6, dup);
+  if (WX) p_term(acc, c.wxh, c.nwxh, c.nwxl, P0);
+  if (WY) p_term(acc, c.wyh, c.nwyh, c.nwyl, P0);
+  if (WZ) p_term(acc, z.wh, z.nwh, z.nwl, P0);
+  if (HAS_ALPHA) p_term(acc, ach, anch, ancl, P0);   // (-alpha_h, -alpha_l) * phi
+  du = dup;
+  return p_add(acc.hi, acc.lo);
+}
+
+// ---------------------------------------------------------------------------
 // TMA-staged residual.  A block owns a tile of kResTX x kResTY points of the
 // (x, y) plane and a segment of up to kResKseg planes; a producer warp
 // streams, plane by plane, the phi pair with a halo (x from i0 - 4 to
@@ -1381,8 +1516,9 @@ constexpr int kResPW = kResTX + 8;                         // phi row: 4 halo co
 constexpr int kResPBytes = ((kResPW * (kResTY + 2) * 4 + 127) / 128) * 128;
 constexpr int kResFBytes = kResTX * kResTY * 4;
 constexpr int kResStage = 2 * kResPBytes + 2 * kResFBytes;
-constexpr int kResZBytes = kResKseg * static_cast<int>(sizeof(ZCoef));
-constexpr int kResSmem = kResStages * kResStage + 2 * kResStages * 8 + kResZBytes + 128;
+constexpr int kResZBytes = kResKseg * static_cast<int>(sizeof(ZCoef2));
+constexpr int kResCBytes = (32 + kResTY) * static_cast<int>(sizeof(TermCoefs2));   // x per lane, y per row
+constexpr int kResSmem = kResStages * kResStage + 2 * kResStages * 8 + kResZBytes + kResCBytes + 128;
 constexpr int kResThreads = 32 * (kResTY + 1);
 
 // The residual of one instance for residual_tma_kernel: tensor maps of the
@@ -1423,7 +1559,8 @@ __device__ __forceinline__ void residual_tma_body(const ResJob& J, int bx, int b
   uint8_t* smem = res_smem_raw + ((128u - (ptx::smem_u32(res_smem_raw) & 127u)) & 127u);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kResStages * kResStage);
   uint64_t* empty = full + kResStages;
-  ZCoef* zc = reinterpret_cast<ZCoef*>(empty + kResStages);
+  ZCoef2* zc = reinterpret_cast<ZCoef2*>(empty + kResStages);
+  TermCoefs2* xyc = reinterpret_cast<TermCoefs2*>(zc + kResKseg);   // [32 lanes | kResTY rows]
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int i0 = bx * kResTX, j0 = by * kResTY;
   const int k0 = bz * kResKseg;
@@ -1438,7 +1575,16 @@ __device__ __forceinline__ void residual_tma_body(const ResJob& J, int bx, int b
   }
   for (int t = threadIdx.x; t < k1 - k0; t += kResThreads) {
     const int k = k0 + t;
-    zc[t] = {RZ.ah[k], RZ.al[k], RZ.ch[k], RZ.cl[k], WZ ? RZ.wh[k] : 0.0f, WZ ? RZ.wl[k] : 0.0f};
+    zc[t] = zcoef2(RZ.ah[k], RZ.al[k], RZ.ch[k], RZ.cl[k], WZ ? RZ.wh[k] : 0.0f, WZ ? RZ.wl[k] : 0.0f);
+  }
+  for (int t = threadIdx.x; t < 32 + kResTY; t += kResThreads) {
+    if (t < 32) {
+      const int ii = i0 + 2 * t < nx ? i0 + 2 * t : 0;
+      xyc[t] = term_coefs2(RX, ii, ii + 1);
+    } else {
+      const int jj = j0 + t - 32 < ny ? j0 + t - 32 : 0;
+      xyc[t] = term_coefs2(RY, jj, jj);
+    }
   }
   __syncthreads();
   if (warp == kResTY) {
@@ -1477,51 +1623,50 @@ __device__ __forceinline__ void residual_tma_body(const ResJob& J, int bx, int b
   const bool active = i < nx && j < ny;
   // periodic directions: the edge points load their wrapped neighbours
   const bool edge = active && ((px && (i == 0 || i + 2 == nx)) || (py && (j == 0 || j == ny - 1)));
-  const PairCoefs c = pair_coefs<WX, WY>(RX, RY, active ? i : 0, active ? j : 0);
+  const WallCoefs2 c = wall_coefs2<WX, WY>(RX, RY, active ? i : 0, active ? j : 0);
   const df fshift = SING ? fshift_of(J.fsums, J.inv_vol) : df{0.0f, 0.0f};
+  const dfx2 FS = {p_dup(fshift.hi), p_dup(fshift.lo)};
+  const float2 ach = p_dup(-alpha_h), anch = p_dup(alpha_h), ancl = p_dup(alpha_l);
   const int pc = (warp + 1) * kResPW + 4 + 2 * lane;          // centre of the pair in a phi stage
   const int fc = warp * kResTX + 2 * lane;
   const long long sz = static_cast<long long>(nx) * ny;
-  auto pair_at = [&](const uint8_t* st, int e, df& a, df& b) {
-    const float2 h = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(st) + e);
-    const float2 l = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(st + kResPBytes) + e);
-    a = {h.x, l.x};
-    b = {h.y, l.y};
+  auto pair_at = [&](const uint8_t* st, int e) -> dfx2 {      // points e, e + 1 (e even)
+    return {*reinterpret_cast<const float2*>(reinterpret_cast<const float*>(st) + e),
+            *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(st + kResPBytes) + e)};
+  };
+  auto point_at = [&](const uint8_t* st, int e) -> df {
+    return {reinterpret_cast<const float*>(st)[e], reinterpret_cast<const float*>(st + kResPBytes)[e]};
   };
   auto release = [&](int s) {
     __syncwarp();
     if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&empty[s]));
   };
   float acc2 = 0.0f;
-  df pma = {0.0f, 0.0f}, pmb = {0.0f, 0.0f}, p0a = {0.0f, 0.0f}, p0b = {0.0f, 0.0f};
+  dfx2 P0 = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)}, du = P0;
   bool ok = ptx::mbar_wait(ptx::smem_u32(&full[0]), 0, err, ptx::kErrWaitFull);
+  dfx2 PM = P0;
   if (ok) {
-    pair_at(smem, pc, pma, pmb);
+    PM = pair_at(smem, pc);
     release(0);
     ok = ptx::mbar_wait(ptx::smem_u32(&full[1]), 0, err, ptx::kErrWaitFull);
   }
-  if (ok) pair_at(smem + kResStage, pc, p0a, p0b);
-  df dza = df_diff(pma, p0a), dzb = df_diff(pmb, p0b);        // down from plane k0
+  if (ok) P0 = pair_at(smem + kResStage, pc);
+  du = p_diff(P0, PM);                                         // phi(k0) - phi(k0 - 1)
   long long ro = i + static_cast<long long>(ldx) * (j + static_cast<long long>(ny) * k0);
   const long long rstep = static_cast<long long>(ldx) * ny;
   int s = 1, sn = 2;                                           // stages of planes k and k + 1
   uint32_t parn = 0;                                           // phase parity of stage sn
 #pragma unroll 2
   for (int k = k0; ok && k < k1; ++k) {
-    const ZCoef z = zc[k - k0];
+    const ZCoef2 z = zc[k - k0];
     if (!ptx::mbar_wait(ptx::smem_u32(&full[sn]), parn, err, ptx::kErrWaitFull)) break;
-    df ppa, ppb;
-    pair_at(smem + sn * kResStage, pc, ppa, ppb);
+    const dfx2 PP = pair_at(smem + sn * kResStage, pc);
     const uint8_t* st = smem + s * kResStage;
-    df xma, xmb, xpa, xpb, yma, ymb, ypa, ypb;
-    pair_at(st, pc - 2, xma, xmb);                             // xmb: the -x neighbour of a
-    pair_at(st, pc + 2, xpa, xpb);                             // xpa: the +x neighbour of b
-    pair_at(st, pc - kResPW, yma, ymb);
-    pair_at(st, pc + kResPW, ypa, ypb);
-    const float2 fhv = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(st + 2 * kResPBytes) + fc);
-    const float2 flv =
-        *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(st + 2 * kResPBytes + kResFBytes) + fc);
-    df xm = xmb, xp = xpa;
+    df xm = point_at(st, pc - 1), xp = point_at(st, pc + 2);
+    dfx2 YM = pair_at(st, pc - kResPW), YP = pair_at(st, pc + kResPW);
+    const dfx2 F = {*reinterpret_cast<const float2*>(reinterpret_cast<const float*>(st + 2 * kResPBytes) + fc),
+                    *reinterpret_cast<const float2*>(
+                        reinterpret_cast<const float*>(st + 2 * kResPBytes + kResFBytes) + fc)};
     if (edge) {
       const long long plane = sz * k;
       if (px && i == 0) {
@@ -1534,28 +1679,25 @@ __device__ __forceinline__ void residual_tma_body(const ResJob& J, int bx, int b
       }
       if (py && j == 0) {
         const long long o = plane + static_cast<long long>(nx) * (ny - 1) + i;
-        const float2 h = *reinterpret_cast<const float2*>(ph + o), l = *reinterpret_cast<const float2*>(pl + o);
-        yma = {h.x, l.x};
-        ymb = {h.y, l.y};
+        YM = {*reinterpret_cast<const float2*>(ph + o), *reinterpret_cast<const float2*>(pl + o)};
       }
       if (py && j == ny - 1) {
         const long long o = plane + i;
-        const float2 h = *reinterpret_cast<const float2*>(ph + o), l = *reinterpret_cast<const float2*>(pl + o);
-        ypa = {h.x, l.x};
-        ypb = {h.y, l.y};
+        YP = {*reinterpret_cast<const float2*>(ph + o), *reinterpret_cast<const float2*>(pl + o)};
       }
     }
     if (active) {
-      float rv[2];
-      residual_pair<HAS_ALPHA, WX, WY, WZ, SING>(c, z, alpha_h, alpha_l, fshift, p0a, p0b, ppa, ppb, xm, xp, yma,
-                                                 ymb, ypa, ypb, {fhv.x, flv.x}, {fhv.y, flv.y}, dza, dzb, rv);
-      Elem2<FMT>::store(r0, r1, ro, rv[0], rv[1]);
-      acc2 = fmaf(rv[0], rv[0], acc2);
-      acc2 = fmaf(rv[1], rv[1], acc2);
+      const dfx2 XL = {make_float2(xm.hi, P0.hi.x), make_float2(xm.lo, P0.lo.x)};   // (phi_{i-1}, phi_a)
+      const dfx2 XR = {make_float2(P0.hi.y, xp.hi), make_float2(P0.lo.y, xp.lo)};   // (phi_b, phi_{i+2})
+      const TermCoefs2 cx = lds_terms(xyc + lane), cy = lds_terms(xyc + 32 + warp);
+      const float2 rv = residual_pair_x2<HAS_ALPHA, WX, WY, WZ, SING>(cx, cy, c, z, ach, anch, ancl, FS, P0, PP,
+                                                                      XL, XR, YM, YP, F, du);
+      Elem2<FMT>::store(r0, r1, ro, rv.x, rv.y);
+      acc2 = fmaf(rv.x, rv.x, acc2);
+      acc2 = fmaf(rv.y, rv.y, acc2);
     }
     release(s);
-    p0a = ppa;
-    p0b = ppb;
+    P0 = PP;
     ro += rstep;
     s = sn;
     if (++sn == kResStages) {
@@ -1568,7 +1710,7 @@ __device__ __forceinline__ void residual_tma_body(const ResJob& J, int bx, int b
 }
 
 template <int FMT, int HAS_ALPHA, int WX, int WY, int WZ, int SING>
-__global__ void __launch_bounds__(kResThreads, 3)
+__global__ void __launch_bounds__(kResThreads, (WX || WY || WZ || HAS_ALPHA) ? 2 : 3)
 residual_tma_kernel(const __grid_constant__ ResJob J) {
   if (J.skip && *J.skip) return;   // the refinement has stopped
   residual_tma_body<FMT, HAS_ALPHA, WX, WY, WZ, SING>(J, blockIdx.x, blockIdx.y, blockIdx.z);
@@ -1588,7 +1730,7 @@ __device__ __forceinline__ int job_index(const Job* __restrict__ jobs, int njobs
 
 // Grouped residual: block b is a tile of the instance whose range holds it.
 template <int FMT, int HAS_ALPHA, int WX, int WY, int WZ, int SING>
-__global__ void __launch_bounds__(kResThreads, 3)
+__global__ void __launch_bounds__(kResThreads, 2)   // the job lookup needs the registers of a third block
 residual_tma_group_kernel(const ResJob* __restrict__ jobs, int njobs) {
   const ResJob& J = jobs[job_index(jobs, njobs, blockIdx.x)];
   if (J.skip && *J.skip) return;
