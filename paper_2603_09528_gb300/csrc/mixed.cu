@@ -522,6 +522,24 @@ __device__ __forceinline__ void store_pair(void* o0, void* o1, int i, float x0, 
   }
 }
 
+// Paired float32 operations (sm_100 and later: __fadd2_rn, __fmul2_rn,
+// __ffma2_rn apply two IEEE round-to-nearest operations in one instruction,
+// component by component).  A subtraction is a fused multiply-add by -1
+// (exact product, one rounding), so it rounds as a - b does.
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p_sub(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
+}
+__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 p_dup(float v) { return make_float2(v, v); }
+
+// Row of thomas2_kernel's shared table with each coefficient duplicated for
+// the thread's two lines: -beta a_k, beta b_k, beta c_k and the shift factor.
+struct RowCoef2 {
+  float2 na, b, c, m;
+};
+
 // The data of one instance for thomas2_kernel: tensor maps of T2 (in) and
 // T3 (out planes), its stage geometry, sizes, tables and flags.  A grouped
 // launch reads these from a device table (`first` = the instance's first
@@ -631,7 +649,7 @@ thomas2_kernel(const __grid_constant__ ThomasJob job0, ThomasGeom lg, int* next_
   static_assert(M >= 2 && M <= 16, "segments of 2 to 16 rows");
   extern __shared__ __align__(128) uint8_t dsm_raw[];
   uint8_t* dsm = dsm_raw + ((1024u - (ptx::smem_u32(dsm_raw) & 1023u)) & 1023u);
-  RowCoef* coef = reinterpret_cast<RowCoef*>(dsm);
+  RowCoef2* coef = reinterpret_cast<RowCoef2*>(dsm);
   uint8_t* in_base = dsm + lg.coef_bytes;
   uint8_t* ot = in_base + static_cast<size_t>(lg.stages) * lg.in_bytes;
   // reduced-system buffer: first g_0, u_0, v_0 of segment s in slot s, then
@@ -733,14 +751,14 @@ thomas2_kernel(const __grid_constant__ ThomasJob job0, ThomasGeom lg, int* next_
     if (jid != cur) {                    // this instance's beta-scaled z rows into the table
       if (cur >= 0) __syncthreads();     // the previous tile is done with them
       for (int k = tid; k < J.geo.sr; k += blockDim.x) {
-        RowCoef rc{0.0f, 1.0f, 0.0f, 0.0f};
+        float a = 0.0f, b = 1.0f, c = 0.0f, m = 0.0f;   // padding rows: identity
         if (k < J.nz) {
-          rc.a = k > 0 ? J.beta * J.az[k] : 0.0f;
-          rc.b = J.beta * J.bz[k];
-          rc.c = k < J.nz - 1 ? J.beta * J.cz[k] : 0.0f;
-          rc.m = 1.0f;
+          a = k > 0 ? J.beta * J.az[k] : 0.0f;
+          b = J.beta * J.bz[k];
+          c = k < J.nz - 1 ? J.beta * J.cz[k] : 0.0f;
+          m = 1.0f;
         }
-        coef[k] = rc;
+        coef[k] = {p_dup(-a), p_dup(b), p_dup(c), p_dup(m)};
       }
       cur = jid;
       __syncthreads();
@@ -769,38 +787,37 @@ thomas2_kernel(const __grid_constant__ ThomasJob job0, ThomasGeom lg, int* next_
     // two lines at a time.  g (zero left boundary) replaces d in the input
     // stage; c' and the spike u (the response to a unit left boundary) stay in
     // registers, so that the final values are x_t = g_t + u_t y_{s-1} - c'_t x_{t+1}.
-    float cpv[2][M - 1], uv[2][M - 1];
-    float cprev[2] = {0.0f, 0.0f}, gprev[2] = {0.0f, 0.0f}, uprev[2] = {0.0f, 0.0f};
+    // The two lines' operations run as paired instructions (float2 .x, .y).
+    float2 ncpv[M - 1], uv[M - 1];       // -c' and u of rows 0 .. M - 2
+    float2 cprev = make_float2(0.0f, 0.0f), gprev = cprev, uprev = cprev;
+    const float2 sh = make_float2(shift[0], shift[1]);
     if (active) {
-      float P[2] = {1.0f, 1.0f}, Gs[2] = {0.0f, 0.0f}, Us[2] = {0.0f, 0.0f};
+      float2 P = make_float2(1.0f, 1.0f), Gs = make_float2(0.0f, 0.0f), Us = Gs;
 #pragma unroll
       for (int t = 0; t < M - 1; ++t) {
-        const RowCoef rc = coef[s0 + t];
+        const RowCoef2 rc = coef[s0 + t];
         const float2 d = *reinterpret_cast<const float2*>(in + (s0 + t) * TLT + l0);
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-          const float m = fmaf(-rc.a, cprev[j], fmaf(rc.m, shift[j], rc.b));
-          const float iv = __fdividef(1.0f, m);
-          const float cp = rc.c * iv;
-          const float g = fmaf(-rc.a, gprev[j], j ? d.y : d.x) * iv;
-          const float u = (t == 0 ? -rc.a : -rc.a * uprev[j]) * iv;
-          cpv[j][t] = cp;
-          uv[j][t] = u;
-          Gs[j] = fmaf(P[j], g, Gs[j]);
-          Us[j] = fmaf(P[j], u, Us[j]);
-          P[j] *= -cp;
-          cprev[j] = cp;
-          gprev[j] = g;
-          uprev[j] = u;
-        }
-        *reinterpret_cast<float2*>(in + (s0 + t) * TLT + l0) = make_float2(gprev[0], gprev[1]);
+        const float2 m = p_fma(rc.na, cprev, p_fma(rc.m, sh, rc.b));
+        const float2 iv = make_float2(__fdividef(1.0f, m.x), __fdividef(1.0f, m.y));
+        const float2 cp = p_mul(rc.c, iv);
+        const float2 g = p_mul(p_fma(rc.na, gprev, d), iv);
+        const float2 u = p_mul(t == 0 ? rc.na : p_mul(rc.na, uprev), iv);
+        ncpv[t] = p_mul(cp, make_float2(-1.0f, -1.0f));
+        uv[t] = u;
+        Gs = p_fma(P, g, Gs);
+        Us = p_fma(P, u, Us);
+        P = p_mul(P, ncpv[t]);
+        cprev = cp;
+        gprev = g;
+        uprev = u;
+        *reinterpret_cast<float2*>(in + (s0 + t) * TLT + l0) = g;
       }
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        X[0][xo + j] = Gs[j];
-        X[1][xo + j] = Us[j];
-        X[2][xo + j] = P[j];
-      }
+      X[0][xo] = Gs.x;
+      X[0][xo + 1] = Gs.y;
+      X[1][xo] = Us.x;
+      X[1][xo + 1] = Us.y;
+      X[2][xo] = P.x;
+      X[2][xo + 1] = P.y;
     } else {
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
@@ -820,18 +837,20 @@ thomas2_kernel(const __grid_constant__ ThomasJob job0, ThomasGeom lg, int* next_
     float ra[2] = {0.0f, 0.0f}, rb[2] = {1.0f, 1.0f}, rcc[2] = {0.0f, 0.0f}, rd[2] = {0.0f, 0.0f};
     if (active) {
       const int k = s0 + M - 1;
-      const RowCoef rc = coef[k];
+      const RowCoef2 rc = coef[k];
+      const float a = -rc.na.x, b = rc.b.x, c = rc.c.x, mf = rc.m.x;
       const float2 d = *reinterpret_cast<const float2*>(in + k * TLT + l0);
+      const float cpr[2] = {cprev.x, cprev.y}, gpr[2] = {gprev.x, gprev.y}, upr[2] = {uprev.x, uprev.y};
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
-        ra[j] = rc.a * uprev[j];
-        rb[j] = fmaf(-rc.a, cprev[j], fmaf(rc.m, shift[j], rc.b));
-        rd[j] = fmaf(-rc.a, gprev[j], j ? d.y : d.x);
+        ra[j] = a * upr[j];
+        rb[j] = fmaf(-a, cpr[j], fmaf(mf, shift[j], b));
+        rd[j] = fmaf(-a, gpr[j], j ? d.y : d.x);
         if (s + 1 < kT2Slots) {
           const int on = xo + kT2Pitch + j;
-          rb[j] = fmaf(rc.c, X[1][on], rb[j]);
-          rcc[j] = rc.c * X[2][on];
-          rd[j] = fmaf(-rc.c, X[0][on], rd[j]);
+          rb[j] = fmaf(c, X[1][on], rb[j]);
+          rcc[j] = c * X[2][on];
+          rd[j] = fmaf(-c, X[0][on], rd[j]);
         }
       }
     }
@@ -903,19 +922,14 @@ thomas2_kernel(const __grid_constant__ ThomasJob job0, ThomasGeom lg, int* next_
     __syncthreads();
     if (active) {
       // back substitution on the segment with boundary values y_{s-1}, y_s
-      float yl[2], x[2];
-#pragma unroll
-      for (int j = 0; j < 2; ++j) {
-        x[j] = X[3][xo + kT2Pitch + j];
-        yl[j] = (s > 0) ? X[3][xo + j] : 0.0f;
-      }
-      store_pair<FMT>(o0, o1, (s0 + M - 1) * TLT + l0, x[0], x[1]);
+      float2 x = make_float2(X[3][xo + kT2Pitch], X[3][xo + kT2Pitch + 1]);
+      const float2 yl = (s > 0) ? make_float2(X[3][xo], X[3][xo + 1]) : make_float2(0.0f, 0.0f);
+      store_pair<FMT>(o0, o1, (s0 + M - 1) * TLT + l0, x.x, x.y);
 #pragma unroll
       for (int t = M - 2; t >= 0; --t) {
         const float2 g = *reinterpret_cast<const float2*>(in + (s0 + t) * TLT + l0);
-        x[0] = fmaf(-cpv[0][t], x[0], fmaf(uv[0][t], yl[0], g.x));
-        x[1] = fmaf(-cpv[1][t], x[1], fmaf(uv[1][t], yl[1], g.y));
-        store_pair<FMT>(o0, o1, (s0 + t) * TLT + l0, x[0], x[1]);
+        x = p_fma(ncpv[t], x, p_fma(uv[t], yl, g));
+        store_pair<FMT>(o0, o1, (s0 + t) * TLT + l0, x.x, x.y);
       }
     }
     if (J.singular && lt == 0) {         // the null line, in float64, over column 0
@@ -1365,24 +1379,15 @@ residual_df2_kernel(int nx, int ny, int nz, int ldx, int kseg, const float* __re
 }
 
 // ---------------------------------------------------------------------------
-// Paired float32 arithmetic: the float pairs of two points side by side, hi
-// and lo parts as float2 (.x point a, .y point b), operated on by the paired
-// instructions of sm_100 and later (__fadd2_rn, __fmul2_rn, __ffma2_rn: two
-// IEEE round-to-nearest operations per instruction).  Every component goes
-// through the operations of the scalar helpers above (two_sum, df_diff,
-// acc_term) in the same order, so results are the same to the bit.  A
-// subtraction is a fused multiply-add by -1 (exact product, one rounding);
-// negated operands are passed in precomputed.
+// Float pairs of two points side by side for the paired instructions (p_add
+// and the rest, defined with the Thomas kernels): hi and lo parts as float2
+// (.x point a, .y point b).  Every component goes through the operations of
+// the scalar helpers above (two_sum, df_diff, acc_term) in the same order, so
+// results are the same to the bit; negated operands are passed in
+// precomputed.
 struct dfx2 {
   float2 hi, lo;
 };
-__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 p_sub(float2 a, float2 b) {
-  return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a);
-}
-__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 p_dup(float v) { return make_float2(v, v); }
 
 // x - y of both points (df_diff): TwoSum of x.hi and -y.hi, whose error
 // RN(-y.hi - bb) enters as -RN(y.hi + bb), then the lo parts
@@ -2252,7 +2257,8 @@ void thomas_shape(int nz, int* tlt, int* m_out) {
 
 // Stage geometry and ring size of thomas_tma_kernel; false when the shared
 // memory budget cannot hold two input stages and the output tile.
-bool thomas_geom(int nz, int m, int tlt, int out_npl, int out_eb, ThomasGeom* g, int budget = kThomasSmemBudget) {
+bool thomas_geom(int nz, int m, int tlt, int out_npl, int out_eb, ThomasGeom* g, int budget = kThomasSmemBudget,
+                 int row_bytes = static_cast<int>(sizeof(RowCoef))) {
   g->nseg = (nz + m - 1) / m;
   const int r = g->nseg * m;
   g->nb = (r + 255) / 256;
@@ -2260,7 +2266,7 @@ bool thomas_geom(int nz, int m, int tlt, int out_npl, int out_eb, ThomasGeom* g,
   g->sr = g->nb * g->rb;
   g->in_bytes = g->sr * tlt * 4;
   g->out_bytes = g->sr * tlt * out_eb * out_npl;
-  g->coef_bytes = (g->sr * static_cast<int>(sizeof(RowCoef)) + 1023) & ~1023;
+  g->coef_bytes = (g->sr * row_bytes + 1023) & ~1023;
   g->stages = (budget - 1024 - g->coef_bytes - g->out_bytes) / g->in_bytes;
   if (g->stages > kThomasMaxStages) g->stages = kThomasMaxStages;
   return g->stages >= 2;
@@ -2349,7 +2355,9 @@ bool thomas2_job(const tpt_plan_s* p, const MixedWork& w, int first, ThomasJob* 
   const int nz = p->n[2];
   if (lines + TLT > 0x7fffffffLL) return false;   // int line indices and TMA coordinates
   std::memset(J, 0, sizeof(*J));
-  if (!thomas_geom(nz, M, TLT, O::NPL, O::EB, &J->geo, kT2SmemBudget) || J->geo.nseg > kT2Slots) return false;
+  if (!thomas_geom(nz, M, TLT, O::NPL, O::EB, &J->geo, kT2SmemBudget, static_cast<int>(sizeof(RowCoef2))) ||
+      J->geo.nseg > kT2Slots)
+    return false;
   if (!tc::make_plain_map(&J->map_in, w.B[0], 4, lines, nz, lines * 4, TLT, J->geo.rb)) return false;
   if (!tc::make_plain_map(&J->map_o0, w.A[0], O::EB, lines, nz, lines * O::EB, TLT, J->geo.rb)) return false;
   if (O::NPL == 2) {
