@@ -83,7 +83,9 @@ struct Cfg {
 
 // Store one 32-column chunk of the accumulator (registers r) for row m.
 template <int OUT>
-__device__ __forceinline__ void store_chunk(const GemmOut& g, long long mterm, int nb, const uint32_t (&r)[32]) {
+// acc: add into the output (float-pair and float64 modes)
+__device__ __forceinline__ void store_chunk(const GemmOut& g, long long mterm, int nb, const uint32_t (&r)[32],
+                                            bool acc) {
   if (OUT == kOutDF) {
     // read-modify-write of the float pair: issue every load of the chunk
     // before any dependent arithmetic so the 64 loads overlap
@@ -94,8 +96,8 @@ __device__ __forceinline__ void store_chunk(const GemmOut& g, long long mterm, i
     for (int j = 0; j < 32; ++j) {
       const int n = nb + j;
       const long long idx = mterm + static_cast<long long>(n < g.N ? n : 0) * g.sn;
-      oh[j] = (g.accumulate && n < g.N) ? ph[idx] : 0.0f;
-      ol[j] = (g.accumulate && n < g.N) ? pl[idx] : 0.0f;
+      oh[j] = (acc && n < g.N) ? ph[idx] : 0.0f;
+      ol[j] = (acc && n < g.N) ? pl[idx] : 0.0f;
     }
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
@@ -111,7 +113,7 @@ __device__ __forceinline__ void store_chunk(const GemmOut& g, long long mterm, i
     }
     return;
   }
-  if (OUT == kOutF64 && g.accumulate) {
+  if (OUT == kOutF64 && acc) {
     // float64 read-modify-write (the levels of an Ozaki product): every load
     // of the chunk is issued before the first store, so the 32 loads overlap
     double* o = static_cast<double*>(g.out0);
@@ -261,6 +263,15 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
     }
     return true;
   };
+  // products per tile (float64 levels), K chunks of product lv and its B offset
+  constexpr bool kLevels = OUT == kOutF64;
+  auto npass_of = [&](const GemmOut& gg) -> int { return (kLevels && gg.levels > 0) ? gg.levels : 1; };
+  auto nk_of = [&](const GemmOut& gg, int lv, int nkq) -> int {
+    return (kLevels && gg.levels > 0) ? ((lv + 1) * gg.level_k) / C::BK : nkq;
+  };
+  auto bofs_of = [&](const GemmOut& gg, int lv) -> int {
+    return (kLevels && gg.levels > 0) ? (gg.levels - 1 - lv) * gg.level_k : 0;
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) {
@@ -309,7 +320,10 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
       const CUtensorMap* mB1 = MULTI ? &mq[3] : &tB1;
       volatile int* abort_q = MULTI ? reinterpret_cast<volatile int*>(gq->err) : abort_flag;
       last_err = gq->err;
-      for (int kc = 0; kc < nkq; ++kc, ++it) {
+      const int npass = npass_of(*gq);
+      for (int lv = 0; lv < npass && ok; ++lv) {
+      const int nkp = nk_of(*gq, lv, nkq), kb = bofs_of(*gq, lv);
+      for (int kc = 0; kc < nkp; ++kc, ++it) {
         const int s = static_cast<int>(it % C::STAGES);
         const long long round = it / C::STAGES;
         if (round > 0)
@@ -326,34 +340,35 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
         uint8_t* st = smem + s * C::STAGE;
         const uint32_t full = ptx::smem_u32(&bars[s]);
         ptx::mbar_arrive_expect_tx(full, C::STAGE);
-        const int kx = kc * C::BK;
+        const int kx = kc * C::BK, kxb = kx + kb;
         if (PAIR == 1) {          // own A; half of the shared B tile, to both CTAs
           const int hb = BN / 2;
           ptx::tma_load_2d(ptx::smem_u32(st), mA0, full, kx, m0);   // n0: the pair's common n-tile
-          ptx::tma_load_2d_mc(ptx::smem_u32(st + NPL * C::A_BYTES + rank * hb * C::SW), mB0, full, kx,
+          ptx::tma_load_2d_mc(ptx::smem_u32(st + NPL * C::A_BYTES + rank * hb * C::SW), mB0, full, kxb,
                               n0 + rank * hb, kPairMask);
           if (NPL == 2) {
             ptx::tma_load_2d(ptx::smem_u32(st + C::A_BYTES), mA1, full, kx, m0);
             ptx::tma_load_2d_mc(ptx::smem_u32(st + NPL * C::A_BYTES + C::B_BYTES + rank * hb * C::SW), mB1, full,
-                                kx, n0 + rank * hb, kPairMask);
+                                kxb, n0 + rank * hb, kPairMask);
           }
         } else if (PAIR == 2) {   // half of the shared A tile, to both CTAs; own B
           const int ha = BM / 2;
           ptx::tma_load_2d_mc(ptx::smem_u32(st + rank * ha * C::SW), mA0, full, kx, m0 + rank * ha, kPairMask);
-          ptx::tma_load_2d(ptx::smem_u32(st + NPL * C::A_BYTES), mB0, full, kx, n0);
+          ptx::tma_load_2d(ptx::smem_u32(st + NPL * C::A_BYTES), mB0, full, kxb, n0);
           if (NPL == 2) {
             ptx::tma_load_2d_mc(ptx::smem_u32(st + C::A_BYTES + rank * ha * C::SW), mA1, full, kx, m0 + rank * ha,
                                 kPairMask);
-            ptx::tma_load_2d(ptx::smem_u32(st + NPL * C::A_BYTES + C::B_BYTES), mB1, full, kx, n0);
+            ptx::tma_load_2d(ptx::smem_u32(st + NPL * C::A_BYTES + C::B_BYTES), mB1, full, kxb, n0);
           }
         } else {
           ptx::tma_load_2d(ptx::smem_u32(st), mA0, full, kx, m0);
-          ptx::tma_load_2d(ptx::smem_u32(st + NPL * C::A_BYTES), mB0, full, kx, n0);
+          ptx::tma_load_2d(ptx::smem_u32(st + NPL * C::A_BYTES), mB0, full, kxb, n0);
           if (NPL == 2) {
             ptx::tma_load_2d(ptx::smem_u32(st + C::A_BYTES), mA1, full, kx, m0);
-            ptx::tma_load_2d(ptx::smem_u32(st + NPL * C::A_BYTES + C::B_BYTES), mB1, full, kx, n0);
+            ptx::tma_load_2d(ptx::smem_u32(st + NPL * C::A_BYTES + C::B_BYTES), mB1, full, kxb, n0);
           }
         }
+      }
       }
     }
     // drain: every issued stage's copies have landed before the CTA may exit
@@ -377,15 +392,21 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
       if (!resolve(q, m0, n0, nkq, gq, mq)) continue;
       volatile int* abort_q = MULTI ? reinterpret_cast<volatile int*>(gq->err) : abort_flag;
       last_err = gq->err;
+      const int npass = npass_of(*gq);
+      for (int lv = 0; lv < npass && ok; ++lv) {
+      const int nkp = nk_of(*gq, lv, nkq);
       const int b = tcount & 1, use = tcount >> 1;
       ++tcount;
       if (use > 0)
         ok = ptx::mbar_wait(ptx::smem_u32(&acce[b]), static_cast<uint32_t>((use - 1) & 1), gq->err,
                             ptx::kErrWaitAccum, polls);
-      if (!ok || (abort_q && *abort_q)) break;
+      if (!ok || (abort_q && *abort_q)) {
+        ok = false;
+        break;
+      }
       ptx::tc_fence_after();
       const uint32_t d = tmem + static_cast<uint32_t>(b * BN);
-      for (int kc = 0; kc < nkq; ++kc, ++it) {
+      for (int kc = 0; kc < nkp; ++kc, ++it) {
         const int s = static_cast<int>(it % C::STAGES);
         ok = ptx::mbar_wait(ptx::smem_u32(&bars[s]), static_cast<uint32_t>((it / C::STAGES) & 1), gq->err,
                             ptx::kErrWaitFull, polls);
@@ -412,6 +433,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
         else ptx::mma_commit(ptx::smem_u32(&bars[C::STAGES + s]));                  // in both CTAs
       }
       ptx::mma_commit(ptx::smem_u32(&accf[b]));                 // accumulator b ready
+      }
     }
     // every MMA this thread issued has completed before the tensor memory is
     // freed, also when a timed-out wait ended the loop early
@@ -433,7 +455,8 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
     uint8_t* ostage = smem + C::STAGES * C::STAGE + 1024 + (warp - 2) * (ONPL * CHUNK);
     int chunk_i = 0;
     int tcount = 0;
-    for (long long q = unit0; q < num_units; q += unit_step) {
+    bool go = true;
+    for (long long q = unit0; q < num_units && go; q += unit_step) {
       int m0, n0, nkq;
       const GemmOut* gq;
       const CUtensorMap* mq;
@@ -442,6 +465,9 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
       const CUtensorMap* mO0 = MULTI ? &mq[4] : &tO0;
       const CUtensorMap* mO1 = MULTI ? &mq[5] : &tO1;
       volatile int* abort_q = MULTI ? reinterpret_cast<volatile int*>(gu.err) : abort_flag;
+      const int npass = npass_of(gu);
+      for (int lv = 0; lv < npass; ++lv) {
+      const bool acc_out = gu.accumulate != 0 || lv > 0;   // later levels add to the earlier ones
       const int b = tcount & 1, use = tcount >> 1;
       ++tcount;
       const bool ok = ptx::mbar_wait(ptx::smem_u32(&accf[b]), static_cast<uint32_t>(use & 1), gu.err,
@@ -449,7 +475,10 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
       ptx::tc_fence_after();
       const bool flagged = abort_q && *abort_q;
       // tcgen05.ld is warp-collective: decide for the whole warp
-      if (!__all_sync(0xffffffffu, ok && !flagged)) break;
+      if (!__all_sync(0xffffffffu, ok && !flagged)) {
+        go = false;
+        break;
+      }
       const int m = m0 + quarter * 32 + lane;
       const bool mvalid = m < gu.M;
       const long long mterm =
@@ -496,12 +525,13 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ 
           }
           ++chunk_i;
         } else if (mvalid) {
-          store_chunk<OUT>(gu, mterm, n0 + c0, r);
+          store_chunk<OUT>(gu, mterm, n0 + c0, r, acc_out);
         }
       }
       ptx::tc_fence_before();
       __syncwarp();
       if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&acce[b]));   // buffer b may be refilled
+      }
     }
     if (TMAO && lane == 0) ptx::bulk_wait_all();   // staging buffers stay until the stores are done
   }

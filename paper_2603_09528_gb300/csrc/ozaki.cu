@@ -21,8 +21,11 @@
 // one plain bf16 GEMM over the slices laid side by side along K, the first
 // operand's slices 1..L-1 against the second's L-1..1; the second operand is
 // therefore stored with its slices in reverse order, so that every level reads
-// a prefix of the first operand's row and a suffix of the second's.  The
-// epilogue adds each level into the float64 output.  Levels 2..S+1 are kept
+// a prefix of the first operand's row and a suffix of the second's.  All
+// levels run in one launch of the transform GEMM: each output tile takes the
+// levels in turn (double-buffered accumulators in tensor memory), and the
+// epilogue adds each level into the float64 output while the tile is still in
+// L2, so the output crosses DRAM once.  Levels 2..S+1 are kept
 // (pairs with s + t > S + 1 are below 2^-(beta (S+1)) of the scale); with
 // S = 7 the product is accurate to ~1e-13 of sum_k |a_k||b_k|, and the float64
 // refinement of the solve removes the rest.
@@ -89,9 +92,33 @@ __host__ __device__ inline int row_exponent(double m) {
   return ex == 0 ? 0 : ex - 1022;
 }
 
+// The digits of slice_value for one value given its bits, with each slice
+// d_t 2^(e - beta t) formed as float(d_t) times a power of two built from its
+// bits (the caller checks that 2^(e - beta S) and 2^(e - beta) are normal
+// floats, so the products are the exact values ldexpf gives).  Integer and
+// float32 operations only: GB300's float64 pipe is ~1/64 of the float32 rate.
+__device__ __forceinline__ void slice_value_dev(unsigned long long bits, int e, float* q) {
+  const int ex = static_cast<int>((bits >> 52) & 0x7ff);
+  long long X = 0;
+  if (ex != 0) {
+    const long long mant = static_cast<long long>((bits & ((1ull << 52) - 1)) | (1ull << 52));
+    const int sh = 1075 + e - kOzBeta * kOzS - ex;
+    if (sh <= 0) X = mant << (-sh);
+    else if (sh < 62) X = (mant + (1LL << (sh - 1))) >> sh;
+    if (bits >> 63) X = -X;
+  }
+  for (int t = kOzS; t >= 2; --t) {
+    const long long d = ((X + (1LL << (kOzBeta - 1))) & ((1LL << kOzBeta) - 1)) - (1LL << (kOzBeta - 1));
+    X = (X - d) >> kOzBeta;
+    q[t - 1] = static_cast<float>(static_cast<int>(d)) * __int_as_float((127 + e - kOzBeta * t) << 23);
+  }
+  q[0] = static_cast<float>(static_cast<int>(X)) * __int_as_float((127 + e - kOzBeta) << 23);
+}
+
 // Rows x K float64 (element (r, k) at src[r rs + k]) into kOzS bf16 slices per
 // row at dst[r ld + pos Kp + k], ld = kOzS Kp, pos = t - 1 (reversed: kOzS - t);
-// columns K..Kp-1 are zero.  One warp per row.
+// columns K..Kp-1 are zero.  One warp per row; the row maximum is taken on
+// the bit patterns (for non-negative doubles they order as the values do).
 __global__ void __launch_bounds__(256)
 ozaki_slice_kernel(long long rows, int K, int Kp, long long rs, const double* __restrict__ src,
                    __nv_bfloat16* __restrict__ dst, int reversed) {
@@ -99,17 +126,20 @@ ozaki_slice_kernel(long long rows, int K, int Kp, long long rs, const double* __
   const long long warps = static_cast<long long>(gridDim.x) * (blockDim.x / 32);
   for (long long r = blockIdx.x * static_cast<long long>(blockDim.x / 32) + threadIdx.x / 32; r < rows;
        r += warps) {
-    const double* row = src + r * rs;
-    double m = 0.0;
-    for (int k = lane; k < K; k += 32) m = fmax(m, fabs(row[k]));
+    const unsigned long long* row = reinterpret_cast<const unsigned long long*>(src + r * rs);
+    unsigned long long m = 0;
+    for (int k = lane; k < K; k += 32) m = max(m, row[k] & 0x7fffffffffffffffull);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    const int e = row_exponent(m);
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    const int e = row_exponent(__longlong_as_double(static_cast<long long>(m)));
+    // 2^(e - beta S) .. 2^(e - beta) normal: the fast slices (uniform over the warp)
+    const bool fast = e - kOzBeta * kOzS >= -126 && e - kOzBeta <= 127;
     __nv_bfloat16* out = dst + r * static_cast<long long>(kOzS) * Kp;
     for (int k = lane; k < Kp; k += 32) {
       float q[kOzS];
       if (k < K) {
-        slice_value(row[k], e, q);
+        if (fast) slice_value_dev(row[k], e, q);
+        else slice_value(__longlong_as_double(static_cast<long long>(row[k])), e, q);
       } else {
 #pragma unroll
         for (int t = 0; t < kOzS; ++t) q[t] = 0.0f;
@@ -189,7 +219,7 @@ int ozaki_setup(tpt_plan_s* p) {
   for (int d = 0; d < 2; ++d) {
     if (p->dir[d].excluded() || p->xform[d] != TPT_XFORM_GEMM) continue;
     const int n = p->n[d];
-    const int kp = (n + 7) & ~7;
+    const int kp = (n + 63) & ~63;   // whole 64-element K chunks per slice (zero padded)
     p->oz_kp[d] = kp;
     for (int inv = 0; inv < 2; ++inv) {
       // the float64 DGEMM's matrix (column-major n x n): x transforms use it as
@@ -248,41 +278,43 @@ cudaError_t ozaki_transform(const tpt_plan_s* p, int d, bool inverse, const doub
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  for (int L = 2; L <= kOzS + 1; ++L) {   // level L: slices 1..L-1 against L-1..1
-    const int kl = (L - 1) * kp;
-    tc::Operand a, b;
-    tc::GemmOut g;
-    std::memset(&g, 0, sizeof(g));
-    if (d == 0) {
-      a = tc::Operand{{tab, nullptr}, nx, kl, ld};
-      b = tc::Operand{{sl + static_cast<long long>(kOzS - L + 1) * kp, nullptr}, static_cast<int>(rows), kl, ld};
-      g.M = nx;
-      g.N = static_cast<int>(rows);
-      g.rm = nx;
-      g.sm = 0;
-      g.sn = nx;
-    } else {
-      a = tc::Operand{{sl, nullptr}, static_cast<int>(rows), kl, ld};
-      b = tc::Operand{{tab + static_cast<long long>(kOzS - L + 1) * kp, nullptr}, ny, kl, ld};
-      g.M = static_cast<int>(rows);
-      g.N = ny;
-      g.rm = nx;
-      g.sm = static_cast<long long>(nx) * ny;
-      g.sn = nx;
-    }
-    g.K = kl;
-    g.out0 = out;
-    g.mode = tc::kOutF64;
-    g.accumulate = (accumulate || L > 2) ? 1 : 0;
-    // consecutive CTAs share the data tile: x (data second) walks the few
-    // m-tiles of the matrix fastest, y (data first) the few n-tiles
-    g.n_fastest = d == 0 ? 0 : 1;
-    g.err = err;
-    g.tma_out = 0;
-    e = tc::gemm(tc::kKindBF16, 1, a, b, g, s);
-    if (e != cudaSuccess) return e;
+  // one launch for the seven levels: every output tile takes level L = 2..8
+  // (slices 1..L-1 of A against L-1..1 of B, K = (L - 1) Kp) in turn, the
+  // first written (or added, when accumulating) and the rest added in float64
+  // while the tile is still in L2
+  const int kall = kOzS * kp;
+  tc::Operand a, b;
+  tc::GemmOut g;
+  std::memset(&g, 0, sizeof(g));
+  if (d == 0) {
+    a = tc::Operand{{tab, nullptr}, nx, kall, ld};
+    b = tc::Operand{{sl, nullptr}, static_cast<int>(rows), kall, ld};
+    g.M = nx;
+    g.N = static_cast<int>(rows);
+    g.rm = nx;
+    g.sm = 0;
+    g.sn = nx;
+  } else {
+    a = tc::Operand{{sl, nullptr}, static_cast<int>(rows), kall, ld};
+    b = tc::Operand{{tab, nullptr}, ny, kall, ld};
+    g.M = static_cast<int>(rows);
+    g.N = ny;
+    g.rm = nx;
+    g.sm = static_cast<long long>(nx) * ny;
+    g.sn = nx;
   }
-  return cudaSuccess;
+  g.K = kall;
+  g.out0 = out;
+  g.mode = tc::kOutF64;
+  g.accumulate = accumulate ? 1 : 0;
+  g.levels = kOzS;
+  g.level_k = kp;
+  // consecutive CTAs share the data tile: x (data second) walks the few
+  // m-tiles of the matrix fastest, y (data first) the few n-tiles
+  g.n_fastest = d == 0 ? 0 : 1;
+  g.err = err;
+  g.tma_out = 0;
+  return tc::gemm(tc::kKindBF16, 1, a, b, g, s);
 }
 
 }  // namespace tpt

@@ -46,6 +46,13 @@ struct GemmOut {
   // waits run out and the kernel returns with TPT_ERR_TIMEOUT in *err.
   unsigned polls = 0;
   int drop_loads = 0;
+  // Float64 output only: `levels` > 0 makes every tile a sequence of that
+  // many products accumulated into the output, product l over K = (l + 1) *
+  // level_k with A from K offset 0 and B from K offset (levels - 1 - l) *
+  // level_k (the levels of an Ozaki product, from operands holding all the
+  // slices); level_k a multiple of the 64-element K chunk.
+  int levels = 0;
+  int level_k = 0;
 };
 
 // One GEMM of a grouped launch: its tensor maps (A0, A1, B0, B1, O0, O1; the
