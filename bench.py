@@ -777,8 +777,9 @@ def fft_leg(tpt, n, stream, steps):
     DFT), z stretched 2.0 and solved by Thomas, Helmholtz (1, -5e-4).  Each
     transform is timed alone with CUDA events (seeded uniform[0, 1) input),
     then the whole solve.  Algorithmic work per point and transform: 16 bytes
-    (one float64 read, one write) and 5 log2(N) + 6 float64 flops (radix-2
-    complex FFT of length N plus the pre/post rotation)."""
+    (one float64 read, one write) and 2.5 log2(N) + 6 float64 flops (one radix-2
+    complex FFT of length N for two real lines, plus the pre/post rotation and
+    the separation of the two lines' spectra)."""
     import torch
     out = {}
     npts = n[0] * n[1] * n[2]
@@ -795,7 +796,7 @@ def fft_leg(tpt, n, stream, steps):
         rec = {}
         for d in (0, 1):
             N = n[d]
-            flops = npts * (5.0 * np.log2(N) + 6.0)
+            flops = npts * (2.5 * np.log2(N) + 6.0)
             for inv in (False, True):
                 for _ in range(2):
                     plan.transform(f, d, inv, out=y, stream=stream)

@@ -12,8 +12,8 @@
 // Mode p of the forward output is an eigenvector of the 1D operator with the
 // plan's eigenvalue lam[p]; mode 0 is the constant (null) mode.  N is a power
 // of two.  A block transforms `tl` lines held as complex arrays in shared
-// memory: iterative radix-2 butterflies on bit-reversed input, one barrier per
-// stage.  Line l of the field starts at (l % L1) * s1 + (l / L1) * s2 and has
+// memory, two real lines per complex array (as its real and imaginary parts):
+// iterative radix-2 butterflies on bit-reversed input, one barrier per stage.  Line l of the field starts at (l % L1) * s1 + (l / L1) * s2 and has
 // element stride es; lines with es > 1 are loaded across consecutive lines so
 // that global accesses stay coalesced in both the x and the y direction.
 #include <cuda_runtime.h>
@@ -33,9 +33,14 @@ fft_lines_kernel(int N, int logN, long long nlines, int tl, long long L1, long l
                  long long es, const R* __restrict__ in, R* __restrict__ out, int accumulate,
                  const R* __restrict__ twc, const R* __restrict__ tws, const R* __restrict__ hc,
                  const R* __restrict__ hs) {
+  // tl lines (even) in tl / 2 complex slots: lines 2c and 2c + 1 of the block
+  // are the real and imaginary parts of slot c, so one complex FFT of length N
+  // transforms two real lines (forward), or two Hermitian spectra whose
+  // transforms are real (inverse)
   extern __shared__ unsigned char smem_raw[];
+  const int ts = tl / 2;
   R* re = reinterpret_cast<R*>(smem_raw);
-  R* im = re + static_cast<size_t>(tl) * N;
+  R* im = re + static_cast<size_t>(ts) * N;
   const long long l0 = static_cast<long long>(blockIdx.x) * tl;
   const int total = tl * N;
   const bool contiguous = (es == 1);
@@ -45,57 +50,71 @@ fft_lines_kernel(int N, int logN, long long nlines, int tl, long long L1, long l
     t = contiguous ? e % N : e / tl;
   };
 
-  // ---- load, pre-process, place at bit-reversed positions
-  for (int e = threadIdx.x; e < total; e += blockDim.x) {
-    int line, t;
-    coords(e, line, t);
-    const long long l = l0 + line;
-    const bool ok = l < nlines;
-    const long long b = ok ? base_of(l) : 0;
-    R fr = R(0), fi = R(0);
-    int pos = t;
-    if (!INV) {
-      const R x = ok ? in[b + t * es] : R(0);
-      fr = x;
+  if (!INV) {
+    // ---- load real lines, place at bit-reversed positions of their part
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+      int line, t;
+      coords(e, line, t);
+      const long long l = l0 + line;
+      const R x = l < nlines ? in[base_of(l) + t * es] : R(0);
+      int pos = t;
       if (KIND == 1) pos = (t % 2 == 0) ? t / 2 : N - 1 - t / 2;   // v_n = x_2n, v_{N-1-n} = x_{2n+1}
-    } else if (ok) {
-      const int k = t;
-      if (KIND == 0) {
-        // F_0 = c_0, F_{N/2} = c_{N-1}, F_k = c_{2k-1} - i c_{2k}, F_{N-k} = conj(F_k)
-        if (k == 0) {
-          fr = in[b];
-        } else if (2 * k == N) {
-          fr = in[b + (N - 1) * es];
-        } else if (2 * k < N) {
-          fr = in[b + (2 * k - 1) * es];
-          fi = -in[b + (2 * k) * es];
-        } else {
-          const int kk = N - k;
-          fr = in[b + (2 * kk - 1) * es];
-          fi = in[b + (2 * kk) * es];
-        }
-      } else {
-        // V_k = e^{i pi k / 2N} (X_k - i X_{N-k}), X_N = 0
-        const R xr = in[b + k * es];
-        const R xi = (k == 0) ? R(0) : -in[b + (N - k) * es];
-        fr = hc[k] * xr - hs[k] * xi;
-        fi = hc[k] * xi + hs[k] * xr;
-      }
+      (line % 2 == 0 ? re : im)[static_cast<size_t>(line / 2) * N + bitrev(pos, logN)] = x;
     }
-    re[static_cast<size_t>(line) * N + bitrev(pos, logN)] = fr;
-    im[static_cast<size_t>(line) * N + bitrev(pos, logN)] = fi;
+  } else {
+    // ---- load both spectra of a slot, combine Z = V_a + i V_b
+    const int tot2 = ts * N;
+    for (int e = threadIdx.x; e < tot2; e += blockDim.x) {
+      const int c = contiguous ? e / N : e % ts;
+      const int k = contiguous ? e % N : e / ts;
+      R vr[2], vi[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const long long l = l0 + 2 * c + h;
+        R fr = R(0), fi = R(0);
+        if (l < nlines) {
+          const long long b = base_of(l);
+          if (KIND == 0) {
+            // F_0 = c_0, F_{N/2} = c_{N-1}, F_k = c_{2k-1} - i c_{2k}, F_{N-k} = conj(F_k)
+            if (k == 0) {
+              fr = in[b];
+            } else if (2 * k == N) {
+              fr = in[b + (N - 1) * es];
+            } else if (2 * k < N) {
+              fr = in[b + (2 * k - 1) * es];
+              fi = -in[b + (2 * k) * es];
+            } else {
+              const int kk = N - k;
+              fr = in[b + (2 * kk - 1) * es];
+              fi = in[b + (2 * kk) * es];
+            }
+          } else {
+            // V_k = e^{i pi k / 2N} (X_k - i X_{N-k}), X_N = 0
+            const R xr = in[b + k * es];
+            const R xi = (k == 0) ? R(0) : -in[b + (N - k) * es];
+            fr = hc[k] * xr - hs[k] * xi;
+            fi = hc[k] * xi + hs[k] * xr;
+          }
+        }
+        vr[h] = fr;
+        vi[h] = fi;
+      }
+      const size_t o = static_cast<size_t>(c) * N + bitrev(k, logN);
+      re[o] = vr[0] - vi[1];
+      im[o] = vi[0] + vr[1];
+    }
   }
   __syncthreads();
 
   // ---- radix-2 butterflies; forward uses e^{-2 pi i m / N}, inverse e^{+...}
   const int half = N / 2;
-  for (int s = 0; s < logN; ++s) {
-    const int h = 1 << s;
+  for (int st = 0; st < logN; ++st) {
+    const int h = 1 << st;
     const int tstep = N / (2 * h);
-    for (int bfly = threadIdx.x; bfly < tl * half; bfly += blockDim.x) {
-      const int line = bfly / half, j = bfly % half;
-      const int grp = j >> s, pos = j & (h - 1);
-      const int i0 = line * N + grp * 2 * h + pos, i1 = i0 + h;
+    for (int bfly = threadIdx.x; bfly < ts * half; bfly += blockDim.x) {
+      const int slot = bfly / half, j = bfly % half;
+      const int grp = j >> st, pos = j & (h - 1);
+      const int i0 = slot * N + grp * 2 * h + pos, i1 = i0 + h;
       const R c = twc[pos * tstep], sn = tws[pos * tstep];
       const R vr = re[i1], vi = im[i1];
       const R tr = INV ? c * vr - sn * vi : c * vr + sn * vi;
@@ -116,21 +135,45 @@ fft_lines_kernel(int N, int logN, long long nlines, int tl, long long L1, long l
     coords(e, line, t);
     const long long l = l0 + line;
     if (l >= nlines) continue;
-    const R* lr = re + static_cast<size_t>(line) * N;
-    const R* li = im + static_cast<size_t>(line) * N;
+    const R* zr = re + static_cast<size_t>(line / 2) * N;
+    const R* zi = im + static_cast<size_t>(line / 2) * N;
+    const int part = line % 2;
     R val;
     if (!INV) {
+      // the transform of this line: (Z_k + conj Z_{N-k}) / 2, or (Z_k - conj Z_{N-k}) / 2i
+      auto spec = [&](int k, R& xr, R& xi) {
+        const int kn = (N - k) & (N - 1);
+        if (part == 0) {
+          xr = R(0.5) * (zr[k] + zr[kn]);
+          xi = R(0.5) * (zi[k] - zi[kn]);
+        } else {
+          xr = R(0.5) * (zi[k] + zi[kn]);
+          xi = R(0.5) * (zr[kn] - zr[k]);
+        }
+      };
+      R xr, xi;
       if (KIND == 0) {
-        if (t == 0) val = lr[0];
-        else if (t == N - 1) val = lr[N / 2];
-        else if (t % 2 == 1) val = lr[(t + 1) / 2];
-        else val = -li[t / 2];
+        if (t == 0) {
+          spec(0, xr, xi);
+          val = xr;
+        } else if (t == N - 1) {
+          spec(N / 2, xr, xi);
+          val = xr;
+        } else if (t % 2 == 1) {
+          spec((t + 1) / 2, xr, xi);
+          val = xr;
+        } else {
+          spec(t / 2, xr, xi);
+          val = -xi;
+        }
       } else {
-        val = lr[t] * hc[t] + li[t] * hs[t];   // Re(e^{-i pi t / 2N} V_t)
+        spec(t, xr, xi);
+        val = xr * hc[t] + xi * hs[t];   // Re(e^{-i pi t / 2N} V_t)
       }
     } else {
-      if (KIND == 0) val = lr[t] * invN;
-      else val = lr[(t % 2 == 0) ? t / 2 : N - 1 - t / 2] * invN;
+      const R* z = part == 0 ? zr : zi;   // the real transform of this line
+      if (KIND == 0) val = z[t] * invN;
+      else val = z[(t % 2 == 0) ? t / 2 : N - 1 - t / 2] * invN;
     }
     const long long o = base_of(l) + t * es;
     out[o] = accumulate ? out[o] + val : val;
@@ -143,9 +186,9 @@ cudaError_t launch_fft(int kind, bool inverse, int N, long long nlines, long lon
                        const R* tws, const R* hc, const R* hs, cudaStream_t s) {
   int logN = 0;
   while ((1 << logN) < N) ++logN;
-  int tl = 4096 / N;
-  tl = tl < 1 ? 1 : (tl > 32 ? 32 : tl);
-  const size_t smem = 2 * static_cast<size_t>(tl) * N * sizeof(R);
+  int tl = 8192 / N;                       // lines per block, two per complex slot
+  tl = tl < 2 ? 2 : (tl > 64 ? 64 : tl);
+  const size_t smem = 2 * static_cast<size_t>(tl / 2) * N * sizeof(R);
   const long long blocks = (nlines + tl - 1) / tl;
   if (blocks <= 0) return cudaSuccess;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
