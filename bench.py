@@ -879,6 +879,18 @@ def projection_leg(tpt, plan, n, stream, steps):
             "bytes_outside_solve_per_point": 32 + 56}
 
 
+# The float-pair residual of the singular headline problem is bound by the
+# float32 datapath (ncu: FMA pipe 67 % busy, math-pipe throttle the largest
+# stall), not by HBM.  Its float32 operations per point, counted from the
+# kernel's arithmetic: five exact face differences (8 each: TwoSum and the lo
+# parts), six exact coefficient products with their TwoSum accumulation (12
+# each), the compatibility shift of f (8), the final hi + lo (1) and the r^2
+# sum (1).  Peak: 152 SMs x 128 float32 lanes x 2.070 GHz (unit counts and
+# the maximum SM clock), one operation per lane and clock.
+RESIDUAL_F32_OPS = 5 * 8 + 6 * 12 + 8 + 1 + 1
+F32_LANE_TOPS = 152 * 128 * 2.070e9 / 1e12
+
+
 def stage_rooflines(ms, iters, n, prec):
     """Per-stage achieved rates from the solve's own CUDA-event stage timings.
     Algorithmic work per point and launch: transforms 2*N_alpha flop per
@@ -922,6 +934,13 @@ def stage_rooflines(ms, iters, n, prec):
         d.update({"kernel": nm, "ms_per_launch": per_launch, "launches_per_solve": iters,
                   "bytes_per_launch": byts, "traffic": None})
         d["frac"] = d["achieved"] / d["peak"]
+        if nm == "residual":
+            # the unit that bounds it: the float32 datapath (see RESIDUAL_F32_OPS)
+            ops = RESIDUAL_F32_OPS * npts
+            achieved = ops / (per_launch / 1e3) / 1e12
+            d["alu"] = {"bound": "alu", "ops_per_point": RESIDUAL_F32_OPS, "achieved": achieved,
+                        "peak": F32_LANE_TOPS, "unit": "Tops/s (float32 lane operations)",
+                        "frac": achieved / F32_LANE_TOPS}
         out.append(d)
     fmt = {1: "mixed_bf16", 2: "mixed_bf16x3", 3: "mixed_tf32"}[prec]
     for d in out:
