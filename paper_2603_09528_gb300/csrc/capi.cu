@@ -696,7 +696,7 @@ int tpt_residual(tpt_plan p, const double* f, const double* phi, double* r, doub
   DeviceGuard guard(p->dev);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // the single-step residual uses f as given (no compatibility shift)
-  return cuda_status(tpt::residual_fp64(p, f, phi, r, sums, nullptr, s));
+  return cuda_status(tpt::residual_fp64(p, f, phi, r, sums, nullptr, s, true));
 }
 
 int tpt_tc_gemm(int precision, int M, int N, int K, const double* A, const double* B, double* D,

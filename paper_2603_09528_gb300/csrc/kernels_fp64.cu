@@ -180,7 +180,14 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // r = (f - fshift) - (alpha phi + beta (Lx + Ly + Lz) phi); one thread per
 // (i, j) marching along k.  End couplings of non-periodic directions are zero,
-// so wrapped neighbour indices only ever meet a zero coefficient.
+// so wrapped neighbour indices only ever meet a zero coefficient.  The
+// beta-scaled rows are formed once (x and y per thread, z per block in shared
+// memory when ROWS, with alpha folded into the z diagonal), so that a point
+// costs six FMAs for the neighbours, one for the diagonal and one subtraction
+// on GB300's float64 pipe (~1/64 of the float32 rate, the bound of this
+// kernel).  sums[0] += sum r^2; with ALL also sums[1] += sum r and sums[2] +=
+// sum vol*r.
+template <bool ROWS, bool ALL>
 __global__ void __launch_bounds__(128)
 residual_fp64_kernel(int nx, int ny, int nz, const double* __restrict__ f,
                      const double* __restrict__ phi, double* __restrict__ r,
@@ -189,44 +196,67 @@ residual_fp64_kernel(int nx, int ny, int nz, const double* __restrict__ f,
                      const double* __restrict__ dyf, const double* __restrict__ dzf,
                      double alpha, double beta, const double* __restrict__ fshift_p,
                      double* sums) {
+  extern __shared__ double zrow[];   // beta a_k, beta b_k + alpha, beta c_k (ROWS)
+  if (ROWS) {
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y, nt = blockDim.x * blockDim.y;
+    for (int k = tid; k < nz; k += nt) {
+      zrow[k] = beta * rz[k];
+      zrow[nz + k] = fma(beta, rz[nz + k], alpha);
+      zrow[2 * nz + k] = beta * rz[2 * nz + k];
+    }
+    __syncthreads();
+  }
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   double s2 = 0.0, s1 = 0.0, sv = 0.0;
   if (i < nx && j < ny) {
-    const long long sx = 1, sy = nx, sz = static_cast<long long>(nx) * ny;
+    const long long sy = nx, sz = static_cast<long long>(nx) * ny;
     const long long base = i + sy * j;
     const int im = (i == 0) ? nx - 1 : i - 1, ip = (i == nx - 1) ? 0 : i + 1;
     const int jm = (j == 0) ? ny - 1 : j - 1, jp = (j == ny - 1) ? 0 : j + 1;
-    const double ax = rx[i], bx = rx[nx + i], cx = rx[2 * nx + i];
-    const double ay = ry[j], by = ry[ny + j], cy = ry[2 * ny + j];
+    const double ax = beta * rx[i], cx = beta * rx[2 * nx + i];
+    const double ay = beta * ry[j], cy = beta * ry[2 * ny + j];
+    const double bxy = beta * (rx[nx + i] + ry[ny + j]);
     const double fshift = fshift_p ? *fshift_p : 0.0;
-    const double vxy = dxf[i] * dyf[j];
-    (void)sx;
+    const double vxy = ALL ? dxf[i] * dyf[j] : 0.0;
     double pm = phi[base + sz * (nz - 1)];   // wrap partner, multiplied by a_0 = 0
     double p0 = phi[base];
     for (int k = 0; k < nz; ++k) {
       const long long o = base + sz * k;
       const double pp = phi[base + sz * ((k == nz - 1) ? 0 : k + 1)];
-      const double lx = fma(ax, phi[im + sy * j + sz * k], fma(cx, phi[ip + sy * j + sz * k], bx * p0));
-      const double ly = fma(ay, phi[i + sy * jm + sz * k], fma(cy, phi[i + sy * jp + sz * k], by * p0));
-      const double lz = fma(rz[k], pm, fma(rz[2 * nz + k], pp, rz[nz + k] * p0));
-      const double val = (f[o] - fshift) - fma(alpha, p0, beta * ((lx + ly) + lz));
+      const double az = ROWS ? zrow[k] : beta * rz[k];
+      const double bz = ROWS ? zrow[nz + k] : fma(beta, rz[nz + k], alpha);
+      const double cz = ROWS ? zrow[2 * nz + k] : beta * rz[2 * nz + k];
+      double acc = ax * phi[im + sy * j + sz * k];
+      acc = fma(cx, phi[ip + sy * j + sz * k], acc);
+      acc = fma(ay, phi[i + sy * jm + sz * k], acc);
+      acc = fma(cy, phi[i + sy * jp + sz * k], acc);
+      acc = fma(az, pm, acc);
+      acc = fma(cz, pp, acc);
+      acc = fma(bxy + bz, p0, acc);
+      const double val = (fshift_p ? f[o] - fshift : f[o]) - acc;
       r[o] = val;
       s2 = fma(val, val, s2);
-      s1 += val;
-      sv = fma(vxy * dzf[k], val, sv);
+      if (ALL) {
+        s1 += val;
+        sv = fma(vxy * dzf[k], val, sv);
+      }
       pm = p0;
       p0 = pp;
     }
   }
   if (sums) {
     s2 = warp_sum(s2);
-    s1 = warp_sum(s1);
-    sv = warp_sum(sv);
+    if (ALL) {
+      s1 = warp_sum(s1);
+      sv = warp_sum(sv);
+    }
     if ((threadIdx.x + blockDim.x * threadIdx.y) % 32 == 0) {
       atomicAdd(&sums[0], s2);
-      atomicAdd(&sums[1], s1);
-      atomicAdd(&sums[2], sv);
+      if (ALL) {
+        atomicAdd(&sums[1], s1);
+        atomicAdd(&sums[2], sv);
+      }
     }
   }
 }
@@ -428,14 +458,18 @@ cudaError_t thomas_fp64(const tpt_plan_s* p, const double* fhat, double* phihat,
 }
 
 cudaError_t residual_fp64(const tpt_plan_s* p, const double* f, const double* phi, double* r,
-                          double* sums, const double* fshift, cudaStream_t s) {
+                          double* sums, const double* fshift, cudaStream_t s, bool all_sums) {
   const int nx = p->n[0], ny = p->n[1], nz = p->n[2];
   dim3 block(32, 4);
   dim3 grid((nx + 31) / 32, (ny + 3) / 4);
+  const size_t rows_bytes = 3 * static_cast<size_t>(nz) * sizeof(double);
+  const bool rows = rows_bytes <= 48 * 1024;   // within the default dynamic limit
+  auto kern = rows ? (all_sums ? residual_fp64_kernel<true, true> : residual_fp64_kernel<true, false>)
+                   : (all_sums ? residual_fp64_kernel<false, true> : residual_fp64_kernel<false, false>);
   note_launch();
-  residual_fp64_kernel<<<grid, block, 0, s>>>(nx, ny, nz, f, phi, r, p->d_rows[0], p->d_rows[1],
-                                              p->d_rows[2], p->d_dxf[0], p->d_dxf[1], p->d_dxf[2],
-                                              p->alpha, p->beta, fshift, sums);
+  kern<<<grid, block, rows ? rows_bytes : 0, s>>>(nx, ny, nz, f, phi, r, p->d_rows[0], p->d_rows[1], p->d_rows[2],
+                                                 p->d_dxf[0], p->d_dxf[1], p->d_dxf[2], p->alpha, p->beta,
+                                                 fshift, sums);
   return cudaGetLastError();
 }
 

@@ -232,8 +232,10 @@ cudaError_t remove_weighted_mean(const tpt_plan_s* p, double* phi, void* scratch
                                  double* mean, cudaStream_t s);
 
 // r = (f - fshift) - (alpha I + beta L) phi; fshift (device scalar) may be NULL.
+// sums (may be NULL): [0] += sum r^2, and with all_sums [1] += sum r, [2] +=
+// sum vol*r.
 cudaError_t residual_fp64(const tpt_plan_s* p, const double* f, const double* phi, double* r,
-                          double* sums, const double* fshift, cudaStream_t s);
+                          double* sums, const double* fshift, cudaStream_t s, bool all_sums = false);
 
 // mixed-precision path (mixed.cu)
 int mixed_setup(tpt_plan_s* p);
