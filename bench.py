@@ -992,6 +992,9 @@ def e2e_server(tpt, device, spec, f_pin, steps, warmup, phi_ref, slots=3):
     gaps = [1e3 * (b - a) for a, b in zip(done, done[1:])]
     return {"seconds": seconds, "slots": slots, "requests": steps,
             "completion_gap_ms": {"median": float(np.median(gaps)), "max": float(max(gaps))} if gaps else None,
+            # one completion per median gap once the slots are busy (the timed
+            # region above also holds the pipeline fill of the first requests)
+            "steady_state_solves_per_s": 1e3 / float(np.median(gaps)) if gaps else None,
             "max_rel_residual": max(r["rel_residual"] for r in res),
             "max_rel_diff_vs_device_solve": diff,
             "timeline_ms": {k: [round((r[key] - t0s) * 1e3, 2) for r in res]
