@@ -70,8 +70,11 @@ enum { TPT_BC_PERIODIC = 0, TPT_BC_NEUMANN = 1, TPT_BC_DIRICHLET = 2, TPT_BC_DIR
 /* Transform of a diagonalised direction (x or y), Sec. 3: numerical eigenbasis
  * applied as a GEMM, or the Fourier-based transform of a uniform direction
  * (real DFT for periodic, DCT-II/III for Neumann-Neumann; Makhoul's
- * reordering, footnote to Sec. 4.2).  FFT needs a float64 plan, uniform
- * spacing and a power-of-two size; AUTO picks it when it applies.          */
+ * reordering, footnote to Sec. 4.2).  FFT needs uniform spacing and a
+ * power-of-two size (16 or more points on a mixed-precision plan, whose
+ * corrections then transform that direction in float32 instead of on the
+ * tensor cores).  AUTO picks it where it applies on float64 and Ozaki plans
+ * and keeps the GEMM on mixed-precision plans.                             */
 enum { TPT_XFORM_AUTO = 0, TPT_XFORM_GEMM = 1, TPT_XFORM_FFT = 2 };
 
 /* Arithmetic of the transforms and the Thomas sweep.  FP64: float64

@@ -263,11 +263,13 @@ int create_plan_impl(const tpt_desc* desc, int cuda_device, tpt::BasisCache* cac
   if (p->dir[2].periodic || p->dir[2].excluded()) return fail(TPT_ERR_UNSUPPORTED);
   if ((p->dir[0].excluded() || p->dir[1].excluded()) && desc->alpha == 0.0) return fail(TPT_ERR_INVALID_ARG);
   for (int d = 0; d < 2; ++d) {
-    // Fourier-based transforms: float64 path, uniform power-of-two directions
-    const bool ok = tpt::fft_supported(p->dir[d]) &&
-                    (desc->precision == TPT_PREC_FP64 || desc->precision == TPT_PREC_FP64_OZAKI);
+    // Fourier-based transforms of uniform power-of-two directions: float64
+    // kernels on the float64 and Ozaki paths, float32 kernels inside the
+    // mixed-precision corrections (from 16 points up)
+    const bool fp64 = desc->precision == TPT_PREC_FP64 || desc->precision == TPT_PREC_FP64_OZAKI;
+    const bool ok = tpt::fft_supported(p->dir[d]) && (fp64 || p->dir[d].n >= 16);
     if (desc->xform[d] == TPT_XFORM_FFT && !ok) return fail(TPT_ERR_UNSUPPORTED);
-    p->xform[d] = (desc->xform[d] == TPT_XFORM_FFT || (desc->xform[d] == TPT_XFORM_AUTO && ok))
+    p->xform[d] = (desc->xform[d] == TPT_XFORM_FFT || (desc->xform[d] == TPT_XFORM_AUTO && ok && fp64))
                       ? TPT_XFORM_FFT
                       : TPT_XFORM_GEMM;
   }

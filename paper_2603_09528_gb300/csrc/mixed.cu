@@ -2631,12 +2631,78 @@ StageGemm stage_gemm(const tpt_plan_s* p, const MixedWork& w, int i, bool accumu
   return t;
 }
 
+// Direction transformed by stage i (x forward, y forward, y inverse, x inverse).
+int stage_dir(int i) { return (i == 0 || i == 3) ? 0 : 1; }
+
+// Stage i as a float32 Fourier-based transform of a uniform direction: the
+// same operands and layouts as stage_gemm's, the direction just transformed
+// written as the slow index (x forward, y inverse) or in place of the rows.
+FftMixedArgs stage_fft(const tpt_plan_s* p, const MixedWork& w, int i, bool accumulate) {
+  const MixedTables& m = p->mixed;
+  const long long nx = p->n[0], ny = p->n[1], nz = p->n[2];
+  const int d = stage_dir(i);
+  FftMixedArgs a;
+  a.kind = m.fft_kind[d];
+  a.inverse = i >= 2;
+  a.N = p->n[d];
+  a.in_fmt = m.fmt;
+  for (int k = 0; k < 4; ++k) a.tw[k] = m.fft_tw[d][k];
+  a.stop = w.skip;
+  const int om = out_mode(m.fmt);
+  switch (i) {
+    case 0:   // R rows (j,k) -> T1 (j, p, k) in A: j fastest, row stride ldy
+      a.nlines = ny * nz;
+      a.in0 = w.R[0];
+      a.in1 = w.R[1];
+      a.ldi = m.ldx;
+      a.out0 = w.A[0];
+      a.out1 = w.A[1];
+      a.out_mode = om;
+      a.ldo = m.ldy;
+      a.L1 = ny;
+      break;
+    case 1:   // T1 rows (p,k) -> T2 rows (p,k), float32 in B
+      a.nlines = nx * nz;
+      a.in0 = w.A[0];
+      a.in1 = w.A[1];
+      a.ldi = m.ldy;
+      a.out0 = w.B[0];
+      a.out_mode = tc::kOutF32;
+      a.ldo = m.ldy;
+      break;
+    case 2:   // T3 rows (p,k) in A -> T4 (p, j, k) in B: p fastest, row stride ldx
+      a.nlines = nx * nz;
+      a.in0 = w.A[0];
+      a.in1 = w.A[1];
+      a.ldi = m.ldy;
+      a.out0 = w.B[0];
+      a.out1 = w.B[1];
+      a.out_mode = om;
+      a.ldo = m.ldx;
+      a.L1 = nx;
+      break;
+    default:  // T4 rows (j,k) in B -> phi (float pair) (+)= result
+      a.nlines = ny * nz;
+      a.in0 = w.B[0];
+      a.in1 = w.B[1];
+      a.ldi = m.ldx;
+      a.out0 = w.ph;
+      a.out1 = w.pl;
+      a.out_mode = tc::kOutDF;
+      a.ldo = nx;
+      a.accumulate = accumulate ? 1 : 0;
+      break;
+  }
+  return a;
+}
+
 template <int FMT>
 int correction(tpt_plan_s* p, const MixedWork& w, bool accumulate, cudaStream_t s) {
   auto mark = [&](int i) {
     if (p->stage_timing) cudaEventRecord(p->ev[i], s);
   };
   auto xform = [&](int i) {
+    if (p->xform[stage_dir(i)] == TPT_XFORM_FFT) return fft_mixed(stage_fft(p, w, i, accumulate), s);
     const StageGemm t = stage_gemm(p, w, i, accumulate);
     tc::GemmOut g = tuned(t.g, p->mixed, i);
     g.skip = w.skip;
@@ -3118,12 +3184,48 @@ int mixed_pack_basis(DevArena& a, int fmt, const Eigen1D& e, const std::vector<d
   return TPT_OK;
 }
 
+// Tables of a Fourier-transformed direction d of a mixed plan: eigenvalues in
+// the transform's mode order and the float32 twiddles (rounded from long
+// double), in the plan's arena.
+int fft_tables_f32(tpt_plan_s* p, int d) {
+  MixedTables& m = p->mixed;
+  const int n = p->n[d];
+  const long double pi = 3.141592653589793238462643383279502884L;
+  std::vector<float> t[4];
+  t[0].assign(n / 2 > 0 ? n / 2 : 1, 1.0f);
+  t[1].assign(t[0].size(), 0.0f);
+  t[2].resize(n);
+  t[3].resize(n);
+  for (int k = 0; k < n / 2; ++k) {
+    t[0][k] = static_cast<float>(std::cos(2.0L * pi * k / n));
+    t[1][k] = static_cast<float>(std::sin(2.0L * pi * k / n));
+  }
+  for (int k = 0; k < n; ++k) {
+    t[2][k] = static_cast<float>(std::cos(pi * k / (2.0L * n)));
+    t[3][k] = static_cast<float>(std::sin(pi * k / (2.0L * n)));
+  }
+  for (int k = 0; k < 4; ++k) {
+    float* dptr = nullptr;
+    MX_TRY(upload_vec(p, t[k], &dptr));
+    m.fft_tw[d][k] = dptr;
+  }
+  std::vector<float> lf(p->eig[d].lam.begin(), p->eig[d].lam.end());
+  MX_TRY(upload_vec(p, lf, &m.lam_f[d]));
+  m.fft_kind[d] = p->fft[d].kind;
+  MX_CUDA(cudaStreamSynchronize(p->arena.stream));   // the host vectors die here
+  return TPT_OK;
+}
+
 int mixed_setup(tpt_plan_s* p) {
   MixedTables& m = p->mixed;
   m.fmt = fmt_of(p->precision);
   m.ldx = (p->n[0] + 7) & ~7;
   m.ldy = (p->n[1] + 7) & ~7;
   for (int d = 0; d < 2; ++d) {
+    if (p->xform[d] == TPT_XFORM_FFT) {   // no operand matrices: float32 twiddles
+      MX_TRY(fft_tables_f32(p, d));
+      continue;
+    }
     void* q[2][2] = {};
     if (p->basis[d]) MX_TRY(entry_mixed_tables(*p->basis[d], m.fmt, p->dev, q, &m.lam_f[d]));
     else MX_TRY(mixed_pack_basis(p->arena, m.fmt, p->eig[d], p->dir[d].dxf, p->dev, q, &m.lam_f[d]));
@@ -3345,7 +3447,8 @@ bool thomas_job_any(int m, const tpt_plan_s* p, const MixedWork& w, int first, T
 
 bool group_eligible(const tpt_plan_s* p) {
   return p->dev >= 0 && p->precision == TPT_PREC_MIXED_BF16X3 && p->mixed.fmt == kFmtSplit && p->rtol > 0.0 &&
-         p->n[0] % 4 == 0 && thomas2_m(p->n[2]) != 0;
+         p->n[0] % 4 == 0 && thomas2_m(p->n[2]) != 0 && p->xform[0] == TPT_XFORM_GEMM &&
+         p->xform[1] == TPT_XFORM_GEMM;
 }
 
 GroupSolve* group_create(tpt_plan_s* const* plans, int n) {
@@ -3665,6 +3768,7 @@ int autotune_gemms(tpt_plan_s* p, void* work, cudaStream_t s) {
   const int kind = kind_of(m.fmt), npl = nplanes(m.fmt);
   constexpr int kReps = 3, kRounds = 3;
   for (int i = 0; i < 4 && status == TPT_OK; ++i) {
+    if (p->xform[stage_dir(i)] == TPT_XFORM_FFT) continue;   // no GEMM to tune
     const StageGemm t = stage_gemm(p, w, i, false);
     const int top = tc::default_bn(t.g.N);
     // the operand common to neighbouring tiles: the transform matrix, which

@@ -96,6 +96,10 @@ struct MixedTables {
   int gemm_pair[4] = {0, 0, 0, 0};
   int res_kernel = 0;               // residual: 0 automatic, 1 direct loads, 2 TMA-staged tiles
   int thomas_kernel = 0;            // modal Thomas: 0 automatic, 1 one line per thread, 2 two lines
+  // Fourier-transformed directions (x, y): float32 tables cos, sin of
+  // 2 pi m / N and cos, sin of pi k / 2N, and the transform kind
+  const float* fft_tw[2][4] = {};
+  int fft_kind[2] = {0, 0};
 };
 
 struct FftTables {    // device tables of a Fourier-transformed direction
@@ -215,6 +219,34 @@ cudaError_t dgemm_cm(int M, int N, int K, const double* A, int lda, long long sA
 // the natural layout (fft.cu); out (+)= result.
 cudaError_t fft_fp64(const tpt_plan_s* p, int d, bool inverse, const double* in, double* out,
                      bool accumulate, cudaStream_t s);
+
+// Float32 Fourier-based transform of a uniform direction inside a mixed-
+// precision correction (fft.cu): nlines contiguous input rows (line l at
+// in + l * ldi, operand format in_fmt: split bf16 planes in0/in1, bf16 in0,
+// or float32 in0), written in tc output mode out_mode as contiguous rows
+// (L1 == 0: line l at l * ldo) or transposed (L1 > 0: element t of line
+// a + L1 * b at b * ldo * N + t * ldo + a); kOutDF updates the float pair
+// (out0, out1) when accumulate is set and overwrites it otherwise.  tw: the
+// float32 tables cos, sin of 2 pi m / N (m < N/2) and cos, sin of pi k / 2N
+// (k < N).  Kernels return at entry when *stop (device, may be NULL) is set.
+struct FftMixedArgs {
+  int kind = 0;                 // 0 real DFT, 1 DCT-II / DCT-III
+  bool inverse = false;
+  int N = 0;
+  long long nlines = 0;
+  const void* in0 = nullptr;
+  const void* in1 = nullptr;
+  int in_fmt = kFmtSplit;
+  long long ldi = 0;
+  void* out0 = nullptr;
+  void* out1 = nullptr;
+  int out_mode = 0;
+  long long ldo = 0, L1 = 0;
+  int accumulate = 0;
+  const float* tw[4] = {nullptr, nullptr, nullptr, nullptr};
+  const int* stop = nullptr;
+};
+cudaError_t fft_mixed(const FftMixedArgs& a, cudaStream_t s);
 
 cudaError_t thomas_fp64(const tpt_plan_s* p, const double* fhat, double* phihat, double* scratch,
                         double* defect, cudaStream_t s);

@@ -166,13 +166,26 @@ def test_transform_selection_rules():
     assert L.lib.tpt_plan_create(C.byref(d), -1, C.byref(h)) == L.TPT_OK
     assert _xforms(h) == (L.TPT_XFORM_GEMM, L.TPT_XFORM_GEMM)   # 24 not a power of two; Dirichlet y
     L.lib.tpt_plan_destroy(h)
-    # explicit FFT where it does not apply, or on a mixed-precision plan
+    # explicit FFT where it does not apply
     d, keep = _desc((32, 32, 8), [st_grid, un, O.tanh_grid(8, 1.0, 1.0)], [(1, 1), (1, 1), (1, 1)],
                     xform=(L.TPT_XFORM_FFT, L.TPT_XFORM_GEMM))
     assert L.lib.tpt_plan_create(C.byref(d), -1, C.byref(h)) == L.TPT_ERR_UNSUPPORTED
-    d, keep = _desc((32, 32, 8), [un, un, O.tanh_grid(8, 1.0, 1.0)], [(1, 1), (1, 1), (1, 1)],
-                    prec=L.TPT_PREC_MIXED_BF16X3, xform=(L.TPT_XFORM_FFT, L.TPT_XFORM_GEMM))
-    assert L.lib.tpt_plan_create(C.byref(d), -1, C.byref(h)) == L.TPT_ERR_UNSUPPORTED
+    # mixed-precision plans: explicit FFT from 16 points (float32 transforms in
+    # the corrections), AUTO keeps the GEMM, fewer than 16 points are refused
+    for prec in (L.TPT_PREC_MIXED_BF16X3, L.TPT_PREC_MIXED_BF16, L.TPT_PREC_MIXED_TF32):
+        d, keep = _desc((32, 16, 8), [un, O.uniform_grid(16), O.tanh_grid(8, 1.0, 1.0)], [(0, 0), (1, 1), (1, 1)],
+                        prec=prec, xform=(L.TPT_XFORM_FFT, L.TPT_XFORM_FFT))
+        assert L.lib.tpt_plan_create(C.byref(d), -1, C.byref(h)) == L.TPT_OK
+        assert _xforms(h) == (L.TPT_XFORM_FFT, L.TPT_XFORM_FFT)
+        L.lib.tpt_plan_destroy(h)
+        d, keep = _desc((32, 16, 8), [un, O.uniform_grid(16), O.tanh_grid(8, 1.0, 1.0)], [(0, 0), (1, 1), (1, 1)],
+                        prec=prec, xform=(L.TPT_XFORM_AUTO, L.TPT_XFORM_AUTO))
+        assert L.lib.tpt_plan_create(C.byref(d), -1, C.byref(h)) == L.TPT_OK
+        assert _xforms(h) == (L.TPT_XFORM_GEMM, L.TPT_XFORM_GEMM)
+        L.lib.tpt_plan_destroy(h)
+        d, keep = _desc((32, 8, 8), [un, O.uniform_grid(8), O.tanh_grid(8, 1.0, 1.0)], [(1, 1), (1, 1), (1, 1)],
+                        prec=prec, xform=(L.TPT_XFORM_GEMM, L.TPT_XFORM_FFT))
+        assert L.lib.tpt_plan_create(C.byref(d), -1, C.byref(h)) == L.TPT_ERR_UNSUPPORTED
 
 
 def test_tile_setters_and_batch_argument_checks():
