@@ -824,11 +824,71 @@ def fft_leg(tpt, n, stream, steps):
         torch.cuda.synchronize()
         rec["solve"] = {"ms": e0.elapsed_time(e1) / reps, "iters": info["iters"],
                         "rel_residual": info["rel_residual"]}
+        rec["mixed"] = fft_mixed_leg(tpt, n, grids, bc, f, stream, steps)
         out[kind] = rec
         del plan, f, y, phi, work
         torch.cuda.empty_cache()
     out["workload"] = "helmholtz_%dx%dx%d_uniform_xy_tanh2.0_z_fp64_fft" % tuple(n)
     return out
+
+
+def fft_mixed_leg(tpt, n, grids, bc, f, stream, steps):
+    """The same Helmholtz problem solved by the split-bf16 refined path (rtol
+    1e-10) with float32 FFT/DCT transforms in x and y, and with the tensor-core
+    eigenbasis GEMMs for comparison: solve time and, from the stage timing
+    pass, each Fourier stage's time per launch against the HBM peak.
+    Algorithmic bytes per point: 8 for x forward (split-bf16 rows in and out),
+    y forward (split bf16 in, float32 out) and y inverse; x inverse 4 in plus
+    the float-pair phi (8 written in the first correction, 16 read and written
+    in the later ones)."""
+    import torch
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    npts = n[0] * n[1] * n[2]
+    res = {}
+    for name, xf in (("fft", (tpt.FFT, tpt.FFT)), ("gemm", (tpt.GEMM, tpt.GEMM))):
+        plan = tpt.Plan(n, [g[0] for g in grids], [g[1] for g in grids], [bc, bc, (1, 1)], xform=xf,
+                        alpha=1.0, beta=-5e-4, precision=PRECISIONS["mixed_bf16x3"], rtol=1e-10, max_refine=8)
+        phi, work = plan.new_field(), plan.new_workspace()
+        if name == "gemm":
+            plan.autotune(work, stream=stream)
+        for _ in range(3):
+            plan.solve(f, phi, work, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = max(3, steps)
+        e0.record(stream)
+        for _ in range(reps):
+            _, info = plan.solve(f, phi, work, stream=stream, want_info=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        plan.set_stage_timing(True)
+        ti = [plan.solve(f, phi, work, stream=stream, want_info=True)[1] for _ in range(2)]
+        plan.set_stage_timing(False)
+        st = np.mean([t["ms_stage"] for t in ti], axis=0)
+        its = float(np.mean([t["iters"] for t in ti]))
+        r = {"ms": ms, "solves_per_s": 1e3 / ms, "iters": info["iters"], "rel_residual": info["rel_residual"]}
+        if name == "fft":
+            stages = {}
+            xinv_bytes = 4.0 + (8.0 + 16.0 * (its - 1.0)) / its
+            for key, i, bpp in (("x_forward", 1, 8.0), ("y_forward", 2, 8.0), ("y_inverse", 4, 8.0),
+                                ("x_inverse", 5, xinv_bytes)):
+                per = float(st[i]) / its
+                gbs = bpp * npts / (per / 1e3) / 1e9
+                stages[key] = {"ms_per_launch": per, "bytes_per_point": bpp, "achieved_gbs": gbs,
+                               "frac_of_hbm": gbs / hbm}
+            r["stages"] = stages
+        res[name] = r
+        del plan, phi, work
+        torch.cuda.empty_cache()
+    res["precision"] = "mixed_bf16x3, float32 FFT/DCT in x and y (gemm: tensor-core eigenbasis GEMMs)"
+    return res
 
 
 def projection_leg(tpt, plan, n, stream, steps):

@@ -71,7 +71,7 @@ enum { TPT_BC_PERIODIC = 0, TPT_BC_NEUMANN = 1, TPT_BC_DIRICHLET = 2, TPT_BC_DIR
  * applied as a GEMM, or the Fourier-based transform of a uniform direction
  * (real DFT for periodic, DCT-II/III for Neumann-Neumann; Makhoul's
  * reordering, footnote to Sec. 4.2).  FFT needs uniform spacing and a
- * power-of-two size (16 or more points on a mixed-precision plan, whose
+ * power-of-two size (16 to 4096 points on a mixed-precision plan, whose
  * corrections then transform that direction in float32 instead of on the
  * tensor cores).  AUTO picks it where it applies on float64 and Ozaki plans
  * and keeps the GEMM on mixed-precision plans.                             */

@@ -265,9 +265,9 @@ int create_plan_impl(const tpt_desc* desc, int cuda_device, tpt::BasisCache* cac
   for (int d = 0; d < 2; ++d) {
     // Fourier-based transforms of uniform power-of-two directions: float64
     // kernels on the float64 and Ozaki paths, float32 kernels inside the
-    // mixed-precision corrections (from 16 points up)
+    // mixed-precision corrections (16 to 4096 points)
     const bool fp64 = desc->precision == TPT_PREC_FP64 || desc->precision == TPT_PREC_FP64_OZAKI;
-    const bool ok = tpt::fft_supported(p->dir[d]) && (fp64 || p->dir[d].n >= 16);
+    const bool ok = tpt::fft_supported(p->dir[d]) && (fp64 || (p->dir[d].n >= 16 && p->dir[d].n <= 4096));
     if (desc->xform[d] == TPT_XFORM_FFT && !ok) return fail(TPT_ERR_UNSUPPORTED);
     p->xform[d] = (desc->xform[d] == TPT_XFORM_FFT || (desc->xform[d] == TPT_XFORM_AUTO && ok && fp64))
                       ? TPT_XFORM_FFT

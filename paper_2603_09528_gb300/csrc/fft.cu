@@ -413,8 +413,12 @@ __device__ __forceinline__ void df_update(float& h, float& l, float v, bool acc)
 
 // Byte offset of the output line bases in a mixed kernel's shared memory:
 // behind the two slot arrays and the twiddles, 16-byte aligned.
+// Elements of each padded twiddle table (cos, sin of 2 pi m / N, m < N/2).
+__host__ __device__ __forceinline__ int tw_stride(int N) { return N / 2 + N / 64 + 1; }
+
 __host__ __device__ __forceinline__ size_t mixed_obase_off(int ts, int N) {
-  const size_t b = (2 * static_cast<size_t>(ts) * slot_stride<float>(N) + static_cast<size_t>(N)) * sizeof(float);
+  const size_t b = (2 * static_cast<size_t>(ts) * slot_stride<float>(N) + 2 * static_cast<size_t>(tw_stride(N))) *
+                   sizeof(float);
   return (b + 15) & ~static_cast<size_t>(15);
 }
 
@@ -430,52 +434,68 @@ struct MixedFftArgs {
   const int* stop;
 };
 
-// R consecutive radix-2 DIT stages st0 .. st0 + R - 1 (span h = 2^s, forward
+// R consecutive radix-2 DIT stages ST0 .. ST0 + R - 1 (span h = 2^s, forward
 // twiddle e^{-2 pi i pos / 2h}, inverse e^{+...}) of every slot, in
-// registers: the 2^R elements base + m 2^st0 (m < 2^R; base = hi 2^(st0+R)
-// + lo, lo < 2^st0) are closed under these stages, so a thread loads them
+// registers: the 2^R elements base + m 2^ST0 (m < 2^R; base = hi 2^(ST0+R)
+// + lo, lo < 2^ST0) are closed under these stages, so a thread loads them
 // once, applies the 2^(R-1) R butterflies in stage order and stores them
-// back.  Each butterfly is the same operation as in a stage-by-stage
-// sweep, so results do not depend on the grouping.
-template <int R, bool INV>
+// back.  Each butterfly is the same operation as in a stage-by-stage sweep
+// (a unit twiddle, which the first pass has for pos = 0, is applied as the
+// exact product it is), so results do not depend on the grouping.  ST0 is a
+// template parameter so that the padded shared-memory offsets of the 2^R
+// elements are fixed offsets from the first (ST0 = 0: consecutive elements
+// of one 32-element row; ST0 >= 5: whole rows apart).
+template <int R, int ST0, bool INV>
 __device__ __forceinline__ void fft_pass(float* re, float* im, const float* stc, const float* sts, int ts, int N,
-                                         int logN, int st0, int S) {
+                                         int logN, int S) {
   constexpr int G = 1 << R;
+  static_assert(ST0 == 0 || ST0 == 3 || ST0 >= 5, "pass origins");
   const int per_slot = N >> R;
   const int items = ts * per_slot;
+  // padded offset of element m relative to element 0 (ST0 == 3: 8 m plus one
+  // padding element per four m, the row of element 0 starting at a multiple
+  // of 64 plus lo < 8)
+  auto moff = [](int m) {
+    return ST0 == 0 ? m : (ST0 == 3 ? 8 * m + m / 4 : m * ((1 << ST0) + (1 << ST0) / 32));
+  };
   for (int it = threadIdx.x; it < items; it += blockDim.x) {
     const int slot = it >> (logN - R), w = it & (per_slot - 1);
-    const int lo = w & ((1 << st0) - 1), hi = w >> st0;
-    const int base = (hi << (st0 + R)) + lo;
+    const int lo = w & ((1 << ST0) - 1), hi = w >> ST0;
+    const int base = (hi << (ST0 + R)) + lo;
+    const int o0 = slot * S + base + base / 32;
     float xr[G], xi[G];
 #pragma unroll
     for (int m = 0; m < G; ++m) {
-      const int i = base + (m << st0);
-      const int o = slot * S + i + i / 32;
-      xr[m] = re[o];
-      xi[m] = im[o];
+      xr[m] = re[o0 + moff(m)];
+      xi[m] = im[o0 + moff(m)];
     }
 #pragma unroll
     for (int q = 0; q < R; ++q) {
       const int hq = 1 << q;
-      const int tsh = logN - 1 - (st0 + q);   // twiddle index pos * N / 2h
+      const int tsh = logN - 1 - (ST0 + q);   // twiddle index pos * N / 2h
       float cw[G / 2], sw[G / 2];
 #pragma unroll
       for (int j = 0; j < G / 2; ++j) {
         if (j < hq) {
-          const int tw = ((j << st0) + lo) << tsh;
-          cw[j] = stc[tw];
-          sw[j] = sts[tw];
+          const int tw = ((j << ST0) + lo) << tsh;
+          cw[j] = stc[tw + tw / 32];   // padded like the slots (see fft_mixed_kernel)
+          sw[j] = sts[tw + tw / 32];
         }
       }
 #pragma unroll
       for (int m = 0; m < G; ++m) {
         if (m & hq) continue;
         const int j = m & (hq - 1);
-        const float c = cw[j], sn = sw[j];
         const float vr = xr[m + hq], vi = xi[m + hq];
-        const float tr = INV ? c * vr - sn * vi : c * vr + sn * vi;
-        const float ti = INV ? c * vi + sn * vr : c * vi - sn * vr;
+        float tr, ti;
+        if (ST0 == 0 && j == 0) {   // pos = 0: the twiddle is 1
+          tr = vr;
+          ti = vi;
+        } else {
+          const float c = cw[j], sn = sw[j];
+          tr = INV ? c * vr - sn * vi : c * vr + sn * vi;
+          ti = INV ? c * vi + sn * vr : c * vi - sn * vr;
+        }
         const float ur = xr[m], ui = xi[m];
         xr[m] = ur + tr;
         xi[m] = ui + ti;
@@ -485,12 +505,29 @@ __device__ __forceinline__ void fft_pass(float* re, float* im, const float* stc,
     }
 #pragma unroll
     for (int m = 0; m < G; ++m) {
-      const int i = base + (m << st0);
-      const int o = slot * S + i + i / 32;
-      re[o] = xr[m];
-      im[o] = xi[m];
+      re[o0 + moff(m)] = xr[m];
+      im[o0 + moff(m)] = xi[m];
     }
   }
+}
+
+// Passes of three stages from stage 0, the last one shorter (logN <= 12).
+template <bool INV>
+__device__ __forceinline__ void fft_passes(float* re, float* im, const float* stc, const float* sts, int ts, int N,
+                                           int logN, int S) {
+#define TPT_PASS(ST0)                                                                                    \
+  if (logN > ST0) {                                                                                      \
+    const int r = logN - ST0;                                                                            \
+    if (r >= 3) fft_pass<3, ST0, INV>(re, im, stc, sts, ts, N, logN, S);                                 \
+    else if (r == 2) fft_pass<2, ST0, INV>(re, im, stc, sts, ts, N, logN, S);                            \
+    else fft_pass<1, ST0, INV>(re, im, stc, sts, ts, N, logN, S);                                        \
+    __syncthreads();                                                                                     \
+  }
+  TPT_PASS(0)
+  TPT_PASS(3)
+  TPT_PASS(6)
+  TPT_PASS(9)
+#undef TPT_PASS
 }
 
 template <int KIND, int STAGE, int FMT>
@@ -506,187 +543,252 @@ fft_mixed_kernel(const MixedFftArgs A, const float* __restrict__ twc, const floa
   constexpr int P = 32;
   const int S = slot_stride<float>(N);
   auto at = [&](int c, int i) { return c * S + i + i / P; };
-  // shared memory: re | im (ts slots of S) | twiddles (N/2 + N/2) | output
-  // line bases (64) | staged input rows (inverse: tl rows of N + 4)
+  // shared memory: re | im (ts slots of S) | two padded twiddle tables |
+  // output line bases (64) | staged input rows (inverse: tl rows of N + 4)
   float* re = reinterpret_cast<float*>(smem_raw);
   float* im = re + static_cast<size_t>(ts) * S;
   float* stc = im + static_cast<size_t>(ts) * S;
-  float* sts = stc + N / 2;
+  float* sts = stc + tw_stride(N);
   long long* obase = reinterpret_cast<long long*>(smem_raw + mixed_obase_off(ts, N));
   const int SL = N + 4;
   float* stg = reinterpret_cast<float*>(obase + 64);
   const long long l0 = static_cast<long long>(blockIdx.x) * tl;
   for (int m = threadIdx.x; m < N / 2; m += blockDim.x) {
-    stc[m] = twc[m];
-    sts[m] = tws[m];
+    // one padding element per 32: the passes read twiddles at strides of
+    // 4 to 32 elements across a warp
+    stc[m + m / 32] = twc[m];
+    sts[m + m / 32] = tws[m];
   }
   for (int line = threadIdx.x; line < tl; line += blockDim.x) {
     const long long l = l0 + line < A.nlines ? l0 + line : 0;
     obase[line] = TRANS ? (l / A.L1) * A.ldo * N + (l % A.L1) : l * A.ldo;
   }
 
+  // Thread mappings below keep what depends on a thread's position along the
+  // line (t, k) in registers and walk the lines or slots: a slot is shared
+  // by kper = min(N, 256) consecutive threads (by N / V of them when rows are
+  // read V at a time), so each thread serves a fixed set of positions.
+
   // ---- input: rows read V elements at a time
   const int npv = N / V;
-  const int lg_npv = logN - (V == 8 ? 3 : 2);
-  const int groups = tl * npv;
-  constexpr int U = 4;
-  for (int g0 = threadIdx.x; g0 < groups; g0 += U * blockDim.x) {
-    float v[U][V];
+  if (npv <= 256) {
+    const int t0 = (threadIdx.x % npv) * V;
+    const int lstep = 256 / npv;
+    int off[V];   // forward: padded bit-reversed position of each element in its slot
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int g = g0 + u * blockDim.x;
-      const int line = g >> lg_npv, t0 = (g & (npv - 1)) * V;
-      const long long l = l0 + line;
-      if (g < groups && l < A.nlines) {
-        InVec<FMT>::load(A.in0, A.in1, l * A.ldi + t0, v[u]);
-      } else {
+    for (int q = 0; q < V; ++q) {
+      const int t = t0 + q;
+      const int pos = KIND == 1 ? ((t % 2 == 0) ? t / 2 : N - 1 - t / 2) : t;   // v_n = x_2n, v_{N-1-n} = x_{2n+1}
+      const int br = bitrev(pos, logN);
+      off[q] = br + br / P;
+    }
+    constexpr int U = 4;
+    for (int line0 = threadIdx.x / npv; line0 < tl; line0 += U * lstep) {
+      float v[U][V];
 #pragma unroll
-        for (int q = 0; q < V; ++q) v[u][q] = 0.0f;
+      for (int u = 0; u < U; ++u) {
+        const int line = line0 + u * lstep;
+        const long long l = l0 + line;
+        if (line < tl && l < A.nlines) {
+          InVec<FMT>::load(A.in0, A.in1, l * A.ldi + t0, v[u]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < V; ++q) v[u][q] = 0.0f;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int line = line0 + u * lstep;
+        if (line >= tl) break;
+        if (!INV) {
+          float* part = ((line & 1) ? im : re) + (line >> 1) * S;
+#pragma unroll
+          for (int q = 0; q < V; ++q) part[off[q]] = v[u][q];
+        } else {
+          float* row = stg + static_cast<size_t>(line) * SL + t0;
+#pragma unroll
+          for (int q = 0; q < V; q += 4)
+            *reinterpret_cast<float4*>(row + q) = make_float4(v[u][q], v[u][q + 1], v[u][q + 2], v[u][q + 3]);
+        }
       }
     }
+  } else {   // lines longer than 256 vectors: one vector at a time
+    for (int g = threadIdx.x; g < tl * npv; g += blockDim.x) {
+      const int line = g / npv, t0 = (g % npv) * V;
+      const long long l = l0 + line;
+      float v[V];
+      if (l < A.nlines) {
+        InVec<FMT>::load(A.in0, A.in1, l * A.ldi + t0, v);
+      } else {
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int g = g0 + u * blockDim.x;
-      if (g >= groups) break;
-      const int line = g >> lg_npv, t0 = (g & (npv - 1)) * V;
+        for (int q = 0; q < V; ++q) v[q] = 0.0f;
+      }
       if (!INV) {
-        // forward: bit-reversed position of the (reordered) element in its part
         float* part = (line & 1) ? im : re;
 #pragma unroll
         for (int q = 0; q < V; ++q) {
           const int t = t0 + q;
-          const int pos = KIND == 1 ? ((t % 2 == 0) ? t / 2 : N - 1 - t / 2) : t;   // v_n = x_2n, v_{N-1-n} = x_{2n+1}
-          part[at(line >> 1, bitrev(pos, logN))] = v[u][q];
+          const int pos = KIND == 1 ? ((t % 2 == 0) ? t / 2 : N - 1 - t / 2) : t;
+          part[at(line >> 1, bitrev(pos, logN))] = v[q];
         }
       } else {
         float* row = stg + static_cast<size_t>(line) * SL + t0;
 #pragma unroll
-        for (int q = 0; q < V; q += 4) *reinterpret_cast<float4*>(row + q) = make_float4(v[u][q], v[u][q + 1], v[u][q + 2], v[u][q + 3]);
+        for (int q = 0; q < V; q += 4)
+          *reinterpret_cast<float4*>(row + q) = make_float4(v[q], v[q + 1], v[q + 2], v[q + 3]);
       }
     }
   }
   __syncthreads();
+  const int kper = N < 256 ? N : 256;
+  const int c0 = threadIdx.x / kper, cstep = 256 / kper;
   if (INV) {
     // ---- both spectra of a slot, combined Z = V_a + i V_b at bit-reversed k
-    for (int e = threadIdx.x; e < ts * N; e += blockDim.x) {
-      const int c = e >> logN, k = e & (N - 1);
-      float vr[2], vi[2];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const float* x = stg + static_cast<size_t>(2 * c + h) * SL;
-        float fr, fi = 0.0f;
-        if (KIND == 0) {
-          // F_0 = c_0, F_{N/2} = c_{N-1}, F_k = c_{2k-1} - i c_{2k}, F_{N-k} = conj(F_k)
-          if (k == 0) {
-            fr = x[0];
-          } else if (2 * k == N) {
-            fr = x[N - 1];
-          } else if (2 * k < N) {
-            fr = x[2 * k - 1];
-            fi = -x[2 * k];
-          } else {
-            fr = x[2 * (N - k) - 1];
-            fi = x[2 * (N - k)];
-          }
-        } else {
-          // V_k = e^{i pi k / 2N} (X_k - i X_{N-k}), X_N = 0
-          const float xr = x[k];
-          const float xi = (k == 0) ? 0.0f : -x[N - k];
-          fr = hc[k] * xr - hs[k] * xi;
-          fi = hc[k] * xi + hs[k] * xr;
-        }
-        vr[h] = fr;
-        vi[h] = fi;
+    for (int k = threadIdx.x % kper; k < N; k += kper) {
+      const int o = bitrev(k, logN);
+      const int ob = o + o / P;
+      // where the spectrum at k comes from: DFT F_0 = c_0, F_{N/2} = c_{N-1},
+      // F_k = c_{2k-1} - i c_{2k}, F_{N-k} = conj(F_k); DCT V_k = e^{i pi k / 2N}
+      // (X_k - i X_{N-k}), X_N = 0
+      int ir, ii;
+      float sr = 1.0f, si = 0.0f, c = 1.0f, sn = 0.0f;
+      if (KIND == 0) {
+        const int kk = 2 * k <= N ? k : N - k;
+        ir = kk == 0 ? 0 : (2 * kk == N ? N - 1 : 2 * kk - 1);
+        ii = (kk == 0 || 2 * kk == N) ? -1 : 2 * kk;
+        si = 2 * k < N ? -1.0f : 1.0f;
+      } else {
+        ir = k;
+        ii = k == 0 ? -1 : N - k;
+        si = -1.0f;
+        c = hc[k];
+        sn = hs[k];
       }
-      const int o = at(c, bitrev(k, logN));
-      re[o] = vr[0] - vi[1];
-      im[o] = vi[0] + vr[1];
+      for (int cc = c0; cc < ts; cc += cstep) {
+        float vr[2], vi[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const float* x = stg + static_cast<size_t>(2 * cc + h) * SL;
+          const float xr = sr * x[ir];
+          const float xi = ii >= 0 ? si * x[ii] : 0.0f;
+          if (KIND == 0) {
+            vr[h] = xr;
+            vi[h] = xi;
+          } else {
+            vr[h] = c * xr - sn * xi;
+            vi[h] = c * xi + sn * xr;
+          }
+        }
+        re[cc * S + ob] = vr[0] - vi[1];
+        im[cc * S + ob] = vi[0] + vr[1];
+      }
     }
     __syncthreads();
   }
 
-  // ---- radix-2 stages, three at a time in registers (fft_pass)
-  for (int st0 = 0; st0 < logN; st0 += 3) {
-    const int r = logN - st0;
-    if (r >= 3) fft_pass<3, INV>(re, im, stc, sts, ts, N, logN, st0, S);
-    else if (r == 2) fft_pass<2, INV>(re, im, stc, sts, ts, N, logN, st0, S);
-    else fft_pass<1, INV>(re, im, stc, sts, ts, N, logN, st0, S);
-    __syncthreads();
-  }
+  // ---- radix-2 stages, three at a time in registers
+  fft_passes<INV>(re, im, stc, sts, ts, N, logN, S);
 
   // ---- output: both lines of a slot per thread
   auto pd = [&](int i) { return i + i / P; };
-  if (!INV) {
-    // slot-fastest for transposed outputs (neighbouring lines of a row block),
-    // t-fastest for contiguous rows
-    for (int e = threadIdx.x; e < ts * N; e += blockDim.x) {
-      const int c = TRANS ? e & (ts - 1) : e >> logN;
-      const int t = TRANS ? e >> A.lg_ts : e & (N - 1);
-      const long long la = l0 + 2 * c;
-      if (la >= A.nlines) continue;
+  if (TRANS) {
+    // slot-fastest (neighbouring lines of a row block next to each other)
+    const int c = threadIdx.x & (ts - 1);
+    const long long la = l0 + 2 * c;
+    if (la < A.nlines) {
       const bool has_b = la + 1 < A.nlines;
-      const float* zr = re + static_cast<size_t>(c) * S;
-      const float* zi = im + static_cast<size_t>(c) * S;
+      const long long oa0 = obase[2 * c], ob0 = obase[2 * c + 1];
+      const float* zr = re + c * S;
+      const float* zi = im + c * S;
+      const float invN = 1.0f / static_cast<float>(N);
+      for (int t = threadIdx.x >> A.lg_ts; t < N; t += 256 >> A.lg_ts) {
+        float va, vb;
+        if (!INV) {
+          int k;
+          if (KIND == 0) k = (t == 0) ? 0 : (t == N - 1 ? N / 2 : (t + 1) / 2);
+          else k = t;
+          const int kn = (N - k) & (N - 1);
+          const float zrk = zr[pd(k)], zrn = zr[pd(kn)], zik = zi[pd(k)], zin = zi[pd(kn)];
+          // spectra of the two lines: (Z_k + conj Z_{N-k}) / 2 and (Z_k - conj Z_{N-k}) / 2i
+          const float ar = 0.5f * (zrk + zrn), ai = 0.5f * (zik - zin);
+          const float br = 0.5f * (zik + zin), bi = 0.5f * (zrn - zrk);
+          if (KIND == 0) {
+            const bool imag = t != 0 && t != N - 1 && t % 2 == 0;
+            va = imag ? -ai : ar;
+            vb = imag ? -bi : br;
+          } else {
+            va = ar * hc[t] + ai * hs[t];   // Re(e^{-i pi t / 2N} V_t)
+            vb = br * hc[t] + bi * hs[t];
+          }
+        } else {
+          const int o = pd(KIND == 0 ? t : ((t % 2 == 0) ? t / 2 : N - 1 - t / 2));
+          va = zr[o] * invN;
+          vb = zi[o] * invN;
+        }
+        const long long tt = static_cast<long long>(t) * A.ldo;
+        store_two<FMT>(A.out0, A.out1, oa0 + tt, ob0 + tt, has_b, va, vb);
+      }
+    }
+  } else if (!INV) {
+    // float32 rows: fixed positions t per thread, the slots in turn
+    float* q = static_cast<float*>(A.out0);
+    for (int t = threadIdx.x % kper; t < N; t += kper) {
       int k;
       if (KIND == 0) k = (t == 0) ? 0 : (t == N - 1 ? N / 2 : (t + 1) / 2);
       else k = t;
-      const int kn = (N - k) & (N - 1);
-      const float zrk = zr[pd(k)], zrn = zr[pd(kn)], zik = zi[pd(k)], zin = zi[pd(kn)];
-      // spectra of the two lines: (Z_k + conj Z_{N-k}) / 2 and (Z_k - conj Z_{N-k}) / 2i
-      const float ar = 0.5f * (zrk + zrn), ai = 0.5f * (zik - zin);
-      const float br = 0.5f * (zik + zin), bi = 0.5f * (zrn - zrk);
-      float va, vb;
-      if (KIND == 0) {
-        const bool imag = t != 0 && t != N - 1 && t % 2 == 0;
-        va = imag ? -ai : ar;
-        vb = imag ? -bi : br;
-      } else {
-        va = ar * hc[t] + ai * hs[t];   // Re(e^{-i pi t / 2N} V_t)
-        vb = br * hc[t] + bi * hs[t];
-      }
-      const long long oa = obase[2 * c] + (TRANS ? static_cast<long long>(t) * A.ldo : t);
-      const long long ob = obase[2 * c + 1] + (TRANS ? static_cast<long long>(t) * A.ldo : t);
-      if (TRANS) {
-        store_two<FMT>(A.out0, A.out1, oa, ob, has_b, va, vb);
-      } else {
-        float* q = static_cast<float*>(A.out0);
-        q[oa] = va;
-        if (has_b) q[ob] = vb;
+      const int pk = pd(k), pkn = pd((N - k) & (N - 1));
+      const bool imag = KIND == 0 && t != 0 && t != N - 1 && t % 2 == 0;
+      const float hct = KIND == 1 ? hc[t] : 0.0f, hst = KIND == 1 ? hs[t] : 0.0f;
+      for (int c = c0; c < ts; c += cstep) {
+        const long long la = l0 + 2 * c;
+        if (la >= A.nlines) break;
+        const float* zr = re + c * S;
+        const float* zi = im + c * S;
+        const float zrk = zr[pk], zrn = zr[pkn], zik = zi[pk], zin = zi[pkn];
+        const float ar = 0.5f * (zrk + zrn), ai = 0.5f * (zik - zin);
+        const float br = 0.5f * (zik + zin), bi = 0.5f * (zrn - zrk);
+        float va, vb;
+        if (KIND == 0) {
+          va = imag ? -ai : ar;
+          vb = imag ? -bi : br;
+        } else {
+          va = ar * hct + ai * hst;
+          vb = br * hct + bi * hst;
+        }
+        q[obase[2 * c] + t] = va;
+        if (la + 1 < A.nlines) q[obase[2 * c + 1] + t] = vb;
       }
     }
   } else {
+    // the float-pair phi update: four consecutive points of both lines, fixed
+    // positions per thread, the slots in turn
+    float* ph = static_cast<float*>(A.out0);
+    float* pl = static_cast<float*>(A.out1);
+    const bool acc = A.accumulate != 0;
     const float invN = 1.0f / static_cast<float>(N);
-    auto src = [&](int t) { return KIND == 0 ? t : ((t % 2 == 0) ? t / 2 : N - 1 - t / 2); };
-    if (TRANS) {
-      for (int e = threadIdx.x; e < ts * N; e += blockDim.x) {
-        const int c = e & (ts - 1), t = e >> A.lg_ts;
-        const long long la = l0 + 2 * c;
-        if (la >= A.nlines) continue;
-        const int o = at(c, src(t));
-        const long long oa = obase[2 * c] + static_cast<long long>(t) * A.ldo;
-        const long long ob = obase[2 * c + 1] + static_cast<long long>(t) * A.ldo;
-        store_two<FMT>(A.out0, A.out1, oa, ob, la + 1 < A.nlines, re[o] * invN, im[o] * invN);
+    const int gper = N / 4 < 256 ? N / 4 : 256;
+    const int g0 = threadIdx.x / gper, gstep = 256 / gper;
+    for (int t0 = (threadIdx.x % gper) * 4; t0 < N; t0 += 4 * gper) {
+      int so[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int t = t0 + q;
+        so[q] = pd(KIND == 0 ? t : ((t % 2 == 0) ? t / 2 : N - 1 - t / 2));
       }
-    } else {
-      // the float-pair phi update, four consecutive points of both lines
-      float* ph = static_cast<float*>(A.out0);
-      float* pl = static_cast<float*>(A.out1);
-      const bool acc = A.accumulate != 0;
-      for (int e = threadIdx.x; e < ts * (N / 4); e += blockDim.x) {
-        const int c = e >> (logN - 2), t0 = (e & (N / 4 - 1)) * 4;
+      for (int c = g0; c < ts; c += gstep) {
         const long long la = l0 + 2 * c;
-        if (la >= A.nlines) continue;
+        if (la >= A.nlines) break;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           if (h == 1 && la + 1 >= A.nlines) break;
-          const float* z = h == 0 ? re : im;
+          const float* z = (h == 0 ? re : im) + c * S;
           const long long o = obase[2 * c + h] + t0;
           float4 H = acc ? *reinterpret_cast<const float4*>(ph + o) : make_float4(0.f, 0.f, 0.f, 0.f);
           float4 L = acc ? *reinterpret_cast<const float4*>(pl + o) : make_float4(0.f, 0.f, 0.f, 0.f);
-          df_update(H.x, L.x, z[at(c, src(t0))] * invN, acc);
-          df_update(H.y, L.y, z[at(c, src(t0 + 1))] * invN, acc);
-          df_update(H.z, L.z, z[at(c, src(t0 + 2))] * invN, acc);
-          df_update(H.w, L.w, z[at(c, src(t0 + 3))] * invN, acc);
+          df_update(H.x, L.x, z[so[0]] * invN, acc);
+          df_update(H.y, L.y, z[so[1]] * invN, acc);
+          df_update(H.z, L.z, z[so[2]] * invN, acc);
+          df_update(H.w, L.w, z[so[3]] * invN, acc);
           *reinterpret_cast<float4*>(ph + o) = H;
           *reinterpret_cast<float4*>(pl + o) = L;
         }
@@ -772,7 +874,8 @@ cudaError_t fft_fp64(const tpt_plan_s* p, int d, bool inverse, const double* in,
 cudaError_t fft_mixed(const FftMixedArgs& a, cudaStream_t s) {
   // 16-byte row accesses: N >= 16, row strides of whole 16-byte units
   const int eb = a.in_fmt == kFmtF32 ? 4 : 2;
-  if (a.N < 16 || (a.N & (a.N - 1)) != 0 || a.nlines < 0 || (a.ldi * eb) % 16 != 0) return cudaErrorInvalidValue;
+  if (a.N < 16 || a.N > 4096 || (a.N & (a.N - 1)) != 0 || a.nlines < 0 || (a.ldi * eb) % 16 != 0)
+    return cudaErrorInvalidValue;
   if (a.L1 == 0 && a.inverse && a.ldo % 4 != 0) return cudaErrorInvalidValue;
   switch (a.in_fmt) {
     case kFmtSplit: return launch_mixed_fmt<kFmtSplit>(a, s);
