@@ -465,7 +465,7 @@ def run_ours(args):
 
     fft = None
     if not args.no_fft:
-        fft = fft_leg(tpt, n, stream, args.steps)
+        fft = fft_leg(tpt, tuple(args.fft_shape) if args.fft_shape else n, stream, args.steps)
 
     batch = None
     if not args.no_batch:
@@ -1110,6 +1110,8 @@ def main():
     ap.add_argument("--cpu-slabs", type=int, default=128)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fft", action="store_true", help="skip the float64 FFT/DCT-transform leg")
+    ap.add_argument("--fft-shape", type=int, nargs=3, default=None, metavar=("NX", "NY", "NZ"),
+                    help="grid of the FFT/DCT leg (power-of-two NX, NY; default: the headline grid)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched uneven-instances leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the open-loop serving leg")
