@@ -125,3 +125,20 @@ def test_mixed_fft_manufactured_solution_and_graph_replay():
     err = float(np.abs(outs[0] - u).max() / np.abs(u).max())
     assert err <= 1e-10, err
     assert np.array_equal(outs[1], outs[2])
+
+
+@pytest.mark.parametrize("n,prec", [((16, 32, 7), "bf16x3"), ((2048, 16, 6), "tf32"), ((4096, 16, 5), "bf16x3")])
+def test_mixed_fft_shortest_and_longest_lines(n, prec):
+    # 16 points: 64 lines per block, the last pass one stage; 2048 points in
+    # float32 operands and 4096 in bf16 pairs: rows read in more than 256
+    # vectors (the one-vector-at-a-time path), a block of two or four lines
+    bcs = [(N_, N_), (P_, P_), (N_, N_)]
+    dirs = O.make_dirs(n, (0.0, 0.0, 1.5), bcs)
+    f = _rhs(n, dirs, (0.0, 1.0), 53)
+    got, info, _ = _solve(n, dirs, bcs, (0.0, 1.0), prec, (tpt.FFT, tpt.FFT), f)
+    r = O.residual(f, got, dirs, 0.0, 1.0, np.longdouble)
+    rel = float(np.sqrt(np.sum(r ** 2) / np.sum(f ** 2)))
+    ref, _ = O.solve_tensor(f, dirs, 0.0, 1.0)
+    err = float(np.abs(got - ref).max() / np.abs(ref).max())
+    print("fft-mixed lengths", n, prec, info["iters"], rel, err)
+    assert info["rel_residual"] <= 1e-10 and rel <= RES_BAR and err <= ERR_BAR, (info, rel, err)

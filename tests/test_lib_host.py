@@ -186,6 +186,10 @@ def test_transform_selection_rules():
         d, keep = _desc((32, 8, 8), [un, O.uniform_grid(8), O.tanh_grid(8, 1.0, 1.0)], [(1, 1), (1, 1), (1, 1)],
                         prec=prec, xform=(L.TPT_XFORM_GEMM, L.TPT_XFORM_FFT))
         assert L.lib.tpt_plan_create(C.byref(d), -1, C.byref(h)) == L.TPT_ERR_UNSUPPORTED
+    # ... and more than 4096 points
+    d, keep = _desc((8192, 16, 4), [O.uniform_grid(8192), O.uniform_grid(16), O.tanh_grid(4, 1.0, 1.0)],
+                    [(0, 0), (1, 1), (1, 1)], prec=L.TPT_PREC_MIXED_BF16X3, xform=(L.TPT_XFORM_FFT, L.TPT_XFORM_FFT))
+    assert L.lib.tpt_plan_create(C.byref(d), -1, C.byref(h)) == L.TPT_ERR_UNSUPPORTED
 
 
 def test_tile_setters_and_batch_argument_checks():
