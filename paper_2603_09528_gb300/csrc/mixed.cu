@@ -1475,7 +1475,7 @@ __device__ __forceinline__ ZCoef2 zcoef2(float ah, float al, float ch, float cl,
 }
 
 // residual_pair with paired instructions: P0 = (phi_a, phi_b), PP the plane
-// above, XL = (phi_{i-1}, phi_a), XR = (phi_b, phi_{i+2}), YM / YP the -y / +y
+// above, XO = (phi_{i-1}, phi_{i+2}), YM / YP the -y / +y
 // neighbours, F = (f_a, f_b), FS the duplicated fshift.  du holds on entry
 // phi(k) - phi(k-1) (the negated face difference below) and leaves holding
 // phi(k+1) - phi(k).  Term by term the operations are residual_pair's: the
@@ -1485,13 +1485,18 @@ template <int HAS_ALPHA, int WX, int WY, int WZ, int SING>
 __device__ __forceinline__ float2 residual_pair_x2(const TermCoefs2& cx, const TermCoefs2& cy,
                                                    const WallCoefs2& c, const ZCoef2& z, float2 ach,
                                                    float2 anch, float2 ancl, const dfx2& FS,
-                                                   const dfx2& P0, const dfx2& PP, const dfx2& XL,
-                                                   const dfx2& XR, const dfx2& YM, const dfx2& YP,
-                                                   const dfx2& F, dfx2& du) {
+                                                   const dfx2& P0, const dfx2& PP, const dfx2& XO,
+                                                   const dfx2& YM, const dfx2& YP, const dfx2& F, dfx2& du) {
   const dfx2 dup = p_diff(PP, P0);
   dfx2 acc = SING ? p_diff(F, FS) : F;
-  p_term(acc, cx.ch0, cx.nch0, cx.ncl0, p_diff(XL, P0));
-  p_term(acc, cx.ch1, cx.nch1, cx.ncl1, p_diff(XR, P0));
+  // x faces: the -x faces of a and b in one paired difference; the +x face of
+  // a is the negated -x face of b (what differencing it again would give, to
+  // the bit), so only b's +x face is differenced on its own
+  const dfx2 dl = p_diff(dfx2{make_float2(XO.hi.x, P0.hi.x), make_float2(XO.lo.x, P0.lo.x)}, P0);
+  p_term(acc, cx.ch0, cx.nch0, cx.ncl0, dl);
+  const df db = df_diff(df{XO.hi.y, XO.lo.y}, df{P0.hi.y, P0.lo.y});   // phi_{i+2} - phi_b
+  p_term(acc, cx.ch1, cx.nch1, cx.ncl1,
+         dfx2{make_float2(-dl.hi.y, db.hi), make_float2(-dl.lo.y, db.lo)});
   p_term(acc, cy.ch0, cy.nch0, cy.ncl0, p_diff(YM, P0));
   p_term(acc, cy.ch1, cy.nch1, cy.ncl1, p_diff(YP, P0));
   p_term(acc, z.ch5, z.nch5, z.ncl5, du);
@@ -1692,11 +1697,10 @@ __device__ __forceinline__ void residual_tma_body(const ResJob& J, int bx, int b
       }
     }
     if (active) {
-      const dfx2 XL = {make_float2(xm.hi, P0.hi.x), make_float2(xm.lo, P0.lo.x)};   // (phi_{i-1}, phi_a)
-      const dfx2 XR = {make_float2(P0.hi.y, xp.hi), make_float2(P0.lo.y, xp.lo)};   // (phi_b, phi_{i+2})
+      const dfx2 XO = {make_float2(xm.hi, xp.hi), make_float2(xm.lo, xp.lo)};   // (phi_{i-1}, phi_{i+2})
       const TermCoefs2 cx = lds_terms(xyc + lane), cy = lds_terms(xyc + 32 + warp);
       const float2 rv = residual_pair_x2<HAS_ALPHA, WX, WY, WZ, SING>(cx, cy, c, z, ach, anch, ancl, FS, P0, PP,
-                                                                      XL, XR, YM, YP, F, du);
+                                                                      XO, YM, YP, F, du);
       Elem2<FMT>::store(r0, r1, ro, rv.x, rv.y);
       acc2 = fmaf(rv.x, rv.x, acc2);
       acc2 = fmaf(rv.y, rv.y, acc2);
