@@ -261,7 +261,7 @@ PRECISIONS = {"fp64": 0, "mixed_bf16": 1, "mixed_bf16x3": 2, "mixed_tf32": 3}
 # x-inverse GEMM of a solve's first correction writes phi without reading it, so it has
 # its own entry ("x_inverse_first").
 MEASURED_TRAFFIC_PER_POINT = {
-    ("residual", "mixed_bf16x3"): (920.336e6 + 212.314e6) / 384 ** 3,
+    ("residual", "mixed_bf16x3"): (921.222e6 + 213.402e6) / 384 ** 3,
     ("thomas", "mixed_bf16x3"): (226.622e6 + 179.088e6) / 384 ** 3,
     ("x_forward", "mixed_bf16x3"): (227.166e6 + 177.864e6) / 384 ** 3,
     ("y_forward", "mixed_bf16x3"): (227.126e6 + 174.007e6) / 384 ** 3,
