@@ -411,11 +411,11 @@ __device__ __forceinline__ void df_update(float& h, float& l, float v, bool acc)
   h = hi;
 }
 
-// Byte offset of the output line bases in a mixed kernel's shared memory:
-// behind the two slot arrays and the twiddles, 16-byte aligned.
 // Elements of each padded twiddle table (cos, sin of 2 pi m / N, m < N/2).
 __host__ __device__ __forceinline__ int tw_stride(int N) { return N / 2 + N / 64 + 1; }
 
+// Byte offset of the output line bases in a mixed kernel's shared memory:
+// behind the two slot arrays and the twiddles, 16-byte aligned.
 __host__ __device__ __forceinline__ size_t mixed_obase_off(int ts, int N) {
   const size_t b = (2 * static_cast<size_t>(ts) * slot_stride<float>(N) + 2 * static_cast<size_t>(tw_stride(N))) *
                    sizeof(float);
