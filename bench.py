@@ -948,14 +948,15 @@ def projection_leg(tpt, plan, n, stream, steps):
 
 
 # The float-pair residual of the singular headline problem is bound by the
-# float32 datapath (ncu: FMA pipe 67 % busy, math-pipe throttle the largest
+# float32 datapath (ncu: FMA pipe 66 % busy, math-pipe throttle the largest
 # stall), not by HBM.  Its float32 operations per point, counted from the
-# kernel's arithmetic: five exact face differences (8 each: TwoSum and the lo
-# parts), six exact coefficient products with their TwoSum accumulation (12
-# each), the compatibility shift of f (8), the final hi + lo (1) and the r^2
-# sum (1).  Peak: 152 SMs x 128 float32 lanes x 2.070 GHz (unit counts and
-# the maximum SM clock), one operation per lane and clock.
-RESIDUAL_F32_OPS = 5 * 8 + 6 * 12 + 8 + 1 + 1
+# kernel's arithmetic: 4.5 exact face differences (8 each: TwoSum and the lo
+# parts; z 1, y 2, x 1.5 as the face between the two points of a lane is
+# differenced once), six exact coefficient products with their TwoSum
+# accumulation (12 each), the compatibility shift of f (8), the final hi + lo
+# (1) and the r^2 sum (1).  Peak: 152 SMs x 128 float32 lanes x 2.070 GHz
+# (unit counts and the maximum SM clock), one operation per lane and clock.
+RESIDUAL_F32_OPS = 36 + 6 * 12 + 8 + 1 + 1
 F32_LANE_TOPS = 152 * 128 * 2.070e9 / 1e12
 
 
