@@ -177,3 +177,36 @@ def test_requests_of_one_shape_merged_equal_their_own_solves():
         dirs = [O.Direction(sp["dxf"][a], sp["dxc"][a], NNN[a]) for a in range(3)]
         rr = O.residual(f, got, dirs, sp["alpha"], sp["beta"], np.longdouble)
         assert float(np.sqrt(np.sum(rr ** 2) / np.sum(f ** 2))) <= 1e-10 + 1e-14, i
+
+
+def test_served_fourier_directions_equal_their_own_solves():
+    # uniform directions transformed by FFT/DCT (float64 kernels on the float64
+    # plan, float32 ones inside the mixed corrections), served through the
+    # eigenbasis cache beside each other: each result equals its own solve
+    P_, N_ = O.PERIODIC, O.NEUMANN
+    layouts = [((64, 48, 32), [(P_, P_), (N_, N_), (N_, N_)], (0.0, 1.5, 2.0), (tpt.FFT, tpt.GEMM)),
+               ((32, 64, 24), [(N_, N_), (P_, P_), (N_, N_)], (0.0, 0.0, 2.5), (tpt.FFT, tpt.FFT))]
+    specs = []
+    for n, bcs, stretch, xf in layouts:
+        grids = [O.tanh_grid(n[a], 1.0, stretch[a]) for a in range(3)]
+        for prec in (L.TPT_PREC_FP64, L.TPT_PREC_MIXED_BF16X3, L.TPT_PREC_MIXED_TF32):
+            mixed = prec != L.TPT_PREC_FP64
+            specs.append(dict(n=n, dxf=[g[0] for g in grids], dxc=[g[1] for g in grids], bc=bcs, xform=xf,
+                              alpha=0.0, beta=1.0, precision=prec, rtol=1e-10 if mixed else 0.0,
+                              max_refine=30 if mixed else 1))
+    fs = [_rhs(sp, 90 + i) for i, sp in enumerate(specs)]
+    f_host = [torch.from_numpy(np.ascontiguousarray(f.ravel(order="F"))).pin_memory() for f in fs]
+    phi_host = [torch.empty_like(t).pin_memory() for t in f_host]
+    srv = tpt.Server(device=0, slots=3, setup_threads=3, memory_budget=4 << 30, cache_budget=1 << 30, merge=1)
+    tickets = [srv.submit(f, p, **sp) for f, p, sp in zip(f_host, phi_host, specs)]
+    res = [srv.wait(t, timeout=300.0) for t in tickets]
+    srv.close()
+    for i, (sp, r) in enumerate(zip(specs, res)):
+        assert r is not None and r["status"] == L.TPT_OK, (i, r)
+        plan = tpt.Plan(**sp)
+        assert plan.transforms() == sp["xform"]
+        phi, info = plan.solve(tpt.field_to_device(fs[i]))
+        alone = tpt.field_to_host(phi, sp["n"])
+        got = phi_host[i].numpy().reshape(sp["n"], order="F")
+        tol = 1e-12 if sp["precision"] == L.TPT_PREC_FP64 else 1e-11
+        assert np.abs(got - alone).max() <= tol * np.abs(alone).max(), (i, np.abs(got - alone).max())
